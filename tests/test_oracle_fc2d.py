@@ -1,0 +1,143 @@
+"""Pins for the oracle 2D-FC evaluation (Sections 3.2-3.6)."""
+import os
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import fc2d as F
+from oracle import geometry as G
+from oracle.fc_matrices import load_fc_matrices
+from tests.fc2d_check import fine_error, paper_setup
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+@pytest.fixture(scope="module")
+def mats():
+    return load_fc_matrices()
+
+
+@pytest.fixture(scope="module", params=["disk128", "star200", "kite160x144"])
+def case(request):
+    w = W.workload(request.param)
+    geo = G.build_geometry(w)
+    return w, geo, F.matching_stencils(geo)
+
+
+def _ext(case, mats, f):
+    w, geo, st = case
+    return F.extension(geo, mats, W.grid_values(w, f), F.boundary_values(geo, f), st)
+
+
+def test_extension_is_f_inside_and_zero_beyond_the_strip(case, mats):
+    w, geo, st = case
+    fg = W.grid_values(w, W.f_expsincos)
+    ext = _ext(case, mats, W.f_expsincos)
+    assert np.array_equal(ext[geo.inside], fg[geo.inside])
+    mask = geo.inside.copy().ravel()
+    mask[geo.strip_lin] = True
+    assert np.all(ext.ravel()[~mask] == 0)
+    assert not np.any(geo.inside.ravel()[geo.strip_lin])
+
+
+def test_extension_ignores_values_outside(case, mats):
+    w, geo, st = case
+    fg = W.grid_values(w, W.f_expsincos)
+    noisy = np.where(geo.inside, fg, 1e6 * W.normal(11, fg.size).reshape(fg.shape))
+    fb = F.boundary_values(geo, W.f_expsincos)
+    assert np.array_equal(F.extension(geo, mats, fg, fb, st), F.extension(geo, mats, noisy, fb, st))
+
+
+def test_extension_is_linear(case, mats):
+    a, b = 1.7, -0.4
+    f1, f2 = W.f_expsincos, W.trig_sum(5, 3)
+    e1, e2 = _ext(case, mats, f1), _ext(case, mats, f2)
+    e12 = _ext(case, mats, lambda x, y: a * f1(x, y) + b * f2(x, y))
+    assert np.abs(e12 - (a * e1 + b * e2)).max() < 1e-11 * np.abs(e12).max()
+
+
+def test_matching_values_reproduce_polynomials(case):
+    """The two-step interpolation of Section 3.2 is exact for polynomials of total
+    degree <= M-1 wherever every line has M candidates."""
+    w, geo, st = case
+    p = w.params
+    f = lambda x, y: 0.3 + x - 0.5 * y + (x ** 3) * (y ** 4) + 0.2 * x ** 7 - y ** 5 * x
+    fD = F.matching_values(geo, st, W.grid_values(w, f), F.boundary_values(geo, f))
+    q = np.arange(p.d)
+    rx = geo.bx[:, None] + geo.nx_[:, None] * (q - p.d + 1) * p.k1
+    ry = geo.by[:, None] + geo.ny_[:, None] * (q - p.d + 1) * p.k1
+    full = np.array([all(len(t) == p.M for t in s["stars"][1:]) for s in st])
+    assert full.mean() > 0.8
+    err = np.abs(fD - f(rx, ry))[full]
+    assert err.max() < 1e-10 * np.abs(f(rx, ry)).max()
+
+
+def test_strip_interpolation_reproduces_polynomials(case):
+    """Section 3.4: the eta- and theta-interpolants are exact for polynomials of degree
+    <= M-1 in the fine normal index and in the (unwrapped) normal index."""
+    w, geo, st = case
+    p = w.params
+    Cr = p.C * p.n_r
+    Kl = (p.M + 1) // 2 - 1
+    qq = np.arange(Cr + 1, dtype=float)
+    pp = np.arange(p.B, dtype=float)
+    g = lambda a, b: 1 + 0.01 * a ** 3 - 0.002 * a * b + 1e-6 * b ** 7 + 1e-9 * a ** 7
+    F_ = g(pp[:, None], qq[None, :])
+    vals = F.interpolate_strip(geo, F_)
+    k2 = 2 * np.pi / p.B
+    tt = geo.strip_theta / k2
+    p0 = np.floor(tt)
+    ok = (p0 - Kl >= 0) & (p0 + p.M - Kl - 1 < p.B)
+    u = geo.strip_eta * p.n_r / p.k1
+    exact = g(tt, u)
+    assert np.abs(vals - exact)[ok].max() < 1e-9 * np.abs(exact).max()
+
+
+def test_coefficients_equal_brute_force_dft():
+    rng = W.normal(5, 12 * 10).reshape(10, 12)
+    assert np.allclose(F.coefficients(rng), F.dft_bruteforce(rng), rtol=0, atol=1e-15)
+    rng = W.normal(6, 9 * 15).reshape(15, 9)
+    assert np.allclose(F.coefficients(rng), F.dft_bruteforce(rng), rtol=0, atol=1e-15)
+
+
+def test_coefficients_parseval_and_mean():
+    x = W.normal(7, 64 * 48).reshape(48, 64)
+    c = F.coefficients(x)
+    full = np.concatenate([c, np.conj(c[:, 1:-1][:, ::-1])], axis=1)  # nx even
+    full = np.fft.fft2(x) / x.size
+    assert np.isclose(np.sum(np.abs(full) ** 2), np.mean(x ** 2))
+    assert np.isclose(c[0, 0].real, x.mean())
+
+
+def _table(name):
+    rows = []
+    for ln in open(os.path.join(GOLD, name)):
+        if ln.strip() and not ln.startswith("#"):
+            rows.append([float(t) for t in ln.split()])
+    return rows
+
+
+def test_disk_accuracy_matches_paper_table1(mats):
+    """Table 1 (d = 5): relative l_inf errors within a factor 3 of the printed ones, and
+    the order between h = 2e-2 and 1e-2 near 5."""
+    rows = [r for r in _table("paper_table1_disk.txt") if r[0] == 5 and r[1] >= 1e-2]
+    errs = []
+    for d, h, B, ref in rows:
+        w = paper_setup(W.disk(), h, d=int(d), B=int(B))
+        e = fine_error(w, mats, W.f_sin5pi)
+        errs.append(e)
+        assert ref / 3 <= e <= ref * 3, (h, e, ref)
+    order = np.log2(errs[0] / errs[1])
+    assert 4.0 < order < 7.0
+
+
+def test_kite_accuracy_matches_paper_table2(mats):
+    """Table 2 (d = 5, M = 8): absolute errors within a factor 4 of the printed ones.
+    (The paper's own errors move by 3x between M = d+2 and d+3 at h = 5e-3; the
+    unstated m_F and gather details allow the same spread.)"""
+    rows = [r for r in _table("paper_table2_kite.txt") if r[0] == 5 and r[1] >= 5e-3]
+    for d, h, ref in rows:
+        w = paper_setup(W.kite(0.35, 0.7), h, d=int(d))
+        e = fine_error(w, mats, W.f_kite_paper, relative=False)
+        assert ref / 4 <= e <= ref * 4, (h, e, ref)
