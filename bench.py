@@ -1,0 +1,375 @@
+#!/usr/bin/env python
+"""Benchmark: 2D-FC extension + 2D DFT throughput (grid points per second) on the kite
+domain x = cos t + 0.65 cos 2t - 0.65, y = 1.5 sin t at 4096^2 with 8192 normals.
+
+One step = the whole hot path for one function: matching values, blending, strip
+interpolation, fused extension + row DFT, column DFT (fc2d_extend_coeffs).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp64|mixed]
+    python bench.py --impl reference ...     # the FP64 CPU oracle as the reference arm
+
+Prints ONE JSON line (rank 0).  With --gpus N > 1 (launched by torch.distributed.run)
+each rank runs an independent replica of the workload on its own GPU: the path has no
+exchange step, so there is no collective beyond the timing barrier and max-reduce.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import workloads as W  # noqa: E402
+
+WORKLOAD = "kite4096"
+METRIC = "2D-FC extend+FFT grid-points/sec at 4096^2"
+UNIT = "grid-points/s"
+FP64_PEAK_TFLOPS = 1.25   # GB300 FP64 (nominal; 152 SMs x 2 DFMA/clk x 2 flop x ~2.06 GHz)
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            m = json.load(fh)
+        return float(m["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# --------------------------------------------------------------------------- #
+# clocks during the timed region
+# --------------------------------------------------------------------------- #
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for ln in self.proc.stdout:
+            self.lines.append(ln.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# --------------------------------------------------------------------------- #
+# the oracle (cpu_baseline and the reference arm)
+# --------------------------------------------------------------------------- #
+def oracle_setup(w):
+    from oracle import fc2d as OF
+    from oracle import geometry as OG
+    from oracle.fc_matrices import load_fc_matrices
+    geo = OG.build_geometry(w)
+    st = OF.matching_stencils(geo)
+    return geo, st, load_fc_matrices()
+
+
+def oracle_step(w, geo, st, mats, f):
+    from oracle import fc2d as OF
+    fg = W.grid_values(w, f)
+    fb = OF.boundary_values(geo, f)
+    t = time.perf_counter()
+    out = OF.coefficients(OF.extension(geo, mats, fg, fb, st))
+    return out, time.perf_counter() - t
+
+
+def bench_functions(w, n):
+    return [W.gaussian_sum(w.boundary, 16, 3 + k) for k in range(n)]
+
+
+def cpu_baseline(w, budget_s=15.0):
+    """The oracle as it stands, single core, on the full workload grid: extension + DFT
+    per function (plan excluded, as on the GPU), functions until the budget is used."""
+    geo, st, mats = oracle_setup(w)
+    npts = w.grid.nx * w.grid.ny
+    total, n, first = 0.0, 0, None
+    for f in bench_functions(w, 64):
+        out, dt = oracle_step(w, geo, st, mats, f)
+        if first is None:
+            first = out
+        total += dt
+        n += 1
+        if total >= budget_s:
+            break
+    return {"value": n * npts / total, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{n} function(s) of the {w.name} workload, full grid, plan excluded; "
+                      f"{total:.1f} s of CPU"}, first
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    # step = one oracle extension + DFT of the kite; the grid is the largest of
+    # 4096^2, 2048^2, 1024^2 that keeps the whole run near two minutes
+    est4096 = 2.5  # seconds per step on one core at 4096^2 (measured on the dev host)
+    n_steps = args.steps + args.warmup
+    name = "kite4096"
+    for cand, scale in (("kite4096", 1.0), ("kite2048", 0.25)):
+        name = cand
+        if n_steps * est4096 * scale <= 120:
+            break
+    else:
+        name = "kite1024"
+    w = W.workload(name)
+    geo, st, mats = oracle_setup(w)
+    f = bench_functions(w, 1)[0]
+    for _ in range(args.warmup):
+        oracle_step(w, geo, st, mats, f)
+    total = 0.0
+    for _ in range(args.steps):
+        total += oracle_step(w, geo, st, mats, f)[1]
+    npts = w.grid.nx * w.grid.ny
+    value = args.steps * npts / total
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "impl": "reference",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample_grid": f"{w.grid.nx}x{w.grid.ny}",
+                       "domain": "kite a=0.65 b=1.5", "normals": w.params.B,
+                       "functions": "sum of 16 Gaussians, seed 3"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{w.name}: one function per step, plan excluded"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------------------- #
+# the GPU arm
+# --------------------------------------------------------------------------- #
+def algorithmic(plan, w, fp64):
+    """Algorithmic bytes and flops per launch of each kernel (one function)."""
+    g = w.grid
+    nx, ny = g.nx, g.ny
+    nh = nx // 2
+    esz = 8 if fp64 else 4
+    csz = 2 * esz
+    spec = ny * (nh + 1) * csz
+    B = w.params.B
+    Cr = w.params.C * w.params.n_r
+    M = w.params.M
+    fft_rows_flops = ny * (5.0 * nh * math.log2(nh) + 10.0 * (nh + 1))
+    fft_cols_flops = (nh + 1) * 5.0 * ny * math.log2(ny)
+    return {
+        "fft_rows_fused": {"bytes": 8 * plan.n_inside + (esz + 4) * plan.n_strip + spec,
+                           "flops": fft_rows_flops},
+        "fft_cols": {"bytes": 2 * spec, "flops": fft_cols_flops},
+        "interp": {"bytes": plan.n_strip * (16 + esz), "flops": plan.n_strip * 2.0 * (M * M + M)},
+        "gather_blend": {"bytes": B * ((M - 1) * M * 12 + (w.params.d - 1) * M * 8 + (Cr + 1) * esz),
+                         "flops": B * 2.0 * ((M - 1) * M + (w.params.d - 1) * M + Cr * w.params.d)},
+    }
+
+
+def run_gpu(args):
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", torch.cuda.current_device())
+
+    from paper_2010_03901_gb300.build import build
+    build()
+    from paper_2010_03901_gb300 import fc2d
+
+    fp64 = args.precision == "fp64"
+    w = W.workload(WORKLOAD)
+    g, p = w.grid, w.params
+    t0 = time.perf_counter()
+    plan = fc2d.fc2d_plan(w.boundary.arrays(), (g.a0, g.b0, g.h, g.nx, g.ny),
+                          dict(B=p.B, k1=p.k1),
+                          precision=fc2d.FC2D_FP64 if fp64 else fc2d.FC2D_MIXED)
+    plan_s = time.perf_counter() - t0
+    f = bench_functions(w, 1)[0]
+    xy = plan.fc2d_boundary_points()
+    fg_h = torch.from_numpy(W.grid_values(w, f)).pin_memory()
+    fb_h = torch.from_numpy(np.ascontiguousarray(f(xy[:, 0], xy[:, 1]))).pin_memory()
+    fg = fg_h.to(dev)
+    fb = fb_h.to(dev)
+    cdt = torch.float64 if fp64 else torch.float32
+    fhat = torch.zeros((g.ny, g.nx // 2 + 1, 2), dtype=cdt, device=dev)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2
+    stream = torch.cuda.current_stream()
+
+    for _ in range(args.warmup):
+        plan.fc2d_extend_coeffs(1, fg, fb, fhat, stream)
+    plan.fc2d_sync_status(stream)
+
+    K = args.steps
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    sampler = ClockSampler(dev.index)
+    plan.fc2d_profile(True)
+    plan.fc2d_profile_read()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    time.sleep(0.3)
+    wall0 = time.perf_counter()
+    for k in range(K):
+        flush.fill_(float(k))
+        starts[k].record(stream)
+        plan.fc2d_extend_coeffs(1, fg, fb, fhat, stream)
+        ends[k].record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = sampler.stop()
+    plan.fc2d_profile(False)
+    prof = plan.fc2d_profile_read()
+    plan.fc2d_sync_status(stream)
+    ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
+    t_max = ms
+    if world > 1:
+        tt = torch.tensor([ms], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        t_max = float(tt.item())
+    npts = g.nx * g.ny
+    value = world * K * npts / (t_max / 1e3)
+
+    # end to end through the public API with host buffers
+    Ke = min(K, 30)
+    fhat_h = torch.empty(fhat.shape, dtype=cdt).pin_memory()
+    fg_d = torch.empty_like(fg)
+    fb_d = torch.empty_like(fb)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(Ke):
+        fg_d.copy_(fg_h, non_blocking=True)
+        fb_d.copy_(fb_h, non_blocking=True)
+        plan.fc2d_extend_coeffs(1, fg_d, fb_d, fhat, stream)
+        fhat_h.copy_(fhat, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1) / Ke
+    e2e_val = world * npts / (e2e_ms / 1e3)
+    if world > 1:
+        tt = torch.tensor([e2e_ms], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        e2e_val = world * npts / (float(tt.item()) / 1e3)
+
+    # roofline of the dominant kernel
+    hbm, src = peaks()
+    alg = algorithmic(plan, w, fp64)
+    dom = max(prof, key=lambda k: prof[k][1])
+    launches, tot_ms = prof[dom]
+    avg_s = tot_ms / launches / 1e3
+    a = alg.get(dom, {"bytes": 0, "flops": 0})
+    t_hbm = a["bytes"] / (hbm * 1e9)
+    t_alu = a["flops"] / (FP64_PEAK_TFLOPS * 1e12) if fp64 else 0.0
+    if fp64 and t_alu > t_hbm:
+        roof = {"bound": "alu", "achieved": a["flops"] / avg_s / 1e12, "peak": FP64_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "peak_source": "nominal FP64 rate"}
+    else:
+        roof = {"bound": "hbm", "achieved": a["bytes"] / avg_s / 1e9, "peak": hbm,
+                "unit": "GB/s", "peak_source": src}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["kernel"] = dom
+    roof["traffic"] = None
+    kernels = {k: {"launches": v[0], "avg_us": 1e3 * v[1] / v[0],
+                   "share": v[1] / sum(x[1] for x in prof.values())} for k, v in prof.items()}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
+            "warmup": args.warmup, "ms_per_step": t_max / K, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if fp64 else "f32+tf32",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "grid": f"{g.nx}x{g.ny}", "normals": p.B,
+                       "domain": "kite a=0.65 b=1.5", "functions_per_step": 1,
+                       "function": "sum of 16 Gaussians (seed 3)", "precision": args.precision,
+                       "d": p.d, "C": p.C, "M": p.M, "n_r": p.n_r,
+                       "l2": "flushed between steps (256 MB write, outside the events)",
+                       "parallelism": f"replicas x{world}"},
+            "clocks": clocks, "roofline": roof, "kernels": kernels,
+            "gpu_launches": sum(v[0] for v in prof.values()),
+            "e2e": {"value": e2e_val, "unit": UNIT,
+                    "h2d_bytes_per_step": int(fg.numel() * 8 + fb.numel() * 8),
+                    "d2h_bytes_per_step": int(fhat.numel() * fhat.element_size())},
+            "plan_s": plan_s, "wall_s_timed": wall}
+    if rank == 0 and world == 1 and not args.no_cpu:
+        base, spec_ref = cpu_baseline(w)
+        line["cpu_baseline"] = base
+        got = fhat.cpu().numpy().astype(np.float64)
+        got = got[..., 0] + 1j * got[..., 1]
+        line["err_vs_oracle"] = float(np.abs(got - spec_ref).max() / np.abs(spec_ref).max())
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=400)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="fc2d", choices=["fc2d", "reference"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    args = ap.parse_args(argv)
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,170 @@
+/*
+ * fc2d.h -- C ABI of the GB300 two-dimensional Fourier Continuation (2D-FC) library.
+ *
+ * Method: O. P. Bruno and J. Paul, "Two-dimensional Fourier Continuation and
+ * applications" (arXiv 2010.03901).  A smooth f given on the Cartesian grid points
+ * inside a smooth closed curve (and on a few points of the curve) is continued to a
+ * bi-periodic function on the whole grid: 1D blending-to-zero along the boundary
+ * normals (Section 2.2, eq. (2.6); Remark 2.2), interpolation of the normal values
+ * onto the grid points of the outer strip (Sections 3.3-3.4), and a 2D DFT (eq. (3.1)).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Grid:      x_i = a0 + i h, y_j = b0 + j h, 0 <= i < nx, 0 <= j < ny (eq. (3.7)).
+ *            Grid arrays are row-major [n_f][ny][nx] (x fastest).
+ * Spectrum:  fhat[f][m][l] = (1/(nx ny)) sum_{j,i} ext[f][j][i] e^{-2 pi i (l i/nx + m j/ny)},
+ *            0 <= l <= nx/2, 0 <= m < ny: the half spectrum [n_f][ny][nx/2+1] of
+ *            interleaved (re, im) pairs in DFT index order (m > ny/2 stands for m - ny).
+ *            The phase is relative to the grid origin (a0, b0).
+ * Boundary data: f_bdry[f][k] holds f at the boundary points listed by
+ *            fc2d_boundary_points: first the B feet q(theta_p) of the normals
+ *            (theta_p = 2 pi p/B, eq. (3.4)), then the crossings of each grid column
+ *            x = x_i with the curve (i ascending, y ascending), then those of each
+ *            grid row (j ascending, x ascending).
+ * Memory:    pointers named *_dev are device pointers owned by the caller; *_host are
+ *            host pointers owned by the caller.  The plan owns only its own tables
+ *            and workspace.
+ * Precision: FC2D_FP64 computes every stage in double and uses double for every
+ *            array.  FC2D_MIXED reads the same double inputs (the blending matrix has
+ *            entries near 4e3, so rounding the data to float first would cost ~1e-4),
+ *            forms the matching values and Gram coefficients in double, runs the
+ *            continuation contraction on the tensor cores in TF32 with hi/lo split
+ *            operands and FP32 accumulation, and the FFT in float: ext is float and
+ *            fhat is (float, float) pairs.
+ * Streams:   every compute call is asynchronous on the given cudaStream_t (passed as
+ *            void*; NULL = legacy default stream) and returns after launching.
+ *            fc2d_plan and the host queries are synchronous.
+ * Errors:    argument and geometry errors are returned synchronously; the text is in
+ *            fc2d_last_error().  Device-side conditions (a Newton search that did not
+ *            converge) are latched in the plan and returned by fc2d_sync_status.
+ *            No entry point aborts, traps or exits the process.
+ * Threads:   a plan may be used by one host thread at a time.
+ */
+#ifndef FC2D_H
+#define FC2D_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fc2d_plan_s* fc2d_plan_t;
+
+typedef enum {
+  FC2D_OK = 0,
+  FC2D_ERR_ARG = 1,            /* bad argument (null pointer, size, parameter)        */
+  FC2D_ERR_GEOMETRY = 2,       /* strip leaves the grid, stencil leaves the domain... */
+  FC2D_ERR_NOT_CONVERGED = 3,  /* a Newton foot search hit its iteration cap          */
+  FC2D_ERR_TIMEOUT = 4,        /* a bounded device wait gave up                       */
+  FC2D_ERR_NOMEM = 5,          /* device or host allocation failed                    */
+  FC2D_ERR_CUDA = 6,           /* a CUDA runtime call failed                          */
+  FC2D_ERR_UNSUPPORTED = 7     /* grid size or option this build does not handle      */
+} fc2d_status;
+
+typedef enum { FC2D_FP64 = 0, FC2D_MIXED = 1 } fc2d_precision;
+
+/* Closed curve as a trigonometric polynomial of degree n_modes-1 (eq. (3.2)):
+ *   x(t) = sum_k cx[k] cos(k t) + sx[k] sin(k t),  y(t) likewise with cy, sy.
+ * Either orientation; the plan re-parametrises a clockwise curve by t -> -t. */
+typedef struct {
+  int n_modes;
+  const double *cx, *sx, *cy, *sy;  /* host arrays of length n_modes */
+} fc2d_boundary;
+
+typedef struct {
+  double a0, b0, h;  /* origin and step of the grid H (eq. (3.7))  */
+  int nx, ny;        /* both even, each of the form 2^a 3^b 5^c    */
+} fc2d_grid;
+
+/* Section 3.6 parameter list.  A zero field takes the paper's default (Remark 3.3):
+ * d=5, C=27, Z=12, n_os=20, n_r=6, M=d+3, B=round(2 pi/h), m_F=20, k1=h. */
+typedef struct {
+  int d, C, Z, n_os, n_r, M, B, m_F;
+  double k1;      /* normal step of V-/V+ (eqs. (3.5)-(3.6)) */
+  int precision;  /* fc2d_precision                          */
+} fc2d_params;
+
+typedef struct {
+  fc2d_grid grid;
+  fc2d_params params;  /* with defaults filled in */
+  int64_t n_strip;     /* grid points in H cap V+ (continuation points)            */
+  int64_t n_inside;    /* grid points in the closed domain                         */
+  int64_t n_bdry;      /* boundary data points (B + column + row crossings)        */
+  int64_t workspace_bytes_per_function;
+} fc2d_info;
+
+/* Geometrical setup, Section 3.5 steps 1-4: boundary grid I_B, curvilinear grids,
+ * the FC matrices Q and A_r (Section 2.2, Remark 2.2; computed here in double-double
+ * arithmetic), the inside test, the feet of the normals through the strip points
+ * (Newton's method in FP64 on the GPU) and the matching stencils of Section 3.2.
+ * Synchronous.  Uses the current CUDA device.  *out receives a new plan.
+ * Returns FC2D_ERR_GEOMETRY when the strip of width C*k1 leaves the grid or a
+ * stencil leaves the domain. */
+fc2d_status fc2d_plan(const fc2d_boundary* boundary, const fc2d_grid* grid,
+                      const fc2d_params* params, fc2d_plan_t* out);
+
+fc2d_status fc2d_plan_info(fc2d_plan_t plan, fc2d_info* out);
+
+/* Boundary data points (x, y), [n_bdry][2], in the order described above. */
+fc2d_status fc2d_boundary_points(fc2d_plan_t plan, double* xy_host);
+
+/* The plan's FC matrices: Q [d][d] and A_r [C n_r][d] (row-major, double). */
+fc2d_status fc2d_fc_matrices(fc2d_plan_t plan, double* Q_host, double* Ar_host);
+
+/* Strip points H cap V+: linear grid index j*nx+i (ascending), foot parameter
+ * theta^Q in [0, 2 pi) and distance eta_Q (Section 3.4). */
+fc2d_status fc2d_strip_points(fc2d_plan_t plan, int32_t* lin_host, double* theta_host,
+                              double* eta_host);
+
+/* Steps 5 of Section 3.5 (Section 3.2 + eq. (2.6)): matching values and blending.
+ * F_dev receives [n_f][B][C n_r + 1] strip values (double for FP64, float for MIXED):
+ * F[f][p][0] = f at q(theta_p), F[f][p][q] = (A_r Q^T f_{D_p})_q. */
+fc2d_status fc2d_blend(fc2d_plan_t plan, int n_f, const double* f_grid_dev,
+                       const double* f_bdry_dev, void* F_dev, void* stream);
+
+/* Step 6 (Section 3.4): continuation values at the strip points from F_dev.
+ * vals_dev receives [n_f][n_strip] in the order of fc2d_strip_points. */
+fc2d_status fc2d_interp(fc2d_plan_t plan, int n_f, const void* F_dev, void* vals_dev,
+                        void* stream);
+
+/* Steps 5-6: the extension.  ext_dev [n_f][ny][nx] receives f at the grid points in
+ * the closed domain, the continuation on the strip and 0 elsewhere.  Grid values
+ * outside the domain are never read.  For FP64, ext_dev may equal f_grid_dev. */
+fc2d_status fc2d_extend(fc2d_plan_t plan, int n_f, const double* f_grid_dev,
+                        const double* f_bdry_dev, void* ext_dev, void* stream);
+
+/* Step 7: the 2D DFT (eq. (3.1)) of an extension, fhat_dev [n_f][ny][nx/2+1][2]. */
+fc2d_status fc2d_coeffs(fc2d_plan_t plan, int n_f, const void* ext_dev, void* fhat_dev,
+                        void* stream);
+
+/* Steps 5-7 fused: the spectrum of the extension of f, without writing the extended
+ * grid (the strip values go to plan workspace, the row DFT reads the domain points
+ * from f_grid_dev and the strip values from the workspace).  Same result as
+ * fc2d_extend followed by fc2d_coeffs. */
+fc2d_status fc2d_extend_coeffs(fc2d_plan_t plan, int n_f, const double* f_grid_dev,
+                               const double* f_bdry_dev, void* fhat_dev, void* stream);
+
+/* Kernel timing (tracing).  While enabled, every kernel the plan launches is
+ * bracketed by a pair of CUDA events recorded on its launching stream.
+ * fc2d_profile_read waits for those events and returns, per kernel name, the number
+ * of launches and their summed device time in milliseconds, then clears the record.
+ * names_host receives up to max_kernels NUL-terminated names of at most 63 chars
+ * (64 bytes each).  *n_out receives the number of kernel names. */
+fc2d_status fc2d_profile(fc2d_plan_t plan, int enable);
+fc2d_status fc2d_profile_read(fc2d_plan_t plan, int max_kernels, char* names_host,
+                              int64_t* launches_host, double* ms_host, int* n_out);
+
+/* Waits for the stream and returns the plan's latched device status. */
+fc2d_status fc2d_sync_status(fc2d_plan_t plan, void* stream);
+
+void fc2d_destroy(fc2d_plan_t plan);
+
+/* Text of the last error on this host thread ("" if none). */
+const char* fc2d_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FC2D_H */

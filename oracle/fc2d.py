@@ -178,19 +178,28 @@ def interpolate_strip(geo, F):
     M, B, Cr = p.M, p.B, p.C * p.n_r
     Kl = (M + 1) // 2 - 1
     k2 = 2 * np.pi / B
-    out = np.zeros(len(geo.strip_lin))
-    nodes = np.arange(M, dtype=np.float64)
-    for n, (th, eta) in enumerate(zip(geo.strip_theta, geo.strip_eta)):
-        tt = th / k2
-        p0 = math.floor(tt)
-        wth = lagrange_weights(nodes, tt - (p0 - Kl))
-        u = eta * p.n_r / p.k1
-        s = min(max(math.floor(u) - Kl, 0), Cr + 1 - M)
-        weta = lagrange_weights(nodes, u - s)
-        rows = [(p0 - Kl + a) % B for a in range(M)]
-        vals = F[rows][:, s:s + M] @ weta
-        out[n] = float(np.dot(wth, vals))
-    return out
+    n = len(geo.strip_lin)
+    tt = geo.strip_theta / k2
+    p0 = np.floor(tt).astype(np.int64)
+    u = geo.strip_eta * p.n_r / p.k1
+    s = np.clip(np.floor(u).astype(np.int64) - Kl, 0, Cr + 1 - M)
+    wth = _lagrange_equispaced(M, tt - (p0 - Kl))     # [n][M]
+    weta = _lagrange_equispaced(M, u - s)              # [n][M]
+    rows = np.mod(p0[:, None] - Kl + np.arange(M)[None, :], B)    # [n][M]
+    cols = s[:, None] + np.arange(M)[None, :]                      # [n][M]
+    vals = F[rows[:, :, None], cols[:, None, :]]                   # [n][M][M]
+    return np.einsum("na,nab,nb->n", wth, vals, weta)
+
+
+def _lagrange_equispaced(M, t):
+    """Lagrange weights of the nodes 0..M-1 at each t (vector): [len(t)][M]."""
+    t = np.asarray(t, dtype=np.float64)
+    w = np.ones((len(t), M))
+    for k in range(M):
+        for m in range(M):
+            if m != k:
+                w[:, k] *= (t - m) / (k - m)
+    return w
 
 
 def extension(geo, mats, f_grid, f_bdry, stencils=None):

@@ -10,7 +10,10 @@ Readings (the paper leaves these open):
   n = (y', -x')/|q'| then points out of the domain, as V+ in eq. (3.3) requires.
 * Inside test (which grid points are in the closed domain): a grid point is inside
   when it lies in a closed interval [X_{2m}, X_{2m+1}] of the sorted crossings of
-  its grid row with the curve (Jordan curve theorem / ray casting).
+  its grid row with the curve (Jordan curve theorem / ray casting).  Crossings are
+  the sign changes of the line's coordinate minus the curve's on 16 B uniform
+  samples, refined; two consecutive crossings closer than 1e-7 times the grid box
+  are a tangency artefact and are both dropped.
 * The foot theta^Q of an exterior point Q is the parameter of the nearest point of
   the curve (the exact quantity the interpolant T(tau) of eq. (3.9) approximates),
   eta_Q = |Q - q(theta^Q)|.  The seed is the nearest of 16 B samples of the curve
@@ -86,11 +89,12 @@ def make_curve(boundary) -> Curve:
 # --------------------------------------------------------------------------- #
 # Crossings of grid lines with the curve
 # --------------------------------------------------------------------------- #
-def _roots(f, fp, n_samples: int):
-    """All roots in [0, 2 pi) of the periodic function f, by sign changes on a
-    uniform sample followed by bisection and two Newton steps."""
+def _roots(f, fp, n_samples: int, samples=None):
+    """All roots in [0, 2 pi) of the periodic function f, by sign changes on the
+    uniform sample t_s = 2 pi s/n_s, s = 0..n_s, followed by bisection and two Newton
+    steps.  ``samples`` may hold f(t_s) already."""
     th = 2 * np.pi * np.arange(n_samples + 1) / n_samples
-    v = f(th)
+    v = f(th) if samples is None else samples
     pos = v > 0
     idx = np.nonzero(pos[:-1] != pos[1:])[0]
     if len(idx) == 0:
@@ -113,14 +117,30 @@ def _roots(f, fp, n_samples: int):
     return np.mod(r, 2 * np.pi)
 
 
-def crossings(curve: Curve, axis: str, value: float, n_samples: int):
+def _drop_tangencies(X, tol):
+    """Remove any two consecutive crossings closer than tol: a line that only touches
+    the curve (a double root) can show up as such a pair when a sample lands exactly
+    on the touching point; its position is then undetermined to ~1e-8."""
+    out = []
+    for x in X:
+        if out and x - out[-1] < tol:
+            out.pop()
+        else:
+            out.append(x)
+    return np.array(out)
+
+
+def crossings(curve: Curve, axis: str, value: float, n_samples: int, samples=None,
+              tol: float = 0.0):
     """Sorted crossing coordinates of the curve with the line y = value (axis='row',
-    returns x's) or x = value (axis='col', returns y's)."""
+    returns x's) or x = value (axis='col', returns y's).  ``samples``: the curve
+    coordinate (y for rows, x for columns) at the uniform sample points."""
+    s = None if samples is None else samples - value
     if axis == "row":
-        th = _roots(lambda t: curve.y(t) - value, lambda t: curve.y(t, 1), n_samples)
-        return np.sort(curve.x(th))
-    th = _roots(lambda t: curve.x(t) - value, lambda t: curve.x(t, 1), n_samples)
-    return np.sort(curve.y(th))
+        th = _roots(lambda t: curve.y(t) - value, lambda t: curve.y(t, 1), n_samples, s)
+        return _drop_tangencies(np.sort(curve.x(th)), tol)
+    th = _roots(lambda t: curve.x(t) - value, lambda t: curve.x(t, 1), n_samples, s)
+    return _drop_tangencies(np.sort(curve.y(th)), tol)
 
 
 @dataclass
@@ -152,6 +172,12 @@ def n_crossing_samples(params) -> int:
     return 16 * params.B
 
 
+def tangency_tolerance(grid) -> float:
+    """Crossing pairs closer than 1e-7 times the larger side of the grid box are
+    tangency artefacts (see _drop_tangencies)."""
+    return 1e-7 * max(grid.nx, grid.ny) * grid.h
+
+
 def build_geometry(w) -> GridGeometry:
     """Section 3.1 (boundary grid I_B, eq. (3.4); Cartesian grid H, eq. (3.7)),
     the inside test, and Sections 3.3-3.4 (feet of normals for H cap V+)."""
@@ -160,8 +186,11 @@ def build_geometry(w) -> GridGeometry:
     xs = g.a0 + g.h * np.arange(g.nx)
     ys = g.b0 + g.h * np.arange(g.ny)
     ns = n_crossing_samples(p)
-    row_cross = [crossings(curve, "row", y, ns) for y in ys]
-    col_cross = [crossings(curve, "col", x, ns) for x in xs]
+    ts = 2 * np.pi * np.arange(ns + 1) / ns
+    sx, sy = curve.point(ts)
+    tol = tangency_tolerance(g)
+    row_cross = [crossings(curve, "row", y, ns, sy, tol) for y in ys]
+    col_cross = [crossings(curve, "col", x, ns, sx, tol) for x in xs]
     inside = np.zeros((g.ny, g.nx), dtype=bool)
     for j, X in enumerate(row_cross):
         for m in range(0, len(X) - 1, 2):

@@ -1,0 +1,327 @@
+// C-ABI entry points that launch the 2D-FC kernels (declared in include/fc2d.h).
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "fc2d_kernels.cuh"
+#include "plan_internal.h"
+
+using namespace fc2d;
+
+namespace fc2d {
+
+fc2d_status ensure_workspace(fc2d_plan_s* p, size_t bytes) {
+  if (p->ws.bytes >= bytes) return FC2D_OK;
+  if (p->ws.base) {
+    cudaDeviceSynchronize();
+    cudaFree(p->ws.base);
+    p->ws.base = nullptr;
+    p->ws.bytes = 0;
+  }
+  if (cudaMalloc(&p->ws.base, bytes) != cudaSuccess)
+    return set_error(FC2D_ERR_NOMEM, "workspace cudaMalloc failed");
+  p->ws.bytes = bytes;
+  return FC2D_OK;
+}
+
+}  // namespace fc2d
+
+namespace {
+
+size_t al(size_t b) { return (b + 255) / 256 * 256; }
+
+struct Layout {
+  size_t F, vals, inter, coef, bvals, total;
+  size_t oF, ovals, ointer, ocoef, obvals;
+};
+
+Layout layout(const fc2d_plan_s* p, int n_f) {
+  Layout L{};
+  const size_t esz = p->prm.precision == FC2D_MIXED ? 4 : 8;
+  const size_t pitch = ((size_t)p->grid.nx / 2 + 1 + 7) / 8 * 8;
+  L.F = al((size_t)n_f * p->prm.B * (p->Cr + 1) * esz);
+  L.vals = al((size_t)n_f * std::max<size_t>(1, p->strip_lin.size()) * esz);
+  L.inter = al((size_t)n_f * p->grid.ny * pitch * 2 * esz);
+  L.coef = al((size_t)n_f * p->prm.B * kMaxD * 8);
+  L.bvals = al((size_t)n_f * p->prm.B * 8);
+  L.oF = 0;
+  L.ovals = L.oF + L.F;
+  L.ointer = L.ovals + L.vals;
+  L.ocoef = L.ointer + L.inter;
+  L.obvals = L.ocoef + L.coef;
+  L.total = L.obvals + L.bvals;
+  return L;
+}
+
+char* ws(fc2d_plan_s* p, size_t off) { return static_cast<char*>(p->ws.base) + off; }
+
+GatherArgs gather_args(fc2d_plan_s* p, const double* fg, const double* fb, void* F,
+                       double* coef, double* bvals) {
+  GatherArgs a{};
+  a.B = p->prm.B;
+  a.M = p->prm.M;
+  a.d = p->prm.d;
+  a.Cr = p->Cr;
+  a.n_bdry = p->n_bdry;
+  a.grid_stride = (int64_t)p->grid.nx * p->grid.ny;
+  a.f_grid = fg;
+  a.f_bdry = fb;
+  a.gidx = p->dev.gidx;
+  a.gw = p->dev.gw;
+  a.wn = p->dev.wn;
+  a.Q = p->dev.Q;
+  a.Ar = p->dev.Ar;
+  a.F = F;
+  a.coef = coef;
+  a.coef_ld = kMaxD;
+  a.bvals = bvals;
+  return a;
+}
+
+InterpArgs interp_args(fc2d_plan_s* p) {
+  InterpArgs a{};
+  a.n_strip = (int)p->strip_lin.size();
+  a.M = p->prm.M;
+  a.B = p->prm.B;
+  a.Cr = p->Cr;
+  a.inv_k2 = p->prm.B / (2.0 * M_PI);
+  a.nr_over_k1 = p->prm.n_r / p->prm.k1;
+  a.theta = p->dev.s_theta;
+  a.eta = p->dev.s_eta;
+  return a;
+}
+
+RowArgs row_args(fc2d_plan_s* p) {
+  RowArgs a{};
+  a.nx = p->grid.nx;
+  a.ny = p->grid.ny;
+  a.grid_stride = (int64_t)p->grid.nx * p->grid.ny;
+  a.n_strip = (int64_t)p->strip_lin.size();
+  a.row_iv_off = p->dev.row_iv_off;
+  a.row_iv = p->dev.row_iv;
+  a.row_strip_off = p->dev.row_strip_off;
+  a.s_lin = p->dev.s_lin;
+  return a;
+}
+
+FftArgs fft_args(fc2d_plan_s* p) {
+  FftArgs a{};
+  const bool f64 = p->prm.precision == FC2D_FP64;
+  a.nx = p->grid.nx;
+  a.ny = p->grid.ny;
+  a.pitch = (p->grid.nx / 2 + 1 + 7) / 8 * 8;
+  a.nrx = p->fx.n_radix;
+  a.nry = p->fy.n_radix;
+  for (int i = 0; i < a.nrx; ++i) a.rx[i] = p->fx.radix[i];
+  for (int i = 0; i < a.nry; ++i) a.ry[i] = p->fy.radix[i];
+  a.twx = f64 ? (const void*)p->fx.tw64 : (const void*)p->fx.tw32;
+  a.twy = f64 ? (const void*)p->fy.tw64 : (const void*)p->fy.tw32;
+  a.rtw = f64 ? (const void*)p->rtw64 : (const void*)p->rtw32;
+  a.scale = 1.0 / ((double)p->grid.nx * p->grid.ny);
+  return a;
+}
+
+fc2d_status check_nf(fc2d_plan_s* p, int n_f) {
+  if (!p) return set_error(FC2D_ERR_ARG, "null plan");
+  if (n_f < 1) return set_error(FC2D_ERR_ARG, "n_f must be >= 1");
+  if ((int64_t)n_f * p->grid.nx * p->grid.ny > INT64_C(1) << 40)
+    return set_error(FC2D_ERR_ARG, "n_f too large");
+  return FC2D_OK;
+}
+
+fc2d_status launched(const char* what) { return cuda_check(cudaGetLastError(), what); }
+
+// Steps 5 and 6 into workspace: strip values F, then the strip-point values.
+fc2d_status strip_values(fc2d_plan_s* p, int n_f, const double* fg, const double* fb,
+                         const Layout& L, cudaStream_t s) {
+  const bool f64 = p->prm.precision == FC2D_FP64;
+  void* F = ws(p, L.oF);
+  if (f64) {
+    ProfScope ps(p, "gather_blend", s);
+    launch_gather_blend(gather_args(p, fg, fb, F, nullptr, nullptr), n_f, true, s);
+  } else {
+    return set_error(FC2D_ERR_UNSUPPORTED, "mixed precision blend not built yet");
+  }
+  {
+    ProfScope ps(p, "interp", s);
+    launch_interp(interp_args(p), n_f, f64, F, ws(p, L.ovals), s);
+  }
+  return launched("strip values");
+}
+
+}  // namespace
+
+extern "C" fc2d_status fc2d_blend(fc2d_plan_t p, int n_f, const double* fg, const double* fb,
+                                  void* F, void* stream) {
+  fc2d_status st = check_nf(p, n_f);
+  if (st) return st;
+  if (!fg || !fb || !F) return set_error(FC2D_ERR_ARG, "fc2d_blend: null pointer");
+  cudaSetDevice(p->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  if (p->prm.precision == FC2D_FP64) {
+    launch_gather_blend(gather_args(p, fg, fb, F, nullptr, nullptr), n_f, true, s);
+    return launched("fc2d_blend");
+  }
+  return set_error(FC2D_ERR_UNSUPPORTED, "mixed precision blend not built yet");
+}
+
+extern "C" fc2d_status fc2d_interp(fc2d_plan_t p, int n_f, const void* F, void* vals,
+                                   void* stream) {
+  fc2d_status st = check_nf(p, n_f);
+  if (st) return st;
+  if (!F || !vals) return set_error(FC2D_ERR_ARG, "fc2d_interp: null pointer");
+  cudaSetDevice(p->device);
+  launch_interp(interp_args(p), n_f, p->prm.precision == FC2D_FP64, F, vals,
+                (cudaStream_t)stream);
+  return launched("fc2d_interp");
+}
+
+extern "C" fc2d_status fc2d_extend(fc2d_plan_t p, int n_f, const double* fg, const double* fb,
+                                   void* ext, void* stream) {
+  fc2d_status st = check_nf(p, n_f);
+  if (st) return st;
+  if (!fg || !fb || !ext) return set_error(FC2D_ERR_ARG, "fc2d_extend: null pointer");
+  cudaSetDevice(p->device);
+  Layout L = layout(p, n_f);
+  if ((st = ensure_workspace(p, L.total))) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  if ((st = strip_values(p, n_f, fg, fb, L, s))) return st;
+  {
+    ProfScope ps(p, "assemble_rows", s);
+    launch_assemble(row_args(p), n_f, p->prm.precision == FC2D_FP64, fg, ws(p, L.ovals), ext, s);
+  }
+  return launched("fc2d_extend");
+}
+
+extern "C" fc2d_status fc2d_coeffs(fc2d_plan_t p, int n_f, const void* ext, void* fhat,
+                                   void* stream) {
+  fc2d_status st = check_nf(p, n_f);
+  if (st) return st;
+  if (!ext || !fhat) return set_error(FC2D_ERR_ARG, "fc2d_coeffs: null pointer");
+  cudaSetDevice(p->device);
+  Layout L = layout(p, n_f);
+  if ((st = ensure_workspace(p, L.total))) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  const bool f64 = p->prm.precision == FC2D_FP64;
+  FftArgs fa = fft_args(p);
+  {
+    ProfScope ps(p, "fft_rows", s);
+    launch_fft_rows(fa, row_args(p), n_f, f64, 0, ext, nullptr, nullptr, ws(p, L.ointer), s);
+  }
+  {
+    ProfScope ps(p, "fft_cols", s);
+    launch_fft_cols(fa, n_f, f64, ws(p, L.ointer), fhat, s);
+  }
+  return launched("fc2d_coeffs");
+}
+
+extern "C" fc2d_status fc2d_extend_coeffs(fc2d_plan_t p, int n_f, const double* fg,
+                                          const double* fb, void* fhat, void* stream) {
+  fc2d_status st = check_nf(p, n_f);
+  if (st) return st;
+  if (!fg || !fb || !fhat) return set_error(FC2D_ERR_ARG, "fc2d_extend_coeffs: null pointer");
+  cudaSetDevice(p->device);
+  Layout L = layout(p, n_f);
+  if ((st = ensure_workspace(p, L.total))) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  if ((st = strip_values(p, n_f, fg, fb, L, s))) return st;
+  const bool f64 = p->prm.precision == FC2D_FP64;
+  FftArgs fa = fft_args(p);
+  {
+    ProfScope ps(p, "fft_rows_fused", s);
+    launch_fft_rows(fa, row_args(p), n_f, f64, 1, nullptr, fg, ws(p, L.ovals),
+                    ws(p, L.ointer), s);
+  }
+  {
+    ProfScope ps(p, "fft_cols", s);
+    launch_fft_cols(fa, n_f, f64, ws(p, L.ointer), fhat, s);
+  }
+  return launched("fc2d_extend_coeffs");
+}
+
+extern "C" fc2d_status fc2d_sync_status(fc2d_plan_t p, void* stream) {
+  if (!p) return set_error(FC2D_ERR_ARG, "null plan");
+  cudaSetDevice(p->device);
+  fc2d_status st = cuda_check(cudaStreamSynchronize((cudaStream_t)stream), "stream sync");
+  if (st) return st;
+  int h = 0;
+  st = cuda_check(cudaMemcpy(&h, p->dev.status, sizeof(int), cudaMemcpyDeviceToHost),
+                  "status read");
+  if (st) return st;
+  if (h) return set_error((fc2d_status)h, "device status latched");
+  return FC2D_OK;
+}
+
+// ------------------------------------------------------------------------- //
+// Kernel timing
+// ------------------------------------------------------------------------- //
+namespace fc2d {
+
+static void* take_event(fc2d_plan_s* p) {
+  if (!p->event_pool.empty()) {
+    void* e = p->event_pool.back();
+    p->event_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return (void*)e;
+}
+
+ProfScope::ProfScope(fc2d_plan_s* p_, const char* name_, void* stream_)
+    : p(p_), name(name_), stream(stream_) {
+  if (!p->profiling) return;
+  ev0 = take_event(p);
+  cudaEventRecord((cudaEvent_t)ev0, (cudaStream_t)stream);
+}
+
+ProfScope::~ProfScope() {
+  if (!p->profiling || !ev0) return;
+  void* ev1 = take_event(p);
+  cudaEventRecord((cudaEvent_t)ev1, (cudaStream_t)stream);
+  p->prof.push_back({name, ev0, ev1});
+}
+
+}  // namespace fc2d
+
+extern "C" fc2d_status fc2d_profile(fc2d_plan_t p, int enable) {
+  if (!p) return set_error(FC2D_ERR_ARG, "null plan");
+  p->profiling = enable != 0;
+  return FC2D_OK;
+}
+
+extern "C" fc2d_status fc2d_profile_read(fc2d_plan_t p, int max_kernels, char* names,
+                                         int64_t* launches, double* ms, int* n_out) {
+  if (!p || !n_out || (max_kernels > 0 && (!names || !launches || !ms)))
+    return set_error(FC2D_ERR_ARG, "fc2d_profile_read: null argument");
+  std::vector<std::string> nm;
+  std::vector<int64_t> cnt;
+  std::vector<double> tot;
+  for (auto& r : p->prof) {
+    cudaEventSynchronize((cudaEvent_t)r.stop);
+    float t = 0.f;
+    cudaEventElapsedTime(&t, (cudaEvent_t)r.start, (cudaEvent_t)r.stop);
+    size_t k = 0;
+    while (k < nm.size() && nm[k] != r.name) ++k;
+    if (k == nm.size()) {
+      nm.push_back(r.name);
+      cnt.push_back(0);
+      tot.push_back(0.0);
+    }
+    cnt[k] += 1;
+    tot[k] += t;
+    p->event_pool.push_back(r.start);
+    p->event_pool.push_back(r.stop);
+  }
+  p->prof.clear();
+  *n_out = (int)nm.size();
+  for (int k = 0; k < (int)nm.size() && k < max_kernels; ++k) {
+    std::snprintf(names + 64 * k, 64, "%s", nm[k].c_str());
+    launches[k] = cnt[k];
+    ms[k] = tot[k];
+  }
+  return FC2D_OK;
+}

@@ -1,0 +1,284 @@
+// 2D-FC Cartesian evaluation kernels (Section 3.5, steps 5-6) and the plan-time Newton
+// foot search (step 4).
+//
+//   k_foot_newton     FP64 Newton on (q(t) - Q).q'(t) = 0 for every strip candidate.
+//   k_gather_blend    one warp per (normal, function): the two-step interpolation of
+//                     Section 3.2 gives the matching values f_{D_p}; then the Gram
+//                     coefficients c = Q^T f_{D_p} and the strip values A_r c (eq. (2.6),
+//                     Remark 2.2).  FP64; in the mixed form the warp stops at c.
+//   k_interp          one thread per (strip point, function): the theta/eta Lagrange
+//                     interpolation of Section 3.4 with FP64 weights.
+//   k_assemble_rows   one block per (row, function): f on the inside intervals, the
+//                     strip values, 0 elsewhere -> the extended grid.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <vector>
+
+#include "fc2d_kernels.cuh"
+#include "plan_internal.h"
+
+namespace fc2d {
+
+// ------------------------------------------------------------------------- //
+// Newton foot search (plan time)
+// ------------------------------------------------------------------------- //
+constexpr int kMaxModes = 64;
+__constant__ double c_curve[4 * kMaxModes];
+
+__device__ void curve_eval(int nm, double t, double* x, double* y) {
+  // x[0..2], y[0..2]: value, first and second derivative
+  for (int d = 0; d < 3; ++d) x[d] = y[d] = 0.0;
+  for (int k = 0; k < nm; ++k) {
+    double s, c;
+    sincos(double(k) * t, &s, &c);
+    double ax = c_curve[k], bx = c_curve[kMaxModes + k];
+    double ay = c_curve[2 * kMaxModes + k], by = c_curve[3 * kMaxModes + k];
+    double kk = double(k);
+    x[0] += ax * c + bx * s;
+    y[0] += ay * c + by * s;
+    x[1] += kk * (-ax * s + bx * c);
+    y[1] += kk * (-ay * s + by * c);
+    x[2] -= kk * kk * (ax * c + bx * s);
+    y[2] -= kk * kk * (ay * c + by * s);
+  }
+}
+
+__global__ void k_foot_newton(int n, int nm, const double* __restrict__ qx,
+                              const double* __restrict__ qy, double* __restrict__ th,
+                              int* __restrict__ conv) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double t = th[i], X = qx[i], Y = qy[i];
+  int ok = 0;
+  for (int it = 0; it < 60; ++it) {  // iteration cap: no unbounded loop
+    double x[3], y[3];
+    curve_eval(nm, t, x, y);
+    double phi = (x[0] - X) * x[1] + (y[0] - Y) * y[1];
+    double dphi = x[1] * x[1] + y[1] * y[1] + (x[0] - X) * x[2] + (y[0] - Y) * y[2];
+    if (!(dphi > 0.0)) break;  // not a local minimum of the distance: give up
+    double step = phi / dphi;
+    t -= step;
+    if (fabs(step) < 1e-15) {
+      ok = 1;
+      break;
+    }
+  }
+  th[i] = t;
+  conv[i] = ok;
+}
+
+fc2d_status foot_newton_gpu(const Curve& c, const std::vector<double>& qx,
+                            const std::vector<double>& qy, std::vector<double>& theta,
+                            std::vector<int>& conv) {
+  int nm = (int)c.cx.size();
+  if (nm > kMaxModes) return set_error(FC2D_ERR_UNSUPPORTED, "boundary has too many modes");
+  size_t n = qx.size();
+  conv.assign(n, 0);
+  if (n == 0) return FC2D_OK;
+  std::vector<double> cc(4 * kMaxModes, 0.0);
+  for (int k = 0; k < nm; ++k) {
+    cc[k] = c.cx[k];
+    cc[kMaxModes + k] = c.sx[k];
+    cc[2 * kMaxModes + k] = c.cy[k];
+    cc[3 * kMaxModes + k] = c.sy[k];
+  }
+  double *dqx = nullptr, *dqy = nullptr, *dth = nullptr;
+  int* dconv = nullptr;
+  fc2d_status st = FC2D_OK;
+  if (cudaMalloc(&dqx, n * 8) || cudaMalloc(&dqy, n * 8) || cudaMalloc(&dth, n * 8) ||
+      cudaMalloc(&dconv, n * 4)) {
+    st = set_error(FC2D_ERR_NOMEM, "foot search: cudaMalloc failed");
+  } else {
+    cudaMemcpyToSymbol(c_curve, cc.data(), cc.size() * 8);
+    cudaMemcpy(dqx, qx.data(), n * 8, cudaMemcpyHostToDevice);
+    cudaMemcpy(dqy, qy.data(), n * 8, cudaMemcpyHostToDevice);
+    cudaMemcpy(dth, theta.data(), n * 8, cudaMemcpyHostToDevice);
+    k_foot_newton<<<(unsigned)((n + 127) / 128), 128>>>((int)n, nm, dqx, dqy, dth, dconv);
+    st = cuda_check(cudaGetLastError(), "foot search launch");
+    if (st == FC2D_OK) st = cuda_check(cudaDeviceSynchronize(), "foot search");
+    if (st == FC2D_OK) {
+      cudaMemcpy(theta.data(), dth, n * 8, cudaMemcpyDeviceToHost);
+      cudaMemcpy(conv.data(), dconv, n * 4, cudaMemcpyDeviceToHost);
+    }
+  }
+  cudaFree(dqx);
+  cudaFree(dqy);
+  cudaFree(dth);
+  cudaFree(dconv);
+  return st;
+}
+
+// ------------------------------------------------------------------------- //
+// Matching values + blending (Section 3.2, eq. (2.6))
+// ------------------------------------------------------------------------- //
+// Lanes 0..M-2 each evaluate one red star (M taps); lanes 0..d-2 form the matching
+// values; c = Q^T f_D; the warp then writes F[q] = (A_r c)_q (FP64 form) or the
+// Gram coefficients c (mixed form, consumed by the tensor-core contraction).
+template <bool kFp64Blend>
+__global__ void __launch_bounds__(256) k_gather_blend(GatherArgs a) {
+  const int lane = threadIdx.x & 31;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int f = blockIdx.y;
+  if (warp >= a.B) return;
+  const int p = warp, M = a.M, d = a.d, NS = M - 1;
+  const double* fg = a.f_grid + (size_t)f * a.grid_stride;
+  const double* fb = a.f_bdry + (size_t)f * a.n_bdry;
+  double star = 0.0;
+  if (lane < NS) {
+    const int32_t* gi = a.gidx + ((size_t)p * NS + lane) * M;
+    const double* gw = a.gw + ((size_t)p * NS + lane) * M;
+    for (int e = 0; e < M; ++e) {
+      int32_t id = __ldg(gi + e);
+      double v = id >= 0 ? __ldg(fg + id) : __ldg(fb + (-1 - id));
+      star = fma(__ldg(gw + e), v, star);
+    }
+  }
+  const double fbp = __ldg(fb + p);
+  // matching values: lane q < d-1 computes f(r_{p,q}); lane d-1 holds the boundary datum
+  double fD = 0.0;
+  {
+    const double* wn = a.wn + ((size_t)p * (d - 1) + (lane < d - 1 ? lane : 0)) * M;
+    double acc = (lane < d - 1) ? __ldg(wn) * fbp : 0.0;
+    for (int e = 1; e < M; ++e) {
+      double s = __shfl_sync(0xffffffffu, star, e - 1);
+      if (lane < d - 1) acc = fma(__ldg(wn + e), s, acc);
+    }
+    fD = lane < d - 1 ? acc : (lane == d - 1 ? fbp : 0.0);
+  }
+  // Gram coefficients c_j = sum_i Q[i][j] f_D[i]
+  double c[kMaxD];
+#pragma unroll
+  for (int j = 0; j < kMaxD; ++j) c[j] = 0.0;
+  for (int i = 0; i < d; ++i) {
+    double v = __shfl_sync(0xffffffffu, fD, i);
+#pragma unroll
+    for (int j = 0; j < kMaxD; ++j)
+      if (j < d) c[j] = fma(a.Q[i * d + j], v, c[j]);
+  }
+  if (kFp64Blend) {
+    double* F = reinterpret_cast<double*>(a.F) + ((size_t)f * a.B + p) * (a.Cr + 1);
+    if (lane == 0) F[0] = fbp;
+    for (int q = lane; q < a.Cr; q += 32) {
+      const double* ar = a.Ar + (size_t)q * d;
+      double v = 0.0;
+#pragma unroll
+      for (int j = 0; j < kMaxD; ++j)
+        if (j < d) v = fma(__ldg(ar + j), c[j], v);
+      F[q + 1] = v;
+    }
+  } else {
+    // mixed form: Gram coefficients for the contraction, and the boundary datum
+    if (lane < d) {
+      double v = 0.0;
+#pragma unroll
+      for (int j = 0; j < kMaxD; ++j)
+        if (j == lane) v = c[j];
+      a.coef[((size_t)f * a.B + p) * a.coef_ld + lane] = v;
+    }
+    if (lane == 0) a.bvals[(size_t)f * a.B + p] = fbp;
+  }
+}
+
+void launch_gather_blend(const GatherArgs& a, int n_f, bool fp64, cudaStream_t s) {
+  dim3 grid((a.B * 32 + 255) / 256, n_f);
+  if (fp64)
+    k_gather_blend<true><<<grid, 256, 0, s>>>(a);
+  else
+    k_gather_blend<false><<<grid, 256, 0, s>>>(a);
+}
+
+// ------------------------------------------------------------------------- //
+// Interpolation onto the strip points (Section 3.4)
+// ------------------------------------------------------------------------- //
+// Lagrange weights at t for the nodes 0..M-1: prefix/suffix products of (t - m)
+// times 1/prod_{m != k}(k - m).
+__device__ __forceinline__ void lagrange_equispaced(int M, double t, double* w) {
+  double pre[kMaxM], suf[kMaxM];
+  pre[0] = 1.0;
+  for (int k = 1; k < M; ++k) pre[k] = pre[k - 1] * (t - double(k - 1));
+  suf[M - 1] = 1.0;
+  for (int k = M - 2; k >= 0; --k) suf[k] = suf[k + 1] * (t - double(k + 1));
+  // 1/prod_{m != k}(k - m) = (-1)^(M-1-k) / (k! (M-1-k)!)
+  double fact[kMaxM];
+  fact[0] = 1.0;
+  for (int k = 1; k < M; ++k) fact[k] = fact[k - 1] * double(k);
+  for (int k = 0; k < M; ++k) {
+    double den = fact[k] * fact[M - 1 - k];
+    double v = pre[k] * suf[k] / den;
+    w[k] = ((M - 1 - k) & 1) ? -v : v;
+  }
+}
+
+template <typename TF, typename TV>
+__global__ void __launch_bounds__(256) k_interp(InterpArgs a, const TF* __restrict__ F,
+                                                TV* __restrict__ vals) {
+  int n = blockIdx.x * blockDim.x + threadIdx.x;
+  int f = blockIdx.y;
+  if (n >= a.n_strip) return;
+  const int M = a.M, Kl = (M + 1) / 2 - 1, B = a.B, ld = a.Cr + 1;
+  double tt = __ldg(a.theta + n) * a.inv_k2;
+  double p0 = floor(tt);
+  double wth[kMaxM], weta[kMaxM];
+  lagrange_equispaced(M, tt - (p0 - Kl), wth);
+  double u = __ldg(a.eta + n) * a.nr_over_k1;
+  int s = (int)floor(u) - Kl;
+  s = s < 0 ? 0 : (s > a.Cr + 1 - M ? a.Cr + 1 - M : s);
+  lagrange_equispaced(M, u - s, weta);
+  const TF* Ff = F + (size_t)f * B * ld;
+  int pb = (int)p0 - Kl;
+  double acc = 0.0;
+  for (int ai = 0; ai < M; ++ai) {
+    int pr = pb + ai;
+    pr = pr < 0 ? pr + B : (pr >= B ? pr - B : pr);
+    const TF* row = Ff + (size_t)pr * ld + s;
+    double v = 0.0;
+    for (int b = 0; b < M; ++b) v = fma(weta[b], (double)__ldg(row + b), v);
+    acc = fma(wth[ai], v, acc);
+  }
+  vals[(size_t)f * a.n_strip + n] = (TV)acc;
+}
+
+void launch_interp(const InterpArgs& a, int n_f, bool fp64, const void* F, void* vals,
+                   cudaStream_t s) {
+  if (a.n_strip == 0) return;
+  dim3 grid((a.n_strip + 255) / 256, n_f);
+  if (fp64)
+    k_interp<double, double><<<grid, 256, 0, s>>>(a, (const double*)F, (double*)vals);
+  else
+    k_interp<float, float><<<grid, 256, 0, s>>>(a, (const float*)F, (float*)vals);
+}
+
+// ------------------------------------------------------------------------- //
+// Assemble the extended grid row by row (shared-memory row buffer)
+// ------------------------------------------------------------------------- //
+template <typename T>
+__global__ void k_assemble_rows(RowArgs a, const double* __restrict__ f_grid,
+                                const T* __restrict__ vals, T* __restrict__ ext) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* row = reinterpret_cast<T*>(smem_raw);
+  const int j = blockIdx.x, f = blockIdx.y, nx = a.nx;
+  const double* fg = f_grid + (size_t)f * a.grid_stride + (size_t)j * nx;
+  load_row<T>(a, j, f, fg, vals, row);
+  __syncthreads();
+  T* out = ext + (size_t)f * a.grid_stride + (size_t)j * nx;
+  for (int i = threadIdx.x; i < nx; i += blockDim.x) out[i] = row[i];
+}
+
+void launch_assemble(const RowArgs& a, int n_f, bool fp64, const double* f_grid,
+                     const void* vals, void* ext, cudaStream_t s) {
+  dim3 grid(a.ny, n_f);
+  size_t sm = (size_t)a.nx * (fp64 ? 8 : 4);
+  if (fp64) {
+    cudaFuncSetAttribute(k_assemble_rows<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)sm);
+    k_assemble_rows<double><<<grid, 256, sm, s>>>(a, f_grid, (const double*)vals,
+                                                  (double*)ext);
+  } else {
+    cudaFuncSetAttribute(k_assemble_rows<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)sm);
+    k_assemble_rows<float><<<grid, 256, sm, s>>>(a, f_grid, (const float*)vals, (float*)ext);
+  }
+}
+
+}  // namespace fc2d

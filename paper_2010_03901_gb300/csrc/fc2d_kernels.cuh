@@ -1,0 +1,88 @@
+// Kernel argument blocks and shared device helpers of the 2D-FC kernels.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+namespace fc2d {
+
+constexpr int kMaxD = 8;
+
+struct GatherArgs {
+  int B, M, d, Cr;
+  int64_t n_bdry, grid_stride;
+  const double* f_grid;   // [n_f][ny][nx]
+  const double* f_bdry;   // [n_f][n_bdry]
+  const int32_t* gidx;    // [B][M-1][M]
+  const double* gw;       // [B][M-1][M]
+  const double* wn;       // [B][d-1][M]
+  const double* Q;        // [d][d]
+  const double* Ar;       // [Cr][d]
+  void* F;                // FP64 form: [n_f][B][Cr+1]
+  double* coef;           // mixed form: Gram coefficients [n_f][B][coef_ld]
+  int coef_ld;
+  double* bvals;          // mixed form: boundary datum per normal [n_f][B]
+};
+
+struct InterpArgs {
+  int n_strip, M, B, Cr;
+  double inv_k2, nr_over_k1;
+  const double* theta;
+  const double* eta;
+};
+
+struct RowArgs {
+  int nx, ny;
+  int64_t grid_stride, n_strip;
+  const int32_t* row_iv_off;
+  const int32_t* row_iv;
+  const int32_t* row_strip_off;
+  const int32_t* s_lin;
+};
+
+// Fill a shared-memory row with the extension: 0, then f on the inside intervals,
+// then the strip values.  Ends with the row complete (after a __syncthreads()).
+template <typename T, typename TV>
+__device__ __forceinline__ void load_row(const RowArgs& a, int j, int f,
+                                         const double* __restrict__ fg_row,
+                                         const TV* __restrict__ vals, T* row) {
+  const int nx = a.nx;
+  for (int i = threadIdx.x; i < nx; i += blockDim.x) row[i] = T(0);
+  __syncthreads();
+  const int iv0 = __ldg(a.row_iv_off + j), iv1 = __ldg(a.row_iv_off + j + 1);
+  for (int k = iv0; k < iv1; ++k) {
+    const int lo = __ldg(a.row_iv + 2 * k), hi = __ldg(a.row_iv + 2 * k + 1);
+    for (int i = lo + threadIdx.x; i <= hi; i += blockDim.x) row[i] = (T)__ldg(fg_row + i);
+  }
+  const int s0 = __ldg(a.row_strip_off + j), s1 = __ldg(a.row_strip_off + j + 1);
+  const TV* v = vals + (size_t)f * a.n_strip;
+  const int base = j * nx;
+  for (int k = s0 + threadIdx.x; k < s1; k += blockDim.x)
+    row[__ldg(a.s_lin + k) - base] = (T)__ldg(v + k);
+}
+
+void launch_gather_blend(const GatherArgs& a, int n_f, bool fp64, cudaStream_t s);
+void launch_interp(const InterpArgs& a, int n_f, bool fp64, const void* F, void* vals,
+                   cudaStream_t s);
+void launch_assemble(const RowArgs& a, int n_f, bool fp64, const double* f_grid,
+                     const void* vals, void* ext, cudaStream_t s);
+
+struct FftArgs {
+  int nx, ny, pitch;          // pitch: complex elements per intermediate row
+  int nrx, nry;               // number of radices
+  int rx[24], ry[24];
+  const void* twx;            // exp(-2 pi i t/(nx/2)) table for the row transform
+  const void* twy;            // exp(-2 pi i t/ny)
+  const void* rtw;            // exp(-2 pi i k/nx), k <= nx/2
+  double scale;               // 1/(nx ny)
+};
+
+// rows: mode 0 reads an extended grid (ext, type T); mode 1 assembles the extension
+// on the fly from f_grid + strip values.
+void launch_fft_rows(const FftArgs& fa, const RowArgs& ra, int n_f, bool fp64, int mode,
+                     const void* ext, const double* f_grid, const void* vals, void* inter,
+                     cudaStream_t s);
+void launch_fft_cols(const FftArgs& fa, int n_f, bool fp64, const void* inter, void* fhat,
+                     cudaStream_t s);
+
+}  // namespace fc2d

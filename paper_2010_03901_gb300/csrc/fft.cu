@@ -1,0 +1,246 @@
+// Hand-written 2D real-to-complex DFT of the extended grid (eq. (3.1), Section 3.5
+// step 7) for sizes 2^a 3^b 5^c.
+//
+// Pass 1 (k_fft_rows): one block per (row, function).  The row of nx reals is loaded
+// into shared memory as nx/2 complex pairs z_n = x_{2n} + i x_{2n+1} -- either from an
+// extended grid or assembled on the fly from f inside the domain and the strip values
+// (fused extension: exterior points are never read).  A mixed-radix Stockham FFT of
+// length nx/2 runs in shared memory, then the standard even/odd split gives X_k,
+// k = 0..nx/2, written to an intermediate [ny][pitch] array.
+// Pass 2 (k_fft_cols): one block per (group of columns, function): the column
+// transforms of length ny, scaled by 1/(nx ny), written to fhat [ny][nx/2+1].
+//
+// Stockham autosort (stage with radix R over sub-transforms of length Ns): butterfly
+// j reads x[j + r N/R], multiplies by exp(-2 pi i r (j mod Ns)/(Ns R)) and writes
+// y[(j/Ns) Ns R + (j mod Ns) + r Ns] (Govindaraju et al., SC 2008).
+#include <cuda_runtime.h>
+
+#include "fc2d_kernels.cuh"
+
+namespace fc2d {
+
+template <typename T> struct Cx;
+template <> struct Cx<double> { using type = double2; };
+template <> struct Cx<float> { using type = float2; };
+
+template <typename C> __device__ __forceinline__ C cadd(C a, C b) { return {a.x + b.x, a.y + b.y}; }
+template <typename C> __device__ __forceinline__ C csub(C a, C b) { return {a.x - b.x, a.y - b.y}; }
+template <typename C> __device__ __forceinline__ C cmul(C a, C b) {
+  return {a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
+}
+template <typename C> __device__ __forceinline__ C mul_mi(C a) { return {a.y, -a.x}; }  // * (-i)
+template <typename C> __device__ __forceinline__ C conj_(C a) { return {a.x, -a.y}; }
+
+// forward DFT of length R in registers (R = 2, 3, 4, 5, 8)
+template <typename T, typename C>
+__device__ __forceinline__ void dft_small(C* v, int R) {
+  if (R == 2) {
+    C a = v[0], b = v[1];
+    v[0] = cadd(a, b);
+    v[1] = csub(a, b);
+  } else if (R == 4) {
+    C t0 = cadd(v[0], v[2]), t1 = csub(v[0], v[2]);
+    C t2 = cadd(v[1], v[3]), t3 = mul_mi(csub(v[1], v[3]));
+    v[0] = cadd(t0, t2);
+    v[2] = csub(t0, t2);
+    v[1] = cadd(t1, t3);
+    v[3] = csub(t1, t3);
+  } else if (R == 8) {
+    const T s = (T)0.70710678118654752440;
+    C e[4] = {v[0], v[2], v[4], v[6]}, o[4] = {v[1], v[3], v[5], v[7]};
+    dft_small<T, C>(e, 4);
+    dft_small<T, C>(o, 4);
+    // twiddles exp(-2 pi i k/8), k = 0..3
+    C w1 = {s * (o[1].x + o[1].y), s * (o[1].y - o[1].x)};
+    C w2 = mul_mi(o[2]);
+    C w3 = {s * (o[3].y - o[3].x), -s * (o[3].x + o[3].y)};
+    v[0] = cadd(e[0], o[0]);
+    v[4] = csub(e[0], o[0]);
+    v[1] = cadd(e[1], w1);
+    v[5] = csub(e[1], w1);
+    v[2] = cadd(e[2], w2);
+    v[6] = csub(e[2], w2);
+    v[3] = cadd(e[3], w3);
+    v[7] = csub(e[3], w3);
+  } else if (R == 3) {
+    const T c1 = (T)-0.5, s1 = (T)0.86602540378443864676;  // exp(-2 pi i/3) = c1 - i s1
+    C a = v[0], b = v[1], c = v[2];
+    C sbc = cadd(b, c), dbc = csub(b, c);
+    v[0] = cadd(a, sbc);
+    C m = {a.x + c1 * sbc.x, a.y + c1 * sbc.y};
+    C r = {s1 * dbc.y, -s1 * dbc.x};  // -i s1 (b - c)
+    v[1] = cadd(m, r);
+    v[2] = csub(m, r);
+  } else if (R == 5) {
+    const T c1 = (T)0.30901699437494742410, s1 = (T)0.95105651629515357212;
+    const T c2 = (T)-0.80901699437494742410, s2 = (T)0.58778525229247312917;
+    C a = v[0];
+    C s14 = cadd(v[1], v[4]), d14 = csub(v[1], v[4]);
+    C s23 = cadd(v[2], v[3]), d23 = csub(v[2], v[3]);
+    v[0] = cadd(a, cadd(s14, s23));
+    C m1 = {a.x + c1 * s14.x + c2 * s23.x, a.y + c1 * s14.y + c2 * s23.y};
+    C m2 = {a.x + c2 * s14.x + c1 * s23.x, a.y + c2 * s14.y + c1 * s23.y};
+    // -i (s1 d14 + s2 d23) and -i (s2 d14 - s1 d23)
+    C r1 = {s1 * d14.y + s2 * d23.y, -(s1 * d14.x + s2 * d23.x)};
+    C r2 = {s2 * d14.y - s1 * d23.y, -(s2 * d14.x - s1 * d23.x)};
+    v[1] = cadd(m1, r1);
+    v[4] = csub(m1, r1);
+    v[2] = cadd(m2, r2);
+    v[3] = csub(m2, r2);
+  }
+}
+
+// nbatch transforms of length N stored contiguously (stride N) in a; b is scratch of
+// the same size.  Returns the buffer holding the result.  tw: exp(-2 pi i t/Ntab),
+// read at stride tws (Ntab = N tws).
+template <typename T>
+__device__ typename Cx<T>::type* stockham(typename Cx<T>::type* a, typename Cx<T>::type* b,
+                                          int N, int nbatch, const int* radix, int nrad,
+                                          const typename Cx<T>::type* __restrict__ tw,
+                                          int tws) {
+  using C = typename Cx<T>::type;
+  int Ns = 1;
+  for (int st = 0; st < nrad; ++st) {
+    const int R = radix[st];
+    const int NR = N / R;
+    const int tstep = N / (Ns * R);
+    for (int idx = threadIdx.x; idx < nbatch * NR; idx += blockDim.x) {
+      const int c = idx / NR, j = idx - c * NR;
+      const int k = j % Ns;
+      const C* src = a + (size_t)c * N;
+      C v[8];
+#pragma unroll
+      for (int r = 0; r < 8; ++r)
+        if (r < R) {
+          C x = src[j + r * NR];
+          if (r > 0 && k > 0) x = cmul(x, __ldg(tw + (size_t)r * k * tstep * tws));
+          v[r] = x;
+        }
+      dft_small<T, C>(v, R);
+      C* dst = b + (size_t)c * N + (j / Ns) * Ns * R + k;
+#pragma unroll
+      for (int r = 0; r < 8; ++r)
+        if (r < R) dst[r * Ns] = v[r];
+    }
+    __syncthreads();
+    C* t = a;
+    a = b;
+    b = t;
+    Ns *= R;
+  }
+  return a;
+}
+
+template <typename T, typename TV>
+__global__ void __launch_bounds__(256) k_fft_rows(FftArgs fa, RowArgs ra, int mode,
+                                                  const T* __restrict__ ext,
+                                                  const double* __restrict__ f_grid,
+                                                  const TV* __restrict__ vals,
+                                                  typename Cx<T>::type* __restrict__ inter) {
+  using C = typename Cx<T>::type;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int nx = fa.nx, Nh = nx / 2;
+  C* A = reinterpret_cast<C*>(smem_raw);
+  C* Bf = A + Nh;
+  const int j = blockIdx.x, f = blockIdx.y;
+  T* rowr = reinterpret_cast<T*>(A);
+  if (mode == 0) {
+    const T* src = ext + (size_t)f * ra.grid_stride + (size_t)j * nx;
+    for (int i = threadIdx.x; i < nx; i += blockDim.x) rowr[i] = src[i];
+  } else {
+    load_row<T>(ra, j, f, f_grid + (size_t)f * ra.grid_stride + (size_t)j * nx, vals, rowr);
+  }
+  __syncthreads();
+  const C* tw = reinterpret_cast<const C*>(fa.twx);
+  C* Z = stockham<T>(A, Bf, Nh, 1, fa.rx, fa.nrx, tw, 1);
+  // even/odd split: X_k = (Z_k + conj Z_{Nh-k})/2 - i w^k (Z_k - conj Z_{Nh-k})/2
+  const C* rtw = reinterpret_cast<const C*>(fa.rtw);
+  C* out = inter + ((size_t)f * fa.ny + j) * fa.pitch;
+  for (int k = threadIdx.x; k <= Nh; k += blockDim.x) {
+    C zk = Z[k == Nh ? 0 : k];
+    C zc = conj_(Z[k == 0 ? 0 : Nh - k]);
+    C e = {(T)0.5 * (zk.x + zc.x), (T)0.5 * (zk.y + zc.y)};
+    C o = {(T)0.5 * (zk.x - zc.x), (T)0.5 * (zk.y - zc.y)};
+    C w = __ldg(rtw + k);
+    C wo = cmul(w, o);
+    out[k] = {e.x + wo.y, e.y - wo.x};  // e - i (w o)
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_fft_cols(FftArgs fa, int cb,
+                                                  const typename Cx<T>::type* __restrict__ inter,
+                                                  typename Cx<T>::type* __restrict__ fhat) {
+  using C = typename Cx<T>::type;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int ny = fa.ny, ncol = fa.nx / 2 + 1;
+  const int c0 = blockIdx.x * cb, f = blockIdx.y;
+  const int nc = min(cb, ncol - c0);
+  C* A = reinterpret_cast<C*>(smem_raw);
+  C* Bf = A + (size_t)cb * ny;
+  const C* src = inter + (size_t)f * ny * fa.pitch + c0;
+  for (int idx = threadIdx.x; idx < ny * cb; idx += blockDim.x) {
+    int y = idx / cb, c = idx - y * cb;
+    A[(size_t)c * ny + y] = c < nc ? src[(size_t)y * fa.pitch + c] : C{0, 0};
+  }
+  __syncthreads();
+  const C* tw = reinterpret_cast<const C*>(fa.twy);
+  C* Y = stockham<T>(A, Bf, ny, cb, fa.ry, fa.nry, tw, 1);
+  C* dst = fhat + (size_t)f * ny * ncol + c0;
+  const T sc = (T)fa.scale;
+  for (int idx = threadIdx.x; idx < ny * cb; idx += blockDim.x) {
+    int y = idx / cb, c = idx - y * cb;
+    if (c < nc) {
+      C v = Y[(size_t)c * ny + y];
+      dst[(size_t)y * ncol + c] = {v.x * sc, v.y * sc};
+    }
+  }
+}
+
+void launch_fft_rows(const FftArgs& fa, const RowArgs& ra, int n_f, bool fp64, int mode,
+                     const void* ext, const double* f_grid, const void* vals, void* inter,
+                     cudaStream_t s) {
+  dim3 grid(fa.ny, n_f);
+  if (fp64) {
+    size_t sm = (size_t)fa.nx * sizeof(double2);  // two buffers of nx/2 complex
+    auto k = k_fft_rows<double, double>;
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k<<<grid, 256, sm, s>>>(fa, ra, mode, (const double*)ext, f_grid, (const double*)vals,
+                            (double2*)inter);
+  } else {
+    size_t sm = (size_t)fa.nx * sizeof(float2);
+    auto k = k_fft_rows<float, float>;
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k<<<grid, 256, sm, s>>>(fa, ra, mode, (const float*)ext, f_grid, (const float*)vals,
+                            (float2*)inter);
+  }
+}
+
+static int pick_cb(int ny, size_t csize) {
+  const size_t budget = 200 * 1024;
+  int cb = 1;
+  while (cb < 8 && 2 * (size_t)(2 * cb) * ny * csize <= budget) cb *= 2;
+  return cb;
+}
+
+void launch_fft_cols(const FftArgs& fa, int n_f, bool fp64, const void* inter, void* fhat,
+                     cudaStream_t s) {
+  const int ncol = fa.nx / 2 + 1;
+  if (fp64) {
+    int cb = pick_cb(fa.ny, sizeof(double2));
+    size_t sm = 2 * (size_t)cb * fa.ny * sizeof(double2);
+    auto k = k_fft_cols<double>;
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k<<<dim3((ncol + cb - 1) / cb, n_f), 256, sm, s>>>(fa, cb, (const double2*)inter,
+                                                       (double2*)fhat);
+  } else {
+    int cb = pick_cb(fa.ny, sizeof(float2));
+    size_t sm = 2 * (size_t)cb * fa.ny * sizeof(float2);
+    auto k = k_fft_cols<float>;
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k<<<dim3((ncol + cb - 1) / cb, n_f), 256, sm, s>>>(fa, cb, (const float2*)inter,
+                                                       (float2*)fhat);
+  }
+}
+
+}  // namespace fc2d

@@ -1,0 +1,113 @@
+// Internal state of an fc2d plan (host tables + device tables + workspace).
+#pragma once
+#include <cstddef>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/fc2d.h"
+
+namespace fc2d {
+
+constexpr int kMaxRadices = 24;
+constexpr int kMaxM = 12;
+
+// One 1D FFT length: its radix sequence and twiddle tables exp(-2 pi i t/N), t < N.
+struct FftAxis {
+  int n = 0;
+  int n_radix = 0;
+  int radix[kMaxRadices] = {0};
+  std::vector<double> tw_host;   // interleaved re, im (2N doubles)
+  double* tw64 = nullptr;        // device, 2N doubles
+  float* tw32 = nullptr;         // device, 2N floats
+};
+
+struct Curve {
+  std::vector<double> cx, sx, cy, sy;
+  void eval(double t, double& x, double& y) const;
+  void eval_d(double t, int der, double& x, double& y) const;
+};
+
+struct DeviceTables {
+  // FC matrices
+  double* Q = nullptr;       // [d][d]
+  double* Ar = nullptr;      // [Cr][d]
+  float* Ar_hi = nullptr;    // [Cr][d] TF32-representable high part of A_r
+  float* Ar_lo = nullptr;    // [Cr][d] remainder
+  // matching stencils
+  int32_t* gidx = nullptr;   // [B][M-1][M]  >= 0 grid index, < 0 boundary index -1-k
+  double* gw = nullptr;      // [B][M-1][M]
+  double* wn = nullptr;      // [B][d-1][M]
+  // strip points
+  int32_t* s_lin = nullptr;  // [n_strip]
+  double* s_theta = nullptr; // [n_strip]
+  double* s_eta = nullptr;   // [n_strip]
+  // per-row tables
+  int32_t* row_iv_off = nullptr;    // [ny+1] offsets into row_iv
+  int32_t* row_iv = nullptr;        // pairs (i_lo, i_hi), inclusive
+  int32_t* row_strip_off = nullptr; // [ny+1] offsets into the strip list
+  int* status = nullptr;            // latched device status word
+};
+
+struct ProfileRecord {
+  const char* name;
+  void* start;  // cudaEvent_t
+  void* stop;
+};
+
+struct Workspace {
+  void* base = nullptr;
+  size_t bytes = 0;
+};
+
+}  // namespace fc2d
+
+struct fc2d_plan_s {
+  fc2d_grid grid;
+  fc2d_params prm;
+  int Cr = 0;
+  int device = 0;
+  fc2d::Curve curve;
+  // host copies
+  std::vector<double> Q, Ar;                 // d*d, Cr*d
+  std::vector<double> bdry_xy;               // 2*n_bdry
+  std::vector<int32_t> strip_lin;
+  std::vector<double> strip_theta, strip_eta;
+  std::vector<int32_t> row_iv_off, row_iv, row_strip_off;
+  int64_t n_inside = 0;
+  int64_t n_bdry = 0;
+  fc2d::FftAxis fx, fy;                      // nx/2 (complex) and ny
+  std::vector<double> rtw_host;              // exp(-2 pi i k/nx), k <= nx/2 (R2C post-process)
+  double* rtw64 = nullptr;
+  float* rtw32 = nullptr;
+  fc2d::DeviceTables dev;
+  fc2d::Workspace ws;
+  int host_status = 0;
+  bool profiling = false;
+  std::vector<fc2d::ProfileRecord> prof;       // events of the current record
+  std::vector<void*> event_pool;               // reusable cudaEvent_t
+};
+
+namespace fc2d {
+// error reporting (thread-local message)
+fc2d_status set_error(fc2d_status s, const std::string& msg);
+fc2d_status cuda_check(int err, const char* what);
+
+// plan-time GPU kernel: Newton foot search.  Returns FC2D_OK or an error.
+fc2d_status foot_newton_gpu(const Curve& c, const std::vector<double>& qx,
+                            const std::vector<double>& qy, std::vector<double>& theta,
+                            std::vector<int>& conv);
+
+// workspace of at least `bytes` bytes (grows, synchronously, when needed)
+fc2d_status ensure_workspace(fc2d_plan_s* p, size_t bytes);
+
+// kernel timing: bracket one launch with events when the plan is profiling
+struct ProfScope {
+  fc2d_plan_s* p;
+  const char* name;
+  void* stream;
+  void* ev0 = nullptr;
+  ProfScope(fc2d_plan_s* p, const char* name, void* stream);
+  ~ProfScope();
+};
+}  // namespace fc2d

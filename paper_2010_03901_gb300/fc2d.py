@@ -1,0 +1,215 @@
+"""Thin ctypes binding of the 2D-FC C ABI (include/fc2d.h).
+
+Argument marshalling only: every computation runs in the CUDA library.  Device
+arrays are passed as anything with a ``data_ptr()`` (torch tensors) or as integer
+addresses; streams as ``torch.cuda.Stream`` objects, raw handles or None (the current
+torch stream).  The names follow the C entry points.  Importing this module loads
+the library and raises if it is missing: there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes as ct
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libfc2d.so")
+
+FC2D_FP64 = 0
+FC2D_MIXED = 1
+
+STATUS = {0: "FC2D_OK", 1: "FC2D_ERR_ARG", 2: "FC2D_ERR_GEOMETRY", 3: "FC2D_ERR_NOT_CONVERGED",
+          4: "FC2D_ERR_TIMEOUT", 5: "FC2D_ERR_NOMEM", 6: "FC2D_ERR_CUDA",
+          7: "FC2D_ERR_UNSUPPORTED"}
+
+
+class Fc2dError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class _Boundary(ct.Structure):
+    _fields_ = [("n_modes", ct.c_int), ("cx", ct.POINTER(ct.c_double)),
+                ("sx", ct.POINTER(ct.c_double)), ("cy", ct.POINTER(ct.c_double)),
+                ("sy", ct.POINTER(ct.c_double))]
+
+
+class _Grid(ct.Structure):
+    _fields_ = [("a0", ct.c_double), ("b0", ct.c_double), ("h", ct.c_double),
+                ("nx", ct.c_int), ("ny", ct.c_int)]
+
+
+class _Params(ct.Structure):
+    _fields_ = [("d", ct.c_int), ("C", ct.c_int), ("Z", ct.c_int), ("n_os", ct.c_int),
+                ("n_r", ct.c_int), ("M", ct.c_int), ("B", ct.c_int), ("m_F", ct.c_int),
+                ("k1", ct.c_double), ("precision", ct.c_int)]
+
+
+class _Info(ct.Structure):
+    _fields_ = [("grid", _Grid), ("params", _Params), ("n_strip", ct.c_int64),
+                ("n_inside", ct.c_int64), ("n_bdry", ct.c_int64),
+                ("workspace_bytes_per_function", ct.c_int64)]
+
+
+def load_library(path: str = LIB_PATH):
+    if not os.path.exists(path):
+        raise ImportError(f"2D-FC CUDA library not built: {path} (run __graft_entry__.build())")
+    lib = ct.CDLL(path)
+    P = ct.c_void_p
+    sigs = {
+        "fc2d_plan": [ct.POINTER(_Boundary), ct.POINTER(_Grid), ct.POINTER(_Params),
+                      ct.POINTER(ct.c_void_p)],
+        "fc2d_plan_info": [P, ct.POINTER(_Info)],
+        "fc2d_boundary_points": [P, P],
+        "fc2d_fc_matrices": [P, P, P],
+        "fc2d_strip_points": [P, P, P, P],
+        "fc2d_blend": [P, ct.c_int, P, P, P, P],
+        "fc2d_interp": [P, ct.c_int, P, P, P],
+        "fc2d_extend": [P, ct.c_int, P, P, P, P],
+        "fc2d_coeffs": [P, ct.c_int, P, P, P],
+        "fc2d_extend_coeffs": [P, ct.c_int, P, P, P, P],
+        "fc2d_sync_status": [P, P],
+        "fc2d_profile": [P, ct.c_int],
+        "fc2d_profile_read": [P, ct.c_int, P, P, P, P],
+    }
+    for name, args in sigs.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = ct.c_int
+    lib.fc2d_destroy.argtypes = [P]
+    lib.fc2d_destroy.restype = None
+    lib.fc2d_last_error.argtypes = []
+    lib.fc2d_last_error.restype = ct.c_char_p
+    return lib
+
+
+_lib = load_library()
+
+
+def _check(status):
+    if status != 0:
+        raise Fc2dError(status, _lib.fc2d_last_error().decode())
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    return x.data_ptr()
+
+
+def _stream(s):
+    if s is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(s, int):
+        return s
+    return s.cuda_stream
+
+
+class Plan:
+    """An fc2d plan: geometry, FC matrices and stencils for one domain and grid."""
+
+    def __init__(self, boundary, grid, params=None, precision=FC2D_FP64):
+        cx, sx, cy, sy = (np.ascontiguousarray(a, dtype=np.float64) for a in boundary)
+        self._keep = (cx, sx, cy, sy)
+        dp = ct.POINTER(ct.c_double)
+        b = _Boundary(len(cx), cx.ctypes.data_as(dp), sx.ctypes.data_as(dp),
+                      cy.ctypes.data_as(dp), sy.ctypes.data_as(dp))
+        a0, b0, h, nx, ny = grid
+        g = _Grid(a0, b0, h, nx, ny)
+        prm = dict(params or {})
+        p = _Params(prm.get("d", 0), prm.get("C", 0), prm.get("Z", 0), prm.get("n_os", 0),
+                    prm.get("n_r", 0), prm.get("M", 0), prm.get("B", 0), prm.get("m_F", 0),
+                    prm.get("k1", 0.0), precision)
+        h_ = ct.c_void_p()
+        _check(_lib.fc2d_plan(ct.byref(b), ct.byref(g), ct.byref(p), ct.byref(h_)))
+        self.handle = h_
+        self.precision = precision
+        inf = _Info()
+        _check(_lib.fc2d_plan_info(self.handle, ct.byref(inf)))
+        self.nx, self.ny = inf.grid.nx, inf.grid.ny
+        self.n_strip, self.n_inside, self.n_bdry = inf.n_strip, inf.n_inside, inf.n_bdry
+        pr = inf.params
+        self.params = dict(d=pr.d, C=pr.C, Z=pr.Z, n_os=pr.n_os, n_r=pr.n_r, M=pr.M, B=pr.B,
+                           m_F=pr.m_F, k1=pr.k1)
+        self.workspace_bytes_per_function = inf.workspace_bytes_per_function
+
+    # host queries -------------------------------------------------------------
+    def fc2d_boundary_points(self):
+        out = np.zeros((self.n_bdry, 2))
+        _check(_lib.fc2d_boundary_points(self.handle, out.ctypes.data))
+        return out
+
+    def fc2d_fc_matrices(self):
+        d, Cr = self.params["d"], self.params["C"] * self.params["n_r"]
+        Q = np.zeros((d, d))
+        Ar = np.zeros((Cr, d))
+        _check(_lib.fc2d_fc_matrices(self.handle, Q.ctypes.data, Ar.ctypes.data))
+        return Q, Ar
+
+    def fc2d_strip_points(self):
+        n = self.n_strip
+        lin = np.zeros(n, np.int32)
+        th = np.zeros(n)
+        eta = np.zeros(n)
+        _check(_lib.fc2d_strip_points(self.handle, lin.ctypes.data, th.ctypes.data,
+                                      eta.ctypes.data))
+        return lin, th, eta
+
+    # device computations ----------------------------------------------------------
+    def fc2d_blend(self, n_f, f_grid, f_bdry, F, stream=None):
+        _check(_lib.fc2d_blend(self.handle, n_f, _ptr(f_grid), _ptr(f_bdry), _ptr(F),
+                               _stream(stream)))
+
+    def fc2d_interp(self, n_f, F, vals, stream=None):
+        _check(_lib.fc2d_interp(self.handle, n_f, _ptr(F), _ptr(vals), _stream(stream)))
+
+    def fc2d_extend(self, n_f, f_grid, f_bdry, ext, stream=None):
+        _check(_lib.fc2d_extend(self.handle, n_f, _ptr(f_grid), _ptr(f_bdry), _ptr(ext),
+                                _stream(stream)))
+
+    def fc2d_coeffs(self, n_f, ext, fhat, stream=None):
+        _check(_lib.fc2d_coeffs(self.handle, n_f, _ptr(ext), _ptr(fhat), _stream(stream)))
+
+    def fc2d_extend_coeffs(self, n_f, f_grid, f_bdry, fhat, stream=None):
+        _check(_lib.fc2d_extend_coeffs(self.handle, n_f, _ptr(f_grid), _ptr(f_bdry),
+                                       _ptr(fhat), _stream(stream)))
+
+    def fc2d_profile(self, enable=True):
+        _check(_lib.fc2d_profile(self.handle, 1 if enable else 0))
+
+    def fc2d_profile_read(self):
+        """{kernel name: (launches, total ms)} since the last read."""
+        n = ct.c_int()
+        _check(_lib.fc2d_profile_read(self.handle, 0, None, None, None, ct.byref(n)))
+        k = max(n.value, 1)
+        names = ct.create_string_buffer(64 * k)
+        launches = np.zeros(k, np.int64)
+        ms = np.zeros(k)
+        _check(_lib.fc2d_profile_read(self.handle, k, names, launches.ctypes.data,
+                                      ms.ctypes.data, ct.byref(n)))
+        raw = names.raw
+        return {raw[64 * i:64 * i + 64].split(b"\0")[0].decode(): (int(launches[i]), float(ms[i]))
+                for i in range(n.value)}
+
+    def fc2d_sync_status(self, stream=None):
+        _check(_lib.fc2d_sync_status(self.handle, _stream(stream)))
+
+    def fc2d_destroy(self):
+        if self.handle:
+            _lib.fc2d_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.fc2d_destroy()
+        except Exception:
+            pass
+
+
+def fc2d_plan(boundary, grid, params=None, precision=FC2D_FP64) -> Plan:
+    return Plan(boundary, grid, params, precision)

@@ -1,0 +1,113 @@
+// Test harness: runs the library's host plan code (plan.cpp) on the CPU.
+//
+// The CUDA runtime calls the plan makes are redirected to host memory, and the plan's
+// GPU Newton foot search is replaced by the same iteration on the host, so that the
+// geometry, boundary points and matching stencils can be compared with the oracle
+// without a GPU.  Output: binary arrays on stdout (see dump()).
+#include <cuda_runtime.h>
+
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <vector>
+
+static cudaError_t h_malloc(void** p, size_t n) {
+  *p = std::malloc(n ? n : 1);
+  return cudaSuccess;
+}
+static cudaError_t h_free(void* p) {
+  std::free(p);
+  return cudaSuccess;
+}
+static cudaError_t h_memcpy(void* d, const void* s, size_t n, int) {
+  std::memcpy(d, s, n);
+  return cudaSuccess;
+}
+static cudaError_t h_getdev(int* d) {
+  *d = 0;
+  return cudaSuccess;
+}
+#define cudaMalloc(p, n) h_malloc((void**)(p), (n))
+#define cudaFree(p) h_free(p)
+#define cudaMemcpy(d, s, n, k) h_memcpy((d), (s), (n), (k))
+#define cudaGetDevice(d) h_getdev(d)
+
+#include "../paper_2010_03901_gb300/csrc/plan.cpp"
+
+namespace fc2d {
+fc2d_status foot_newton_gpu(const Curve& c, const std::vector<double>& qx,
+                            const std::vector<double>& qy, std::vector<double>& th,
+                            std::vector<int>& conv) {
+  conv.assign(qx.size(), 0);
+  for (size_t i = 0; i < qx.size(); ++i) {
+    double t = th[i];
+    for (int it = 0; it < 60; ++it) {
+      double x, y, x1, y1, x2, y2;
+      c.eval(t, x, y);
+      c.eval_d(t, 1, x1, y1);
+      c.eval_d(t, 2, x2, y2);
+      double phi = (x - qx[i]) * x1 + (y - qy[i]) * y1;
+      double dphi = x1 * x1 + y1 * y1 + (x - qx[i]) * x2 + (y - qy[i]) * y2;
+      if (!(dphi > 0)) break;
+      double step = phi / dphi;
+      t -= step;
+      if (std::fabs(step) < 1e-15) {
+        conv[i] = 1;
+        break;
+      }
+    }
+    th[i] = t;
+  }
+  return FC2D_OK;
+}
+}  // namespace fc2d
+
+template <typename T>
+static void dump(const char* name, const T* p, size_t n) {
+  std::printf("%s %zu %zu\n", name, n, sizeof(T));
+  std::fwrite(p, sizeof(T), n, stdout);
+  std::printf("\n");
+}
+
+int main(int argc, char** argv) {
+  // argv: n_modes cx.. sx.. cy.. sy.. a0 b0 h nx ny d C Z n_os n_r M B m_F k1
+  int a = 1;
+  int nm = std::atoi(argv[a++]);
+  std::vector<double> cx(nm), sx(nm), cy(nm), sy(nm);
+  for (auto* v : {&cx, &sx, &cy, &sy})
+    for (int k = 0; k < nm; ++k) (*v)[k] = std::atof(argv[a++]);
+  fc2d_grid g;
+  g.a0 = std::atof(argv[a++]);
+  g.b0 = std::atof(argv[a++]);
+  g.h = std::atof(argv[a++]);
+  g.nx = std::atoi(argv[a++]);
+  g.ny = std::atoi(argv[a++]);
+  fc2d_params P{};
+  P.d = std::atoi(argv[a++]);
+  P.C = std::atoi(argv[a++]);
+  P.Z = std::atoi(argv[a++]);
+  P.n_os = std::atoi(argv[a++]);
+  P.n_r = std::atoi(argv[a++]);
+  P.M = std::atoi(argv[a++]);
+  P.B = std::atoi(argv[a++]);
+  P.m_F = std::atoi(argv[a++]);
+  P.k1 = std::atof(argv[a++]);
+  fc2d_boundary b{nm, cx.data(), sx.data(), cy.data(), sy.data()};
+  fc2d_plan_t p = nullptr;
+  fc2d_status st = fc2d_plan(&b, &g, &P, &p);
+  std::printf("status %d %s\n", (int)st, fc2d_last_error());
+  if (st) return 0;
+  const size_t B = P.B, M = P.M, d = P.d;
+  dump("Q", p->Q.data(), p->Q.size());
+  dump("Ar", p->Ar.data(), p->Ar.size());
+  dump("strip_lin", p->strip_lin.data(), p->strip_lin.size());
+  dump("strip_theta", p->strip_theta.data(), p->strip_theta.size());
+  dump("strip_eta", p->strip_eta.data(), p->strip_eta.size());
+  dump("bdry_xy", p->bdry_xy.data(), p->bdry_xy.size());
+  dump("row_iv_off", p->row_iv_off.data(), p->row_iv_off.size());
+  dump("row_iv", p->row_iv.data(), p->row_iv.size());
+  dump("gidx", p->dev.gidx, B * (M - 1) * M);
+  dump("gw", p->dev.gw, B * (M - 1) * M);
+  dump("wn", p->dev.wn, B * (d - 1) * M);
+  return 0;
+}

@@ -1,0 +1,186 @@
+"""GPU parity: the CUDA path, called through the C ABI, against the FP64 oracle on the
+same seeded inputs.  Errors are relative max-norms ||gpu - oracle||_inf / ||oracle||_inf
+per output array; geometry decisions are bit-exact.
+
+Bars (FP64 path):
+* spectrum hat f^c (eq. (3.1)), the path's result, and the DFT alone: 1e-12;
+* strip values F and the extended grid: 3e-11.  The blending matrix W = A_r Q^T has
+  ||W||_inf = 1.18e4, so one ulp of relative change in the matching values moves F by up
+  to 9e-13, and two FP64 evaluations of the matching values in different summation
+  orders already disagree on F by up to 7.3e-12 (tests/test_oracle_fc2d.py pins this floor
+  on the oracle alone).  3e-11 is about four times that floor."""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import fc2d as OF
+from oracle import geometry as OG
+from oracle.fc_matrices import load_fc_matrices
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-12          # spectrum, DFT, interpolation from given strip values
+TOL_STRIP = 3e-11    # strip values and extended grid (about 4x the conditioning floor)
+CASES = ["disk64", "disk128", "star200", "kite160x144"]
+
+
+def rel(a, b):
+    return float(np.abs(np.asarray(a) - np.asarray(b)).max() / max(np.abs(b).max(), 1e-300))
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.fail("GPU test run without a CUDA device")
+    return torch
+
+
+@pytest.fixture(scope="module")
+def fc2d():
+    from paper_2010_03901_gb300 import fc2d as mod
+    return mod
+
+
+@pytest.fixture(scope="module")
+def mats():
+    return load_fc_matrices()
+
+
+def functions(w):
+    return [W.f_expsincos, W.gaussian_sum(w.boundary, 16, 3), W.trig_sum(12, 4)]
+
+
+class Case:
+    def __init__(self, name, fc2d, torch):
+        self.w = w = W.workload(name)
+        g, p = w.grid, w.params
+        self.geo = OG.build_geometry(w)
+        self.st = OF.matching_stencils(self.geo)
+        self.plan = fc2d.fc2d_plan(w.boundary.arrays(), (g.a0, g.b0, g.h, g.nx, g.ny),
+                                   dict(B=p.B, k1=p.k1))
+        self.fs = functions(w)
+        self.fg = np.stack([W.grid_values(w, f) for f in self.fs])
+        self.fb = np.stack([OF.boundary_values(self.geo, f) for f in self.fs])
+        dev = torch.device("cuda:0")
+        self.tg = torch.tensor(self.fg, dtype=torch.float64, device=dev)
+        self.tb = torch.tensor(self.fb, dtype=torch.float64, device=dev)
+        self.torch = torch
+        self.dev = dev
+
+
+_cases = {}
+
+
+@pytest.fixture(scope="module", params=CASES)
+def case(request, fc2d, torch_cuda):
+    if request.param not in _cases:
+        _cases[request.param] = Case(request.param, fc2d, torch_cuda)
+    return _cases[request.param]
+
+
+def test_fc_matrices_equal_oracle(case, mats):
+    Q, Ar = case.plan.fc2d_fc_matrices()
+    assert np.abs(Q - mats["Q"]).max() <= 2e-16
+    assert np.abs(Ar - mats["Ar"]).max() <= 4 * np.spacing(np.abs(mats["Ar"]).max())
+
+
+def test_strip_set_and_feet_equal_oracle(case):
+    lin, th, eta = case.plan.fc2d_strip_points()
+    geo = case.geo
+    assert np.array_equal(lin, geo.strip_lin)
+    dth = np.angle(np.exp(1j * (th - geo.strip_theta)))
+    assert np.abs(dth).max() < 1e-12
+    assert np.abs(eta - geo.strip_eta).max() < 1e-13
+    assert case.plan.n_inside == int(geo.inside.sum())
+
+
+def test_boundary_points_equal_oracle(case):
+    xy = case.plan.fc2d_boundary_points()
+    assert xy.shape[0] == len(case.geo.bdry_x)
+    assert np.abs(xy[:, 0] - case.geo.bdry_x).max() < 1e-13
+    assert np.abs(xy[:, 1] - case.geo.bdry_y).max() < 1e-13
+
+
+def test_blend_parity(case, mats):
+    """Section 3.2 + eq. (2.6): strip values F[f][p][q]."""
+    torch = case.torch
+    p = case.w.params
+    n_f = len(case.fs)
+    F = torch.zeros((n_f, p.B, p.C * p.n_r + 1), dtype=torch.float64, device=case.dev)
+    case.plan.fc2d_blend(n_f, case.tg, case.tb, F)
+    case.plan.fc2d_sync_status()
+    got = F.cpu().numpy()
+    for k in range(n_f):
+        fD = OF.matching_values(case.geo, case.st, case.fg[k], case.fb[k])
+        ref = OF.blend(mats, fD)
+        assert rel(got[k], ref) < TOL_STRIP, k
+
+
+def test_interp_parity(case, mats):
+    """Section 3.4 with the oracle's strip values as input."""
+    torch = case.torch
+    fD = OF.matching_values(case.geo, case.st, case.fg[0], case.fb[0])
+    F = OF.blend(mats, fD)
+    tF = torch.tensor(F[None], dtype=torch.float64, device=case.dev)
+    vals = torch.zeros((1, case.plan.n_strip), dtype=torch.float64, device=case.dev)
+    case.plan.fc2d_interp(1, tF, vals)
+    case.plan.fc2d_sync_status()
+    ref = OF.interpolate_strip(case.geo, F)
+    assert rel(vals.cpu().numpy()[0], ref) < TOL
+
+
+def test_extend_parity(case, mats):
+    torch = case.torch
+    g = case.w.grid
+    n_f = len(case.fs)
+    ext = torch.full((n_f, g.ny, g.nx), 7.0, dtype=torch.float64, device=case.dev)
+    case.plan.fc2d_extend(n_f, case.tg, case.tb, ext)
+    case.plan.fc2d_sync_status()
+    got = ext.cpu().numpy()
+    for k in range(n_f):
+        ref = OF.extension(case.geo, mats, case.fg[k], case.fb[k], case.st)
+        assert rel(got[k], ref) < TOL_STRIP, k
+        assert np.array_equal(got[k][case.geo.inside], case.fg[k][case.geo.inside])
+
+
+def test_coeffs_parity(case, mats):
+    """Eq. (3.1) DFT of the oracle's extension."""
+    torch = case.torch
+    g = case.w.grid
+    ref_ext = OF.extension(case.geo, mats, case.fg[1], case.fb[1], case.st)
+    t = torch.tensor(ref_ext[None], dtype=torch.float64, device=case.dev)
+    fhat = torch.zeros((1, g.ny, g.nx // 2 + 1, 2), dtype=torch.float64, device=case.dev)
+    case.plan.fc2d_coeffs(1, t, fhat)
+    case.plan.fc2d_sync_status()
+    got = fhat.cpu().numpy()[0]
+    got = got[..., 0] + 1j * got[..., 1]
+    assert rel(got, OF.coefficients(ref_ext)) < TOL
+
+
+def test_extend_coeffs_parity(case, mats):
+    torch = case.torch
+    g = case.w.grid
+    n_f = len(case.fs)
+    fhat = torch.zeros((n_f, g.ny, g.nx // 2 + 1, 2), dtype=torch.float64, device=case.dev)
+    case.plan.fc2d_extend_coeffs(n_f, case.tg, case.tb, fhat)
+    case.plan.fc2d_sync_status()
+    got = fhat.cpu().numpy()
+    for k in range(n_f):
+        ref = OF.coefficients(OF.extension(case.geo, mats, case.fg[k], case.fb[k], case.st))
+        gk = got[k][..., 0] + 1j * got[k][..., 1]
+        assert rel(gk, ref) < TOL, k
+
+
+def test_values_outside_the_domain_are_ignored(case):
+    torch = case.torch
+    g = case.w.grid
+    noisy = case.tg.clone()
+    mask = torch.tensor(~case.geo.inside, device=case.dev)
+    noisy[:, mask] = 1e30
+    a = torch.zeros((len(case.fs), g.ny, g.nx // 2 + 1, 2), dtype=torch.float64, device=case.dev)
+    b = torch.zeros_like(a)
+    case.plan.fc2d_extend_coeffs(len(case.fs), case.tg, case.tb, a)
+    case.plan.fc2d_extend_coeffs(len(case.fs), noisy, case.tb, b)
+    case.plan.fc2d_sync_status()
+    assert torch.equal(a, b)

@@ -1,0 +1,76 @@
+"""The library's host plan (plan.cpp), run on the CPU through tests/host_plan_harness.cpp,
+against the oracle: FC matrices, inside test, strip points and feet, boundary points and
+the matching stencils of Section 3.2."""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import fc2d as OF
+from oracle import geometry as OG
+from oracle.fc_matrices import load_fc_matrices
+from tests import host_plan
+
+CASES = ["disk64", "disk128", "star200", "kite160x144"]
+
+
+@pytest.fixture(scope="module", params=CASES)
+def both(request):
+    w = W.workload(request.param)
+    r = host_plan.run(w)
+    assert r["status"] == 0, r["error"]
+    return w, r, OG.build_geometry(w)
+
+
+def test_fc_matrices_in_double_double_equal_the_oracle(both):
+    w, r, geo = both
+    m = load_fc_matrices()
+    assert np.array_equal(r["Q"].reshape(m["Q"].shape), m["Q"]) or \
+        np.abs(r["Q"].reshape(m["Q"].shape) - m["Q"]).max() <= 2e-16
+    Ar = r["Ar"].reshape(m["Ar"].shape)
+    assert np.abs(Ar - m["Ar"]).max() <= 4 * np.spacing(np.abs(m["Ar"]).max())
+
+
+def test_inside_intervals_equal_oracle(both):
+    w, r, geo = both
+    g = w.grid
+    inside = np.zeros((g.ny, g.nx), bool)
+    off, iv = r["row_iv_off"], r["row_iv"].reshape(-1, 2)
+    for j in range(g.ny):
+        for k in range(off[j], off[j + 1]):
+            inside[j, iv[k, 0]:iv[k, 1] + 1] = True
+    assert np.array_equal(inside, geo.inside)
+
+
+def test_strip_points_equal_oracle(both):
+    w, r, geo = both
+    assert np.array_equal(r["strip_lin"], geo.strip_lin)
+    dth = np.angle(np.exp(1j * (r["strip_theta"] - geo.strip_theta)))
+    assert np.abs(dth).max() < 1e-12
+    assert np.abs(r["strip_eta"] - geo.strip_eta).max() < 1e-13
+
+
+def test_boundary_points_equal_oracle(both):
+    w, r, geo = both
+    xy = r["bdry_xy"].reshape(-1, 2)
+    assert len(xy) == len(geo.bdry_x)
+    assert np.abs(xy[:, 0] - geo.bdry_x).max() < 1e-13
+    assert np.abs(xy[:, 1] - geo.bdry_y).max() < 1e-13
+
+
+def test_matching_stencils_give_the_oracle_matching_values(both):
+    w, r, geo = both
+    p = w.params
+    B, M, d = p.B, p.M, p.d
+    f = W.f_expsincos
+    fg = W.grid_values(w, f).ravel()
+    fb = OF.boundary_values(geo, f)
+    gidx = r["gidx"].reshape(B, M - 1, M)
+    gw = r["gw"].reshape(B, M - 1, M)
+    wn = r["wn"].reshape(B, d - 1, M)
+    vals = np.where(gidx >= 0, fg[np.maximum(gidx, 0)], fb[np.maximum(-1 - gidx, 0)])
+    stars = np.einsum("bse,bse->bs", gw, vals)
+    nodes = np.concatenate([fb[:B, None], stars], axis=1)
+    fD = np.einsum("bqe,be->bq", wn, nodes)
+    st = OF.matching_stencils(geo)
+    ref = OF.matching_values(geo, st, W.grid_values(w, f), fb)
+    assert np.abs(fD - ref[:, :d - 1]).max() < 1e-13 * np.abs(ref).max()

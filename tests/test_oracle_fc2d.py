@@ -141,3 +141,28 @@ def test_kite_accuracy_matches_paper_table2(mats):
         w = paper_setup(W.kite(0.35, 0.7), h, d=int(d))
         e = fine_error(w, mats, W.f_kite_paper, relative=False)
         assert ref / 4 <= e <= ref * 4, (h, e, ref)
+
+
+def test_blend_conditioning_floor(mats):
+    """The strip values are ill-conditioned in the matching values: ||A_r Q^T||_inf is
+    ~1.2e4, so evaluating the matching values in two FP64 summation orders (here the
+    oracle's per-term sum against one einsum over the stencil weights) moves F by a few
+    1e-12 relative.  This floor (7e-12 here) justifies the 3e-11 parity bar on strip values."""
+    W_ = mats["Ar"] @ mats["Q"].T
+    assert 1.0e4 < np.abs(W_).sum(axis=1).max() < 1.5e4
+    w = W.workload("star200")
+    geo = G.build_geometry(w)
+    st = F.matching_stencils(geo)
+    f = W.f_expsincos
+    fg = W.grid_values(w, f)
+    fb = F.boundary_values(geo, f)
+    fD0 = F.matching_values(geo, st, fg, fb)
+    flat = fg.ravel()
+    fD1 = fD0.copy()
+    for k, s in enumerate(st):
+        stars = np.array([np.einsum("i,i->", np.array(list(t.values())),
+                                    np.array([flat[key[1]] if key[0] == "g" else fb[key[1]]
+                                              for key in t])) for t in s["stars"]])
+        fD1[k, :-1] = np.einsum("qe,e->q", np.array(s["wn"]), stars)
+    d = np.abs(F.blend(mats, fD1) - F.blend(mats, fD0)).max() / np.abs(F.blend(mats, fD0)).max()
+    assert 1e-13 < d < 3e-11 / 3, d

@@ -163,6 +163,8 @@ WORKLOADS = {
     # The same kite at 2048^2 (wave workload).
     "kite2048": Workload("kite2048", kite(0.65, 1.5), _sq(-1.776, -1.53, 3.06, 2048),
                          Params(B=4096, k1=3.06 / 2048)),
+    "kite1024": Workload("kite1024", kite(0.65, 1.5), _sq(-1.776, -1.53, 3.06, 1024),
+                         Params(B=2048, k1=3.06 / 1024)),
     # Small cases for CPU tests and quick parity: several tiles and ragged sizes.
     "disk64": Workload("disk64", disk(), _sq(-2.0, -2.0, 4.0, 64), Params(B=128, k1=0.03)),
     "kite160x144": Workload("kite160x144", kite(0.65, 1.5),
