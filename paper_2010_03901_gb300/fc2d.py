@@ -182,19 +182,18 @@ class Plan:
     def fc2d_profile(self, enable=True):
         _check(_lib.fc2d_profile(self.handle, 1 if enable else 0))
 
-    def fc2d_profile_read(self):
-        """{kernel name: (launches, total ms)} since the last read."""
+    def fc2d_profile_read(self, max_kernels=64):
+        """{kernel name: (launches, total ms)} since the last read (the read clears)."""
         n = ct.c_int()
-        _check(_lib.fc2d_profile_read(self.handle, 0, None, None, None, ct.byref(n)))
-        k = max(n.value, 1)
-        names = ct.create_string_buffer(64 * k)
-        launches = np.zeros(k, np.int64)
-        ms = np.zeros(k)
-        _check(_lib.fc2d_profile_read(self.handle, k, names, launches.ctypes.data,
+        names = ct.create_string_buffer(64 * max_kernels)
+        launches = np.zeros(max_kernels, np.int64)
+        ms = np.zeros(max_kernels)
+        _check(_lib.fc2d_profile_read(self.handle, max_kernels, names, launches.ctypes.data,
                                       ms.ctypes.data, ct.byref(n)))
         raw = names.raw
+        k = min(n.value, max_kernels)
         return {raw[64 * i:64 * i + 64].split(b"\0")[0].decode(): (int(launches[i]), float(ms[i]))
-                for i in range(n.value)}
+                for i in range(k)}
 
     def fc2d_sync_status(self, stream=None):
         _check(_lib.fc2d_sync_status(self.handle, _stream(stream)))
