@@ -145,6 +145,24 @@ fc2d_status fc2d_coeffs(fc2d_plan_t plan, int n_f, const void* ext_dev, void* fh
 fc2d_status fc2d_extend_coeffs(fc2d_plan_t plan, int n_f, const double* f_grid_dev,
                                const double* f_bdry_dev, void* fhat_dev, void* stream);
 
+/* The DFT of fc2d_coeffs for callers that cannot allocate device memory at call time.
+ * The paper has no counterpart: this is a service of the library.  fc2d_coeffs grows
+ * plan workspace with cudaMalloc on the first call of a new size; this entry point
+ * calls no allocator (no cudaMalloc, cudaFree or allocating library routine).  It is
+ * meant for callers that own all device memory through their own allocator, or that
+ * run where an allocation's implicit device synchronisation is not acceptable.
+ * Its scratch is one fixed device array of 64 MiB (the row-DFT intermediate,
+ * n_f * ny * (nx/2+1 rounded up to 8) complex values), held by every GPU that loads
+ * the library until the process exits.  Larger requests return FC2D_ERR_ARG.
+ * The first call on a device looks up the array's device address for that device
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * All calls share the one array: calls that overlap on the GPU (different streams,
+ * or different plans, at the same time) race; serialise them.  Nothing in the array
+ * has to start at zero.  Arguments and result as fc2d_coeffs; the plan's tables were
+ * allocated by fc2d_plan. */
+fc2d_status fc2d_coeffs_static(fc2d_plan_t plan, int n_f, const void* ext_dev, void* fhat_dev,
+                               void* stream);
+
 /* Kernel timing (tracing).  While enabled, every kernel the plan launches is
  * bracketed by a pair of CUDA events recorded on its launching stream.
  * fc2d_profile_read waits for those events and returns, per kernel name, the number

@@ -70,6 +70,7 @@ def load_library(path: str = LIB_PATH):
         "fc2d_extend": [P, ct.c_int, P, P, P, P],
         "fc2d_coeffs": [P, ct.c_int, P, P, P],
         "fc2d_extend_coeffs": [P, ct.c_int, P, P, P, P],
+        "fc2d_coeffs_static": [P, ct.c_int, P, P, P],
         "fc2d_sync_status": [P, P],
         "fc2d_profile": [P, ct.c_int],
         "fc2d_profile_read": [P, ct.c_int, P, P, P, P],
@@ -178,6 +179,11 @@ class Plan:
     def fc2d_extend_coeffs(self, n_f, f_grid, f_bdry, fhat, stream=None):
         _check(_lib.fc2d_extend_coeffs(self.handle, n_f, _ptr(f_grid), _ptr(f_bdry),
                                        _ptr(fhat), _stream(stream)))
+
+    def fc2d_coeffs_static(self, n_f, ext, fhat, stream=None):
+        """fc2d_coeffs without any device allocation (fixed 64 MiB scratch)."""
+        _check(_lib.fc2d_coeffs_static(self.handle, n_f, _ptr(ext), _ptr(fhat),
+                                       _stream(stream)))
 
     def fc2d_profile(self, enable=True):
         _check(_lib.fc2d_profile(self.handle, 1 if enable else 0))
