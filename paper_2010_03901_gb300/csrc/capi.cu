@@ -87,10 +87,9 @@ InterpArgs interp_args(fc2d_plan_s* p) {
   a.M = p->prm.M;
   a.B = p->prm.B;
   a.Cr = p->Cr;
-  a.inv_k2 = p->prm.B / (2.0 * M_PI);
-  a.nr_over_k1 = p->prm.n_r / p->prm.k1;
-  a.theta = p->dev.s_theta;
-  a.eta = p->dev.s_eta;
+  a.w = p->dev.s_w;
+  a.pb = p->dev.s_pb;
+  a.sb = p->dev.s_sb;
   return a;
 }
 
@@ -134,6 +133,21 @@ fc2d_status check_nf(fc2d_plan_s* p, int n_f) {
 
 fc2d_status launched(const char* what) { return cuda_check(cudaGetLastError(), what); }
 
+// Mixed form of step 5: matching values and Gram coefficients in FP64, then the
+// contraction with A_r on the tensor cores into float strip values F.
+fc2d_status mixed_blend(fc2d_plan_s* p, int n_f, const double* fg, const double* fb, void* F,
+                        const Layout& L, cudaStream_t s) {
+  double* coef = reinterpret_cast<double*>(ws(p, L.ocoef));
+  double* bvals = reinterpret_cast<double*>(ws(p, L.obvals));
+  {
+    ProfScope ps(p, "gather_coef", s);
+    launch_gather_blend(gather_args(p, fg, fb, nullptr, coef, bvals), n_f, false, s);
+  }
+  ProfScope ps(p, "blend_tc", s);
+  return launch_blend_tc(n_f * p->prm.B, p->Cr, p->prm.d, p->Cr + 1, coef, kMaxD, bvals,
+                         p->dev.Ar_hi, p->dev.Ar_lo, static_cast<float*>(F), p->dev.status, s);
+}
+
 // Steps 5 and 6 into workspace: strip values F, then the strip-point values.
 fc2d_status strip_values(fc2d_plan_s* p, int n_f, const double* fg, const double* fb,
                          const Layout& L, cudaStream_t s) {
@@ -143,7 +157,8 @@ fc2d_status strip_values(fc2d_plan_s* p, int n_f, const double* fg, const double
     ProfScope ps(p, "gather_blend", s);
     launch_gather_blend(gather_args(p, fg, fb, F, nullptr, nullptr), n_f, true, s);
   } else {
-    return set_error(FC2D_ERR_UNSUPPORTED, "mixed precision blend not built yet");
+    fc2d_status st = mixed_blend(p, n_f, fg, fb, F, L, s);
+    if (st) return st;
   }
   {
     ProfScope ps(p, "interp", s);
@@ -165,7 +180,10 @@ extern "C" fc2d_status fc2d_blend(fc2d_plan_t p, int n_f, const double* fg, cons
     launch_gather_blend(gather_args(p, fg, fb, F, nullptr, nullptr), n_f, true, s);
     return launched("fc2d_blend");
   }
-  return set_error(FC2D_ERR_UNSUPPORTED, "mixed precision blend not built yet");
+  Layout L = layout(p, n_f);
+  if ((st = ensure_workspace(p, L.total))) return st;
+  if ((st = mixed_blend(p, n_f, fg, fb, F, L, s))) return st;
+  return launched("fc2d_blend");
 }
 
 extern "C" fc2d_status fc2d_interp(fc2d_plan_t p, int n_f, const void* F, void* vals,

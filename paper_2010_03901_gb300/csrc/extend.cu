@@ -210,43 +210,103 @@ __device__ __forceinline__ void lagrange_equispaced(int M, double t, double* w) 
   }
 }
 
-template <typename TF, typename TV>
-__global__ void __launch_bounds__(256) k_interp(InterpArgs a, const TF* __restrict__ F,
-                                                TV* __restrict__ vals) {
+// Plan time, FP64: per strip point the theta and eta Lagrange weights (2 M values,
+// stored [2M][n_strip], as double for the FP64 form and rounded to float for the mixed
+// form), the first normal index p0 - K_l (may be negative: rows wrap mod B) and the
+// first fine index s.
+template <typename TW>
+__global__ void k_interp_weights(int n_strip, int M, int Cr, double inv_k2, double nr_over_k1,
+                                 const double* __restrict__ theta, const double* __restrict__ eta,
+                                 TW* __restrict__ w, int32_t* __restrict__ pb,
+                                 int32_t* __restrict__ sb) {
   int n = blockIdx.x * blockDim.x + threadIdx.x;
-  int f = blockIdx.y;
-  if (n >= a.n_strip) return;
-  const int M = a.M, Kl = (M + 1) / 2 - 1, B = a.B, ld = a.Cr + 1;
-  double tt = __ldg(a.theta + n) * a.inv_k2;
+  if (n >= n_strip) return;
+  const int Kl = (M + 1) / 2 - 1;
+  double tt = theta[n] * inv_k2;
   double p0 = floor(tt);
   double wth[kMaxM], weta[kMaxM];
   lagrange_equispaced(M, tt - (p0 - Kl), wth);
-  double u = __ldg(a.eta + n) * a.nr_over_k1;
+  double u = eta[n] * nr_over_k1;
   int s = (int)floor(u) - Kl;
-  s = s < 0 ? 0 : (s > a.Cr + 1 - M ? a.Cr + 1 - M : s);
+  s = s < 0 ? 0 : (s > Cr + 1 - M ? Cr + 1 - M : s);
   lagrange_equispaced(M, u - s, weta);
+  for (int k = 0; k < M; ++k) {
+    w[(size_t)k * n_strip + n] = (TW)wth[k];
+    w[(size_t)(M + k) * n_strip + n] = (TW)weta[k];
+  }
+  pb[n] = (int32_t)p0 - Kl;
+  sb[n] = s;
+}
+
+fc2d_status interp_weights_gpu(int n_strip, int M, int Cr, int B, double k1, int n_r,
+                               const double* theta_dev, const double* eta_dev, bool fp64,
+                               void* w_dev, int32_t* pb_dev, int32_t* sb_dev) {
+  if (n_strip == 0) return FC2D_OK;
+  const double inv_k2 = B / (2.0 * M_PI), nr_over_k1 = n_r / k1;
+  const unsigned g = (unsigned)((n_strip + 255) / 256);
+  if (fp64)
+    k_interp_weights<double><<<g, 256>>>(n_strip, M, Cr, inv_k2, nr_over_k1, theta_dev, eta_dev,
+                                         (double*)w_dev, pb_dev, sb_dev);
+  else
+    k_interp_weights<float><<<g, 256>>>(n_strip, M, Cr, inv_k2, nr_over_k1, theta_dev, eta_dev,
+                                        (float*)w_dev, pb_dev, sb_dev);
+  fc2d_status st = cuda_check(cudaGetLastError(), "interpolation weights launch");
+  if (st == FC2D_OK) st = cuda_check(cudaDeviceSynchronize(), "interpolation weights");
+  return st;
+}
+
+// Per call: value = sum_a wth[a] sum_b weta[b] F[(pb + a) mod B][s + b], accumulated in
+// TA (double for the FP64 form, float for the mixed form).  MM > 0: compile-time M.
+template <int MM, typename TF, typename TW, typename TA, typename TV>
+__global__ void __launch_bounds__(256) k_interp(InterpArgs a, const TF* __restrict__ F,
+                                                TV* __restrict__ vals) {
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  const int f = blockIdx.y;
+  if (n >= a.n_strip) return;
+  const int M = MM > 0 ? MM : a.M;
+  const int B = a.B, ld = a.Cr + 1, ns = a.n_strip;
+  const TW* w = reinterpret_cast<const TW*>(a.w);
+  const int pb = __ldg(a.pb + n), s = __ldg(a.sb + n);
+  TW weta[MM > 0 ? MM : kMaxM];
+#pragma unroll
+  for (int b = 0; b < (MM > 0 ? MM : kMaxM); ++b)
+    if (b < M) weta[b] = __ldg(w + (size_t)(M + b) * ns + n);
   const TF* Ff = F + (size_t)f * B * ld;
-  int pb = (int)p0 - Kl;
-  double acc = 0.0;
-  for (int ai = 0; ai < M; ++ai) {
+  TA acc = 0;
+#pragma unroll
+  for (int ai = 0; ai < (MM > 0 ? MM : kMaxM); ++ai) {
+    if (ai >= M) break;
     int pr = pb + ai;
     pr = pr < 0 ? pr + B : (pr >= B ? pr - B : pr);
     const TF* row = Ff + (size_t)pr * ld + s;
-    double v = 0.0;
-    for (int b = 0; b < M; ++b) v = fma(weta[b], (double)__ldg(row + b), v);
-    acc = fma(wth[ai], v, acc);
+    TA v = 0;
+#pragma unroll
+    for (int b = 0; b < (MM > 0 ? MM : kMaxM); ++b)
+      if (b < M) v = fma((TA)weta[b], (TA)__ldg(row + b), v);
+    acc = fma((TA)__ldg(w + (size_t)ai * ns + n), v, acc);
   }
-  vals[(size_t)f * a.n_strip + n] = (TV)acc;
+  vals[(size_t)f * ns + n] = (TV)acc;
 }
 
 void launch_interp(const InterpArgs& a, int n_f, bool fp64, const void* F, void* vals,
                    cudaStream_t s) {
   if (a.n_strip == 0) return;
   dim3 grid((a.n_strip + 255) / 256, n_f);
-  if (fp64)
-    k_interp<double, double><<<grid, 256, 0, s>>>(a, (const double*)F, (double*)vals);
-  else
-    k_interp<float, float><<<grid, 256, 0, s>>>(a, (const float*)F, (float*)vals);
+  if (fp64) {
+    if (a.M == 8)
+      k_interp<8, double, double, double, double><<<grid, 256, 0, s>>>(a, (const double*)F,
+                                                                       (double*)vals);
+    else
+      k_interp<0, double, double, double, double><<<grid, 256, 0, s>>>(a, (const double*)F,
+                                                                       (double*)vals);
+  } else {
+    if (a.M == 8)
+      k_interp<8, float, float, float, float><<<grid, 256, 0, s>>>(a, (const float*)F,
+                                                                   (float*)vals);
+    else
+      k_interp<0, float, float, float, float><<<grid, 256, 0, s>>>(a, (const float*)F,
+                                                                   (float*)vals);
+  }
 }
 
 // ------------------------------------------------------------------------- //

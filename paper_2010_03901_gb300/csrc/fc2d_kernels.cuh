@@ -4,6 +4,8 @@
 
 #include <cstdint>
 
+#include "../../include/fc2d.h"
+
 namespace fc2d {
 
 constexpr int kMaxD = 8;
@@ -26,10 +28,14 @@ struct GatherArgs {
 
 struct InterpArgs {
   int n_strip, M, B, Cr;
-  double inv_k2, nr_over_k1;
-  const double* theta;
-  const double* eta;
+  const void* w;         // [2M][n_strip] theta then eta weights (double or float)
+  const int32_t* pb;     // first normal index (mod B)
+  const int32_t* sb;     // first fine index along the normal
 };
+
+fc2d_status interp_weights_gpu(int n_strip, int M, int Cr, int B, double k1, int n_r,
+                               const double* theta_dev, const double* eta_dev, bool fp64,
+                               void* w_dev, int32_t* pb_dev, int32_t* sb_dev);
 
 struct RowArgs {
   int nx, ny;
@@ -40,6 +46,7 @@ struct RowArgs {
   const int32_t* s_lin;
 };
 
+#if defined(__CUDACC__)
 // Fill a shared-memory row with the extension: 0, then f on the inside intervals,
 // then the strip values.  Ends with the row complete (after a __syncthreads()).
 template <typename T, typename TV>
@@ -60,8 +67,14 @@ __device__ __forceinline__ void load_row(const RowArgs& a, int j, int f,
   for (int k = s0 + threadIdx.x; k < s1; k += blockDim.x)
     row[__ldg(a.s_lin + k) - base] = (T)__ldg(v + k);
 }
+#endif
 
 void launch_gather_blend(const GatherArgs& a, int n_f, bool fp64, cudaStream_t s);
+// mixed form of the blend: F[n][0] = bvals[n], F[n][1+q] = (A_r c_n)_q on the tensor
+// cores (TF32 hi/lo, FP32 accumulate); n over n_cols = n_f * B normals, row stride ldF.
+fc2d_status launch_blend_tc(int n_cols, int Cr, int d, int ldF, const double* coef,
+                            int coef_ld, const double* bvals, const float* Ar_hi,
+                            const float* Ar_lo, float* F, int* status, cudaStream_t s);
 void launch_interp(const InterpArgs& a, int n_f, bool fp64, const void* F, void* vals,
                    cudaStream_t s);
 void launch_assemble(const RowArgs& a, int n_f, bool fp64, const double* f_grid,

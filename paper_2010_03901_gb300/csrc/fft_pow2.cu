@@ -1,0 +1,349 @@
+// Power-of-two DFT kernels (eq. (3.1)): compile-time radix, one shared buffer.
+//
+// A transform of N = 2^LOGN complex points is done by NT = N/E threads, each holding
+// E complex values in registers (E = 16 for float, 8 for double).  Every Stockham
+// stage (radix R dividing E; R = E except a smaller last stage) is:
+//   read the thread's E inputs x[j + r N/R] from shared memory, barrier,
+//   twiddle by exp(-2 pi i r (j mod Ns)/(Ns R)) (table lookups), length-R DFT,
+//   write y[(j/Ns) Ns R + (j mod Ns) + r Ns], barrier,
+// so one buffer of N values suffices.  Shared indices are padded by one element per
+// 32 (float) or 16 (double) to break the bank conflicts of the strided writes.
+//
+// k_fft_rows_p2: one block per (row, function): the extension row (fused load from
+// f and the strip values, or a plain grid row) as nx/2 complex pairs, the length-nx/2
+// transform, the even/odd split to X_k, k = 0..nx/2, written to the intermediate.
+// k_fft_cols_p2: one block per (CB columns, function): length-ny column transforms,
+// scaled by 1/(nx ny), written to the half spectrum [ny][nx/2+1].
+#include <cuda_runtime.h>
+
+#include "fc2d_kernels.cuh"
+
+namespace fc2d {
+namespace p2 {
+
+template <typename T> struct Cx;
+template <> struct Cx<double> { using type = double2; };
+template <> struct Cx<float> { using type = float2; };
+
+template <typename C> __device__ __forceinline__ C add(C a, C b) { return {a.x + b.x, a.y + b.y}; }
+template <typename C> __device__ __forceinline__ C sub(C a, C b) { return {a.x - b.x, a.y - b.y}; }
+template <typename C> __device__ __forceinline__ C mul(C a, C b) {
+  return {a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
+}
+template <typename C> __device__ __forceinline__ C mul_mi(C a) { return {a.y, -a.x}; }
+
+// exp(-2 pi i m/16), m = 0..15
+template <typename T, typename C>
+__device__ __forceinline__ C w16(int m) {
+  const T c1 = (T)0.92387953251128675613, s1 = (T)0.38268343236508977173;
+  const T h = (T)0.70710678118654752440;
+  switch (m & 15) {
+    case 0: return C{(T)1, (T)0};
+    case 1: return C{c1, -s1};
+    case 2: return C{h, -h};
+    case 3: return C{s1, -c1};
+    case 4: return C{(T)0, (T)-1};
+    case 5: return C{-s1, -c1};
+    case 6: return C{-h, -h};
+    case 7: return C{-c1, -s1};
+    case 8: return C{(T)-1, (T)0};
+    case 9: return C{-c1, s1};
+    case 10: return C{-h, h};
+    case 11: return C{-s1, c1};
+    case 12: return C{(T)0, (T)1};
+    case 13: return C{s1, c1};
+    case 14: return C{h, h};
+    default: return C{c1, s1};
+  }
+}
+
+template <typename C> __device__ __forceinline__ void dft2(C* v) {
+  C a = v[0], b = v[1];
+  v[0] = add(a, b);
+  v[1] = sub(a, b);
+}
+
+template <typename C> __device__ __forceinline__ void dft4(C& a0, C& a1, C& a2, C& a3) {
+  C t0 = add(a0, a2), t1 = sub(a0, a2), t2 = add(a1, a3), t3 = mul_mi(sub(a1, a3));
+  a0 = add(t0, t2);
+  a2 = sub(t0, t2);
+  a1 = add(t1, t3);
+  a3 = sub(t1, t3);
+}
+
+template <typename T, typename C> __device__ __forceinline__ void dft8(C* v) {
+  const T s = (T)0.70710678118654752440;
+  C e0 = v[0], e1 = v[2], e2 = v[4], e3 = v[6];
+  C o0 = v[1], o1 = v[3], o2 = v[5], o3 = v[7];
+  dft4(e0, e1, e2, e3);
+  dft4(o0, o1, o2, o3);
+  C w1 = {s * (o1.x + o1.y), s * (o1.y - o1.x)};
+  C w2 = mul_mi(o2);
+  C w3 = {s * (o3.y - o3.x), -s * (o3.x + o3.y)};
+  v[0] = add(e0, o0);
+  v[4] = sub(e0, o0);
+  v[1] = add(e1, w1);
+  v[5] = sub(e1, w1);
+  v[2] = add(e2, w2);
+  v[6] = sub(e2, w2);
+  v[3] = add(e3, w3);
+  v[7] = sub(e3, w3);
+}
+
+// 16-point DFT as 4 x 4: inner DFT4 over n1 for each n2, twiddle w16^(n2 k1), outer
+// DFT4 over n2; X[k1 + 4 k2] lands in v[k1 + 4 k2].
+template <typename T, typename C> __device__ __forceinline__ void dft16(C* v) {
+  C a[16];
+#pragma unroll
+  for (int n2 = 0; n2 < 4; ++n2) {
+    C x0 = v[n2], x1 = v[4 + n2], x2 = v[8 + n2], x3 = v[12 + n2];
+    dft4(x0, x1, x2, x3);  // x_k1 = sum_n1 v[4 n1 + n2] w4^(n1 k1)
+    a[4 * n2 + 0] = x0;
+    a[4 * n2 + 1] = n2 ? mul(x1, w16<T, C>(n2)) : x1;
+    a[4 * n2 + 2] = n2 ? mul(x2, w16<T, C>(2 * n2)) : x2;
+    a[4 * n2 + 3] = n2 ? mul(x3, w16<T, C>(3 * n2)) : x3;
+  }
+#pragma unroll
+  for (int k1 = 0; k1 < 4; ++k1) {
+    C y0 = a[k1], y1 = a[4 + k1], y2 = a[8 + k1], y3 = a[12 + k1];
+    dft4(y0, y1, y2, y3);
+    v[k1] = y0;
+    v[k1 + 4] = y1;
+    v[k1 + 8] = y2;
+    v[k1 + 12] = y3;
+  }
+}
+
+template <typename T, typename C, int R> __device__ __forceinline__ void dft(C* v) {
+  if constexpr (R == 2) dft2(v);
+  else if constexpr (R == 4) dft4(v[0], v[1], v[2], v[3]);
+  else if constexpr (R == 8) dft8<T, C>(v);
+  else dft16<T, C>(v);
+}
+
+template <typename T> __host__ __device__ constexpr int pad_shift() { return sizeof(T) == 4 ? 5 : 4; }
+template <typename T> __device__ __forceinline__ int pad(int i) { return i + (i >> pad_shift<T>()); }
+template <typename T> __host__ __device__ constexpr int padded(int n) { return n + (n >> pad_shift<T>()); }
+
+// One Stockham stage of radix R on buffer `buf` (padded), NT threads, butterflies
+// j = t + m NT, m < E/R.  Ns = product of the earlier radices.
+template <typename T, int LOGN, int E, int R, int NS>
+__device__ __forceinline__ void stage(typename Cx<T>::type* buf, int t, bool active,
+                                      const typename Cx<T>::type* __restrict__ tw, int tws) {
+  using C = typename Cx<T>::type;
+  constexpr int N = 1 << LOGN;
+  constexpr int NT = N / E;
+  constexpr int NR = N / R;
+  constexpr int M = E / R;
+  constexpr int TSTEP = N / (NS * R);
+  C v[E];
+  if (active) {
+#pragma unroll
+    for (int m = 0; m < M; ++m) {
+      const int j = t + m * NT;
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[m * R + r] = buf[pad<T>(j + r * NR)];
+    }
+  }
+  __syncthreads();
+  if (active) {
+#pragma unroll
+  for (int m = 0; m < M; ++m) {
+    const int j = t + m * NT;
+    const int k = j & (NS - 1);
+    if (NS > 1) {
+#pragma unroll
+      for (int r = 1; r < R; ++r) v[m * R + r] = mul(v[m * R + r], __ldg(tw + (size_t)r * k * TSTEP * tws));
+    }
+    dft<T, C, R>(v + m * R);
+    const int base = (j / NS) * NS * R + k;
+#pragma unroll
+    for (int r = 0; r < R; ++r) buf[pad<T>(base + r * NS)] = v[m * R + r];
+  }
+  }
+  __syncthreads();
+}
+
+// Whole transform of N = 2^LOGN points in buf (padded), threads t < NT = N/E.
+// Threads with active == false take part in the barriers only.
+template <typename T, int LOGN, int E, int NS = 1>
+__device__ __forceinline__ void block_fft(typename Cx<T>::type* buf, int t, bool active,
+                                          const typename Cx<T>::type* __restrict__ tw, int tws) {
+  constexpr int N = 1 << LOGN;
+  if constexpr (NS < N) {
+    constexpr int R = (N / NS >= E) ? E : N / NS;
+    stage<T, LOGN, E, R, NS>(buf, t, active, tw, tws);
+    block_fft<T, LOGN, E, NS * R>(buf, t, active, tw, tws);
+  }
+}
+
+// complex values per thread (8: about 48 registers, two 1024-thread blocks per SM)
+template <typename T> __host__ __device__ constexpr int elems() { return 8; }
+
+// rows: nx = 2^(LOGNH+1); block = NT = 2^LOGNH / E threads
+template <typename T, typename TV, int LOGNH>
+__global__ void __launch_bounds__((1 << LOGNH) / elems<T>() < 32 ? 32 : (1 << LOGNH) / elems<T>())
+k_fft_rows_p2(FftArgs fa, RowArgs ra, int mode, const T* __restrict__ ext,
+              const double* __restrict__ f_grid, const TV* __restrict__ vals,
+              typename Cx<T>::type* __restrict__ inter) {
+  using C = typename Cx<T>::type;
+  constexpr int E = elems<T>();
+  constexpr int NH = 1 << LOGNH;
+  constexpr int NT = NH / E < 1 ? 1 : NH / E;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* buf = reinterpret_cast<C*>(smem_raw);
+  const int j = blockIdx.x, f = blockIdx.y, t = threadIdx.x, nx = 2 * NH;
+  // assemble the row: reals x_i -> pair n = i/2, component i%2 (padded pairs)
+  auto put = [&](int i, T v) { reinterpret_cast<T*>(&buf[pad<T>(i >> 1)])[i & 1] = v; };
+  if (mode == 0) {
+    const T* src = ext + (size_t)f * ra.grid_stride + (size_t)j * nx;
+    for (int n = threadIdx.x; n < NH; n += blockDim.x) {
+      const C v = reinterpret_cast<const C*>(src)[n];
+      buf[pad<T>(n)] = v;
+    }
+  } else {
+    for (int n = threadIdx.x; n < NH; n += blockDim.x) buf[pad<T>(n)] = C{(T)0, (T)0};
+    __syncthreads();
+    const double* fg = f_grid + (size_t)f * ra.grid_stride + (size_t)j * nx;
+    const int iv0 = __ldg(ra.row_iv_off + j), iv1 = __ldg(ra.row_iv_off + j + 1);
+    for (int k = iv0; k < iv1; ++k) {
+      const int lo = __ldg(ra.row_iv + 2 * k), hi = __ldg(ra.row_iv + 2 * k + 1);
+      for (int i = lo + threadIdx.x; i <= hi; i += blockDim.x) put(i, (T)__ldg(fg + i));
+    }
+    const int s0 = __ldg(ra.row_strip_off + j), s1 = __ldg(ra.row_strip_off + j + 1);
+    const TV* v = vals + (size_t)f * ra.n_strip;
+    const int base = j * nx;
+    for (int k = s0 + threadIdx.x; k < s1; k += blockDim.x) put(__ldg(ra.s_lin + k) - base, (T)__ldg(v + k));
+  }
+  __syncthreads();
+  const C* tw = reinterpret_cast<const C*>(fa.twx);
+  block_fft<T, LOGNH, E>(buf, t, t < NT, tw, 1);
+  const C* rtw = reinterpret_cast<const C*>(fa.rtw);
+  C* out = inter + ((size_t)f * fa.ny + j) * fa.pitch;
+  for (int k = threadIdx.x; k <= NH; k += blockDim.x) {
+    const C zk = buf[pad<T>(k == NH ? 0 : k)];
+    C zc = buf[pad<T>(k == 0 ? 0 : NH - k)];
+    zc.y = -zc.y;
+    const C e = {(T)0.5 * (zk.x + zc.x), (T)0.5 * (zk.y + zc.y)};
+    const C o = {(T)0.5 * (zk.x - zc.x), (T)0.5 * (zk.y - zc.y)};
+    const C wo = mul(__ldg(rtw + k), o);
+    out[k] = C{e.x + wo.y, e.y - wo.x};
+  }
+}
+
+// cols: ny = 2^LOGNY, CB columns per block, block = CB * NT threads
+template <typename T, int LOGNY, int CB>
+__global__ void __launch_bounds__(CB * ((1 << LOGNY) / elems<T>()))
+k_fft_cols_p2(FftArgs fa, const typename Cx<T>::type* __restrict__ inter,
+              typename Cx<T>::type* __restrict__ fhat) {
+  using C = typename Cx<T>::type;
+  constexpr int E = elems<T>();
+  constexpr int N = 1 << LOGNY;
+  constexpr int NT = N / E;
+  constexpr int PN = padded<T>(N);
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* buf = reinterpret_cast<C*>(smem_raw);
+  const int ncol = fa.nx / 2 + 1;
+  const int c0 = blockIdx.x * CB, f = blockIdx.y;
+  const C* src = inter + (size_t)f * N * fa.pitch + c0;
+  for (int idx = threadIdx.x; idx < N * CB; idx += blockDim.x) {
+    const int y = idx / CB, c = idx - y * CB;
+    buf[c * PN + pad<T>(y)] = (c0 + c < ncol) ? src[(size_t)y * fa.pitch + c] : C{(T)0, (T)0};
+  }
+  __syncthreads();
+  const int c = threadIdx.x / NT, t = threadIdx.x - c * NT;
+  const C* tw = reinterpret_cast<const C*>(fa.twy);
+  block_fft<T, LOGNY, E>(buf + c * PN, t, true, tw, 1);
+  C* dst = fhat + (size_t)f * N * ncol + c0;
+  const T sc = (T)fa.scale;
+  for (int idx = threadIdx.x; idx < N * CB; idx += blockDim.x) {
+    const int y = idx / CB, cc = idx - y * CB;
+    if (c0 + cc < ncol) {
+      const C v = buf[cc * PN + pad<T>(y)];
+      dst[(size_t)y * ncol + cc] = C{v.x * sc, v.y * sc};
+    }
+  }
+}
+
+template <typename T, typename TV, int L>
+static void rows_launch(const FftArgs& fa, const RowArgs& ra, int n_f, int mode, const void* ext,
+                        const double* fg, const void* vals, void* inter, cudaStream_t s) {
+  constexpr int NT = (1 << L) / elems<T>() < 32 ? 32 : (1 << L) / elems<T>();
+  const size_t sm = (size_t)padded<T>(1 << L) * sizeof(typename Cx<T>::type);
+  auto k = k_fft_rows_p2<T, TV, L>;
+  cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  k<<<dim3(fa.ny, n_f), NT, sm, s>>>(fa, ra, mode, (const T*)ext, fg, (const TV*)vals,
+                                     (typename Cx<T>::type*)inter);
+}
+
+template <typename T, int L, int CB>
+static void cols_launch(const FftArgs& fa, int n_f, const void* inter, void* fhat,
+                        cudaStream_t s) {
+  using C = typename Cx<T>::type;
+  constexpr int NT = (1 << L) / elems<T>();
+  const size_t sm = (size_t)CB * padded<T>(1 << L) * sizeof(C);
+  auto k = k_fft_cols_p2<T, L, CB>;
+  cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  const int ncol = fa.nx / 2 + 1;
+  k<<<dim3((ncol + CB - 1) / CB, n_f), CB * NT, sm, s>>>(fa, (const C*)inter, (C*)fhat);
+}
+
+}  // namespace p2
+
+static int ilog2_exact(int n) {
+  if (n <= 0 || (n & (n - 1))) return -1;
+  int l = 0;
+  while ((1 << l) < n) ++l;
+  return l;
+}
+
+// Power-of-two fast path.  Returns false (nothing launched) for other sizes.
+bool launch_fft_rows_p2(const FftArgs& fa, const RowArgs& ra, int n_f, bool fp64, int mode,
+                        const void* ext, const double* f_grid, const void* vals, void* inter,
+                        cudaStream_t s) {
+  const int L = ilog2_exact(fa.nx / 2);
+#define FC2D_ROWS(LL)                                                                    \
+  case LL:                                                                               \
+    if (fp64)                                                                            \
+      p2::rows_launch<double, double, LL>(fa, ra, n_f, mode, ext, f_grid, vals, inter, s); \
+    else                                                                                 \
+      p2::rows_launch<float, float, LL>(fa, ra, n_f, mode, ext, f_grid, vals, inter, s);   \
+    return true;
+  switch (L) {
+    FC2D_ROWS(5)
+    FC2D_ROWS(6)
+    FC2D_ROWS(7)
+    FC2D_ROWS(8)
+    FC2D_ROWS(9)
+    FC2D_ROWS(10)
+    FC2D_ROWS(11)
+    FC2D_ROWS(12)
+    default: return false;
+  }
+#undef FC2D_ROWS
+}
+
+bool launch_fft_cols_p2(const FftArgs& fa, int n_f, bool fp64, const void* inter, void* fhat,
+                        cudaStream_t s) {
+  const int L = ilog2_exact(fa.ny);
+#define FC2D_COLS(LL, CB32, CB64)                                  \
+  case LL:                                                         \
+    if (fp64)                                                      \
+      p2::cols_launch<double, LL, CB64>(fa, n_f, inter, fhat, s);  \
+    else                                                           \
+      p2::cols_launch<float, LL, CB32>(fa, n_f, inter, fhat, s);   \
+    return true;
+  switch (L) {
+    FC2D_COLS(6, 8, 8)
+    FC2D_COLS(7, 8, 8)
+    FC2D_COLS(8, 8, 4)
+    FC2D_COLS(9, 4, 4)
+    FC2D_COLS(10, 4, 2)
+    FC2D_COLS(11, 2, 2)
+    FC2D_COLS(12, 2, 1)
+    default: return false;
+  }
+#undef FC2D_COLS
+}
+
+}  // namespace fc2d

@@ -15,6 +15,7 @@
 #include <vector>
 
 #include "dd.h"
+#include "fc2d_kernels.cuh"
 #include "plan_internal.h"
 
 namespace fc2d {
@@ -695,6 +696,19 @@ extern "C" fc2d_status fc2d_plan(const fc2d_boundary* boundary, const fc2d_grid*
       (st = upload(&p->fy.tw64, p->fy.tw_host)) || (st = upload(&p->fy.tw32, tw32y)) ||
       (st = upload(&p->rtw64, p->rtw_host)) || (st = upload(&p->rtw32, rtw32)))
     return fail(st);
+  // interpolation weights (Section 3.4), computed once in FP64 on the GPU
+  {
+    const size_t ns = p->strip_lin.size();
+    const size_t wbytes = std::max<size_t>(1, ns) * 2 * M *
+                          (P.precision == FC2D_FP64 ? sizeof(double) : sizeof(float));
+    if (cudaMalloc(&p->dev.s_w, wbytes) != cudaSuccess ||
+        cudaMalloc((void**)&p->dev.s_pb, std::max<size_t>(1, ns) * 4) != cudaSuccess ||
+        cudaMalloc((void**)&p->dev.s_sb, std::max<size_t>(1, ns) * 4) != cudaSuccess)
+      return fail(set_error(FC2D_ERR_NOMEM, "cudaMalloc of the interpolation weights failed"));
+    st = interp_weights_gpu((int)ns, M, p->Cr, B, k1, P.n_r, p->dev.s_theta, p->dev.s_eta,
+                            P.precision == FC2D_FP64, p->dev.s_w, p->dev.s_pb, p->dev.s_sb);
+    if (st) return fail(st);
+  }
   *out = p;
   return FC2D_OK;
 }
@@ -742,7 +756,8 @@ extern "C" fc2d_status fc2d_strip_points(fc2d_plan_t p, int32_t* lin, double* th
 extern "C" void fc2d_destroy(fc2d_plan_t p) {
   if (!p) return;
   void* ptrs[] = {p->dev.Q, p->dev.Ar, p->dev.Ar_hi, p->dev.Ar_lo, p->dev.gidx, p->dev.gw,
-                  p->dev.wn, p->dev.s_lin, p->dev.s_theta, p->dev.s_eta, p->dev.row_iv_off,
+                  p->dev.wn, p->dev.s_lin, p->dev.s_theta, p->dev.s_eta, p->dev.s_w,
+                  p->dev.s_pb, p->dev.s_sb, p->dev.row_iv_off,
                   p->dev.row_iv, p->dev.row_strip_off, p->dev.status, p->fx.tw64, p->fx.tw32,
                   p->fy.tw64, p->fy.tw32, p->rtw64, p->rtw32, p->ws.base};
   for (void* q : ptrs)

@@ -42,6 +42,9 @@ struct DeviceTables {
   int32_t* s_lin = nullptr;  // [n_strip]
   double* s_theta = nullptr; // [n_strip]
   double* s_eta = nullptr;   // [n_strip]
+  void* s_w = nullptr;       // [2M][n_strip] interpolation weights (double or float)
+  int32_t* s_pb = nullptr;   // [n_strip] first normal index
+  int32_t* s_sb = nullptr;   // [n_strip] first fine index
   // per-row tables
   int32_t* row_iv_off = nullptr;    // [ny+1] offsets into row_iv
   int32_t* row_iv = nullptr;        // pairs (i_lo, i_hi), inclusive

@@ -60,6 +60,11 @@ fc2d_status foot_newton_gpu(const Curve& c, const std::vector<double>& qx,
   }
   return FC2D_OK;
 }
+// interpolation weights are a GPU step of the plan; the harness leaves them unset
+fc2d_status interp_weights_gpu(int, int, int, int, double, int, const double*, const double*,
+                               bool, void*, int32_t*, int32_t*) {
+  return FC2D_OK;
+}
 }  // namespace fc2d
 
 template <typename T>

@@ -184,3 +184,86 @@ def test_values_outside_the_domain_are_ignored(case):
     case.plan.fc2d_extend_coeffs(len(case.fs), noisy, case.tb, b)
     case.plan.fc2d_sync_status()
     assert torch.equal(a, b)
+
+
+# --------------------------------------------------------------------------- #
+# mixed precision: FP64 matching values and Gram coefficients, TF32 hi/lo tensor-core
+# contraction with FP32 accumulation, FP32 DFT.  Bar: 1e-6 relative max-norm against
+# the FP64 oracle (BASELINE's mixed-precision target).
+# --------------------------------------------------------------------------- #
+TOL_MIXED = 1e-6
+_mplans = {}
+
+
+@pytest.fixture(scope="module")
+def mixed(case, fc2d):
+    if case.w.name not in _mplans:
+        g, p = case.w.grid, case.w.params
+        _mplans[case.w.name] = fc2d.fc2d_plan(case.w.boundary.arrays(),
+                                              (g.a0, g.b0, g.h, g.nx, g.ny),
+                                              dict(B=p.B, k1=p.k1), precision=fc2d.FC2D_MIXED)
+    return _mplans[case.w.name]
+
+
+def test_mixed_blend_within_1e6(case, mixed, mats):
+    torch = case.torch
+    p = case.w.params
+    n_f = len(case.fs)
+    F = torch.zeros((n_f, p.B, p.C * p.n_r + 1), dtype=torch.float32, device=case.dev)
+    mixed.fc2d_blend(n_f, case.tg, case.tb, F)
+    mixed.fc2d_sync_status()
+    got = F.cpu().numpy().astype(np.float64)
+    for k in range(n_f):
+        ref = OF.blend(mats, OF.matching_values(case.geo, case.st, case.fg[k], case.fb[k]))
+        assert rel(got[k], ref) < TOL_MIXED, (k, rel(got[k], ref))
+
+
+def test_mixed_extend_within_1e6(case, mixed, mats):
+    torch = case.torch
+    g = case.w.grid
+    n_f = len(case.fs)
+    ext = torch.zeros((n_f, g.ny, g.nx), dtype=torch.float32, device=case.dev)
+    mixed.fc2d_extend(n_f, case.tg, case.tb, ext)
+    mixed.fc2d_sync_status()
+    got = ext.cpu().numpy().astype(np.float64)
+    for k in range(n_f):
+        ref = OF.extension(case.geo, mats, case.fg[k], case.fb[k], case.st)
+        assert rel(got[k], ref) < TOL_MIXED, (k, rel(got[k], ref))
+
+
+def test_mixed_extend_coeffs_within_1e6(case, mixed, mats):
+    torch = case.torch
+    g = case.w.grid
+    n_f = len(case.fs)
+    fhat = torch.zeros((n_f, g.ny, g.nx // 2 + 1, 2), dtype=torch.float32, device=case.dev)
+    mixed.fc2d_extend_coeffs(n_f, case.tg, case.tb, fhat)
+    mixed.fc2d_sync_status()
+    got = fhat.cpu().numpy().astype(np.float64)
+    for k in range(n_f):
+        ref = OF.coefficients(OF.extension(case.geo, mats, case.fg[k], case.fb[k], case.st))
+        gk = got[k][..., 0] + 1j * got[k][..., 1]
+        assert rel(gk, ref) < TOL_MIXED, (k, rel(gk, ref))
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_dft_large_power_of_two(fc2d, torch_cuda, precision):
+    """The power-of-two DFT kernels at 4096 x 2048 (ny x nx) on seeded random data:
+    1e-12 (FP64) / 1e-6 (FP32) relative max-norm against numpy's FFT of the same data."""
+    torch = torch_cuda
+    w = W.workload("kite2048")
+    g, p = w.grid, w.params
+    nx, ny = 2048, 4096
+    prec = fc2d.FC2D_FP64 if precision == "fp64" else fc2d.FC2D_MIXED
+    plan = fc2d.fc2d_plan(w.boundary.arrays(), (g.a0, g.b0 - 0.5 * ny * g.h + 0.5 * g.ny * g.h,
+                                                g.h, nx, ny), dict(B=p.B, k1=p.k1), precision=prec)
+    x = W.normal(77, ny * nx).reshape(ny, nx)
+    dt = torch.float64 if precision == "fp64" else torch.float32
+    t = torch.tensor(x[None], dtype=dt, device="cuda:0")
+    fhat = torch.zeros((1, ny, nx // 2 + 1, 2), dtype=dt, device="cuda:0")
+    plan.fc2d_coeffs(1, t, fhat)
+    plan.fc2d_sync_status()
+    got = fhat.cpu().numpy().astype(np.float64)[0]
+    got = got[..., 0] + 1j * got[..., 1]
+    ref = np.fft.rfft2(t.cpu().numpy().astype(np.float64)[0]) / (nx * ny)
+    tol = TOL if precision == "fp64" else TOL_MIXED
+    assert rel(got, ref) < tol, rel(got, ref)
