@@ -163,6 +163,31 @@ fc2d_status fc2d_extend_coeffs(fc2d_plan_t plan, int n_f, const double* f_grid_d
 fc2d_status fc2d_coeffs_static(fc2d_plan_t plan, int n_f, const void* ext_dev, void* fhat_dev,
                                void* stream);
 
+/* Poisson problem Delta u = f in the domain, u = g on the curve (Section 4.1,
+ * eqs. (4.1)-(4.6)), FP64 plans.  fc2d_poisson_plan builds the boundary-integral tables
+ * once (synchronous): n_b equispaced parameters 2 pi k/n_b (n_b <= 0 means nx, as in
+ * Section 4.1.1), the Nystrom matrix of the double-layer equation -phi/2 + K phi = g_hom,
+ * the boundary interpolation stencils of u_p, and the near-boundary point lists.
+ * fc2d_poisson_nodes returns n_b and, if xy_host is not NULL, the nodes [n_b][2] where
+ * the Dirichlet data g are needed. */
+fc2d_status fc2d_poisson_plan(fc2d_plan_t plan, int n_b);
+fc2d_status fc2d_poisson_nodes(fc2d_plan_t plan, double* xy_host, int* n_b);
+
+/* Solve: u = u_p + v.  u_p from the 2D-FC spectrum of f (multiplier of eq. (4.6), the
+ * constant term + hat f_00 (x^2+y^2)/4), its values on the curve by iterated degree M-1
+ * interpolation, the density by GMRES (tolerance 1e-14), v at the grid points inside by
+ * the trapezoidal rule with near-boundary refinement.  f_grid_dev [n_f][ny][nx] and
+ * f_bdry_dev [n_f][n_bdry] as for fc2d_extend; g_nodes_dev [n_f][n_b]; u_dev [n_f][ny][nx]
+ * receives u inside the domain and 0 elsewhere; phi_dev (NULL allowed) receives the
+ * density [n_f][n_b].  The GMRES iteration is driven from the host: this call waits
+ * for the stream.  Returns FC2D_ERR_NOT_CONVERGED if GMRES stalls. */
+fc2d_status fc2d_poisson(fc2d_plan_t plan, int n_f, const double* f_grid_dev,
+                         const double* f_bdry_dev, const double* g_nodes_dev, double* u_dev,
+                         double* phi_dev, void* stream);
+/* Last solve: GMRES iterations and relative residual; number of near-boundary points. */
+fc2d_status fc2d_poisson_info(fc2d_plan_t plan, int* gmres_iters, double* gmres_resid,
+                              int64_t* n_near);
+
 /* Kernel timing (tracing).  While enabled, every kernel the plan launches is
  * bracketed by a pair of CUDA events recorded on its launching stream.
  * fc2d_profile_read waits for those events and returns, per kernel name, the number

@@ -3,6 +3,7 @@
 
 #include <cstdint>
 #include <cstdio>
+#include <cstring>
 #include <string>
 #include <vector>
 
@@ -342,4 +343,50 @@ extern "C" fc2d_status fc2d_profile_read(fc2d_plan_t p, int max_kernels, char* n
     ms[k] = tot[k];
   }
   return FC2D_OK;
+}
+
+// ------------------------------------------------------------------------- //
+// Poisson solver (Section 4.1)
+// ------------------------------------------------------------------------- //
+extern "C" fc2d_status fc2d_poisson_plan(fc2d_plan_t p, int n_b) {
+  if (!p) return set_error(FC2D_ERR_ARG, "null plan");
+  cudaSetDevice(p->device);
+  return poisson_setup(p, n_b);
+}
+
+extern "C" fc2d_status fc2d_poisson_nodes(fc2d_plan_t p, double* xy_host, int* n_b) {
+  if (!p || !n_b) return set_error(FC2D_ERR_ARG, "fc2d_poisson_nodes: null argument");
+  *n_b = poisson_nb(p);
+  if (!*n_b) return set_error(FC2D_ERR_ARG, "fc2d_poisson_nodes: call fc2d_poisson_plan first");
+  if (xy_host) std::memcpy(xy_host, poisson_nodes(p), sizeof(double) * 2 * (size_t)*n_b);
+  return FC2D_OK;
+}
+
+extern "C" fc2d_status fc2d_poisson_info(fc2d_plan_t p, int* gmres_iters, double* gmres_resid,
+                                         int64_t* n_near) {
+  if (!p) return set_error(FC2D_ERR_ARG, "null plan");
+  poisson_stats(p, gmres_iters, gmres_resid, n_near);
+  return FC2D_OK;
+}
+
+extern "C" fc2d_status fc2d_poisson(fc2d_plan_t p, int n_f, const double* fg, const double* fb,
+                                    const double* g_nodes, double* u, double* phi,
+                                    void* stream) {
+  fc2d_status st = check_nf(p, n_f);
+  if (st) return st;
+  if (!fg || !fb || !g_nodes || !u) return set_error(FC2D_ERR_ARG, "fc2d_poisson: null pointer");
+  if (!p->poisson) return set_error(FC2D_ERR_ARG, "fc2d_poisson: call fc2d_poisson_plan first");
+  if (p->prm.precision != FC2D_FP64)
+    return set_error(FC2D_ERR_UNSUPPORTED, "fc2d_poisson: FP64 plans only");
+  cudaSetDevice(p->device);
+  Layout L = layout(p, n_f);
+  if ((st = ensure_workspace(p, L.total))) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  if ((st = strip_values(p, n_f, fg, fb, L, s))) return st;
+  {
+    ProfScope ps(p, "fft_rows_fused", s);
+    launch_fft_rows(fft_args(p), row_args(p), n_f, true, 1, nullptr, fg, ws(p, L.ovals),
+                    ws(p, L.ointer), s);
+  }
+  return poisson_solve(p, n_f, fg, fb, g_nodes, u, phi, ws(p, L.ointer), s);
 }

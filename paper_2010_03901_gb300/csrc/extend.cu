@@ -44,12 +44,30 @@ __device__ void curve_eval(int nm, double t, double* x, double* y) {
   }
 }
 
+// Seed: the closest of 2 kFootSamples + 1 curve samples within +-window of the given
+// parameter; then Newton.
+constexpr int kFootSamples = 24;
+
 __global__ void k_foot_newton(int n, int nm, const double* __restrict__ qx,
                               const double* __restrict__ qy, double* __restrict__ th,
-                              int* __restrict__ conv) {
+                              int* __restrict__ conv, double window) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   double t = th[i], X = qx[i], Y = qy[i];
+  {
+    const double t0 = t;
+    double best = 1e300;
+    for (int k = -kFootSamples; k <= kFootSamples; ++k) {
+      const double tk = t0 + window * double(k) / kFootSamples;
+      double x[3], y[3];
+      curve_eval(nm, tk, x, y);
+      const double d2 = (x[0] - X) * (x[0] - X) + (y[0] - Y) * (y[0] - Y);
+      if (d2 < best) {
+        best = d2;
+        t = tk;
+      }
+    }
+  }
   int ok = 0;
   for (int it = 0; it < 60; ++it) {  // iteration cap: no unbounded loop
     double x[3], y[3];
@@ -59,7 +77,11 @@ __global__ void k_foot_newton(int n, int nm, const double* __restrict__ qx,
     if (!(dphi > 0.0)) break;  // not a local minimum of the distance: give up
     double step = phi / dphi;
     t -= step;
-    if (fabs(step) < 1e-15) {
+    if (fabs(step) < 1e-12) {  // quadratic convergence: one more step reaches round-off
+      curve_eval(nm, t, x, y);
+      phi = (x[0] - X) * x[1] + (y[0] - Y) * y[1];
+      dphi = x[1] * x[1] + y[1] * y[1] + (x[0] - X) * x[2] + (y[0] - Y) * y[2];
+      if (dphi > 0.0) t -= phi / dphi;
       ok = 1;
       break;
     }
@@ -70,7 +92,7 @@ __global__ void k_foot_newton(int n, int nm, const double* __restrict__ qx,
 
 fc2d_status foot_newton_gpu(const Curve& c, const std::vector<double>& qx,
                             const std::vector<double>& qy, std::vector<double>& theta,
-                            std::vector<int>& conv) {
+                            std::vector<int>& conv, double window) {
   int nm = (int)c.cx.size();
   if (nm > kMaxModes) return set_error(FC2D_ERR_UNSUPPORTED, "boundary has too many modes");
   size_t n = qx.size();
@@ -94,7 +116,8 @@ fc2d_status foot_newton_gpu(const Curve& c, const std::vector<double>& qx,
     cudaMemcpy(dqx, qx.data(), n * 8, cudaMemcpyHostToDevice);
     cudaMemcpy(dqy, qy.data(), n * 8, cudaMemcpyHostToDevice);
     cudaMemcpy(dth, theta.data(), n * 8, cudaMemcpyHostToDevice);
-    k_foot_newton<<<(unsigned)((n + 127) / 128), 128>>>((int)n, nm, dqx, dqy, dth, dconv);
+    k_foot_newton<<<(unsigned)((n + 127) / 128), 128>>>((int)n, nm, dqx, dqy, dth, dconv,
+                                                         window);
     st = cuda_check(cudaGetLastError(), "foot search launch");
     if (st == FC2D_OK) st = cuda_check(cudaDeviceSynchronize(), "foot search");
     if (st == FC2D_OK) {

@@ -511,7 +511,7 @@ extern "C" fc2d_status fc2d_plan(const fc2d_boundary* boundary, const fc2d_grid*
     tq[n] = cand[n].seed;
   }
   std::vector<int> conv;
-  fc2d_status st = foot_newton_gpu(cv, qx, qy, tq, conv);
+  fc2d_status st = foot_newton_gpu(cv, qx, qy, tq, conv, 1.5 * k2);
   if (st != FC2D_OK) return fail(st);
   const double width = P.C * k1;
   const double two_pi = 2.0 * M_PI;
@@ -755,6 +755,7 @@ extern "C" fc2d_status fc2d_strip_points(fc2d_plan_t p, int32_t* lin, double* th
 
 extern "C" void fc2d_destroy(fc2d_plan_t p) {
   if (!p) return;
+  poisson_destroy(p);
   void* ptrs[] = {p->dev.Q, p->dev.Ar, p->dev.Ar_hi, p->dev.Ar_lo, p->dev.gidx, p->dev.gw,
                   p->dev.wn, p->dev.s_lin, p->dev.s_theta, p->dev.s_eta, p->dev.s_w,
                   p->dev.s_pb, p->dev.s_sb, p->dev.row_iv_off,

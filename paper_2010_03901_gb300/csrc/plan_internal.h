@@ -5,6 +5,8 @@
 #include <string>
 #include <vector>
 
+#include <cuda_runtime.h>
+
 #include "../../include/fc2d.h"
 
 namespace fc2d {
@@ -89,6 +91,7 @@ struct fc2d_plan_s {
   bool profiling = false;
   std::vector<fc2d::ProfileRecord> prof;       // events of the current record
   std::vector<void*> event_pool;               // reusable cudaEvent_t
+  void* poisson = nullptr;                     // Poisson tables (poisson.cu)
 };
 
 namespace fc2d {
@@ -96,13 +99,24 @@ namespace fc2d {
 fc2d_status set_error(fc2d_status s, const std::string& msg);
 fc2d_status cuda_check(int err, const char* what);
 
-// plan-time GPU kernel: Newton foot search.  Returns FC2D_OK or an error.
+// plan-time GPU kernel: foot of the normal through each point (nearest curve point):
+// the best of 49 samples within +-window of theta[i], then Newton's method.
 fc2d_status foot_newton_gpu(const Curve& c, const std::vector<double>& qx,
                             const std::vector<double>& qy, std::vector<double>& theta,
-                            std::vector<int>& conv);
+                            std::vector<int>& conv, double window);
 
 // workspace of at least `bytes` bytes (grows, synchronously, when needed)
 fc2d_status ensure_workspace(fc2d_plan_s* p, size_t bytes);
+
+// Poisson solver (poisson.cu)
+fc2d_status poisson_setup(fc2d_plan_s* p, int n_b);
+fc2d_status poisson_solve(fc2d_plan_s* p, int n_f, const double* f_grid, const double* f_bdry,
+                          const double* g_nodes, double* u, double* phi_out, void* inter,
+                          cudaStream_t s);
+void poisson_destroy(fc2d_plan_s* p);
+int poisson_nb(const fc2d_plan_s* p);
+const double* poisson_nodes(const fc2d_plan_s* p);
+void poisson_stats(const fc2d_plan_s* p, int* iters, double* resid, int64_t* n_near);
 
 // kernel timing: bracket one launch with events when the plan is profiling
 struct ProfScope {

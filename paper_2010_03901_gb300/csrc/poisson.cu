@@ -1,0 +1,762 @@
+// 2D-FC Poisson solver (Section 4.1, eqs. (4.1)-(4.6)), FP64.
+//
+//   u = u_p + v.  u_p: the spectrum of the extension of f times the inverse Laplacian
+//   symbol -1/((2 pi l/L_x)^2 + (2 pi m/L_y)^2) (0 at the origin), inverse DFT, plus
+//   hat f_00 (x^2 + y^2)/4 (sign taken so that Delta u_p = f^c).
+//   v: double-layer potential, -phi/2 + K phi = g - u_p on the curve, trapezoidal
+//   Nystrom on N_b equispaced parameters, solved by GMRES (host-driven, device
+//   mat-vec and orthogonalisation kernels).  v on the grid points inside: the
+//   trapezoidal sum; within 5 s of the curve (s = (2 pi/N_b) max|q'|) the density is
+//   refined R = 8 times by trigonometric interpolation and, closer than 5 s/R, v is
+//   the degree M_P - 1 Lagrange interpolant along the normal through the boundary
+//   value (trigonometric interpolation of g - u_p) and refined sums at 5s/R..(M_P+3)s/R.
+//
+// Kernels: k_poisson_cols (forward column DFT, multiplier, inverse column DFT in
+// shared memory), k_poisson_rows (inverse real row DFT + quadratic term), k_up_nodes,
+// GMRES kernels, k_density_dft / k_density_refine, k_dlp (trapezoidal sums over a point
+// list), k_dlp_close (one block per close point), k_zero_outside.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "dd.h"
+#include "fc2d_kernels.cuh"
+#include "fft_generic.cuh"
+#include "plan_internal.h"
+
+namespace fc2d {
+
+constexpr int kGmresMax = 200;
+constexpr int kRefine = 8;
+
+struct PoissonState {
+  int Nb = 0, R = kRefine, MP = 8;
+  double s = 0, delta = 0;
+  double *bx = nullptr, *by = nullptr, *bx1 = nullptr, *by1 = nullptr;  // nodes [Nb]
+  double* A = nullptr;                                                  // [Nb][Nb]
+  double *rx = nullptr, *ry = nullptr, *rx1 = nullptr, *ry1 = nullptr;  // refined [R Nb]
+  double* twb = nullptr;                                                // e^{-2 pi i t/Nb}
+  double* twr = nullptr;                                                // e^{+2 pi i t/(R Nb)}
+  int32_t *ui0 = nullptr, *uj0 = nullptr;                               // [Nb]
+  double *uwx = nullptr, *uwy = nullptr;                                // [Nb][MP]
+  int64_t n_far = 0, n_mid = 0, n_close = 0;
+  int32_t *far_lin = nullptr, *mid_lin = nullptr, *close_lin = nullptr;
+  double* close_geo = nullptr;  // [n_close][5]: foot x, y, normal x, y, theta
+  double* close_w = nullptr;    // [n_close][MP]
+  std::vector<double> close_nodes;  // [MP] distances along the normal
+  double* dnodes = nullptr;         // device copy
+  // per-solve workspace
+  double *V = nullptr, *w = nullptr, *h = nullptr, *g = nullptr, *phi = nullptr;
+  double *ghat = nullptr, *phiR = nullptr, *ab = nullptr, *abR = nullptr, *c00 = nullptr;
+  std::vector<double> xy_host;  // node coordinates [Nb][2]
+  int last_iters = 0;
+  double last_resid = 0;
+  std::vector<void*> allocs;
+};
+
+static void poisson_free(PoissonState* P) {
+  if (!P) return;
+  for (void* q : P->allocs) cudaFree(q);
+  delete P;
+}
+
+void poisson_destroy(fc2d_plan_s* p) {
+  poisson_free(static_cast<PoissonState*>(p->poisson));
+  p->poisson = nullptr;
+}
+
+// ------------------------------------------------------------------------- //
+// Kernels
+// ------------------------------------------------------------------------- //
+// Forward column DFT, hat f = scale * DFT, record hat f_00, multiply by the inverse
+// Laplacian symbol, inverse (unnormalised) column DFT by conj(DFT(conj)), in place.
+__global__ void __launch_bounds__(256) k_poisson_cols(FftArgs fa, int cb, double2* inter,
+                                                      double* c00, double Lx, double Ly) {
+  using C = double2;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int ny = fa.ny, ncol = fa.nx / 2 + 1;
+  const int c0 = blockIdx.x * cb, f = blockIdx.y;
+  const int nc = min(cb, ncol - c0);
+  C* A = reinterpret_cast<C*>(smem_raw);
+  C* Bf = A + (size_t)cb * ny;
+  C* col = inter + (size_t)f * ny * fa.pitch + c0;
+  for (int idx = threadIdx.x; idx < ny * cb; idx += blockDim.x) {
+    int y = idx / cb, c = idx - y * cb;
+    A[(size_t)c * ny + y] = c < nc ? col[(size_t)y * fa.pitch + c] : C{0, 0};
+  }
+  __syncthreads();
+  const C* tw = reinterpret_cast<const C*>(fa.twy);
+  C* Y = stockham<double>(A, Bf, ny, cb, fa.ry, fa.nry, tw, 1);
+  C* other = (Y == A) ? Bf : A;
+  const double two_pi = 6.283185307179586476925286766559;
+  for (int idx = threadIdx.x; idx < ny * cb; idx += blockDim.x) {
+    int c = idx / ny, ky = idx - c * ny;
+    int kx = c0 + c;
+    C v = Y[idx];
+    v.x *= fa.scale;
+    v.y *= fa.scale;
+    int m = ky <= ny / 2 ? ky : ky - ny;
+    double kxx = two_pi * kx / Lx, kyy = two_pi * m / Ly;
+    double k2 = kxx * kxx + kyy * kyy;
+    C b;
+    if (kx == 0 && ky == 0) {
+      c00[f] = v.x;
+      b = C{0, 0};
+    } else {
+      b = C{-v.x / k2, -v.y / k2};
+    }
+    Y[idx] = C{b.x, -b.y};  // conj for the inverse
+  }
+  __syncthreads();
+  C* Z = stockham<double>(Y, other, ny, cb, fa.ry, fa.nry, tw, 1);
+  for (int idx = threadIdx.x; idx < ny * cb; idx += blockDim.x) {
+    int y = idx / cb, c = idx - y * cb;
+    if (c < nc) {
+      C v = Z[(size_t)c * ny + y];
+      col[(size_t)y * fa.pitch + c] = C{v.x, -v.y};
+    }
+  }
+}
+
+// Inverse real row DFT: from B_k (k = 0..nx/2) the real row x_n = sum B_k e^{2 pi i k n/nx}
+// (full Hermitian sum), via z = length-nx/2 inverse DFT of
+// Z'_k = (B_k + conj B_{nx/2-k}) + i (B_k - conj B_{nx/2-k}) conj(w^k), w = e^{-2 pi i/nx},
+// x_{2m} = Re z_m, x_{2m+1} = Im z_m; plus c00 (x^2 + y^2)/4.
+__global__ void __launch_bounds__(256) k_poisson_rows(FftArgs fa, const double2* inter,
+                                                      const double* c00, double a0, double b0,
+                                                      double h, double* up) {
+  using C = double2;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int nx = fa.nx, Nh = nx / 2, j = blockIdx.x, f = blockIdx.y;
+  C* A = reinterpret_cast<C*>(smem_raw);
+  C* Bf = A + Nh;
+  const C* row = inter + ((size_t)f * fa.ny + j) * fa.pitch;
+  const C* rtw = reinterpret_cast<const C*>(fa.rtw);
+  for (int k = threadIdx.x; k < Nh; k += blockDim.x) {
+    C bk = row[k];
+    C bc = row[Nh - k];
+    bc.y = -bc.y;  // conj B_{Nh-k}
+    C s = C{bk.x + bc.x, bk.y + bc.y};
+    C d = C{bk.x - bc.x, bk.y - bc.y};
+    C w = rtw[k];
+    w.y = -w.y;  // conj(w^k)
+    C dw = C{d.x * w.x - d.y * w.y, d.x * w.y + d.y * w.x};
+    C z = C{s.x - dw.y, s.y + dw.x};  // s + i dw
+    A[k] = C{z.x, -z.y};              // conj for the inverse
+  }
+  __syncthreads();
+  const C* tw = reinterpret_cast<const C*>(fa.twx);
+  C* Z = stockham<double>(A, Bf, Nh, 1, fa.rx, fa.nrx, tw, 1);
+  const double q = c00[f] * 0.25;
+  const double y = b0 + h * double(j);
+  double* out = up + ((size_t)f * fa.ny + j) * nx;
+  for (int m = threadIdx.x; m < Nh; m += blockDim.x) {
+    C z = Z[m];
+    double x0 = a0 + h * double(2 * m), x1 = a0 + h * double(2 * m + 1);
+    out[2 * m] = z.x + q * (x0 * x0 + y * y);
+    out[2 * m + 1] = -z.y + q * (x1 * x1 + y * y);
+  }
+}
+
+// u_p at the BIE nodes: iterated 1D interpolation (x on MP rows, then y).
+__global__ void k_up_nodes(int Nb, int MP, int nx, const int32_t* i0, const int32_t* j0,
+                           const double* wx, const double* wy, const double* up,
+                           const double* g, double* ghom) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= Nb) return;
+  double acc = 0.0;
+  for (int a = 0; a < MP; ++a) {
+    const double* r = up + (size_t)(j0[k] + a) * nx + i0[k];
+    double v = 0.0;
+    for (int b = 0; b < MP; ++b) v = fma(wx[k * MP + b], r[b], v);
+    acc = fma(wy[k * MP + a], v, acc);
+  }
+  ghom[k] = g[k] - acc;
+}
+
+__global__ void k_bie_matrix(int Nb, const double* x, const double* y, const double* x1,
+                             const double* y1, const double* diag, double* A) {
+  int i = blockIdx.y, k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= Nb) return;
+  const double w = 1.0 / Nb;  // (2 pi/Nb) * 1/(2 pi)
+  double v;
+  if (i == k) {
+    v = -0.5 + diag[i];
+  } else {
+    double dx = x[i] - x[k], dy = y[i] - y[k];
+    v = w * (y1[k] * dx - x1[k] * dy) / (dx * dx + dy * dy);
+  }
+  A[(size_t)i * Nb + k] = v;
+}
+
+// y = A x, one warp per row
+__global__ void k_gemv(int n, const double* A, const double* x, double* y) {
+  int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (row >= n) return;
+  const double* a = A + (size_t)row * n;
+  double s = 0.0;
+  for (int k = lane; k < n; k += 32) s = fma(a[k], x[k], s);
+  for (int o = 16; o; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  if (lane == 0) y[row] = s;
+}
+
+// h[i] = <V_i, w>, i < m (one block per i)
+__global__ void k_dots(int n, int m, const double* V, const double* w, double* h) {
+  __shared__ double red[256];
+  int i = blockIdx.x;
+  if (i >= m) return;
+  double s = 0.0;
+  for (int k = threadIdx.x; k < n; k += blockDim.x) s = fma(V[(size_t)i * n + k], w[k], s);
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) h[i] = red[0];
+}
+
+// w -= sum_{i<m} h[i] V_i
+__global__ void k_sub_proj(int n, int m, const double* V, const double* h, double* w) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  double s = w[k];
+  for (int i = 0; i < m; ++i) s = fma(-h[i], V[(size_t)i * n + k], s);
+  w[k] = s;
+}
+
+__global__ void k_scale_to(int n, const double* w, const double* nrm, double* v) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < n) v[k] = w[k] / *nrm;
+}
+
+// x = sum_{i<m} y[i] V_i
+__global__ void k_combine(int n, int m, const double* V, const double* y, double* x) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  double s = 0.0;
+  for (int i = 0; i < m; ++i) s = fma(y[i], V[(size_t)i * n + k], s);
+  x[k] = s;
+}
+
+// hat phi_k = (1/Nb) sum_j phi_j e^{-2 pi i jk/Nb}, k = 0..Nb/2
+__global__ void k_density_dft(int Nb, const double* phi, const double2* twb, double2* ghat) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k > Nb / 2) return;
+  double re = 0.0, im = 0.0;
+  for (int j = 0; j < Nb; ++j) {
+    double2 w = twb[(int)(((int64_t)j * k) % Nb)];
+    re = fma(phi[j], w.x, re);
+    im = fma(phi[j], w.y, im);
+  }
+  ghat[k] = double2{re / Nb, im / Nb};
+}
+
+// trigonometric interpolant of the density at the R Nb refined parameters
+__global__ void k_density_refine(int Nb, int NR, const double2* ghat, const double2* twr,
+                                 double* out) {
+  int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= NR) return;
+  const int half = Nb / 2;
+  double s = ghat[0].x;
+  for (int k = 1; k <= half; ++k) {
+    double2 e = twr[(int)(((int64_t)k * m) % NR)];  // e^{+2 pi i k m/NR}
+    double re = ghat[k].x * e.x - ghat[k].y * e.y;
+    double fac = (2 * k == Nb) ? 1.0 : 2.0;
+    s = fma(fac, re, s);
+  }
+  out[m] = s;
+}
+
+// node coefficients of the trapezoidal sum: a_k = y'_k phi_k / N, b_k = x'_k phi_k / N
+__global__ void k_node_coef(int N, const double* x1, const double* y1, const double* phi,
+                            double2* ab) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < N) ab[k] = double2{y1[k] * phi[k] / N, x1[k] * phi[k] / N};
+}
+
+// v at listed grid points by the trapezoidal sum over N nodes; u = u_p + v there.
+__global__ void __launch_bounds__(256) k_dlp(int n_pts, const int32_t* lin, int nx, double a0,
+                                             double b0, double h, int N, const double* x,
+                                             const double* y, const double2* ab, double* u) {
+  __shared__ double sx[256], sy[256];
+  __shared__ double2 sab[256];
+  int n = blockIdx.x * blockDim.x + threadIdx.x;
+  bool act = n < n_pts;
+  int l = act ? lin[n] : 0;
+  double px = a0 + h * double(l % nx), py = b0 + h * double(l / nx);
+  double acc = 0.0;
+  for (int t0 = 0; t0 < N; t0 += 256) {
+    __syncthreads();
+    if (t0 + (int)threadIdx.x < N) {
+      sx[threadIdx.x] = x[t0 + threadIdx.x];
+      sy[threadIdx.x] = y[t0 + threadIdx.x];
+      sab[threadIdx.x] = ab[t0 + threadIdx.x];
+    }
+    __syncthreads();
+    int cnt = min(256, N - t0);
+    for (int k = 0; k < cnt; ++k) {
+      double dx = px - sx[k], dy = py - sy[k];
+      double r2 = fma(dx, dx, dy * dy);
+      double num = fma(sab[k].x, dx, -sab[k].y * dy);
+      acc += num / r2;
+    }
+  }
+  if (act) u[l] += acc;
+}
+
+// close points: one block per point; 7 refined sums along the normal, the boundary
+// value by trigonometric interpolation of g - u_p, and the Lagrange combination.
+__global__ void __launch_bounds__(256) k_dlp_close(int n_close, const int32_t* lin,
+                                                   const double* cgeo, const double* cw,
+                                                   const double* nodes, int MP, int NR,
+                                                   const double* rx, const double* ry,
+                                                   const double2* abR, int Nb,
+                                                   const double2* ghat_g, double* u) {
+  __shared__ double red[256];
+  const int n = blockIdx.x;
+  if (n >= n_close) return;
+  const double fx = cgeo[5 * n], fy = cgeo[5 * n + 1], nxv = cgeo[5 * n + 2],
+               nyv = cgeo[5 * n + 3], th = cgeo[5 * n + 4];
+  double vals[kMaxM];
+  for (int j = 1; j < MP; ++j) {
+    const double px = fx - nodes[j] * nxv, py = fy - nodes[j] * nyv;
+    double acc = 0.0;
+    for (int k = threadIdx.x; k < NR; k += blockDim.x) {
+      double dx = px - rx[k], dy = py - ry[k];
+      double r2 = fma(dx, dx, dy * dy);
+      acc += fma(abR[k].x, dx, -abR[k].y * dy) / r2;
+    }
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o; o >>= 1) {
+      if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+      __syncthreads();
+    }
+    vals[j] = red[0];
+    __syncthreads();
+  }
+  // boundary value: sum_k c_k e^{i k theta} over the Hermitian half (Nyquist halved)
+  {
+    double acc = 0.0;
+    const int half = Nb / 2;
+    for (int k = threadIdx.x; k <= half; k += blockDim.x) {
+      double s, c;
+      sincos(double(k) * th, &s, &c);
+      double re = ghat_g[k].x * c - ghat_g[k].y * s;
+      double fac = (k == 0 || 2 * k == Nb) ? 1.0 : 2.0;
+      acc = fma(fac, re, acc);
+    }
+    red[threadIdx.x] = acc;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o; o >>= 1) {
+      if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+      __syncthreads();
+    }
+    vals[0] = red[0];
+  }
+  if (threadIdx.x == 0) {
+    double v = 0.0;
+    for (int j = 0; j < MP; ++j) v = fma(cw[(size_t)n * MP + j], vals[j], v);
+    u[lin[n]] += v;
+  }
+}
+
+__global__ void k_zero_outside(int nx, const int32_t* row_iv_off, const int32_t* row_iv,
+                               double* u) {
+  const int j = blockIdx.x;
+  double* r = u + (size_t)j * nx;
+  const int iv0 = row_iv_off[j], iv1 = row_iv_off[j + 1];
+  for (int i = threadIdx.x; i < nx; i += blockDim.x) {
+    bool in = false;
+    for (int k = iv0; k < iv1; ++k) in |= (i >= row_iv[2 * k] && i <= row_iv[2 * k + 1]);
+    if (!in) r[i] = 0.0;
+  }
+}
+
+// ------------------------------------------------------------------------- //
+// Setup
+// ------------------------------------------------------------------------- //
+template <typename T>
+static fc2d_status up(PoissonState* P, T** dst, const std::vector<T>& src) {
+  size_t bytes = std::max<size_t>(1, src.size()) * sizeof(T);
+  if (cudaMalloc((void**)dst, bytes) != cudaSuccess)
+    return set_error(FC2D_ERR_NOMEM, "Poisson setup: cudaMalloc failed");
+  P->allocs.push_back(*dst);
+  if (!src.empty() &&
+      cudaMemcpy(*dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice) != cudaSuccess)
+    return set_error(FC2D_ERR_CUDA, "Poisson setup: cudaMemcpy failed");
+  return FC2D_OK;
+}
+
+template <typename T>
+static fc2d_status alloc(PoissonState* P, T** dst, size_t n) {
+  if (cudaMalloc((void**)dst, std::max<size_t>(1, n) * sizeof(T)) != cudaSuccess)
+    return set_error(FC2D_ERR_NOMEM, "Poisson setup: cudaMalloc failed");
+  P->allocs.push_back(*dst);
+  return FC2D_OK;
+}
+
+static void lagr(const double* nodes, int n, double t, double* w) {
+  for (int k = 0; k < n; ++k) {
+    double v = 1.0;
+    for (int m = 0; m < n; ++m)
+      if (m != k) v *= (t - nodes[m]) / (nodes[k] - nodes[m]);
+    w[k] = v;
+  }
+}
+
+fc2d_status poisson_setup(fc2d_plan_s* p, int Nb) {
+  if (p->prm.precision != FC2D_FP64)
+    return set_error(FC2D_ERR_UNSUPPORTED, "fc2d_poisson_plan: the Poisson solver needs an FP64 plan");
+  const int nx = p->grid.nx, ny = p->grid.ny, MP = p->prm.M;
+  if (Nb <= 0) Nb = nx;
+  if (Nb < 16 || Nb > 65536) return set_error(FC2D_ERR_ARG, "fc2d_poisson_plan: bad n_b");
+  poisson_destroy(p);
+  auto* P = new PoissonState();
+  P->Nb = Nb;
+  P->MP = MP;
+  const Curve& cv = p->curve;
+  const double a0 = p->grid.a0, b0 = p->grid.b0, h = p->grid.h;
+  const double two_pi = 2.0 * M_PI;
+  auto fail = [&](fc2d_status s) {
+    poisson_free(P);
+    return s;
+  };
+  // nodes
+  std::vector<double> x(Nb), y(Nb), x1(Nb), y1(Nb), diag(Nb);
+  P->xy_host.assign(2 * (size_t)Nb, 0.0);
+  for (int k = 0; k < Nb; ++k) {
+    double t = two_pi * k / Nb, xx, yy, xd, yd, x2, y2;
+    cv.eval(t, xx, yy);
+    cv.eval_d(t, 1, xd, yd);
+    cv.eval_d(t, 2, x2, y2);
+    x[k] = xx;
+    y[k] = yy;
+    x1[k] = xd;
+    y1[k] = yd;
+    diag[k] = (x2 * yd - xd * y2) / (4.0 * M_PI * (xd * xd + yd * yd)) * (two_pi / Nb);
+    P->xy_host[2 * k] = xx;
+    P->xy_host[2 * k + 1] = yy;
+  }
+  // largest node spacing and the near bands
+  double smax = 0.0;
+  for (int k = 0; k < 4096; ++k) {
+    double xd, yd;
+    cv.eval_d(two_pi * k / 4096, 1, xd, yd);
+    smax = std::max(smax, std::hypot(xd, yd));
+  }
+  P->s = two_pi / Nb * smax;
+  P->delta = 5.0 * P->s;
+  const int R = P->R, NR = R * Nb;
+  std::vector<double> rx(NR), ry(NR), rx1(NR), ry1(NR);
+  for (int m = 0; m < NR; ++m) {
+    double t = two_pi * m / NR;
+    cv.eval(t, rx[m], ry[m]);
+    cv.eval_d(t, 1, rx1[m], ry1[m]);
+  }
+  std::vector<double> twb(2 * (size_t)Nb), twr(2 * (size_t)NR);
+  for (int t = 0; t < Nb; ++t) {
+    double ang = two_pi * t / Nb;
+    twb[2 * t] = std::cos(ang);
+    twb[2 * t + 1] = -std::sin(ang);
+  }
+  for (int t = 0; t < NR; ++t) {
+    double ang = two_pi * t / NR;
+    twr[2 * t] = std::cos(ang);
+    twr[2 * t + 1] = std::sin(ang);
+  }
+  // u_p interpolation stencils at the nodes
+  std::vector<int32_t> ui0(Nb), uj0(Nb);
+  std::vector<double> uwx((size_t)Nb * MP), uwy((size_t)Nb * MP);
+  const int off = (MP + 1) / 2 - 1;
+  for (int k = 0; k < Nb; ++k) {
+    int i0 = (int)std::floor((x[k] - a0) / h) - off;
+    int j0 = (int)std::floor((y[k] - b0) / h) - off;
+    i0 = std::min(std::max(i0, 0), nx - MP);
+    j0 = std::min(std::max(j0, 0), ny - MP);
+    ui0[k] = i0;
+    uj0[k] = j0;
+    double nxs[kMaxM], nys[kMaxM];
+    for (int e = 0; e < MP; ++e) {
+      nxs[e] = a0 + h * double(i0 + e);
+      nys[e] = b0 + h * double(j0 + e);
+    }
+    lagr(nxs, MP, x[k], &uwx[(size_t)k * MP]);
+    lagr(nys, MP, y[k], &uwy[(size_t)k * MP]);
+  }
+  // near points: inside points closer than delta; seeds from the nearest node of a
+  // fine sampling of the curve (boxes around each sample)
+  std::vector<uint8_t> inside((size_t)nx * ny, 0);
+  for (int j = 0; j < ny; ++j)
+    for (int k = p->row_iv_off[j]; k < p->row_iv_off[j + 1]; ++k)
+      for (int i = p->row_iv[2 * k]; i <= p->row_iv[2 * k + 1]; ++i) inside[(size_t)j * nx + i] = 1;
+  const int ns = std::max(p->prm.B, 4 * Nb);
+  std::vector<double> seed((size_t)nx * ny, -1.0), best((size_t)nx * ny, 1e300);
+  const double reach = P->delta + 2.0 * h;
+  for (int q = 0; q < ns; ++q) {
+    double t = two_pi * q / ns, cx, cy;
+    cv.eval(t, cx, cy);
+    int i0 = std::max(0, (int)std::floor((cx - reach - a0) / h));
+    int i1 = std::min(nx - 1, (int)std::ceil((cx + reach - a0) / h));
+    int j0 = std::max(0, (int)std::floor((cy - reach - b0) / h));
+    int j1 = std::min(ny - 1, (int)std::ceil((cy + reach - b0) / h));
+    for (int j = j0; j <= j1; ++j)
+      for (int i = i0; i <= i1; ++i) {
+        size_t l = (size_t)j * nx + i;
+        if (!inside[l]) continue;
+        double dx = a0 + h * double(i) - cx, dy = b0 + h * double(j) - cy;
+        double d2 = dx * dx + dy * dy;
+        if (d2 < best[l] && d2 <= reach * reach) {
+          best[l] = d2;
+          seed[l] = t;
+        }
+      }
+  }
+  std::vector<int32_t> cl;
+  std::vector<double> qx, qy, tq;
+  for (size_t l = 0; l < seed.size(); ++l)
+    if (seed[l] >= 0) {
+      cl.push_back((int32_t)l);
+      qx.push_back(a0 + h * double(l % nx));
+      qy.push_back(b0 + h * double(l / nx));
+      tq.push_back(seed[l]);
+    }
+  std::vector<int> conv;
+  fc2d_status st = foot_newton_gpu(cv, qx, qy, tq, conv, two_pi / ns);
+  if (st) return fail(st);
+  std::vector<uint8_t> near((size_t)nx * ny, 0);
+  std::vector<int32_t> mid, close;
+  std::vector<double> cgeo, cw;
+  P->close_nodes.assign(MP, 0.0);
+  for (int j = 1; j < MP; ++j) P->close_nodes[j] = (P->delta + P->s * (j - 1)) / R;
+  for (size_t n = 0; n < cl.size(); ++n) {
+    double fx, fy;
+    cv.eval(tq[n], fx, fy);
+    double eta = std::hypot(qx[n] - fx, qy[n] - fy);
+    if (!(eta < P->delta)) continue;
+    if (!conv[n]) return fail(set_error(FC2D_ERR_NOT_CONVERGED, "Poisson setup: foot search"));
+    near[cl[n]] = 1;
+    if (eta >= P->delta / R) {
+      mid.push_back(cl[n]);
+    } else {
+      double t = std::fmod(tq[n], two_pi);
+      if (t < 0) t += two_pi;
+      double xd, yd;
+      cv.eval_d(t, 1, xd, yd);
+      double sp = std::hypot(xd, yd);
+      close.push_back(cl[n]);
+      cgeo.insert(cgeo.end(), {fx, fy, yd / sp, -xd / sp, t});
+      double w[kMaxM];
+      lagr(P->close_nodes.data(), MP, eta, w);
+      cw.insert(cw.end(), w, w + MP);
+    }
+  }
+  std::vector<int32_t> far;
+  for (size_t l = 0; l < inside.size(); ++l)
+    if (inside[l] && !near[l]) far.push_back((int32_t)l);
+  P->n_far = (int64_t)far.size();
+  P->n_mid = (int64_t)mid.size();
+  P->n_close = (int64_t)close.size();
+  if ((st = up(P, &P->bx, x)) || (st = up(P, &P->by, y)) || (st = up(P, &P->bx1, x1)) ||
+      (st = up(P, &P->by1, y1)) || (st = up(P, &P->rx, rx)) || (st = up(P, &P->ry, ry)) ||
+      (st = up(P, &P->rx1, rx1)) || (st = up(P, &P->ry1, ry1)) || (st = up(P, &P->twb, twb)) ||
+      (st = up(P, &P->twr, twr)) || (st = up(P, &P->ui0, ui0)) || (st = up(P, &P->uj0, uj0)) ||
+      (st = up(P, &P->uwx, uwx)) || (st = up(P, &P->uwy, uwy)) ||
+      (st = up(P, &P->far_lin, far)) || (st = up(P, &P->mid_lin, mid)) ||
+      (st = up(P, &P->close_lin, close)) || (st = up(P, &P->close_geo, cgeo)) ||
+      (st = up(P, &P->close_w, cw)) || (st = up(P, &P->dnodes, P->close_nodes)))
+    return fail(st);
+  double* ddiag = nullptr;
+  if ((st = up(P, &ddiag, diag)) || (st = alloc(P, &P->A, (size_t)Nb * Nb)) ||
+      (st = alloc(P, &P->V, (size_t)(kGmresMax + 1) * Nb)) || (st = alloc(P, &P->w, Nb)) ||
+      (st = alloc(P, &P->h, kGmresMax + 2)) || (st = alloc(P, &P->g, Nb)) ||
+      (st = alloc(P, &P->phi, Nb)) || (st = alloc(P, &P->ghat, 2 * (Nb / 2 + 1))) ||
+      (st = alloc(P, &P->phiR, NR)) || (st = alloc(P, &P->ab, 2 * (size_t)Nb)) ||
+      (st = alloc(P, &P->abR, 2 * (size_t)NR)) || (st = alloc(P, &P->c00, 1024)))
+    return fail(st);
+  k_bie_matrix<<<dim3((Nb + 255) / 256, Nb), 256>>>(Nb, P->bx, P->by, P->bx1, P->by1, ddiag,
+                                                    P->A);
+  if ((st = cuda_check(cudaDeviceSynchronize(), "BIE matrix"))) return fail(st);
+  p->poisson = P;
+  return FC2D_OK;
+}
+
+// GMRES (no restart) for A phi = g on device vectors, host-side Hessenberg least squares.
+static fc2d_status gmres(PoissonState* P, cudaStream_t s, double tol) {
+  const int n = P->Nb;
+  const unsigned gb = (unsigned)((n + 255) / 256);
+  std::vector<double> H((size_t)(kGmresMax + 1) * kGmresMax, 0.0), cs(kGmresMax), sn(kGmresMax),
+      e(kGmresMax + 1, 0.0), hcol(kGmresMax + 2);
+  // beta = ||g||, V_0 = g / beta
+  k_dots<<<1, 256, 0, s>>>(n, 1, P->g, P->g, P->h);
+  double beta2 = 0;
+  cudaMemcpyAsync(&beta2, P->h, 8, cudaMemcpyDeviceToHost, s);
+  cudaStreamSynchronize(s);
+  double beta = std::sqrt(beta2);
+  if (beta == 0) {
+    cudaMemsetAsync(P->phi, 0, n * 8, s);
+    P->last_iters = 0;
+    return FC2D_OK;
+  }
+  double hb[1] = {beta};
+  cudaMemcpyAsync(P->h + kGmresMax + 1, hb, 8, cudaMemcpyHostToDevice, s);
+  k_scale_to<<<gb, 256, 0, s>>>(n, P->g, P->h + kGmresMax + 1, P->V);
+  e[0] = beta;
+  int m = 0;
+  for (int j = 0; j < kGmresMax; ++j) {
+    double* vj = P->V + (size_t)j * n;
+    k_gemv<<<(unsigned)((n * 32 + 255) / 256), 256, 0, s>>>(n, P->A, vj, P->w);
+    // classical Gram-Schmidt, twice
+    for (int pass = 0; pass < 2; ++pass) {
+      k_dots<<<j + 1, 256, 0, s>>>(n, j + 1, P->V, P->w, P->h);
+      k_sub_proj<<<gb, 256, 0, s>>>(n, j + 1, P->V, P->h, P->w);
+      std::vector<double> hp(j + 1);
+      cudaMemcpyAsync(hp.data(), P->h, (j + 1) * 8, cudaMemcpyDeviceToHost, s);
+      cudaStreamSynchronize(s);
+      for (int i = 0; i <= j; ++i) H[(size_t)i * kGmresMax + j] += hp[i];
+    }
+    k_dots<<<1, 256, 0, s>>>(n, 1, P->w, P->w, P->h);
+    double nn = 0;
+    cudaMemcpyAsync(&nn, P->h, 8, cudaMemcpyDeviceToHost, s);
+    cudaStreamSynchronize(s);
+    double hn = std::sqrt(nn);
+    H[(size_t)(j + 1) * kGmresMax + j] = hn;
+    if (hn > 0) {
+      double hv[1] = {hn};
+      cudaMemcpyAsync(P->h + kGmresMax + 1, hv, 8, cudaMemcpyHostToDevice, s);
+      k_scale_to<<<gb, 256, 0, s>>>(n, P->w, P->h + kGmresMax + 1, P->V + (size_t)(j + 1) * n);
+    }
+    // Givens rotations
+    for (int i = 0; i < j; ++i) {
+      double a = H[(size_t)i * kGmresMax + j], b = H[(size_t)(i + 1) * kGmresMax + j];
+      H[(size_t)i * kGmresMax + j] = cs[i] * a + sn[i] * b;
+      H[(size_t)(i + 1) * kGmresMax + j] = -sn[i] * a + cs[i] * b;
+    }
+    double a = H[(size_t)j * kGmresMax + j], b = H[(size_t)(j + 1) * kGmresMax + j];
+    double r = std::hypot(a, b);
+    cs[j] = r == 0 ? 1.0 : a / r;
+    sn[j] = r == 0 ? 0.0 : b / r;
+    H[(size_t)j * kGmresMax + j] = r;
+    H[(size_t)(j + 1) * kGmresMax + j] = 0.0;
+    e[j + 1] = -sn[j] * e[j];
+    e[j] = cs[j] * e[j];
+    m = j + 1;
+    if (std::fabs(e[j + 1]) <= tol * beta || hn == 0) break;
+  }
+  // solve the triangular system and combine
+  std::vector<double> yv(m);
+  for (int i = m - 1; i >= 0; --i) {
+    double sacc = e[i];
+    for (int k = i + 1; k < m; ++k) sacc -= H[(size_t)i * kGmresMax + k] * yv[k];
+    yv[i] = sacc / H[(size_t)i * kGmresMax + i];
+  }
+  cudaMemcpyAsync(P->h, yv.data(), m * 8, cudaMemcpyHostToDevice, s);
+  k_combine<<<gb, 256, 0, s>>>(n, m, P->V, P->h, P->phi);
+  P->last_iters = m;
+  P->last_resid = std::fabs(e[m]) / beta;
+  if (std::fabs(e[m]) > 1e3 * tol * beta)
+    return set_error(FC2D_ERR_NOT_CONVERGED, "GMRES did not reach its tolerance");
+  return cuda_check(cudaGetLastError(), "GMRES");
+}
+
+fc2d_status poisson_solve(fc2d_plan_s* p, int n_f, const double* fg, const double* fb,
+                          const double* gn, double* u, double* phi_out, void* inter,
+                          cudaStream_t s) {
+  auto* P = static_cast<PoissonState*>(p->poisson);
+  const int nx = p->grid.nx, ny = p->grid.ny, Nb = P->Nb, MP = P->MP, NR = P->R * Nb;
+  const double a0 = p->grid.a0, b0 = p->grid.b0, h = p->grid.h;
+  if (n_f > 1024) return set_error(FC2D_ERR_ARG, "fc2d_poisson: n_f <= 1024");
+  // u_p (forward rows already in `inter` from the caller): multiplier + inverse
+  FftArgs fa{};
+  fa.nx = nx;
+  fa.ny = ny;
+  fa.pitch = (nx / 2 + 1 + 7) / 8 * 8;
+  fa.nrx = p->fx.n_radix;
+  fa.nry = p->fy.n_radix;
+  for (int i = 0; i < fa.nrx; ++i) fa.rx[i] = p->fx.radix[i];
+  for (int i = 0; i < fa.nry; ++i) fa.ry[i] = p->fy.radix[i];
+  fa.twx = p->fx.tw64;
+  fa.twy = p->fy.tw64;
+  fa.rtw = p->rtw64;
+  fa.scale = 1.0 / ((double)nx * ny);
+  {
+    ProfScope ps(p, "poisson_cols", s);
+    const int ncol = nx / 2 + 1;
+    int cb = 1;
+    while (cb < 8 && 2 * (size_t)(2 * cb) * ny * sizeof(double2) <= 200 * 1024) cb *= 2;
+    size_t sm = 2 * (size_t)cb * ny * sizeof(double2);
+    cudaFuncSetAttribute(k_poisson_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_poisson_cols<<<dim3((ncol + cb - 1) / cb, n_f), 256, sm, s>>>(
+        fa, cb, (double2*)inter, P->c00, nx * h, ny * h);
+  }
+  {
+    ProfScope ps(p, "poisson_rows", s);
+    size_t sm = (size_t)nx * sizeof(double2);
+    cudaFuncSetAttribute(k_poisson_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_poisson_rows<<<dim3(ny, n_f), 256, sm, s>>>(fa, (const double2*)inter, P->c00, a0, b0, h, u);
+  }
+  fc2d_status st = cuda_check(cudaGetLastError(), "Poisson particular solution");
+  if (st) return st;
+  const unsigned gb = (unsigned)((Nb + 255) / 256);
+  for (int f = 0; f < n_f; ++f) {
+    double* uf = u + (size_t)f * nx * ny;
+    k_up_nodes<<<gb, 256, 0, s>>>(Nb, MP, nx, P->ui0, P->uj0, P->uwx, P->uwy, uf,
+                                  gn + (size_t)f * Nb, P->g);
+    if ((st = gmres(P, s, 1e-14))) return st;
+    if (phi_out) cudaMemcpyAsync(phi_out + (size_t)f * Nb, P->phi, Nb * 8, cudaMemcpyDeviceToDevice, s);
+    // density refinement and node coefficients
+    k_density_dft<<<(unsigned)((Nb / 2 + 1 + 127) / 128), 128, 0, s>>>(Nb, P->phi,
+                                                                     (const double2*)P->twb,
+                                                                     (double2*)P->ghat);
+    k_density_refine<<<(unsigned)((NR + 255) / 256), 256, 0, s>>>(Nb, NR, (const double2*)P->ghat,
+                                                                 (const double2*)P->twr, P->phiR);
+    k_node_coef<<<gb, 256, 0, s>>>(Nb, P->bx1, P->by1, P->phi, (double2*)P->ab);
+    k_node_coef<<<(unsigned)((NR + 255) / 256), 256, 0, s>>>(NR, P->rx1, P->ry1, P->phiR,
+                                                            (double2*)P->abR);
+    {
+      ProfScope ps(p, "dlp_far", s);
+      if (P->n_far)
+        k_dlp<<<(unsigned)((P->n_far + 255) / 256), 256, 0, s>>>(
+            (int)P->n_far, P->far_lin, nx, a0, b0, h, Nb, P->bx, P->by, (const double2*)P->ab, uf);
+    }
+    {
+      ProfScope ps(p, "dlp_near", s);
+      if (P->n_mid)
+        k_dlp<<<(unsigned)((P->n_mid + 255) / 256), 256, 0, s>>>(
+            (int)P->n_mid, P->mid_lin, nx, a0, b0, h, NR, P->rx, P->ry, (const double2*)P->abR, uf);
+      if (P->n_close) {
+        // boundary values g - u_p: reuse ghat for their coefficients
+        k_density_dft<<<(unsigned)((Nb / 2 + 1 + 127) / 128), 128, 0, s>>>(
+            Nb, P->g, (const double2*)P->twb, (double2*)P->ghat);
+        k_dlp_close<<<(unsigned)P->n_close, 256, 0, s>>>(
+            (int)P->n_close, P->close_lin, P->close_geo, P->close_w, P->dnodes, MP, NR, P->rx,
+            P->ry, (const double2*)P->abR, Nb, (const double2*)P->ghat, uf);
+      }
+    }
+    k_zero_outside<<<ny, 256, 0, s>>>(nx, p->dev.row_iv_off, p->dev.row_iv, uf);
+  }
+  return cuda_check(cudaGetLastError(), "Poisson solve");
+}
+
+int poisson_nb(const fc2d_plan_s* p) {
+  return p->poisson ? static_cast<const PoissonState*>(p->poisson)->Nb : 0;
+}
+
+const double* poisson_nodes(const fc2d_plan_s* p) {
+  return p->poisson ? static_cast<const PoissonState*>(p->poisson)->xy_host.data() : nullptr;
+}
+
+void poisson_stats(const fc2d_plan_s* p, int* iters, double* resid, int64_t* n_near) {
+  auto* P = static_cast<const PoissonState*>(p->poisson);
+  if (iters) *iters = P ? P->last_iters : 0;
+  if (resid) *resid = P ? P->last_resid : 0.0;
+  if (n_near) *n_near = P ? P->n_mid + P->n_close : 0;
+}
+
+}  // namespace fc2d

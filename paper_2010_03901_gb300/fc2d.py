@@ -72,6 +72,10 @@ def load_library(path: str = LIB_PATH):
         "fc2d_extend_coeffs": [P, ct.c_int, P, P, P, P],
         "fc2d_coeffs_static": [P, ct.c_int, P, P, P],
         "fc2d_sync_status": [P, P],
+        "fc2d_poisson_plan": [P, ct.c_int],
+        "fc2d_poisson_nodes": [P, P, P],
+        "fc2d_poisson_info": [P, P, P, P],
+        "fc2d_poisson": [P, ct.c_int, P, P, P, P, P, P],
         "fc2d_profile": [P, ct.c_int],
         "fc2d_profile_read": [P, ct.c_int, P, P, P, P],
     }
@@ -184,6 +188,25 @@ class Plan:
         """fc2d_coeffs without any device allocation (fixed 64 MiB scratch)."""
         _check(_lib.fc2d_coeffs_static(self.handle, n_f, _ptr(ext), _ptr(fhat),
                                        _stream(stream)))
+
+    def fc2d_poisson_plan(self, n_b=0):
+        _check(_lib.fc2d_poisson_plan(self.handle, n_b))
+
+    def fc2d_poisson_nodes(self):
+        n = ct.c_int()
+        _check(_lib.fc2d_poisson_nodes(self.handle, None, ct.byref(n)))
+        xy = np.zeros((n.value, 2))
+        _check(_lib.fc2d_poisson_nodes(self.handle, xy.ctypes.data, ct.byref(n)))
+        return xy
+
+    def fc2d_poisson(self, n_f, f_grid, f_bdry, g_nodes, u, phi=None, stream=None):
+        _check(_lib.fc2d_poisson(self.handle, n_f, _ptr(f_grid), _ptr(f_bdry), _ptr(g_nodes),
+                                 _ptr(u), _ptr(phi), _stream(stream)))
+
+    def fc2d_poisson_info(self):
+        it, res, nn = ct.c_int(), ct.c_double(), ct.c_int64()
+        _check(_lib.fc2d_poisson_info(self.handle, ct.byref(it), ct.byref(res), ct.byref(nn)))
+        return {"gmres_iters": it.value, "gmres_resid": res.value, "n_near": nn.value}
 
     def fc2d_profile(self, enable=True):
         _check(_lib.fc2d_profile(self.handle, 1 if enable else 0))

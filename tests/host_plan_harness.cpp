@@ -37,10 +37,23 @@ static cudaError_t h_getdev(int* d) {
 namespace fc2d {
 fc2d_status foot_newton_gpu(const Curve& c, const std::vector<double>& qx,
                             const std::vector<double>& qy, std::vector<double>& th,
-                            std::vector<int>& conv) {
+                            std::vector<int>& conv, double window) {
   conv.assign(qx.size(), 0);
   for (size_t i = 0; i < qx.size(); ++i) {
     double t = th[i];
+    {
+      const double t0 = t;
+      double best = 1e300;
+      for (int k = -24; k <= 24; ++k) {
+        double tk = t0 + window * double(k) / 24, x, y;
+        c.eval(tk, x, y);
+        double d2 = (x - qx[i]) * (x - qx[i]) + (y - qy[i]) * (y - qy[i]);
+        if (d2 < best) {
+          best = d2;
+          t = tk;
+        }
+      }
+    }
     for (int it = 0; it < 60; ++it) {
       double x, y, x1, y1, x2, y2;
       c.eval(t, x, y);
@@ -51,7 +64,13 @@ fc2d_status foot_newton_gpu(const Curve& c, const std::vector<double>& qx,
       if (!(dphi > 0)) break;
       double step = phi / dphi;
       t -= step;
-      if (std::fabs(step) < 1e-15) {
+      if (std::fabs(step) < 1e-12) {
+        c.eval(t, x, y);
+        c.eval_d(t, 1, x1, y1);
+        c.eval_d(t, 2, x2, y2);
+        phi = (x - qx[i]) * x1 + (y - qy[i]) * y1;
+        dphi = x1 * x1 + y1 * y1 + (x - qx[i]) * x2 + (y - qy[i]) * y2;
+        if (dphi > 0) t -= phi / dphi;
         conv[i] = 1;
         break;
       }
@@ -60,6 +79,7 @@ fc2d_status foot_newton_gpu(const Curve& c, const std::vector<double>& qx,
   }
   return FC2D_OK;
 }
+void poisson_destroy(fc2d_plan_s*) {}
 // interpolation weights are a GPU step of the plan; the harness leaves them unset
 fc2d_status interp_weights_gpu(int, int, int, int, double, int, const double*, const double*,
                                bool, void*, int32_t*, int32_t*) {

@@ -1,0 +1,78 @@
+"""GPU Poisson solver (Section 4.1) against the oracle, and the star 1024^2 workload
+(manufactured u = sin(2x) e^y) against the exact solution."""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import fc2d as OF
+from oracle import geometry as OG
+from oracle import poisson as OP
+from oracle.fc_matrices import load_fc_matrices
+
+pytestmark = pytest.mark.gpu
+
+# u = u_p + v: u_p inherits the 1e-12 spectrum bar; v is a sum of ~N_b terms of size up
+# to ~1/(N_b * 5 s) near the curve, where the GMRES (1e-14) and summation orders differ.
+TOL_U = 1e-11
+
+
+def rel(a, b):
+    return float(np.abs(a - b).max() / np.abs(b).max())
+
+
+def run_gpu(w, f, g_fn, fc2d, torch):
+    g, p = w.grid, w.params
+    plan = fc2d.fc2d_plan(w.boundary.arrays(), (g.a0, g.b0, g.h, g.nx, g.ny),
+                          dict(B=p.B, k1=p.k1))
+    plan.fc2d_poisson_plan(0)
+    xy = plan.fc2d_poisson_nodes()
+    bxy = plan.fc2d_boundary_points()
+    dev = torch.device("cuda:0")
+    fg = torch.tensor(W.grid_values(w, f)[None], device=dev)
+    fb = torch.tensor(f(bxy[:, 0], bxy[:, 1])[None], device=dev)
+    gn = torch.tensor(g_fn(xy[:, 0], xy[:, 1])[None], device=dev)
+    u = torch.zeros_like(fg)
+    phi = torch.zeros((1, len(xy)), dtype=torch.float64, device=dev)
+    plan.fc2d_poisson(1, fg, fb, gn, u, phi)
+    plan.fc2d_sync_status()
+    return u.cpu().numpy()[0], phi.cpu().numpy()[0], plan
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    torch = pytest.importorskip("torch")
+    assert torch.cuda.is_available()
+    return torch
+
+
+@pytest.fixture(scope="module")
+def fc2d():
+    from paper_2010_03901_gb300 import fc2d as mod
+    return mod
+
+
+@pytest.mark.parametrize("name", ["disk128", "star200", "kite160x144"])
+def test_poisson_parity(name, fc2d, torch_cuda):
+    w = W.workload(name)
+    u_ex, f = W.u_manufactured, W.lap_u_manufactured
+    geo = OG.build_geometry(w)
+    bx, by = OP.bie_points(geo.curve, w.grid.nx)
+    ref = OP.solve(geo, load_fc_matrices(), W.grid_values(w, f), OF.boundary_values(geo, f),
+                   u_ex(bx, by))
+    u, phi, plan = run_gpu(w, f, u_ex, fc2d, torch_cuda)
+    assert rel(phi, ref["phi"]) < 1e-12
+    assert rel(u, ref["u"]) < TOL_U, rel(u, ref["u"])
+    info = plan.fc2d_poisson_info()
+    assert 0 < info["gmres_iters"] < 100 and info["gmres_resid"] < 1e-13
+
+
+def test_star1024_manufactured(fc2d, torch_cuda):
+    """The star r = 1 + 0.3 cos 5 theta at 1024^2 (k1 = 0.0013): max error against the
+    exact u = sin(2x) e^y, and parity with the oracle on sampled grid points."""
+    w = W.workload("star1024")
+    u_ex, f = W.u_manufactured, W.lap_u_manufactured
+    u, phi, plan = run_gpu(w, f, u_ex, fc2d, torch_cuda)
+    geo = OG.build_geometry(w)
+    X, Y = np.meshgrid(geo.xs, geo.ys)
+    err = np.abs(u - u_ex(X, Y))[geo.inside].max() / np.abs(u_ex(X, Y)[geo.inside]).max()
+    assert err < 1e-9, err

@@ -10,7 +10,7 @@ from oracle import geometry as OG
 from oracle.fc_matrices import load_fc_matrices
 from tests import host_plan
 
-CASES = ["disk64", "disk128", "star200", "kite160x144"]
+CASES = ["disk64", "disk128", "star200", "kite160x144", "star1024"]
 
 
 @pytest.fixture(scope="module", params=CASES)
