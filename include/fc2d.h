@@ -188,6 +188,19 @@ fc2d_status fc2d_poisson(fc2d_plan_t plan, int n_f, const double* f_grid_dev,
 fc2d_status fc2d_poisson_info(fc2d_plan_t plan, int* gmres_iters, double* gmres_resid,
                               int64_t* n_near);
 
+/* Fourier Forwarding interior propagator (Section 4.2, eqs. (4.8)-(4.12)), FP64 plans.
+ * For n_f pairs of initial data (u, u_t), given like f in fc2d_extend (grid values
+ * [n_f][ny][nx] and boundary data [n_f][n_bdry]): the 2D-FC expansions F and G, the modal
+ * solutions a = hat f cos(w t) + hat g sin(w t)/w (a_00 = hat f_00 + t hat g_00),
+ * w = 2 pi c sqrt((l/L_x)^2 + (m/L_y)^2), and their inverse DFTs.  u_out and ut_out
+ * [n_f][ny][nx] receive U_FC(., t) and its time derivative on the whole grid; they are
+ * the wave solution at the grid points farther than c t from the curve (domain of
+ * dependence).  ny <= 4736. */
+fc2d_status fc2d_wave_interior(fc2d_plan_t plan, int n_f, double c, double t,
+                               const double* u0_grid_dev, const double* u0_bdry_dev,
+                               const double* ut0_grid_dev, const double* ut0_bdry_dev,
+                               double* u_out_dev, double* ut_out_dev, void* stream);
+
 /* Kernel timing (tracing).  While enabled, every kernel the plan launches is
  * bracketed by a pair of CUDA events recorded on its launching stream.
  * fc2d_profile_read waits for those events and returns, per kernel name, the number

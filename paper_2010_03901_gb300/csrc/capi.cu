@@ -390,3 +390,59 @@ extern "C" fc2d_status fc2d_poisson(fc2d_plan_t p, int n_f, const double* fg, co
   }
   return poisson_solve(p, n_f, fg, fb, g_nodes, u, phi, ws(p, L.ointer), s);
 }
+
+// ------------------------------------------------------------------------- //
+// Fourier Forwarding interior propagator (Section 4.2)
+// ------------------------------------------------------------------------- //
+extern "C" fc2d_status fc2d_wave_interior(fc2d_plan_t p, int n_f, double c, double t,
+                                          const double* u0, const double* u0_bdry,
+                                          const double* ut0, const double* ut0_bdry,
+                                          double* u_out, double* ut_out, void* stream) {
+  fc2d_status st = check_nf(p, n_f);
+  if (st) return st;
+  if (!u0 || !u0_bdry || !ut0 || !ut0_bdry || !u_out || !ut_out)
+    return set_error(FC2D_ERR_ARG, "fc2d_wave_interior: null pointer");
+  if (!(c > 0) || !(t >= 0)) return set_error(FC2D_ERR_ARG, "fc2d_wave_interior: c > 0, t >= 0");
+  if (p->prm.precision != FC2D_FP64)
+    return set_error(FC2D_ERR_UNSUPPORTED, "fc2d_wave_interior: FP64 plans only");
+  if (3 * (size_t)p->grid.ny * sizeof(double2) > 227 * 1024)
+    return set_error(FC2D_ERR_UNSUPPORTED, "fc2d_wave_interior: ny <= 4736");
+  cudaSetDevice(p->device);
+  Layout L = layout(p, 2 * n_f);
+  if ((st = ensure_workspace(p, L.total))) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t pitch = ((size_t)p->grid.nx / 2 + 1 + 7) / 8 * 8;
+  FftArgs fa = fft_args(p);
+  for (int half = 0; half < 2; ++half) {
+    const double* fg = half ? ut0 : u0;
+    const double* fb = half ? ut0_bdry : u0_bdry;
+    double* F = reinterpret_cast<double*>(ws(p, L.oF)) + (size_t)half * n_f * p->prm.B * (p->Cr + 1);
+    double* vals = reinterpret_cast<double*>(ws(p, L.ovals)) + (size_t)half * n_f * p->strip_lin.size();
+    double2* inter = reinterpret_cast<double2*>(ws(p, L.ointer)) + (size_t)half * n_f * p->grid.ny * pitch;
+    {
+      ProfScope ps(p, "gather_blend", s);
+      launch_gather_blend(gather_args(p, fg, fb, F, nullptr, nullptr), n_f, true, s);
+    }
+    {
+      ProfScope ps(p, "interp", s);
+      launch_interp(interp_args(p), n_f, true, F, vals, s);
+    }
+    {
+      ProfScope ps(p, "fft_rows_fused", s);
+      launch_fft_rows(fa, row_args(p), n_f, true, 1, nullptr, fg, vals, inter, s);
+    }
+  }
+  {
+    ProfScope ps(p, "wave_cols", s);
+    launch_wave_cols(fa, n_f, ws(p, L.ointer), c, t, p->grid.nx * p->grid.h,
+                     p->grid.ny * p->grid.h, s);
+  }
+  {
+    ProfScope ps(p, "inverse_rows", s);
+    double2* inter = reinterpret_cast<double2*>(ws(p, L.ointer));
+    launch_inverse_rows(fa, n_f, inter, nullptr, p->grid.a0, p->grid.b0, p->grid.h, u_out, s);
+    launch_inverse_rows(fa, n_f, inter + (size_t)n_f * p->grid.ny * pitch, nullptr, p->grid.a0,
+                        p->grid.b0, p->grid.h, ut_out, s);
+  }
+  return launched("fc2d_wave_interior");
+}

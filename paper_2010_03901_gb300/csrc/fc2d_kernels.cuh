@@ -97,5 +97,12 @@ void launch_fft_rows(const FftArgs& fa, const RowArgs& ra, int n_f, bool fp64, i
                      cudaStream_t s);
 void launch_fft_cols(const FftArgs& fa, int n_f, bool fp64, const void* inter, void* fhat,
                      cudaStream_t s);
+// Fourier Forwarding: modal advance of [2 n_f] row spectra (u's then u_t's), in place.
+void launch_wave_cols(const FftArgs& fa, int n_f, void* inter, double c, double t, double Lx,
+                      double Ly, cudaStream_t s);
+// FP64 inverse real row DFT of an [n_f][ny][pitch] half spectrum already inverted along
+// the columns; c00 (NULL allowed) adds c00[f] (x^2 + y^2)/4.
+void launch_inverse_rows(const FftArgs& fa, int n_f, const void* inter, const double* c00,
+                         double a0, double b0, double h, double* out, cudaStream_t s);
 
 }  // namespace fc2d

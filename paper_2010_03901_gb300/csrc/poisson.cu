@@ -152,7 +152,7 @@ __global__ void __launch_bounds__(256) k_poisson_rows(FftArgs fa, const double2*
   __syncthreads();
   const C* tw = reinterpret_cast<const C*>(fa.twx);
   C* Z = stockham<double>(A, Bf, Nh, 1, fa.rx, fa.nrx, tw, 1);
-  const double q = c00[f] * 0.25;
+  const double q = c00 ? c00[f] * 0.25 : 0.0;
   const double y = b0 + h * double(j);
   double* out = up + ((size_t)f * fa.ny + j) * nx;
   for (int m = threadIdx.x; m < Nh; m += blockDim.x) {
@@ -742,6 +742,14 @@ fc2d_status poisson_solve(fc2d_plan_s* p, int n_f, const double* fg, const doubl
     k_zero_outside<<<ny, 256, 0, s>>>(nx, p->dev.row_iv_off, p->dev.row_iv, uf);
   }
   return cuda_check(cudaGetLastError(), "Poisson solve");
+}
+
+// inverse real 2D-DFT rows (after an inverse column pass) for callers outside this file
+void launch_inverse_rows(const FftArgs& fa, int n_f, const void* inter, const double* c00,
+                         double a0, double b0, double h, double* out, cudaStream_t s) {
+  size_t sm = (size_t)fa.nx * sizeof(double2);
+  cudaFuncSetAttribute(k_poisson_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  k_poisson_rows<<<dim3(fa.ny, n_f), 256, sm, s>>>(fa, (const double2*)inter, c00, a0, b0, h, out);
 }
 
 int poisson_nb(const fc2d_plan_s* p) {

@@ -76,6 +76,7 @@ def load_library(path: str = LIB_PATH):
         "fc2d_poisson_nodes": [P, P, P],
         "fc2d_poisson_info": [P, P, P, P],
         "fc2d_poisson": [P, ct.c_int, P, P, P, P, P, P],
+        "fc2d_wave_interior": [P, ct.c_int, ct.c_double, ct.c_double, P, P, P, P, P, P, P],
         "fc2d_profile": [P, ct.c_int],
         "fc2d_profile_read": [P, ct.c_int, P, P, P, P],
     }
@@ -207,6 +208,12 @@ class Plan:
         it, res, nn = ct.c_int(), ct.c_double(), ct.c_int64()
         _check(_lib.fc2d_poisson_info(self.handle, ct.byref(it), ct.byref(res), ct.byref(nn)))
         return {"gmres_iters": it.value, "gmres_resid": res.value, "n_near": nn.value}
+
+    def fc2d_wave_interior(self, n_f, c, t, u0, u0_bdry, ut0, ut0_bdry, u_out, ut_out,
+                           stream=None):
+        _check(_lib.fc2d_wave_interior(self.handle, n_f, c, t, _ptr(u0), _ptr(u0_bdry),
+                                       _ptr(ut0), _ptr(ut0_bdry), _ptr(u_out), _ptr(ut_out),
+                                       _stream(stream)))
 
     def fc2d_profile(self, enable=True):
         _check(_lib.fc2d_profile(self.handle, 1 if enable else 0))
