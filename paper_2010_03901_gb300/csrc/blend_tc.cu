@@ -234,4 +234,184 @@ fc2d_status launch_blend_tc(int n_cols, int Cr, int d, int ldF, const double* co
   return cuda_check(cudaGetLastError(), "tensor-core blend launch");
 }
 
+
+// ------------------------------------------------------------------------- //
+// Fused form: the matching values and Gram coefficients of the CTA's 128 normals are
+// computed by its 8 warps (4 normals per warp and pass, groups of 8 lanes, as in
+// k_gather_blend) straight into the MMA operand tiles; then the three MMAs and the
+// epilogue, warps w and w+4 reading the two halves of the TMEM columns of lanes
+// 32(w%4)..32(w%4)+31.  Requires M - 1 <= 8 and d <= 8.
+// ------------------------------------------------------------------------- //
+__global__ void __launch_bounds__(256, 1) k_gather_blend_tc(GatherArgs g, TcArgs a) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  unsigned char* c_hi = smem;
+  unsigned char* c_lo = smem + 4096;
+  unsigned char* a_hi = smem + 8192;
+  unsigned char* a_lo = a_hi + kMaxCrPad * 32;
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(a_lo + kMaxCrPad * 32);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mbar + 1);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int n0 = blockIdx.x * kTileN;
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                 ::"r"(smem_u32(tmem_slot)), "r"(kTmemCols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(mbar)));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  for (int idx = tid; idx < a.ncr_pad * 8; idx += blockDim.x) {
+    const int q = idx >> 3, k = idx & 7;
+    float hi = 0.f, lo = 0.f;
+    if (q < a.Cr && k < a.d) {
+      hi = a.Ar_hi[q * a.d + k];
+      lo = a.Ar_lo[q * a.d + k];
+    }
+    *reinterpret_cast<float*>(a_hi + kmaj_off(q, k)) = hi;
+    *reinterpret_cast<float*>(a_lo + kmaj_off(q, k)) = lo;
+  }
+  // matching values and Gram coefficients (Section 3.2, eq. (2.6)) into the C tiles
+  {
+    const int s = lane & 7, g0 = lane & ~7;
+    const int M = g.M, d = g.d, NS = M - 1;
+    for (int pass = 0; pass < kTileN / 32; ++pass) {
+      const int ln = pass * 32 + warp * 4 + (lane >> 3);  // local normal (tile row)
+      const int n = n0 + ln;
+      const bool live = n < a.n_cols;
+      const int nn = live ? n : 0;
+      const int f = nn / g.B, pp = nn - f * g.B;
+      const double* fg = g.f_grid + (size_t)f * g.grid_stride;
+      const double* fb = g.f_bdry + (size_t)f * g.n_bdry;
+      double star = 0.0;
+      if (s < NS) {
+        const int32_t* gi = g.gidx + ((size_t)pp * NS + s) * M;
+        const double* gw = g.gw + ((size_t)pp * NS + s) * M;
+        for (int e = 0; e < M; ++e) {
+          const int32_t id = __ldg(gi + e);
+          const double v = id >= 0 ? __ldg(fg + id) : __ldg(fb + (-1 - id));
+          star = fma(__ldg(gw + e), v, star);
+        }
+      }
+      const double fbp = __ldg(fb + pp);
+      double fD;
+      {
+        const double* wn = g.wn + ((size_t)pp * (d - 1) + (s < d - 1 ? s : 0)) * M;
+        double acc = (s < d - 1) ? __ldg(wn) * fbp : 0.0;
+        for (int e = 1; e < M; ++e) {
+          const double st = __shfl_sync(0xffffffffu, star, g0 + e - 1);
+          if (s < d - 1) acc = fma(__ldg(wn + e), st, acc);
+        }
+        fD = s < d - 1 ? acc : (s == d - 1 ? fbp : 0.0);
+      }
+      double cs = 0.0;
+      for (int i = 0; i < d; ++i) {
+        const double v = __shfl_sync(0xffffffffu, fD, g0 + i);
+        if (s < d) cs = fma(__ldg(g.Q + i * d + s), v, cs);
+      }
+      const double v = (live && s < d) ? cs : 0.0;
+      const float hi = to_tf32((float)v);
+      *reinterpret_cast<float*>(c_hi + kmaj_off(ln, s)) = hi;
+      *reinterpret_cast<float*>(c_lo + kmaj_off(ln, s)) = (float)(v - (double)hi);
+      if (live && s == 0) a.F[(size_t)n * a.ldF] = (float)fbp;
+    }
+  }
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+  if (tid == 0) {
+    const uint32_t idesc = idesc_tf32(kTileN, a.ncr_pad);
+    const uint64_t dch = umma_desc(smem_u32(c_hi), 128, 256);
+    const uint64_t dcl = umma_desc(smem_u32(c_lo), 128, 256);
+    const uint64_t dah = umma_desc(smem_u32(a_hi), 128, 256);
+    const uint64_t dal = umma_desc(smem_u32(a_lo), 128, 256);
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n"
+        ::"r"(tmem), "l"(dch), "l"(dah), "r"(idesc), "r"(0));
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n"
+        ::"r"(tmem), "l"(dch), "l"(dal), "r"(idesc), "r"(1));
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n"
+        ::"r"(tmem), "l"(dcl), "l"(dah), "r"(idesc), "r"(1));
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+        ::"r"(smem_u32(mbar)) : "memory");
+  }
+  uint32_t done = 0;
+  for (uint32_t it = 0; it < kSpinLimit && !done; ++it) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(done) : "r"(smem_u32(mbar)), "r"(0) : "memory");
+  }
+  if (!done) {
+    if (tid == 0) atomicExch(a.status, (int)FC2D_ERR_TIMEOUT);
+    for (uint32_t it = 0; it < kSpinLimit && !done; ++it) {
+      asm volatile(
+          "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+          "selp.u32 %0, 1, 0, p;\n\t}\n"
+          : "=r"(done) : "r"(smem_u32(mbar)), "r"(0) : "memory");
+    }
+  }
+  done = __all_sync(0xffffffffu, done != 0) ? 1u : 0u;
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (done) {
+    const int quarter = warp & 3;
+    const int half = ((a.ncr_pad / 2) + 7) / 8 * 8;
+    const int cbeg = warp < 4 ? 0 : half, cend = warp < 4 ? half : a.ncr_pad;
+    const int n = n0 + quarter * 32 + lane;
+    float* Frow = a.F + (size_t)n * a.ldF;
+    for (int c0 = cbeg; c0 < cend; c0 += 8) {
+      uint32_t r[8];
+      const uint32_t addr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)c0;
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+          : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
+            "=r"(r[6]), "=r"(r[7])
+          : "r"(addr));
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      if (n < a.n_cols) {
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+          const int q = c0 + e;
+          if (q < a.Cr) Frow[1 + q] = __uint_as_float(r[e]);
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(kTmemCols));
+  }
+}
+
+fc2d_status launch_gather_blend_tc(const GatherArgs& g, int n_f, int ldF, const float* Ar_hi,
+                                   const float* Ar_lo, float* F, int* status, cudaStream_t s) {
+  if (g.Cr > kMaxCrPad || g.d > 8 || g.M - 1 > 8)
+    return set_error(FC2D_ERR_UNSUPPORTED, "fused tensor-core blend: C n_r <= 256, d <= 8, M <= 9");
+  TcArgs a{};
+  a.n_cols = n_f * g.B;
+  a.Cr = g.Cr;
+  a.d = g.d;
+  a.ldF = ldF;
+  a.ncr_pad = (g.Cr + 15) / 16 * 16;
+  a.Ar_hi = Ar_hi;
+  a.Ar_lo = Ar_lo;
+  a.F = F;
+  a.status = status;
+  size_t sm = 96 * 1024;  // caps residency at two CTAs per SM (256 TMEM columns each)
+  cudaFuncSetAttribute(k_gather_blend_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  k_gather_blend_tc<<<(a.n_cols + kTileN - 1) / kTileN, 256, sm, s>>>(g, a);
+  return cuda_check(cudaGetLastError(), "fused tensor-core blend launch");
+}
+
 }  // namespace fc2d

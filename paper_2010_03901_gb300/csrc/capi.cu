@@ -120,6 +120,8 @@ FftArgs fft_args(fc2d_plan_s* p) {
   a.twx = f64 ? (const void*)p->fx.tw64 : (const void*)p->fx.tw32;
   a.twy = f64 ? (const void*)p->fy.tw64 : (const void*)p->fy.tw32;
   a.rtw = f64 ? (const void*)p->rtw64 : (const void*)p->rtw32;
+  a.tsx = f64 ? (const void*)p->fx.tws64 : (const void*)p->fx.tws32;
+  a.tsy = f64 ? (const void*)p->fy.tws64 : (const void*)p->fy.tws32;
   a.scale = 1.0 / ((double)p->grid.nx * p->grid.ny);
   return a;
 }
@@ -138,6 +140,12 @@ fc2d_status launched(const char* what) { return cuda_check(cudaGetLastError(), w
 // contraction with A_r on the tensor cores into float strip values F.
 fc2d_status mixed_blend(fc2d_plan_s* p, int n_f, const double* fg, const double* fb, void* F,
                         const Layout& L, cudaStream_t s) {
+  if (p->prm.M - 1 <= 8 && p->prm.d <= 8) {
+    ProfScope ps(p, "gather_blend_tc", s);
+    return launch_gather_blend_tc(gather_args(p, fg, fb, nullptr, nullptr, nullptr), n_f,
+                                  p->Cr + 1, p->dev.Ar_hi, p->dev.Ar_lo, static_cast<float*>(F),
+                                  p->dev.status, s);
+  }
   double* coef = reinterpret_cast<double*>(ws(p, L.ocoef));
   double* bvals = reinterpret_cast<double*>(ws(p, L.obvals));
   {

@@ -135,54 +135,57 @@ fc2d_status foot_newton_gpu(const Curve& c, const std::vector<double>& qx,
 // ------------------------------------------------------------------------- //
 // Matching values + blending (Section 3.2, eq. (2.6))
 // ------------------------------------------------------------------------- //
-// Lanes 0..M-2 each evaluate one red star (M taps); lanes 0..d-2 form the matching
-// values; c = Q^T f_D; the warp then writes F[q] = (A_r c)_q (FP64 form) or the
-// Gram coefficients c (mixed form, consumed by the tensor-core contraction).
-template <bool kFp64Blend>
+// A warp serves 32/GS normals, one group of GS lanes each.  In a group, lane s < M-1
+// evaluates red star s (M taps), lane s < d-1 forms the matching value at r_{p,s}
+// (lane d-1 holds the boundary datum), lane s < d the Gram coefficient
+// c_s = sum_i Q[i][s] f_D[i]; then the group writes F[q] = (A_r c)_q (FP64 form) or the
+// Gram coefficients (mixed form, consumed by the tensor-core contraction).
+template <bool kFp64Blend, int GS>
 __global__ void __launch_bounds__(256) k_gather_blend(GatherArgs a) {
   const int lane = threadIdx.x & 31;
+  const int s = lane & (GS - 1), g0 = lane & ~(GS - 1);
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int f = blockIdx.y;
-  if (warp >= a.B) return;
-  const int p = warp, M = a.M, d = a.d, NS = M - 1;
+  const int p = warp * (32 / GS) + lane / GS;
+  const bool live = p < a.B;
+  const int pp = live ? p : 0;
+  const int M = a.M, d = a.d, NS = M - 1;
   const double* fg = a.f_grid + (size_t)f * a.grid_stride;
   const double* fb = a.f_bdry + (size_t)f * a.n_bdry;
   double star = 0.0;
-  if (lane < NS) {
-    const int32_t* gi = a.gidx + ((size_t)p * NS + lane) * M;
-    const double* gw = a.gw + ((size_t)p * NS + lane) * M;
+  if (s < NS) {
+    const int32_t* gi = a.gidx + ((size_t)pp * NS + s) * M;
+    const double* gw = a.gw + ((size_t)pp * NS + s) * M;
     for (int e = 0; e < M; ++e) {
       int32_t id = __ldg(gi + e);
       double v = id >= 0 ? __ldg(fg + id) : __ldg(fb + (-1 - id));
       star = fma(__ldg(gw + e), v, star);
     }
   }
-  const double fbp = __ldg(fb + p);
-  // matching values: lane q < d-1 computes f(r_{p,q}); lane d-1 holds the boundary datum
-  double fD = 0.0;
+  const double fbp = __ldg(fb + pp);
+  double fD;
   {
-    const double* wn = a.wn + ((size_t)p * (d - 1) + (lane < d - 1 ? lane : 0)) * M;
-    double acc = (lane < d - 1) ? __ldg(wn) * fbp : 0.0;
+    const double* wn = a.wn + ((size_t)pp * (d - 1) + (s < d - 1 ? s : 0)) * M;
+    double acc = (s < d - 1) ? __ldg(wn) * fbp : 0.0;
     for (int e = 1; e < M; ++e) {
-      double s = __shfl_sync(0xffffffffu, star, e - 1);
-      if (lane < d - 1) acc = fma(__ldg(wn + e), s, acc);
+      const double st = __shfl_sync(0xffffffffu, star, g0 + e - 1);
+      if (s < d - 1) acc = fma(__ldg(wn + e), st, acc);
     }
-    fD = lane < d - 1 ? acc : (lane == d - 1 ? fbp : 0.0);
+    fD = s < d - 1 ? acc : (s == d - 1 ? fbp : 0.0);
   }
-  // Gram coefficients c_j = sum_i Q[i][j] f_D[i]
-  double c[kMaxD];
-#pragma unroll
-  for (int j = 0; j < kMaxD; ++j) c[j] = 0.0;
+  double cs = 0.0;  // Gram coefficient c_s (lanes s < d)
   for (int i = 0; i < d; ++i) {
-    double v = __shfl_sync(0xffffffffu, fD, i);
-#pragma unroll
-    for (int j = 0; j < kMaxD; ++j)
-      if (j < d) c[j] = fma(a.Q[i * d + j], v, c[j]);
+    const double v = __shfl_sync(0xffffffffu, fD, g0 + i);
+    if (s < d) cs = fma(__ldg(a.Q + i * d + s), v, cs);
   }
   if (kFp64Blend) {
+    double c[kMaxD];
+#pragma unroll
+    for (int j = 0; j < kMaxD; ++j) c[j] = __shfl_sync(0xffffffffu, cs, g0 + (j < d ? j : 0));
+    if (!live) return;
     double* F = reinterpret_cast<double*>(a.F) + ((size_t)f * a.B + p) * (a.Cr + 1);
-    if (lane == 0) F[0] = fbp;
-    for (int q = lane; q < a.Cr; q += 32) {
+    if (s == 0) F[0] = fbp;
+    for (int q = s; q < a.Cr; q += GS) {
       const double* ar = a.Ar + (size_t)q * d;
       double v = 0.0;
 #pragma unroll
@@ -191,24 +194,25 @@ __global__ void __launch_bounds__(256) k_gather_blend(GatherArgs a) {
       F[q + 1] = v;
     }
   } else {
-    // mixed form: Gram coefficients for the contraction, and the boundary datum
-    if (lane < d) {
-      double v = 0.0;
-#pragma unroll
-      for (int j = 0; j < kMaxD; ++j)
-        if (j == lane) v = c[j];
-      a.coef[((size_t)f * a.B + p) * a.coef_ld + lane] = v;
-    }
-    if (lane == 0) a.bvals[(size_t)f * a.B + p] = fbp;
+    if (!live) return;
+    if (s < d) a.coef[((size_t)f * a.B + p) * a.coef_ld + s] = cs;
+    if (s == 0) a.bvals[(size_t)f * a.B + p] = fbp;
   }
 }
 
 void launch_gather_blend(const GatherArgs& a, int n_f, bool fp64, cudaStream_t s) {
-  dim3 grid((a.B * 32 + 255) / 256, n_f);
-  if (fp64)
-    k_gather_blend<true><<<grid, 256, 0, s>>>(a);
-  else
-    k_gather_blend<false><<<grid, 256, 0, s>>>(a);
+  // group size: the larger of M-1 red stars and d coefficients, rounded up to 8 or 16
+  const int GS = (a.M - 1 <= 8 && a.d <= 8) ? 8 : 16;
+  const int per_warp = 32 / GS;
+  const int warps = (a.B + per_warp - 1) / per_warp;
+  dim3 grid((warps * 32 + 255) / 256, n_f);
+  if (GS == 8) {
+    if (fp64) k_gather_blend<true, 8><<<grid, 256, 0, s>>>(a);
+    else k_gather_blend<false, 8><<<grid, 256, 0, s>>>(a);
+  } else {
+    if (fp64) k_gather_blend<true, 16><<<grid, 256, 0, s>>>(a);
+    else k_gather_blend<false, 16><<<grid, 256, 0, s>>>(a);
+  }
 }
 
 // ------------------------------------------------------------------------- //

@@ -75,6 +75,10 @@ void launch_gather_blend(const GatherArgs& a, int n_f, bool fp64, cudaStream_t s
 fc2d_status launch_blend_tc(int n_cols, int Cr, int d, int ldF, const double* coef,
                             int coef_ld, const double* bvals, const float* Ar_hi,
                             const float* Ar_lo, float* F, int* status, cudaStream_t s);
+// fused mixed form: matching values + Gram coefficients + tensor-core contraction in one
+// kernel (M <= 9, d <= 8); F [n_f*B][ldF] float.
+fc2d_status launch_gather_blend_tc(const GatherArgs& g, int n_f, int ldF, const float* Ar_hi,
+                                   const float* Ar_lo, float* F, int* status, cudaStream_t s);
 void launch_interp(const InterpArgs& a, int n_f, bool fp64, const void* F, void* vals,
                    cudaStream_t s);
 void launch_assemble(const RowArgs& a, int n_f, bool fp64, const double* f_grid,
@@ -87,6 +91,8 @@ struct FftArgs {
   const void* twx;            // exp(-2 pi i t/(nx/2)) table for the row transform
   const void* twy;            // exp(-2 pi i t/ny)
   const void* rtw;            // exp(-2 pi i k/nx), k <= nx/2
+  const void* tsx;            // per-stage twiddles of the row transform (power-of-two sizes)
+  const void* tsy;            // per-stage twiddles of the column transform
   double scale;               // 1/(nx ny)
 };
 

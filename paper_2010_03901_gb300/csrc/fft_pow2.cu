@@ -121,9 +121,38 @@ template <typename T, typename C, int R> __device__ __forceinline__ void dft(C* 
   else dft16<T, C>(v);
 }
 
+// Round-to-nearest-even double -> float on the integer pipe (the FP64 pipe that the
+// conversion instruction uses is narrow on this part).  Normal results only; values
+// that would be subnormal, infinite or NaN in float take the hardware conversion.
+__device__ __forceinline__ float d2f_rn(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
+  const int fe = (int)((b >> 52) & 0x7FF) - 1023 + 127;
+  if (fe <= 0 || fe >= 254) return (float)x;
+  const unsigned long long m = b & 0xFFFFFFFFFFFFFull;
+  unsigned r = ((unsigned)fe << 23) | (unsigned)(m >> 29);
+  const unsigned long long rem = m & 0x1FFFFFFFull;
+  if (rem > 0x10000000ull || (rem == 0x10000000ull && (r & 1u))) r += 1u;
+  return __uint_as_float(sign | r);
+}
+template <typename T> __device__ __forceinline__ T from_double(double x) { return (T)x; }
+template <> __device__ __forceinline__ float from_double<float>(double x) { return d2f_rn(x); }
+
 template <typename T> __host__ __device__ constexpr int pad_shift() { return sizeof(T) == 4 ? 5 : 4; }
 template <typename T> __device__ __forceinline__ int pad(int i) { return i + (i >> pad_shift<T>()); }
 template <typename T> __host__ __device__ constexpr int padded(int n) { return n + (n >> pad_shift<T>()); }
+
+// Offset of the twiddle block of the stage with sub-transform length NS in the
+// per-stage table (blocks of R x NS entries for every stage with NS > 1, in order).
+__host__ __device__ constexpr int stage_off(int N, int E, int NS) {
+  int off = 0, ns = 1;
+  while (ns < NS) {
+    const int R = (N / ns >= E) ? E : N / ns;
+    if (ns > 1) off += R * ns;
+    ns *= R;
+  }
+  return off;
+}
 
 // One Stockham stage of radix R on buffer `buf` (padded), NT threads, butterflies
 // j = t + m NT, m < E/R.  Ns = product of the earlier radices.
@@ -152,8 +181,9 @@ __device__ __forceinline__ void stage(typename Cx<T>::type* buf, int t, bool act
     const int j = t + m * NT;
     const int k = j & (NS - 1);
     if (NS > 1) {
+      constexpr int OFF = stage_off(N, E, NS);
 #pragma unroll
-      for (int r = 1; r < R; ++r) v[m * R + r] = mul(v[m * R + r], __ldg(tw + (size_t)r * k * TSTEP * tws));
+      for (int r = 1; r < R; ++r) v[m * R + r] = mul(v[m * R + r], __ldg(tw + OFF + r * NS + k));
     }
     dft<T, C, R>(v + m * R);
     const int base = (j / NS) * NS * R + k;
@@ -177,8 +207,91 @@ __device__ __forceinline__ void block_fft(typename Cx<T>::type* buf, int t, bool
   }
 }
 
-// complex values per thread (8: about 48 registers, two 1024-thread blocks per SM)
-template <typename T> __host__ __device__ constexpr int elems() { return 8; }
+// complex values per thread: 16 for float (radix-16 stages, three for 4096 points),
+// 8 for double (register pressure of FP64 complex values)
+template <typename T> __host__ __device__ constexpr int elems() { return sizeof(T) == 4 ? 16 : 8; }
+
+// First stage (Ns = 1, radix R) straight from global memory: x[j + r N/R] at stride
+// `stride`, length-R DFT, written to the shared buffer, then a barrier.
+template <typename T, int LOGN, int E, int R>
+__device__ __forceinline__ void stage_first_global(const typename Cx<T>::type* __restrict__ src,
+                                                   size_t stride, typename Cx<T>::type* buf,
+                                                   int t) {
+  using C = typename Cx<T>::type;
+  constexpr int N = 1 << LOGN;
+  constexpr int NT = N / E;
+  constexpr int NR = N / R;
+  constexpr int M = E / R;
+  C v[E];
+#pragma unroll
+  for (int m = 0; m < M; ++m) {
+    const int j = t + m * NT;
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[m * R + r] = __ldg(src + (size_t)(j + r * NR) * stride);
+  }
+#pragma unroll
+  for (int m = 0; m < M; ++m) {
+    const int j = t + m * NT;
+    dft<T, C, R>(v + m * R);
+#pragma unroll
+    for (int r = 0; r < R; ++r) buf[pad<T>(j * R + r)] = v[m * R + r];
+  }
+  __syncthreads();
+}
+
+// Last stage (Ns * R = N) from the shared buffer straight to global memory, scaled.
+template <typename T, int LOGN, int E, int R, int NS>
+__device__ __forceinline__ void stage_last_global(const typename Cx<T>::type* buf, int t,
+                                                  const typename Cx<T>::type* __restrict__ tw,
+                                                  typename Cx<T>::type* __restrict__ dst,
+                                                  size_t stride, T scale, bool store) {
+  using C = typename Cx<T>::type;
+  constexpr int N = 1 << LOGN;
+  constexpr int NT = N / E;
+  constexpr int NR = N / R;
+  constexpr int M = E / R;
+  constexpr int TSTEP = N / (NS * R);
+  C v[E];
+#pragma unroll
+  for (int m = 0; m < M; ++m) {
+    const int j = t + m * NT;
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[m * R + r] = buf[pad<T>(j + r * NR)];
+  }
+#pragma unroll
+  for (int m = 0; m < M; ++m) {
+    const int j = t + m * NT;
+    const int k = j & (NS - 1);
+    constexpr int OFF = stage_off(N, E, NS);
+#pragma unroll
+    for (int r = 1; r < R; ++r) v[m * R + r] = mul(v[m * R + r], __ldg(tw + OFF + r * NS + k));
+    dft<T, C, R>(v + m * R);
+    const int base = (j / NS) * NS * R + k;
+    if (store) {
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const C x = v[m * R + r];
+        dst[(size_t)(base + r * NS) * stride] = C{x.x * scale, x.y * scale};
+      }
+    }
+  }
+}
+
+// Stages after the first: shared-memory stages, the last one to global memory.
+template <typename T, int LOGN, int E, int NS>
+__device__ __forceinline__ void fft_rest_to_global(typename Cx<T>::type* buf, int t,
+                                                   const typename Cx<T>::type* __restrict__ tw,
+                                                   typename Cx<T>::type* __restrict__ dst,
+                                                   size_t stride, T scale, bool store) {
+  constexpr int N = 1 << LOGN;
+  constexpr int R = (N / NS >= E) ? E : N / NS;
+  if constexpr (NS * R == N) {
+    stage_last_global<T, LOGN, E, R, NS>(buf, t, tw, dst, stride, scale, store);
+  } else {
+    stage<T, LOGN, E, R, NS>(buf, t, true, tw, 1);
+    fft_rest_to_global<T, LOGN, E, NS * R>(buf, t, tw, dst, stride, scale, store);
+  }
+}
 
 // rows: nx = 2^(LOGNH+1); block = NT = 2^LOGNH / E threads
 template <typename T, typename TV, int LOGNH>
@@ -208,7 +321,20 @@ k_fft_rows_p2(FftArgs fa, RowArgs ra, int mode, const T* __restrict__ ext,
     const int iv0 = __ldg(ra.row_iv_off + j), iv1 = __ldg(ra.row_iv_off + j + 1);
     for (int k = iv0; k < iv1; ++k) {
       const int lo = __ldg(ra.row_iv + 2 * k), hi = __ldg(ra.row_iv + 2 * k + 1);
-      for (int i = lo + threadIdx.x; i <= hi; i += blockDim.x) put(i, (T)__ldg(fg + i));
+      // eight independent loads in flight per thread before the shared-memory stores
+      for (int i0 = lo + threadIdx.x; i0 <= hi; i0 += 8 * blockDim.x) {
+        double v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int i = i0 + u * blockDim.x;
+          v[u] = i <= hi ? __ldg(fg + i) : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int i = i0 + u * blockDim.x;
+          if (i <= hi) put(i, from_double<T>(v[u]));
+        }
+      }
     }
     const int s0 = __ldg(ra.row_strip_off + j), s1 = __ldg(ra.row_strip_off + j + 1);
     const TV* v = vals + (size_t)f * ra.n_strip;
@@ -216,7 +342,7 @@ k_fft_rows_p2(FftArgs fa, RowArgs ra, int mode, const T* __restrict__ ext,
     for (int k = s0 + threadIdx.x; k < s1; k += blockDim.x) put(__ldg(ra.s_lin + k) - base, (T)__ldg(v + k));
   }
   __syncthreads();
-  const C* tw = reinterpret_cast<const C*>(fa.twx);
+  const C* tw = reinterpret_cast<const C*>(fa.tsx);
   block_fft<T, LOGNH, E>(buf, t, t < NT, tw, 1);
   const C* rtw = reinterpret_cast<const C*>(fa.rtw);
   C* out = inter + ((size_t)f * fa.ny + j) * fa.pitch;
@@ -231,7 +357,9 @@ k_fft_rows_p2(FftArgs fa, RowArgs ra, int mode, const T* __restrict__ ext,
   }
 }
 
-// cols: ny = 2^LOGNY, CB columns per block, block = CB * NT threads
+// cols: ny = 2^LOGNY, CB columns per block, block = CB * NT threads.  Thread
+// (c = tid % CB, t = tid / CB): the CB columns of a row are read by neighbouring
+// threads.  First stage from the intermediate, last stage to the spectrum.
 template <typename T, int LOGNY, int CB>
 __global__ void __launch_bounds__(CB * ((1 << LOGNY) / elems<T>()))
 k_fft_cols_p2(FftArgs fa, const typename Cx<T>::type* __restrict__ inter,
@@ -239,30 +367,21 @@ k_fft_cols_p2(FftArgs fa, const typename Cx<T>::type* __restrict__ inter,
   using C = typename Cx<T>::type;
   constexpr int E = elems<T>();
   constexpr int N = 1 << LOGNY;
-  constexpr int NT = N / E;
   constexpr int PN = padded<T>(N);
+  constexpr int R1 = N >= E ? E : N;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* buf = reinterpret_cast<C*>(smem_raw);
   const int ncol = fa.nx / 2 + 1;
-  const int c0 = blockIdx.x * CB, f = blockIdx.y;
-  const C* src = inter + (size_t)f * N * fa.pitch + c0;
-  for (int idx = threadIdx.x; idx < N * CB; idx += blockDim.x) {
-    const int y = idx / CB, c = idx - y * CB;
-    buf[c * PN + pad<T>(y)] = (c0 + c < ncol) ? src[(size_t)y * fa.pitch + c] : C{(T)0, (T)0};
-  }
-  __syncthreads();
-  const int c = threadIdx.x / NT, t = threadIdx.x - c * NT;
-  const C* tw = reinterpret_cast<const C*>(fa.twy);
-  block_fft<T, LOGNY, E>(buf + c * PN, t, true, tw, 1);
-  C* dst = fhat + (size_t)f * N * ncol + c0;
-  const T sc = (T)fa.scale;
-  for (int idx = threadIdx.x; idx < N * CB; idx += blockDim.x) {
-    const int y = idx / CB, cc = idx - y * CB;
-    if (c0 + cc < ncol) {
-      const C v = buf[cc * PN + pad<T>(y)];
-      dst[(size_t)y * ncol + cc] = C{v.x * sc, v.y * sc};
-    }
-  }
+  const int c = threadIdx.x % CB, t = threadIdx.x / CB;
+  const int kx = blockIdx.x * CB + c, f = blockIdx.y;
+  // kx < pitch always (pitch = nx/2+1 rounded up to 8, CB divides 8): reads stay in the
+  // intermediate row; columns beyond nx/2 are computed and not stored
+  const C* src = inter + (size_t)f * N * fa.pitch + kx;
+  C* col = buf + c * PN;
+  stage_first_global<T, LOGNY, E, R1>(src, fa.pitch, col, t);
+  const C* tw = reinterpret_cast<const C*>(fa.tsy);
+  fft_rest_to_global<T, LOGNY, E, R1>(col, t, tw, fhat + (size_t)f * N * ncol + kx, ncol,
+                                      (T)fa.scale, kx < ncol);
 }
 
 template <typename T, typename TV, int L>

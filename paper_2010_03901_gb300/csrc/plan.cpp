@@ -324,6 +324,27 @@ static bool fft_axis(int n, FftAxis& ax) {
   return true;
 }
 
+// Twiddles of each Stockham stage after the first, for a power-of-two length N and
+// radices min(E, N/Ns): block s holds w^(r k N/(Ns R)), r < R, k < Ns, stored [r][k], so
+// that the lanes of a warp (consecutive k) read consecutive entries.
+static std::vector<double> stage_twiddles(const FftAxis& ax, int E) {
+  std::vector<double> out;
+  const int N = ax.n;
+  if (N <= 0 || (N & (N - 1))) return out;
+  for (int ns = 1; ns < N;) {
+    const int R = (N / ns >= E) ? E : N / ns;
+    if (ns > 1)
+      for (int r = 0; r < R; ++r)
+        for (int k = 0; k < ns; ++k) {
+          const long long t = ((long long)r * k * (N / (ns * R))) % N;
+          out.push_back(ax.tw_host[2 * t]);
+          out.push_back(ax.tw_host[2 * t + 1]);
+        }
+    ns *= R;
+  }
+  return out;
+}
+
 // ------------------------------------------------------------------------- //
 // Lagrange weights
 // ------------------------------------------------------------------------- //
@@ -681,6 +702,9 @@ extern "C" fc2d_status fc2d_plan(const fc2d_boundary* boundary, const fc2d_grid*
   std::vector<float> tw32x(p->fx.tw_host.begin(), p->fx.tw_host.end());
   std::vector<float> tw32y(p->fy.tw_host.begin(), p->fy.tw_host.end());
   std::vector<float> rtw32(p->rtw_host.begin(), p->rtw_host.end());
+  std::vector<double> tsx64 = stage_twiddles(p->fx, 8), tsy64 = stage_twiddles(p->fy, 8);
+  std::vector<double> tsx16 = stage_twiddles(p->fx, 16), tsy16 = stage_twiddles(p->fy, 16);
+  std::vector<float> tsx32(tsx16.begin(), tsx16.end()), tsy32(tsy16.begin(), tsy16.end());
   std::vector<int> zero_status(1, 0);
   if ((st = upload(&p->dev.Q, p->Q)) || (st = upload(&p->dev.Ar, p->Ar)) ||
       (st = upload(&p->dev.Ar_hi, arh)) || (st = upload(&p->dev.Ar_lo, arl)) ||
@@ -694,7 +718,9 @@ extern "C" fc2d_status fc2d_plan(const fc2d_boundary* boundary, const fc2d_grid*
       (st = upload(&p->dev.status, zero_status)) ||
       (st = upload(&p->fx.tw64, p->fx.tw_host)) || (st = upload(&p->fx.tw32, tw32x)) ||
       (st = upload(&p->fy.tw64, p->fy.tw_host)) || (st = upload(&p->fy.tw32, tw32y)) ||
-      (st = upload(&p->rtw64, p->rtw_host)) || (st = upload(&p->rtw32, rtw32)))
+      (st = upload(&p->rtw64, p->rtw_host)) || (st = upload(&p->rtw32, rtw32)) ||
+      (st = upload(&p->fx.tws64, tsx64)) || (st = upload(&p->fy.tws64, tsy64)) ||
+      (st = upload(&p->fx.tws32, tsx32)) || (st = upload(&p->fy.tws32, tsy32)))
     return fail(st);
   // interpolation weights (Section 3.4), computed once in FP64 on the GPU
   {
@@ -760,7 +786,8 @@ extern "C" void fc2d_destroy(fc2d_plan_t p) {
                   p->dev.wn, p->dev.s_lin, p->dev.s_theta, p->dev.s_eta, p->dev.s_w,
                   p->dev.s_pb, p->dev.s_sb, p->dev.row_iv_off,
                   p->dev.row_iv, p->dev.row_strip_off, p->dev.status, p->fx.tw64, p->fx.tw32,
-                  p->fy.tw64, p->fy.tw32, p->rtw64, p->rtw32, p->ws.base};
+                  p->fy.tw64, p->fy.tw32, p->rtw64, p->rtw32, p->ws.base,
+                  p->fx.tws64, p->fx.tws32, p->fy.tws64, p->fy.tws32};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   for (auto& r : p->prof) {

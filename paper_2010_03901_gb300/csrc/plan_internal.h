@@ -22,6 +22,10 @@ struct FftAxis {
   std::vector<double> tw_host;   // interleaved re, im (2N doubles)
   double* tw64 = nullptr;        // device, 2N doubles
   float* tw32 = nullptr;         // device, 2N floats
+  // power-of-two lengths: per-stage twiddles [stage][r][k] for the radix-8 (double) and
+  // radix-16 (float) Stockham sequences (see stage_twiddles in plan.cpp)
+  double* tws64 = nullptr;
+  float* tws32 = nullptr;
 };
 
 struct Curve {

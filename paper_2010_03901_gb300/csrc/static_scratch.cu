@@ -82,6 +82,8 @@ extern "C" fc2d_status fc2d_coeffs_static(fc2d_plan_t p, int n_f, const void* ex
   fa.twx = f64 ? (const void*)p->fx.tw64 : (const void*)p->fx.tw32;
   fa.twy = f64 ? (const void*)p->fy.tw64 : (const void*)p->fy.tw32;
   fa.rtw = f64 ? (const void*)p->rtw64 : (const void*)p->rtw32;
+  fa.tsx = f64 ? (const void*)p->fx.tws64 : (const void*)p->fx.tws32;
+  fa.tsy = f64 ? (const void*)p->fy.tws64 : (const void*)p->fy.tws32;
   fa.scale = 1.0 / ((double)p->grid.nx * p->grid.ny);
   RowArgs ra{};
   ra.nx = p->grid.nx;
