@@ -23,6 +23,7 @@
 // again, frees its TMEM and returns.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
 
 #include "fc2d_kernels.cuh"
@@ -34,6 +35,7 @@ constexpr int kTileN = 128;           // normals per CTA (MMA M)
 constexpr int kMaxCrPad = 256;        // MMA N limit
 constexpr int kTmemCols = 256;        // power of two >= N
 constexpr uint32_t kSpinLimit = 1u << 22;
+constexpr int kStageBytes = kTileN * (kMaxCrPad + 1) * 4;  // fused kernel's output staging
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -77,8 +79,9 @@ struct TcArgs {
   const double* bvals;  // [n_cols] boundary datum
   const float* Ar_hi;   // [Cr][d]
   const float* Ar_lo;
-  float* F;             // [n_cols][ldF]
+  float* F;             // [n_cols][ldF], or [Cr+1][n_cols] when q_major
   int* status;
+  int q_major;          // 1: F[q * n_cols + n] (coalesced epilogue stores)
 };
 
 __global__ void __launch_bounds__(128, 1) k_blend_tc(TcArgs a) {
@@ -248,10 +251,13 @@ __global__ void __launch_bounds__(256, 1) k_gather_blend_tc(GatherArgs g, TcArgs
   unsigned char* c_lo = smem + 4096;
   unsigned char* a_hi = smem + 8192;
   unsigned char* a_lo = a_hi + kMaxCrPad * 32;
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(a_lo + kMaxCrPad * 32);
+  // after the MMAs the operand tiles are dead: the output tile is staged over them
+  float* stage = reinterpret_cast<float*>(smem);            // [128][Cr+1]
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + kStageBytes);
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mbar + 1);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int n0 = blockIdx.x * kTileN;
+  const int ldS = a.Cr + 1;
 
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
@@ -273,6 +279,7 @@ __global__ void __launch_bounds__(256, 1) k_gather_blend_tc(GatherArgs g, TcArgs
     *reinterpret_cast<float*>(a_lo + kmaj_off(q, k)) = lo;
   }
   // matching values and Gram coefficients (Section 3.2, eq. (2.6)) into the C tiles
+  float bd_row[kTileN / 32];
   {
     const int s = lane & 7, g0 = lane & ~7;
     const int M = g.M, d = g.d, NS = M - 1;
@@ -314,7 +321,8 @@ __global__ void __launch_bounds__(256, 1) k_gather_blend_tc(GatherArgs g, TcArgs
       const float hi = to_tf32((float)v);
       *reinterpret_cast<float*>(c_hi + kmaj_off(ln, s)) = hi;
       *reinterpret_cast<float*>(c_lo + kmaj_off(ln, s)) = (float)(v - (double)hi);
-      if (live && s == 0) a.F[(size_t)n * a.ldF] = (float)fbp;
+      // boundary datum of row ln, kept in a register until the staging area is free
+      if (s == 0) bd_row[pass] = (float)fbp;
     }
   }
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -363,11 +371,11 @@ __global__ void __launch_bounds__(256, 1) k_gather_blend_tc(GatherArgs g, TcArgs
   done = __all_sync(0xffffffffu, done != 0) ? 1u : 0u;
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   if (done) {
+    // TMEM -> staging [local normal][q] (rows of the tile), then one contiguous store
     const int quarter = warp & 3;
     const int half = ((a.ncr_pad / 2) + 7) / 8 * 8;
     const int cbeg = warp < 4 ? 0 : half, cend = warp < 4 ? half : a.ncr_pad;
-    const int n = n0 + quarter * 32 + lane;
-    float* Frow = a.F + (size_t)n * a.ldF;
+    const int ln = quarter * 32 + lane;
     for (int c0 = cbeg; c0 < cend; c0 += 8) {
       uint32_t r[8];
       const uint32_t addr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)c0;
@@ -377,14 +385,24 @@ __global__ void __launch_bounds__(256, 1) k_gather_blend_tc(GatherArgs g, TcArgs
             "=r"(r[6]), "=r"(r[7])
           : "r"(addr));
       asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-      if (n < a.n_cols) {
 #pragma unroll
-        for (int e = 0; e < 8; ++e) {
-          const int q = c0 + e;
-          if (q < a.Cr) Frow[1 + q] = __uint_as_float(r[e]);
-        }
+      for (int e = 0; e < 8; ++e) {
+        const int q = c0 + e;
+        if (q < a.Cr) stage[ln * ldS + 1 + q] = __uint_as_float(r[e]);
       }
     }
+  }
+  // boundary data: group lane s == 0 of (warp, group) served rows pass*32 + warp*4 + group
+  if ((lane & 7) == 0) {
+#pragma unroll
+    for (int pass = 0; pass < kTileN / 32; ++pass)
+      stage[(pass * 32 + warp * 4 + (lane >> 3)) * ldS] = bd_row[pass];
+  }
+  __syncthreads();
+  if (done) {
+    const int rows = min(kTileN, a.n_cols - n0);
+    float* dst = a.F + (size_t)n0 * a.ldF;  // rows n0.. are contiguous (ldF = Cr + 1)
+    for (int idx = tid; idx < rows * ldS; idx += blockDim.x) dst[idx] = stage[idx];
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
@@ -395,8 +413,9 @@ __global__ void __launch_bounds__(256, 1) k_gather_blend_tc(GatherArgs g, TcArgs
 }
 
 fc2d_status launch_gather_blend_tc(const GatherArgs& g, int n_f, int ldF, const float* Ar_hi,
-                                   const float* Ar_lo, float* F, int* status, cudaStream_t s) {
-  if (g.Cr > kMaxCrPad || g.d > 8 || g.M - 1 > 8)
+                                   const float* Ar_lo, float* F, int* status, cudaStream_t s,
+                                   bool q_major) {
+  if (g.Cr > kMaxCrPad || g.d > 8 || g.M - 1 > 8 || q_major)
     return set_error(FC2D_ERR_UNSUPPORTED, "fused tensor-core blend: C n_r <= 256, d <= 8, M <= 9");
   TcArgs a{};
   a.n_cols = n_f * g.B;
@@ -408,7 +427,9 @@ fc2d_status launch_gather_blend_tc(const GatherArgs& g, int n_f, int ldF, const 
   a.Ar_lo = Ar_lo;
   a.F = F;
   a.status = status;
-  size_t sm = 96 * 1024;  // caps residency at two CTAs per SM (256 TMEM columns each)
+  a.q_major = q_major ? 1 : 0;
+  // staging + barrier; at most two CTAs per SM (256 TMEM columns each)
+  size_t sm = std::max<size_t>(96 * 1024, kStageBytes + 64);
   cudaFuncSetAttribute(k_gather_blend_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   k_gather_blend_tc<<<(a.n_cols + kTileN - 1) / kTileN, 256, sm, s>>>(g, a);
   return cuda_check(cudaGetLastError(), "fused tensor-core blend launch");

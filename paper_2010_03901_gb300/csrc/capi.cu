@@ -139,12 +139,12 @@ fc2d_status launched(const char* what) { return cuda_check(cudaGetLastError(), w
 // Mixed form of step 5: matching values and Gram coefficients in FP64, then the
 // contraction with A_r on the tensor cores into float strip values F.
 fc2d_status mixed_blend(fc2d_plan_s* p, int n_f, const double* fg, const double* fb, void* F,
-                        const Layout& L, cudaStream_t s) {
+                        const Layout& L, cudaStream_t s, bool q_major) {
   if (p->prm.M - 1 <= 8 && p->prm.d <= 8) {
     ProfScope ps(p, "gather_blend_tc", s);
     return launch_gather_blend_tc(gather_args(p, fg, fb, nullptr, nullptr, nullptr), n_f,
                                   p->Cr + 1, p->dev.Ar_hi, p->dev.Ar_lo, static_cast<float*>(F),
-                                  p->dev.status, s);
+                                  p->dev.status, s, q_major);
   }
   double* coef = reinterpret_cast<double*>(ws(p, L.ocoef));
   double* bvals = reinterpret_cast<double*>(ws(p, L.obvals));
@@ -166,7 +166,7 @@ fc2d_status strip_values(fc2d_plan_s* p, int n_f, const double* fg, const double
     ProfScope ps(p, "gather_blend", s);
     launch_gather_blend(gather_args(p, fg, fb, F, nullptr, nullptr), n_f, true, s);
   } else {
-    fc2d_status st = mixed_blend(p, n_f, fg, fb, F, L, s);
+    fc2d_status st = mixed_blend(p, n_f, fg, fb, F, L, s, false);
     if (st) return st;
   }
   {
@@ -191,7 +191,7 @@ extern "C" fc2d_status fc2d_blend(fc2d_plan_t p, int n_f, const double* fg, cons
   }
   Layout L = layout(p, n_f);
   if ((st = ensure_workspace(p, L.total))) return st;
-  if ((st = mixed_blend(p, n_f, fg, fb, F, L, s))) return st;
+  if ((st = mixed_blend(p, n_f, fg, fb, F, L, s, false))) return st;
   return launched("fc2d_blend");
 }
 

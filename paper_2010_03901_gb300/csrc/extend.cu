@@ -298,18 +298,20 @@ __global__ void __launch_bounds__(256) k_interp(InterpArgs a, const TF* __restri
 #pragma unroll
   for (int b = 0; b < (MM > 0 ? MM : kMaxM); ++b)
     if (b < M) weta[b] = __ldg(w + (size_t)(M + b) * ns + n);
-  const TF* Ff = F + (size_t)f * B * ld;
+  // F[f][p][q] at Ff + p * pst + q * qst
+  const size_t pst = a.q_major ? 1 : (size_t)ld, qst = a.q_major ? (size_t)a.n_cols : 1;
+  const TF* Ff = F + (a.q_major ? (size_t)f * B : (size_t)f * B * ld);
   TA acc = 0;
 #pragma unroll
   for (int ai = 0; ai < (MM > 0 ? MM : kMaxM); ++ai) {
     if (ai >= M) break;
     int pr = pb + ai;
     pr = pr < 0 ? pr + B : (pr >= B ? pr - B : pr);
-    const TF* row = Ff + (size_t)pr * ld + s;
+    const TF* row = Ff + (size_t)pr * pst + (size_t)s * qst;
     TA v = 0;
 #pragma unroll
     for (int b = 0; b < (MM > 0 ? MM : kMaxM); ++b)
-      if (b < M) v = fma((TA)weta[b], (TA)__ldg(row + b), v);
+      if (b < M) v = fma((TA)weta[b], (TA)__ldg(row + (size_t)b * qst), v);
     acc = fma((TA)__ldg(w + (size_t)ai * ns + n), v, acc);
   }
   vals[(size_t)f * ns + n] = (TV)acc;

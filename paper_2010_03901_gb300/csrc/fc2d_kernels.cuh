@@ -28,6 +28,8 @@ struct GatherArgs {
 
 struct InterpArgs {
   int n_strip, M, B, Cr;
+  int q_major;           // F layout [Cr+1][n_f*B] instead of [n_f][B][Cr+1]
+  int n_cols;            // n_f * B (q-major row length)
   const void* w;         // [2M][n_strip] theta then eta weights (double or float)
   const int32_t* pb;     // first normal index (mod B)
   const int32_t* sb;     // first fine index along the normal
@@ -76,9 +78,10 @@ fc2d_status launch_blend_tc(int n_cols, int Cr, int d, int ldF, const double* co
                             int coef_ld, const double* bvals, const float* Ar_hi,
                             const float* Ar_lo, float* F, int* status, cudaStream_t s);
 // fused mixed form: matching values + Gram coefficients + tensor-core contraction in one
-// kernel (M <= 9, d <= 8); F [n_f*B][ldF] float.
+// kernel (M <= 9, d <= 8); F [n_f*B][ldF] float, or [Cr+1][n_f*B] when q_major.
 fc2d_status launch_gather_blend_tc(const GatherArgs& g, int n_f, int ldF, const float* Ar_hi,
-                                   const float* Ar_lo, float* F, int* status, cudaStream_t s);
+                                   const float* Ar_lo, float* F, int* status, cudaStream_t s,
+                                   bool q_major);
 void launch_interp(const InterpArgs& a, int n_f, bool fp64, const void* F, void* vals,
                    cudaStream_t s);
 void launch_assemble(const RowArgs& a, int n_f, bool fp64, const double* f_grid,

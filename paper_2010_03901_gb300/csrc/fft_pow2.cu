@@ -361,7 +361,7 @@ k_fft_rows_p2(FftArgs fa, RowArgs ra, int mode, const T* __restrict__ ext,
 // (c = tid % CB, t = tid / CB): the CB columns of a row are read by neighbouring
 // threads.  First stage from the intermediate, last stage to the spectrum.
 template <typename T, int LOGNY, int CB>
-__global__ void __launch_bounds__(CB * ((1 << LOGNY) / elems<T>()))
+__global__ void __launch_bounds__(CB * ((1 << LOGNY) / elems<T>()), (CB * ((1 << LOGNY) / elems<T>()) <= 512 ? 2 : 1))
 k_fft_cols_p2(FftArgs fa, const typename Cx<T>::type* __restrict__ inter,
               typename Cx<T>::type* __restrict__ fhat) {
   using C = typename Cx<T>::type;
