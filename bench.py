@@ -3,7 +3,10 @@
 domain x = cos t + 0.65 cos 2t - 0.65, y = 1.5 sin t at 4096^2 with 8192 normals.
 
 One step = the whole hot path for one function: matching values, blending, strip
-interpolation, fused extension + row DFT, column DFT (fc2d_extend_coeffs).
+interpolation, fused extension + row DFT, column DFT (fc2d_extend_coeffs).  The headline
+is the mixed-precision form; the FP64 form is timed beside it, and both spectra are
+compared with the FP64 oracle's.  The Poisson solve on the star workload at 1024^2 is
+reported as a second line item.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp64|mixed]
     python bench.py --impl reference ...     # the FP64 CPU oracle as the reference arm
@@ -210,33 +213,16 @@ def algorithmic(plan, w, fp64):
     }
 
 
-def run_gpu(args):
-    import torch
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    if world > 1:
-        import torch.distributed as dist
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl")
-    dev = torch.device("cuda", torch.cuda.current_device())
-
-    from paper_2010_03901_gb300.build import build
-    build()
-    from paper_2010_03901_gb300 import fc2d
-
-    fp64 = args.precision == "fp64"
-    w = W.workload(WORKLOAD)
+def measure(fc2d, torch, w, precision, K, warmup, world, dev, fg_h, fb_h, sample_clocks):
+    """Time K steps of fc2d_extend_coeffs (one function) in one precision; per-kernel
+    CUDA-event profile over the same timed region; e2e with host buffers."""
     g, p = w.grid, w.params
+    fp64 = precision == "fp64"
     t0 = time.perf_counter()
     plan = fc2d.fc2d_plan(w.boundary.arrays(), (g.a0, g.b0, g.h, g.nx, g.ny),
                           dict(B=p.B, k1=p.k1),
                           precision=fc2d.FC2D_FP64 if fp64 else fc2d.FC2D_MIXED)
     plan_s = time.perf_counter() - t0
-    f = bench_functions(w, 1)[0]
-    xy = plan.fc2d_boundary_points()
-    fg_h = torch.from_numpy(W.grid_values(w, f)).pin_memory()
-    fb_h = torch.from_numpy(np.ascontiguousarray(f(xy[:, 0], xy[:, 1]))).pin_memory()
     fg = fg_h.to(dev)
     fb = fb_h.to(dev)
     cdt = torch.float64 if fp64 else torch.float32
@@ -246,22 +232,20 @@ def run_gpu(args):
     flush = torch.ones(64 * 1024 * 1024, dtype=torch.float32, device=dev)
     flush_out = torch.empty(1, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
-
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         plan.fc2d_extend_coeffs(1, fg, fb, fhat, stream)
     plan.fc2d_sync_status(stream)
-
-    K = args.steps
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
-    sampler = ClockSampler(dev.index)
+    sampler = ClockSampler(dev.index) if sample_clocks else None
     plan.fc2d_profile(True)
     plan.fc2d_profile_read()
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
-    sampler.start()
-    time.sleep(0.3)
+    if sampler:
+        sampler.start()
+        time.sleep(0.3)
     wall0 = time.perf_counter()
     for k in range(K):
         torch.sum(flush, dim=0, out=flush_out[0])
@@ -272,19 +256,17 @@ def run_gpu(args):
     wall = time.perf_counter() - wall0
     if world > 1:
         torch.distributed.barrier()
-    clocks = sampler.stop()
+    clocks = sampler.stop() if sampler else None
     plan.fc2d_profile(False)
     prof = plan.fc2d_profile_read()
     plan.fc2d_sync_status(stream)
     ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
-    t_max = ms
     if world > 1:
         tt = torch.tensor([ms], device=dev, dtype=torch.float64)
         torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        t_max = float(tt.item())
+        ms = float(tt.item())
     npts = g.nx * g.ny
-    value = world * K * npts / (t_max / 1e3)
-
+    value = world * K * npts / (ms / 1e3)
     # end to end through the public API with host buffers
     Ke = min(K, 30)
     fhat_h = torch.empty(fhat.shape, dtype=cdt).pin_memory()
@@ -302,12 +284,10 @@ def run_gpu(args):
     e1.record(stream)
     torch.cuda.synchronize()
     e2e_ms = e0.elapsed_time(e1) / Ke
-    e2e_val = world * npts / (e2e_ms / 1e3)
     if world > 1:
         tt = torch.tensor([e2e_ms], device=dev, dtype=torch.float64)
         torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        e2e_val = world * npts / (float(tt.item()) / 1e3)
-
+        e2e_ms = float(tt.item())
     # roofline of the dominant kernel
     hbm, src = peaks()
     alg = algorithmic(plan, w, fp64)
@@ -328,29 +308,110 @@ def run_gpu(args):
     roof["traffic"] = None
     kernels = {k: {"launches": v[0], "avg_us": 1e3 * v[1] / v[0],
                    "share": v[1] / sum(x[1] for x in prof.values())} for k, v in prof.items()}
+    return {"value": value, "ms_per_step": ms / K, "steps": K, "plan_s": plan_s,
+            "wall_s_timed": wall, "clocks": clocks, "roofline": roof, "kernels": kernels,
+            "gpu_launches": sum(v[0] for v in prof.values()),
+            "e2e": {"value": world * npts / (e2e_ms / 1e3), "unit": UNIT,
+                    "h2d_bytes_per_step": int(fg.numel() * 8 + fb.numel() * 8),
+                    "d2h_bytes_per_step": int(fhat.numel() * fhat.element_size())},
+            "fhat": fhat}
 
-    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
-            "warmup": args.warmup, "ms_per_step": t_max / K, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if fp64 else "f32+tf32",
+
+def poisson_star1024(fc2d, torch, dev, solves=3):
+    """The star r = 1 + 0.3 cos 5 theta at 1024^2: Poisson with u = sin(2x) e^y (FP64)."""
+    w = W.workload("star1024")
+    g, p = w.grid, w.params
+    plan = fc2d.fc2d_plan(w.boundary.arrays(), (g.a0, g.b0, g.h, g.nx, g.ny),
+                          dict(B=p.B, k1=p.k1))
+    plan.fc2d_poisson_plan(0)
+    xy = plan.fc2d_poisson_nodes()
+    bxy = plan.fc2d_boundary_points()
+    f, u = W.lap_u_manufactured, W.u_manufactured
+    fg = torch.tensor(W.grid_values(w, f)[None], device=dev)
+    fb = torch.tensor(f(bxy[:, 0], bxy[:, 1])[None], device=dev)
+    gn = torch.tensor(u(xy[:, 0], xy[:, 1])[None], device=dev)
+    out = torch.zeros_like(fg)
+    plan.fc2d_poisson(1, fg, fb, gn, out)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(solves):
+        plan.fc2d_poisson(1, fg, fb, gn, out)
+    torch.cuda.synchronize()
+    dt = (time.perf_counter() - t0) / solves
+    X, Y = np.meshgrid(*w.grid.coords())
+    ue = u(X, Y)
+    got = out.cpu().numpy()[0]
+    inside = got != 0
+    err = float(np.abs(got - ue)[inside].max() / np.abs(ue[inside]).max())
+    return {"workload": "star1024 Poisson, u = sin(2x) e^y", "ms_per_solve": 1e3 * dt,
+            "value": g.nx * g.ny / dt, "unit": UNIT, "max_rel_err_vs_exact": err,
+            "gmres": plan.fc2d_poisson_info()}
+
+
+def run_gpu(args):
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", torch.cuda.current_device())
+
+    from paper_2010_03901_gb300.build import build
+    build()
+    from paper_2010_03901_gb300 import fc2d
+
+    w = W.workload(WORKLOAD)
+    g, p = w.grid, w.params
+    f = bench_functions(w, 1)[0]
+    probe = fc2d.fc2d_plan(w.boundary.arrays(), (g.a0, g.b0, g.h, g.nx, g.ny),
+                           dict(B=p.B, k1=p.k1))
+    xy = probe.fc2d_boundary_points()
+    probe.fc2d_destroy()
+    fg_h = torch.from_numpy(W.grid_values(w, f)).pin_memory()
+    fb_h = torch.from_numpy(np.ascontiguousarray(f(xy[:, 0], xy[:, 1]))).pin_memory()
+
+    head = "fp64" if args.precision == "fp64" else "mixed"
+    res = {head: measure(fc2d, torch, w, head, args.steps, args.warmup, world, dev, fg_h, fb_h,
+                         True)}
+    if args.precision == "both":
+        k64 = max(3, args.steps // 8)
+        res["fp64"] = measure(fc2d, torch, w, "fp64", k64, args.warmup, world, dev, fg_h, fb_h,
+                              False)
+    r = res[head]
+    line = {"metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["ms_per_step"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if head == "fp64" else "f32+tf32 (f64 matching values, weights)",
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "grid": f"{g.nx}x{g.ny}", "normals": p.B,
                        "domain": "kite a=0.65 b=1.5", "functions_per_step": 1,
-                       "function": "sum of 16 Gaussians (seed 3)", "precision": args.precision,
+                       "function": "sum of 16 Gaussians (seed 3)", "precision": head,
                        "d": p.d, "C": p.C, "M": p.M, "n_r": p.n_r,
                        "l2": "flushed between steps (256 MB read, outside the events)",
                        "parallelism": f"replicas x{world}"},
-            "clocks": clocks, "roofline": roof, "kernels": kernels,
-            "gpu_launches": sum(v[0] for v in prof.values()),
-            "e2e": {"value": e2e_val, "unit": UNIT,
-                    "h2d_bytes_per_step": int(fg.numel() * 8 + fb.numel() * 8),
-                    "d2h_bytes_per_step": int(fhat.numel() * fhat.element_size())},
-            "plan_s": plan_s, "wall_s_timed": wall}
+            "clocks": r["clocks"], "roofline": r["roofline"], "kernels": r["kernels"],
+            "gpu_launches": r["gpu_launches"], "e2e": r["e2e"], "plan_s": r["plan_s"],
+            "wall_s_timed": r["wall_s_timed"]}
+    if "fp64" in res and head != "fp64":
+        q = res["fp64"]
+        line["fp64"] = {k: q[k] for k in ("value", "ms_per_step", "steps", "roofline",
+                                          "kernels", "e2e")}
     if rank == 0 and world == 1 and not args.no_cpu:
         base, spec_ref = cpu_baseline(w)
         line["cpu_baseline"] = base
-        got = fhat.cpu().numpy().astype(np.float64)
-        got = got[..., 0] + 1j * got[..., 1]
-        line["err_vs_oracle"] = float(np.abs(got - spec_ref).max() / np.abs(spec_ref).max())
+        for name, q in res.items():
+            got = q["fhat"].cpu().numpy().astype(np.float64)
+            got = got[..., 0] + 1j * got[..., 1]
+            err = float(np.abs(got - spec_ref).max() / np.abs(spec_ref).max())
+            if name == head:
+                line["err_vs_oracle"] = err
+            else:
+                line[name]["err_vs_oracle"] = err
+    if rank == 0 and world == 1 and not args.no_extra:
+        line["poisson_star1024"] = poisson_star1024(fc2d, torch, dev)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -363,8 +424,10 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=400)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="fc2d", choices=["fc2d", "reference"])
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--precision", default="both", choices=["both", "fp64", "mixed"],
+                    help="both: mixed is the headline, FP64 reported beside it")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-extra", action="store_true", help="skip the Poisson line")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
