@@ -213,6 +213,24 @@ def algorithmic(plan, w, fp64):
     }
 
 
+def max_over_ranks(x, world, dev):
+    """The largest value of x over all ranks (the slowest replica's time).  Works on any
+    process-group backend: NCCL with a CUDA device, gloo with the CPU."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], device=dev, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(world, steps, points_per_step, ms):
+    """Whole-job points/s: every rank processes `steps` grids of `points_per_step` points
+    (replicas, weak scaling), divided by the slowest rank's time `ms`."""
+    return world * steps * points_per_step / (ms / 1e3)
+
+
 def measure(fc2d, torch, w, precision, K, warmup, world, dev, fg_h, fb_h, sample_clocks):
     """Time K steps of fc2d_extend_coeffs (one function) in one precision; per-kernel
     CUDA-event profile over the same timed region; e2e with host buffers."""
@@ -260,13 +278,9 @@ def measure(fc2d, torch, w, precision, K, warmup, world, dev, fg_h, fb_h, sample
     plan.fc2d_profile(False)
     prof = plan.fc2d_profile_read()
     plan.fc2d_sync_status(stream)
-    ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
-    if world > 1:
-        tt = torch.tensor([ms], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        ms = float(tt.item())
+    ms = max_over_ranks(sum(s.elapsed_time(e) for s, e in zip(starts, ends)), world, dev)
     npts = g.nx * g.ny
-    value = world * K * npts / (ms / 1e3)
+    value = replica_throughput(world, K, npts, ms)
     # end to end through the public API with host buffers
     Ke = min(K, 30)
     fhat_h = torch.empty(fhat.shape, dtype=cdt).pin_memory()
@@ -283,11 +297,7 @@ def measure(fc2d, torch, w, precision, K, warmup, world, dev, fg_h, fb_h, sample
         fhat_h.copy_(fhat, non_blocking=True)
     e1.record(stream)
     torch.cuda.synchronize()
-    e2e_ms = e0.elapsed_time(e1) / Ke
-    if world > 1:
-        tt = torch.tensor([e2e_ms], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        e2e_ms = float(tt.item())
+    e2e_ms = max_over_ranks(e0.elapsed_time(e1) / Ke, world, dev)
     # roofline of the dominant kernel
     hbm, src = peaks()
     alg = algorithmic(plan, w, fp64)
@@ -311,7 +321,7 @@ def measure(fc2d, torch, w, precision, K, warmup, world, dev, fg_h, fb_h, sample
     return {"value": value, "ms_per_step": ms / K, "steps": K, "plan_s": plan_s,
             "wall_s_timed": wall, "clocks": clocks, "roofline": roof, "kernels": kernels,
             "gpu_launches": sum(v[0] for v in prof.values()),
-            "e2e": {"value": world * npts / (e2e_ms / 1e3), "unit": UNIT,
+            "e2e": {"value": replica_throughput(world, 1, npts, e2e_ms), "unit": UNIT,
                     "h2d_bytes_per_step": int(fg.numel() * 8 + fb.numel() * 8),
                     "d2h_bytes_per_step": int(fhat.numel() * fhat.element_size())},
             "fhat": fhat}
