@@ -7,7 +7,7 @@
 //   twiddle by exp(-2 pi i r (j mod Ns)/(Ns R)) (table lookups), length-R DFT,
 //   write y[(j/Ns) Ns R + (j mod Ns) + r Ns], barrier,
 // so one buffer of N values suffices.  Shared indices are padded by one element per
-// 32 (float) or 16 (double) to break the bank conflicts of the strided writes.
+// E to break the bank conflicts of the strided first-stage writes.
 //
 // k_fft_rows_p2: one block per (row, function): the extension row (fused load from
 // f and the strip values, or a plain grid row) as nx/2 complex pairs, the length-nx/2
@@ -138,7 +138,10 @@ __device__ __forceinline__ float d2f_rn(double x) {
 template <typename T> __device__ __forceinline__ T from_double(double x) { return (T)x; }
 template <> __device__ __forceinline__ float from_double<float>(double x) { return d2f_rn(x); }
 
-template <typename T> __host__ __device__ constexpr int pad_shift() { return sizeof(T) == 4 ? 5 : 4; }
+// One pad element per E = elems<T>() elements: the first stage writes at stride E
+// (index E j + r), which the pad spreads over all banks; the other stages access
+// contiguous runs of the thread index, which the pad leaves contiguous.
+template <typename T> __host__ __device__ constexpr int pad_shift() { return sizeof(T) == 4 ? 4 : 3; }
 template <typename T> __device__ __forceinline__ int pad(int i) { return i + (i >> pad_shift<T>()); }
 template <typename T> __host__ __device__ constexpr int padded(int n) { return n + (n >> pad_shift<T>()); }
 
