@@ -39,6 +39,12 @@ METRIC = "2D-FC extend+FFT grid-points/sec at 4096^2"
 UNIT = "grid-points/s"
 FP64_PEAK_TFLOPS = 1.25   # GB300 FP64 (nominal; 152 SMs x 2 DFMA/clk x 2 flop x ~2.06 GHz)
 
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of a kernel scope
+# on this workload, from one ncu capture of the current kernels (cold cache, serialised
+# launches; a scope with two kernels sums both).  A kernel changed after its capture
+# has no entry, and the roofline then reports traffic null.
+MEASURED_TRAFFIC = {}
+
 
 def peaks():
     try:
@@ -281,22 +287,53 @@ def measure(fc2d, torch, w, precision, K, warmup, world, dev, fg_h, fb_h, sample
     ms = max_over_ranks(sum(s.elapsed_time(e) for s, e in zip(starts, ends)), world, dev)
     npts = g.nx * g.ny
     value = replica_throughput(world, K, npts, ms)
-    # end to end through the public API with host buffers
+    # end to end through the public API with host buffers: every step copies its
+    # inputs from pinned host memory, calls fc2d_extend_coeffs and reads its spectrum
+    # back to pinned host memory.  Steps are pipelined as a user streaming functions
+    # would: copies in on one stream, compute on another, copies out on a third, with
+    # two device buffers of each kind (the plan's workspace is used by one compute
+    # stream only).
     Ke = min(K, 30)
-    fhat_h = torch.empty(fhat.shape, dtype=cdt).pin_memory()
-    fg_d = torch.empty_like(fg)
-    fb_d = torch.empty_like(fb)
+    fhat_h = [torch.empty(fhat.shape, dtype=cdt).pin_memory() for _ in range(2)]
+    fg_d = [torch.empty_like(fg) for _ in range(2)]
+    fb_d = [torch.empty_like(fb) for _ in range(2)]
+    fh_d = [torch.empty_like(fhat) for _ in range(2)]
+    s_in, s_cmp, s_out = torch.cuda.Stream(dev), torch.cuda.Stream(dev), torch.cuda.Stream(dev)
+    ev = lambda: torch.cuda.Event()
+    in_done = [ev(), ev()]
+    cmp_done = [ev(), ev()]
+    out_done = [ev(), ev()]
+
+    def e2e_step(k):
+        b = k % 2
+        with torch.cuda.stream(s_in):
+            s_in.wait_event(cmp_done[b])          # compute k-2 has read these inputs
+            fg_d[b].copy_(fg_h, non_blocking=True)
+            fb_d[b].copy_(fb_h, non_blocking=True)
+            in_done[b].record(s_in)
+        s_cmp.wait_event(in_done[b])
+        s_cmp.wait_event(out_done[b])             # copy-out k-2 has read this spectrum
+        plan.fc2d_extend_coeffs(1, fg_d[b], fb_d[b], fh_d[b], s_cmp)
+        cmp_done[b].record(s_cmp)
+        with torch.cuda.stream(s_out):
+            s_out.wait_event(cmp_done[b])
+            fhat_h[b].copy_(fh_d[b], non_blocking=True)
+            out_done[b].record(s_out)
+
+    torch.cuda.synchronize()
+    for k in range(2):
+        e2e_step(k)
+    torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(s_in)
+    for k in range(Ke):
+        e2e_step(k)
+    for b in range(2):
+        s_out.wait_event(out_done[b])
+    e1.record(s_out)
     torch.cuda.synchronize()
-    e0.record(stream)
-    for _ in range(Ke):
-        fg_d.copy_(fg_h, non_blocking=True)
-        fb_d.copy_(fb_h, non_blocking=True)
-        plan.fc2d_extend_coeffs(1, fg_d, fb_d, fhat, stream)
-        fhat_h.copy_(fhat, non_blocking=True)
-    e1.record(stream)
-    torch.cuda.synchronize()
+    plan.fc2d_sync_status(s_cmp)
     e2e_ms = max_over_ranks(e0.elapsed_time(e1) / Ke, world, dev)
     # roofline of the dominant kernel
     hbm, src = peaks()
@@ -315,13 +352,14 @@ def measure(fc2d, torch, w, precision, K, warmup, world, dev, fg_h, fb_h, sample
                 "unit": "GB/s", "peak_source": src}
     roof["frac"] = roof["achieved"] / roof["peak"]
     roof["kernel"] = dom
-    roof["traffic"] = None
+    roof["traffic"] = MEASURED_TRAFFIC.get((precision, dom))
     kernels = {k: {"launches": v[0], "avg_us": 1e3 * v[1] / v[0],
                    "share": v[1] / sum(x[1] for x in prof.values())} for k, v in prof.items()}
     return {"value": value, "ms_per_step": ms / K, "steps": K, "plan_s": plan_s,
             "wall_s_timed": wall, "clocks": clocks, "roofline": roof, "kernels": kernels,
             "gpu_launches": sum(v[0] for v in prof.values()),
             "e2e": {"value": replica_throughput(world, 1, npts, e2e_ms), "unit": UNIT,
+                    "pipeline": "copy-in, compute, copy-out on three streams, two buffers",
                     "h2d_bytes_per_step": int(fg.numel() * 8 + fb.numel() * 8),
                     "d2h_bytes_per_step": int(fhat.numel() * fhat.element_size())},
             "fhat": fhat}

@@ -79,9 +79,8 @@ struct TcArgs {
   const double* bvals;  // [n_cols] boundary datum
   const float* Ar_hi;   // [Cr][d]
   const float* Ar_lo;
-  float* F;             // [n_cols][ldF], or [Cr+1][n_cols] when q_major
+  float* F;             // [n_cols][ldF]
   int* status;
-  int q_major;          // 1: F[q * n_cols + n] (coalesced epilogue stores)
 };
 
 __global__ void __launch_bounds__(128, 1) k_blend_tc(TcArgs a) {
@@ -200,7 +199,10 @@ __global__ void __launch_bounds__(128, 1) k_blend_tc(TcArgs a) {
         }
       }
     }
-    if (n < a.n_cols) Frow[0] = (float)a.bvals[n];
+    if (n < a.n_cols) {
+      Frow[0] = (float)a.bvals[n];
+      for (int q = a.Cr + 1; q < a.ldF; ++q) Frow[q] = 0.f;  // row padding
+    }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
@@ -239,91 +241,132 @@ fc2d_status launch_blend_tc(int n_cols, int Cr, int d, int ldF, const double* co
 
 
 // ------------------------------------------------------------------------- //
-// Fused form: the matching values and Gram coefficients of the CTA's 128 normals are
-// computed by its 8 warps (4 normals per warp and pass, groups of 8 lanes, as in
-// k_gather_blend) straight into the MMA operand tiles; then the three MMAs and the
-// epilogue, warps w and w+4 reading the two halves of the TMEM columns of lanes
-// 32(w%4)..32(w%4)+31.  Requires M - 1 <= 8 and d <= 8.
+// Fused form, one CTA per 32 normals.  The roles of the operands are swapped so
+// that a small group of normals fills an MMA: the fine points are the M side,
+//   D_t[q][n] = A_r[128 t + q][:] . C[n][:]   (M = 128 fine points per tile t,
+//                                             N = 32 normals, K = 8),
+// with ceil(Cr/128) tiles, three split MMAs each (A_hi C_hi, A_hi C_lo, A_lo C_hi).
+// The 8 warps first compute the matching values and Gram coefficients of the 32
+// normals (groups of 8 lanes, as in k_gather_blend) into the C tiles; the stencil
+// indices and weights are plan constants and are loaded before the dependent-launch
+// wait, the grid values after it.  Epilogue: warp w reads TMEM lanes 32(w%4).. of
+// tile w/4 (fine points) for the 32 normals (columns), writes them transposed into a
+// [32][Cr+1] staging tile (column 0 = the boundary datum) and the CTA stores the 32
+// contiguous rows of F.  Requires M - 1 <= 8, d <= 8, Cr <= 256.
 // ------------------------------------------------------------------------- //
-__global__ void __launch_bounds__(256, 1) k_gather_blend_tc(GatherArgs g, TcArgs a) {
+constexpr int kTcNormals = 32;      // normals per CTA (MMA N)
+constexpr int kTcQTile = 128;       // fine points per MMA (MMA M)
+constexpr int kTcTmemCols = 64;     // two tiles of 32 columns
+constexpr int kTcStageOff = 2 * kMaxCrPad * 32 + 2 * kTcNormals * 32;  // after A and C tiles
+constexpr int kTcMaxLd = kMaxCrPad + 16;  // staging row length limit (ldF)
+constexpr int kTcBarOff = kTcStageOff + kTcNormals * kTcMaxLd * 4;
+constexpr int kTcSmem = kTcBarOff + 16;
+
+template <int MM>
+__global__ void __launch_bounds__(256, 2) k_gather_blend_tc(GatherArgs g, TcArgs a) {
   extern __shared__ __align__(1024) unsigned char smem[];
-  unsigned char* c_hi = smem;
-  unsigned char* c_lo = smem + 4096;
-  unsigned char* a_hi = smem + 8192;
-  unsigned char* a_lo = a_hi + kMaxCrPad * 32;
-  // after the MMAs the operand tiles are dead: the output tile is staged over them
-  float* stage = reinterpret_cast<float*>(smem);            // [128][Cr+1]
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + kStageBytes);
+  unsigned char* a_hi = smem;                                 // [256 q][8 k] K-major
+  unsigned char* a_lo = smem + kMaxCrPad * 32;
+  unsigned char* c_hi = smem + 2 * kMaxCrPad * 32;            // [32 n][8 k] K-major
+  unsigned char* c_lo = c_hi + kTcNormals * 32;
+  float* stage = reinterpret_cast<float*>(smem + kTcStageOff);  // [32][ldF]
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + kTcBarOff);
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mbar + 1);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int n0 = blockIdx.x * kTileN;
-  const int ldS = a.Cr + 1;
+  const int n0 = blockIdx.x * kTcNormals;
+  const int ldS = a.ldF;  // staging rows as in F: Cr + 1 values, then zeros
+  const int nqt = (a.Cr + kTcQTile - 1) / kTcQTile;
+  for (int idx = tid; idx < kTcNormals * (ldS - a.Cr - 1); idx += blockDim.x) {
+    const int r = idx / (ldS - a.Cr - 1);
+    stage[r * ldS + a.Cr + 1 + (idx - r * (ldS - a.Cr - 1))] = 0.f;
+  }
 
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
-                 ::"r"(smem_u32(tmem_slot)), "r"(kTmemCols));
+                 ::"r"(smem_u32(tmem_slot)), "r"(kTcTmemCols));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   if (tid == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(mbar)));
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  for (int idx = tid; idx < a.ncr_pad * 8; idx += blockDim.x) {
-    const int q = idx >> 3, k = idx & 7;
-    float hi = 0.f, lo = 0.f;
-    if (q < a.Cr && k < a.d) {
-      hi = a.Ar_hi[q * a.d + k];
-      lo = a.Ar_lo[q * a.d + k];
+  // A_r tiles (plan constants): all loads of a thread in flight, then the stores
+  {
+    constexpr int kPer = kMaxCrPad * 8 / 256;
+    float hi[kPer], lo[kPer];
+#pragma unroll
+    for (int u = 0; u < kPer; ++u) {
+      const int idx = tid + u * 256, q = idx >> 3, k = idx & 7;
+      const bool on = q < a.Cr && k < a.d;
+      hi[u] = on ? __ldg(a.Ar_hi + q * a.d + k) : 0.f;
+      lo[u] = on ? __ldg(a.Ar_lo + q * a.d + k) : 0.f;
     }
-    *reinterpret_cast<float*>(a_hi + kmaj_off(q, k)) = hi;
-    *reinterpret_cast<float*>(a_lo + kmaj_off(q, k)) = lo;
+#pragma unroll
+    for (int u = 0; u < kPer; ++u) {
+      const int idx = tid + u * 256, q = idx >> 3, k = idx & 7;
+      *reinterpret_cast<float*>(a_hi + kmaj_off(q, k)) = hi[u];
+      *reinterpret_cast<float*>(a_lo + kmaj_off(q, k)) = lo[u];
+    }
   }
   // matching values and Gram coefficients (Section 3.2, eq. (2.6)) into the C tiles
-  float bd_row[kTileN / 32];
+  constexpr int kTaps = MM > 0 ? MM : 9;
+  const int s = lane & 7, g0 = lane & ~7;
+  const int ln = warp * 4 + (lane >> 3);  // local normal = C tile row
   {
-    const int s = lane & 7, g0 = lane & ~7;
-    const int M = g.M, d = g.d, NS = M - 1;
-    for (int pass = 0; pass < kTileN / 32; ++pass) {
-      const int ln = pass * 32 + warp * 4 + (lane >> 3);  // local normal (tile row)
-      const int n = n0 + ln;
-      const bool live = n < a.n_cols;
-      const int nn = live ? n : 0;
-      const int f = nn / g.B, pp = nn - f * g.B;
-      const double* fg = g.f_grid + (size_t)f * g.grid_stride;
-      const double* fb = g.f_bdry + (size_t)f * g.n_bdry;
-      double star = 0.0;
-      if (s < NS) {
-        const int32_t* gi = g.gidx + ((size_t)pp * NS + s) * M;
-        const double* gw = g.gw + ((size_t)pp * NS + s) * M;
-        for (int e = 0; e < M; ++e) {
-          const int32_t id = __ldg(gi + e);
-          const double v = id >= 0 ? __ldg(fg + id) : __ldg(fb + (-1 - id));
-          star = fma(__ldg(gw + e), v, star);
-        }
-      }
-      const double fbp = __ldg(fb + pp);
-      double fD;
-      {
-        const double* wn = g.wn + ((size_t)pp * (d - 1) + (s < d - 1 ? s : 0)) * M;
-        double acc = (s < d - 1) ? __ldg(wn) * fbp : 0.0;
-        for (int e = 1; e < M; ++e) {
-          const double st = __shfl_sync(0xffffffffu, star, g0 + e - 1);
-          if (s < d - 1) acc = fma(__ldg(wn + e), st, acc);
-        }
-        fD = s < d - 1 ? acc : (s == d - 1 ? fbp : 0.0);
-      }
-      double cs = 0.0;
-      for (int i = 0; i < d; ++i) {
-        const double v = __shfl_sync(0xffffffffu, fD, g0 + i);
-        if (s < d) cs = fma(__ldg(g.Q + i * d + s), v, cs);
-      }
-      const double v = (live && s < d) ? cs : 0.0;
-      const float hi = to_tf32((float)v);
-      *reinterpret_cast<float*>(c_hi + kmaj_off(ln, s)) = hi;
-      *reinterpret_cast<float*>(c_lo + kmaj_off(ln, s)) = (float)(v - (double)hi);
-      // boundary datum of row ln, kept in a register until the staging area is free
-      if (s == 0) bd_row[pass] = (float)fbp;
+    const int M = MM > 0 ? MM : g.M, d = g.d, NS = M - 1;
+    const bool star_lane = s < NS;
+    const int n = n0 + ln;
+    const bool live = n < a.n_cols;
+    const int nn = live ? n : 0;
+    const int ff = nn / g.B, pp = nn - ff * g.B;
+    const size_t base = ((size_t)pp * NS + (star_lane ? s : 0)) * M;
+    int32_t id[kTaps];
+    double wv[kTaps];
+#pragma unroll
+    for (int e = 0; e < kTaps; ++e) {
+      const bool on = star_lane && e < M;
+      id[e] = on ? __ldg(g.gidx + base + e) : 0;
+      wv[e] = on ? __ldg(g.gw + base + e) : 0.0;
     }
+    const double* wn = g.wn + ((size_t)pp * (d - 1) + (s < d - 1 ? s : 0)) * M;
+    double wnv[kTaps];
+#pragma unroll
+    for (int e = 0; e < kTaps; ++e) wnv[e] = (s < d - 1 && e < M) ? __ldg(wn + e) : 0.0;
+    double qv[kMaxD];
+#pragma unroll
+    for (int i = 0; i < kMaxD; ++i) qv[i] = (s < d && i < d) ? __ldg(g.Q + i * d + s) : 0.0;
+    pdl_wait();
+    pdl_trigger();
+    const double* fg = g.f_grid + (size_t)ff * g.grid_stride;
+    const double* fb = g.f_bdry + (size_t)ff * g.n_bdry;
+    double val[kTaps];
+#pragma unroll
+    for (int e = 0; e < kTaps; ++e) {
+      const int32_t k = id[e];
+      val[e] = (star_lane && e < M) ? __ldg(k >= 0 ? fg + k : fb + (-1 - k)) : 0.0;
+    }
+    const double fbp = __ldg(fb + pp);
+    double star = 0.0;
+#pragma unroll
+    for (int e = 0; e < kTaps; ++e) star = fma(wv[e], val[e], star);
+    double acc = wnv[0] * fbp;
+#pragma unroll
+    for (int e = 1; e < kTaps; ++e) {
+      const double st = __shfl_sync(0xffffffffu, star, g0 + (e - 1 < 8 ? e - 1 : 0));
+      if (e < M) acc = fma(wnv[e], st, acc);
+    }
+    const double fD = s < d - 1 ? acc : (s == d - 1 ? fbp : 0.0);
+    double cs = 0.0;
+#pragma unroll
+    for (int i = 0; i < kMaxD; ++i) {
+      const double v = __shfl_sync(0xffffffffu, fD, g0 + i);
+      if (i < d) cs = fma(qv[i], v, cs);
+    }
+    const double v = (live && s < d) ? cs : 0.0;
+    const float hi = to_tf32((float)v);
+    *reinterpret_cast<float*>(c_hi + kmaj_off(ln, s)) = hi;
+    *reinterpret_cast<float*>(c_lo + kmaj_off(ln, s)) = (float)(v - (double)hi);
+    if (s == 0) stage[ln * ldS] = (float)fbp;  // column 0: the boundary datum
   }
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -331,23 +374,26 @@ __global__ void __launch_bounds__(256, 1) k_gather_blend_tc(GatherArgs g, TcArgs
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tmem_slot;
   if (tid == 0) {
-    const uint32_t idesc = idesc_tf32(kTileN, a.ncr_pad);
+    const uint32_t idesc = idesc_tf32(kTcQTile, kTcNormals);
     const uint64_t dch = umma_desc(smem_u32(c_hi), 128, 256);
     const uint64_t dcl = umma_desc(smem_u32(c_lo), 128, 256);
-    const uint64_t dah = umma_desc(smem_u32(a_hi), 128, 256);
-    const uint64_t dal = umma_desc(smem_u32(a_lo), 128, 256);
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n"
-        ::"r"(tmem), "l"(dch), "l"(dah), "r"(idesc), "r"(0));
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n"
-        ::"r"(tmem), "l"(dch), "l"(dal), "r"(idesc), "r"(1));
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n"
-        ::"r"(tmem), "l"(dcl), "l"(dah), "r"(idesc), "r"(1));
+    for (int t = 0; t < nqt; ++t) {
+      const uint32_t dt = tmem + (uint32_t)(t * kTcNormals);
+      const uint64_t dah = umma_desc(smem_u32(a_hi) + t * kTcQTile * 32, 128, 256);
+      const uint64_t dal = umma_desc(smem_u32(a_lo) + t * kTcQTile * 32, 128, 256);
+      asm volatile(
+          "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+          "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n"
+          ::"r"(dt), "l"(dah), "l"(dch), "r"(idesc), "r"(0));
+      asm volatile(
+          "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+          "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n"
+          ::"r"(dt), "l"(dah), "l"(dcl), "r"(idesc), "r"(1));
+      asm volatile(
+          "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+          "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n"
+          ::"r"(dt), "l"(dal), "l"(dch), "r"(idesc), "r"(1));
+    }
     asm volatile(
         "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
         ::"r"(smem_u32(mbar)) : "memory");
@@ -370,52 +416,54 @@ __global__ void __launch_bounds__(256, 1) k_gather_blend_tc(GatherArgs g, TcArgs
   }
   done = __all_sync(0xffffffffu, done != 0) ? 1u : 0u;
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  if (done) {
-    // TMEM -> staging [local normal][q] (rows of the tile), then one contiguous store
-    const int quarter = warp & 3;
-    const int half = ((a.ncr_pad / 2) + 7) / 8 * 8;
-    const int cbeg = warp < 4 ? 0 : half, cend = warp < 4 ? half : a.ncr_pad;
-    const int ln = quarter * 32 + lane;
-    for (int c0 = cbeg; c0 < cend; c0 += 8) {
-      uint32_t r[8];
-      const uint32_t addr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)c0;
-      asm volatile(
-          "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-          : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
-            "=r"(r[6]), "=r"(r[7])
-          : "r"(addr));
-      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+  const int quarter = warp & 3, t = warp >> 2;
+  if (done && t < nqt) {
+    // TMEM lanes = fine points 128 t + 32 quarter + lane, columns = the 32 normals
+    uint32_t r[32];
+    const uint32_t addr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(t * kTcNormals);
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]),
+          "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]),
+          "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]),
+          "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]),
+          "=r"(r[30]), "=r"(r[31])
+        : "r"(addr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+    const int q = t * kTcQTile + quarter * 32 + lane;
+    if (q < a.Cr) {
 #pragma unroll
-      for (int e = 0; e < 8; ++e) {
-        const int q = c0 + e;
-        if (q < a.Cr) stage[ln * ldS + 1 + q] = __uint_as_float(r[e]);
-      }
+      for (int nl = 0; nl < kTcNormals; ++nl) stage[nl * ldS + 1 + q] = __uint_as_float(r[nl]);
     }
-  }
-  // boundary data: group lane s == 0 of (warp, group) served rows pass*32 + warp*4 + group
-  if ((lane & 7) == 0) {
-#pragma unroll
-    for (int pass = 0; pass < kTileN / 32; ++pass)
-      stage[(pass * 32 + warp * 4 + (lane >> 3)) * ldS] = bd_row[pass];
   }
   __syncthreads();
   if (done) {
-    const int rows = min(kTileN, a.n_cols - n0);
-    float* dst = a.F + (size_t)n0 * a.ldF;  // rows n0.. are contiguous (ldF = Cr + 1)
-    for (int idx = tid; idx < rows * ldS; idx += blockDim.x) dst[idx] = stage[idx];
+    // rows n0.. of F are contiguous and laid out as the staging tile
+    const int rows = min(kTcNormals, a.n_cols - n0);
+    float* dst = a.F + (size_t)n0 * ldS;
+    const int total = rows * ldS;
+    if ((ldS & 3) == 0 && (reinterpret_cast<uintptr_t>(dst) & 15) == 0) {
+      const float4* src4 = reinterpret_cast<const float4*>(stage);
+      float4* dst4 = reinterpret_cast<float4*>(dst);
+      for (int idx = tid; idx < total / 4; idx += blockDim.x) dst4[idx] = src4[idx];
+    } else {
+      for (int idx = tid; idx < total; idx += blockDim.x) dst[idx] = stage[idx];
+    }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if (warp == 0) {
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
-                 "r"(kTmemCols));
+                 "r"(kTcTmemCols));
   }
 }
 
 fc2d_status launch_gather_blend_tc(const GatherArgs& g, int n_f, int ldF, const float* Ar_hi,
-                                   const float* Ar_lo, float* F, int* status, cudaStream_t s,
-                                   bool q_major) {
-  if (g.Cr > kMaxCrPad || g.d > 8 || g.M - 1 > 8 || q_major)
+                                   const float* Ar_lo, float* F, int* status, cudaStream_t s) {
+  if (g.Cr > kMaxCrPad || g.d > 8 || g.M - 1 > 8 || ldF < g.Cr + 1 || ldF > kTcMaxLd)
     return set_error(FC2D_ERR_UNSUPPORTED, "fused tensor-core blend: C n_r <= 256, d <= 8, M <= 9");
   TcArgs a{};
   a.n_cols = n_f * g.B;
@@ -427,12 +475,12 @@ fc2d_status launch_gather_blend_tc(const GatherArgs& g, int n_f, int ldF, const 
   a.Ar_lo = Ar_lo;
   a.F = F;
   a.status = status;
-  a.q_major = q_major ? 1 : 0;
-  // staging + barrier; at most two CTAs per SM (256 TMEM columns each)
-  size_t sm = std::max<size_t>(96 * 1024, kStageBytes + 64);
-  cudaFuncSetAttribute(k_gather_blend_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  k_gather_blend_tc<<<(a.n_cols + kTileN - 1) / kTileN, 256, sm, s>>>(g, a);
-  return cuda_check(cudaGetLastError(), "fused tensor-core blend launch");
+  const size_t sm = kTcSmem;
+  auto k = g.M == 8 ? k_gather_blend_tc<8> : (g.M == 7 ? k_gather_blend_tc<7> : k_gather_blend_tc<0>);
+  cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  return cuda_check(
+      launch_pdl(k, dim3((a.n_cols + kTcNormals - 1) / kTcNormals), dim3(256), sm, s, g, a),
+      "fused tensor-core blend launch");
 }
 
 }  // namespace fc2d

@@ -39,11 +39,17 @@ struct Layout {
   size_t oF, ovals, ointer, ocoef, obvals;
 };
 
+// Row length of the strip values F in workspace: Cr + 1 for FP64; for the mixed form
+// a multiple of 4 floats with room for the interpolation's aligned float4 windows.
+int ws_ldF(const fc2d_plan_s* p) {
+  return p->prm.precision == FC2D_MIXED ? (p->Cr + 12 + 3) / 4 * 4 : p->Cr + 1;
+}
+
 Layout layout(const fc2d_plan_s* p, int n_f) {
   Layout L{};
   const size_t esz = p->prm.precision == FC2D_MIXED ? 4 : 8;
   const size_t pitch = ((size_t)p->grid.nx / 2 + 1 + 7) / 8 * 8;
-  L.F = al((size_t)n_f * p->prm.B * (p->Cr + 1) * esz);
+  L.F = al((size_t)n_f * p->prm.B * ws_ldF(p) * esz);
   L.vals = al((size_t)n_f * std::max<size_t>(1, p->strip_lin.size()) * esz);
   L.inter = al((size_t)n_f * p->grid.ny * pitch * 2 * esz);
   L.coef = al((size_t)n_f * p->prm.B * kMaxD * 8);
@@ -82,12 +88,13 @@ GatherArgs gather_args(fc2d_plan_s* p, const double* fg, const double* fb, void*
   return a;
 }
 
-InterpArgs interp_args(fc2d_plan_s* p) {
+InterpArgs interp_args(fc2d_plan_s* p, int ldF) {
   InterpArgs a{};
   a.n_strip = (int)p->strip_lin.size();
   a.M = p->prm.M;
   a.B = p->prm.B;
   a.Cr = p->Cr;
+  a.ldF = ldF;
   a.w = p->dev.s_w;
   a.pb = p->dev.s_pb;
   a.sb = p->dev.s_sb;
@@ -139,12 +146,12 @@ fc2d_status launched(const char* what) { return cuda_check(cudaGetLastError(), w
 // Mixed form of step 5: matching values and Gram coefficients in FP64, then the
 // contraction with A_r on the tensor cores into float strip values F.
 fc2d_status mixed_blend(fc2d_plan_s* p, int n_f, const double* fg, const double* fb, void* F,
-                        const Layout& L, cudaStream_t s, bool q_major) {
+                        int ldF, const Layout& L, cudaStream_t s) {
   if (p->prm.M - 1 <= 8 && p->prm.d <= 8) {
     ProfScope ps(p, "gather_blend_tc", s);
     return launch_gather_blend_tc(gather_args(p, fg, fb, nullptr, nullptr, nullptr), n_f,
-                                  p->Cr + 1, p->dev.Ar_hi, p->dev.Ar_lo, static_cast<float*>(F),
-                                  p->dev.status, s, q_major);
+                                  ldF, p->dev.Ar_hi, p->dev.Ar_lo, static_cast<float*>(F),
+                                  p->dev.status, s);
   }
   double* coef = reinterpret_cast<double*>(ws(p, L.ocoef));
   double* bvals = reinterpret_cast<double*>(ws(p, L.obvals));
@@ -153,7 +160,7 @@ fc2d_status mixed_blend(fc2d_plan_s* p, int n_f, const double* fg, const double*
     launch_gather_blend(gather_args(p, fg, fb, nullptr, coef, bvals), n_f, false, s);
   }
   ProfScope ps(p, "blend_tc", s);
-  return launch_blend_tc(n_f * p->prm.B, p->Cr, p->prm.d, p->Cr + 1, coef, kMaxD, bvals,
+  return launch_blend_tc(n_f * p->prm.B, p->Cr, p->prm.d, ldF, coef, kMaxD, bvals,
                          p->dev.Ar_hi, p->dev.Ar_lo, static_cast<float*>(F), p->dev.status, s);
 }
 
@@ -166,12 +173,12 @@ fc2d_status strip_values(fc2d_plan_s* p, int n_f, const double* fg, const double
     ProfScope ps(p, "gather_blend", s);
     launch_gather_blend(gather_args(p, fg, fb, F, nullptr, nullptr), n_f, true, s);
   } else {
-    fc2d_status st = mixed_blend(p, n_f, fg, fb, F, L, s, false);
+    fc2d_status st = mixed_blend(p, n_f, fg, fb, F, ws_ldF(p), L, s);
     if (st) return st;
   }
   {
     ProfScope ps(p, "interp", s);
-    launch_interp(interp_args(p), n_f, f64, F, ws(p, L.ovals), s);
+    launch_interp(interp_args(p, ws_ldF(p)), n_f, f64, F, ws(p, L.ovals), s);
   }
   return launched("strip values");
 }
@@ -191,7 +198,7 @@ extern "C" fc2d_status fc2d_blend(fc2d_plan_t p, int n_f, const double* fg, cons
   }
   Layout L = layout(p, n_f);
   if ((st = ensure_workspace(p, L.total))) return st;
-  if ((st = mixed_blend(p, n_f, fg, fb, F, L, s, false))) return st;
+  if ((st = mixed_blend(p, n_f, fg, fb, F, p->Cr + 1, L, s))) return st;
   return launched("fc2d_blend");
 }
 
@@ -201,7 +208,7 @@ extern "C" fc2d_status fc2d_interp(fc2d_plan_t p, int n_f, const void* F, void* 
   if (st) return st;
   if (!F || !vals) return set_error(FC2D_ERR_ARG, "fc2d_interp: null pointer");
   cudaSetDevice(p->device);
-  launch_interp(interp_args(p), n_f, p->prm.precision == FC2D_FP64, F, vals,
+  launch_interp(interp_args(p, p->Cr + 1), n_f, p->prm.precision == FC2D_FP64, F, vals,
                 (cudaStream_t)stream);
   return launched("fc2d_interp");
 }
@@ -433,7 +440,7 @@ extern "C" fc2d_status fc2d_wave_interior(fc2d_plan_t p, int n_f, double c, doub
     }
     {
       ProfScope ps(p, "interp", s);
-      launch_interp(interp_args(p), n_f, true, F, vals, s);
+      launch_interp(interp_args(p, p->Cr + 1), n_f, true, F, vals, s);
     }
     {
       ProfScope ps(p, "fft_rows_fused", s);

@@ -152,6 +152,8 @@ __global__ void __launch_bounds__(256) k_gather_blend(GatherArgs a) {
   const int M = a.M, d = a.d, NS = M - 1;
   const double* fg = a.f_grid + (size_t)f * a.grid_stride;
   const double* fb = a.f_bdry + (size_t)f * a.n_bdry;
+  pdl_wait();
+  pdl_trigger();
   double star = 0.0;
   if (s < NS) {
     const int32_t* gi = a.gidx + ((size_t)pp * NS + s) * M;
@@ -206,13 +208,9 @@ void launch_gather_blend(const GatherArgs& a, int n_f, bool fp64, cudaStream_t s
   const int per_warp = 32 / GS;
   const int warps = (a.B + per_warp - 1) / per_warp;
   dim3 grid((warps * 32 + 255) / 256, n_f);
-  if (GS == 8) {
-    if (fp64) k_gather_blend<true, 8><<<grid, 256, 0, s>>>(a);
-    else k_gather_blend<false, 8><<<grid, 256, 0, s>>>(a);
-  } else {
-    if (fp64) k_gather_blend<true, 16><<<grid, 256, 0, s>>>(a);
-    else k_gather_blend<false, 16><<<grid, 256, 0, s>>>(a);
-  }
+  auto k = GS == 8 ? (fp64 ? k_gather_blend<true, 8> : k_gather_blend<false, 8>)
+                    : (fp64 ? k_gather_blend<true, 16> : k_gather_blend<false, 16>);
+  launch_pdl(k, grid, dim3(256), 0, s, a);
 }
 
 // ------------------------------------------------------------------------- //
@@ -284,35 +282,72 @@ fc2d_status interp_weights_gpu(int n_strip, int M, int Cr, int B, double k1, int
 
 // Per call: value = sum_a wth[a] sum_b weta[b] F[(pb + a) mod B][s + b], accumulated in
 // TA (double for the FP64 form, float for the mixed form).  MM > 0: compile-time M.
-template <int MM, typename TF, typename TW, typename TA, typename TV>
+// One thread per (strip point, function).  VEC (float F, ldF a multiple of 4 and
+// ldF >= Cr + 12): the M values s..s+M-1 of a normal come from the three aligned float4
+// at (s & ~3).. and a register shift by s & 3, instead of M scalar loads.
+template <int MM, typename TF, typename TW, typename TA, typename TV, bool VEC>
 __global__ void __launch_bounds__(256) k_interp(InterpArgs a, const TF* __restrict__ F,
                                                 TV* __restrict__ vals) {
   const int n = blockIdx.x * blockDim.x + threadIdx.x;
   const int f = blockIdx.y;
   if (n >= a.n_strip) return;
   const int M = MM > 0 ? MM : a.M;
-  const int B = a.B, ld = a.Cr + 1, ns = a.n_strip;
+  const int B = a.B, ld = a.ldF, ns = a.n_strip;
   const TW* w = reinterpret_cast<const TW*>(a.w);
   const int pb = __ldg(a.pb + n), s = __ldg(a.sb + n);
-  TW weta[MM > 0 ? MM : kMaxM];
+  // the weights are plan constants: loaded before the wait on the blend kernel
+  TW weta[MM > 0 ? MM : kMaxM], wth[MM > 0 ? MM : kMaxM];
 #pragma unroll
-  for (int b = 0; b < (MM > 0 ? MM : kMaxM); ++b)
+  for (int b = 0; b < (MM > 0 ? MM : kMaxM); ++b) {
     if (b < M) weta[b] = __ldg(w + (size_t)(M + b) * ns + n);
-  // F[f][p][q] at Ff + p * pst + q * qst
-  const size_t pst = a.q_major ? 1 : (size_t)ld, qst = a.q_major ? (size_t)a.n_cols : 1;
-  const TF* Ff = F + (a.q_major ? (size_t)f * B : (size_t)f * B * ld);
+    if (b < M) wth[b] = __ldg(w + (size_t)b * ns + n);
+  }
+  pdl_wait();
+  pdl_trigger();
+  const TF* Ff = F + (size_t)f * B * ld;
   TA acc = 0;
+  if constexpr (VEC) {
+    static_assert(MM > 0 && MM <= 9, "vector path needs a compile-time M <= 9");
+    const int s0 = s & ~3, sh = s & 3;
+    // eta weights shifted into the 12-value window (s0 .. s0+11): the same for every row
+    TA ws[12];
 #pragma unroll
-  for (int ai = 0; ai < (MM > 0 ? MM : kMaxM); ++ai) {
-    if (ai >= M) break;
-    int pr = pb + ai;
-    pr = pr < 0 ? pr + B : (pr >= B ? pr - B : pr);
-    const TF* row = Ff + (size_t)pr * pst + (size_t)s * qst;
-    TA v = 0;
+    for (int b = 0; b < 12; ++b) {
+      const TA w0 = b < MM ? (TA)weta[b] : (TA)0;
+      const TA w1 = (b >= 1 && b - 1 < MM) ? (TA)weta[b >= 1 ? b - 1 : 0] : (TA)0;
+      const TA w2 = (b >= 2 && b - 2 < MM) ? (TA)weta[b >= 2 ? b - 2 : 0] : (TA)0;
+      const TA w3 = (b >= 3 && b - 3 < MM) ? (TA)weta[b >= 3 ? b - 3 : 0] : (TA)0;
+      ws[b] = sh == 0 ? w0 : sh == 1 ? w1 : sh == 2 ? w2 : w3;
+    }
 #pragma unroll
-    for (int b = 0; b < (MM > 0 ? MM : kMaxM); ++b)
-      if (b < M) v = fma((TA)weta[b], (TA)__ldg(row + (size_t)b * qst), v);
-    acc = fma((TA)__ldg(w + (size_t)ai * ns + n), v, acc);
+    for (int ai = 0; ai < MM; ++ai) {
+      int pr = pb + ai;
+      pr = pr < 0 ? pr + B : (pr >= B ? pr - B : pr);
+      const float4* row = reinterpret_cast<const float4*>(Ff + (size_t)pr * ld + s0);
+      TA v = 0;
+#pragma unroll
+      for (int u = 0; u < 3; ++u) {
+        const float4 q = __ldg(row + u);
+        v = fma(ws[4 * u], (TA)q.x, v);
+        v = fma(ws[4 * u + 1], (TA)q.y, v);
+        v = fma(ws[4 * u + 2], (TA)q.z, v);
+        v = fma(ws[4 * u + 3], (TA)q.w, v);
+      }
+      acc = fma((TA)wth[ai], v, acc);
+    }
+  } else {
+#pragma unroll
+    for (int ai = 0; ai < (MM > 0 ? MM : kMaxM); ++ai) {
+      if (ai >= M) break;
+      int pr = pb + ai;
+      pr = pr < 0 ? pr + B : (pr >= B ? pr - B : pr);
+      const TF* row = Ff + (size_t)pr * ld + s;
+      TA v = 0;
+#pragma unroll
+      for (int b = 0; b < (MM > 0 ? MM : kMaxM); ++b)
+        if (b < M) v = fma((TA)weta[b], (TA)__ldg(row + b), v);
+      acc = fma((TA)wth[ai], v, acc);
+    }
   }
   vals[(size_t)f * ns + n] = (TV)acc;
 }
@@ -322,19 +357,17 @@ void launch_interp(const InterpArgs& a, int n_f, bool fp64, const void* F, void*
   if (a.n_strip == 0) return;
   dim3 grid((a.n_strip + 255) / 256, n_f);
   if (fp64) {
-    if (a.M == 8)
-      k_interp<8, double, double, double, double><<<grid, 256, 0, s>>>(a, (const double*)F,
-                                                                       (double*)vals);
-    else
-      k_interp<0, double, double, double, double><<<grid, 256, 0, s>>>(a, (const double*)F,
-                                                                       (double*)vals);
+    auto k = a.M == 8 ? k_interp<8, double, double, double, double, false>
+                      : k_interp<0, double, double, double, double, false>;
+    launch_pdl(k, grid, dim3(256), 0, s, a, (const double*)F, (double*)vals);
   } else {
-    if (a.M == 8)
-      k_interp<8, float, float, float, float><<<grid, 256, 0, s>>>(a, (const float*)F,
-                                                                   (float*)vals);
-    else
-      k_interp<0, float, float, float, float><<<grid, 256, 0, s>>>(a, (const float*)F,
-                                                                   (float*)vals);
+    const bool vec = a.ldF % 4 == 0 && a.ldF >= a.Cr + 12 &&
+                     (reinterpret_cast<uintptr_t>(F) & 15) == 0;
+    auto k = (a.M == 8 && vec) ? k_interp<8, float, float, float, float, true>
+             : (a.M == 7 && vec) ? k_interp<7, float, float, float, float, true>
+             : a.M == 8 ? k_interp<8, float, float, float, float, false>
+                        : k_interp<0, float, float, float, float, false>;
+    launch_pdl(k, grid, dim3(256), 0, s, a, (const float*)F, (float*)vals);
   }
 }
 

@@ -28,8 +28,7 @@ struct GatherArgs {
 
 struct InterpArgs {
   int n_strip, M, B, Cr;
-  int q_major;           // F layout [Cr+1][n_f*B] instead of [n_f][B][Cr+1]
-  int n_cols;            // n_f * B (q-major row length)
+  int ldF;               // row length of F (>= Cr + 1)
   const void* w;         // [2M][n_strip] theta then eta weights (double or float)
   const int32_t* pb;     // first normal index (mod B)
   const int32_t* sb;     // first fine index along the normal
@@ -49,6 +48,34 @@ struct RowArgs {
 };
 
 #if defined(__CUDACC__)
+// Programmatic dependent launch.  A kernel started by launch_pdl may begin while the
+// previous kernel on its stream is still finishing.  It calls pdl_wait() before it reads
+// anything written by earlier work on the stream and before its first global write;
+// pdl_wait() returns once the previous grid has completed and its writes are visible
+// (immediately when the kernel was launched without the attribute).  Plan constants
+// (tables written at plan time) may be read before it.  pdl_trigger() lets the next
+// kernel on the stream be launched early.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                              cudaStream_t stream, Args... args) {
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
 // Fill a shared-memory row with the extension: 0, then f on the inside intervals,
 // then the strip values.  Ends with the row complete (after a __syncthreads()).
 template <typename T, typename TV>
@@ -78,10 +105,9 @@ fc2d_status launch_blend_tc(int n_cols, int Cr, int d, int ldF, const double* co
                             int coef_ld, const double* bvals, const float* Ar_hi,
                             const float* Ar_lo, float* F, int* status, cudaStream_t s);
 // fused mixed form: matching values + Gram coefficients + tensor-core contraction in one
-// kernel (M <= 9, d <= 8); F [n_f*B][ldF] float, or [Cr+1][n_f*B] when q_major.
+// kernel (M <= 9, d <= 8); F [n_f*B][ldF] float.
 fc2d_status launch_gather_blend_tc(const GatherArgs& g, int n_f, int ldF, const float* Ar_hi,
-                                   const float* Ar_lo, float* F, int* status, cudaStream_t s,
-                                   bool q_major);
+                                   const float* Ar_lo, float* F, int* status, cudaStream_t s);
 void launch_interp(const InterpArgs& a, int n_f, bool fp64, const void* F, void* vals,
                    cudaStream_t s);
 void launch_assemble(const RowArgs& a, int n_f, bool fp64, const double* f_grid,
@@ -104,7 +130,10 @@ struct FftArgs {
 void launch_fft_rows(const FftArgs& fa, const RowArgs& ra, int n_f, bool fp64, int mode,
                      const void* ext, const double* f_grid, const void* vals, void* inter,
                      cudaStream_t s);
-void launch_fft_cols(const FftArgs& fa, int n_f, bool fp64, const void* inter, void* fhat,
+// cols: the length-ny column DFTs of the row-pass intermediate into the half spectrum;
+// the intermediate is scratch and may be overwritten (the 4096-point FP32 form works
+// in place in two passes).
+void launch_fft_cols(const FftArgs& fa, int n_f, bool fp64, void* inter, void* fhat,
                      cudaStream_t s);
 // Fourier Forwarding: modal advance of [2 n_f] row spectra (u's then u_t's), in place.
 void launch_wave_cols(const FftArgs& fa, int n_f, void* inter, double c, double t, double Lx,

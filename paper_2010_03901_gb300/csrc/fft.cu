@@ -89,7 +89,7 @@ __global__ void __launch_bounds__(256) k_fft_cols(FftArgs fa, int cb,
 bool launch_fft_rows_p2(const FftArgs& fa, const RowArgs& ra, int n_f, bool fp64, int mode,
                         const void* ext, const double* f_grid, const void* vals, void* inter,
                         cudaStream_t s);
-bool launch_fft_cols_p2(const FftArgs& fa, int n_f, bool fp64, const void* inter, void* fhat,
+bool launch_fft_cols_p2(const FftArgs& fa, int n_f, bool fp64, void* inter, void* fhat,
                         cudaStream_t s);
 
 void launch_fft_rows(const FftArgs& fa, const RowArgs& ra, int n_f, bool fp64, int mode,
@@ -119,7 +119,7 @@ static int pick_cb(int ny, size_t csize) {
   return cb;
 }
 
-void launch_fft_cols(const FftArgs& fa, int n_f, bool fp64, const void* inter, void* fhat,
+void launch_fft_cols(const FftArgs& fa, int n_f, bool fp64, void* inter, void* fhat,
                      cudaStream_t s) {
   if (launch_fft_cols_p2(fa, n_f, fp64, inter, fhat, s)) return;
   const int ncol = fa.nx / 2 + 1;

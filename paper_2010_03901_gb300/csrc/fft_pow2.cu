@@ -16,6 +16,8 @@
 // scaled by 1/(nx ny), written to the half spectrum [ny][nx/2+1].
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "fc2d_kernels.cuh"
 
 namespace fc2d {
@@ -122,18 +124,20 @@ template <typename T, typename C, int R> __device__ __forceinline__ void dft(C* 
 }
 
 // Round-to-nearest-even double -> float on the integer pipe (the FP64 pipe that the
-// conversion instruction uses is narrow on this part).  Normal results only; values
-// that would be subnormal, infinite or NaN in float take the hardware conversion.
+// conversion instruction uses is narrow on this part).  For doubles whose exponent e
+// lies in [897, 1148] (float exponents 1..252, so no overflow even after rounding up):
+// the high word of (hi:lo) << 3 holds e's low 9 bits above the top 23 mantissa bits;
+// subtracting 896 << 23 (mod 2^32) rebases the exponent, the 29 dropped bits round the
+// result (ties to even; a mantissa carry moves into the exponent), and the sign is put
+// back.  Other values (zero, subnormal, huge, inf, NaN) take the hardware conversion.
 __device__ __forceinline__ float d2f_rn(double x) {
-  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-  const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
-  const int fe = (int)((b >> 52) & 0x7FF) - 1023 + 127;
-  if (fe <= 0 || fe >= 254) return (float)x;
-  const unsigned long long m = b & 0xFFFFFFFFFFFFFull;
-  unsigned r = ((unsigned)fe << 23) | (unsigned)(m >> 29);
-  const unsigned long long rem = m & 0x1FFFFFFFull;
-  if (rem > 0x10000000ull || (rem == 0x10000000ull && (r & 1u))) r += 1u;
-  return __uint_as_float(sign | r);
+  const unsigned lo = (unsigned)__double2loint(x), hi = (unsigned)__double2hiint(x);
+  const unsigned e = (hi >> 20) & 0x7FFu;
+  if (e - 897u > 251u) return __double2float_rn(x);
+  unsigned r = __funnelshift_l(lo, hi, 3) - (896u << 23);
+  const unsigned dropped = lo & 0x1FFFFFFFu;
+  r += (dropped + (r & 1u)) > 0x10000000u ? 1u : 0u;
+  return __uint_as_float(r | (hi & 0x80000000u));
 }
 template <typename T> __device__ __forceinline__ T from_double(double x) { return (T)x; }
 template <> __device__ __forceinline__ float from_double<float>(double x) { return d2f_rn(x); }
@@ -209,6 +213,9 @@ __device__ __forceinline__ void block_fft(typename Cx<T>::type* buf, int t, bool
     block_fft<T, LOGN, E, NS * R>(buf, t, active, tw, tws);
   }
 }
+
+// lanes served by one shared-memory wavefront for complex values of type T
+template <typename T> __host__ __device__ constexpr int col_lanes() { return sizeof(T) == 4 ? 16 : 8; }
 
 // complex values per thread: 16 for float (radix-16 stages, three for 4096 points),
 // 8 for double (register pressure of FP64 complex values)
@@ -309,6 +316,8 @@ k_fft_rows_p2(FftArgs fa, RowArgs ra, int mode, const T* __restrict__ ext,
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* buf = reinterpret_cast<C*>(smem_raw);
   const int j = blockIdx.x, f = blockIdx.y, t = threadIdx.x, nx = 2 * NH;
+  pdl_wait();
+  pdl_trigger();
   // assemble the row: reals x_i -> pair n = i/2, component i%2 (padded pairs)
   auto put = [&](int i, T v) { reinterpret_cast<T*>(&buf[pad<T>(i >> 1)])[i & 1] = v; };
   if (mode == 0) {
@@ -318,25 +327,36 @@ k_fft_rows_p2(FftArgs fa, RowArgs ra, int mode, const T* __restrict__ ext,
       buf[pad<T>(n)] = v;
     }
   } else {
-    for (int n = threadIdx.x; n < NH; n += blockDim.x) buf[pad<T>(n)] = C{(T)0, (T)0};
-    __syncthreads();
     const double* fg = f_grid + (size_t)f * ra.grid_stride + (size_t)j * nx;
     const int iv0 = __ldg(ra.row_iv_off + j), iv1 = __ldg(ra.row_iv_off + j + 1);
+    for (int n = threadIdx.x; n < NH; n += blockDim.x) buf[pad<T>(n)] = C{(T)0, (T)0};
+    __syncthreads();
+    // inside intervals [lo, hi]: the pairs n with lo <= 2n and 2n + 1 <= hi as one
+    // 16-byte load each when the row is 16-byte aligned (eight loads in flight per
+    // thread), the odd ends element by element
+    const bool vec = (reinterpret_cast<uintptr_t>(fg) & 15) == 0;
     for (int k = iv0; k < iv1; ++k) {
       const int lo = __ldg(ra.row_iv + 2 * k), hi = __ldg(ra.row_iv + 2 * k + 1);
-      // eight independent loads in flight per thread before the shared-memory stores
-      for (int i0 = lo + threadIdx.x; i0 <= hi; i0 += 8 * blockDim.x) {
-        double v[8];
+      if (vec) {
+        const int p0 = (lo + 1) >> 1, p1 = (hi + 1) >> 1;  // pairs p0 .. p1 - 1
+        const double2* fg2 = reinterpret_cast<const double2*>(fg);
+        for (int n0 = p0 + threadIdx.x; n0 < p1; n0 += 8 * blockDim.x) {
+          double2 d[8];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
-          const int i = i0 + u * blockDim.x;
-          v[u] = i <= hi ? __ldg(fg + i) : 0.0;
-        }
+          for (int u = 0; u < 8; ++u) {
+            const int n = n0 + u * blockDim.x;
+            d[u] = n < p1 ? __ldg(fg2 + n) : make_double2(0.0, 0.0);
+          }
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
-          const int i = i0 + u * blockDim.x;
-          if (i <= hi) put(i, from_double<T>(v[u]));
+          for (int u = 0; u < 8; ++u) {
+            const int n = n0 + u * blockDim.x;
+            if (n < p1) buf[pad<T>(n)] = C{from_double<T>(d[u].x), from_double<T>(d[u].y)};
+          }
         }
+        if (threadIdx.x == 0 && (lo & 1)) put(lo, from_double<T>(__ldg(fg + lo)));
+        if (threadIdx.x == 0 && !(hi & 1)) put(hi, from_double<T>(__ldg(fg + hi)));
+      } else {
+        for (int i = lo + threadIdx.x; i <= hi; i += blockDim.x) put(i, from_double<T>(__ldg(fg + i)));
       }
     }
     const int s0 = __ldg(ra.row_strip_off + j), s1 = __ldg(ra.row_strip_off + j + 1);
@@ -349,14 +369,17 @@ k_fft_rows_p2(FftArgs fa, RowArgs ra, int mode, const T* __restrict__ ext,
   block_fft<T, LOGNH, E>(buf, t, t < NT, tw, 1);
   const C* rtw = reinterpret_cast<const C*>(fa.rtw);
   C* out = inter + ((size_t)f * fa.ny + j) * fa.pitch;
-  for (int k = threadIdx.x; k <= NH; k += blockDim.x) {
-    const C zk = buf[pad<T>(k == NH ? 0 : k)];
+  // X_k and X_{NH-k} from Z_k and Z_{NH-k} (k = 0..NH/2; k = 0 pairs with NH):
+  // e' = conj(e), o' = -conj(o), rtw_{NH-k} = -conj(rtw_k), so w'o' = conj(w o)
+  for (int k = threadIdx.x; k <= NH / 2; k += blockDim.x) {
+    const C zk = buf[pad<T>(k)];
     C zc = buf[pad<T>(k == 0 ? 0 : NH - k)];
     zc.y = -zc.y;
     const C e = {(T)0.5 * (zk.x + zc.x), (T)0.5 * (zk.y + zc.y)};
     const C o = {(T)0.5 * (zk.x - zc.x), (T)0.5 * (zk.y - zc.y)};
     const C wo = mul(__ldg(rtw + k), o);
     out[k] = C{e.x + wo.y, e.y - wo.x};
+    if (k != NH - k) out[NH - k] = C{e.x - wo.y, -e.y - wo.x};
   }
 }
 
@@ -380,11 +403,109 @@ k_fft_cols_p2(FftArgs fa, const typename Cx<T>::type* __restrict__ inter,
   // kx < pitch always (pitch = nx/2+1 rounded up to 8, CB divides 8): reads stay in the
   // intermediate row; columns beyond nx/2 are computed and not stored
   const C* src = inter + (size_t)f * N * fa.pitch + kx;
-  C* col = buf + c * PN;
+  // column c starts c * W/CB elements after c * PN (W = lanes per shared-memory
+  // wavefront: 16 for 8-byte, 8 for 16-byte elements), so that the CB interleaved
+  // columns served by one wavefront fall in disjoint banks (no conflicts in the
+  // first-stage writes and the stage reads, for every size and CB launched below)
+  C* col = buf + c * PN + c * (col_lanes<T>() / CB);
+  pdl_wait();
+  pdl_trigger();
   stage_first_global<T, LOGNY, E, R1>(src, fa.pitch, col, t);
   const C* tw = reinterpret_cast<const C*>(fa.tsy);
   fft_rest_to_global<T, LOGNY, E, R1>(col, t, tw, fhat + (size_t)f * N * ncol + kx, ncol,
                                       (T)fa.scale, kx < ncol);
+}
+
+// ------------------------------------------------------------------------- //
+// Columns of 4096 points (FP32) in two passes, N = 64 x 64 ("four-step"):
+//   j = 64 j1 + j2, m = m1 + 64 m2,
+//   pass A: Y[m1][j2] = w_4096^(j2 m1) sum_j1 x[64 j1 + j2] w_64^(j1 m1), written in
+//           place to row 64 m1 + j2 of the intermediate;
+//   pass B: X[m1 + 64 m2] = sum_j2 Y[m1][j2] w_64^(j2 m2), scaled, to the spectrum.
+// A block of 128 threads serves 16 adjacent columns; thread (c = tid % 16, l = tid / 16)
+// holds the 8 values of input index l + 8 i of its column.  Each 64-point DFT is a
+// length-8 DFT over i in registers, the twiddles w_64^(l m'), an exchange through
+// shared memory and a length-8 DFT over l, after which thread (c, L) holds the outputs
+// L + 8 m'.  Consecutive lanes take consecutive columns, so a warp's load or store is
+// two rows of 16 columns (two 128-byte lines).  Blocks need 8 KB of shared memory, so
+// many are resident per SM, and the 67 MB intermediate of a 4096^2 grid can stay in L2
+// between the passes.
+// ------------------------------------------------------------------------- //
+constexpr int kC4Cols = 16;   // columns per block
+
+// 64-point DFT of a[i] = x[l + 8 i] held by the threads (c, l = 0..7) of column c;
+// on return a[m'] = X[l + 8 m'].  ex: the block's [8][8][16] exchange buffer; w: the
+// 4096-entry table w_4096^t (w_64^k = w[64 k]).
+__device__ __forceinline__ void dft64_cols(float2* a, int c, int l, float2* ex,
+                                           const float2* __restrict__ w) {
+  dft<float, float2, 8>(a);
+#pragma unroll
+  for (int m = 1; m < 8; ++m) a[m] = mul(a[m], __ldg(w + ((64 * l * m) & 4095)));
+#pragma unroll
+  for (int m = 0; m < 8; ++m) ex[(m * 8 + l) * kC4Cols + c] = a[m];
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < 8; ++k) a[k] = ex[(l * 8 + k) * kC4Cols + c];
+  dft<float, float2, 8>(a);
+}
+
+__global__ void __launch_bounds__(128) k_cols4k_a(FftArgs fa, float2* __restrict__ inter) {
+  __shared__ float2 ex[64 * kC4Cols];
+  const int c = threadIdx.x & (kC4Cols - 1), l = threadIdx.x / kC4Cols;
+  const int ncol = fa.nx / 2 + 1;
+  const int kx = blockIdx.x * kC4Cols + c;
+  const int j2 = blockIdx.y, f = blockIdx.z;
+  const bool live = kx < ncol;
+  const float2* w = reinterpret_cast<const float2*>(fa.twy);
+  float2* col = inter + (size_t)f * 4096 * fa.pitch + kx;
+  pdl_wait();
+  pdl_trigger();
+  float2 a[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+    a[i] = live ? col[(size_t)(64 * (l + 8 * i) + j2) * fa.pitch] : make_float2(0.f, 0.f);
+  dft64_cols(a, c, l, ex, w);
+#pragma unroll
+  for (int m2 = 0; m2 < 8; ++m2) {
+    const int m1 = l + 8 * m2;
+    const float2 y = mul(a[m2], __ldg(w + ((j2 * m1) & 4095)));
+    if (live) col[(size_t)(64 * m1 + j2) * fa.pitch] = y;
+  }
+}
+
+__global__ void __launch_bounds__(128) k_cols4k_b(FftArgs fa, const float2* __restrict__ inter,
+                                                   float2* __restrict__ fhat) {
+  __shared__ float2 ex[64 * kC4Cols];
+  const int c = threadIdx.x & (kC4Cols - 1), l = threadIdx.x / kC4Cols;
+  const int ncol = fa.nx / 2 + 1;
+  const int kx = blockIdx.x * kC4Cols + c;
+  const int m1 = blockIdx.y, f = blockIdx.z;
+  const bool live = kx < ncol;
+  const float2* w = reinterpret_cast<const float2*>(fa.twy);
+  const float2* col = inter + (size_t)f * 4096 * fa.pitch + kx;
+  pdl_wait();
+  pdl_trigger();
+  float2 a[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+    a[i] = live ? col[(size_t)(64 * m1 + l + 8 * i) * fa.pitch] : make_float2(0.f, 0.f);
+  dft64_cols(a, c, l, ex, w);
+  const float sc = (float)fa.scale;
+  float2* out = fhat + (size_t)f * 4096 * ncol + kx;
+  if (live) {
+#pragma unroll
+    for (int m2p = 0; m2p < 8; ++m2p) {
+      const int m2 = l + 8 * m2p;
+      out[(size_t)(m1 + 64 * m2) * ncol] = make_float2(a[m2p].x * sc, a[m2p].y * sc);
+    }
+  }
+}
+
+static void cols4k_launch(const FftArgs& fa, int n_f, void* inter, void* fhat, cudaStream_t s) {
+  const int ncol = fa.nx / 2 + 1;
+  const dim3 grid((ncol + kC4Cols - 1) / kC4Cols, 64, n_f);
+  launch_pdl(k_cols4k_a, grid, dim3(128), 0, s, fa, (float2*)inter);
+  launch_pdl(k_cols4k_b, grid, dim3(128), 0, s, fa, (const float2*)inter, (float2*)fhat);
 }
 
 template <typename T, typename TV, int L>
@@ -394,8 +515,8 @@ static void rows_launch(const FftArgs& fa, const RowArgs& ra, int n_f, int mode,
   const size_t sm = (size_t)padded<T>(1 << L) * sizeof(typename Cx<T>::type);
   auto k = k_fft_rows_p2<T, TV, L>;
   cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  k<<<dim3(fa.ny, n_f), NT, sm, s>>>(fa, ra, mode, (const T*)ext, fg, (const TV*)vals,
-                                     (typename Cx<T>::type*)inter);
+  launch_pdl(k, dim3(fa.ny, n_f), dim3(NT), sm, s, fa, ra, mode, (const T*)ext, fg,
+             (const TV*)vals, (typename Cx<T>::type*)inter);
 }
 
 template <typename T, int L, int CB>
@@ -403,11 +524,12 @@ static void cols_launch(const FftArgs& fa, int n_f, const void* inter, void* fha
                         cudaStream_t s) {
   using C = typename Cx<T>::type;
   constexpr int NT = (1 << L) / elems<T>();
-  const size_t sm = (size_t)CB * padded<T>(1 << L) * sizeof(C);
+  const size_t sm = ((size_t)CB * padded<T>(1 << L) + col_lanes<T>()) * sizeof(C);
   auto k = k_fft_cols_p2<T, L, CB>;
   cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   const int ncol = fa.nx / 2 + 1;
-  k<<<dim3((ncol + CB - 1) / CB, n_f), CB * NT, sm, s>>>(fa, (const C*)inter, (C*)fhat);
+  launch_pdl(k, dim3((ncol + CB - 1) / CB, n_f), dim3(CB * NT), sm, s, fa, (const C*)inter,
+             (C*)fhat);
 }
 
 }  // namespace p2
@@ -445,7 +567,7 @@ bool launch_fft_rows_p2(const FftArgs& fa, const RowArgs& ra, int n_f, bool fp64
 #undef FC2D_ROWS
 }
 
-bool launch_fft_cols_p2(const FftArgs& fa, int n_f, bool fp64, const void* inter, void* fhat,
+bool launch_fft_cols_p2(const FftArgs& fa, int n_f, bool fp64, void* inter, void* fhat,
                         cudaStream_t s) {
   const int L = ilog2_exact(fa.ny);
 #define FC2D_COLS(LL, CB32, CB64)                                  \
@@ -461,8 +583,18 @@ bool launch_fft_cols_p2(const FftArgs& fa, int n_f, bool fp64, const void* inter
     FC2D_COLS(8, 8, 4)
     FC2D_COLS(9, 4, 4)
     FC2D_COLS(10, 4, 2)
-    FC2D_COLS(11, 2, 2)
-    FC2D_COLS(12, 2, 1)
+    default: break;
+  }
+  // 4096-point FP32 columns: two coalesced passes (64 x 64)
+  switch (L) {
+    case 11:
+      if (fp64) p2::cols_launch<double, 11, 2>(fa, n_f, inter, fhat, s);
+      else p2::cols_launch<float, 11, 2>(fa, n_f, inter, fhat, s);
+      return true;
+    case 12:
+      if (fp64) p2::cols_launch<double, 12, 1>(fa, n_f, inter, fhat, s);
+      else p2::cols4k_launch(fa, n_f, inter, fhat, s);
+      return true;
     default: return false;
   }
 #undef FC2D_COLS
