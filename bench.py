@@ -43,7 +43,12 @@ FP64_PEAK_TFLOPS = 1.25   # GB300 FP64 (nominal; 152 SMs x 2 DFMA/clk x 2 flop x
 # on this workload, from one ncu capture of the current kernels (cold cache, serialised
 # launches; a scope with two kernels sums both).  A kernel changed after its capture
 # has no entry, and the roofline then reports traffic null.
-MEASURED_TRAFFIC = {}
+MEASURED_TRAFFIC = {
+    # k_cols4k_a (67410432 + 10120704) + k_cols4k_b (67525888 + 15047680)
+    ("mixed", "fft_cols"): 160104704,
+    # k_fft_rows_p2<float, float, 11>
+    ("mixed", "fft_rows_fused"): 70921216 + 19520256,
+}
 
 
 def peaks():
