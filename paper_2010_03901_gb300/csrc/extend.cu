@@ -16,6 +16,7 @@
 #include <vector>
 
 #include "fc2d_kernels.cuh"
+#include "interp.cuh"
 #include "plan_internal.h"
 
 namespace fc2d {
@@ -280,76 +281,20 @@ fc2d_status interp_weights_gpu(int n_strip, int M, int Cr, int B, double k1, int
   return st;
 }
 
-// Per call: value = sum_a wth[a] sum_b weta[b] F[(pb + a) mod B][s + b], accumulated in
-// TA (double for the FP64 form, float for the mixed form).  MM > 0: compile-time M.
-// One thread per (strip point, function).  VEC (float F, ldF a multiple of 4 and
-// ldF >= Cr + 12): the M values s..s+M-1 of a normal come from the three aligned float4
-// at (s & ~3).. and a register shift by s & 3, instead of M scalar loads.
+// One thread per (strip point, function); the arithmetic is interp_load/interp_apply
+// (interp.cuh), accumulated in TA (double for the FP64 form, float for the mixed form).
+// The weights are plan constants and are loaded before the wait on the blend kernel.
 template <int MM, typename TF, typename TW, typename TA, typename TV, bool VEC>
 __global__ void __launch_bounds__(256) k_interp(InterpArgs a, const TF* __restrict__ F,
                                                 TV* __restrict__ vals) {
   const int n = blockIdx.x * blockDim.x + threadIdx.x;
   const int f = blockIdx.y;
   if (n >= a.n_strip) return;
-  const int M = MM > 0 ? MM : a.M;
-  const int B = a.B, ld = a.ldF, ns = a.n_strip;
-  const TW* w = reinterpret_cast<const TW*>(a.w);
-  const int pb = __ldg(a.pb + n), s = __ldg(a.sb + n);
-  // the weights are plan constants: loaded before the wait on the blend kernel
-  TW weta[MM > 0 ? MM : kMaxM], wth[MM > 0 ? MM : kMaxM];
-#pragma unroll
-  for (int b = 0; b < (MM > 0 ? MM : kMaxM); ++b) {
-    if (b < M) weta[b] = __ldg(w + (size_t)(M + b) * ns + n);
-    if (b < M) wth[b] = __ldg(w + (size_t)b * ns + n);
-  }
+  const InterpPoint<MM, TW> q = interp_load<MM, TW>(a, n);
   pdl_wait();
   pdl_trigger();
-  const TF* Ff = F + (size_t)f * B * ld;
-  TA acc = 0;
-  if constexpr (VEC) {
-    static_assert(MM > 0 && MM <= 9, "vector path needs a compile-time M <= 9");
-    const int s0 = s & ~3, sh = s & 3;
-    // eta weights shifted into the 12-value window (s0 .. s0+11): the same for every row
-    TA ws[12];
-#pragma unroll
-    for (int b = 0; b < 12; ++b) {
-      const TA w0 = b < MM ? (TA)weta[b] : (TA)0;
-      const TA w1 = (b >= 1 && b - 1 < MM) ? (TA)weta[b >= 1 ? b - 1 : 0] : (TA)0;
-      const TA w2 = (b >= 2 && b - 2 < MM) ? (TA)weta[b >= 2 ? b - 2 : 0] : (TA)0;
-      const TA w3 = (b >= 3 && b - 3 < MM) ? (TA)weta[b >= 3 ? b - 3 : 0] : (TA)0;
-      ws[b] = sh == 0 ? w0 : sh == 1 ? w1 : sh == 2 ? w2 : w3;
-    }
-#pragma unroll
-    for (int ai = 0; ai < MM; ++ai) {
-      int pr = pb + ai;
-      pr = pr < 0 ? pr + B : (pr >= B ? pr - B : pr);
-      const float4* row = reinterpret_cast<const float4*>(Ff + (size_t)pr * ld + s0);
-      TA v = 0;
-#pragma unroll
-      for (int u = 0; u < 3; ++u) {
-        const float4 q = __ldg(row + u);
-        v = fma(ws[4 * u], (TA)q.x, v);
-        v = fma(ws[4 * u + 1], (TA)q.y, v);
-        v = fma(ws[4 * u + 2], (TA)q.z, v);
-        v = fma(ws[4 * u + 3], (TA)q.w, v);
-      }
-      acc = fma((TA)wth[ai], v, acc);
-    }
-  } else {
-#pragma unroll
-    for (int ai = 0; ai < (MM > 0 ? MM : kMaxM); ++ai) {
-      if (ai >= M) break;
-      int pr = pb + ai;
-      pr = pr < 0 ? pr + B : (pr >= B ? pr - B : pr);
-      const TF* row = Ff + (size_t)pr * ld + s;
-      TA v = 0;
-#pragma unroll
-      for (int b = 0; b < (MM > 0 ? MM : kMaxM); ++b)
-        if (b < M) v = fma((TA)weta[b], (TA)__ldg(row + b), v);
-      acc = fma((TA)wth[ai], v, acc);
-    }
-  }
-  vals[(size_t)f * ns + n] = (TV)acc;
+  const TF* Ff = F + (size_t)f * a.B * a.ldF;
+  vals[(size_t)f * a.n_strip + n] = (TV)interp_apply<MM, TF, TW, TA, VEC>(a, Ff, q);
 }
 
 void launch_interp(const InterpArgs& a, int n_f, bool fp64, const void* F, void* vals,

@@ -45,6 +45,10 @@ struct RowArgs {
   const int32_t* row_iv;
   const int32_t* row_strip_off;
   const int32_t* s_lin;
+  // strip values computed in the row kernel (mixed form, M = 8): the interpolation
+  // tables and the strip values F [n_f][B][ia.ldF]; F == nullptr: read `vals` instead
+  InterpArgs ia;
+  const float* F;
 };
 
 #if defined(__CUDACC__)
