@@ -95,6 +95,9 @@ def _roots(f, fp, n_samples: int, samples=None):
     steps.  ``samples`` may hold f(t_s) already."""
     th = 2 * np.pi * np.arange(n_samples + 1) / n_samples
     v = f(th) if samples is None else samples
+    # the curve is closed: the sample at 2 pi is the one at 0 (f(2 pi) may round
+    # differently and hide a root at theta = 0 between the two)
+    v = np.append(v[:-1], v[0])
     pos = v > 0
     idx = np.nonzero(pos[:-1] != pos[1:])[0]
     if len(idx) == 0:

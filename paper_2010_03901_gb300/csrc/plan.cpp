@@ -264,12 +264,16 @@ static void line_crossings(const Curve& c, int which, int nlines, double o, doub
   out.assign(nlines, {});
   std::vector<double> v(n_s + 1), ts(n_s + 1);
   const double two_pi = 2.0 * M_PI;
-  for (int s = 0; s <= n_s; ++s) {
+  for (int s = 0; s < n_s; ++s) {
     ts[s] = two_pi * s / n_s;
     double x, y;
     c.eval(ts[s], x, y);
     v[s] = which == 0 ? x : y;
   }
+  // the curve is closed: the sample at 2 pi is the sample at 0 (evaluated at 2 pi it
+  // could round differently and hide a crossing at theta = 0 between the two)
+  ts[n_s] = two_pi;
+  v[n_s] = v[0];
   for (int s = 0; s < n_s; ++s) {
     double lo = std::min(v[s], v[s + 1]), hi = std::max(v[s], v[s + 1]);
     if (lo == hi) continue;
@@ -446,10 +450,18 @@ extern "C" fc2d_status fc2d_plan(const fc2d_boundary* boundary, const fc2d_grid*
   const double tang_tol = 1e-7 * std::max(nx, ny) * h;
   line_crossings(cv, 1, ny, b0, h, n_s, tang_tol, rowc);
   line_crossings(cv, 0, nx, a0, h, n_s, tang_tol, colc);
-  for (auto& r : rowc)
-    if (r.size() % 2) return fail(set_error(FC2D_ERR_GEOMETRY, "odd number of row crossings"));
-  for (auto& r : colc)
-    if (r.size() % 2) return fail(set_error(FC2D_ERR_GEOMETRY, "odd number of column crossings"));
+  for (int j = 0; j < ny; ++j)
+    if (rowc[j].size() % 2)
+      return fail(set_error(FC2D_ERR_GEOMETRY,
+                            "odd number of crossings of grid row " + std::to_string(j) +
+                                " (y = " + std::to_string(b0 + h * j) + ") with the curve: " +
+                                std::to_string(rowc[j].size())));
+  for (int i = 0; i < nx; ++i)
+    if (colc[i].size() % 2)
+      return fail(set_error(FC2D_ERR_GEOMETRY,
+                            "odd number of crossings of grid column " + std::to_string(i) +
+                                " (x = " + std::to_string(a0 + h * i) + ") with the curve: " +
+                                std::to_string(colc[i].size())));
   std::vector<double> xs(nx), ys(ny);
   for (int i = 0; i < nx; ++i) xs[i] = a0 + h * double(i);
   for (int j = 0; j < ny; ++j) ys[j] = b0 + h * double(j);

@@ -74,3 +74,17 @@ def test_matching_stencils_give_the_oracle_matching_values(both):
     st = OF.matching_stencils(geo)
     ref = OF.matching_values(geo, st, W.grid_values(w, f), fb)
     assert np.abs(fD - ref[:, :d - 1]).max() < 1e-13 * np.abs(ref).max()
+
+
+def test_plans_of_the_eight_star_workload():
+    """The library's plan builds on all eight stars of the batched workload (several of
+    them symmetric about y = 0 with a grid row on it), and on the smallest one its strip
+    set and inside count equal the oracle's."""
+    stars = W.stars8()
+    for w in stars:
+        r = host_plan.run(w)
+        assert r["status"] == 0, (w.name, r["error"])
+    w = min(stars, key=lambda s: s.grid.nx)
+    r = host_plan.run(w)
+    geo = OG.build_geometry(w)
+    assert np.array_equal(np.sort(r["strip_lin"]), np.sort(geo.strip_lin))

@@ -116,3 +116,15 @@ def test_clockwise_input_is_reoriented():
     cv = G.make_curve(cw)
     nx, ny = cv.normal(np.array([0.3]))
     assert nx[0] > 0.9  # outward at theta = 0.3
+
+
+@pytest.mark.parametrize("y", [0.0, -1e-17, 1e-17, 5e-324])
+def test_row_through_theta_zero_crosses_twice(y):
+    """A row through the curve's point at theta = 0 (where the sample sequence closes):
+    the star r = 1 + a cos 3 theta meets y = 0 at x = 1 + a and x = -(1 - a), and a row
+    within rounding of y = 0 must find both crossings."""
+    a = 0.1113
+    cv = G.make_curve(W.star(a, 3))
+    X = G.crossings(cv, "row", y, 16 * 608)
+    assert len(X) == 2, X
+    assert abs(X[0] + (1 - a)) < 1e-12 and abs(X[1] - (1 + a)) < 1e-12, X

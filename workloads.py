@@ -186,6 +186,61 @@ def fit_grid(xmin, xmax, ymin, ymax, h, C=27, k1=None, margin=4) -> Grid:
                 h=h, nx=nx, ny=ny)
 
 
+def star_min_radius(a: float, k: int, n: int = 8192) -> float:
+    """Smallest radius of curvature of r = 1 + a cos(k theta) (sampled): 1/max kappa with
+    kappa = |r^2 + 2 r'^2 - r r''| / (r^2 + r'^2)^(3/2)."""
+    th = 2 * np.pi * np.arange(n) / n
+    r = 1 + a * np.cos(k * th)
+    r1 = -a * k * np.sin(k * th)
+    r2 = -a * k * k * np.cos(k * th)
+    kappa = np.abs(r * r + 2 * r1 * r1 - r * r2) / (r * r + r1 * r1) ** 1.5
+    return float(1.0 / kappa.max())
+
+
+def square_grid_for(boundary: Boundary, N: int, rho_min: float, C: int = 27,
+                    margin: int = 4) -> tuple:
+    """An N x N grid centred on the curve's bounding box, and k1.  The strip step is
+    k1 = min(h, rho_min / (2C)) (the strip C k1 stays within half the smallest radius of
+    curvature), and h = (W + 2 C k1) / (N - 2 margin) with W the larger side of the
+    bounding box, so the strip ends `margin` cells inside the grid on every side."""
+    px, py = boundary.polygon(8192)
+    xmin, xmax, ymin, ymax = px.min(), px.max(), py.min(), py.max()
+    W = max(xmax - xmin, ymax - ymin)
+    cap = rho_min / (2 * C)
+    h = W / (N - 2 * margin - 2 * C)           # k1 = h
+    k1 = h
+    if h > cap:
+        k1 = cap
+        h = (W + 2 * C * k1) / (N - 2 * margin)
+    xc, yc = 0.5 * (xmin + xmax), 0.5 * (ymin + ymax)
+    return Grid(a0=xc - 0.5 * N * h, b0=yc - 0.5 * N * h, h=h, nx=N, ny=N), k1
+
+
+STAR_SIZES = (256, 384, 512, 640, 768, 1024, 1536, 2048)
+
+
+def stars8(seed: int = 4, sizes=STAR_SIZES) -> list:
+    """Eight stars r = 1 + a cos(k theta), a ~ U[0.1, 0.3], k ~ U{3..7} (seeded), each on
+    a square grid: the more concave a star (smaller radius of curvature), the larger its
+    grid.  B: the multiple of 32 at or above the perimeter over h."""
+    u = uniform(seed, 16)
+    shapes = [(0.1 + 0.2 * u[2 * i], 3 + int(5 * u[2 * i + 1])) for i in range(8)]
+    rho = [star_min_radius(a, k) for a, k in shapes]
+    order = np.argsort(rho)[::-1]              # least concave first -> smallest grid
+    out = [None] * 8
+    for rank, i in enumerate(order):
+        a, k = shapes[i]
+        bd = star(a, k)
+        N = sorted(sizes)[rank]
+        grid, k1 = square_grid_for(bd, N, rho[i])
+        px, py = bd.polygon(8192)
+        L = float(np.sum(np.hypot(np.diff(np.append(px, px[0])), np.diff(np.append(py, py[0])))))
+        B = int(math.ceil(L / grid.h / 32.0)) * 32
+        out[i] = Workload(f"star{i}_{N}", bd, grid, Params(B=B, k1=k1),
+                          note=f"a={a:.4f} k={k} rho_min={rho[i]:.4f}")
+    return out
+
+
 def workload(name: str, **overrides) -> Workload:
     w = WORKLOADS[name]
     if overrides:
@@ -290,6 +345,28 @@ class TrigSum:
             ph = p * x + q * y
             out = out + s * (al * np.cos(ph) + be * np.sin(ph))
         return out
+
+
+def trig_grid(t: TrigSum, xs: np.ndarray, ys: np.ndarray) -> np.ndarray:
+    """t on the tensor grid (ys x xs), shape [len(ys)][len(xs)], evaluated separably:
+    cos(px + qy) = cos px cos qy - sin px sin qy, sin(px + qy) = sin px cos qy +
+    cos px sin qy, so the sum is Y^T G X with X = [cos px; sin px], Y = [cos qy; sin qy]."""
+    ps = np.unique(t.p)
+    qs = np.unique(t.q)
+    pi = {v: i for i, v in enumerate(ps)}
+    qi = {v: i for i, v in enumerate(qs)}
+    npx, nqy = len(ps), len(qs)
+    G = np.zeros((2 * nqy, 2 * npx))
+    s = 1.0 / math.sqrt(len(t.p))
+    for p, q, al, be in zip(t.p, t.q, t.alpha, t.beta):
+        a, b = pi[p], qi[q]
+        G[b, a] += s * al               # cos qy cos px
+        G[nqy + b, npx + a] -= s * al   # sin qy sin px
+        G[b, npx + a] += s * be         # cos qy sin px
+        G[nqy + b, a] += s * be         # sin qy cos px
+    X = np.concatenate([np.cos(np.outer(ps, xs)), np.sin(np.outer(ps, xs))])
+    Y = np.concatenate([np.cos(np.outer(qs, ys)), np.sin(np.outer(qs, ys))])
+    return Y.T @ (G @ X)
 
 
 def trig_sum(deg: int, seed: int) -> TrigSum:
