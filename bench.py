@@ -419,6 +419,86 @@ def poisson_star1024(fc2d, torch, dev, solves=3):
             "gmres": plan.fc2d_poisson_info()}
 
 
+def stars8_batched(fc2d, torch, dev, replays=10):
+    """Eight stars (grids 256^2..2048^2 by concavity), 32 trigonometric sums per domain,
+    fc2d_extend_coeffs per domain, the 8 calls captured in one CUDA graph and replayed;
+    mixed and FP64.  Inputs are made on the host and copied once; the error is checked
+    against the oracle on function 0 of the smallest and of the largest domain."""
+    from oracle import fc2d as OF
+    from oracle import geometry as OG
+    from oracle.fc_matrices import load_fc_matrices
+    stars = W.stars8()
+    n_f = 32
+    inputs = []
+    for i, w in enumerate(stars):
+        g, p = w.grid, w.params
+        probe = fc2d.fc2d_plan(w.boundary.arrays(), (g.a0, g.b0, g.h, g.nx, g.ny),
+                               dict(B=p.B, k1=p.k1))
+        xy = probe.fc2d_boundary_points()
+        probe.fc2d_destroy()
+        fs = W.star_functions(w, i, n_f)
+        xs, ys = g.coords()
+        fg = torch.empty((n_f, g.ny, g.nx), dtype=torch.float64, device=dev)
+        for m, t in enumerate(fs):
+            fg[m].copy_(torch.from_numpy(W.trig_grid(t, xs, ys)))
+        fb = torch.tensor(np.stack([t(xy[:, 0], xy[:, 1]) for t in fs]), device=dev)
+        inputs.append((w, fs, fg, fb))
+    points = n_f * sum(w.grid.nx * w.grid.ny for w in stars)
+    out = {"workload": "8 stars r = 1 + a cos k theta, a ~ U[0.1,0.3], k ~ U{3..7} (seed 4), "
+                       "grids " + ", ".join(f"{w.grid.nx}^2" for w in sorted(
+                           stars, key=lambda s: s.grid.nx)) +
+                       ", 32 degree-12 trigonometric sums per domain",
+           "points_per_step": points, "unit": UNIT, "launch": "one CUDA graph of the 8 calls"}
+    small = min(range(8), key=lambda i: stars[i].grid.nx)
+    large = max(range(8), key=lambda i: stars[i].grid.nx)
+    for name, prec, dt in (("mixed", fc2d.FC2D_MIXED, torch.float32),
+                           ("fp64", fc2d.FC2D_FP64, torch.float64)):
+        runs = []
+        for w, fs, fg, fb in inputs:
+            g, p = w.grid, w.params
+            plan = fc2d.fc2d_plan(w.boundary.arrays(), (g.a0, g.b0, g.h, g.nx, g.ny),
+                                  dict(B=p.B, k1=p.k1), precision=prec)
+            fh = torch.empty((n_f, g.ny, g.nx // 2 + 1, 2), dtype=dt, device=dev)
+            runs.append((plan, fg, fb, fh))
+        s = torch.cuda.Stream(dev)
+        with torch.cuda.stream(s):
+            for plan, fg, fb, fh in runs:
+                plan.fc2d_extend_coeffs(n_f, fg, fb, fh, s)
+        s.synchronize()
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph, stream=s):
+            for plan, fg, fb, fh in runs:
+                plan.fc2d_extend_coeffs(n_f, fg, fb, fh, s)
+        for _ in range(3):
+            graph.replay()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(replays):
+            graph.replay()
+        e1.record()
+        torch.cuda.synchronize()
+        for plan, *_ in runs:
+            plan.fc2d_sync_status()
+        ms = e0.elapsed_time(e1) / replays
+        errs = {}
+        for i in (small, large):
+            w, fs, _, _ = inputs[i]
+            geo = OG.build_geometry(w)
+            st = OF.matching_stencils(geo)
+            xs, ys = w.grid.coords()
+            ref = OF.coefficients(OF.extension(geo, load_fc_matrices(), W.trig_grid(fs[0], xs, ys),
+                                               OF.boundary_values(geo, fs[0]), st))
+            got = runs[i][3][0].cpu().numpy().astype(np.float64)
+            got = got[..., 0] + 1j * got[..., 1]
+            errs[w.name] = float(np.abs(got - ref).max() / np.abs(ref).max())
+        out[name] = {"value": points / (ms / 1e3), "ms_per_step": ms, "replays": replays,
+                     "err_vs_oracle": errs}
+        for plan, *_ in runs:
+            plan.fc2d_destroy()
+    return out
+
+
 def run_gpu(args):
     import torch
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -486,6 +566,7 @@ def run_gpu(args):
                 line[name]["err_vs_oracle"] = err
     if rank == 0 and world == 1 and not args.no_extra:
         line["poisson_star1024"] = poisson_star1024(fc2d, torch, dev)
+        line["stars8_batched"] = stars8_batched(fc2d, torch, dev)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

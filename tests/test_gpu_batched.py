@@ -1,0 +1,88 @@
+"""The batched eight-star workload on the GPU: 32 functions per domain in one call,
+non-power-of-two grids, against the oracle on sampled functions, and the same calls
+replayed from one CUDA graph."""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import fc2d as OF
+from oracle import geometry as OG
+from oracle.fc_matrices import load_fc_matrices
+
+pytestmark = pytest.mark.gpu
+
+N_F = 32
+SAMPLED = (0, 17, 31)
+
+
+def rel(a, b):
+    return float(np.abs(a - b).max() / np.abs(b).max())
+
+
+def setup(w, index, fc2d, torch, precision):
+    g, p = w.grid, w.params
+    plan = fc2d.fc2d_plan(w.boundary.arrays(), (g.a0, g.b0, g.h, g.nx, g.ny),
+                          dict(B=p.B, k1=p.k1), precision=precision)
+    xy = plan.fc2d_boundary_points()
+    fs = W.star_functions(w, index, N_F)
+    xs, ys = g.coords()
+    dev = torch.device("cuda:0")
+    fg = torch.tensor(np.stack([W.trig_grid(t, xs, ys) for t in fs]), device=dev)
+    fb = torch.tensor(np.stack([t(xy[:, 0], xy[:, 1]) for t in fs]), device=dev)
+    dt = torch.float64 if precision == fc2d.FC2D_FP64 else torch.float32
+    fh = torch.zeros((N_F, g.ny, g.nx // 2 + 1, 2), dtype=dt, device=dev)
+    return plan, fs, fg, fb, fh
+
+
+@pytest.fixture(scope="module")
+def stars():
+    return W.stars8()
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("nx", [256, 384])
+def test_batched_star_against_oracle(stars, nx, precision):
+    torch = pytest.importorskip("torch")
+    from paper_2010_03901_gb300 import fc2d
+    index, w = next((i, s) for i, s in enumerate(stars) if s.grid.nx == nx)
+    prec = fc2d.FC2D_FP64 if precision == "fp64" else fc2d.FC2D_MIXED
+    plan, fs, fg, fb, fh = setup(w, index, fc2d, torch, prec)
+    plan.fc2d_extend_coeffs(N_F, fg, fb, fh)
+    plan.fc2d_sync_status()
+    got = fh.cpu().numpy().astype(np.float64)
+    geo = OG.build_geometry(w)
+    st = OF.matching_stencils(geo)
+    mats = load_fc_matrices()
+    xs, ys = w.grid.coords()
+    tol = 1e-12 if precision == "fp64" else 1e-6
+    for m in SAMPLED:
+        ref = OF.coefficients(OF.extension(geo, mats, W.trig_grid(fs[m], xs, ys),
+                                           OF.boundary_values(geo, fs[m]), st))
+        gm = got[m][..., 0] + 1j * got[m][..., 1]
+        assert rel(gm, ref) < tol, (w.name, m, rel(gm, ref))
+
+
+def test_graph_replay_equals_eager(stars):
+    torch = pytest.importorskip("torch")
+    from paper_2010_03901_gb300 import fc2d
+    runs = []
+    for nx in (256, 384):
+        index, w = next((i, s) for i, s in enumerate(stars) if s.grid.nx == nx)
+        runs.append(setup(w, index, fc2d, torch, fc2d.FC2D_MIXED))
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        for plan, _, fg, fb, fh in runs:       # eager (also sizes the workspaces)
+            plan.fc2d_extend_coeffs(N_F, fg, fb, fh, s)
+    s.synchronize()
+    eager = [fh.clone() for *_, fh in runs]
+    for *_, fh in runs:
+        fh.zero_()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=s):
+        for plan, _, fg, fb, fh in runs:
+            plan.fc2d_extend_coeffs(N_F, fg, fb, fh, s)
+    graph.replay()
+    torch.cuda.synchronize()
+    for (plan, *_), e, (*_, fh) in zip(runs, eager, runs):
+        plan.fc2d_sync_status()
+        assert torch.equal(e, fh)

@@ -369,6 +369,11 @@ def trig_grid(t: TrigSum, xs: np.ndarray, ys: np.ndarray) -> np.ndarray:
     return Y.T @ (G @ X)
 
 
+def star_functions(w: Workload, index: int, n: int = 32) -> list:
+    """The n trigonometric sums (degree 12) of star `index` of the batched workload."""
+    return [trig_sum(12, 4 * 1000 + 32 * index + m) for m in range(n)]
+
+
 def trig_sum(deg: int, seed: int) -> TrigSum:
     pq = [(p, q) for p in range(0, deg + 1) for q in range(-deg, deg + 1)
           if abs(p) + abs(q) <= deg and (p > 0 or q >= 0)]
