@@ -199,10 +199,8 @@ def run_reference(args):
 # --------------------------------------------------------------------------- #
 # the GPU arm
 # --------------------------------------------------------------------------- #
-def algorithmic(plan, w, fp64, interp_in_rows=False):
-    """Algorithmic bytes and flops per launch of each kernel (one function).  With
-    interp_in_rows the row kernel also computes the strip values: it reads the 2M
-    interpolation weights and two indices of each strip point instead of its value."""
+def algorithmic(plan, w, fp64):
+    """Algorithmic bytes and flops per launch of each kernel scope (one function)."""
     g = w.grid
     nx, ny = g.nx, g.ny
     nh = nx // 2
@@ -214,14 +212,20 @@ def algorithmic(plan, w, fp64, interp_in_rows=False):
     M = w.params.M
     fft_rows_flops = ny * (5.0 * nh * math.log2(nh) + 10.0 * (nh + 1))
     fft_cols_flops = (nh + 1) * 5.0 * ny * math.log2(ny)
-    strip_bytes = (2 * M * esz + 8 + 4) if interp_in_rows else (esz + 4)
+    gather = {"bytes": B * ((M - 1) * M * 12 + (w.params.d - 1) * M * 8 + (Cr + 1) * esz),
+              "flops": B * 2.0 * ((M - 1) * M + (w.params.d - 1) * M + Cr * w.params.d)}
+    interp = {"bytes": plan.n_strip * (16 + esz), "flops": plan.n_strip * 2.0 * (M * M + M)}
     return {
-        "fft_rows_fused": {"bytes": 8 * plan.n_inside + strip_bytes * plan.n_strip + spec,
+        "fft_rows_fused": {"bytes": 8 * plan.n_inside + (esz + 4) * plan.n_strip + spec,
                            "flops": fft_rows_flops},
+        # blend + interpolation in one kernel: the gather's taps, the weights (2M x 4 B),
+        # the grouped index and packed nodes (8 B) and the value (4 B) of each strip point
+        "gather_blend_interp_tc": {
+            "bytes": gather["bytes"] - B * (Cr + 1) * esz + plan.n_strip * (2 * M * 4 + 8 + 4),
+            "flops": gather["flops"] + interp["flops"]},
         "fft_cols": {"bytes": 2 * spec, "flops": fft_cols_flops},
-        "interp": {"bytes": plan.n_strip * (16 + esz), "flops": plan.n_strip * 2.0 * (M * M + M)},
-        "gather_blend": {"bytes": B * ((M - 1) * M * 12 + (w.params.d - 1) * M * 8 + (Cr + 1) * esz),
-                         "flops": B * 2.0 * ((M - 1) * M + (w.params.d - 1) * M + Cr * w.params.d)},
+        "interp": interp,
+        "gather_blend": gather,
     }
 
 
@@ -359,7 +363,7 @@ def measure(fc2d, torch, w, precision, K, warmup, world, dev, fg_h, fb_h, sample
     e2e_ms = max_over_ranks(e0.elapsed_time(e1) / Ke, world, dev)
     # roofline of the dominant kernel
     hbm, src = peaks()
-    alg = algorithmic(plan, w, fp64, interp_in_rows="interp" not in prof)
+    alg = algorithmic(plan, w, fp64)
     dom = max(prof, key=lambda k: prof[k][1])
     launches, tot_ms = prof[dom]
     avg_s = tot_ms / launches / 1e3

@@ -27,6 +27,7 @@
 #include <cstdint>
 
 #include "fc2d_kernels.cuh"
+#include "interp.cuh"
 #include "plan_internal.h"
 
 namespace fc2d {
@@ -459,6 +460,269 @@ __global__ void __launch_bounds__(256, 2) k_gather_blend_tc(GatherArgs g, TcArgs
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
                  "r"(kTcTmemCols));
   }
+}
+
+// ------------------------------------------------------------------------- //
+// Blend and interpolation in one kernel (mixed form, M = 8).  CTA (c, f) computes the
+// kTcComputed = 64 normals c*kTcOwned + i (mod B) of function f as above (MMA N = 64,
+// 16 warps, one gather pass), keeps their strip values in a shared [64][ldS] tile (zero
+// padded; ldS a multiple of 4, >= Cr + 12, and not 16 mod 32 words so that neighbouring
+// rows fall in different banks) and interpolates the strip points it owns (Section 3.4)
+// from that tile, two per thread in flight, writing the strip-point values; F is not
+// written.  B = 8192 gives 144 CTAs: one wave on 152 SMs.
+// ------------------------------------------------------------------------- //
+constexpr int kGiThreads = kTcComputed * 8;
+constexpr int kGiTmemCols = 128;  // two tiles of 64 columns
+constexpr int kGiStageOff = 2 * kMaxCrPad * 32 + 2 * kTcComputed * 32;
+constexpr int kGiBarOff = kGiStageOff + kTcComputed * kTcMaxLd * 4;
+constexpr int kGiSmem = kGiBarOff + 16;
+
+struct OwnArgs {
+  const int32_t* off;   // [n_own + 1]
+  const int32_t* k;     // [n_strip] strip index
+  const int32_t* pack;  // [n_strip] local first normal | first fine node << 8
+  const float* w;       // [16][n_strip] theta weights then eta weights
+  int n_own, n_strip;
+  float* vals;          // [n_f][n_strip]
+};
+
+__global__ void __launch_bounds__(kGiThreads, 1) k_gather_interp_tc(GatherArgs g, TcArgs a,
+                                                                      OwnArgs o) {
+  constexpr int MM = 8;
+  extern __shared__ __align__(1024) unsigned char smem[];
+  unsigned char* a_hi = smem;
+  unsigned char* a_lo = smem + kMaxCrPad * 32;
+  unsigned char* c_hi = smem + 2 * kMaxCrPad * 32;
+  unsigned char* c_lo = c_hi + kTcComputed * 32;
+  float* stage = reinterpret_cast<float*>(smem + kGiStageOff);  // [64][ldS]
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + kGiBarOff);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mbar + 1);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int c = blockIdx.x, f = blockIdx.y;
+  const int ldS = a.ldF;  // staging row length (see the launcher)
+  const int nqt = (a.Cr + kTcQTile - 1) / kTcQTile;
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                 ::"r"(smem_u32(tmem_slot)), "r"(kGiTmemCols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(mbar)));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  for (int idx = tid; idx < kTcComputed * (ldS - a.Cr - 1); idx += blockDim.x) {
+    const int r = idx / (ldS - a.Cr - 1);
+    stage[r * ldS + a.Cr + 1 + (idx - r * (ldS - a.Cr - 1))] = 0.f;
+  }
+  {
+    constexpr int kPer = (kMaxCrPad * 8 + kGiThreads - 1) / kGiThreads;
+    float hi[kPer], lo[kPer];
+#pragma unroll
+    for (int u = 0; u < kPer; ++u) {
+      const int idx = tid + u * kGiThreads, q = idx >> 3, k = idx & 7;
+      const bool on = idx < kMaxCrPad * 8 && q < a.Cr && k < a.d;
+      hi[u] = on ? __ldg(a.Ar_hi + q * a.d + k) : 0.f;
+      lo[u] = on ? __ldg(a.Ar_lo + q * a.d + k) : 0.f;
+    }
+#pragma unroll
+    for (int u = 0; u < kPer; ++u) {
+      const int idx = tid + u * kGiThreads, q = idx >> 3, k = idx & 7;
+      if (idx < kMaxCrPad * 8) {
+        *reinterpret_cast<float*>(a_hi + kmaj_off(q, k)) = hi[u];
+        *reinterpret_cast<float*>(a_lo + kmaj_off(q, k)) = lo[u];
+      }
+    }
+  }
+  // matching values and Gram coefficients of the 64 normals into the C tiles
+  const int s = lane & 7, g0 = lane & ~7;
+  const int ln = warp * 4 + (lane >> 3);
+  {
+    const int M = MM, d = g.d, NS = M - 1;
+    const bool star_lane = s < NS;
+    const int pp = (c * kTcOwned + ln) % g.B;
+    const size_t base = ((size_t)pp * NS + (star_lane ? s : 0)) * M;
+    int32_t id[MM];
+    double wv[MM], wnv[MM], qv[kMaxD];
+#pragma unroll
+    for (int e = 0; e < MM; ++e) {
+      id[e] = star_lane ? __ldg(g.gidx + base + e) : 0;
+      wv[e] = star_lane ? __ldg(g.gw + base + e) : 0.0;
+    }
+    const double* wn = g.wn + ((size_t)pp * (d - 1) + (s < d - 1 ? s : 0)) * M;
+#pragma unroll
+    for (int e = 0; e < MM; ++e) wnv[e] = s < d - 1 ? __ldg(wn + e) : 0.0;
+#pragma unroll
+    for (int i = 0; i < kMaxD; ++i) qv[i] = (s < d && i < d) ? __ldg(g.Q + i * d + s) : 0.0;
+    pdl_wait();
+    pdl_trigger();
+    const double* fg = g.f_grid + (size_t)f * g.grid_stride;
+    const double* fb = g.f_bdry + (size_t)f * g.n_bdry;
+    double val[MM];
+#pragma unroll
+    for (int e = 0; e < MM; ++e) {
+      const int32_t k = id[e];
+      val[e] = star_lane ? __ldg(k >= 0 ? fg + k : fb + (-1 - k)) : 0.0;
+    }
+    const double fbp = __ldg(fb + pp);
+    double star = 0.0;
+#pragma unroll
+    for (int e = 0; e < MM; ++e) star = fma(wv[e], val[e], star);
+    double acc = wnv[0] * fbp;
+#pragma unroll
+    for (int e = 1; e < MM; ++e) acc = fma(wnv[e], __shfl_sync(0xffffffffu, star, g0 + e - 1), acc);
+    const double fD = s < d - 1 ? acc : (s == d - 1 ? fbp : 0.0);
+    double cs = 0.0;
+#pragma unroll
+    for (int i = 0; i < kMaxD; ++i) {
+      const double v = __shfl_sync(0xffffffffu, fD, g0 + i);
+      if (i < d) cs = fma(qv[i], v, cs);
+    }
+    const double v = s < d ? cs : 0.0;
+    const float hi = to_tf32((float)v);
+    *reinterpret_cast<float*>(c_hi + kmaj_off(ln, s)) = hi;
+    *reinterpret_cast<float*>(c_lo + kmaj_off(ln, s)) = (float)(v - (double)hi);
+    if (s == 0) stage[ln * ldS] = (float)fbp;
+  }
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+  if (tid == 0) {
+    const uint32_t idesc = idesc_tf32(kTcQTile, kTcComputed);
+    const uint64_t dch = umma_desc(smem_u32(c_hi), 128, 256);
+    const uint64_t dcl = umma_desc(smem_u32(c_lo), 128, 256);
+    for (int t = 0; t < nqt; ++t) {
+      const uint32_t dt = tmem + (uint32_t)(t * kTcComputed);
+      const uint64_t dah = umma_desc(smem_u32(a_hi) + t * kTcQTile * 32, 128, 256);
+      const uint64_t dal = umma_desc(smem_u32(a_lo) + t * kTcQTile * 32, 128, 256);
+      asm volatile(
+          "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+          "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n"
+          ::"r"(dt), "l"(dah), "l"(dch), "r"(idesc), "r"(0));
+      asm volatile(
+          "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+          "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n"
+          ::"r"(dt), "l"(dah), "l"(dcl), "r"(idesc), "r"(1));
+      asm volatile(
+          "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+          "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n"
+          ::"r"(dt), "l"(dal), "l"(dch), "r"(idesc), "r"(1));
+    }
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+        ::"r"(smem_u32(mbar)) : "memory");
+  }
+  uint32_t done = 0;
+  for (uint32_t it = 0; it < kSpinLimit && !done; ++it) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(done) : "r"(smem_u32(mbar)), "r"(0) : "memory");
+  }
+  if (!done) {
+    if (tid == 0) atomicExch(a.status, (int)FC2D_ERR_TIMEOUT);
+    for (uint32_t it = 0; it < kSpinLimit && !done; ++it) {
+      asm volatile(
+          "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+          "selp.u32 %0, 1, 0, p;\n\t}\n"
+          : "=r"(done) : "r"(smem_u32(mbar)), "r"(0) : "memory");
+    }
+  }
+  done = __all_sync(0xffffffffu, done != 0) ? 1u : 0u;
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const int quarter = warp & 3, t = warp >> 2;
+  if (done && t < nqt) {
+    // lanes = fine points 128 t + 32 quarter + lane; columns = the 64 normals
+    uint32_t r[kTcComputed];
+    const uint32_t addr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(t * kTcComputed);
+#pragma unroll
+    for (int h = 0; h < kTcComputed / 32; ++h) {
+      uint32_t* rr = r + 32 * h;
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+          "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+          "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+          : "=r"(rr[0]), "=r"(rr[1]), "=r"(rr[2]), "=r"(rr[3]), "=r"(rr[4]), "=r"(rr[5]),
+            "=r"(rr[6]), "=r"(rr[7]), "=r"(rr[8]), "=r"(rr[9]), "=r"(rr[10]), "=r"(rr[11]),
+            "=r"(rr[12]), "=r"(rr[13]), "=r"(rr[14]), "=r"(rr[15]), "=r"(rr[16]),
+            "=r"(rr[17]), "=r"(rr[18]), "=r"(rr[19]), "=r"(rr[20]), "=r"(rr[21]),
+            "=r"(rr[22]), "=r"(rr[23]), "=r"(rr[24]), "=r"(rr[25]), "=r"(rr[26]),
+            "=r"(rr[27]), "=r"(rr[28]), "=r"(rr[29]), "=r"(rr[30]), "=r"(rr[31])
+          : "r"(addr + 32u * h));
+    }
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+    const int q = t * kTcQTile + quarter * 32 + lane;
+    if (q < a.Cr) {
+#pragma unroll
+      for (int nl = 0; nl < kTcComputed; ++nl) stage[nl * ldS + 1 + q] = __uint_as_float(r[nl]);
+    }
+  }
+  __syncthreads();
+  if (done) {
+    // the strip points owned by this CTA (Section 3.4), from the shared tile
+    InterpArgs ia{};
+    ia.M = MM;
+    ia.B = kTcComputed;  // local rows: no wrap inside the tile
+    ia.ldF = ldS;
+    const int o0 = __ldg(o.off + c), o1 = __ldg(o.off + c + 1);
+    auto load = [&](int idx, InterpPoint<MM, float>& q) {
+      const int pk = __ldg(o.pack + idx);
+      q.pb = pk & 0xFF;
+      q.s = pk >> 8;
+#pragma unroll
+      for (int b = 0; b < MM; ++b) {
+        q.th[b] = __ldg(o.w + (size_t)b * o.n_strip + idx);
+        q.eta[b] = __ldg(o.w + (size_t)(MM + b) * o.n_strip + idx);
+      }
+    };
+    const int step = blockDim.x;
+    for (int idx = o0 + tid; idx < o1; idx += 2 * step) {
+      const int idx2 = idx + step;
+      InterpPoint<MM, float> q0, q1;
+      load(idx, q0);
+      const int k0 = __ldg(o.k + idx);
+      int k1 = -1;
+      if (idx2 < o1) {
+        load(idx2, q1);
+        k1 = __ldg(o.k + idx2);
+      }
+      o.vals[(size_t)f * o.n_strip + k0] = interp_apply<MM, float, float, float, true>(ia, stage, q0);
+      if (k1 >= 0)
+        o.vals[(size_t)f * o.n_strip + k1] = interp_apply<MM, float, float, float, true>(ia, stage, q1);
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(kGiTmemCols));
+  }
+}
+
+fc2d_status launch_gather_interp_tc(const GatherArgs& g, int n_f, int ldS, const float* Ar_hi,
+                                    const float* Ar_lo, const int32_t* own_off,
+                                    const int32_t* own_k, const int32_t* own_pack,
+                                    const float* own_w, int n_own, int n_strip, float* vals,
+                                    int* status, cudaStream_t s) {
+  if (g.Cr > kMaxCrPad || g.d > 8 || g.M != 8 || ldS % 4 || ldS < g.Cr + 12 ||
+      ldS + 4 > kTcMaxLd || !own_off)
+    return set_error(FC2D_ERR_UNSUPPORTED, "blend + interpolation kernel: M = 8, d <= 8");
+  TcArgs a{};
+  a.n_cols = n_f * g.B;
+  a.Cr = g.Cr;
+  a.d = g.d;
+  a.ldF = (ldS % 32 == 16) ? ldS + 4 : ldS;  // staging rows: avoid a 16-word stride
+  a.ncr_pad = (g.Cr + 15) / 16 * 16;
+  a.Ar_hi = Ar_hi;
+  a.Ar_lo = Ar_lo;
+  a.status = status;
+  OwnArgs o{own_off, own_k, own_pack, own_w, n_own, n_strip, vals};
+  cudaFuncSetAttribute(k_gather_interp_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kGiSmem);
+  return cuda_check(launch_pdl(k_gather_interp_tc, dim3(n_own, n_f), dim3(kGiThreads),
+                               (size_t)kGiSmem, s, g, a, o),
+                    "blend + interpolation launch");
 }
 
 fc2d_status launch_gather_blend_tc(const GatherArgs& g, int n_f, int ldF, const float* Ar_hi,

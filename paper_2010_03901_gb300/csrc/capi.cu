@@ -164,19 +164,20 @@ fc2d_status mixed_blend(fc2d_plan_s* p, int n_f, const double* fg, const double*
                          p->dev.Ar_hi, p->dev.Ar_lo, static_cast<float*>(F), p->dev.status, s);
 }
 
-// The mixed form with M = 8 and power-of-two rows of 64..8192 points computes the
-// strip-point values inside the row DFT kernel (from F, with the plan's weights).
-bool strip_values_in_rows(const fc2d_plan_s* p) {
-  const int h = p->grid.nx / 2;
-  return p->prm.precision == FC2D_MIXED && p->prm.M == 8 && p->prm.d <= 8 &&
-         p->grid.nx % 2 == 0 && h >= 32 && h <= 4096 && (h & (h - 1)) == 0;
-}
-
 // Steps 5 and 6 into workspace: strip values F, then the strip-point values.
 fc2d_status strip_values(fc2d_plan_s* p, int n_f, const double* fg, const double* fb,
                          const Layout& L, cudaStream_t s) {
   const bool f64 = p->prm.precision == FC2D_FP64;
   void* F = ws(p, L.oF);
+  if (!f64 && p->dev.own_off) {
+    // mixed form, M = 8: blend and interpolation in one kernel, F stays on chip
+    ProfScope ps(p, "gather_blend_interp_tc", s);
+    return launch_gather_interp_tc(gather_args(p, fg, fb, nullptr, nullptr, nullptr), n_f,
+                                   ws_ldF(p), p->dev.Ar_hi, p->dev.Ar_lo, p->dev.own_off,
+                                   p->dev.own_k, p->dev.own_pack, p->dev.own_w, p->dev.n_own,
+                                   (int)p->strip_lin.size(),
+                                   reinterpret_cast<float*>(ws(p, L.ovals)), p->dev.status, s);
+  }
   if (f64) {
     ProfScope ps(p, "gather_blend", s);
     launch_gather_blend(gather_args(p, fg, fb, F, nullptr, nullptr), n_f, true, s);
@@ -271,16 +272,8 @@ extern "C" fc2d_status fc2d_extend_coeffs(fc2d_plan_t p, int n_f, const double* 
   cudaStream_t s = (cudaStream_t)stream;
   const bool f64 = p->prm.precision == FC2D_FP64;
   FftArgs fa = fft_args(p);
-  if (strip_values_in_rows(p)) {
-    // steps 5 and 7 with step 6 inside the row kernel: F, then the rows
-    if ((st = mixed_blend(p, n_f, fg, fb, ws(p, L.oF), ws_ldF(p), L, s))) return st;
-    RowArgs ra = row_args(p);
-    ra.ia = interp_args(p, ws_ldF(p));
-    ra.F = reinterpret_cast<const float*>(ws(p, L.oF));
-    ProfScope ps(p, "fft_rows_fused", s);
-    launch_fft_rows(fa, ra, n_f, false, 1, nullptr, fg, nullptr, ws(p, L.ointer), s);
-  } else {
-    if ((st = strip_values(p, n_f, fg, fb, L, s))) return st;
+  if ((st = strip_values(p, n_f, fg, fb, L, s))) return st;
+  {
     ProfScope ps(p, "fft_rows_fused", s);
     launch_fft_rows(fa, row_args(p), n_f, f64, 1, nullptr, fg, ws(p, L.ovals),
                     ws(p, L.ointer), s);

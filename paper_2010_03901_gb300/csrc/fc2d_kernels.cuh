@@ -45,10 +45,6 @@ struct RowArgs {
   const int32_t* row_iv;
   const int32_t* row_strip_off;
   const int32_t* s_lin;
-  // strip values computed in the row kernel (mixed form, M = 8): the interpolation
-  // tables and the strip values F [n_f][B][ia.ldF]; F == nullptr: read `vals` instead
-  InterpArgs ia;
-  const float* F;
 };
 
 #if defined(__CUDACC__)
@@ -112,6 +108,13 @@ fc2d_status launch_blend_tc(int n_cols, int Cr, int d, int ldF, const double* co
 // kernel (M <= 9, d <= 8); F [n_f*B][ldF] float.
 fc2d_status launch_gather_blend_tc(const GatherArgs& g, int n_f, int ldF, const float* Ar_hi,
                                    const float* Ar_lo, float* F, int* status, cudaStream_t s);
+// Mixed form, M = 8: matching values, blend and interpolation in one kernel; writes the
+// strip-point values (the plan's owner tables group the strip points by CTA).
+fc2d_status launch_gather_interp_tc(const GatherArgs& g, int n_f, int ldS, const float* Ar_hi,
+                                    const float* Ar_lo, const int32_t* own_off,
+                                    const int32_t* own_k, const int32_t* own_pack,
+                                    const float* own_w, int n_own, int n_strip, float* vals,
+                                    int* status, cudaStream_t s);
 void launch_interp(const InterpArgs& a, int n_f, bool fp64, const void* F, void* vals,
                    cudaStream_t s);
 void launch_assemble(const RowArgs& a, int n_f, bool fp64, const double* f_grid,

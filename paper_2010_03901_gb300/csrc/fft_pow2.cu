@@ -19,7 +19,6 @@
 #include <algorithm>
 
 #include "fc2d_kernels.cuh"
-#include "interp.cuh"
 
 namespace fc2d {
 namespace p2 {
@@ -305,7 +304,7 @@ __device__ __forceinline__ void fft_rest_to_global(typename Cx<T>::type* buf, in
 }
 
 // rows: nx = 2^(LOGNH+1); block = NT = 2^LOGNH / E threads
-template <typename T, typename TV, int LOGNH, bool FUSE>
+template <typename T, typename TV, int LOGNH>
 __global__ void __launch_bounds__((1 << LOGNH) / elems<T>() < 32 ? 32 : (1 << LOGNH) / elems<T>())
 k_fft_rows_p2(FftArgs fa, RowArgs ra, int mode, const T* __restrict__ ext,
               const double* __restrict__ f_grid, const TV* __restrict__ vals,
@@ -362,17 +361,8 @@ k_fft_rows_p2(FftArgs fa, RowArgs ra, int mode, const T* __restrict__ ext,
     }
     const int s0 = __ldg(ra.row_strip_off + j), s1 = __ldg(ra.row_strip_off + j + 1);
     const int base = j * nx;
-    if constexpr (FUSE) {
-      // strip values interpolated here from F (Section 3.4) instead of read back
-      const float* Ff = ra.F + (size_t)f * ra.ia.B * ra.ia.ldF;
-      for (int k = s0 + threadIdx.x; k < s1; k += blockDim.x) {
-        const InterpPoint<8, float> q = interp_load<8, float>(ra.ia, k);
-        put(__ldg(ra.s_lin + k) - base, (T)interp_apply<8, float, float, float, true>(ra.ia, Ff, q));
-      }
-    } else {
-      const TV* v = vals + (size_t)f * ra.n_strip;
-      for (int k = s0 + threadIdx.x; k < s1; k += blockDim.x) put(__ldg(ra.s_lin + k) - base, (T)__ldg(v + k));
-    }
+    const TV* v = vals + (size_t)f * ra.n_strip;
+    for (int k = s0 + threadIdx.x; k < s1; k += blockDim.x) put(__ldg(ra.s_lin + k) - base, (T)__ldg(v + k));
   }
   __syncthreads();
   const C* tw = reinterpret_cast<const C*>(fa.tsx);
@@ -518,12 +508,12 @@ static void cols4k_launch(const FftArgs& fa, int n_f, void* inter, void* fhat, c
   launch_pdl(k_cols4k_b, grid, dim3(128), 0, s, fa, (const float2*)inter, (float2*)fhat);
 }
 
-template <typename T, typename TV, int L, bool FUSE = false>
+template <typename T, typename TV, int L>
 static void rows_launch(const FftArgs& fa, const RowArgs& ra, int n_f, int mode, const void* ext,
                         const double* fg, const void* vals, void* inter, cudaStream_t s) {
   constexpr int NT = (1 << L) / elems<T>() < 32 ? 32 : (1 << L) / elems<T>();
   const size_t sm = (size_t)padded<T>(1 << L) * sizeof(typename Cx<T>::type);
-  auto k = k_fft_rows_p2<T, TV, L, FUSE>;
+  auto k = k_fft_rows_p2<T, TV, L>;
   cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   launch_pdl(k, dim3(fa.ny, n_f), dim3(NT), sm, s, fa, ra, mode, (const T*)ext, fg,
              (const TV*)vals, (typename Cx<T>::type*)inter);
@@ -560,8 +550,6 @@ bool launch_fft_rows_p2(const FftArgs& fa, const RowArgs& ra, int n_f, bool fp64
   case LL:                                                                               \
     if (fp64)                                                                            \
       p2::rows_launch<double, double, LL>(fa, ra, n_f, mode, ext, f_grid, vals, inter, s); \
-    else if (mode == 1 && ra.F)                                                          \
-      p2::rows_launch<float, float, LL, true>(fa, ra, n_f, mode, ext, f_grid, vals, inter, s); \
     else                                                                                 \
       p2::rows_launch<float, float, LL>(fa, ra, n_f, mode, ext, f_grid, vals, inter, s);   \
     return true;

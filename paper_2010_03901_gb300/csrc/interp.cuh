@@ -36,7 +36,8 @@ __device__ __forceinline__ InterpPoint<MM, TW> interp_load(const InterpArgs& a, 
   return q;
 }
 
-// The value of a strip point from the strip values Ff of one function ([B][ldF]).
+// The value of a strip point from the strip values Ff of one function ([B][ldF]); Ff
+// may be global or shared memory (plain loads).
 template <int MM, typename TF, typename TW, typename TA, bool VEC>
 __device__ __forceinline__ TA interp_apply(const InterpArgs& a, const TF* __restrict__ Ff,
                                            const InterpPoint<MM, TW>& q) {
@@ -63,7 +64,7 @@ __device__ __forceinline__ TA interp_apply(const InterpArgs& a, const TF* __rest
       TA v = 0;
 #pragma unroll
       for (int u = 0; u < 3; ++u) {
-        const float4 x = __ldg(row + u);
+        const float4 x = row[u];
         v = fma(ws[4 * u], (TA)x.x, v);
         v = fma(ws[4 * u + 1], (TA)x.y, v);
         v = fma(ws[4 * u + 2], (TA)x.z, v);
@@ -81,7 +82,7 @@ __device__ __forceinline__ TA interp_apply(const InterpArgs& a, const TF* __rest
       TA v = 0;
 #pragma unroll
       for (int b = 0; b < (MM > 0 ? MM : kMaxM); ++b)
-        if (b < M) v = fma((TA)q.eta[b], (TA)__ldg(row + b), v);
+        if (b < M) v = fma((TA)q.eta[b], (TA)row[b], v);
       acc = fma((TA)q.th[ai], v, acc);
     }
   }

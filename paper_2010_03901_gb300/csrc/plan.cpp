@@ -385,6 +385,43 @@ struct Cand {
 
 }  // namespace
 
+// Strip points grouped by the blend CTA that interpolates them (mixed form, M = 8):
+// CTA c of a function computes normals c*kTcOwned .. c*kTcOwned + kTcComputed - 1 (mod B)
+// and owns the strip points whose first normal pb lies in [c*kTcOwned, (c+1)*kTcOwned),
+// so that pb .. pb + M - 1 are among its normals.  The weights are reordered to match.
+static fc2d_status owner_tables(fc2d_plan_s* p, int ns, int M) {
+  const int B = p->prm.B;
+  const int n_own = (B + kTcOwned - 1) / kTcOwned;
+  std::vector<int32_t> pb(ns), sb(ns);
+  std::vector<float> w((size_t)2 * M * ns);
+  if (cudaMemcpy(pb.data(), p->dev.s_pb, (size_t)ns * 4, cudaMemcpyDeviceToHost) != cudaSuccess ||
+      cudaMemcpy(sb.data(), p->dev.s_sb, (size_t)ns * 4, cudaMemcpyDeviceToHost) != cudaSuccess ||
+      cudaMemcpy(w.data(), p->dev.s_w, w.size() * 4, cudaMemcpyDeviceToHost) != cudaSuccess)
+    return set_error(FC2D_ERR_CUDA, "reading the interpolation tables back failed");
+  std::vector<int32_t> off(n_own + 1, 0);
+  for (int k = 0; k < ns; ++k) {
+    pb[k] = ((pb[k] % B) + B) % B;  // the first normal is stored unreduced near theta = 0
+    if (sb[k] < 0 || sb[k] > 255)
+      return set_error(FC2D_ERR_GEOMETRY, "interpolation node index out of range");
+    ++off[pb[k] / kTcOwned + 1];
+  }
+  for (int c = 0; c < n_own; ++c) off[c + 1] += off[c];
+  std::vector<int32_t> fill(off.begin(), off.end() - 1), perm(ns), pack(ns);
+  std::vector<float> wp(w.size());
+  for (int k = 0; k < ns; ++k) {
+    const int c = pb[k] / kTcOwned, idx = fill[c]++;
+    perm[idx] = k;
+    pack[idx] = (pb[k] - c * kTcOwned) | (sb[k] << 8);
+    for (int b = 0; b < 2 * M; ++b) wp[(size_t)b * ns + idx] = w[(size_t)b * ns + k];
+  }
+  p->dev.n_own = n_own;
+  fc2d_status st;
+  if ((st = upload(&p->dev.own_off, off)) || (st = upload(&p->dev.own_k, perm)) ||
+      (st = upload(&p->dev.own_pack, pack)) || (st = upload(&p->dev.own_w, wp)))
+    return st;
+  return FC2D_OK;
+}
+
 extern "C" fc2d_status fc2d_plan(const fc2d_boundary* boundary, const fc2d_grid* grid,
                                  const fc2d_params* params, fc2d_plan_t* out) {
   if (!boundary || !grid || !out || boundary->n_modes < 2 || !boundary->cx ||
@@ -746,6 +783,8 @@ extern "C" fc2d_status fc2d_plan(const fc2d_boundary* boundary, const fc2d_grid*
     st = interp_weights_gpu((int)ns, M, p->Cr, B, k1, P.n_r, p->dev.s_theta, p->dev.s_eta,
                             P.precision == FC2D_FP64, p->dev.s_w, p->dev.s_pb, p->dev.s_sb);
     if (st) return fail(st);
+    if (P.precision == FC2D_MIXED && M == 8 && ns > 0 && (st = owner_tables(p, (int)ns, M)))
+      return fail(st);
   }
   *out = p;
   return FC2D_OK;
@@ -796,7 +835,8 @@ extern "C" void fc2d_destroy(fc2d_plan_t p) {
   poisson_destroy(p);
   void* ptrs[] = {p->dev.Q, p->dev.Ar, p->dev.Ar_hi, p->dev.Ar_lo, p->dev.gidx, p->dev.gw,
                   p->dev.wn, p->dev.s_lin, p->dev.s_theta, p->dev.s_eta, p->dev.s_w,
-                  p->dev.s_pb, p->dev.s_sb, p->dev.row_iv_off,
+                  p->dev.s_pb, p->dev.s_sb, p->dev.own_off, p->dev.own_k,
+                  p->dev.own_pack, p->dev.own_w, p->dev.row_iv_off,
                   p->dev.row_iv, p->dev.row_strip_off, p->dev.status, p->fx.tw64, p->fx.tw32,
                   p->fy.tw64, p->fy.tw32, p->rtw64, p->rtw32, p->ws.base,
                   p->fx.tws64, p->fx.tws32, p->fy.tws64, p->fy.tws32};

@@ -13,6 +13,11 @@ namespace fc2d {
 
 constexpr int kMaxRadices = 24;
 constexpr int kMaxM = 12;
+// Mixed form, M = 8: a blend CTA computes kTcComputed consecutive normals (mod B) and
+// interpolates the strip points whose first normal lies in its first kTcOwned, whose
+// M-normal stencils then lie within the CTA's normals.
+constexpr int kTcComputed = 64;
+constexpr int kTcOwned = 57;
 
 // One 1D FFT length: its radix sequence and twiddle tables exp(-2 pi i t/N), t < N.
 struct FftAxis {
@@ -51,6 +56,12 @@ struct DeviceTables {
   void* s_w = nullptr;       // [2M][n_strip] interpolation weights (double or float)
   int32_t* s_pb = nullptr;   // [n_strip] first normal index
   int32_t* s_sb = nullptr;   // [n_strip] first fine index
+  // strip points grouped by owning blend CTA (mixed form, M = 8; else null)
+  int32_t* own_off = nullptr;   // [n_own + 1] offsets of each CTA's points
+  int32_t* own_k = nullptr;     // [n_strip] strip index of each grouped point
+  int32_t* own_pack = nullptr;  // [n_strip] (first normal - CTA's first normal) | s << 8
+  float* own_w = nullptr;       // [2M][n_strip] interpolation weights, grouped order
+  int n_own = 0;                // CTAs per function: ceil(B / kTcOwned)
   // per-row tables
   int32_t* row_iv_off = nullptr;    // [ny+1] offsets into row_iv
   int32_t* row_iv = nullptr;        // pairs (i_lo, i_hi), inclusive
