@@ -44,8 +44,12 @@ FP64_PEAK_TFLOPS = 1.25   # GB300 FP64 (nominal; 152 SMs x 2 DFMA/clk x 2 flop x
 # launches; a scope with two kernels sums both).  A kernel changed after its capture
 # has no entry, and the roofline then reports traffic null.
 MEASURED_TRAFFIC = {
-    # k_cols4k_a (67410432 + 10120704) + k_cols4k_b (67525888 + 15047680)
-    ("mixed", "fft_cols"): 160104704,
+    # k_cols4k_a (67409408 + 9991424) + k_cols4k_b (67500800 + 15403520)
+    ("mixed", "fft_cols"): 160305152,
+    ("mixed", "fft_rows_fused"): 70920960 + 19312640,
+    ("mixed", "gather_blend_interp_tc"): 34109440 + 256,
+    ("fp64", "fft_cols"): 141588736 + 92130048,
+    ("fp64", "fft_rows_fused"): 72346368 + 74370560,
 }
 
 
