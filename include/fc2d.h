@@ -152,7 +152,7 @@ fc2d_status fc2d_extend_coeffs(fc2d_plan_t plan, int n_f, const double* f_grid_d
  * meant for callers that own all device memory through their own allocator, or that
  * run where an allocation's implicit device synchronisation is not acceptable.
  * Its scratch is one fixed device array of 64 MiB (the row-DFT intermediate,
- * n_f * ny * (nx/2+1 rounded up to 8) complex values), held by every GPU that loads
+ * n_f * ny * (nx/2+1 rounded up to 16) complex values), held by every GPU that loads
  * the library until the process exits.  Larger requests return FC2D_ERR_ARG.
  * The first call on a device looks up the array's device address for that device
  * (cudaGetSymbolAddress); make that first call before any stream capture.

@@ -48,7 +48,7 @@ int ws_ldF(const fc2d_plan_s* p) {
 Layout layout(const fc2d_plan_s* p, int n_f) {
   Layout L{};
   const size_t esz = p->prm.precision == FC2D_MIXED ? 4 : 8;
-  const size_t pitch = ((size_t)p->grid.nx / 2 + 1 + 7) / 8 * 8;
+  const size_t pitch = row_pitch(p);
   L.F = al((size_t)n_f * p->prm.B * ws_ldF(p) * esz);
   L.vals = al((size_t)n_f * std::max<size_t>(1, p->strip_lin.size()) * esz);
   L.inter = al((size_t)n_f * p->grid.ny * pitch * 2 * esz);
@@ -119,7 +119,7 @@ FftArgs fft_args(fc2d_plan_s* p) {
   const bool f64 = p->prm.precision == FC2D_FP64;
   a.nx = p->grid.nx;
   a.ny = p->grid.ny;
-  a.pitch = (p->grid.nx / 2 + 1 + 7) / 8 * 8;
+  a.pitch = (int)row_pitch(p);
   a.nrx = p->fx.n_radix;
   a.nry = p->fy.n_radix;
   for (int i = 0; i < a.nrx; ++i) a.rx[i] = p->fx.radix[i];
@@ -435,7 +435,7 @@ extern "C" fc2d_status fc2d_wave_interior(fc2d_plan_t p, int n_f, double c, doub
   Layout L = layout(p, 2 * n_f);
   if ((st = ensure_workspace(p, L.total))) return st;
   cudaStream_t s = (cudaStream_t)stream;
-  const size_t pitch = ((size_t)p->grid.nx / 2 + 1 + 7) / 8 * 8;
+  const size_t pitch = row_pitch(p);
   FftArgs fa = fft_args(p);
   for (int half = 0; half < 2; ++half) {
     const double* fg = half ? ut0 : u0;

@@ -400,7 +400,7 @@ k_fft_cols_p2(FftArgs fa, const typename Cx<T>::type* __restrict__ inter,
   const int ncol = fa.nx / 2 + 1;
   const int c = threadIdx.x % CB, t = threadIdx.x / CB;
   const int kx = blockIdx.x * CB + c, f = blockIdx.y;
-  // kx < pitch always (pitch = nx/2+1 rounded up to 8, CB divides 8): reads stay in the
+  // kx < pitch always (pitch = nx/2+1 rounded up to 16, CB divides 16): reads stay in the
   // intermediate row; columns beyond nx/2 are computed and not stored
   const C* src = inter + (size_t)f * N * fa.pitch + kx;
   // column c starts c * W/CB elements after c * PN (W = lanes per shared-memory
@@ -473,7 +473,8 @@ __global__ void __launch_bounds__(128) k_cols4k_a(FftArgs fa, float2* __restrict
   }
 }
 
-__global__ void __launch_bounds__(128) k_cols4k_b(FftArgs fa, const float2* __restrict__ inter,
+__global__ void __launch_bounds__(128) k_cols4k_b(FftArgs fa, int drop,
+                                                   float2* __restrict__ inter,
                                                    float2* __restrict__ fhat) {
   __shared__ float2 ex[64 * kC4Cols];
   const int c = threadIdx.x & (kC4Cols - 1), l = threadIdx.x / kC4Cols;
@@ -482,7 +483,7 @@ __global__ void __launch_bounds__(128) k_cols4k_b(FftArgs fa, const float2* __re
   const int m1 = blockIdx.y, f = blockIdx.z;
   const bool live = kx < ncol;
   const float2* w = reinterpret_cast<const float2*>(fa.twy);
-  const float2* col = inter + (size_t)f * 4096 * fa.pitch + kx;
+  float2* col = inter + (size_t)f * 4096 * fa.pitch + kx;
   pdl_wait();
   pdl_trigger();
   float2 a[8];
@@ -490,6 +491,16 @@ __global__ void __launch_bounds__(128) k_cols4k_b(FftArgs fa, const float2* __re
   for (int i = 0; i < 8; ++i)
     a[i] = live ? col[(size_t)(64 * m1 + l + 8 * i) * fa.pitch] : make_float2(0.f, 0.f);
   dft64_cols(a, c, l, ex, w);
+  // the intermediate is scratch and this block was the last reader of its 8 x 16
+  // values per thread group: drop the lines from L2 without writing them back (each
+  // row of 16 columns is one 128-byte line; `drop` is set only when the host has
+  // checked the 128-byte alignment of the buffer and the pitch)
+  if (drop && c == 0) {
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+      asm volatile("discard.global.L2 [%0], 128;" ::"l"(col + (size_t)(64 * m1 + l + 8 * i) * fa.pitch)
+                   : "memory");
+  }
   const float sc = (float)fa.scale;
   float2* out = fhat + (size_t)f * 4096 * ncol + kx;
   if (live) {
@@ -504,8 +515,9 @@ __global__ void __launch_bounds__(128) k_cols4k_b(FftArgs fa, const float2* __re
 static void cols4k_launch(const FftArgs& fa, int n_f, void* inter, void* fhat, cudaStream_t s) {
   const int ncol = fa.nx / 2 + 1;
   const dim3 grid((ncol + kC4Cols - 1) / kC4Cols, 64, n_f);
+  const int drop = (reinterpret_cast<uintptr_t>(inter) % 128 == 0 && fa.pitch % 16 == 0) ? 1 : 0;
   launch_pdl(k_cols4k_a, grid, dim3(128), 0, s, fa, (float2*)inter);
-  launch_pdl(k_cols4k_b, grid, dim3(128), 0, s, fa, (const float2*)inter, (float2*)fhat);
+  launch_pdl(k_cols4k_b, grid, dim3(128), 0, s, fa, drop, (float2*)inter, (float2*)fhat);
 }
 
 template <typename T, typename TV, int L>

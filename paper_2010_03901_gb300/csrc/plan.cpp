@@ -800,7 +800,7 @@ extern "C" fc2d_status fc2d_plan_info(fc2d_plan_t p, fc2d_info* out) {
   size_t esz = p->prm.precision == FC2D_MIXED ? 4 : 8;
   size_t F = (size_t)p->prm.B * (p->Cr + 1) * esz;
   size_t S = p->strip_lin.size() * esz;
-  size_t pitch = ((size_t)p->grid.nx / 2 + 1 + 7) / 8 * 8;
+  size_t pitch = row_pitch(p);
   size_t I = (size_t)p->grid.ny * pitch * 2 * esz;
   out->workspace_bytes_per_function = (int64_t)(F + S + I + 256 * 3);
   return FC2D_OK;

@@ -110,6 +110,12 @@ struct fc2d_plan_s {
 };
 
 namespace fc2d {
+// Row length (complex values) of the row-DFT intermediate: nx/2 + 1 rounded up to 16,
+// so that every row starts on a 128-byte line (16 FP32 complex values).
+inline size_t row_pitch(const fc2d_plan_s* p) { return ((size_t)p->grid.nx / 2 + 1 + 15) / 16 * 16; }
+}  // namespace fc2d
+
+namespace fc2d {
 // error reporting (thread-local message)
 fc2d_status set_error(fc2d_status s, const std::string& msg);
 fc2d_status cuda_check(int err, const char* what);

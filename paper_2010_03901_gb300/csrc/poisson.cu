@@ -676,7 +676,7 @@ fc2d_status poisson_solve(fc2d_plan_s* p, int n_f, const double* fg, const doubl
   FftArgs fa{};
   fa.nx = nx;
   fa.ny = ny;
-  fa.pitch = (nx / 2 + 1 + 7) / 8 * 8;
+  fa.pitch = (int)row_pitch(p);
   fa.nrx = p->fx.n_radix;
   fa.nry = p->fy.n_radix;
   for (int i = 0; i < fa.nrx; ++i) fa.rx[i] = p->fx.radix[i];

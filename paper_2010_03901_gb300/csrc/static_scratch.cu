@@ -57,11 +57,11 @@ extern "C" fc2d_status fc2d_coeffs_static(fc2d_plan_t p, int n_f, const void* ex
   if (!p || !ext || !fhat) return set_error(FC2D_ERR_ARG, "fc2d_coeffs_static: null argument");
   if (n_f < 1) return set_error(FC2D_ERR_ARG, "fc2d_coeffs_static: n_f must be >= 1");
   const bool f64 = p->prm.precision == FC2D_FP64;
-  const size_t pitch = ((size_t)p->grid.nx / 2 + 1 + 7) / 8 * 8;
+  const size_t pitch = row_pitch(p);
   const size_t need = (size_t)n_f * p->grid.ny * pitch * 2 * (f64 ? 8 : 4);
   if (need > kStaticScratchBytes)
     return set_error(FC2D_ERR_ARG,
-                     "fc2d_coeffs_static: n_f * ny * (nx/2+1 rounded up to 8) complex values need " +
+                     "fc2d_coeffs_static: n_f * ny * (nx/2+1 rounded up to 16) complex values need " +
                          std::to_string(need) + " bytes, above the fixed scratch of " +
                          std::to_string(kStaticScratchBytes) + " bytes");
   cudaError_t e = cudaSetDevice(p->device);
