@@ -91,6 +91,8 @@ bool launch_fft_rows_p2(const FftArgs& fa, const RowArgs& ra, int n_f, bool fp64
                         cudaStream_t s);
 bool launch_fft_cols_p2(const FftArgs& fa, int n_f, bool fp64, void* inter, void* fhat,
                         cudaStream_t s);
+bool launch_fft_cols_64n(const FftArgs& fa, int n_f, bool fp64, void* inter, void* fhat,
+                         cudaStream_t s);
 
 void launch_fft_rows(const FftArgs& fa, const RowArgs& ra, int n_f, bool fp64, int mode,
                      const void* ext, const double* f_grid, const void* vals, void* inter,
@@ -122,6 +124,7 @@ static int pick_cb(int ny, size_t csize) {
 void launch_fft_cols(const FftArgs& fa, int n_f, bool fp64, void* inter, void* fhat,
                      cudaStream_t s) {
   if (launch_fft_cols_p2(fa, n_f, fp64, inter, fhat, s)) return;
+  if (launch_fft_cols_64n(fa, n_f, fp64, inter, fhat, s)) return;
   const int ncol = fa.nx / 2 + 1;
   if (fp64) {
     int cb = pick_cb(fa.ny, sizeof(double2));

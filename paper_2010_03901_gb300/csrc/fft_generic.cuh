@@ -93,9 +93,13 @@ __device__ typename Cx<T>::type* stockham(typename Cx<T>::type* a, typename Cx<T
     const int R = radix[st];
     const int NR = N / R;
     const int tstep = N / (Ns * R);
+    // quotients by NR and Ns as (x + 1/2) * (1/d) truncated: exact for every x < 2^22
+    // and every divisor 2^a 3^b 5^c <= 8192, far cheaper than integer division by a
+    // runtime divisor
+    const float inv_NR = 1.0f / (float)NR, inv_Ns = 1.0f / (float)Ns;
     for (int idx = threadIdx.x; idx < nbatch * NR; idx += blockDim.x) {
-      const int c = idx / NR, j = idx - c * NR;
-      const int k = j % Ns;
+      const int c = (int)(((float)idx + 0.5f) * inv_NR), j = idx - c * NR;
+      const int q = (int)(((float)j + 0.5f) * inv_Ns), k = j - q * Ns;
       const C* src = a + (size_t)c * N;
       C v[8];
 #pragma unroll
@@ -106,7 +110,7 @@ __device__ typename Cx<T>::type* stockham(typename Cx<T>::type* a, typename Cx<T
           v[r] = x;
         }
       dft_small<T, C>(v, R);
-      C* dst = b + (size_t)c * N + (j / Ns) * Ns * R + k;
+      C* dst = b + (size_t)c * N + q * Ns * R + k;
 #pragma unroll
       for (int r = 0; r < 8; ++r)
         if (r < R) dst[r * Ns] = v[r];

@@ -116,8 +116,37 @@ template <typename T, typename C> __device__ __forceinline__ void dft16(C* v) {
   }
 }
 
+template <typename T, typename C> __device__ __forceinline__ void dft3(C* v) {
+  const T c1 = (T)-0.5, s1 = (T)0.86602540378443864676;  // exp(-2 pi i/3) = c1 - i s1
+  const C a = v[0], sbc = add(v[1], v[2]), dbc = sub(v[1], v[2]);
+  v[0] = add(a, sbc);
+  const C m = {a.x + c1 * sbc.x, a.y + c1 * sbc.y};
+  const C r = {s1 * dbc.y, -s1 * dbc.x};  // -i s1 (b - c)
+  v[1] = add(m, r);
+  v[2] = sub(m, r);
+}
+
+template <typename T, typename C> __device__ __forceinline__ void dft5(C* v) {
+  const T c1 = (T)0.30901699437494742410, s1 = (T)0.95105651629515357212;  // 2 pi/5
+  const T c2 = (T)-0.80901699437494742410, s2 = (T)0.58778525229247312917;  // 4 pi/5
+  const C a = v[0];
+  const C s14 = add(v[1], v[4]), d14 = sub(v[1], v[4]);
+  const C s23 = add(v[2], v[3]), d23 = sub(v[2], v[3]);
+  v[0] = add(a, add(s14, s23));
+  const C m1 = {a.x + c1 * s14.x + c2 * s23.x, a.y + c1 * s14.y + c2 * s23.y};
+  const C m2 = {a.x + c2 * s14.x + c1 * s23.x, a.y + c2 * s14.y + c1 * s23.y};
+  const C r1 = {s1 * d14.y + s2 * d23.y, -(s1 * d14.x + s2 * d23.x)};
+  const C r2 = {s2 * d14.y - s1 * d23.y, -(s2 * d14.x - s1 * d23.x)};
+  v[1] = add(m1, r1);
+  v[4] = sub(m1, r1);
+  v[2] = add(m2, r2);
+  v[3] = sub(m2, r2);
+}
+
 template <typename T, typename C, int R> __device__ __forceinline__ void dft(C* v) {
   if constexpr (R == 2) dft2(v);
+  else if constexpr (R == 3) dft3<T, C>(v);
+  else if constexpr (R == 5) dft5<T, C>(v);
   else if constexpr (R == 4) dft4(v[0], v[1], v[2], v[3]);
   else if constexpr (R == 8) dft8<T, C>(v);
   else dft16<T, C>(v);
@@ -435,12 +464,12 @@ constexpr int kC4Cols = 16;   // columns per block
 
 // 64-point DFT of a[i] = x[l + 8 i] held by the threads (c, l = 0..7) of column c;
 // on return a[m'] = X[l + 8 m'].  ex: the block's [8][8][16] exchange buffer; w: the
-// 4096-entry table w_4096^t (w_64^k = w[64 k]).
+// table w_N^t of the column length N = 64 n2 (w_64^k = w[n2 k]).
 __device__ __forceinline__ void dft64_cols(float2* a, int c, int l, float2* ex,
-                                           const float2* __restrict__ w) {
+                                           const float2* __restrict__ w, int n2 = 64) {
   dft<float, float2, 8>(a);
 #pragma unroll
-  for (int m = 1; m < 8; ++m) a[m] = mul(a[m], __ldg(w + ((64 * l * m) & 4095)));
+  for (int m = 1; m < 8; ++m) a[m] = mul(a[m], __ldg(w + ((l * m) & 63) * n2));
 #pragma unroll
   for (int m = 0; m < 8; ++m) ex[(m * 8 + l) * kC4Cols + c] = a[m];
   __syncthreads();
@@ -512,6 +541,112 @@ __global__ void __launch_bounds__(128) k_cols4k_b(FftArgs fa, int drop,
   }
 }
 
+// ------------------------------------------------------------------------- //
+// FP32 columns of N = 64 N2 points (N2 = 6, 10, 12, 24: non-power-of-two sizes), in the
+// same two passes: j = N2 j1 + j2, m = m1 + 64 m2,
+//   pass A: 64-point DFTs over j1 (rows N2 j1 + j2, as k_cols4k_a with stride N2), the
+//           twiddle w_N^(j2 m1), in place to row N2 m1 + j2;
+//   pass B: N2-point DFTs over the N2 consecutive rows N2 m1 + j2, one per thread
+//           (16 columns x 8 values of m1 per block), scaled, to the spectrum rows
+//           m1 + 64 m2; then the intermediate's lines are dropped from L2.
+// ------------------------------------------------------------------------- //
+
+// Length R1 R2 DFT in registers (Cooley-Tukey, n = R2 n1 + n2, k = k1 + R1 k2):
+// R2 DFTs of length R1, the twiddles w_{R1 R2}^(n2 k1) (wt[t * ws] = w_{R1 R2}^t), R1
+// DFTs of length R2.  x holds the input in natural order and receives the output.
+template <int R1, int R2>
+__device__ __forceinline__ void dft_ct(float2* x, const float2* __restrict__ wt, int ws) {
+  float2 a[R1 * R2];
+#pragma unroll
+  for (int n2 = 0; n2 < R2; ++n2) {
+    float2 v[R1];
+#pragma unroll
+    for (int n1 = 0; n1 < R1; ++n1) v[n1] = x[R2 * n1 + n2];
+    dft<float, float2, R1>(v);
+#pragma unroll
+    for (int k1 = 0; k1 < R1; ++k1)
+      a[n2 * R1 + k1] = (n2 * k1) ? mul(v[k1], __ldg(wt + (n2 * k1) * ws)) : v[k1];
+  }
+#pragma unroll
+  for (int k1 = 0; k1 < R1; ++k1) {
+    float2 u[R2];
+#pragma unroll
+    for (int n2 = 0; n2 < R2; ++n2) u[n2] = a[n2 * R1 + k1];
+    dft<float, float2, R2>(u);
+#pragma unroll
+    for (int k2 = 0; k2 < R2; ++k2) x[k1 + R1 * k2] = u[k2];
+  }
+}
+
+__global__ void __launch_bounds__(128) k_cols64_a(FftArgs fa, int n2, float2* __restrict__ inter) {
+  __shared__ float2 ex[64 * kC4Cols];
+  const int c = threadIdx.x & (kC4Cols - 1), l = threadIdx.x / kC4Cols;
+  const int ncol = fa.nx / 2 + 1, N = fa.ny;
+  const int kx = blockIdx.x * kC4Cols + c;
+  const int j2 = blockIdx.y, f = blockIdx.z;
+  const bool live = kx < ncol;
+  const float2* w = reinterpret_cast<const float2*>(fa.twy);
+  float2* col = inter + (size_t)f * N * fa.pitch + kx;
+  pdl_wait();
+  pdl_trigger();
+  float2 a[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+    a[i] = live ? col[(size_t)(n2 * (l + 8 * i) + j2) * fa.pitch] : make_float2(0.f, 0.f);
+  dft64_cols(a, c, l, ex, w, n2);
+#pragma unroll
+  for (int m2 = 0; m2 < 8; ++m2) {
+    const int m1 = l + 8 * m2;
+    const float2 y = mul(a[m2], __ldg(w + j2 * m1));  // j2 m1 < N
+    if (live) col[(size_t)(n2 * m1 + j2) * fa.pitch] = y;
+  }
+}
+
+template <int R1, int R2>
+__global__ void __launch_bounds__(128) k_cols64_b(FftArgs fa, int drop, float2* __restrict__ inter,
+                                                   float2* __restrict__ fhat) {
+  constexpr int N2 = R1 * R2;
+  const int c = threadIdx.x & (kC4Cols - 1);
+  const int ncol = fa.nx / 2 + 1, N = fa.ny;
+  const int kx = blockIdx.x * kC4Cols + c;
+  const int m1 = blockIdx.y * 8 + threadIdx.x / kC4Cols, f = blockIdx.z;
+  const bool live = kx < ncol;
+  const float2* w = reinterpret_cast<const float2*>(fa.twy);
+  float2* col = inter + (size_t)f * N * fa.pitch + kx;
+  pdl_wait();
+  pdl_trigger();
+  float2 x[N2];
+#pragma unroll
+  for (int j2 = 0; j2 < N2; ++j2)
+    x[j2] = live ? col[(size_t)(N2 * m1 + j2) * fa.pitch] : make_float2(0.f, 0.f);
+  dft_ct<R1, R2>(x, w, 64);  // w_N2^t = w_N^(64 t)
+  const float sc = (float)fa.scale;
+  float2* out = fhat + (size_t)f * N * ncol + kx;
+  if (live) {
+#pragma unroll
+    for (int m2 = 0; m2 < N2; ++m2)
+      out[(size_t)(m1 + 64 * m2) * ncol] = make_float2(x[m2].x * sc, x[m2].y * sc);
+  }
+  // last reader of the intermediate: drop its lines (one 128-byte line per row of the
+  // block's 16 columns; `drop` only when the host checked the alignment)
+  if (drop && c == 0) {
+#pragma unroll
+    for (int j2 = 0; j2 < N2; ++j2)
+      asm volatile("discard.global.L2 [%0], 128;" ::"l"(col + (size_t)(N2 * m1 + j2) * fa.pitch)
+                   : "memory");
+  }
+}
+
+template <int R1, int R2>
+static void cols64_launch(const FftArgs& fa, int n_f, void* inter, void* fhat, cudaStream_t s) {
+  const int ncol = fa.nx / 2 + 1;
+  const int groups = (ncol + kC4Cols - 1) / kC4Cols;
+  const int drop = (reinterpret_cast<uintptr_t>(inter) % 128 == 0 && fa.pitch % 16 == 0) ? 1 : 0;
+  launch_pdl(k_cols64_a, dim3(groups, R1 * R2, n_f), dim3(128), 0, s, fa, R1 * R2, (float2*)inter);
+  launch_pdl(k_cols64_b<R1, R2>, dim3(groups, 8, n_f), dim3(128), 0, s, fa, drop, (float2*)inter,
+             (float2*)fhat);
+}
+
 static void cols4k_launch(const FftArgs& fa, int n_f, void* inter, void* fhat, cudaStream_t s) {
   const int ncol = fa.nx / 2 + 1;
   const dim3 grid((ncol + kC4Cols - 1) / kC4Cols, 64, n_f);
@@ -577,6 +712,20 @@ bool launch_fft_rows_p2(const FftArgs& fa, const RowArgs& ra, int n_f, bool fp64
     default: return false;
   }
 #undef FC2D_ROWS
+}
+
+// FP32 columns of 64 N2 points for N2 = 6, 10, 12, 24 (two passes).  Returns false
+// (nothing launched) for other sizes.
+bool launch_fft_cols_64n(const FftArgs& fa, int n_f, bool fp64, void* inter, void* fhat,
+                         cudaStream_t s) {
+  if (fp64 || fa.ny % 64) return false;
+  switch (fa.ny / 64) {
+    case 6: p2::cols64_launch<2, 3>(fa, n_f, inter, fhat, s); return true;
+    case 10: p2::cols64_launch<2, 5>(fa, n_f, inter, fhat, s); return true;
+    case 12: p2::cols64_launch<4, 3>(fa, n_f, inter, fhat, s); return true;
+    case 24: p2::cols64_launch<8, 3>(fa, n_f, inter, fhat, s); return true;
+    default: return false;
+  }
 }
 
 bool launch_fft_cols_p2(const FftArgs& fa, int n_f, bool fp64, void* inter, void* fhat,

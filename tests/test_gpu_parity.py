@@ -267,3 +267,30 @@ def test_dft_large_power_of_two(fc2d, torch_cuda, precision):
     ref = np.fft.rfft2(t.cpu().numpy().astype(np.float64)[0]) / (nx * ny)
     tol = TOL if precision == "fp64" else TOL_MIXED
     assert rel(got, ref) < tol, rel(got, ref)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("ny,nx", [(1536, 768), (640, 384), (768, 1280), (384, 640)])
+def test_dft_mixed_radix_sizes(fc2d, torch_cuda, precision, ny, nx):
+    """The DFT at non-power-of-two sizes (64 N2 columns with N2 = 24, 10, 12, 6 and the
+    mixed-radix rows) on seeded random data, two functions batched: 1e-12 (FP64) / 1e-6
+    (FP32) relative max-norm against numpy's FFT of the same data."""
+    torch = torch_cuda
+    w = W.workload("kite1024")
+    h = 3.3 / min(nx, ny)
+    prec = fc2d.FC2D_FP64 if precision == "fp64" else fc2d.FC2D_MIXED
+    # a kite plan on an ny x nx box around it (only the DFT is exercised)
+    plan = fc2d.fc2d_plan(w.boundary.arrays(), (-0.15 - 0.5 * nx * h, -0.5 * ny * h, h, nx, ny),
+                          dict(B=w.params.B, k1=0.004), precision=prec)
+    x = W.normal(78 + nx, 2 * ny * nx).reshape(2, ny, nx)
+    dt = torch.float64 if precision == "fp64" else torch.float32
+    t = torch.tensor(x, dtype=dt, device="cuda:0")
+    fhat = torch.zeros((2, ny, nx // 2 + 1, 2), dtype=dt, device="cuda:0")
+    plan.fc2d_coeffs(2, t, fhat)
+    plan.fc2d_sync_status()
+    got = fhat.cpu().numpy().astype(np.float64)
+    got = got[..., 0] + 1j * got[..., 1]
+    tol = TOL if precision == "fp64" else TOL_MIXED
+    for k in range(2):
+        ref = np.fft.rfft2(t[k].cpu().numpy().astype(np.float64)) / (nx * ny)
+        assert rel(got[k], ref) < tol, (k, rel(got[k], ref))
