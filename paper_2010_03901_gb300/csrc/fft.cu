@@ -89,6 +89,9 @@ __global__ void __launch_bounds__(256) k_fft_cols(FftArgs fa, int cb,
 bool launch_fft_rows_p2(const FftArgs& fa, const RowArgs& ra, int n_f, bool fp64, int mode,
                         const void* ext, const double* f_grid, const void* vals, void* inter,
                         cudaStream_t s);
+bool launch_fft_rows_64n(const FftArgs& fa, const RowArgs& ra, int n_f, bool fp64, int mode,
+                         const void* ext, const double* f_grid, const void* vals, void* inter,
+                         cudaStream_t s);
 bool launch_fft_cols_p2(const FftArgs& fa, int n_f, bool fp64, void* inter, void* fhat,
                         cudaStream_t s);
 bool launch_fft_cols_64n(const FftArgs& fa, int n_f, bool fp64, void* inter, void* fhat,
@@ -98,6 +101,7 @@ void launch_fft_rows(const FftArgs& fa, const RowArgs& ra, int n_f, bool fp64, i
                      const void* ext, const double* f_grid, const void* vals, void* inter,
                      cudaStream_t s) {
   if (launch_fft_rows_p2(fa, ra, n_f, fp64, mode, ext, f_grid, vals, inter, s)) return;
+  if (launch_fft_rows_64n(fa, ra, n_f, fp64, mode, ext, f_grid, vals, inter, s)) return;
   dim3 grid(fa.ny, n_f);
   if (fp64) {
     size_t sm = (size_t)fa.nx * sizeof(double2);  // two buffers of nx/2 complex

@@ -152,6 +152,33 @@ template <typename T, typename C, int R> __device__ __forceinline__ void dft(C* 
   else dft16<T, C>(v);
 }
 
+// Length R1 R2 DFT in registers (Cooley-Tukey, n = R2 n1 + n2, k = k1 + R1 k2):
+// R2 DFTs of length R1, the twiddles w_{R1 R2}^(n2 k1) (wt[t * ws] = w_{R1 R2}^t), R1
+// DFTs of length R2.  x holds the input in natural order and receives the output.
+template <int R1, int R2>
+__device__ __forceinline__ void dft_ct(float2* x, const float2* __restrict__ wt, int ws) {
+  float2 a[R1 * R2];
+#pragma unroll
+  for (int n2 = 0; n2 < R2; ++n2) {
+    float2 v[R1];
+#pragma unroll
+    for (int n1 = 0; n1 < R1; ++n1) v[n1] = x[R2 * n1 + n2];
+    dft<float, float2, R1>(v);
+#pragma unroll
+    for (int k1 = 0; k1 < R1; ++k1)
+      a[n2 * R1 + k1] = (n2 * k1) ? mul(v[k1], __ldg(wt + (n2 * k1) * ws)) : v[k1];
+  }
+#pragma unroll
+  for (int k1 = 0; k1 < R1; ++k1) {
+    float2 u[R2];
+#pragma unroll
+    for (int n2 = 0; n2 < R2; ++n2) u[n2] = a[n2 * R1 + k1];
+    dft<float, float2, R2>(u);
+#pragma unroll
+    for (int k2 = 0; k2 < R2; ++k2) x[k1 + R1 * k2] = u[k2];
+  }
+}
+
 // Round-to-nearest-even double -> float on the integer pipe (the FP64 pipe that the
 // conversion instruction uses is narrow on this part).  For doubles whose exponent e
 // lies in [897, 1148] (float exponents 1..252, so no overflow even after rounding up):
@@ -332,22 +359,17 @@ __device__ __forceinline__ void fft_rest_to_global(typename Cx<T>::type* buf, in
   }
 }
 
-// rows: nx = 2^(LOGNH+1); block = NT = 2^LOGNH / E threads
-template <typename T, typename TV, int LOGNH>
-__global__ void __launch_bounds__((1 << LOGNH) / elems<T>() < 32 ? 32 : (1 << LOGNH) / elems<T>())
-k_fft_rows_p2(FftArgs fa, RowArgs ra, int mode, const T* __restrict__ ext,
-              const double* __restrict__ f_grid, const TV* __restrict__ vals,
-              typename Cx<T>::type* __restrict__ inter) {
+// The extended row j of function f as NH complex pairs z_n = x_{2n} + i x_{2n+1} in the
+// padded shared buffer: mode 0 from an extended grid; mode 1 assembled (zeros, the
+// inside reals of f, the strip values).  Ends with a barrier.
+template <typename T, typename TV>
+__device__ __forceinline__ void assemble_row(const RowArgs& ra, int mode, int NH, int j, int f,
+                                             const T* __restrict__ ext,
+                                             const double* __restrict__ f_grid,
+                                             const TV* __restrict__ vals,
+                                             typename Cx<T>::type* buf) {
   using C = typename Cx<T>::type;
-  constexpr int E = elems<T>();
-  constexpr int NH = 1 << LOGNH;
-  constexpr int NT = NH / E < 1 ? 1 : NH / E;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  C* buf = reinterpret_cast<C*>(smem_raw);
-  const int j = blockIdx.x, f = blockIdx.y, t = threadIdx.x, nx = 2 * NH;
-  pdl_wait();
-  pdl_trigger();
-  // assemble the row: reals x_i -> pair n = i/2, component i%2 (padded pairs)
+  const int nx = 2 * NH;
   auto put = [&](int i, T v) { reinterpret_cast<T*>(&buf[pad<T>(i >> 1)])[i & 1] = v; };
   if (mode == 0) {
     const T* src = ext + (size_t)f * ra.grid_stride + (size_t)j * nx;
@@ -394,12 +416,16 @@ k_fft_rows_p2(FftArgs fa, RowArgs ra, int mode, const T* __restrict__ ext,
     for (int k = s0 + threadIdx.x; k < s1; k += blockDim.x) put(__ldg(ra.s_lin + k) - base, (T)__ldg(v + k));
   }
   __syncthreads();
-  const C* tw = reinterpret_cast<const C*>(fa.tsx);
-  block_fft<T, LOGNH, E>(buf, t, t < NT, tw, 1);
-  const C* rtw = reinterpret_cast<const C*>(fa.rtw);
-  C* out = inter + ((size_t)f * fa.ny + j) * fa.pitch;
-  // X_k and X_{NH-k} from Z_k and Z_{NH-k} (k = 0..NH/2; k = 0 pairs with NH):
-  // e' = conj(e), o' = -conj(o), rtw_{NH-k} = -conj(rtw_k), so w'o' = conj(w o)
+}
+
+// The real row's spectrum X_k, k = 0..NH, from the complex transform Z of the pairs (in
+// the padded buffer): X_k and X_{NH-k} from Z_k and Z_{NH-k} (k = 0..NH/2; k = 0 pairs
+// with NH): e' = conj(e), o' = -conj(o), rtw_{NH-k} = -conj(rtw_k), so w'o' = conj(w o).
+template <typename T>
+__device__ __forceinline__ void even_odd_split(const typename Cx<T>::type* buf, int NH,
+                                               const typename Cx<T>::type* __restrict__ rtw,
+                                               typename Cx<T>::type* __restrict__ out) {
+  using C = typename Cx<T>::type;
   for (int k = threadIdx.x; k <= NH / 2; k += blockDim.x) {
     const C zk = buf[pad<T>(k)];
     C zc = buf[pad<T>(k == 0 ? 0 : NH - k)];
@@ -410,6 +436,106 @@ k_fft_rows_p2(FftArgs fa, RowArgs ra, int mode, const T* __restrict__ ext,
     out[k] = C{e.x + wo.y, e.y - wo.x};
     if (k != NH - k) out[NH - k] = C{e.x - wo.y, -e.y - wo.x};
   }
+}
+
+// rows: nx = 2^(LOGNH+1); block = NT = 2^LOGNH / E threads
+template <typename T, typename TV, int LOGNH>
+__global__ void __launch_bounds__((1 << LOGNH) / elems<T>() < 32 ? 32 : (1 << LOGNH) / elems<T>())
+k_fft_rows_p2(FftArgs fa, RowArgs ra, int mode, const T* __restrict__ ext,
+              const double* __restrict__ f_grid, const TV* __restrict__ vals,
+              typename Cx<T>::type* __restrict__ inter) {
+  using C = typename Cx<T>::type;
+  constexpr int E = elems<T>();
+  constexpr int NH = 1 << LOGNH;
+  constexpr int NT = NH / E < 1 ? 1 : NH / E;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* buf = reinterpret_cast<C*>(smem_raw);
+  const int j = blockIdx.x, f = blockIdx.y, t = threadIdx.x;
+  pdl_wait();
+  pdl_trigger();
+  assemble_row<T, TV>(ra, mode, NH, j, f, ext, f_grid, vals, buf);
+  const C* tw = reinterpret_cast<const C*>(fa.tsx);
+  block_fft<T, LOGNH, E>(buf, t, t < NT, tw, 1);
+  even_odd_split<T>(buf, NH, reinterpret_cast<const C*>(fa.rtw),
+                    inter + ((size_t)f * fa.ny + j) * fa.pitch);
+}
+
+// rows of NH = 64 N2 complex pairs (N2 = 3, 5, 6, 10, 12: the non-power-of-two row
+// lengths), FP32, one block of 128 threads per (row, function), in shared memory:
+//   n = N2 n1 + n2, k = k1 + 64 k2;
+//   step 1: for each n2 (a group of 8 lanes, 8 values each): the 64-point DFT over n1
+//           (length-8 DFT in registers, twiddles w_64^(l m), exchange inside the group,
+//           length-8 DFT), the twiddle w_NH^(n2 k1), back in place at N2 k1 + n2;
+//   step 2: for each k1 (64 threads): the N2-point DFT over n2 in registers, written to
+//           k1 + 64 k2 (natural order), then the even/odd split to the spectrum.
+// Twiddles from the row table w_NH^t (w_64^k = w[N2 k], w_N2^k = w[64 k]).
+template <int N2> __device__ __forceinline__ void dft_len(float2* x, const float2* __restrict__ w) {
+  if constexpr (N2 == 3 || N2 == 5) dft<float, float2, N2>(x);
+  else if constexpr (N2 == 6) dft_ct<2, 3>(x, w, 64);
+  else if constexpr (N2 == 10) dft_ct<2, 5>(x, w, 64);
+  else dft_ct<4, 3>(x, w, 64);  // 12
+}
+
+template <int N2>
+__global__ void __launch_bounds__(128)
+k_rows_64n(FftArgs fa, RowArgs ra, int mode, const float* __restrict__ ext,
+           const double* __restrict__ f_grid, const float* __restrict__ vals,
+           float2* __restrict__ inter) {
+  constexpr int NH = 64 * N2;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float2* buf = reinterpret_cast<float2*>(smem_raw);
+  float2* ex = buf + padded<float>(NH);  // [N2][8][9] exchange tiles
+  const int j = blockIdx.x, f = blockIdx.y, t = threadIdx.x;
+  const float2* w = reinterpret_cast<const float2*>(fa.twx);
+  pdl_wait();
+  pdl_trigger();
+  assemble_row<float, float>(ra, mode, NH, j, f, ext, f_grid, vals, buf);
+  if (t < 8 * N2) {
+    const int n2 = t >> 3, l = t & 7;
+    float2* e = ex + n2 * 72;
+    float2 a[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) a[i] = buf[pad<float>(N2 * (l + 8 * i) + n2)];
+    dft<float, float2, 8>(a);
+#pragma unroll
+    for (int m = 1; m < 8; ++m) a[m] = mul(a[m], __ldg(w + ((l * m) & 63) * N2));
+#pragma unroll
+    for (int m = 0; m < 8; ++m) e[m * 9 + l] = a[m];
+    __syncwarp(0xFFu << (t & 24));
+#pragma unroll
+    for (int k = 0; k < 8; ++k) a[k] = e[l * 9 + k];
+    dft<float, float2, 8>(a);
+#pragma unroll
+    for (int m2 = 0; m2 < 8; ++m2) {
+      const int k1 = l + 8 * m2;
+      buf[pad<float>(N2 * k1 + n2)] = mul(a[m2], __ldg(w + n2 * k1));  // n2 k1 < NH
+    }
+  }
+  __syncthreads();
+  float2 x[N2];
+  if (t < 64) {
+#pragma unroll
+    for (int n2 = 0; n2 < N2; ++n2) x[n2] = buf[pad<float>(N2 * t + n2)];
+    dft_len<N2>(x, w);
+  }
+  __syncthreads();
+  if (t < 64) {
+#pragma unroll
+    for (int k2 = 0; k2 < N2; ++k2) buf[pad<float>(t + 64 * k2)] = x[k2];
+  }
+  __syncthreads();
+  even_odd_split<float>(buf, NH, reinterpret_cast<const float2*>(fa.rtw),
+                        inter + ((size_t)f * fa.ny + j) * fa.pitch);
+}
+
+template <int N2>
+static void rows64n_launch(const FftArgs& fa, const RowArgs& ra, int n_f, int mode, const void* ext,
+                           const double* fg, const void* vals, void* inter, cudaStream_t s) {
+  const size_t sm = ((size_t)padded<float>(64 * N2) + 72 * N2) * sizeof(float2);
+  auto k = k_rows_64n<N2>;
+  cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  launch_pdl(k, dim3(fa.ny, n_f), dim3(128), sm, s, fa, ra, mode, (const float*)ext, fg,
+             (const float*)vals, (float2*)inter);
 }
 
 // cols: ny = 2^LOGNY, CB columns per block, block = CB * NT threads.  Thread
@@ -551,33 +677,6 @@ __global__ void __launch_bounds__(128) k_cols4k_b(FftArgs fa, int drop,
 //           m1 + 64 m2; then the intermediate's lines are dropped from L2.
 // ------------------------------------------------------------------------- //
 
-// Length R1 R2 DFT in registers (Cooley-Tukey, n = R2 n1 + n2, k = k1 + R1 k2):
-// R2 DFTs of length R1, the twiddles w_{R1 R2}^(n2 k1) (wt[t * ws] = w_{R1 R2}^t), R1
-// DFTs of length R2.  x holds the input in natural order and receives the output.
-template <int R1, int R2>
-__device__ __forceinline__ void dft_ct(float2* x, const float2* __restrict__ wt, int ws) {
-  float2 a[R1 * R2];
-#pragma unroll
-  for (int n2 = 0; n2 < R2; ++n2) {
-    float2 v[R1];
-#pragma unroll
-    for (int n1 = 0; n1 < R1; ++n1) v[n1] = x[R2 * n1 + n2];
-    dft<float, float2, R1>(v);
-#pragma unroll
-    for (int k1 = 0; k1 < R1; ++k1)
-      a[n2 * R1 + k1] = (n2 * k1) ? mul(v[k1], __ldg(wt + (n2 * k1) * ws)) : v[k1];
-  }
-#pragma unroll
-  for (int k1 = 0; k1 < R1; ++k1) {
-    float2 u[R2];
-#pragma unroll
-    for (int n2 = 0; n2 < R2; ++n2) u[n2] = a[n2 * R1 + k1];
-    dft<float, float2, R2>(u);
-#pragma unroll
-    for (int k2 = 0; k2 < R2; ++k2) x[k1 + R1 * k2] = u[k2];
-  }
-}
-
 __global__ void __launch_bounds__(128) k_cols64_a(FftArgs fa, int n2, float2* __restrict__ inter) {
   __shared__ float2 ex[64 * kC4Cols];
   const int c = threadIdx.x & (kC4Cols - 1), l = threadIdx.x / kC4Cols;
@@ -712,6 +811,22 @@ bool launch_fft_rows_p2(const FftArgs& fa, const RowArgs& ra, int n_f, bool fp64
     default: return false;
   }
 #undef FC2D_ROWS
+}
+
+// FP32 rows of 2 x 64 N2 reals for N2 = 3, 5, 6, 10, 12.  Returns false (nothing launched)
+// for other sizes.
+bool launch_fft_rows_64n(const FftArgs& fa, const RowArgs& ra, int n_f, bool fp64, int mode,
+                         const void* ext, const double* f_grid, const void* vals, void* inter,
+                         cudaStream_t s) {
+  if (fp64 || fa.nx % 128) return false;
+  switch (fa.nx / 128) {
+    case 3: p2::rows64n_launch<3>(fa, ra, n_f, mode, ext, f_grid, vals, inter, s); return true;
+    case 5: p2::rows64n_launch<5>(fa, ra, n_f, mode, ext, f_grid, vals, inter, s); return true;
+    case 6: p2::rows64n_launch<6>(fa, ra, n_f, mode, ext, f_grid, vals, inter, s); return true;
+    case 10: p2::rows64n_launch<10>(fa, ra, n_f, mode, ext, f_grid, vals, inter, s); return true;
+    case 12: p2::rows64n_launch<12>(fa, ra, n_f, mode, ext, f_grid, vals, inter, s); return true;
+    default: return false;
+  }
 }
 
 // FP32 columns of 64 N2 points for N2 = 6, 10, 12, 24 (two passes).  Returns false
