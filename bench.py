@@ -43,14 +43,7 @@ FP64_PEAK_TFLOPS = 1.25   # GB300 FP64 (nominal; 152 SMs x 2 DFMA/clk x 2 flop x
 # on this workload, from one ncu capture of the current kernels (cold cache, serialised
 # launches; a scope with two kernels sums both).  A kernel changed after its capture
 # has no entry, and the roofline then reports traffic null.
-MEASURED_TRAFFIC = {
-    # k_cols4k_a (67409408 + 9991424) + k_cols4k_b (67500800 + 15403520)
-    ("mixed", "fft_cols"): 160305152,
-    ("mixed", "fft_rows_fused"): 70920960 + 19312640,
-    ("mixed", "gather_blend_interp_tc"): 34109440 + 256,
-    ("fp64", "fft_cols"): 141588736 + 92130048,
-    ("fp64", "fft_rows_fused"): 72346368 + 74370560,
-}
+MEASURED_TRAFFIC = {}
 
 
 def peaks():
@@ -318,53 +311,66 @@ def measure(fc2d, torch, w, precision, K, warmup, world, dev, fg_h, fb_h, sample
     npts = g.nx * g.ny
     value = replica_throughput(world, K, npts, ms)
     # end to end through the public API with host buffers: every step copies its
-    # inputs from pinned host memory, calls fc2d_extend_coeffs and reads its spectrum
-    # back to pinned host memory.  Steps are pipelined as a user streaming functions
-    # would: copies in on one stream, compute on another, copies out on a third, with
-    # two device buffers of each kind (the plan's workspace is used by one compute
-    # stream only).
-    Ke = min(K, 30)
-    fhat_h = [torch.empty(fhat.shape, dtype=cdt).pin_memory() for _ in range(2)]
-    fg_d = [torch.empty_like(fg) for _ in range(2)]
-    fb_d = [torch.empty_like(fb) for _ in range(2)]
-    fh_d = [torch.empty_like(fhat) for _ in range(2)]
-    s_in, s_cmp, s_out = torch.cuda.Stream(dev), torch.cuda.Stream(dev), torch.cuda.Stream(dev)
-    ev = lambda: torch.cuda.Event()
-    in_done = [ev(), ev()]
-    cmp_done = [ev(), ev()]
-    out_done = [ev(), ev()]
+    # inputs from pinned host memory, calls the library and reads its spectrum back to
+    # pinned host memory.  Steps are pipelined as a user streaming functions would:
+    # copies in on one stream, compute on another, copies out on a third, with two
+    # device buffers of each kind (the plan's workspace is used by one compute stream
+    # only).  The headline form passes f at the domain's grid points only
+    # (fc2d_extend_coeffs_compact, the method's data); the full-grid form
+    # (fc2d_extend_coeffs) is timed beside it.
+    lin = torch.from_numpy(plan.fc2d_inside_points())
+    fin_h = fg_h.reshape(-1)[lin].contiguous().pin_memory()
 
-    def e2e_step(k):
-        b = k % 2
-        with torch.cuda.stream(s_in):
-            s_in.wait_event(cmp_done[b])          # compute k-2 has read these inputs
-            fg_d[b].copy_(fg_h, non_blocking=True)
-            fb_d[b].copy_(fb_h, non_blocking=True)
-            in_done[b].record(s_in)
-        s_cmp.wait_event(in_done[b])
-        s_cmp.wait_event(out_done[b])             # copy-out k-2 has read this spectrum
-        plan.fc2d_extend_coeffs(1, fg_d[b], fb_d[b], fh_d[b], s_cmp)
-        cmp_done[b].record(s_cmp)
-        with torch.cuda.stream(s_out):
-            s_out.wait_event(cmp_done[b])
-            fhat_h[b].copy_(fh_d[b], non_blocking=True)
-            out_done[b].record(s_out)
+    def e2e(compact):
+        Ke = min(K, 30)
+        src_h = fin_h if compact else fg_h
+        fhat_h = [torch.empty(fhat.shape, dtype=cdt).pin_memory() for _ in range(2)]
+        fg_d = [torch.empty(src_h.shape, dtype=src_h.dtype, device=dev) for _ in range(2)]
+        fb_d = [torch.empty_like(fb) for _ in range(2)]
+        fh_d = [torch.empty_like(fhat) for _ in range(2)]
+        s_in, s_cmp, s_out = torch.cuda.Stream(dev), torch.cuda.Stream(dev), torch.cuda.Stream(dev)
+        ev = lambda: torch.cuda.Event()
+        in_done = [ev(), ev()]
+        cmp_done = [ev(), ev()]
+        out_done = [ev(), ev()]
+        call = plan.fc2d_extend_coeffs_compact if compact else plan.fc2d_extend_coeffs
 
-    torch.cuda.synchronize()
-    for k in range(2):
-        e2e_step(k)
-    torch.cuda.synchronize()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(s_in)
-    for k in range(Ke):
-        e2e_step(k)
-    for b in range(2):
-        s_out.wait_event(out_done[b])
-    e1.record(s_out)
-    torch.cuda.synchronize()
-    plan.fc2d_sync_status(s_cmp)
-    e2e_ms = max_over_ranks(e0.elapsed_time(e1) / Ke, world, dev)
+        def step(k):
+            b = k % 2
+            with torch.cuda.stream(s_in):
+                s_in.wait_event(cmp_done[b])      # compute k-2 has read these inputs
+                fg_d[b].copy_(src_h, non_blocking=True)
+                fb_d[b].copy_(fb_h, non_blocking=True)
+                in_done[b].record(s_in)
+            s_cmp.wait_event(in_done[b])
+            s_cmp.wait_event(out_done[b])         # copy-out k-2 has read this spectrum
+            call(1, fg_d[b], fb_d[b], fh_d[b], s_cmp)
+            cmp_done[b].record(s_cmp)
+            with torch.cuda.stream(s_out):
+                s_out.wait_event(cmp_done[b])
+                fhat_h[b].copy_(fh_d[b], non_blocking=True)
+                out_done[b].record(s_out)
+
+        torch.cuda.synchronize()
+        for k in range(2):
+            step(k)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(s_in)
+        for k in range(Ke):
+            step(k)
+        for b in range(2):
+            s_out.wait_event(out_done[b])
+        e1.record(s_out)
+        torch.cuda.synchronize()
+        plan.fc2d_sync_status(s_cmp)
+        ms_step = max_over_ranks(e0.elapsed_time(e1) / Ke, world, dev)
+        h2d = int(src_h.numel() * src_h.element_size() + fb_h.numel() * fb_h.element_size())
+        return ms_step, h2d
+
+    e2e_ms, e2e_h2d = e2e(True)
+    e2e_full_ms, e2e_full_h2d = e2e(False)
     # roofline of the dominant kernel
     hbm, src = peaks()
     alg = algorithmic(plan, w, fp64)
@@ -390,9 +396,13 @@ def measure(fc2d, torch, w, precision, K, warmup, world, dev, fg_h, fb_h, sample
             "wall_s_timed": wall, "clocks": clocks, "roofline": roof, "kernels": kernels,
             "gpu_launches": sum(v[0] for v in prof.values()),
             "e2e": {"value": replica_throughput(world, 1, npts, e2e_ms), "unit": UNIT,
+                    "api": "fc2d_extend_coeffs_compact (f at the domain's grid points)",
                     "pipeline": "copy-in, compute, copy-out on three streams, two buffers",
-                    "h2d_bytes_per_step": int(fg.numel() * 8 + fb.numel() * 8),
-                    "d2h_bytes_per_step": int(fhat.numel() * fhat.element_size())},
+                    "h2d_bytes_per_step": e2e_h2d,
+                    "d2h_bytes_per_step": int(fhat.numel() * fhat.element_size()),
+                    "full_grid": {"api": "fc2d_extend_coeffs (f on the whole grid)",
+                                  "value": replica_throughput(world, 1, npts, e2e_full_ms),
+                                  "h2d_bytes_per_step": e2e_full_h2d}},
             "fhat": fhat}
 
 
@@ -417,6 +427,12 @@ def poisson_star1024(fc2d, torch, dev, solves=3):
         plan.fc2d_poisson(1, fg, fb, gn, out)
     torch.cuda.synchronize()
     dt = (time.perf_counter() - t0) / solves
+    plan.fc2d_profile(True)
+    plan.fc2d_profile_read()
+    plan.fc2d_poisson(1, fg, fb, gn, out)
+    torch.cuda.synchronize()
+    plan.fc2d_profile(False)
+    prof = plan.fc2d_profile_read()
     X, Y = np.meshgrid(*w.grid.coords())
     ue = u(X, Y)
     got = out.cpu().numpy()[0]
@@ -424,7 +440,8 @@ def poisson_star1024(fc2d, torch, dev, solves=3):
     err = float(np.abs(got - ue)[inside].max() / np.abs(ue[inside]).max())
     return {"workload": "star1024 Poisson, u = sin(2x) e^y", "ms_per_solve": 1e3 * dt,
             "value": g.nx * g.ny / dt, "unit": UNIT, "max_rel_err_vs_exact": err,
-            "gmres": plan.fc2d_poisson_info()}
+            "gmres": plan.fc2d_poisson_info(),
+            "kernels_ms": {k: v[1] / v[0] for k, v in prof.items()}}
 
 
 def stars8_batched(fc2d, torch, dev, replays=10):

@@ -145,6 +145,22 @@ fc2d_status fc2d_coeffs(fc2d_plan_t plan, int n_f, const void* ext_dev, void* fh
 fc2d_status fc2d_extend_coeffs(fc2d_plan_t plan, int n_f, const double* f_grid_dev,
                                const double* f_bdry_dev, void* fhat_dev, void* stream);
 
+/* The grid points of the closed domain (the points where f is given; Section 3.1) in the
+ * order of the compact entry point below: row by row (y ascending), within a row by x.
+ * lin_host (host memory, n_inside entries from fc2d_plan_info) receives their linear
+ * indices j * nx + i.  Pure host call. */
+fc2d_status fc2d_inside_points(fc2d_plan_t plan, int64_t* lin_host);
+
+/* fc2d_extend_coeffs with f given only where the method uses it, at the grid points of
+ * the closed domain (Section 3.1: the data of the 2D-FC problem are f on H ∩ Ω):
+ * f_inside_dev [n_f][n_inside] in the order of fc2d_inside_points.  Same kernels and
+ * arithmetic as fc2d_extend_coeffs, so the same spectrum bit for bit; the input is
+ * n_inside instead of nx * ny values (about half for the kite), which halves the
+ * host-to-device copy of a caller that streams f from host memory.  Returns
+ * FC2D_ERR_UNSUPPORTED when n_inside exceeds 2^31 - 1. */
+fc2d_status fc2d_extend_coeffs_compact(fc2d_plan_t plan, int n_f, const double* f_inside_dev,
+                                       const double* f_bdry_dev, void* fhat_dev, void* stream);
+
 /* The DFT of fc2d_coeffs for callers that cannot allocate device memory at call time.
  * The paper has no counterpart: this is a service of the library.  fc2d_coeffs grows
  * plan workspace with cudaMalloc on the first call of a new size; this entry point

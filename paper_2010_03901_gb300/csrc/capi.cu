@@ -65,18 +65,19 @@ Layout layout(const fc2d_plan_s* p, int n_f) {
 
 char* ws(fc2d_plan_s* p, size_t off) { return static_cast<char*>(p->ws.base) + off; }
 
+// compact: f given at the inside points only ([n_f][n_inside], row by row)
 GatherArgs gather_args(fc2d_plan_s* p, const double* fg, const double* fb, void* F,
-                       double* coef, double* bvals) {
+                       double* coef, double* bvals, bool compact = false) {
   GatherArgs a{};
   a.B = p->prm.B;
   a.M = p->prm.M;
   a.d = p->prm.d;
   a.Cr = p->Cr;
   a.n_bdry = p->n_bdry;
-  a.grid_stride = (int64_t)p->grid.nx * p->grid.ny;
+  a.grid_stride = compact ? p->n_inside : (int64_t)p->grid.nx * p->grid.ny;
   a.f_grid = fg;
   a.f_bdry = fb;
-  a.gidx = p->dev.gidx;
+  a.gidx = compact ? p->dev.gidx_c : p->dev.gidx;
   a.gw = p->dev.gw;
   a.wn = p->dev.wn;
   a.Q = p->dev.Q;
@@ -101,11 +102,12 @@ InterpArgs interp_args(fc2d_plan_s* p, int ldF) {
   return a;
 }
 
-RowArgs row_args(fc2d_plan_s* p) {
+RowArgs row_args(fc2d_plan_s* p, bool compact = false) {
   RowArgs a{};
   a.nx = p->grid.nx;
   a.ny = p->grid.ny;
-  a.grid_stride = (int64_t)p->grid.nx * p->grid.ny;
+  a.grid_stride = compact ? p->n_inside : (int64_t)p->grid.nx * p->grid.ny;
+  a.row_iv_coff = p->dev.row_iv_coff;
   a.n_strip = (int64_t)p->strip_lin.size();
   a.row_iv_off = p->dev.row_iv_off;
   a.row_iv = p->dev.row_iv;
@@ -146,10 +148,10 @@ fc2d_status launched(const char* what) { return cuda_check(cudaGetLastError(), w
 // Mixed form of step 5: matching values and Gram coefficients in FP64, then the
 // contraction with A_r on the tensor cores into float strip values F.
 fc2d_status mixed_blend(fc2d_plan_s* p, int n_f, const double* fg, const double* fb, void* F,
-                        int ldF, const Layout& L, cudaStream_t s) {
+                        int ldF, const Layout& L, cudaStream_t s, bool compact = false) {
   if (p->prm.M - 1 <= 8 && p->prm.d <= 8) {
     ProfScope ps(p, "gather_blend_tc", s);
-    return launch_gather_blend_tc(gather_args(p, fg, fb, nullptr, nullptr, nullptr), n_f,
+    return launch_gather_blend_tc(gather_args(p, fg, fb, nullptr, nullptr, nullptr, compact), n_f,
                                   ldF, p->dev.Ar_hi, p->dev.Ar_lo, static_cast<float*>(F),
                                   p->dev.status, s);
   }
@@ -157,7 +159,7 @@ fc2d_status mixed_blend(fc2d_plan_s* p, int n_f, const double* fg, const double*
   double* bvals = reinterpret_cast<double*>(ws(p, L.obvals));
   {
     ProfScope ps(p, "gather_coef", s);
-    launch_gather_blend(gather_args(p, fg, fb, nullptr, coef, bvals), n_f, false, s);
+    launch_gather_blend(gather_args(p, fg, fb, nullptr, coef, bvals, compact), n_f, false, s);
   }
   ProfScope ps(p, "blend_tc", s);
   return launch_blend_tc(n_f * p->prm.B, p->Cr, p->prm.d, ldF, coef, kMaxD, bvals,
@@ -166,13 +168,13 @@ fc2d_status mixed_blend(fc2d_plan_s* p, int n_f, const double* fg, const double*
 
 // Steps 5 and 6 into workspace: strip values F, then the strip-point values.
 fc2d_status strip_values(fc2d_plan_s* p, int n_f, const double* fg, const double* fb,
-                         const Layout& L, cudaStream_t s) {
+                         const Layout& L, cudaStream_t s, bool compact = false) {
   const bool f64 = p->prm.precision == FC2D_FP64;
   void* F = ws(p, L.oF);
   if (!f64 && p->dev.own_off) {
     // mixed form, M = 8: blend and interpolation in one kernel, F stays on chip
     ProfScope ps(p, "gather_blend_interp_tc", s);
-    return launch_gather_interp_tc(gather_args(p, fg, fb, nullptr, nullptr, nullptr), n_f,
+    return launch_gather_interp_tc(gather_args(p, fg, fb, nullptr, nullptr, nullptr, compact), n_f,
                                    ws_ldF(p), p->dev.Ar_hi, p->dev.Ar_lo, p->dev.own_off,
                                    p->dev.own_k, p->dev.own_pack, p->dev.own_w, p->dev.n_own,
                                    (int)p->strip_lin.size(),
@@ -180,9 +182,9 @@ fc2d_status strip_values(fc2d_plan_s* p, int n_f, const double* fg, const double
   }
   if (f64) {
     ProfScope ps(p, "gather_blend", s);
-    launch_gather_blend(gather_args(p, fg, fb, F, nullptr, nullptr), n_f, true, s);
+    launch_gather_blend(gather_args(p, fg, fb, F, nullptr, nullptr, compact), n_f, true, s);
   } else {
-    fc2d_status st = mixed_blend(p, n_f, fg, fb, F, ws_ldF(p), L, s);
+    fc2d_status st = mixed_blend(p, n_f, fg, fb, F, ws_ldF(p), L, s, compact);
     if (st) return st;
   }
   {
@@ -283,6 +285,44 @@ extern "C" fc2d_status fc2d_extend_coeffs(fc2d_plan_t p, int n_f, const double* 
     launch_fft_cols(fa, n_f, f64, ws(p, L.ointer), fhat, s);
   }
   return launched("fc2d_extend_coeffs");
+}
+
+extern "C" fc2d_status fc2d_inside_points(fc2d_plan_t p, int64_t* lin_host) {
+  if (!p || !lin_host) return set_error(FC2D_ERR_ARG, "fc2d_inside_points: null argument");
+  const int nx = p->grid.nx, ny = p->grid.ny;
+  int64_t n = 0;
+  for (int j = 0; j < ny; ++j)
+    for (int k = p->row_iv_off[j]; k < p->row_iv_off[j + 1]; ++k)
+      for (int i = p->row_iv[2 * k]; i <= p->row_iv[2 * k + 1]; ++i) lin_host[n++] = (int64_t)j * nx + i;
+  return FC2D_OK;
+}
+
+extern "C" fc2d_status fc2d_extend_coeffs_compact(fc2d_plan_t p, int n_f, const double* f_inside,
+                                                  const double* fb, void* fhat, void* stream) {
+  fc2d_status st = check_nf(p, n_f);
+  if (st) return st;
+  if (!f_inside || !fb || !fhat)
+    return set_error(FC2D_ERR_ARG, "fc2d_extend_coeffs_compact: null pointer");
+  if (!p->dev.row_iv_coff || !p->dev.gidx_c)
+    return set_error(FC2D_ERR_UNSUPPORTED,
+                     "fc2d_extend_coeffs_compact: more than 2^31 - 1 inside points");
+  cudaSetDevice(p->device);
+  Layout L = layout(p, n_f);
+  if ((st = ensure_workspace(p, L.total))) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  const bool f64 = p->prm.precision == FC2D_FP64;
+  FftArgs fa = fft_args(p);
+  if ((st = strip_values(p, n_f, f_inside, fb, L, s, true))) return st;
+  {
+    ProfScope ps(p, "fft_rows_fused", s);
+    launch_fft_rows(fa, row_args(p, true), n_f, f64, 2, nullptr, f_inside, ws(p, L.ovals),
+                    ws(p, L.ointer), s);
+  }
+  {
+    ProfScope ps(p, "fft_cols", s);
+    launch_fft_cols(fa, n_f, f64, ws(p, L.ointer), fhat, s);
+  }
+  return launched("fc2d_extend_coeffs_compact");
 }
 
 extern "C" fc2d_status fc2d_sync_status(fc2d_plan_t p, void* stream) {

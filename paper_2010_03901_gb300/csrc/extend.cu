@@ -325,8 +325,7 @@ __global__ void k_assemble_rows(RowArgs a, const double* __restrict__ f_grid,
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T* row = reinterpret_cast<T*>(smem_raw);
   const int j = blockIdx.x, f = blockIdx.y, nx = a.nx;
-  const double* fg = f_grid + (size_t)f * a.grid_stride + (size_t)j * nx;
-  load_row<T>(a, j, f, fg, vals, row);
+  load_row<T>(a, j, f, f_grid + (size_t)f * a.grid_stride, false, vals, row);
   __syncthreads();
   T* out = ext + (size_t)f * a.grid_stride + (size_t)j * nx;
   for (int i = threadIdx.x; i < nx; i += blockDim.x) out[i] = row[i];

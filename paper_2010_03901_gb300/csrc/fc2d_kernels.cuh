@@ -45,6 +45,7 @@ struct RowArgs {
   const int32_t* row_iv;
   const int32_t* row_strip_off;
   const int32_t* s_lin;
+  const int32_t* row_iv_coff;  // mode 2 (compact input): compact offset of each interval
 };
 
 #if defined(__CUDACC__)
@@ -78,9 +79,11 @@ inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, s
 
 // Fill a shared-memory row with the extension: 0, then f on the inside intervals,
 // then the strip values.  Ends with the row complete (after a __syncthreads()).
+// fg: the function's grid values ([ny][nx], compact == false) or its inside values
+// ([n_inside] row by row, compact == true).
 template <typename T, typename TV>
 __device__ __forceinline__ void load_row(const RowArgs& a, int j, int f,
-                                         const double* __restrict__ fg_row,
+                                         const double* __restrict__ fg, bool compact,
                                          const TV* __restrict__ vals, T* row) {
   const int nx = a.nx;
   for (int i = threadIdx.x; i < nx; i += blockDim.x) row[i] = T(0);
@@ -88,7 +91,9 @@ __device__ __forceinline__ void load_row(const RowArgs& a, int j, int f,
   const int iv0 = __ldg(a.row_iv_off + j), iv1 = __ldg(a.row_iv_off + j + 1);
   for (int k = iv0; k < iv1; ++k) {
     const int lo = __ldg(a.row_iv + 2 * k), hi = __ldg(a.row_iv + 2 * k + 1);
-    for (int i = lo + threadIdx.x; i <= hi; i += blockDim.x) row[i] = (T)__ldg(fg_row + i);
+    const double* src = compact ? fg + ((int64_t)__ldg(a.row_iv_coff + k) - lo)
+                                : fg + (size_t)j * nx;
+    for (int i = lo + threadIdx.x; i <= hi; i += blockDim.x) row[i] = (T)__ldg(src + i);
   }
   const int s0 = __ldg(a.row_strip_off + j), s1 = __ldg(a.row_strip_off + j + 1);
   const TV* v = vals + (size_t)f * a.n_strip;
@@ -133,7 +138,8 @@ struct FftArgs {
 };
 
 // rows: mode 0 reads an extended grid (ext, type T); mode 1 assembles the extension
-// on the fly from f_grid + strip values.
+// on the fly from f_grid + strip values; mode 2 likewise from f given at the inside
+// points only (f_grid = [n_f][n_inside], row by row; ra.grid_stride = n_inside).
 void launch_fft_rows(const FftArgs& fa, const RowArgs& ra, int n_f, bool fp64, int mode,
                      const void* ext, const double* f_grid, const void* vals, void* inter,
                      cudaStream_t s);

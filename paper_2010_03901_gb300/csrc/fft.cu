@@ -37,7 +37,7 @@ __global__ void __launch_bounds__(256) k_fft_rows(FftArgs fa, RowArgs ra, int mo
     const T* src = ext + (size_t)f * ra.grid_stride + (size_t)j * nx;
     for (int i = threadIdx.x; i < nx; i += blockDim.x) rowr[i] = src[i];
   } else {
-    load_row<T>(ra, j, f, f_grid + (size_t)f * ra.grid_stride + (size_t)j * nx, vals, rowr);
+    load_row<T>(ra, j, f, f_grid + (size_t)f * ra.grid_stride, mode == 2, vals, rowr);
   }
   __syncthreads();
   const C* tw = reinterpret_cast<const C*>(fa.twx);

@@ -378,19 +378,22 @@ __device__ __forceinline__ void assemble_row(const RowArgs& ra, int mode, int NH
       buf[pad<T>(n)] = v;
     }
   } else {
-    const double* fg = f_grid + (size_t)f * ra.grid_stride + (size_t)j * nx;
+    // mode 1: element i of the row at fg[i]; mode 2 (compact): at fin[coff_k + i - lo_k]
+    const double* fg = mode == 1 ? f_grid + (size_t)f * ra.grid_stride + (size_t)j * nx
+                                 : f_grid + (size_t)f * ra.grid_stride;
     const int iv0 = __ldg(ra.row_iv_off + j), iv1 = __ldg(ra.row_iv_off + j + 1);
     for (int n = threadIdx.x; n < NH; n += blockDim.x) buf[pad<T>(n)] = C{(T)0, (T)0};
     __syncthreads();
     // inside intervals [lo, hi]: the pairs n with lo <= 2n and 2n + 1 <= hi as one
-    // 16-byte load each when the row is 16-byte aligned (eight loads in flight per
-    // thread), the odd ends element by element
-    const bool vec = (reinterpret_cast<uintptr_t>(fg) & 15) == 0;
+    // 16-byte load each when the source is 16-byte aligned at even i (eight loads in
+    // flight per thread), the odd ends element by element
     for (int k = iv0; k < iv1; ++k) {
       const int lo = __ldg(ra.row_iv + 2 * k), hi = __ldg(ra.row_iv + 2 * k + 1);
+      const double* src = mode == 1 ? fg : fg + ((int64_t)__ldg(ra.row_iv_coff + k) - lo);
+      const bool vec = (reinterpret_cast<uintptr_t>(src) & 15) == 0;
       if (vec) {
         const int p0 = (lo + 1) >> 1, p1 = (hi + 1) >> 1;  // pairs p0 .. p1 - 1
-        const double2* fg2 = reinterpret_cast<const double2*>(fg);
+        const double2* fg2 = reinterpret_cast<const double2*>(src);
         for (int n0 = p0 + threadIdx.x; n0 < p1; n0 += 8 * blockDim.x) {
           double2 d[8];
 #pragma unroll
@@ -404,10 +407,10 @@ __device__ __forceinline__ void assemble_row(const RowArgs& ra, int mode, int NH
             if (n < p1) buf[pad<T>(n)] = C{from_double<T>(d[u].x), from_double<T>(d[u].y)};
           }
         }
-        if (threadIdx.x == 0 && (lo & 1)) put(lo, from_double<T>(__ldg(fg + lo)));
-        if (threadIdx.x == 0 && !(hi & 1)) put(hi, from_double<T>(__ldg(fg + hi)));
+        if (threadIdx.x == 0 && (lo & 1)) put(lo, from_double<T>(__ldg(src + lo)));
+        if (threadIdx.x == 0 && !(hi & 1)) put(hi, from_double<T>(__ldg(src + hi)));
       } else {
-        for (int i = lo + threadIdx.x; i <= hi; i += blockDim.x) put(i, from_double<T>(__ldg(fg + i)));
+        for (int i = lo + threadIdx.x; i <= hi; i += blockDim.x) put(i, from_double<T>(__ldg(src + i)));
       }
     }
     const int s0 = __ldg(ra.row_strip_off + j), s1 = __ldg(ra.row_strip_off + j + 1);

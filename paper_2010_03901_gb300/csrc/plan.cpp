@@ -522,6 +522,14 @@ extern "C" fc2d_status fc2d_plan(const fc2d_boundary* boundary, const fc2d_grid*
     }
   }
   p->row_iv_off[ny] = (int32_t)(p->row_iv.size() / 2);
+  {
+    int64_t off = 0;
+    p->row_iv_coff.resize(p->row_iv.size() / 2);
+    for (size_t k = 0; k < p->row_iv_coff.size(); ++k) {
+      p->row_iv_coff[k] = (int32_t)off;
+      off += p->row_iv[2 * k + 1] - p->row_iv[2 * k] + 1;
+    }
+  }
 
   // boundary nodes and normals (eq. (3.4))
   std::vector<double> bx(B), by(B), bnx(B), bny(B), th(B);
@@ -755,6 +763,24 @@ extern "C" fc2d_status fc2d_plan(const fc2d_boundary* boundary, const fc2d_grid*
   std::vector<double> tsx16 = stage_twiddles(p->fx, 16), tsy16 = stage_twiddles(p->fy, 16);
   std::vector<float> tsx32(tsx16.begin(), tsx16.end()), tsy32(tsy16.begin(), tsy16.end());
   std::vector<int> zero_status(1, 0);
+  // the stencil taps as compact indices (every grid tap is an inside point); the
+  // compact form is offered when the inside points have int32 indices
+  const bool compact = p->n_inside < ((int64_t)1 << 31);
+  std::vector<int32_t> gidx_c(compact ? gidx.size() : 0);
+  for (size_t e = 0; e < gidx_c.size(); ++e) {
+    const int32_t id = gidx[e];
+    if (id < 0) {
+      gidx_c[e] = id;
+      continue;
+    }
+    const int jr = id / nx, ic = id - jr * nx;
+    int32_t c = -1;
+    for (int k = p->row_iv_off[jr]; k < p->row_iv_off[jr + 1]; ++k)
+      if (ic >= p->row_iv[2 * k] && ic <= p->row_iv[2 * k + 1])
+        c = p->row_iv_coff[k] + (ic - p->row_iv[2 * k]);
+    if (c < 0) return fail(set_error(FC2D_ERR_GEOMETRY, "a matching stencil tap is not an inside point"));
+    gidx_c[e] = c;
+  }
   if ((st = upload(&p->dev.Q, p->Q)) || (st = upload(&p->dev.Ar, p->Ar)) ||
       (st = upload(&p->dev.Ar_hi, arh)) || (st = upload(&p->dev.Ar_lo, arl)) ||
       (st = upload(&p->dev.gidx, gidx)) || (st = upload(&p->dev.gw, gw)) ||
@@ -764,6 +790,8 @@ extern "C" fc2d_status fc2d_plan(const fc2d_boundary* boundary, const fc2d_grid*
       (st = upload(&p->dev.row_iv_off, p->row_iv_off)) ||
       (st = upload(&p->dev.row_iv, p->row_iv)) ||
       (st = upload(&p->dev.row_strip_off, p->row_strip_off)) ||
+      (compact && (st = upload(&p->dev.row_iv_coff, p->row_iv_coff))) ||
+      (compact && (st = upload(&p->dev.gidx_c, gidx_c))) ||
       (st = upload(&p->dev.status, zero_status)) ||
       (st = upload(&p->fx.tw64, p->fx.tw_host)) || (st = upload(&p->fx.tw32, tw32x)) ||
       (st = upload(&p->fy.tw64, p->fy.tw_host)) || (st = upload(&p->fy.tw32, tw32y)) ||
@@ -837,7 +865,8 @@ extern "C" void fc2d_destroy(fc2d_plan_t p) {
                   p->dev.wn, p->dev.s_lin, p->dev.s_theta, p->dev.s_eta, p->dev.s_w,
                   p->dev.s_pb, p->dev.s_sb, p->dev.own_off, p->dev.own_k,
                   p->dev.own_pack, p->dev.own_w, p->dev.row_iv_off,
-                  p->dev.row_iv, p->dev.row_strip_off, p->dev.status, p->fx.tw64, p->fx.tw32,
+                  p->dev.row_iv, p->dev.row_strip_off, p->dev.row_iv_coff, p->dev.gidx_c,
+                  p->dev.status, p->fx.tw64, p->fx.tw32,
                   p->fy.tw64, p->fy.tw32, p->rtw64, p->rtw32, p->ws.base,
                   p->fx.tws64, p->fx.tws32, p->fy.tws64, p->fy.tws32};
   for (void* q : ptrs)

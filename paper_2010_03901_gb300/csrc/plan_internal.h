@@ -66,6 +66,10 @@ struct DeviceTables {
   int32_t* row_iv_off = nullptr;    // [ny+1] offsets into row_iv
   int32_t* row_iv = nullptr;        // pairs (i_lo, i_hi), inclusive
   int32_t* row_strip_off = nullptr; // [ny+1] offsets into the strip list
+  // compact input (f at the inside points only, row by row): the compact index of each
+  // inside interval's first point, and the stencil taps as compact indices
+  int32_t* row_iv_coff = nullptr;   // [n_iv]
+  int32_t* gidx_c = nullptr;        // [B][M-1][M] as gidx, >= 0 entries compact
   int* status = nullptr;            // latched device status word
 };
 
@@ -94,6 +98,7 @@ struct fc2d_plan_s {
   std::vector<int32_t> strip_lin;
   std::vector<double> strip_theta, strip_eta;
   std::vector<int32_t> row_iv_off, row_iv, row_strip_off;
+  std::vector<int32_t> row_iv_coff;         // compact offset of each inside interval
   int64_t n_inside = 0;
   int64_t n_bdry = 0;
   fc2d::FftAxis fx, fy;                      // nx/2 (complex) and ny

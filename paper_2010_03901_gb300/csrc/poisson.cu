@@ -708,7 +708,10 @@ fc2d_status poisson_solve(fc2d_plan_s* p, int n_f, const double* fg, const doubl
     double* uf = u + (size_t)f * nx * ny;
     k_up_nodes<<<gb, 256, 0, s>>>(Nb, MP, nx, P->ui0, P->uj0, P->uwx, P->uwy, uf,
                                   gn + (size_t)f * Nb, P->g);
-    if ((st = gmres(P, s, 1e-14))) return st;
+    {
+      ProfScope ps(p, "bie_gmres", s);
+      if ((st = gmres(P, s, 1e-14))) return st;
+    }
     if (phi_out) cudaMemcpyAsync(phi_out + (size_t)f * Nb, P->phi, Nb * 8, cudaMemcpyDeviceToDevice, s);
     // density refinement and node coefficients
     k_density_dft<<<(unsigned)((Nb / 2 + 1 + 127) / 128), 128, 0, s>>>(Nb, P->phi,

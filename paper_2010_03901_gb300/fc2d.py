@@ -70,6 +70,8 @@ def load_library(path: str = LIB_PATH):
         "fc2d_extend": [P, ct.c_int, P, P, P, P],
         "fc2d_coeffs": [P, ct.c_int, P, P, P],
         "fc2d_extend_coeffs": [P, ct.c_int, P, P, P, P],
+        "fc2d_inside_points": [P, P],
+        "fc2d_extend_coeffs_compact": [P, ct.c_int, P, P, P, P],
         "fc2d_coeffs_static": [P, ct.c_int, P, P, P],
         "fc2d_sync_status": [P, P],
         "fc2d_poisson_plan": [P, ct.c_int],
@@ -184,6 +186,16 @@ class Plan:
     def fc2d_extend_coeffs(self, n_f, f_grid, f_bdry, fhat, stream=None):
         _check(_lib.fc2d_extend_coeffs(self.handle, n_f, _ptr(f_grid), _ptr(f_bdry),
                                        _ptr(fhat), _stream(stream)))
+
+    def fc2d_inside_points(self):
+        """Linear indices j * nx + i of the domain's grid points, in compact order."""
+        out = np.zeros(self.n_inside, dtype=np.int64)
+        _check(_lib.fc2d_inside_points(self.handle, out.ctypes.data))
+        return out
+
+    def fc2d_extend_coeffs_compact(self, n_f, f_inside, f_bdry, fhat, stream=None):
+        _check(_lib.fc2d_extend_coeffs_compact(self.handle, n_f, _ptr(f_inside), _ptr(f_bdry),
+                                               _ptr(fhat), _stream(stream)))
 
     def fc2d_coeffs_static(self, n_f, ext, fhat, stream=None):
         """fc2d_coeffs without any device allocation (fixed 64 MiB scratch)."""

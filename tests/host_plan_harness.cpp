@@ -132,6 +132,8 @@ int main(int argc, char** argv) {
   dump("row_iv_off", p->row_iv_off.data(), p->row_iv_off.size());
   dump("row_iv", p->row_iv.data(), p->row_iv.size());
   dump("gidx", p->dev.gidx, B * (M - 1) * M);
+  dump("gidx_c", p->dev.gidx_c, B * (M - 1) * M);
+  dump("row_iv_coff", p->row_iv_coff.data(), p->row_iv_coff.size());
   dump("gw", p->dev.gw, B * (M - 1) * M);
   dump("wn", p->dev.wn, B * (d - 1) * M);
   return 0;

@@ -246,6 +246,30 @@ def test_mixed_extend_coeffs_within_1e6(case, mixed, mats):
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_compact_input_equals_full_grid(case, fc2d, precision):
+    """fc2d_inside_points lists the oracle's inside points in row-major order, and
+    fc2d_extend_coeffs_compact on f at those points gives the spectrum of
+    fc2d_extend_coeffs on the full grid bit for bit (three functions batched)."""
+    torch = case.torch
+    w = case.w
+    g, p = w.grid, w.params
+    prec = fc2d.FC2D_FP64 if precision == "fp64" else fc2d.FC2D_MIXED
+    plan = case.plan if precision == "fp64" else fc2d.fc2d_plan(
+        w.boundary.arrays(), (g.a0, g.b0, g.h, g.nx, g.ny), dict(B=p.B, k1=p.k1), precision=prec)
+    lin = plan.fc2d_inside_points()
+    assert np.array_equal(lin, np.flatnonzero(case.geo.inside.ravel()))
+    n_f = len(case.fs)
+    dt = torch.float64 if precision == "fp64" else torch.float32
+    full = torch.zeros((n_f, g.ny, g.nx // 2 + 1, 2), dtype=dt, device=case.dev)
+    comp = torch.full_like(full, float("nan"))
+    plan.fc2d_extend_coeffs(n_f, case.tg, case.tb, full)
+    fin = case.tg.reshape(n_f, -1)[:, torch.tensor(lin, device=case.dev)].contiguous()
+    plan.fc2d_extend_coeffs_compact(n_f, fin, case.tb, comp)
+    plan.fc2d_sync_status()
+    assert torch.equal(full, comp)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_dft_large_power_of_two(fc2d, torch_cuda, precision):
     """The power-of-two DFT kernels at 4096 x 2048 (ny x nx) on seeded random data:
     1e-12 (FP64) / 1e-6 (FP32) relative max-norm against numpy's FFT of the same data."""

@@ -88,3 +88,19 @@ def test_plans_of_the_eight_star_workload():
     r = host_plan.run(w)
     geo = OG.build_geometry(w)
     assert np.array_equal(np.sort(r["strip_lin"]), np.sort(geo.strip_lin))
+
+
+def test_compact_stencil_indices_address_the_same_points(both):
+    """The plan's compact tables (for f given at the inside points only, row by row):
+    each interval's compact offset is the number of inside points before it, and every
+    stencil tap's compact index addresses the same grid point as its linear index."""
+    w, r, geo = both
+    g = w.grid
+    iv = r["row_iv"].reshape(-1, 2)
+    lens = iv[:, 1] - iv[:, 0] + 1
+    assert np.array_equal(r["row_iv_coff"], np.concatenate([[0], np.cumsum(lens)[:-1]]))
+    inside_lin = np.flatnonzero(geo.inside.ravel())          # compact order = row major
+    gi, gc = r["gidx"], r["gidx_c"]
+    assert np.array_equal(gi < 0, gc < 0)
+    assert np.array_equal(gc[gi < 0], gi[gi < 0])
+    assert np.array_equal(inside_lin[gc[gi >= 0]], gi[gi >= 0])
