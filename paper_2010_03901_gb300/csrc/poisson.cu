@@ -281,6 +281,15 @@ __global__ void k_node_coef(int N, const double* x1, const double* y1, const dou
 }
 
 // v at listed grid points by the trapezoidal sum over N nodes; u = u_p + v there.
+// 1/r2 for the double-layer sums without an FP64 division (a long sequence on the narrow
+// FP64 pipe): the correctly rounded FP32 reciprocal as seed, then one Newton step for
+// 1/a, y1 = y0 + y0 (1 - a y0), whose relative error is the square of the seed's
+// (about 2^-46 here), far below the 1e-11 accuracy of the solver.  r2 > 0.
+__device__ __forceinline__ double rcp_newton(double r2) {
+  const double y0 = (double)__frcp_rn((float)r2);
+  return fma(y0, fma(-r2, y0, 1.0), y0);
+}
+
 __global__ void __launch_bounds__(256) k_dlp(int n_pts, const int32_t* lin, int nx, double a0,
                                              double b0, double h, int N, const double* x,
                                              const double* y, const double2* ab, double* u) {
@@ -304,7 +313,7 @@ __global__ void __launch_bounds__(256) k_dlp(int n_pts, const int32_t* lin, int 
       double dx = px - sx[k], dy = py - sy[k];
       double r2 = fma(dx, dx, dy * dy);
       double num = fma(sab[k].x, dx, -sab[k].y * dy);
-      acc += num / r2;
+      acc = fma(num, rcp_newton(r2), acc);
     }
   }
   if (act) u[l] += acc;
@@ -330,7 +339,7 @@ __global__ void __launch_bounds__(256) k_dlp_close(int n_close, const int32_t* l
     for (int k = threadIdx.x; k < NR; k += blockDim.x) {
       double dx = px - rx[k], dy = py - ry[k];
       double r2 = fma(dx, dx, dy * dy);
-      acc += fma(abR[k].x, dx, -abR[k].y * dy) / r2;
+      acc = fma(fma(abR[k].x, dx, -abR[k].y * dy), rcp_newton(r2), acc);
     }
     red[threadIdx.x] = acc;
     __syncthreads();
@@ -345,12 +354,18 @@ __global__ void __launch_bounds__(256) k_dlp_close(int n_close, const int32_t* l
   {
     double acc = 0.0;
     const int half = Nb / 2;
+    // e^{i k theta} for k = tid, tid + blockDim, ...: one sincos each for the first k and
+    // the stride, then complex products (at most a few steps: Nb/2 <= a few blockDim)
+    double s, c, ss, cs;
+    sincos(double(threadIdx.x) * th, &s, &c);
+    sincos(double(blockDim.x) * th, &ss, &cs);
     for (int k = threadIdx.x; k <= half; k += blockDim.x) {
-      double s, c;
-      sincos(double(k) * th, &s, &c);
       double re = ghat_g[k].x * c - ghat_g[k].y * s;
       double fac = (k == 0 || 2 * k == Nb) ? 1.0 : 2.0;
       acc = fma(fac, re, acc);
+      const double c2 = c * cs - s * ss, s2 = s * cs + c * ss;
+      c = c2;
+      s = s2;
     }
     red[threadIdx.x] = acc;
     __syncthreads();
