@@ -43,7 +43,13 @@ FP64_PEAK_TFLOPS = 1.25   # GB300 FP64 (nominal; 152 SMs x 2 DFMA/clk x 2 flop x
 # on this workload, from one ncu capture of the current kernels (cold cache, serialised
 # launches; a scope with two kernels sums both).  A kernel changed after its capture
 # has no entry, and the roofline then reports traffic null.
-MEASURED_TRAFFIC = {}
+MEASURED_TRAFFIC = {
+    ("mixed", "fft_cols"): 67670784 + 6779904 + 67738624 + 8792064,  # k_cols4k_a + k_cols4k_b
+    ("mixed", "fft_rows_fused"): 70924032 + 19624704,
+    ("mixed", "gather_blend_interp_tc"): 34107904 + 0,
+    ("fp64", "fft_rows_fused"): 72342784 + 74411264,
+    ("fp64", "fft_cols"): 141897984 + 92180992,
+}
 
 
 def peaks():
