@@ -78,7 +78,8 @@ typedef struct {
 } fc2d_grid;
 
 /* Section 3.6 parameter list.  A zero field takes the paper's default (Remark 3.3):
- * d=5, C=27, Z=12, n_os=20, n_r=6, M=d+3, B=round(2 pi/h), m_F=20, k1=h. */
+ * d=5, C=27, Z=12, n_os=20, n_r=6, M=d+3, B=round(2 pi/h), m_F=20, k1=h.
+ * Ranges: 2 <= d <= 12 (d <= 8 for FC2D_MIXED), 2 <= M <= 16, M <= C n_r + 1. */
 typedef struct {
   int d, C, Z, n_os, n_r, M, B, m_F;
   double k1;      /* normal step of V-/V+ (eqs. (3.5)-(3.6)) */

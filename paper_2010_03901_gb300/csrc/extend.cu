@@ -182,9 +182,9 @@ __global__ void __launch_bounds__(256) k_gather_blend(GatherArgs a) {
     if (s < d) cs = fma(__ldg(a.Q + i * d + s), v, cs);
   }
   if (kFp64Blend) {
-    double c[kMaxD];
+    double c[GS];  // d <= GS: every Gram coefficient of the group
 #pragma unroll
-    for (int j = 0; j < kMaxD; ++j) c[j] = __shfl_sync(0xffffffffu, cs, g0 + (j < d ? j : 0));
+    for (int j = 0; j < GS; ++j) c[j] = __shfl_sync(0xffffffffu, cs, g0 + (j < d ? j : 0));
     if (!live) return;
     double* F = reinterpret_cast<double*>(a.F) + ((size_t)f * a.B + p) * (a.Cr + 1);
     if (s == 0) F[0] = fbp;
@@ -192,7 +192,7 @@ __global__ void __launch_bounds__(256) k_gather_blend(GatherArgs a) {
       const double* ar = a.Ar + (size_t)q * d;
       double v = 0.0;
 #pragma unroll
-      for (int j = 0; j < kMaxD; ++j)
+      for (int j = 0; j < GS; ++j)
         if (j < d) v = fma(__ldg(ar + j), c[j], v);
       F[q + 1] = v;
     }
@@ -205,6 +205,7 @@ __global__ void __launch_bounds__(256) k_gather_blend(GatherArgs a) {
 
 void launch_gather_blend(const GatherArgs& a, int n_f, bool fp64, cudaStream_t s) {
   // group size: the larger of M-1 red stars and d coefficients, rounded up to 8 or 16
+  // (the plan keeps M <= 16 and d <= 12)
   const int GS = (a.M - 1 <= 8 && a.d <= 8) ? 8 : 16;
   const int per_warp = 32 / GS;
   const int warps = (a.B + per_warp - 1) / per_warp;

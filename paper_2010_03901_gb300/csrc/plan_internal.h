@@ -12,7 +12,7 @@
 namespace fc2d {
 
 constexpr int kMaxRadices = 24;
-constexpr int kMaxM = 12;
+constexpr int kMaxM = 16;
 // Mixed form, M = 8: a blend CTA computes kTcComputed consecutive normals (mod B) and
 // interpolates the strip points whose first normal lies in its first kTcOwned, whose
 // M-normal stencils then lie within the CTA's normals.

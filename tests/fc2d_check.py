@@ -29,12 +29,14 @@ def inside_fine(curve, xf, yf):
     return out
 
 
-def paper_setup(boundary, h, d=5, M=None, B=None):
-    """Grid and parameters of the paper's experiments: k1 = k2 = h (Remark 3.3)."""
+def paper_setup(boundary, h, d=5, M=None, B=None, smooth=False):
+    """Grid and parameters of the paper's experiments: k1 = k2 = h (Remark 3.3).
+    smooth: grid sizes raised to even 2^a 3^b 5^c (what the library's DFT takes)."""
     cv = G.make_curve(boundary)
     th = np.linspace(0, 2 * np.pi, 20001)
     xx, yy = cv.point(th)
-    grid = W.fit_grid(xx.min(), xx.max(), yy.min(), yy.max(), h)
+    fit = W.fit_grid_smooth if smooth else W.fit_grid
+    grid = fit(xx.min(), xx.max(), yy.min(), yy.max(), h)
     B = B or int(round(2 * math.pi / h))
     return W.Workload("paper", boundary, grid, W.Params(d=d, M=M or d + 3, B=B, k1=h))
 
@@ -54,3 +56,4 @@ def fine_error(w, mats, f, relative=True):
     if relative:
         err /= np.abs(f(X, Y)[ins]).max()
     return err
+

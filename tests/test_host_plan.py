@@ -10,12 +10,21 @@ from oracle import geometry as OG
 from oracle.fc_matrices import load_fc_matrices
 from tests import host_plan
 
-CASES = ["disk64", "disk128", "star200", "kite160x144", "star1024"]
+# name, or name:d for the paper's higher orders (M = d + 3, Section 3.6)
+CASES = ["disk64", "disk128", "star200", "kite160x144", "star1024", "disk128:10",
+         "star200:12"]
+
+
+def case_workload(name):
+    if ":" in name:
+        base, d = name.split(":")
+        return W.workload(base, d=int(d), M=int(d) + 3)
+    return W.workload(name)
 
 
 @pytest.fixture(scope="module", params=CASES)
 def both(request):
-    w = W.workload(request.param)
+    w = case_workload(request.param)
     r = host_plan.run(w)
     assert r["status"] == 0, r["error"]
     return w, r, OG.build_geometry(w)
@@ -23,7 +32,8 @@ def both(request):
 
 def test_fc_matrices_in_double_double_equal_the_oracle(both):
     w, r, geo = both
-    m = load_fc_matrices()
+    p = w.params
+    m = load_fc_matrices(p.d, p.C, p.Z, p.n_os, p.n_r, p.m_F)
     assert np.array_equal(r["Q"].reshape(m["Q"].shape), m["Q"]) or \
         np.abs(r["Q"].reshape(m["Q"].shape) - m["Q"]).max() <= 2e-16
     Ar = r["Ar"].reshape(m["Ar"].shape)

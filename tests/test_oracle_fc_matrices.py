@@ -72,6 +72,39 @@ def test_fc1d_converges_at_order_d(mats):
     assert errs[-1] < 1e-7
 
 
+@pytest.mark.parametrize("d,order", [(10, 8.0), (12, 9.5)])
+def test_fc1d_converges_at_high_order(d, order):
+    """Section 2.3 at the paper's higher orders (d = 10, 12; same C, Z, n_os, n_r and
+    m_F = 20): the 1D-FC of Figure 1's phi converges faster than O(k^order) from
+    N = 51 to 201 and reaches 1e-9.  The least-squares misfit of the highest Gram
+    columns is 5e-7 (d = 10) and 2e-5 (d = 12), but smooth data carry almost nothing
+    in those columns."""
+    m = load_fc_matrices(d)
+    phi = lambda x: np.exp(np.sin(5.4 * np.pi * x - 2.7 * np.pi) - np.cos(2 * np.pi * x)) \
+        - np.sin(2.5 * np.pi * x) + 1
+    errs = []
+    for N in (51, 101, 201):
+        x = np.linspace(0, 1, N)
+        xe = np.linspace(0, 1, 4 * N + 1)
+        errs.append(np.abs(fc1d_eval(m, phi(x), xe) - phi(xe)).max())
+    orders = np.log2(np.array(errs[:-1]) / np.array(errs[1:]))
+    assert np.all(orders > order), (errs, orders)
+    assert errs[-1] < 1e-9
+
+
+@pytest.mark.parametrize("d", [10, 12])
+def test_high_order_gram_qr(d):
+    """Eq. (2.2) at d = 10, 12: Q orthonormal, R upper triangular with a positive
+    diagonal, QR = P, and Q R^{-1} reproduces the oversampled Vandermonde rows."""
+    m = load_fc_matrices(d)
+    Q, R = m["Q"], m["R"]
+    x = np.arange(d, dtype=float)
+    P = x[:, None] ** np.arange(d)[None, :]
+    assert np.allclose(Q.T @ Q, np.eye(d), atol=1e-13)
+    assert np.allclose(np.tril(R, -1), 0) and np.all(np.diag(R) > 0)
+    assert np.abs(Q @ R - P).max() <= 1e-12 * np.abs(P).max()
+
+
 @pytest.mark.slow
 def test_golden_matrices_regenerate_bit_for_bit():
     """The cached matrices are what the 50-digit computation gives."""
@@ -81,12 +114,14 @@ def test_golden_matrices_regenerate_bit_for_bit():
         assert np.array_equal(fresh[k], cached[k]), k
 
 
-def test_matrices_agree_with_an_independent_multiprecision_qr(mats):
+@pytest.mark.parametrize("d", [5, 10])
+def test_matrices_agree_with_an_independent_multiprecision_qr(d):
     """Re-derive A_r by mpmath's QR least squares at 40 digits (a different
     algorithm and library): every entry agrees after rounding to double."""
     mp = pytest.importorskip("mpmath")
     mp.mp.dps = 40
-    d, C, Z, n_os, n_r, m_F = 5, 27, 12, 20, 6, 20
+    mats = load_fc_matrices(d)
+    C, Z, n_os, n_r, m_F = 27, 12, 20, 6, 20
     Per = d + 2 * C + Z - 1
     x = [mp.mpf(i) for i in range(d)]
     P = mp.matrix([[x[i] ** j if j else mp.mpf(1) for j in range(d)] for i in range(d)])

@@ -186,6 +186,50 @@ def fit_grid(xmin, xmax, ymin, ymax, h, C=27, k1=None, margin=4) -> Grid:
                 h=h, nx=nx, ny=ny)
 
 
+def next_smooth_even(n: int) -> int:
+    """Smallest even m >= n of the form 2^a 3^b 5^c (a DFT-friendly length)."""
+    m = n + (n & 1)
+    while True:
+        r = m
+        for q in (2, 3, 5):
+            while r % q == 0:
+                r //= q
+        if r == 1:
+            return m
+        m += 2
+
+
+def fit_grid_smooth(xmin, xmax, ymin, ymax, h, C=27, margin=4) -> Grid:
+    """fit_grid with both sizes raised to the next even 2^a 3^b 5^c, same centre."""
+    g = fit_grid(xmin, xmax, ymin, ymax, h, C=C, margin=margin)
+    nx, ny = next_smooth_even(g.nx), next_smooth_even(g.ny)
+    return Grid(a0=0.5 * (xmin + xmax) - 0.5 * nx * h, b0=0.5 * (ymin + ymax) - 0.5 * ny * h,
+                h=h, nx=nx, ny=ny)
+
+
+def far_inside(boundary: Boundary, xs, ys, dmin: float, n: int = 20000) -> np.ndarray:
+    """Mask [len(ys)][len(xs)] of the grid points inside the curve at a distance
+    greater than dmin from it (where errors are measured away from the boundary).  The
+    curve is sampled at n points (spacing ~2.5e-4 on the test domains, so distances are
+    overestimated by at most about half of that): the distance test is a
+    nearest-neighbour search among the samples, the inside test an even-odd count of
+    polygon crossings along each row."""
+    from scipy.spatial import cKDTree
+    cx, cy = boundary.polygon(n)
+    X, Y = np.meshgrid(xs, ys)
+    d, _ = cKDTree(np.column_stack([cx, cy])).query(
+        np.column_stack([X.ravel(), Y.ravel()]), distance_upper_bound=dmin, workers=-1)
+    far = np.isinf(d).reshape(X.shape)
+    x2, y2 = np.roll(cx, -1), np.roll(cy, -1)
+    inside = np.zeros(X.shape, bool)
+    for r, y in enumerate(ys):
+        e = (cy > y) != (y2 > y)
+        xc = np.sort(cx[e] + (y - cy[e]) * (x2[e] - cx[e]) / (y2[e] - cy[e]))
+        for a, b in zip(xc[0::2], xc[1::2]):
+            inside[r] |= (xs > a) & (xs < b)
+    return far & inside
+
+
 def star_min_radius(a: float, k: int, n: int = 8192) -> float:
     """Smallest radius of curvature of r = 1 + a cos(k theta) (sampled): 1/max kappa with
     kappa = |r^2 + 2 r'^2 - r r''| / (r^2 + r'^2)^(3/2)."""
