@@ -271,7 +271,8 @@ def test_compact_input_equals_full_grid(case, fc2d, precision):
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_dft_large_power_of_two(fc2d, torch_cuda, precision):
-    """The power-of-two DFT kernels at 4096 x 2048 (ny x nx) on seeded random data:
+    """The power-of-two DFT kernels at 4096 x 2048 (ny x nx) on seeded random data, two
+    functions batched (1025 columns: a ragged last column group):
     1e-12 (FP64) / 1e-6 (FP32) relative max-norm against numpy's FFT of the same data."""
     torch = torch_cuda
     w = W.workload("kite2048")
@@ -280,17 +281,18 @@ def test_dft_large_power_of_two(fc2d, torch_cuda, precision):
     prec = fc2d.FC2D_FP64 if precision == "fp64" else fc2d.FC2D_MIXED
     plan = fc2d.fc2d_plan(w.boundary.arrays(), (g.a0, g.b0 - 0.5 * ny * g.h + 0.5 * g.ny * g.h,
                                                 g.h, nx, ny), dict(B=p.B, k1=p.k1), precision=prec)
-    x = W.normal(77, ny * nx).reshape(ny, nx)
+    x = W.normal(77, 2 * ny * nx).reshape(2, ny, nx)
     dt = torch.float64 if precision == "fp64" else torch.float32
-    t = torch.tensor(x[None], dtype=dt, device="cuda:0")
-    fhat = torch.zeros((1, ny, nx // 2 + 1, 2), dtype=dt, device="cuda:0")
-    plan.fc2d_coeffs(1, t, fhat)
+    t = torch.tensor(x, dtype=dt, device="cuda:0")
+    fhat = torch.zeros((2, ny, nx // 2 + 1, 2), dtype=dt, device="cuda:0")
+    plan.fc2d_coeffs(2, t, fhat)
     plan.fc2d_sync_status()
-    got = fhat.cpu().numpy().astype(np.float64)[0]
-    got = got[..., 0] + 1j * got[..., 1]
-    ref = np.fft.rfft2(t.cpu().numpy().astype(np.float64)[0]) / (nx * ny)
     tol = TOL if precision == "fp64" else TOL_MIXED
-    assert rel(got, ref) < tol, rel(got, ref)
+    for k in range(2):
+        got = fhat.cpu().numpy().astype(np.float64)[k]
+        got = got[..., 0] + 1j * got[..., 1]
+        ref = np.fft.rfft2(t.cpu().numpy().astype(np.float64)[k]) / (nx * ny)
+        assert rel(got, ref) < tol, (k, rel(got, ref))
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
