@@ -478,12 +478,13 @@ constexpr int kGiBarOff = kGiStageOff + kTcComputed * kTcMaxLd * 4;
 constexpr int kGiSmem = kGiBarOff + 16;
 
 struct OwnArgs {
-  const int32_t* off;   // [n_own + 1]
-  const int32_t* k;     // [n_strip] strip index
-  const int32_t* pack;  // [n_strip] local first normal | first fine node << 8
-  const float* w;       // [16][n_strip] theta weights then eta weights
+  const int32_t* off;    // [n_own + 1]
+  const int32_t* k;      // [n_strip] strip index
+  const int32_t* pack;   // [n_strip] local first normal | first fine node << 8
+  const float* w;        // [16][n_strip] theta weights then eta weights
+  const int32_t* start;  // [n_own + 1] first normal of each CTA's range
   int n_own, n_strip;
-  float* vals;          // [n_f][n_strip]
+  float* vals;           // [n_f][n_strip]
 };
 
 __global__ void __launch_bounds__(kGiThreads, 1) k_gather_interp_tc(GatherArgs g, TcArgs a,
@@ -501,6 +502,19 @@ __global__ void __launch_bounds__(kGiThreads, 1) k_gather_interp_tc(GatherArgs g
   const int c = blockIdx.x, f = blockIdx.y;
   const int ldS = a.ldF;  // staging row length (see the launcher)
   const int nqt = (a.Cr + kTcQTile - 1) / kTcQTile;
+  const int o0 = __ldg(o.off + c), o1 = __ldg(o.off + c + 1);
+  {
+    // the owned points' weights, indices and packed nodes are plan constants: pull
+    // their 18 contiguous ranges into L2 now, to be read after the gather and the MMAs
+    const int bytes = (o1 - o0) * 4, lines = (bytes + 127) / 128;
+    for (int t = tid; t < 18 * lines; t += blockDim.x) {
+      const int seg = t / lines, li = t - seg * lines;
+      const char* b = seg < 16 ? reinterpret_cast<const char*>(o.w + (size_t)seg * o.n_strip + o0)
+                      : seg == 16 ? reinterpret_cast<const char*>(o.pack + o0)
+                                  : reinterpret_cast<const char*>(o.k + o0);
+      asm volatile("prefetch.global.L2 [%0];" ::"l"(b + (size_t)li * 128));
+    }
+  }
 
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
@@ -540,7 +554,7 @@ __global__ void __launch_bounds__(kGiThreads, 1) k_gather_interp_tc(GatherArgs g
   {
     const int M = MM, d = g.d, NS = M - 1;
     const bool star_lane = s < NS;
-    const int pp = (c * kTcOwned + ln) % g.B;
+    const int pp = (__ldg(o.start + c) + ln) % g.B;
     const size_t base = ((size_t)pp * NS + (star_lane ? s : 0)) * M;
     int32_t id[MM];
     double wv[MM], wnv[MM], qv[kMaxD];
@@ -666,7 +680,6 @@ __global__ void __launch_bounds__(kGiThreads, 1) k_gather_interp_tc(GatherArgs g
     ia.M = MM;
     ia.B = kTcComputed;  // local rows: no wrap inside the tile
     ia.ldF = ldS;
-    const int o0 = __ldg(o.off + c), o1 = __ldg(o.off + c + 1);
     auto load = [&](int idx, InterpPoint<MM, float>& q) {
       const int pk = __ldg(o.pack + idx);
       q.pb = pk & 0xFF;
@@ -704,8 +717,8 @@ __global__ void __launch_bounds__(kGiThreads, 1) k_gather_interp_tc(GatherArgs g
 fc2d_status launch_gather_interp_tc(const GatherArgs& g, int n_f, int ldS, const float* Ar_hi,
                                     const float* Ar_lo, const int32_t* own_off,
                                     const int32_t* own_k, const int32_t* own_pack,
-                                    const float* own_w, int n_own, int n_strip, float* vals,
-                                    int* status, cudaStream_t s) {
+                                    const float* own_w, const int32_t* own_start, int n_own,
+                                    int n_strip, float* vals, int* status, cudaStream_t s) {
   if (g.Cr > kMaxCrPad || g.d > 8 || g.M != 8 || ldS % 4 || ldS < g.Cr + 12 ||
       ldS + 4 > kTcMaxLd || !own_off)
     return set_error(FC2D_ERR_UNSUPPORTED, "blend + interpolation kernel: M = 8, d <= 8");
@@ -718,7 +731,7 @@ fc2d_status launch_gather_interp_tc(const GatherArgs& g, int n_f, int ldS, const
   a.Ar_hi = Ar_hi;
   a.Ar_lo = Ar_lo;
   a.status = status;
-  OwnArgs o{own_off, own_k, own_pack, own_w, n_own, n_strip, vals};
+  OwnArgs o{own_off, own_k, own_pack, own_w, own_start, n_own, n_strip, vals};
   cudaFuncSetAttribute(k_gather_interp_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kGiSmem);
   return cuda_check(launch_pdl(k_gather_interp_tc, dim3(n_own, n_f), dim3(kGiThreads),
                                (size_t)kGiSmem, s, g, a, o),

@@ -176,7 +176,8 @@ fc2d_status strip_values(fc2d_plan_s* p, int n_f, const double* fg, const double
     ProfScope ps(p, "gather_blend_interp_tc", s);
     return launch_gather_interp_tc(gather_args(p, fg, fb, nullptr, nullptr, nullptr, compact), n_f,
                                    ws_ldF(p), p->dev.Ar_hi, p->dev.Ar_lo, p->dev.own_off,
-                                   p->dev.own_k, p->dev.own_pack, p->dev.own_w, p->dev.n_own,
+                                   p->dev.own_k, p->dev.own_pack, p->dev.own_w,
+                                   p->dev.own_start, p->dev.n_own,
                                    (int)p->strip_lin.size(),
                                    reinterpret_cast<float*>(ws(p, L.ovals)), p->dev.status, s);
   }

@@ -114,12 +114,13 @@ fc2d_status launch_blend_tc(int n_cols, int Cr, int d, int ldF, const double* co
 fc2d_status launch_gather_blend_tc(const GatherArgs& g, int n_f, int ldF, const float* Ar_hi,
                                    const float* Ar_lo, float* F, int* status, cudaStream_t s);
 // Mixed form, M = 8: matching values, blend and interpolation in one kernel; writes the
-// strip-point values (the plan's owner tables group the strip points by CTA).
+// strip-point values (the plan's owner tables group the strip points by CTA, each CTA
+// owning the points of a balanced range of at most kTcOwned normals).
 fc2d_status launch_gather_interp_tc(const GatherArgs& g, int n_f, int ldS, const float* Ar_hi,
                                     const float* Ar_lo, const int32_t* own_off,
                                     const int32_t* own_k, const int32_t* own_pack,
-                                    const float* own_w, int n_own, int n_strip, float* vals,
-                                    int* status, cudaStream_t s);
+                                    const float* own_w, const int32_t* own_start, int n_own,
+                                    int n_strip, float* vals, int* status, cudaStream_t s);
 void launch_interp(const InterpArgs& a, int n_f, bool fp64, const void* F, void* vals,
                    cudaStream_t s);
 void launch_assemble(const RowArgs& a, int n_f, bool fp64, const double* f_grid,

@@ -385,39 +385,110 @@ struct Cand {
 
 }  // namespace
 
+// Ownership ranges of the blend + interpolation CTAs: consecutive normal ranges
+// [start_c, start_{c+1}) of at most `cap` normals covering 0..B-1, with at most n_cta
+// ranges, such that the largest number of strip points owned by one range is as small
+// as possible (binary search on that number; for a given bound, taking as many normals
+// as fit into each range in turn uses the fewest ranges).  cnt[p]: points per normal.
+static std::vector<int32_t> partition_owners(const std::vector<int64_t>& cnt, int cap, int n_cta) {
+  const int B = (int)cnt.size();
+  auto greedy = [&](int64_t T, std::vector<int32_t>* start) {
+    int parts = 0, owned = 0;
+    int64_t run = 0;
+    if (start) start->assign(1, 0);
+    for (int p = 0; p < B; ++p) {
+      if (owned == cap || (owned > 0 && run + cnt[p] > T)) {
+        ++parts;
+        if (start) start->push_back(p);
+        run = 0;
+        owned = 0;
+      }
+      run += cnt[p];
+      ++owned;
+    }
+    ++parts;
+    if (start) start->push_back(B);
+    return parts;
+  };
+  int64_t lo = 0, hi = 0;
+  for (int64_t v : cnt) {
+    lo = std::max(lo, v);
+    hi += v;
+  }
+  lo = std::max(lo, (hi + n_cta - 1) / n_cta);
+  hi = std::max(hi, lo);
+  while (lo < hi) {  // smallest bound whose greedy partition uses <= n_cta ranges
+    const int64_t mid = lo + (hi - lo) / 2;
+    if (greedy(mid, nullptr) <= n_cta) hi = mid;
+    else lo = mid + 1;
+  }
+  std::vector<int32_t> start;
+  greedy(lo, &start);
+  return start;
+}
+
 // Strip points grouped by the blend CTA that interpolates them (mixed form, M = 8):
-// CTA c of a function computes normals c*kTcOwned .. c*kTcOwned + kTcComputed - 1 (mod B)
-// and owns the strip points whose first normal pb lies in [c*kTcOwned, (c+1)*kTcOwned),
-// so that pb .. pb + M - 1 are among its normals.  The weights are reordered to match.
+// CTA c of a function computes the kTcComputed normals from start_c on (mod B) and owns
+// the strip points whose first normal pb lies in [start_c, start_{c+1}), at most
+// kTcOwned normals, so that pb .. pb + M - 1 are among its normals.  One CTA per SM
+// (at least ceil(B / kTcOwned)), the ranges balanced by their numbers of points.  The
+// weights are reordered to match.
 static fc2d_status owner_tables(fc2d_plan_s* p, int ns, int M) {
   const int B = p->prm.B;
-  const int n_own = (B + kTcOwned - 1) / kTcOwned;
+  int n_sm = 0;
+  if (cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, p->device) != cudaSuccess)
+    n_sm = 0;
+  const int n_cta = std::max((B + kTcOwned - 1) / kTcOwned, n_sm);
   std::vector<int32_t> pb(ns), sb(ns);
   std::vector<float> w((size_t)2 * M * ns);
   if (cudaMemcpy(pb.data(), p->dev.s_pb, (size_t)ns * 4, cudaMemcpyDeviceToHost) != cudaSuccess ||
       cudaMemcpy(sb.data(), p->dev.s_sb, (size_t)ns * 4, cudaMemcpyDeviceToHost) != cudaSuccess ||
       cudaMemcpy(w.data(), p->dev.s_w, w.size() * 4, cudaMemcpyDeviceToHost) != cudaSuccess)
     return set_error(FC2D_ERR_CUDA, "reading the interpolation tables back failed");
-  std::vector<int32_t> off(n_own + 1, 0);
+  std::vector<int64_t> cnt(B, 0);
   for (int k = 0; k < ns; ++k) {
     pb[k] = ((pb[k] % B) + B) % B;  // the first normal is stored unreduced near theta = 0
     if (sb[k] < 0 || sb[k] > 255)
       return set_error(FC2D_ERR_GEOMETRY, "interpolation node index out of range");
-    ++off[pb[k] / kTcOwned + 1];
+    ++cnt[pb[k]];
   }
+  const std::vector<int32_t> start = partition_owners(cnt, kTcOwned, n_cta);
+  const int n_own = (int)start.size() - 1;
+  std::vector<int32_t> cta_of(B);
+  for (int c = 0; c < n_own; ++c)
+    for (int q = start[c]; q < start[c + 1]; ++q) cta_of[q] = c;
+  std::vector<int32_t> off(n_own + 1, 0);
+  for (int k = 0; k < ns; ++k) ++off[cta_of[pb[k]] + 1];
   for (int c = 0; c < n_own; ++c) off[c + 1] += off[c];
   std::vector<int32_t> fill(off.begin(), off.end() - 1), perm(ns), pack(ns);
-  std::vector<float> wp(w.size());
   for (int k = 0; k < ns; ++k) {
-    const int c = pb[k] / kTcOwned, idx = fill[c]++;
+    const int c = cta_of[pb[k]], idx = fill[c]++;
     perm[idx] = k;
-    pack[idx] = (pb[k] - c * kTcOwned) | (sb[k] << 8);
-    for (int b = 0; b < 2 * M; ++b) wp[(size_t)b * ns + idx] = w[(size_t)b * ns + k];
+    pack[idx] = (pb[k] - start[c]) | (sb[k] << 8);
   }
+  // within a CTA, order the points by first normal, then first fine node: neighbouring
+  // lanes then read the same or adjacent rows of the shared-memory tile
+  for (int c = 0; c < n_own; ++c) {
+    std::vector<int32_t> ord(off[c + 1] - off[c]);
+    for (size_t i = 0; i < ord.size(); ++i) ord[i] = off[c] + (int32_t)i;
+    auto key = [&](int32_t i) { return (pack[i] & 0xFF) * 256 + (pack[i] >> 8); };
+    std::stable_sort(ord.begin(), ord.end(), [&](int32_t x, int32_t y) { return key(x) < key(y); });
+    std::vector<int32_t> pk(ord.size()), pm(ord.size());
+    for (size_t i = 0; i < ord.size(); ++i) {
+      pk[i] = pack[ord[i]];
+      pm[i] = perm[ord[i]];
+    }
+    std::copy(pk.begin(), pk.end(), pack.begin() + off[c]);
+    std::copy(pm.begin(), pm.end(), perm.begin() + off[c]);
+  }
+  std::vector<float> wp(w.size());
+  for (int idx = 0; idx < ns; ++idx)
+    for (int b = 0; b < 2 * M; ++b) wp[(size_t)b * ns + idx] = w[(size_t)b * ns + perm[idx]];
   p->dev.n_own = n_own;
   fc2d_status st;
   if ((st = upload(&p->dev.own_off, off)) || (st = upload(&p->dev.own_k, perm)) ||
-      (st = upload(&p->dev.own_pack, pack)) || (st = upload(&p->dev.own_w, wp)))
+      (st = upload(&p->dev.own_pack, pack)) || (st = upload(&p->dev.own_w, wp)) ||
+      (st = upload(&p->dev.own_start, start)))
     return st;
   return FC2D_OK;
 }
@@ -864,7 +935,7 @@ extern "C" void fc2d_destroy(fc2d_plan_t p) {
   void* ptrs[] = {p->dev.Q, p->dev.Ar, p->dev.Ar_hi, p->dev.Ar_lo, p->dev.gidx, p->dev.gw,
                   p->dev.wn, p->dev.s_lin, p->dev.s_theta, p->dev.s_eta, p->dev.s_w,
                   p->dev.s_pb, p->dev.s_sb, p->dev.own_off, p->dev.own_k,
-                  p->dev.own_pack, p->dev.own_w, p->dev.row_iv_off,
+                  p->dev.own_pack, p->dev.own_w, p->dev.own_start, p->dev.row_iv_off,
                   p->dev.row_iv, p->dev.row_strip_off, p->dev.row_iv_coff, p->dev.gidx_c,
                   p->dev.status, p->fx.tw64, p->fx.tw32,
                   p->fy.tw64, p->fy.tw32, p->rtw64, p->rtw32, p->ws.base,

@@ -61,7 +61,8 @@ struct DeviceTables {
   int32_t* own_k = nullptr;     // [n_strip] strip index of each grouped point
   int32_t* own_pack = nullptr;  // [n_strip] (first normal - CTA's first normal) | s << 8
   float* own_w = nullptr;       // [2M][n_strip] interpolation weights, grouped order
-  int n_own = 0;                // CTAs per function: ceil(B / kTcOwned)
+  int32_t* own_start = nullptr; // [n_own + 1] first normal owned by each CTA, then B
+  int n_own = 0;                // CTAs per function (ownership ranges)
   // per-row tables
   int32_t* row_iv_off = nullptr;    // [ny+1] offsets into row_iv
   int32_t* row_iv = nullptr;        // pairs (i_lo, i_hi), inclusive

@@ -49,3 +49,12 @@ def run(w):
         res[name] = arr
         pos = end + 1 + n * sz + 1
     return res
+
+
+def partition(cnt, cap, n_cta):
+    """The plan's ownership ranges (partition_owners) for points-per-normal counts."""
+    exe = build()
+    inp = f"{cap} {n_cta} {len(cnt)} " + " ".join(str(int(v)) for v in cnt)
+    out = subprocess.run([exe, "partition"], input=inp.encode(), check=True,
+                         capture_output=True).stdout
+    return np.array([int(t) for t in out.split()], dtype=np.int64)

@@ -31,6 +31,11 @@ static cudaError_t h_getdev(int* d) {
 #define cudaFree(p) h_free(p)
 #define cudaMemcpy(d, s, n, k) h_memcpy((d), (s), (n), (k))
 #define cudaGetDevice(d) h_getdev(d)
+static cudaError_t h_attr(int* v, int, int) {
+  *v = 152;
+  return cudaSuccess;
+}
+#define cudaDeviceGetAttribute(v, a, d) h_attr((v), (int)(a), (d))
 
 #include "../paper_2010_03901_gb300/csrc/plan.cpp"
 
@@ -95,6 +100,17 @@ static void dump(const char* name, const T* p, size_t n) {
 }
 
 int main(int argc, char** argv) {
+  if (argc > 1 && !std::strcmp(argv[1], "partition")) {
+    // stdin: cap n_cta B cnt_0 .. cnt_{B-1}; stdout: the range starts
+    int cap, n_cta, B;
+    if (std::scanf("%d %d %d", &cap, &n_cta, &B) != 3) return 1;
+    std::vector<int64_t> cnt(B);
+    for (auto& v : cnt)
+      if (std::scanf("%lld", reinterpret_cast<long long*>(&v)) != 1) return 1;
+    for (int32_t v : partition_owners(cnt, cap, n_cta)) std::printf("%d ", v);
+    std::printf("\n");
+    return 0;
+  }
   // argv: n_modes cx.. sx.. cy.. sy.. a0 b0 h nx ny d C Z n_os n_r M B m_F k1
   int a = 1;
   int nm = std::atoi(argv[a++]);

@@ -114,3 +114,36 @@ def test_compact_stencil_indices_address_the_same_points(both):
     assert np.array_equal(gi < 0, gc < 0)
     assert np.array_equal(gc[gi < 0], gi[gi < 0])
     assert np.array_equal(inside_lin[gc[gi >= 0]], gi[gi >= 0])
+
+
+def _min_max_partition(cnt, cap, n_cta):
+    """Brute force: the smallest possible largest range sum over partitions of cnt into
+    at most n_cta consecutive ranges of at most cap entries (dynamic programming)."""
+    B = len(cnt)
+    pre = np.concatenate([[0], np.cumsum(cnt)])
+    INF = float("inf")
+    best = np.full((n_cta + 1, B + 1), INF)
+    best[0, 0] = 0
+    for k in range(1, n_cta + 1):
+        for e in range(1, B + 1):
+            for s in range(max(0, e - cap), e):
+                v = max(best[k - 1, s], pre[e] - pre[s])
+                if v < best[k, e]:
+                    best[k, e] = v
+    return best[:, B].min()
+
+
+@pytest.mark.parametrize("seed,B,cap,n_cta", [(1, 240, 57, 8), (2, 300, 57, 6), (3, 128, 20, 9)])
+def test_owner_partition_is_balanced(seed, B, cap, n_cta):
+    """The ranges of strip points given to the blend + interpolation CTAs cover the
+    normals in order, hold at most cap normals each, number at most n_cta, and the
+    largest point count equals the brute-force optimum (skewed counts, as the strip
+    points per normal vary with the curvature)."""
+    u = W.uniform(seed, B)
+    cnt = np.floor(60 * u ** 3).astype(np.int64)
+    st = host_plan.partition(cnt, cap, n_cta)
+    assert st[0] == 0 and st[-1] == B
+    d = np.diff(st)
+    assert np.all(d >= 1) and np.all(d <= cap) and len(d) <= n_cta
+    pre = np.concatenate([[0], np.cumsum(cnt)])
+    assert (pre[st[1:]] - pre[st[:-1]]).max() == _min_max_partition(cnt, cap, n_cta)
