@@ -43,6 +43,8 @@ FP64_PEAK_TFLOPS = 1.25   # GB300 FP64 (nominal; 152 SMs x 2 DFMA/clk x 2 flop x
 # on this workload, from one ncu capture of the current kernels (cold cache, serialised
 # launches; a scope with two kernels sums both).  A kernel changed after its capture
 # has no entry, and the roofline then reports traffic null.
+ROT = 3   # rotating input/output buffers of the timed steps
+
 MEASURED_TRAFFIC = {
     ("mixed", "fft_cols"): 67670784 + 6779904 + 67738624 + 8792064,  # k_cols4k_a + k_cols4k_b
     ("mixed", "fft_rows_fused"): 70924032 + 19624704,
@@ -260,23 +262,30 @@ def measure(fc2d, torch, w, precision, K, warmup, world, dev, fg_h, fb_h, sample
                           dict(B=p.B, k1=p.k1),
                           precision=fc2d.FC2D_FP64 if fp64 else fc2d.FC2D_MIXED)
     plan_s = time.perf_counter() - t0
-    fg = fg_h.to(dev)
+    # inputs larger than L2: ROT copies of f on the whole grid (FP64, 134 MB each at
+    # 4096^2, above the 129 MB of L2) and ROT spectra, used in turn, so that no step finds
+    # another step's input or output in L2
+    fgs = [fg_h.to(dev) for _ in range(ROT)]
     fb = fb_h.to(dev)
+    fg = fgs[0]
     cdt = torch.float64 if fp64 else torch.float32
-    fhat = torch.zeros((g.ny, g.nx // 2 + 1, 2), dtype=cdt, device=dev)
-    # L2 flush between timed steps: a read-only pass over 256 MB (> 129 MB of L2), which
-    # evicts the step's data without leaving dirty lines for the next step to write back
+    fhats = [torch.zeros((g.ny, g.nx // 2 + 1, 2), dtype=cdt, device=dev) for _ in range(ROT)]
+    fhat = fhats[0]
+    # for the flushed variant: a read-only pass over 256 MB (> 129 MB of L2) before each
+    # step, which evicts the previous step's data without leaving dirty lines behind
     flush = torch.ones(64 * 1024 * 1024, dtype=torch.float32, device=dev)
     flush_out = torch.empty(1, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
-    for _ in range(warmup):
-        plan.fc2d_extend_coeffs(1, fg, fb, fhat, stream)
+    for k in range(warmup):
+        plan.fc2d_extend_coeffs(1, fgs[k % ROT], fb, fhats[k % ROT], stream)
     plan.fc2d_sync_status(stream)
     sampler = ClockSampler(dev.index) if sample_clocks else None
 
-    def timed_region(profile):
-        """K steps, the L2 flushed before each (outside the events); with `profile`
-        the library also records CUDA events around each of its kernels."""
+    def timed_region(profile=False, flushed=False):
+        """K steps of fc2d_extend_coeffs.  Default: back to back between two events,
+        each step on the next of the ROT input/output buffers.  flushed: the L2 flushed
+        before each step, outside per-step events.  profile: the library also records
+        CUDA events around each of its kernels."""
         starts = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
         ends = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
         if profile:
@@ -286,10 +295,13 @@ def measure(fc2d, torch, w, precision, K, warmup, world, dev, fg_h, fb_h, sample
             torch.distributed.barrier()
         torch.cuda.synchronize()
         for k in range(K):
-            torch.sum(flush, dim=0, out=flush_out[0])
-            starts[k].record(stream)
-            plan.fc2d_extend_coeffs(1, fg, fb, fhat, stream)
-            ends[k].record(stream)
+            if flushed:
+                torch.sum(flush, dim=0, out=flush_out[0])
+            if flushed or k == 0:
+                starts[k].record(stream)
+            plan.fc2d_extend_coeffs(1, fgs[k % ROT], fb, fhats[k % ROT], stream)
+            if flushed or k == K - 1:
+                ends[k].record(stream)
         torch.cuda.synchronize()
         if world > 1:
             torch.distributed.barrier()
@@ -298,21 +310,26 @@ def measure(fc2d, torch, w, precision, K, warmup, world, dev, fg_h, fb_h, sample
             plan.fc2d_profile(False)
             prof = plan.fc2d_profile_read()
         plan.fc2d_sync_status(stream)
-        return sum(s.elapsed_time(e) for s, e in zip(starts, ends)), prof
+        if flushed:
+            return sum(s.elapsed_time(e) for s, e in zip(starts, ends)), prof
+        return starts[0].elapsed_time(ends[K - 1]), prof
 
-    # the headline: K steps with nothing between the library's kernels (per-kernel
-    # events would stop each kernel's launch from overlapping the previous one's tail)
+    # the headline: K steps back to back, nothing between the library's kernels
+    # (per-kernel events would stop each kernel's launch from overlapping the previous
+    # one's tail)
     if sampler:
         sampler.start()
         time.sleep(0.3)
     wall0 = time.perf_counter()
-    ms_raw, _ = timed_region(False)
+    ms_raw, _ = timed_region()
     wall = time.perf_counter() - wall0
     clocks = sampler.stop() if sampler else None
     ms = max_over_ranks(ms_raw, world, dev)
+    # the same K steps with the L2 flushed before each step (outside the events)
+    ms_fl = max_over_ranks(timed_region(flushed=True)[0], world, dev)
     # the per-kernel profile (roofline, launch count): the same K steps again with the
     # library's CUDA events around each kernel
-    ms_prof_raw, prof = timed_region(True)
+    ms_prof_raw, prof = timed_region(profile=True)
     ms_prof = max_over_ranks(ms_prof_raw, world, dev)
     npts = g.nx * g.ny
     value = replica_throughput(world, K, npts, ms)
@@ -398,6 +415,10 @@ def measure(fc2d, torch, w, precision, K, warmup, world, dev, fg_h, fb_h, sample
     kernels = {k: {"launches": v[0], "avg_us": 1e3 * v[1] / v[0],
                    "share": v[1] / sum(x[1] for x in prof.values())} for k, v in prof.items()}
     return {"value": value, "ms_per_step": ms / K, "steps": K, "plan_s": plan_s,
+            "l2_flushed": {"value": replica_throughput(world, K, npts, ms_fl),
+                           "ms_per_step": ms_fl / K,
+                           "note": "L2 flushed before each step (256 MB read, outside "
+                                   "per-step events)"},
             "profiled_ms_per_step": ms_prof / K,
             "wall_s_timed": wall, "clocks": clocks, "roofline": roof, "kernels": kernels,
             "gpu_launches": sum(v[0] for v in prof.values()),
@@ -615,10 +636,13 @@ def run_gpu(args):
                        "domain": "kite a=0.65 b=1.5", "functions_per_step": 1,
                        "function": "sum of 16 Gaussians (seed 3)", "precision": head,
                        "d": p.d, "C": p.C, "M": p.M, "n_r": p.n_r,
-                       "l2": "flushed between steps (256 MB read, outside the events)",
+                       "l2": f"inputs larger than L2: {ROT} rotating copies of f on the "
+                             "whole grid (FP64, 134 MB each) and of the spectrum; steps back "
+                             "to back (the flushed variant is l2_flushed)",
                        "parallelism": f"replicas x{world}"},
             "clocks": r["clocks"], "roofline": r["roofline"], "kernels": r["kernels"],
-            "gpu_launches": r["gpu_launches"], "e2e": r["e2e"], "plan_s": r["plan_s"],
+            "gpu_launches": r["gpu_launches"], "e2e": r["e2e"], "l2_flushed": r["l2_flushed"],
+            "plan_s": r["plan_s"],
             "profiled_ms_per_step": r["profiled_ms_per_step"],
             "kernels_note": "per-kernel times and roofline from a second region of the same "
                             "K steps with CUDA events around each kernel",
@@ -626,7 +650,7 @@ def run_gpu(args):
     if "fp64" in res and head != "fp64":
         q = res["fp64"]
         line["fp64"] = {k: q[k] for k in ("value", "ms_per_step", "profiled_ms_per_step",
-                                          "steps", "roofline", "kernels", "e2e")}
+                                          "steps", "roofline", "kernels", "e2e", "l2_flushed")}
     if rank == 0 and world == 1 and not args.no_cpu:
         base, spec_ref = cpu_baseline(w)
         line["cpu_baseline"] = base

@@ -503,18 +503,6 @@ __global__ void __launch_bounds__(kGiThreads, 1) k_gather_interp_tc(GatherArgs g
   const int ldS = a.ldF;  // staging row length (see the launcher)
   const int nqt = (a.Cr + kTcQTile - 1) / kTcQTile;
   const int o0 = __ldg(o.off + c), o1 = __ldg(o.off + c + 1);
-  {
-    // the owned points' weights, indices and packed nodes are plan constants: pull
-    // their 18 contiguous ranges into L2 now, to be read after the gather and the MMAs
-    const int bytes = (o1 - o0) * 4, lines = (bytes + 127) / 128;
-    for (int t = tid; t < 18 * lines; t += blockDim.x) {
-      const int seg = t / lines, li = t - seg * lines;
-      const char* b = seg < 16 ? reinterpret_cast<const char*>(o.w + (size_t)seg * o.n_strip + o0)
-                      : seg == 16 ? reinterpret_cast<const char*>(o.pack + o0)
-                                  : reinterpret_cast<const char*>(o.k + o0);
-      asm volatile("prefetch.global.L2 [%0];" ::"l"(b + (size_t)li * 128));
-    }
-  }
 
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
