@@ -361,7 +361,11 @@ __device__ __forceinline__ void fft_rest_to_global(typename Cx<T>::type* buf, in
 
 // The extended row j of function f as NH complex pairs z_n = x_{2n} + i x_{2n+1} in the
 // padded shared buffer: mode 0 from an extended grid; mode 1 assembled (zeros, the
-// inside reals of f, the strip values).  Ends with a barrier.
+// inside reals of f, the strip values).  Ends with a barrier.  It makes the kernel's
+// dependent-launch wait: in mode 0 before anything else; in the assembled modes only
+// before the strip values, which the previous kernel (the blend + interpolation) writes.
+// f itself was written before that kernel's own wait returned, and this kernel was
+// launched after that kernel triggered, so f may be read before the wait.
 template <typename T, typename TV>
 __device__ __forceinline__ void assemble_row(const RowArgs& ra, int mode, int NH, int j, int f,
                                              const T* __restrict__ ext,
@@ -372,6 +376,8 @@ __device__ __forceinline__ void assemble_row(const RowArgs& ra, int mode, int NH
   const int nx = 2 * NH;
   auto put = [&](int i, T v) { reinterpret_cast<T*>(&buf[pad<T>(i >> 1)])[i & 1] = v; };
   if (mode == 0) {
+    pdl_wait();
+    pdl_trigger();
     const T* src = ext + (size_t)f * ra.grid_stride + (size_t)j * nx;
     for (int n = threadIdx.x; n < NH; n += blockDim.x) {
       const C v = reinterpret_cast<const C*>(src)[n];
@@ -416,6 +422,8 @@ __device__ __forceinline__ void assemble_row(const RowArgs& ra, int mode, int NH
     const int s0 = __ldg(ra.row_strip_off + j), s1 = __ldg(ra.row_strip_off + j + 1);
     const int base = j * nx;
     const TV* v = vals + (size_t)f * ra.n_strip;
+    pdl_wait();
+    pdl_trigger();
     for (int k = s0 + threadIdx.x; k < s1; k += blockDim.x) put(__ldg(ra.s_lin + k) - base, (T)__ldg(v + k));
   }
   __syncthreads();
@@ -443,7 +451,8 @@ __device__ __forceinline__ void even_odd_split(const typename Cx<T>::type* buf, 
 
 // rows: nx = 2^(LOGNH+1); block = NT = 2^LOGNH / E threads
 template <typename T, typename TV, int LOGNH>
-__global__ void __launch_bounds__((1 << LOGNH) / elems<T>() < 32 ? 32 : (1 << LOGNH) / elems<T>())
+__global__ void __launch_bounds__((1 << LOGNH) / elems<T>() < 32 ? 32 : (1 << LOGNH) / elems<T>(),
+                                  (sizeof(T) == 4 && LOGNH == 11) ? 8 : 1)
 k_fft_rows_p2(FftArgs fa, RowArgs ra, int mode, const T* __restrict__ ext,
               const double* __restrict__ f_grid, const TV* __restrict__ vals,
               typename Cx<T>::type* __restrict__ inter) {
@@ -454,8 +463,6 @@ k_fft_rows_p2(FftArgs fa, RowArgs ra, int mode, const T* __restrict__ ext,
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* buf = reinterpret_cast<C*>(smem_raw);
   const int j = blockIdx.x, f = blockIdx.y, t = threadIdx.x;
-  pdl_wait();
-  pdl_trigger();
   assemble_row<T, TV>(ra, mode, NH, j, f, ext, f_grid, vals, buf);
   const C* tw = reinterpret_cast<const C*>(fa.tsx);
   block_fft<T, LOGNH, E>(buf, t, t < NT, tw, 1);
@@ -490,8 +497,6 @@ k_rows_64n(FftArgs fa, RowArgs ra, int mode, const float* __restrict__ ext,
   float2* ex = buf + padded<float>(NH);  // [N2][8][9] exchange tiles
   const int j = blockIdx.x, f = blockIdx.y, t = threadIdx.x;
   const float2* w = reinterpret_cast<const float2*>(fa.twx);
-  pdl_wait();
-  pdl_trigger();
   assemble_row<float, float>(ra, mode, NH, j, f, ext, f_grid, vals, buf);
   if (t < 8 * N2) {
     const int n2 = t >> 3, l = t & 7;
