@@ -27,6 +27,12 @@ Matching values (Section 3.2, "two-step polynomial interpolation"), reading:
 * The matching value at r_{p,q} (eq. (3.5); t = (q-d+1) k1) is the degree M-1 Lagrange
   interpolant in t over M nodes: t = 0 with the boundary datum f(b) and the M-1 red
   stars, q = 0..d-2; r_{p,d-1} = b takes the boundary datum itself.
+Interior data only (Remark 3.2 II: no boundary values given), reading: the same lines
+  and red stars, each star interpolated from the grid nodes of its inside interval
+  alone (no squares, no node dropped), the M consecutive nodes with ceil(M/2) at or
+  below R_k; along the normal the degree M-2 Lagrange interpolant over the M-1 red
+  stars, evaluated at every matching point r_{p,q}, q = 0..d-1, including the foot b
+  itself (q = d-1, an extrapolation), whose value also serves as F_{p,0}.
 Blending (eq. (2.6) with A_r of Remark 2.2): F_{p,0} = f(b) and
 F_{p,q} = (A_r (Q^T f_{D_p}))_q for q = 1..C_r, evaluated right to left.
 Interpolation onto H cap V+ (Section 3.4), reading:
@@ -64,12 +70,13 @@ def lagrange_weights(nodes, t):
     return w
 
 
-def _line_candidates(coord_nodes, cross, star, h, drop=DROP):
+def _line_candidates(coord_nodes, cross, star, h, drop=DROP, squares=True):
     """Candidates (coordinate, kind, index) on one grid line around the red star.
 
     coord_nodes: coordinates of the grid nodes along the line; cross: sorted crossings
     of the line with the curve.  kind 0 = grid node (index along the line), kind 1 =
-    square (index into ``cross``)."""
+    square (index into ``cross``).  squares=False (interior data only): the grid nodes
+    of the inside interval alone, none dropped."""
     m = np.searchsorted(cross, star, side="right") - 1
     if m < 0 or m % 2 == 1 or m + 1 >= len(cross):
         raise ValueError("red star outside the domain along its grid line")
@@ -83,6 +90,8 @@ def _line_candidates(coord_nodes, cross, star, h, drop=DROP):
         jl += 1
     while jh >= jl and coord_nodes[jh] > hi:
         jh -= 1
+    if not squares:
+        return [(coord_nodes[j], 0, j) for j in range(jl, jh + 1)]
     if jl <= jh and coord_nodes[jl] - lo < drop * h:
         jl += 1
     if jl <= jh and hi - coord_nodes[jh] < drop * h:
@@ -100,11 +109,12 @@ def _choose_window(cands, star, M):
     return cands[s:s + M]
 
 
-def matching_stencils(geo):
+def matching_stencils(geo, interior=False):
     """Per normal p: the red-star parameters t_k, for each red star a dict
     {("g", lin) or ("b", idx): weight} over grid values and boundary data, and the
-    along-normal weights giving f(r_{p,q}), q = 0..d-2, from the red stars
-    (Section 3.2)."""
+    along-normal weights giving f(r_{p,q}), q = 0..d-2, from the boundary datum and
+    the red stars (Section 3.2).  interior: interior data only (Remark 3.2 II), the
+    weights give f(r_{p,q}), q = 0..d-1, from the red stars alone."""
     g, p = geo.grid, geo.params
     M, d, h = p.M, p.d, g.h
     out = []
@@ -124,15 +134,16 @@ def matching_stencils(geo):
         sigma = 1 if nb > 0 else -1
         xi = (base - 0.5 * h * nb - o0) / h
         i0 = math.floor(xi) if sigma > 0 else math.ceil(xi)
-        tk = [0.0]
-        star_terms = [{("b", k): 1.0}]
+        tk = [] if interior else [0.0]
+        star_terms = [] if interior else [{("b", k): 1.0}]
         for kk in range(M - 1):
             li = i0 - sigma * kk
             if li < 0 or li >= nlines:
                 raise ValueError("matching stencil leaves the grid")
             t = (line_coord[li] - base) / nb
             star = other_b + t * other_n
-            cands = _choose_window(_line_candidates(node_coords, crosses[li], star, h), star, M)
+            cands = _choose_window(_line_candidates(node_coords, crosses[li], star, h,
+                                                    squares=not interior), star, M)
             wv = lagrange_weights([c[0] for c in cands], star)
             terms = {}
             for (coord, kind, idx), wgt in zip(cands, wv):
@@ -144,23 +155,26 @@ def matching_stencils(geo):
                 terms[key] = terms.get(key, 0.0) + wgt
             tk.append(t)
             star_terms.append(terms)
-        wns = [lagrange_weights(tk, (q - d + 1) * p.k1) for q in range(d - 1)]
-        out.append({"t": tk, "stars": star_terms, "wn": wns})
+        nq = d if interior else d - 1
+        wns = [lagrange_weights(tk, (q - d + 1) * p.k1) for q in range(nq)]
+        out.append({"t": tk, "stars": star_terms, "wn": wns, "interior": interior})
     return out
 
 
 def matching_values(geo, stencils, f_grid, f_bdry):
-    """f_{D_p}: [B][d] matching values (q = d-1 is the boundary datum at the node)."""
+    """f_{D_p}: [B][d] matching values (q = d-1 is the boundary datum at the node; with
+    interior stencils and f_bdry None, its extrapolation from the red stars)."""
     p = geo.params
     fg = np.asarray(f_grid, dtype=np.float64).ravel()
-    fb = np.asarray(f_bdry, dtype=np.float64)
+    fb = None if f_bdry is None else np.asarray(f_bdry, dtype=np.float64)
     fD = np.zeros((p.B, p.d))
     for k, st in enumerate(stencils):
         stars = np.array([sum(wgt * (fg[key[1]] if key[0] == "g" else fb[key[1]])
                               for key, wgt in terms.items()) for terms in st["stars"]])
-        for q in range(p.d - 1):
+        for q in range(len(st["wn"])):
             fD[k, q] = float(np.dot(st["wn"][q], stars))
-        fD[k, p.d - 1] = fb[k]
+        if not st.get("interior", False):
+            fD[k, p.d - 1] = fb[k]
     return fD
 
 
@@ -203,9 +217,10 @@ def _lagrange_equispaced(M, t):
 
 
 def extension(geo, mats, f_grid, f_bdry, stencils=None):
-    """f^c on H: f inside, interpolated continuation on H cap V+, 0 elsewhere."""
+    """f^c on H: f inside, interpolated continuation on H cap V+, 0 elsewhere.
+    f_bdry None: interior data only (Remark 3.2 II)."""
     if stencils is None:
-        stencils = matching_stencils(geo)
+        stencils = matching_stencils(geo, interior=f_bdry is None)
     fD = matching_values(geo, stencils, f_grid, f_bdry)
     F = blend(mats, fD)
     vals = interpolate_strip(geo, F)

@@ -219,3 +219,78 @@ def test_blend_conditioning_floor(mats):
         fD1[k, :-1] = np.einsum("qe,e->q", np.array(s["wn"]), stars)
     d = np.abs(F.blend(mats, fD1) - F.blend(mats, fD0)).max() / np.abs(F.blend(mats, fD0)).max()
     assert 1e-13 < d < 3e-11 / 3, d
+
+
+# --------------------------------------------------------------------------- #
+# Interior data only (Remark 3.2 II)
+# --------------------------------------------------------------------------- #
+def test_interior_stencils_use_grid_nodes_only():
+    w = W.workload("star200")
+    st = F.matching_stencils(G.build_geometry(w), interior=True)
+    d, M = w.params.d, w.params.M
+    for s in st:
+        assert len(s["t"]) == M - 1 and len(s["wn"]) == d
+        assert all(key[0] == "g" for terms in s["stars"] for key in terms)
+
+
+@pytest.mark.parametrize("name", ["star200", "kite160x144"])
+def test_interior_matching_values_reproduce_polynomials(name):
+    """Each red star interpolates degree (its node count - 1) along its line and the
+    normal interpolant runs through M-1 stars: every polynomial of total degree up to
+    min(M-2, smallest node count - 1) is reproduced at all d matching points,
+    including the extrapolated foot value (degree 6 on star200, where every star has
+    M = 8 nodes; degree 5 on the coarse kite, whose shortest chords hold 6)."""
+    w = W.workload(name)
+    geo = G.build_geometry(w)
+    st = F.matching_stencils(geo, interior=True)
+    deg = min(w.params.M - 2, min(len(t) for s in st for t in s["stars"]) - 1)
+    assert deg == (6 if name == "star200" else 5)
+    poly = (lambda x, y: 1 + 0.3 * x ** 3 - 0.2 * x ** 2 * y ** 4 + 0.1 * y ** 6) if deg == 6 \
+        else (lambda x, y: 1 + 0.3 * x ** 3 - 0.2 * x ** 2 * y ** 3 + 0.1 * y ** 5)
+    fD = F.matching_values(geo, st, W.grid_values(w, poly), None)
+    d, k1 = w.params.d, w.params.k1
+    t = (np.arange(d) - d + 1) * k1
+    ex = poly(geo.bx[:, None] + t[None, :] * geo.nx_[:, None],
+              geo.by[:, None] + t[None, :] * geo.ny_[:, None])
+    assert np.abs(fD - ex).max() < 1e-12 * np.abs(ex).max()
+
+
+def test_interior_extension_is_f_inside_and_zero_beyond(mats):
+    w = W.workload("disk128")
+    geo = G.build_geometry(w)
+    fg = W.grid_values(w, W.f_expsincos)
+    ext = F.extension(geo, mats, fg, None)
+    assert np.array_equal(ext[geo.inside], fg[geo.inside])
+    mask = geo.inside.copy().ravel()
+    mask[geo.strip_lin] = True
+    assert np.all(ext.ravel()[~mask] == 0)
+
+
+def test_interior_only_converges_with_reduced_accuracy(mats):
+    """Remark 3.2 II: without boundary values the 2D-FC still converges, less
+    accurately near the boundary.  On the disk (f = -sin 5 pi x sin 5 pi y, d = 5):
+    order above 4 from h = 2e-2 to 1e-2, error below 3e-4 at h = 1e-2 and above the
+    error with boundary data at the same h."""
+    e = {}
+    for h in (2e-2, 1e-2):
+        w = paper_setup(W.disk(), h)
+        geo = G.build_geometry(w)
+        fg = W.grid_values(w, W.f_sin5pi)
+        ext_i = F.extension(geo, mats, fg, None)
+        e[h] = _fine_error_of(w, geo, ext_i, W.f_sin5pi)
+        if h == 1e-2:
+            ext_b = F.extension(geo, mats, fg, F.boundary_values(geo, W.f_sin5pi))
+            e_b = _fine_error_of(w, geo, ext_b, W.f_sin5pi)
+    assert np.log2(e[2e-2] / e[1e-2]) > 4, e
+    assert e_b < e[1e-2] < 3e-4, (e, e_b)
+
+
+def _fine_error_of(w, geo, ext, f):
+    from tests.fc2d_check import inside_fine, upsample2
+    fine = upsample2(ext)
+    g = w.grid
+    xf = g.a0 + (g.h / 2) * np.arange(2 * g.nx)
+    yf = g.b0 + (g.h / 2) * np.arange(2 * g.ny)
+    X, Y = np.meshgrid(xf, yf)
+    ins = inside_fine(geo.curve, xf, yf)
+    return np.abs(fine - f(X, Y))[ins].max() / np.abs(f(X, Y)[ins]).max()
