@@ -21,6 +21,13 @@
  *            (theta_p = 2 pi p/B, eq. (3.4)), then the crossings of each grid column
  *            x = x_i with the curve (i ascending, y ascending), then those of each
  *            grid row (j ascending, x ascending).
+ *            f_bdry_dev may be NULL in fc2d_blend, fc2d_extend, fc2d_extend_coeffs and
+ *            fc2d_extend_coeffs_compact: interior data only (Remark 3.2 II).  Each red
+ *            star is then interpolated from grid nodes alone and the matching value at
+ *            the foot is extrapolated from the red stars (degree M-2); it also serves
+ *            as F[f][p][0].  Accuracy near the boundary is lower, as the remark says.
+ *            These calls return FC2D_ERR_UNSUPPORTED with NULL boundary data when some
+ *            red star's chord holds no grid node (then only the boundary form exists).
  * Memory:    pointers named *_dev are device pointers owned by the caller; *_host are
  *            host pointers owned by the caller.  The plan owns only its own tables
  *            and workspace.
@@ -120,7 +127,8 @@ fc2d_status fc2d_strip_points(fc2d_plan_t plan, int32_t* lin_host, double* theta
 
 /* Steps 5 of Section 3.5 (Section 3.2 + eq. (2.6)): matching values and blending.
  * F_dev receives [n_f][B][C n_r + 1] strip values (double for FP64, float for MIXED):
- * F[f][p][0] = f at q(theta_p), F[f][p][q] = (A_r Q^T f_{D_p})_q. */
+ * F[f][p][0] = f at q(theta_p) (its extrapolation with NULL boundary data),
+ * F[f][p][q] = (A_r Q^T f_{D_p})_q. */
 fc2d_status fc2d_blend(fc2d_plan_t plan, int n_f, const double* f_grid_dev,
                        const double* f_bdry_dev, void* F_dev, void* stream);
 

@@ -329,24 +329,25 @@ __global__ void __launch_bounds__(256, 2) k_gather_blend_tc(GatherArgs g, TcArgs
       id[e] = on ? __ldg(g.gidx + base + e) : 0;
       wv[e] = on ? __ldg(g.gw + base + e) : 0.0;
     }
-    const double* wn = g.wn + ((size_t)pp * (d - 1) + (s < d - 1 ? s : 0)) * M;
+    const int nq = g.nq;
+    const double* wn = g.wn + ((size_t)pp * nq + (s < nq ? s : 0)) * M;
     double wnv[kTaps];
 #pragma unroll
-    for (int e = 0; e < kTaps; ++e) wnv[e] = (s < d - 1 && e < M) ? __ldg(wn + e) : 0.0;
+    for (int e = 0; e < kTaps; ++e) wnv[e] = (s < nq && e < M) ? __ldg(wn + e) : 0.0;
     double qv[kMaxD];
 #pragma unroll
     for (int i = 0; i < kMaxD; ++i) qv[i] = (s < d && i < d) ? __ldg(g.Q + i * d + s) : 0.0;
     pdl_wait();
     pdl_trigger();
     const double* fg = g.f_grid + (size_t)ff * g.grid_stride;
-    const double* fb = g.f_bdry + (size_t)ff * g.n_bdry;
+    const double* fb = g.f_bdry ? g.f_bdry + (size_t)ff * g.n_bdry : nullptr;
     double val[kTaps];
 #pragma unroll
     for (int e = 0; e < kTaps; ++e) {
       const int32_t k = id[e];
       val[e] = (star_lane && e < M) ? __ldg(k >= 0 ? fg + k : fb + (-1 - k)) : 0.0;
     }
-    const double fbp = __ldg(fb + pp);
+    const double fbp = fb ? __ldg(fb + pp) : 0.0;
     double star = 0.0;
 #pragma unroll
     for (int e = 0; e < kTaps; ++e) star = fma(wv[e], val[e], star);
@@ -356,7 +357,9 @@ __global__ void __launch_bounds__(256, 2) k_gather_blend_tc(GatherArgs g, TcArgs
       const double st = __shfl_sync(0xffffffffu, star, g0 + (e - 1 < 8 ? e - 1 : 0));
       if (e < M) acc = fma(wnv[e], st, acc);
     }
-    const double fD = s < d - 1 ? acc : (s == d - 1 ? fbp : 0.0);
+    const double fD = s < nq ? acc : (s == d - 1 ? fbp : 0.0);
+    // the value at the foot: the boundary datum, or its extrapolation (interior data)
+    const double f0 = __shfl_sync(0xffffffffu, fD, g0 + d - 1);
     double cs = 0.0;
 #pragma unroll
     for (int i = 0; i < kMaxD; ++i) {
@@ -367,7 +370,7 @@ __global__ void __launch_bounds__(256, 2) k_gather_blend_tc(GatherArgs g, TcArgs
     const float hi = to_tf32((float)v);
     *reinterpret_cast<float*>(c_hi + kmaj_off(ln, s)) = hi;
     *reinterpret_cast<float*>(c_lo + kmaj_off(ln, s)) = (float)(v - (double)hi);
-    if (s == 0) stage[ln * ldS] = (float)fbp;  // column 0: the boundary datum
+    if (s == 0) stage[ln * ldS] = (float)f0;  // column 0: the boundary datum
   }
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -551,29 +554,32 @@ __global__ void __launch_bounds__(kGiThreads, 1) k_gather_interp_tc(GatherArgs g
       id[e] = star_lane ? __ldg(g.gidx + base + e) : 0;
       wv[e] = star_lane ? __ldg(g.gw + base + e) : 0.0;
     }
-    const double* wn = g.wn + ((size_t)pp * (d - 1) + (s < d - 1 ? s : 0)) * M;
+    const int nq = g.nq;
+    const double* wn = g.wn + ((size_t)pp * nq + (s < nq ? s : 0)) * M;
 #pragma unroll
-    for (int e = 0; e < MM; ++e) wnv[e] = s < d - 1 ? __ldg(wn + e) : 0.0;
+    for (int e = 0; e < MM; ++e) wnv[e] = s < nq ? __ldg(wn + e) : 0.0;
 #pragma unroll
     for (int i = 0; i < kMaxD; ++i) qv[i] = (s < d && i < d) ? __ldg(g.Q + i * d + s) : 0.0;
     pdl_wait();
     pdl_trigger();
     const double* fg = g.f_grid + (size_t)f * g.grid_stride;
-    const double* fb = g.f_bdry + (size_t)f * g.n_bdry;
+    const double* fb = g.f_bdry ? g.f_bdry + (size_t)f * g.n_bdry : nullptr;
     double val[MM];
 #pragma unroll
     for (int e = 0; e < MM; ++e) {
       const int32_t k = id[e];
       val[e] = star_lane ? __ldg(k >= 0 ? fg + k : fb + (-1 - k)) : 0.0;
     }
-    const double fbp = __ldg(fb + pp);
+    const double fbp = fb ? __ldg(fb + pp) : 0.0;
     double star = 0.0;
 #pragma unroll
     for (int e = 0; e < MM; ++e) star = fma(wv[e], val[e], star);
     double acc = wnv[0] * fbp;
 #pragma unroll
     for (int e = 1; e < MM; ++e) acc = fma(wnv[e], __shfl_sync(0xffffffffu, star, g0 + e - 1), acc);
-    const double fD = s < d - 1 ? acc : (s == d - 1 ? fbp : 0.0);
+    const double fD = s < nq ? acc : (s == d - 1 ? fbp : 0.0);
+    // the value at the foot: the boundary datum, or its extrapolation (interior data)
+    const double f0 = __shfl_sync(0xffffffffu, fD, g0 + d - 1);
     double cs = 0.0;
 #pragma unroll
     for (int i = 0; i < kMaxD; ++i) {
@@ -584,7 +590,7 @@ __global__ void __launch_bounds__(kGiThreads, 1) k_gather_interp_tc(GatherArgs g
     const float hi = to_tf32((float)v);
     *reinterpret_cast<float*>(c_hi + kmaj_off(ln, s)) = hi;
     *reinterpret_cast<float*>(c_lo + kmaj_off(ln, s)) = (float)(v - (double)hi);
-    if (s == 0) stage[ln * ldS] = (float)fbp;
+    if (s == 0) stage[ln * ldS] = (float)f0;
   }
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");

@@ -77,9 +77,17 @@ GatherArgs gather_args(fc2d_plan_s* p, const double* fg, const double* fb, void*
   a.grid_stride = compact ? p->n_inside : (int64_t)p->grid.nx * p->grid.ny;
   a.f_grid = fg;
   a.f_bdry = fb;
-  a.gidx = compact ? p->dev.gidx_c : p->dev.gidx;
-  a.gw = p->dev.gw;
-  a.wn = p->dev.wn;
+  if (fb) {
+    a.nq = p->prm.d - 1;
+    a.gidx = compact ? p->dev.gidx_c : p->dev.gidx;
+    a.gw = p->dev.gw;
+    a.wn = p->dev.wn;
+  } else {  // interior data only (Remark 3.2 II)
+    a.nq = p->prm.d;
+    a.gidx = compact ? p->dev.gidx_ic : p->dev.gidx_i;
+    a.gw = p->dev.gw_i;
+    a.wn = p->dev.wn_i;
+  }
   a.Q = p->dev.Q;
   a.Ar = p->dev.Ar;
   a.F = F;
@@ -197,11 +205,22 @@ fc2d_status strip_values(fc2d_plan_s* p, int n_f, const double* fg, const double
 
 }  // namespace
 
+// fb == null selects the interior-data-only stencils; they exist unless a red star's
+// chord held no grid node
+static fc2d_status check_interior(fc2d_plan_t p, const double* fb, const char* who) {
+  if (!fb && !p->interior_ok)
+    return set_error(FC2D_ERR_UNSUPPORTED, std::string(who) +
+                                               ": no interior-only stencils (a red star's chord "
+                                               "holds no grid node); pass boundary values");
+  return FC2D_OK;
+}
+
 extern "C" fc2d_status fc2d_blend(fc2d_plan_t p, int n_f, const double* fg, const double* fb,
                                   void* F, void* stream) {
   fc2d_status st = check_nf(p, n_f);
   if (st) return st;
-  if (!fg || !fb || !F) return set_error(FC2D_ERR_ARG, "fc2d_blend: null pointer");
+  if (!fg || !F) return set_error(FC2D_ERR_ARG, "fc2d_blend: null pointer");
+  if ((st = check_interior(p, fb, "fc2d_blend"))) return st;
   cudaSetDevice(p->device);
   cudaStream_t s = (cudaStream_t)stream;
   if (p->prm.precision == FC2D_FP64) {
@@ -229,7 +248,8 @@ extern "C" fc2d_status fc2d_extend(fc2d_plan_t p, int n_f, const double* fg, con
                                    void* ext, void* stream) {
   fc2d_status st = check_nf(p, n_f);
   if (st) return st;
-  if (!fg || !fb || !ext) return set_error(FC2D_ERR_ARG, "fc2d_extend: null pointer");
+  if (!fg || !ext) return set_error(FC2D_ERR_ARG, "fc2d_extend: null pointer");
+  if ((st = check_interior(p, fb, "fc2d_extend"))) return st;
   cudaSetDevice(p->device);
   Layout L = layout(p, n_f);
   if ((st = ensure_workspace(p, L.total))) return st;
@@ -268,7 +288,8 @@ extern "C" fc2d_status fc2d_extend_coeffs(fc2d_plan_t p, int n_f, const double* 
                                           const double* fb, void* fhat, void* stream) {
   fc2d_status st = check_nf(p, n_f);
   if (st) return st;
-  if (!fg || !fb || !fhat) return set_error(FC2D_ERR_ARG, "fc2d_extend_coeffs: null pointer");
+  if (!fg || !fhat) return set_error(FC2D_ERR_ARG, "fc2d_extend_coeffs: null pointer");
+  if ((st = check_interior(p, fb, "fc2d_extend_coeffs"))) return st;
   cudaSetDevice(p->device);
   Layout L = layout(p, n_f);
   if ((st = ensure_workspace(p, L.total))) return st;
@@ -302,8 +323,9 @@ extern "C" fc2d_status fc2d_extend_coeffs_compact(fc2d_plan_t p, int n_f, const 
                                                   const double* fb, void* fhat, void* stream) {
   fc2d_status st = check_nf(p, n_f);
   if (st) return st;
-  if (!f_inside || !fb || !fhat)
+  if (!f_inside || !fhat)
     return set_error(FC2D_ERR_ARG, "fc2d_extend_coeffs_compact: null pointer");
+  if ((st = check_interior(p, fb, "fc2d_extend_coeffs_compact"))) return st;
   if (!p->dev.row_iv_coff || !p->dev.gidx_c)
     return set_error(FC2D_ERR_UNSUPPORTED,
                      "fc2d_extend_coeffs_compact: more than 2^31 - 1 inside points");

@@ -152,7 +152,8 @@ __global__ void __launch_bounds__(256) k_gather_blend(GatherArgs a) {
   const int pp = live ? p : 0;
   const int M = a.M, d = a.d, NS = M - 1;
   const double* fg = a.f_grid + (size_t)f * a.grid_stride;
-  const double* fb = a.f_bdry + (size_t)f * a.n_bdry;
+  const double* fb = a.f_bdry ? a.f_bdry + (size_t)f * a.n_bdry : nullptr;
+  const int nq = a.nq;
   pdl_wait();
   pdl_trigger();
   double star = 0.0;
@@ -165,17 +166,19 @@ __global__ void __launch_bounds__(256) k_gather_blend(GatherArgs a) {
       star = fma(__ldg(gw + e), v, star);
     }
   }
-  const double fbp = __ldg(fb + pp);
+  const double fbp = fb ? __ldg(fb + pp) : 0.0;
   double fD;
   {
-    const double* wn = a.wn + ((size_t)pp * (d - 1) + (s < d - 1 ? s : 0)) * M;
-    double acc = (s < d - 1) ? __ldg(wn) * fbp : 0.0;
+    const double* wn = a.wn + ((size_t)pp * nq + (s < nq ? s : 0)) * M;
+    double acc = (s < nq) ? __ldg(wn) * fbp : 0.0;
     for (int e = 1; e < M; ++e) {
       const double st = __shfl_sync(0xffffffffu, star, g0 + e - 1);
-      if (s < d - 1) acc = fma(__ldg(wn + e), st, acc);
+      if (s < nq) acc = fma(__ldg(wn + e), st, acc);
     }
-    fD = s < d - 1 ? acc : (s == d - 1 ? fbp : 0.0);
+    fD = s < nq ? acc : (s == d - 1 ? fbp : 0.0);
   }
+  // the value at the foot: the boundary datum, or its extrapolation (interior data)
+  const double f0 = __shfl_sync(0xffffffffu, fD, g0 + d - 1);
   double cs = 0.0;  // Gram coefficient c_s (lanes s < d)
   for (int i = 0; i < d; ++i) {
     const double v = __shfl_sync(0xffffffffu, fD, g0 + i);
@@ -187,7 +190,7 @@ __global__ void __launch_bounds__(256) k_gather_blend(GatherArgs a) {
     for (int j = 0; j < GS; ++j) c[j] = __shfl_sync(0xffffffffu, cs, g0 + (j < d ? j : 0));
     if (!live) return;
     double* F = reinterpret_cast<double*>(a.F) + ((size_t)f * a.B + p) * (a.Cr + 1);
-    if (s == 0) F[0] = fbp;
+    if (s == 0) F[0] = f0;
     for (int q = s; q < a.Cr; q += GS) {
       const double* ar = a.Ar + (size_t)q * d;
       double v = 0.0;
@@ -199,7 +202,7 @@ __global__ void __launch_bounds__(256) k_gather_blend(GatherArgs a) {
   } else {
     if (!live) return;
     if (s < d) a.coef[((size_t)f * a.B + p) * a.coef_ld + s] = cs;
-    if (s == 0) a.bvals[(size_t)f * a.B + p] = fbp;
+    if (s == 0) a.bvals[(size_t)f * a.B + p] = f0;
   }
 }
 

@@ -12,12 +12,13 @@ constexpr int kMaxD = 8;
 
 struct GatherArgs {
   int B, M, d, Cr;
+  int nq;                 // rows of wn: d-1 (boundary data given) or d (interior data only)
   int64_t n_bdry, grid_stride;
   const double* f_grid;   // [n_f][ny][nx]
-  const double* f_bdry;   // [n_f][n_bdry]
+  const double* f_bdry;   // [n_f][n_bdry], or null: interior data only
   const int32_t* gidx;    // [B][M-1][M]
   const double* gw;       // [B][M-1][M]
-  const double* wn;       // [B][d-1][M]
+  const double* wn;       // [B][nq][M]: weights of (boundary datum, red stars)
   const double* Q;        // [d][d]
   const double* Ar;       // [Cr][d]
   void* F;                // FP64 form: [n_f][B][Cr+1]

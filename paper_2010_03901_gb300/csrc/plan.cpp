@@ -722,10 +722,13 @@ extern "C" fc2d_status fc2d_plan(const fc2d_boundary* boundary, const fc2d_grid*
   row_off[ny] = off;
   p->n_bdry = off;
 
-  // matching stencils (Section 3.2)
+  // matching stencils (Section 3.2), with boundary data and (gidx_i, gw_i, wn_i) from
+  // interior data only (Remark 3.2 II: stars from grid nodes alone, the foot value
+  // extrapolated; wn_i has d rows and a zero weight on the boundary-datum slot)
   const int NS = M - 1;
-  std::vector<int32_t> gidx((size_t)B * NS * M, 0);
+  std::vector<int32_t> gidx((size_t)B * NS * M, 0), gidx_i((size_t)B * NS * M, 0);
   std::vector<double> gw((size_t)B * NS * M, 0.0), wn((size_t)B * (d - 1) * M, 0.0);
+  std::vector<double> gw_i((size_t)B * NS * M, 0.0), wn_i((size_t)B * d * M, 0.0);
   const double tie = std::ldexp(1.0, -30), drop = 0.5;
   for (int k = 0; k < B; ++k) {
     bool vertical = std::fabs(bnx[k]) >= std::fabs(bny[k]) * (1.0 - tie);
@@ -765,6 +768,29 @@ extern "C" fc2d_status fc2d_plan(const fc2d_boundary* boundary, const fc2d_grid*
       int jh = std::min(nnodes - 1, (int)std::floor((hi - no) / h) + 1);
       while (jl <= jh && (*node_c)[jl] < lo) ++jl;
       while (jh >= jl && (*node_c)[jh] > hi) --jh;
+      const size_t base_i = ((size_t)k * NS + s) * M;
+      {
+        // interior data only: the nodes of the inside interval, none dropped (a chord
+        // without a node leaves the plan without the interior-only form)
+        if (jl > jh) p->interior_ok = false;
+        const int n = std::max(jh - jl + 1, 1);
+        int s0 = 0, len = n;
+        if (n > M) {
+          int c = 0;
+          for (int j = jl; j <= jh; ++j) c += ((*node_c)[j] <= star);
+          s0 = std::min(std::max(c - (M + 1) / 2, 0), n - M);
+          len = M;
+        }
+        double cn[kMaxM], w[kMaxM];
+        const int jb = std::min(jl, nnodes - 1);
+        for (int e = 0; e < len; ++e) cn[e] = (*node_c)[jb + s0 + e];
+        lagrange(cn, len, star, w);
+        for (int e = 0; e < M; ++e) {
+          const int j = jb + s0 + (e < len ? e : 0);
+          gidx_i[base_i + e] = vertical ? (int32_t)((int64_t)j * nx + li) : (int32_t)(li * (int64_t)nx + j);
+          gw_i[base_i + e] = e < len ? w[e] : 0.0;
+        }
+      }
       if (jl <= jh && (*node_c)[jl] - lo < drop * h) ++jl;
       if (jl <= jh && hi - (*node_c)[jh] < drop * h) --jh;
       // candidates: lower square, nodes, upper square
@@ -787,7 +813,6 @@ extern "C" fc2d_status fc2d_plan(const fc2d_boundary* boundary, const fc2d_grid*
       }
       double w[kMaxM];
       lagrange(&cc[s0], len, star, w);
-      size_t base_i = ((size_t)k * NS + s) * M;
       for (int e = 0; e < M; ++e) {
         if (e < len) {
           gidx[base_i + e] = ci[s0 + e];
@@ -802,6 +827,11 @@ extern "C" fc2d_status fc2d_plan(const fc2d_boundary* boundary, const fc2d_grid*
       double w[kMaxM];
       lagrange(tk, M, (q - d + 1) * k1, w);
       for (int e = 0; e < M; ++e) wn[((size_t)k * (d - 1) + q) * M + e] = w[e];
+    }
+    for (int q = 0; q < d; ++q) {
+      double w[kMaxM];
+      lagrange(tk + 1, M - 1, (q - d + 1) * k1, w);
+      for (int e = 1; e < M; ++e) wn_i[((size_t)k * d + q) * M + e] = w[e - 1];
     }
   }
 
@@ -837,25 +867,33 @@ extern "C" fc2d_status fc2d_plan(const fc2d_boundary* boundary, const fc2d_grid*
   // the stencil taps as compact indices (every grid tap is an inside point); the
   // compact form is offered when the inside points have int32 indices
   const bool compact = p->n_inside < ((int64_t)1 << 31);
-  std::vector<int32_t> gidx_c(compact ? gidx.size() : 0);
-  for (size_t e = 0; e < gidx_c.size(); ++e) {
-    const int32_t id = gidx[e];
-    if (id < 0) {
-      gidx_c[e] = id;
-      continue;
+  auto to_compact = [&](const std::vector<int32_t>& gi, std::vector<int32_t>& gc) {
+    gc.assign(compact ? gi.size() : 0, 0);
+    for (size_t e = 0; e < gc.size(); ++e) {
+      const int32_t id = gi[e];
+      if (id < 0) {
+        gc[e] = id;
+        continue;
+      }
+      const int jr = id / nx, ic = id - jr * nx;
+      int32_t c = -1;
+      for (int k = p->row_iv_off[jr]; k < p->row_iv_off[jr + 1]; ++k)
+        if (ic >= p->row_iv[2 * k] && ic <= p->row_iv[2 * k + 1])
+          c = p->row_iv_coff[k] + (ic - p->row_iv[2 * k]);
+      if (c < 0) return false;
+      gc[e] = c;
     }
-    const int jr = id / nx, ic = id - jr * nx;
-    int32_t c = -1;
-    for (int k = p->row_iv_off[jr]; k < p->row_iv_off[jr + 1]; ++k)
-      if (ic >= p->row_iv[2 * k] && ic <= p->row_iv[2 * k + 1])
-        c = p->row_iv_coff[k] + (ic - p->row_iv[2 * k]);
-    if (c < 0) return fail(set_error(FC2D_ERR_GEOMETRY, "a matching stencil tap is not an inside point"));
-    gidx_c[e] = c;
-  }
+    return true;
+  };
+  std::vector<int32_t> gidx_c, gidx_ic;
+  if (!to_compact(gidx, gidx_c) || !to_compact(gidx_i, gidx_ic))
+    return fail(set_error(FC2D_ERR_GEOMETRY, "a matching stencil tap is not an inside point"));
   if ((st = upload(&p->dev.Q, p->Q)) || (st = upload(&p->dev.Ar, p->Ar)) ||
       (st = upload(&p->dev.Ar_hi, arh)) || (st = upload(&p->dev.Ar_lo, arl)) ||
       (st = upload(&p->dev.gidx, gidx)) || (st = upload(&p->dev.gw, gw)) ||
-      (st = upload(&p->dev.wn, wn)) || (st = upload(&p->dev.s_lin, p->strip_lin)) ||
+      (st = upload(&p->dev.wn, wn)) || (st = upload(&p->dev.gidx_i, gidx_i)) ||
+      (st = upload(&p->dev.gw_i, gw_i)) || (st = upload(&p->dev.wn_i, wn_i)) ||
+      (st = upload(&p->dev.s_lin, p->strip_lin)) ||
       (st = upload(&p->dev.s_theta, p->strip_theta)) ||
       (st = upload(&p->dev.s_eta, p->strip_eta)) ||
       (st = upload(&p->dev.row_iv_off, p->row_iv_off)) ||
@@ -863,6 +901,7 @@ extern "C" fc2d_status fc2d_plan(const fc2d_boundary* boundary, const fc2d_grid*
       (st = upload(&p->dev.row_strip_off, p->row_strip_off)) ||
       (compact && (st = upload(&p->dev.row_iv_coff, p->row_iv_coff))) ||
       (compact && (st = upload(&p->dev.gidx_c, gidx_c))) ||
+      (compact && (st = upload(&p->dev.gidx_ic, gidx_ic))) ||
       (st = upload(&p->dev.status, zero_status)) ||
       (st = upload(&p->fx.tw64, p->fx.tw_host)) || (st = upload(&p->fx.tw32, tw32x)) ||
       (st = upload(&p->fy.tw64, p->fy.tw_host)) || (st = upload(&p->fy.tw32, tw32y)) ||
@@ -937,6 +976,7 @@ extern "C" void fc2d_destroy(fc2d_plan_t p) {
                   p->dev.s_pb, p->dev.s_sb, p->dev.own_off, p->dev.own_k,
                   p->dev.own_pack, p->dev.own_w, p->dev.own_start, p->dev.row_iv_off,
                   p->dev.row_iv, p->dev.row_strip_off, p->dev.row_iv_coff, p->dev.gidx_c,
+                  p->dev.gidx_i, p->dev.gw_i, p->dev.wn_i, p->dev.gidx_ic,
                   p->dev.status, p->fx.tw64, p->fx.tw32,
                   p->fy.tw64, p->fy.tw32, p->rtw64, p->rtw32, p->ws.base,
                   p->fx.tws64, p->fx.tws32, p->fy.tws64, p->fy.tws32};

@@ -71,6 +71,11 @@ struct DeviceTables {
   // inside interval's first point, and the stencil taps as compact indices
   int32_t* row_iv_coff = nullptr;   // [n_iv]
   int32_t* gidx_c = nullptr;        // [B][M-1][M] as gidx, >= 0 entries compact
+  // interior data only (no boundary values): stencils from grid nodes alone
+  int32_t* gidx_i = nullptr;        // [B][M-1][M] grid indices
+  int32_t* gidx_ic = nullptr;       // [B][M-1][M] the same as compact indices
+  double* gw_i = nullptr;           // [B][M-1][M]
+  double* wn_i = nullptr;           // [B][d][M] (slot 0, the boundary datum, is zero)
   int* status = nullptr;            // latched device status word
 };
 
@@ -102,6 +107,7 @@ struct fc2d_plan_s {
   std::vector<int32_t> row_iv_coff;         // compact offset of each inside interval
   int64_t n_inside = 0;
   int64_t n_bdry = 0;
+  bool interior_ok = true;  // every red star has a grid node (interior-only form usable)
   fc2d::FftAxis fx, fy;                      // nx/2 (complex) and ny
   std::vector<double> rtw_host;              // exp(-2 pi i k/nx), k <= nx/2 (R2C post-process)
   double* rtw64 = nullptr;

@@ -43,7 +43,8 @@ def run(w):
         name, n, sz = out[pos:end].decode().split()
         n, sz = int(n), int(sz)
         dt = types[sz]
-        if name in ("row_iv_off", "row_iv", "strip_lin", "gidx", "gidx_c", "row_iv_coff"):
+        if name in ("row_iv_off", "row_iv", "strip_lin", "gidx", "gidx_c", "row_iv_coff",
+                    "gidx_i", "interior_ok"):
             dt = np.int32
         arr = np.frombuffer(out[end + 1:end + 1 + n * sz], dtype=dt)
         res[name] = arr

@@ -152,5 +152,10 @@ int main(int argc, char** argv) {
   dump("row_iv_coff", p->row_iv_coff.data(), p->row_iv_coff.size());
   dump("gw", p->dev.gw, B * (M - 1) * M);
   dump("wn", p->dev.wn, B * (d - 1) * M);
+  dump("gidx_i", p->dev.gidx_i, B * (M - 1) * M);
+  dump("gw_i", p->dev.gw_i, B * (M - 1) * M);
+  dump("wn_i", p->dev.wn_i, B * d * M);
+  const int32_t ok = p->interior_ok ? 1 : 0;
+  dump("interior_ok", &ok, 1);
   return 0;
 }

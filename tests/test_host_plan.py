@@ -86,6 +86,28 @@ def test_matching_stencils_give_the_oracle_matching_values(both):
     assert np.abs(fD - ref[:, :d - 1]).max() < 1e-13 * np.abs(ref).max()
 
 
+def test_interior_stencils_give_the_oracle_matching_values(both):
+    """Interior data only (Remark 3.2 II): the plan's grid-node stencils and d-row
+    normal weights give the oracle's matching values, foot value included."""
+    w, r, geo = both
+    p = w.params
+    B, M, d = p.B, p.M, p.d
+    assert r["interior_ok"][0] == 1
+    fg = W.grid_values(w, W.f_expsincos).ravel()
+    gidx = r["gidx_i"].reshape(B, M - 1, M)
+    assert np.all(gidx >= 0)
+    stars = np.einsum("bse,bse->bs", r["gw_i"].reshape(B, M - 1, M), fg[gidx])
+    wn = r["wn_i"].reshape(B, d, M)
+    assert np.all(wn[:, :, 0] == 0)
+    fD = np.einsum("bqe,be->bq", wn[:, :, 1:], stars)
+    st = OF.matching_stencils(geo, interior=True)
+    ref = OF.matching_values(geo, st, W.grid_values(w, W.f_expsincos), None)
+    # two summation orders of sums whose terms reach (sum |wn|)(sum |gw|) max|f|: the
+    # foot extrapolation's weights grow with M (about 4e3 in sum at M = 13)
+    amp = np.abs(wn).sum(axis=2).max() * np.abs(r["gw_i"].reshape(B, M - 1, M)).sum(axis=2).max()
+    assert np.abs(fD - ref).max() < 16 * np.finfo(float).eps * amp * np.abs(fg).max()
+
+
 def test_plans_of_the_eight_star_workload():
     """The library's plan builds on all eight stars of the batched workload (several of
     them symmetric about y = 0 with a grid row on it), and on the smallest one its strip

@@ -294,3 +294,23 @@ def _fine_error_of(w, geo, ext, f):
     X, Y = np.meshgrid(xf, yf)
     ins = inside_fine(geo.curve, xf, yf)
     return np.abs(fine - f(X, Y))[ins].max() / np.abs(f(X, Y)[ins]).max()
+
+
+def test_interior_blend_conditioning_floor(mats):
+    """Interior data only: the foot value is an extrapolation (normal weights up to
+    ~3e2 in absolute sum at d = 5, M = 8), so two FP64 summation orders of the
+    matching values move F by up to ~4e-11 relative, against ~7e-12 with boundary
+    data.  The GPU bar on interior-mode strip values, 2e-10, is five times that."""
+    w = W.workload("star200")
+    geo = G.build_geometry(w)
+    st = F.matching_stencils(geo, interior=True)
+    fg = W.grid_values(w, W.f_expsincos)
+    flat = fg.ravel()
+    fD0 = F.matching_values(geo, st, fg, None)
+    fD1 = fD0.copy()
+    for k, s in enumerate(st):
+        stars = np.array([np.einsum("i,i->", np.array(list(t.values())),
+                                    np.array([flat[key[1]] for key in t])) for t in s["stars"]])
+        fD1[k, :] = np.einsum("qe,e->q", np.array(s["wn"]), stars)
+    d = np.abs(F.blend(mats, fD1) - F.blend(mats, fD0)).max() / np.abs(F.blend(mats, fD0)).max()
+    assert 1e-12 < d < 2e-10 / 3, d
