@@ -4,6 +4,7 @@ TEST INFRASTRUCTURE ONLY (see ``oracle/__init__.py``).
 
 extension(geo, mats, f_grid, f_bdry) -> f^c on the grid H   (steps 5 and 6)
 coefficients(ext)                    -> hat f^c, eq. (3.1)  (step 7)
+extension_complex, coefficients_complex: the same for complex f (full spectrum)
 
 Matching values (Section 3.2, "two-step polynomial interpolation"), reading:
 * Normal p with foot b = q(theta_p), outward normal n.  If |n_x| >= |n_y| (with a
@@ -236,6 +237,37 @@ def coefficients(ext):
     numpy's FFT serves as the library primitive for the DFT."""
     ny, nx = ext.shape
     return np.fft.rfft2(ext) / (nx * ny)
+
+
+def extension_complex(geo, mats, f_grid, f_bdry, stencils=None):
+    """f^c of a complex f (Section 3: f maps the domain to C): every step is linear and
+    real, so f^c = (Re f)^c + i (Im f)^c.  f_grid complex [ny][nx]; f_bdry complex or None."""
+    fg = np.asarray(f_grid)
+    fb = None if f_bdry is None else np.asarray(f_bdry)
+    re = extension(geo, mats, fg.real, None if fb is None else fb.real, stencils)
+    im = extension(geo, mats, fg.imag, None if fb is None else fb.imag, stencils)
+    return re + 1j * im
+
+
+def coefficients_complex(ext):
+    """hat f^c_{l,m} of eq. (3.1) for complex data: the full spectrum [Ny][Nx] in DFT
+    index order (l > Nx/2 and m > Ny/2 stand for l - Nx and m - Ny).  numpy's FFT
+    serves as the library primitive for the DFT."""
+    ny, nx = ext.shape
+    return np.fft.fft2(ext) / (nx * ny)
+
+
+def dft_bruteforce_complex(ext):
+    """The full spectrum by the O(N^4) definition (small grids only)."""
+    ny, nx = ext.shape
+    i = np.arange(nx)
+    j = np.arange(ny)
+    out = np.zeros((ny, nx), dtype=np.complex128)
+    for m in range(ny):
+        for l in range(nx):
+            ph = np.exp(-2j * np.pi * (l * i[None, :] / nx + m * j[:, None] / ny))
+            out[m, l] = np.sum(ext * ph) / (nx * ny)
+    return out
 
 
 def dft_bruteforce(ext):

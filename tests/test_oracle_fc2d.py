@@ -314,3 +314,37 @@ def test_interior_blend_conditioning_floor(mats):
         fD1[k, :] = np.einsum("qe,e->q", np.array(s["wn"]), stars)
     d = np.abs(F.blend(mats, fD1) - F.blend(mats, fD0)).max() / np.abs(F.blend(mats, fD0)).max()
     assert 1e-12 < d < 2e-10 / 3, d
+
+
+# --------------------------------------------------------------------------- #
+# Complex-valued f (Section 3: f maps the domain to C)
+# --------------------------------------------------------------------------- #
+def test_complex_spectrum_matches_the_brute_force_definition():
+    rng = np.random.default_rng(5)
+    ext = rng.standard_normal((6, 10)) + 1j * rng.standard_normal((6, 10))
+    assert np.allclose(F.coefficients_complex(ext), F.dft_bruteforce_complex(ext),
+                       rtol=0, atol=1e-15)
+
+
+def test_complex_spectrum_of_real_data_is_the_completed_half_spectrum():
+    """For real f the full spectrum is the R2C half spectrum completed by Hermitian
+    symmetry: X[m][l] = conj(X[-m][-l])."""
+    rng = np.random.default_rng(6)
+    ext = rng.standard_normal((8, 12))
+    full = F.coefficients_complex(ext)
+    half = F.coefficients(ext)
+    assert np.allclose(full[:, :7], half, rtol=0, atol=1e-16)
+    m, l = np.meshgrid(np.arange(8), np.arange(7, 12), indexing="ij")
+    assert np.allclose(full[m, l], np.conj(half[(-m) % 8, 12 - l]), rtol=0, atol=1e-16)
+
+
+def test_complex_extension_is_linear_and_exact_inside(mats):
+    w = W.workload("star200")
+    geo = G.build_geometry(w)
+    fr, fi = W.f_expsincos, W.trig_sum(6, 2)
+    fg = W.grid_values(w, fr) + 1j * W.grid_values(w, fi)
+    fb = F.boundary_values(geo, fr) + 1j * F.boundary_values(geo, fi)
+    ext = F.extension_complex(geo, mats, fg, fb)
+    assert np.array_equal(ext[geo.inside], fg[geo.inside])
+    assert np.abs(ext.real - F.extension(geo, mats, fg.real, fb.real)).max() == 0
+    assert np.abs(ext.imag - F.extension(geo, mats, fg.imag, fb.imag)).max() == 0
