@@ -154,6 +154,18 @@ fc2d_status fc2d_coeffs(fc2d_plan_t plan, int n_f, const void* ext_dev, void* fh
 fc2d_status fc2d_extend_coeffs(fc2d_plan_t plan, int n_f, const double* f_grid_dev,
                                const double* f_bdry_dev, void* fhat_dev, void* stream);
 
+/* Steps 5-7 for a complex-valued f (Section 3: f maps the domain to C).  f_grid_dev
+ * [n_f][2][ny][nx] double: the real part of function f, then its imaginary part;
+ * f_bdry_dev [n_f][2][n_bdry] in the same way, or NULL (interior data only).
+ * fhat_dev receives the full spectrum [n_f][ny][nx][2] (re, im; double for FP64, float
+ * for MIXED), fhat[f][m][l] = (1/(nx ny)) sum_{j,i} ext[f][j][i] e^{-2 pi i (l i/nx +
+ * m j/ny)}, 0 <= l < nx, 0 <= m < ny, with ext = ext(Re f) + i ext(Im f) (the method is
+ * linear and real).  The two parts run through the real path as functions 2f and 2f+1;
+ * a last kernel assembles the full spectrum from their half spectra by Hermitian
+ * symmetry.  Plan workspace: that of 2 n_f functions plus their half spectra. */
+fc2d_status fc2d_extend_coeffs_complex(fc2d_plan_t plan, int n_f, const double* f_grid_dev,
+                                       const double* f_bdry_dev, void* fhat_dev, void* stream);
+
 /* The grid points of the closed domain (the points where f is given; Section 3.1) in the
  * order of the compact entry point below: row by row (y ascending), within a row by x.
  * lin_host (host memory, n_inside entries from fc2d_plan_info) receives their linear

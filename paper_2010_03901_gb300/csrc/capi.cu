@@ -309,6 +309,40 @@ extern "C" fc2d_status fc2d_extend_coeffs(fc2d_plan_t p, int n_f, const double* 
   return launched("fc2d_extend_coeffs");
 }
 
+extern "C" fc2d_status fc2d_extend_coeffs_complex(fc2d_plan_t p, int n_f, const double* fg,
+                                                  const double* fb, void* fhat, void* stream) {
+  fc2d_status st = check_nf(p, n_f);
+  if (st) return st;
+  if (n_f > (1 << 29)) return set_error(FC2D_ERR_ARG, "fc2d_extend_coeffs_complex: n_f too large");
+  if (!fg || !fhat) return set_error(FC2D_ERR_ARG, "fc2d_extend_coeffs_complex: null pointer");
+  if ((st = check_interior(p, fb, "fc2d_extend_coeffs_complex"))) return st;
+  cudaSetDevice(p->device);
+  const int n2 = 2 * n_f;  // the real and imaginary parts as functions 2f and 2f + 1
+  Layout L = layout(p, n2);
+  const bool f64 = p->prm.precision == FC2D_FP64;
+  const size_t esz = f64 ? 8 : 4;
+  const size_t ohalf = L.total;
+  const size_t half = al((size_t)n2 * p->grid.ny * (p->grid.nx / 2 + 1) * 2 * esz);
+  if ((st = ensure_workspace(p, ohalf + half))) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  FftArgs fa = fft_args(p);
+  if ((st = strip_values(p, n2, fg, fb, L, s))) return st;
+  {
+    ProfScope ps(p, "fft_rows_fused", s);
+    launch_fft_rows(fa, row_args(p), n2, f64, 1, nullptr, fg, ws(p, L.ovals), ws(p, L.ointer),
+                    s);
+  }
+  {
+    ProfScope ps(p, "fft_cols", s);
+    launch_fft_cols(fa, n2, f64, ws(p, L.ointer), ws(p, ohalf), s);
+  }
+  {
+    ProfScope ps(p, "complex_spectrum", s);
+    launch_complex_spectrum(p->grid.nx, p->grid.ny, n_f, f64, ws(p, ohalf), fhat, s);
+  }
+  return launched("fc2d_extend_coeffs_complex");
+}
+
 extern "C" fc2d_status fc2d_inside_points(fc2d_plan_t p, int64_t* lin_host) {
   if (!p || !lin_host) return set_error(FC2D_ERR_ARG, "fc2d_inside_points: null argument");
   const int nx = p->grid.nx, ny = p->grid.ny;

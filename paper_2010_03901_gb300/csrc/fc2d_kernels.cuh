@@ -150,6 +150,10 @@ void launch_fft_rows(const FftArgs& fa, const RowArgs& ra, int n_f, bool fp64, i
 // in place in two passes).
 void launch_fft_cols(const FftArgs& fa, int n_f, bool fp64, void* inter, void* fhat,
                      cudaStream_t s);
+// complex f: the full spectrum [n_f][ny][nx] from the half spectra of the real and
+// imaginary parts, stored as functions 2f and 2f + 1 of `half`
+void launch_complex_spectrum(int nx, int ny, int n_f, bool fp64, const void* half, void* out,
+                             cudaStream_t s);
 // Fourier Forwarding: modal advance of [2 n_f] row spectra (u's then u_t's), in place.
 void launch_wave_cols(const FftArgs& fa, int n_f, void* inter, double c, double t, double Lx,
                       double Ly, cudaStream_t s);

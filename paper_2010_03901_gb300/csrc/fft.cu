@@ -147,4 +147,44 @@ void launch_fft_cols(const FftArgs& fa, int n_f, bool fp64, void* inter, void* f
   }
 }
 
+// Full spectrum of a complex function u + i v from the half spectra A of u and B of v
+// ([2 n_f][ny][nx/2+1], u and v of function f at 2f and 2f + 1): X[m][l] = A[m][l] +
+// i B[m][l] for l <= nx/2, and above, from the Hermitian symmetry of a real function's
+// spectrum, X[m][l] = conj(A[-m][nx-l]) + i conj(B[-m][nx-l]).  One block row per (m, f).
+template <typename C>
+__global__ void __launch_bounds__(256) k_complex_spectrum(int nx, int ny, const C* __restrict__ half,
+                                                          C* __restrict__ out) {
+  const int m = blockIdx.y, f = blockIdx.z, nh = nx / 2 + 1;
+  const C* A = half + (size_t)2 * f * ny * nh;
+  const C* B = A + (size_t)ny * nh;
+  C* o = out + ((size_t)f * ny + m) * nx;
+  const int mc = m ? ny - m : 0;
+  pdl_wait();
+  pdl_trigger();
+  for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < nx; l += gridDim.x * blockDim.x) {
+    C a, b;
+    if (l < nh) {
+      a = A[(size_t)m * nh + l];
+      b = B[(size_t)m * nh + l];
+    } else {
+      a = A[(size_t)mc * nh + (nx - l)];
+      b = B[(size_t)mc * nh + (nx - l)];
+      a.y = -a.y;
+      b.y = -b.y;
+    }
+    o[l] = C{a.x - b.y, a.y + b.x};
+  }
+}
+
+void launch_complex_spectrum(int nx, int ny, int n_f, bool fp64, const void* half, void* out,
+                             cudaStream_t s) {
+  const dim3 grid((nx + 255) / 256, ny, n_f);
+  if (fp64)
+    launch_pdl(k_complex_spectrum<double2>, grid, dim3(256), 0, s, nx, ny,
+               static_cast<const double2*>(half), static_cast<double2*>(out));
+  else
+    launch_pdl(k_complex_spectrum<float2>, grid, dim3(256), 0, s, nx, ny,
+               static_cast<const float2*>(half), static_cast<float2*>(out));
+}
+
 }  // namespace fc2d

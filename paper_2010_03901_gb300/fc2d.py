@@ -72,6 +72,7 @@ def load_library(path: str = LIB_PATH):
         "fc2d_extend_coeffs": [P, ct.c_int, P, P, P, P],
         "fc2d_inside_points": [P, P],
         "fc2d_extend_coeffs_compact": [P, ct.c_int, P, P, P, P],
+        "fc2d_extend_coeffs_complex": [P, ct.c_int, P, P, P, P],
         "fc2d_coeffs_static": [P, ct.c_int, P, P, P],
         "fc2d_sync_status": [P, P],
         "fc2d_poisson_plan": [P, ct.c_int],
@@ -195,6 +196,12 @@ class Plan:
 
     def fc2d_extend_coeffs_compact(self, n_f, f_inside, f_bdry, fhat, stream=None):
         _check(_lib.fc2d_extend_coeffs_compact(self.handle, n_f, _ptr(f_inside), _ptr(f_bdry),
+                                               _ptr(fhat), _stream(stream)))
+
+    def fc2d_extend_coeffs_complex(self, n_f, f_grid, f_bdry, fhat, stream=None):
+        """Complex f: f_grid [n_f][2][ny][nx] (re, im), f_bdry [n_f][2][n_bdry] or None;
+        fhat [n_f][ny][nx][2] receives the full spectrum."""
+        _check(_lib.fc2d_extend_coeffs_complex(self.handle, n_f, _ptr(f_grid), _ptr(f_bdry),
                                                _ptr(fhat), _stream(stream)))
 
     def fc2d_coeffs_static(self, n_f, ext, fhat, stream=None):
