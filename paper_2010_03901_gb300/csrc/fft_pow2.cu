@@ -270,6 +270,84 @@ __device__ __forceinline__ void block_fft(typename Cx<T>::type* buf, int t, bool
   }
 }
 
+// All stages but the last one (the stages of block_fft with NS * R < N).
+template <typename T, int LOGN, int E, int NS = 1>
+__device__ __forceinline__ void block_fft_head(typename Cx<T>::type* buf, int t, bool active,
+                                               const typename Cx<T>::type* __restrict__ tw,
+                                               int tws) {
+  constexpr int N = 1 << LOGN;
+  constexpr int R = (N / NS >= E) ? E : N / NS;
+  if constexpr (NS * R < N) {
+    stage<T, LOGN, E, R, NS>(buf, t, active, tw, tws);
+    block_fft_head<T, LOGN, E, NS * R>(buf, t, active, tw, tws);
+  }
+}
+
+// Sub-transform length NS of the last stage of block_fft.
+template <int LOGN, int E> __host__ __device__ constexpr int last_ns() {
+  int ns = 1;
+  while (true) {
+    const int R = ((1 << LOGN) / ns >= E) ? E : (1 << LOGN) / ns;
+    if (ns * R == (1 << LOGN)) return ns;
+    ns *= R;
+  }
+}
+
+// The real row's spectrum from the complex transform Z of its pairs (as
+// even_odd_split), with the last Stockham stage done in registers: thread t takes the
+// butterflies j = t and j = NS - t (thread 0: 0 and NS/2), whose outputs are Z_k,
+// k = j + NS r, and their partners Z_{NH-k}, so the split needs no exchange.  Needs
+// NS = 2 NT (true for nx/2 = 2048 with E = 16 or 8).  buf holds the input of the last
+// stage; X_k, k = 0..NH, go to out.
+template <typename T, int LOGN, int E>
+__device__ __forceinline__ void last_stage_split(const typename Cx<T>::type* buf, int t,
+                                                 const typename Cx<T>::type* __restrict__ tw,
+                                                 const typename Cx<T>::type* __restrict__ rtw,
+                                                 typename Cx<T>::type* __restrict__ out) {
+  using C = typename Cx<T>::type;
+  constexpr int N = 1 << LOGN, NS = last_ns<LOGN, E>(), R = N / NS;
+  constexpr int OFF = stage_off(N, E, NS);
+  static_assert(NS == 2 * (N / E), "last_stage_split: NS must be twice the thread count");
+  const int j1 = t, j2 = t ? NS - t : NS / 2;
+  C a[R], b[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    a[r] = buf[pad<T>(j1 + r * NS)];
+    b[r] = buf[pad<T>(j2 + r * NS)];
+  }
+#pragma unroll
+  for (int r = 1; r < R; ++r) {
+    a[r] = mul(a[r], __ldg(tw + OFF + r * NS + j1));
+    b[r] = mul(b[r], __ldg(tw + OFF + r * NS + j2));
+  }
+  dft<T, C, R>(a);
+  dft<T, C, R>(b);
+  // X_ks and X_kl (kl = NH - ks) from zk = Z_ks and zl = Z_kl
+  auto put = [&](int ks, int kl, C zk, C zl) {
+    zl.y = -zl.y;
+    const C e = {(T)0.5 * (zk.x + zl.x), (T)0.5 * (zk.y + zl.y)};
+    const C o = {(T)0.5 * (zk.x - zl.x), (T)0.5 * (zk.y - zl.y)};
+    const C wo = mul(__ldg(rtw + ks), o);
+    out[ks] = C{e.x + wo.y, e.y - wo.x};
+    if (ks != kl) out[kl] = C{e.x - wo.y, -e.y - wo.x};
+  };
+  if (t) {
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int k = j1 + r * NS;  // partner N - k = j2 + (R - 1 - r) NS
+      if (r < R / 2) put(k, N - k, a[r], b[R - 1 - r]);
+      else put(N - k, k, b[R - 1 - r], a[r]);
+    }
+  } else {
+    put(0, N, a[0], a[0]);
+#pragma unroll
+    for (int r = 1; r < R / 2; ++r) put(r * NS, N - r * NS, a[r], a[R - r]);
+    put(N / 2, N / 2, a[R / 2], a[R / 2]);
+#pragma unroll
+    for (int r = 0; r < R / 2; ++r) put(NS / 2 + r * NS, N - NS / 2 - r * NS, b[r], b[R - 1 - r]);
+  }
+}
+
 // lanes served by one shared-memory wavefront for complex values of type T
 template <typename T> __host__ __device__ constexpr int col_lanes() { return sizeof(T) == 4 ? 16 : 8; }
 
@@ -465,9 +543,16 @@ k_fft_rows_p2(FftArgs fa, RowArgs ra, int mode, const T* __restrict__ ext,
   const int j = blockIdx.x, f = blockIdx.y, t = threadIdx.x;
   assemble_row<T, TV>(ra, mode, NH, j, f, ext, f_grid, vals, buf);
   const C* tw = reinterpret_cast<const C*>(fa.tsx);
-  block_fft<T, LOGNH, E>(buf, t, t < NT, tw, 1);
-  even_odd_split<T>(buf, NH, reinterpret_cast<const C*>(fa.rtw),
-                    inter + ((size_t)f * fa.ny + j) * fa.pitch);
+  C* out = inter + ((size_t)f * fa.ny + j) * fa.pitch;
+  // FP32: the last stage and the split in registers (for FP64, bound by its FP64 pipe,
+  // the extra registers cost more than the saved shared-memory passes)
+  if constexpr (sizeof(T) == 4 && NH / E >= 32 && last_ns<LOGNH, E>() == 2 * (NH / E)) {
+    block_fft_head<T, LOGNH, E>(buf, t, true, tw, 1);
+    last_stage_split<T, LOGNH, E>(buf, t, tw, reinterpret_cast<const C*>(fa.rtw), out);
+  } else {
+    block_fft<T, LOGNH, E>(buf, t, t < NT, tw, 1);
+    even_odd_split<T>(buf, NH, reinterpret_cast<const C*>(fa.rtw), out);
+  }
 }
 
 // rows of NH = 64 N2 complex pairs (N2 = 3, 5, 6, 10, 12: the non-power-of-two row
