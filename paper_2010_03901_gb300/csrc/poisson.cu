@@ -52,7 +52,9 @@ struct PoissonState {
   double* dnodes = nullptr;         // device copy
   // per-solve workspace
   double *V = nullptr, *w = nullptr, *h = nullptr, *g = nullptr, *phi = nullptr;
-  double *ghat = nullptr, *phiR = nullptr, *ab = nullptr, *abR = nullptr, *c00 = nullptr;
+  double *ghat = nullptr, *phiR = nullptr, *c00 = nullptr;
+  float4 *ab = nullptr, *abR = nullptr;        // double-float node coefficients [Nb], [R Nb]
+  float4 *posB = nullptr, *posR = nullptr;     // nodes in grid units [Nb][2], [R Nb][2]
   std::vector<double> xy_host;  // node coordinates [Nb][2]
   int last_iters = 0;
   double last_resid = 0;
@@ -274,85 +276,165 @@ __global__ void k_density_refine(int Nb, int NR, const double2* ghat, const doub
 }
 
 // node coefficients of the trapezoidal sum: a_k = y'_k phi_k / N, b_k = x'_k phi_k / N
+// ------------------------------------------------------------------------- //
+// Double-layer sums in double-float arithmetic on the FP32 units.  A value is the
+// unevaluated sum hi + lo of two floats (about 48 significant bits), built from Knuth's
+// TwoSum, the FMA form of Dekker's TwoProduct and the sums and products of Dekker
+// (1971).  The narrow FP64 pipe would need ~12 operations per (point, node) term.
+// Coordinates are in grid units: a grid point is an exact integer pair, a node or an
+// off-grid point an integer cell index plus a double-float fraction, so every
+// coordinate difference is an integer minus a fraction, accurate to ~2^-48 of a cell.
+// With d' = d/h, r2' = r2/h^2 the term (a dx - b dy)/r2 = (a dx' - b dy')/(h r2').
+// ------------------------------------------------------------------------- //
+struct dfl {
+  float hi, lo;
+};
+__device__ __forceinline__ dfl two_sum(float a, float b) {
+  const float s = a + b, bb = s - a;
+  return {s, (a - (s - bb)) + (b - bb)};
+}
+__device__ __forceinline__ dfl fast_two_sum(float a, float b) {  // |a| >= |b|
+  const float s = a + b;
+  return {s, b - (s - a)};
+}
+__device__ __forceinline__ dfl df_add(dfl x, dfl y) {
+  dfl s = two_sum(x.hi, y.hi);
+  const dfl t = two_sum(x.lo, y.lo);
+  s = fast_two_sum(s.hi, s.lo + t.hi);
+  return fast_two_sum(s.hi, s.lo + t.lo);
+}
+__device__ __forceinline__ dfl df_mul(dfl x, dfl y) {
+  const float p = x.hi * y.hi;
+  float e = fmaf(x.hi, y.hi, -p);
+  e = fmaf(x.hi, y.lo, e);
+  e = fmaf(x.lo, y.hi, e);
+  return fast_two_sum(p, e);
+}
+// integer n minus the fraction (fh, fl)
+__device__ __forceinline__ dfl int_minus(float n, float fh, float fl) {
+  const dfl s = two_sum(n, -fh);
+  return fast_two_sum(s.hi, s.lo - fl);
+}
+// (a dx - b dy) / (dx^2 + dy^2) with a = (ah, al), b = (bh, bl)
+__device__ __forceinline__ dfl dl_term(dfl dx, dfl dy, float ah, float al, float bh, float bl) {
+  const dfl xx = df_mul(dx, dx), yy = df_mul(dy, dy);
+  const dfl r2 = df_add(xx, yy);
+  const dfl num = df_add(df_mul({ah, al}, dx), df_mul({-bh, -bl}, dy));
+  // 1/r2: the correctly rounded float reciprocal and one Newton step (relative error
+  // about the square of the seed's, 2^-46)
+  const float y0 = __frcp_rn(r2.hi);
+  float t = fmaf(-r2.hi, y0, 1.0f);
+  t = fmaf(-r2.lo, y0, t);
+  return df_mul(num, fast_two_sum(y0, y0 * t));
+}
+__device__ __forceinline__ void split_df(double v, float& hi, float& lo) {
+  hi = (float)v;
+  lo = (float)(v - (double)hi);
+}
+
+// per-solve node coefficients (y' phi/N, x' phi/N) as double-float pairs (ah, al, bh, bl)
 __global__ void k_node_coef(int N, const double* x1, const double* y1, const double* phi,
-                            double2* ab) {
+                            float4* ab) {
   int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k < N) ab[k] = double2{y1[k] * phi[k] / N, x1[k] * phi[k] / N};
+  if (k >= N) return;
+  float4 c;
+  split_df(y1[k] * phi[k] / N, c.x, c.y);
+  split_df(x1[k] * phi[k] / N, c.z, c.w);
+  ab[k] = c;
 }
 
 // v at listed grid points by the trapezoidal sum over N nodes; u = u_p + v there.
-// 1/r2 for the double-layer sums without an FP64 division (a long sequence on the narrow
-// FP64 pipe): the correctly rounded FP32 reciprocal as seed, then one Newton step for
-// 1/a, y1 = y0 + y0 (1 - a y0), whose relative error is the square of the seed's
-// (about 2^-46 here), far below the 1e-11 accuracy of the solver.  r2 > 0.
-__device__ __forceinline__ double rcp_newton(double r2) {
-  const double y0 = (double)__frcp_rn((float)r2);
-  return fma(y0, fma(-r2, y0, 1.0), y0);
-}
-
-__global__ void __launch_bounds__(256) k_dlp(int n_pts, const int32_t* lin, int nx, double a0,
-                                             double b0, double h, int N, const double* x,
-                                             const double* y, const double2* ab, double* u) {
-  __shared__ double sx[256], sy[256];
-  __shared__ double2 sab[256];
+// pos: per node (ix, iy, fx_hi, fx_lo), (fy_hi, fy_lo, -, -) in grid units.
+__global__ void __launch_bounds__(256) k_dlp(int n_pts, const int32_t* lin, int nx, double inv_h,
+                                             int N, const float4* pos, const float4* ab,
+                                             double* u) {
+  __shared__ float4 s0[256], s1[256], sc[256];
   int n = blockIdx.x * blockDim.x + threadIdx.x;
   bool act = n < n_pts;
   int l = act ? lin[n] : 0;
-  double px = a0 + h * double(l % nx), py = b0 + h * double(l / nx);
-  double acc = 0.0;
+  const float pi = (float)(l % nx), pj = (float)(l / nx);
+  dfl acc = {0.f, 0.f};
   for (int t0 = 0; t0 < N; t0 += 256) {
     __syncthreads();
     if (t0 + (int)threadIdx.x < N) {
-      sx[threadIdx.x] = x[t0 + threadIdx.x];
-      sy[threadIdx.x] = y[t0 + threadIdx.x];
-      sab[threadIdx.x] = ab[t0 + threadIdx.x];
+      s0[threadIdx.x] = pos[2 * (t0 + threadIdx.x)];
+      s1[threadIdx.x] = pos[2 * (t0 + threadIdx.x) + 1];
+      sc[threadIdx.x] = ab[t0 + threadIdx.x];
     }
     __syncthreads();
-    int cnt = min(256, N - t0);
+    const int cnt = min(256, N - t0);
     for (int k = 0; k < cnt; ++k) {
-      double dx = px - sx[k], dy = py - sy[k];
-      double r2 = fma(dx, dx, dy * dy);
-      double num = fma(sab[k].x, dx, -sab[k].y * dy);
-      acc = fma(num, rcp_newton(r2), acc);
+      const float4 a = s0[k], b = s1[k], c = sc[k];
+      const dfl dx = int_minus(pi - a.x, a.z, a.w), dy = int_minus(pj - a.y, b.x, b.y);
+      const dfl term = dl_term(dx, dy, c.x, c.y, c.z, c.w);
+      const dfl s = two_sum(acc.hi, term.hi);
+      acc = fast_two_sum(s.hi, s.lo + (acc.lo + term.lo));
     }
   }
-  if (act) u[l] += acc;
+  if (act) u[l] += ((double)acc.hi + (double)acc.lo) * inv_h;
 }
 
-// close points: one block per point; 7 refined sums along the normal, the boundary
-// value by trigonometric interpolation of g - u_p, and the Lagrange combination.
+// close points: one block per point; the MP - 1 refined sums along the normal (each
+// thread takes a node once for all of them), the boundary value by trigonometric
+// interpolation of g - u_p, and the Lagrange combination.
+template <int KMP>  // compile-time M_P (0: any M_P <= kMaxM)
 __global__ void __launch_bounds__(256) k_dlp_close(int n_close, const int32_t* lin,
                                                    const double* cgeo, const double* cw,
                                                    const double* nodes, int MP, int NR,
-                                                   const double* rx, const double* ry,
-                                                   const double2* abR, int Nb,
-                                                   const double2* ghat_g, double* u) {
+                                                   double a0, double b0, double h,
+                                                   const float4* posR, const float4* abR,
+                                                   int Nb, const double2* ghat_g, double* u) {
+  constexpr int NP = KMP > 0 ? KMP : kMaxM;
+  if (KMP > 0) MP = KMP;
   __shared__ double red[256];
+  __shared__ float pt[NP][6];  // per point: ix, iy, fx_hi, fx_lo, fy_hi, fy_lo
   const int n = blockIdx.x;
   if (n >= n_close) return;
   const double fx = cgeo[5 * n], fy = cgeo[5 * n + 1], nxv = cgeo[5 * n + 2],
                nyv = cgeo[5 * n + 3], th = cgeo[5 * n + 4];
-  double vals[kMaxM];
-  for (int j = 1; j < MP; ++j) {
-    const double px = fx - nodes[j] * nxv, py = fy - nodes[j] * nyv;
-    double acc = 0.0;
-    for (int k = threadIdx.x; k < NR; k += blockDim.x) {
-      double dx = px - rx[k], dy = py - ry[k];
-      double r2 = fma(dx, dx, dy * dy);
-      acc = fma(fma(abR[k].x, dx, -abR[k].y * dy), rcp_newton(r2), acc);
+  const double inv_h = 1.0 / h;
+  if (threadIdx.x < MP - 1) {
+    const int j = threadIdx.x + 1;
+    const double ux = (fx - nodes[j] * nxv - a0) * inv_h, uy = (fy - nodes[j] * nyv - b0) * inv_h;
+    const double ix = floor(ux), iy = floor(uy);
+    pt[j][0] = (float)ix;
+    pt[j][1] = (float)iy;
+    split_df(ux - ix, pt[j][2], pt[j][3]);
+    split_df(uy - iy, pt[j][4], pt[j][5]);
+  }
+  __syncthreads();
+  dfl acc[NP];
+#pragma unroll
+  for (int j = 0; j < NP; ++j) acc[j] = {0.f, 0.f};
+  for (int k = threadIdx.x; k < NR; k += blockDim.x) {
+    const float4 a = posR[2 * k], b = posR[2 * k + 1], c = abR[k];
+#pragma unroll
+    for (int j = 1; j < NP; ++j) {
+      if (KMP == 0 && j >= MP) break;
+      // (point - node) = (i_p - i_n) + (f_p - f_n)
+      const dfl dx = df_add(int_minus(pt[j][0] - a.x, a.z, a.w), {pt[j][2], pt[j][3]});
+      const dfl dy = df_add(int_minus(pt[j][1] - a.y, b.x, b.y), {pt[j][4], pt[j][5]});
+      const dfl term = dl_term(dx, dy, c.x, c.y, c.z, c.w);
+      const dfl s = two_sum(acc[j].hi, term.hi);
+      acc[j] = fast_two_sum(s.hi, s.lo + (acc[j].lo + term.lo));
     }
-    red[threadIdx.x] = acc;
+  }
+  double vals[NP];
+#pragma unroll
+  for (int j = 1; j < NP; ++j) {
+    if (KMP == 0 && j >= MP) break;
+    red[threadIdx.x] = (double)acc[j].hi + (double)acc[j].lo;
     __syncthreads();
     for (int o = blockDim.x / 2; o; o >>= 1) {
       if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
       __syncthreads();
     }
-    vals[j] = red[0];
+    vals[j] = red[0] * inv_h;
     __syncthreads();
   }
   // boundary value: sum_k c_k e^{i k theta} over the Hermitian half (Nyquist halved)
   {
-    double acc = 0.0;
+    double acc0 = 0.0;
     const int half = Nb / 2;
     // e^{i k theta} for k = tid, tid + blockDim, ...: one sincos each for the first k and
     // the stride, then complex products (at most a few steps: Nb/2 <= a few blockDim)
@@ -362,12 +444,12 @@ __global__ void __launch_bounds__(256) k_dlp_close(int n_close, const int32_t* l
     for (int k = threadIdx.x; k <= half; k += blockDim.x) {
       double re = ghat_g[k].x * c - ghat_g[k].y * s;
       double fac = (k == 0 || 2 * k == Nb) ? 1.0 : 2.0;
-      acc = fma(fac, re, acc);
+      acc0 = fma(fac, re, acc0);
       const double c2 = c * cs - s * ss, s2 = s * cs + c * ss;
       c = c2;
       s = s2;
     }
-    red[threadIdx.x] = acc;
+    red[threadIdx.x] = acc0;
     __syncthreads();
     for (int o = blockDim.x / 2; o; o >>= 1) {
       if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
@@ -377,7 +459,11 @@ __global__ void __launch_bounds__(256) k_dlp_close(int n_close, const int32_t* l
   }
   if (threadIdx.x == 0) {
     double v = 0.0;
-    for (int j = 0; j < MP; ++j) v = fma(cw[(size_t)n * MP + j], vals[j], v);
+#pragma unroll
+    for (int j = 0; j < NP; ++j) {
+      if (KMP == 0 && j >= MP) break;
+      v = fma(cw[(size_t)n * MP + j], vals[j], v);
+    }
     u[lin[n]] += v;
   }
 }
@@ -415,6 +501,21 @@ static fc2d_status alloc(PoissonState* P, T** dst, size_t n) {
     return set_error(FC2D_ERR_NOMEM, "Poisson setup: cudaMalloc failed");
   P->allocs.push_back(*dst);
   return FC2D_OK;
+}
+
+// Node positions in grid units for the double-float sums: per node (ix, iy, fx_hi,
+// fx_lo), (fy_hi, fy_lo, 0, 0), with (x - a0)/h = ix + fx, 0 <= fx < 1 (the same in y).
+static std::vector<float4> grid_units(const std::vector<double>& x, const std::vector<double>& y,
+                                      double a0, double b0, double h) {
+  std::vector<float4> out(2 * x.size());
+  for (size_t k = 0; k < x.size(); ++k) {
+    const double ux = (x[k] - a0) / h, uy = (y[k] - b0) / h;
+    const double ix = std::floor(ux), iy = std::floor(uy), fx = ux - ix, fy = uy - iy;
+    const float fxh = (float)fx, fyh = (float)fy;
+    out[2 * k] = make_float4((float)ix, (float)iy, fxh, (float)(fx - (double)fxh));
+    out[2 * k + 1] = make_float4(fyh, (float)(fy - (double)fyh), 0.f, 0.f);
+  }
+  return out;
 }
 
 static void lagr(const double* nodes, int n, double t, double* w) {
@@ -585,15 +686,17 @@ fc2d_status poisson_setup(fc2d_plan_s* p, int Nb) {
       (st = up(P, &P->uwx, uwx)) || (st = up(P, &P->uwy, uwy)) ||
       (st = up(P, &P->far_lin, far)) || (st = up(P, &P->mid_lin, mid)) ||
       (st = up(P, &P->close_lin, close)) || (st = up(P, &P->close_geo, cgeo)) ||
-      (st = up(P, &P->close_w, cw)) || (st = up(P, &P->dnodes, P->close_nodes)))
+      (st = up(P, &P->close_w, cw)) || (st = up(P, &P->dnodes, P->close_nodes)) ||
+      (st = up(P, &P->posB, grid_units(x, y, a0, b0, h))) ||
+      (st = up(P, &P->posR, grid_units(rx, ry, a0, b0, h))))
     return fail(st);
   double* ddiag = nullptr;
   if ((st = up(P, &ddiag, diag)) || (st = alloc(P, &P->A, (size_t)Nb * Nb)) ||
       (st = alloc(P, &P->V, (size_t)(kGmresMax + 1) * Nb)) || (st = alloc(P, &P->w, Nb)) ||
       (st = alloc(P, &P->h, kGmresMax + 2)) || (st = alloc(P, &P->g, Nb)) ||
       (st = alloc(P, &P->phi, Nb)) || (st = alloc(P, &P->ghat, 2 * (Nb / 2 + 1))) ||
-      (st = alloc(P, &P->phiR, NR)) || (st = alloc(P, &P->ab, 2 * (size_t)Nb)) ||
-      (st = alloc(P, &P->abR, 2 * (size_t)NR)) || (st = alloc(P, &P->c00, 1024)))
+      (st = alloc(P, &P->phiR, NR)) || (st = alloc(P, &P->ab, (size_t)Nb)) ||
+      (st = alloc(P, &P->abR, (size_t)NR)) || (st = alloc(P, &P->c00, 1024)))
     return fail(st);
   k_bie_matrix<<<dim3((Nb + 255) / 256, Nb), 256>>>(Nb, P->bx, P->by, P->bx1, P->by1, ddiag,
                                                     P->A);
@@ -734,27 +837,28 @@ fc2d_status poisson_solve(fc2d_plan_s* p, int n_f, const double* fg, const doubl
                                                                      (double2*)P->ghat);
     k_density_refine<<<(unsigned)((NR + 255) / 256), 256, 0, s>>>(Nb, NR, (const double2*)P->ghat,
                                                                  (const double2*)P->twr, P->phiR);
-    k_node_coef<<<gb, 256, 0, s>>>(Nb, P->bx1, P->by1, P->phi, (double2*)P->ab);
+    k_node_coef<<<gb, 256, 0, s>>>(Nb, P->bx1, P->by1, P->phi, P->ab);
     k_node_coef<<<(unsigned)((NR + 255) / 256), 256, 0, s>>>(NR, P->rx1, P->ry1, P->phiR,
-                                                            (double2*)P->abR);
+                                                            P->abR);
     {
       ProfScope ps(p, "dlp_far", s);
       if (P->n_far)
         k_dlp<<<(unsigned)((P->n_far + 255) / 256), 256, 0, s>>>(
-            (int)P->n_far, P->far_lin, nx, a0, b0, h, Nb, P->bx, P->by, (const double2*)P->ab, uf);
+            (int)P->n_far, P->far_lin, nx, 1.0 / h, Nb, P->posB, P->ab, uf);
     }
     {
       ProfScope ps(p, "dlp_near", s);
       if (P->n_mid)
         k_dlp<<<(unsigned)((P->n_mid + 255) / 256), 256, 0, s>>>(
-            (int)P->n_mid, P->mid_lin, nx, a0, b0, h, NR, P->rx, P->ry, (const double2*)P->abR, uf);
+            (int)P->n_mid, P->mid_lin, nx, 1.0 / h, NR, P->posR, P->abR, uf);
       if (P->n_close) {
         // boundary values g - u_p: reuse ghat for their coefficients
         k_density_dft<<<(unsigned)((Nb / 2 + 1 + 127) / 128), 128, 0, s>>>(
             Nb, P->g, (const double2*)P->twb, (double2*)P->ghat);
-        k_dlp_close<<<(unsigned)P->n_close, 256, 0, s>>>(
-            (int)P->n_close, P->close_lin, P->close_geo, P->close_w, P->dnodes, MP, NR, P->rx,
-            P->ry, (const double2*)P->abR, Nb, (const double2*)P->ghat, uf);
+        auto kc = MP == 8 ? k_dlp_close<8> : k_dlp_close<0>;
+        kc<<<(unsigned)P->n_close, 256, 0, s>>>(
+            (int)P->n_close, P->close_lin, P->close_geo, P->close_w, P->dnodes, MP, NR, a0, b0,
+            h, P->posR, P->abR, Nb, (const double2*)P->ghat, uf);
       }
     }
     k_zero_outside<<<ny, 256, 0, s>>>(nx, p->dev.row_iv_off, p->dev.row_iv, uf);
