@@ -201,7 +201,8 @@ fc2d_status fc2d_coeffs_static(fc2d_plan_t plan, int n_f, const void* ext_dev, v
                                void* stream);
 
 /* Poisson problem Delta u = f in the domain, u = g on the curve (Section 4.1,
- * eqs. (4.1)-(4.6)), FP64 plans.  fc2d_poisson_plan builds the boundary-integral tables
+ * eqs. (4.1)-(4.6)), FP64 plans (FP64 data and arithmetic, except the double-layer sums
+ * on the grid: double-float, about 48 bits).  fc2d_poisson_plan builds the boundary-integral tables
  * once (synchronous): n_b equispaced parameters 2 pi k/n_b (n_b <= 0 means nx, as in
  * Section 4.1.1), the Nystrom matrix of the double-layer equation -phi/2 + K phi = g_hom,
  * the boundary interpolation stencils of u_p, and the near-boundary point lists.

@@ -1,4 +1,5 @@
-// 2D-FC Poisson solver (Section 4.1, eqs. (4.1)-(4.6)), FP64.
+// 2D-FC Poisson solver (Section 4.1, eqs. (4.1)-(4.6)), FP64 data; the double-layer
+// sums on the grid in double-float arithmetic (about 48 bits, see below).
 //
 //   u = u_p + v.  u_p: the spectrum of the extension of f times the inverse Laplacian
 //   symbol -1/((2 pi l/L_x)^2 + (2 pi m/L_y)^2) (0 at the origin), inverse DFT, plus
