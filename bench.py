@@ -515,6 +515,48 @@ def poisson_kite_oscillatory(fc2d, torch, dev, h=1.25e-3, solves=3):
             "gmres": plan.fc2d_poisson_info()}
 
 
+def ff_interior_kite2048(fc2d, torch, dev, steps=20):
+    """One Fourier Forwarding large step, the interior propagator U_FC (Section 4.2):
+    both extensions, both DFTs, the modal advance, both inverse DFTs.  The kite at 2048^2
+    with d = 4 (the paper's FF order), c = 1, Delta T = n_c h with n_c = 8; u = 32
+    Gaussians of width 0.05 centred at least 0.3 inside the curve (seed 5), u_t = 0;
+    FP64.  Calls back to back on the launching stream between two events."""
+    w = W.workload("kite2048", d=4, M=7)
+    g, p = w.grid, w.params
+    plan = fc2d.fc2d_plan(w.boundary.arrays(), (g.a0, g.b0, g.h, g.nx, g.ny),
+                          dict(d=4, M=7, B=p.B, k1=p.k1))
+    xy = plan.fc2d_boundary_points()
+    f0 = W.gaussian_sum(w.boundary, 32, 5, wmin=0.05, wmax=0.05, margin=0.3)
+    u0 = torch.tensor(W.grid_values(w, f0)[None], device=dev)
+    ub = torch.tensor(f0(xy[:, 0], xy[:, 1])[None], device=dev)
+    ut0, utb = torch.zeros_like(u0), torch.zeros_like(ub)
+    u1, ut1 = torch.empty_like(u0), torch.empty_like(u0)
+    dT = 8 * g.h
+    stream = torch.cuda.current_stream()
+    for _ in range(3):
+        plan.fc2d_wave_interior(1, 1.0, dT, u0, ub, ut0, utb, u1, ut1, stream)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(steps):
+        plan.fc2d_wave_interior(1, 1.0, dT, u0, ub, ut0, utb, u1, ut1, stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    plan.fc2d_profile(True)
+    plan.fc2d_profile_read()
+    plan.fc2d_wave_interior(1, 1.0, dT, u0, ub, ut0, utb, u1, ut1, stream)
+    torch.cuda.synchronize()
+    plan.fc2d_profile(False)
+    prof = plan.fc2d_profile_read()
+    plan.fc2d_sync_status(stream)
+    return {"workload": f"kite 2048^2 (a=0.65, b=1.5), d = 4, c = 1, Delta T = 8 h = {dT:.4g}, "
+                        "u = 32 Gaussians (w = 0.05, centres >= 0.3 inside), u_t = 0",
+            "ms_per_large_step": ms, "large_steps_per_s": 1e3 / ms,
+            "value": g.nx * g.ny / (ms * 1e-3), "unit": UNIT,
+            "kernels_ms": {k: v[1] / v[0] for k, v in prof.items()}}
+
+
 def stars8_batched(fc2d, torch, dev, replays=10):
     """Eight stars (grids 256^2..2048^2 by concavity), 32 trigonometric sums per domain,
     fc2d_extend_coeffs per domain, the 8 calls captured in one CUDA graph and replayed;
@@ -666,6 +708,7 @@ def run_gpu(args):
     if rank == 0 and world == 1 and not args.no_extra:
         line["poisson_star1024"] = poisson_star1024(fc2d, torch, dev)
         line["poisson_kite_d10"] = poisson_kite_oscillatory(fc2d, torch, dev)
+        line["ff_interior_kite2048"] = ff_interior_kite2048(fc2d, torch, dev)
         line["stars8_batched"] = stars8_batched(fc2d, torch, dev)
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -683,7 +726,7 @@ def main(argv=None):
                     help="both: mixed is the headline, FP64 reported beside it")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-extra", action="store_true",
-                    help="skip the Poisson and batched-star lines")
+                    help="skip the Poisson, Fourier Forwarding and batched-star lines")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

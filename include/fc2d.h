@@ -228,7 +228,8 @@ fc2d_status fc2d_poisson_info(fc2d_plan_t plan, int* gmres_iters, double* gmres_
 
 /* Fourier Forwarding interior propagator (Section 4.2, eqs. (4.8)-(4.12)), FP64 plans.
  * For n_f pairs of initial data (u, u_t), given like f in fc2d_extend (grid values
- * [n_f][ny][nx] and boundary data [n_f][n_bdry]): the 2D-FC expansions F and G, the modal
+ * [n_f][ny][nx] and boundary data [n_f][n_bdry], or NULL for interior data only): the
+ * 2D-FC expansions F and G, the modal
  * solutions a = hat f cos(w t) + hat g sin(w t)/w (a_00 = hat f_00 + t hat g_00),
  * w = 2 pi c sqrt((l/L_x)^2 + (m/L_y)^2), and their inverse DFTs.  u_out and ut_out
  * [n_f][ny][nx] receive U_FC(., t) and its time derivative on the whole grid; they are

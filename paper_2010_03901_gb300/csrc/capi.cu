@@ -521,8 +521,11 @@ extern "C" fc2d_status fc2d_wave_interior(fc2d_plan_t p, int n_f, double c, doub
                                           double* u_out, double* ut_out, void* stream) {
   fc2d_status st = check_nf(p, n_f);
   if (st) return st;
-  if (!u0 || !u0_bdry || !ut0 || !ut0_bdry || !u_out || !ut_out)
+  if (!u0 || !ut0 || !u_out || !ut_out)
     return set_error(FC2D_ERR_ARG, "fc2d_wave_interior: null pointer");
+  if ((st = check_interior(p, u0_bdry, "fc2d_wave_interior")) ||
+      (st = check_interior(p, ut0_bdry, "fc2d_wave_interior")))
+    return st;
   if (!(c > 0) || !(t >= 0)) return set_error(FC2D_ERR_ARG, "fc2d_wave_interior: c > 0, t >= 0");
   if (p->prm.precision != FC2D_FP64)
     return set_error(FC2D_ERR_UNSUPPORTED, "fc2d_wave_interior: FP64 plans only");
