@@ -179,13 +179,16 @@ fc2d_status strip_values(fc2d_plan_s* p, int n_f, const double* fg, const double
                          const Layout& L, cudaStream_t s, bool compact = false) {
   const bool f64 = p->prm.precision == FC2D_FP64;
   void* F = ws(p, L.oF);
-  if (!f64 && p->dev.own_off) {
-    // mixed form, M = 8: blend and interpolation in one kernel, F stays on chip
+  if (!f64 && p->dev.own[0].off) {
+    // mixed form, M = 8: blend and interpolation in one kernel, F stays on chip.  One CTA
+    // per SM when the call's CTAs fit in about one wave, else the fewest CTAs.
+    const auto& o = (p->dev.own[1].n && (int64_t)n_f * p->dev.own[0].n > 3 * (int64_t)p->n_sm / 2)
+                        ? p->dev.own[1]
+                        : p->dev.own[0];
     ProfScope ps(p, "gather_blend_interp_tc", s);
     return launch_gather_interp_tc(gather_args(p, fg, fb, nullptr, nullptr, nullptr, compact), n_f,
-                                   ws_ldF(p), p->dev.Ar_hi, p->dev.Ar_lo, p->dev.own_off,
-                                   p->dev.own_k, p->dev.own_pack, p->dev.own_w,
-                                   p->dev.own_start, p->dev.n_own,
+                                   ws_ldF(p), p->dev.Ar_hi, p->dev.Ar_lo, o.off, o.k, o.pack,
+                                   o.w, o.start, o.n,
                                    (int)p->strip_lin.size(),
                                    reinterpret_cast<float*>(ws(p, L.ovals)), p->dev.status, s);
   }

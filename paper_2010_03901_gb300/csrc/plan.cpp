@@ -430,28 +430,17 @@ static std::vector<int32_t> partition_owners(const std::vector<int64_t>& cnt, in
 // Strip points grouped by the blend CTA that interpolates them (mixed form, M = 8):
 // CTA c of a function computes the kTcComputed normals from start_c on (mod B) and owns
 // the strip points whose first normal pb lies in [start_c, start_{c+1}), at most
-// kTcOwned normals, so that pb .. pb + M - 1 are among its normals.  One CTA per SM
-// (at least ceil(B / kTcOwned)), the ranges balanced by their numbers of points.  The
-// weights are reordered to match.
-static fc2d_status owner_tables(fc2d_plan_s* p, int ns, int M) {
-  const int B = p->prm.B;
-  int n_sm = 0;
-  if (cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, p->device) != cudaSuccess)
-    n_sm = 0;
-  const int n_cta = std::max((B + kTcOwned - 1) / kTcOwned, n_sm);
-  std::vector<int32_t> pb(ns), sb(ns);
-  std::vector<float> w((size_t)2 * M * ns);
-  if (cudaMemcpy(pb.data(), p->dev.s_pb, (size_t)ns * 4, cudaMemcpyDeviceToHost) != cudaSuccess ||
-      cudaMemcpy(sb.data(), p->dev.s_sb, (size_t)ns * 4, cudaMemcpyDeviceToHost) != cudaSuccess ||
-      cudaMemcpy(w.data(), p->dev.s_w, w.size() * 4, cudaMemcpyDeviceToHost) != cudaSuccess)
-    return set_error(FC2D_ERR_CUDA, "reading the interpolation tables back failed");
-  std::vector<int64_t> cnt(B, 0);
-  for (int k = 0; k < ns; ++k) {
-    pb[k] = ((pb[k] % B) + B) % B;  // the first normal is stored unreduced near theta = 0
-    if (sb[k] < 0 || sb[k] > 255)
-      return set_error(FC2D_ERR_GEOMETRY, "interpolation node index out of range");
-    ++cnt[pb[k]];
-  }
+// kTcOwned normals, so that pb .. pb + M - 1 are among its normals.  Two partitions:
+// one CTA per SM where B allows ~48 normals each (a call of few functions then fills
+// the SMs once, with the ranges balanced by their numbers of points), and the fewest
+// CTAs, ceil(B / kTcOwned) (for calls of many functions, whose CTAs fill the SMs anyway
+// and where extra CTAs only repeat gathers).  Within a CTA the points are ordered by
+// first normal, then fine node; the weights are reordered to match.
+static fc2d_status owner_set(fc2d_plan_s* p, const std::vector<int32_t>& pb,
+                             const std::vector<int32_t>& sb, const std::vector<float>& w,
+                             const std::vector<int64_t>& cnt, int n_cta, int M,
+                             DeviceTables::Owners& out) {
+  const int B = p->prm.B, ns = (int)pb.size();
   const std::vector<int32_t> start = partition_owners(cnt, kTcOwned, n_cta);
   const int n_own = (int)start.size() - 1;
   std::vector<int32_t> cta_of(B);
@@ -484,13 +473,39 @@ static fc2d_status owner_tables(fc2d_plan_s* p, int ns, int M) {
   std::vector<float> wp(w.size());
   for (int idx = 0; idx < ns; ++idx)
     for (int b = 0; b < 2 * M; ++b) wp[(size_t)b * ns + idx] = w[(size_t)b * ns + perm[idx]];
-  p->dev.n_own = n_own;
+  out.n = n_own;
   fc2d_status st;
-  if ((st = upload(&p->dev.own_off, off)) || (st = upload(&p->dev.own_k, perm)) ||
-      (st = upload(&p->dev.own_pack, pack)) || (st = upload(&p->dev.own_w, wp)) ||
-      (st = upload(&p->dev.own_start, start)))
+  if ((st = upload(&out.off, off)) || (st = upload(&out.k, perm)) ||
+      (st = upload(&out.pack, pack)) || (st = upload(&out.w, wp)) ||
+      (st = upload(&out.start, start)))
     return st;
   return FC2D_OK;
+}
+
+static fc2d_status owner_tables(fc2d_plan_s* p, int ns, int M) {
+  const int B = p->prm.B;
+  int n_sm = 0;
+  if (cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, p->device) != cudaSuccess)
+    n_sm = 0;
+  p->n_sm = n_sm;
+  const int n_min = (B + kTcOwned - 1) / kTcOwned;
+  const int n_wide = std::max(n_min, std::min(n_sm, B / 48));
+  std::vector<int32_t> pb(ns), sb(ns);
+  std::vector<float> w((size_t)2 * M * ns);
+  if (cudaMemcpy(pb.data(), p->dev.s_pb, (size_t)ns * 4, cudaMemcpyDeviceToHost) != cudaSuccess ||
+      cudaMemcpy(sb.data(), p->dev.s_sb, (size_t)ns * 4, cudaMemcpyDeviceToHost) != cudaSuccess ||
+      cudaMemcpy(w.data(), p->dev.s_w, w.size() * 4, cudaMemcpyDeviceToHost) != cudaSuccess)
+    return set_error(FC2D_ERR_CUDA, "reading the interpolation tables back failed");
+  std::vector<int64_t> cnt(B, 0);
+  for (int k = 0; k < ns; ++k) {
+    pb[k] = ((pb[k] % B) + B) % B;  // the first normal is stored unreduced near theta = 0
+    if (sb[k] < 0 || sb[k] > 255)
+      return set_error(FC2D_ERR_GEOMETRY, "interpolation node index out of range");
+    ++cnt[pb[k]];
+  }
+  fc2d_status st = owner_set(p, pb, sb, w, cnt, n_wide, M, p->dev.own[0]);
+  if (!st && n_wide > n_min) st = owner_set(p, pb, sb, w, cnt, n_min, M, p->dev.own[1]);
+  return st;
 }
 
 extern "C" fc2d_status fc2d_plan(const fc2d_boundary* boundary, const fc2d_grid* grid,
@@ -973,8 +988,10 @@ extern "C" void fc2d_destroy(fc2d_plan_t p) {
   poisson_destroy(p);
   void* ptrs[] = {p->dev.Q, p->dev.Ar, p->dev.Ar_hi, p->dev.Ar_lo, p->dev.gidx, p->dev.gw,
                   p->dev.wn, p->dev.s_lin, p->dev.s_theta, p->dev.s_eta, p->dev.s_w,
-                  p->dev.s_pb, p->dev.s_sb, p->dev.own_off, p->dev.own_k,
-                  p->dev.own_pack, p->dev.own_w, p->dev.own_start, p->dev.row_iv_off,
+                  p->dev.s_pb, p->dev.s_sb, p->dev.own[0].off, p->dev.own[0].k,
+                  p->dev.own[0].pack, p->dev.own[0].w, p->dev.own[0].start,
+                  p->dev.own[1].off, p->dev.own[1].k, p->dev.own[1].pack, p->dev.own[1].w,
+                  p->dev.own[1].start, p->dev.row_iv_off,
                   p->dev.row_iv, p->dev.row_strip_off, p->dev.row_iv_coff, p->dev.gidx_c,
                   p->dev.gidx_i, p->dev.gw_i, p->dev.wn_i, p->dev.gidx_ic,
                   p->dev.status, p->fx.tw64, p->fx.tw32,

@@ -57,12 +57,16 @@ struct DeviceTables {
   int32_t* s_pb = nullptr;   // [n_strip] first normal index
   int32_t* s_sb = nullptr;   // [n_strip] first fine index
   // strip points grouped by owning blend CTA (mixed form, M = 8; else null)
-  int32_t* own_off = nullptr;   // [n_own + 1] offsets of each CTA's points
-  int32_t* own_k = nullptr;     // [n_strip] strip index of each grouped point
-  int32_t* own_pack = nullptr;  // [n_strip] (first normal - CTA's first normal) | s << 8
-  float* own_w = nullptr;       // [2M][n_strip] interpolation weights, grouped order
-  int32_t* own_start = nullptr; // [n_own + 1] first normal owned by each CTA, then B
-  int n_own = 0;                // CTAs per function (ownership ranges)
+  // ownership of the strip points by the blend + interpolation CTAs (mixed, M = 8):
+  // own[0] one CTA per SM (balanced ranges), own[1] the fewest CTAs (n = 0: same as 0)
+  struct Owners {
+    int32_t* off = nullptr;    // [n + 1] offsets of each CTA's points
+    int32_t* k = nullptr;      // [n_strip] strip index of each grouped point
+    int32_t* pack = nullptr;   // [n_strip] (first normal - CTA's first normal) | s << 8
+    float* w = nullptr;        // [2M][n_strip] interpolation weights, grouped order
+    int32_t* start = nullptr;  // [n + 1] first normal owned by each CTA, then B
+    int n = 0;                 // CTAs per function (ownership ranges)
+  } own[2];
   // per-row tables
   int32_t* row_iv_off = nullptr;    // [ny+1] offsets into row_iv
   int32_t* row_iv = nullptr;        // pairs (i_lo, i_hi), inclusive
@@ -108,6 +112,7 @@ struct fc2d_plan_s {
   int64_t n_inside = 0;
   int64_t n_bdry = 0;
   bool interior_ok = true;  // every red star has a grid node (interior-only form usable)
+  int n_sm = 0;             // SMs of the plan's device
   fc2d::FftAxis fx, fy;                      // nx/2 (complex) and ny
   std::vector<double> rtw_host;              // exp(-2 pi i k/nx), k <= nx/2 (R2C post-process)
   double* rtw64 = nullptr;
