@@ -46,9 +46,9 @@ FP64_PEAK_TFLOPS = 1.25   # GB300 FP64 (nominal; 152 SMs x 2 DFMA/clk x 2 flop x
 ROT = 3   # rotating input/output buffers of the timed steps
 
 MEASURED_TRAFFIC = {
-    ("mixed", "fft_cols"): 67671808 + 7233536 + 67741440 + 9267456,  # k_cols4k_a + k_cols4k_b
-    ("mixed", "fft_rows_fused"): 70925824 + 19409920,
-    ("mixed", "gather_blend_interp_tc"): 34109696 + 512,
+    ("mixed", "fft_cols"): 67672064 + 7467264 + 67702784 + 8807424,  # k_cols4k_a + k_cols4k_b
+    ("mixed", "fft_rows_fused"): 70923520 + 19281408,
+    ("mixed", "gather_blend_interp_tc"): 34109952 + 0,
     ("fp64", "fft_rows_fused"): 72384768 + 75083008,
     ("fp64", "fft_cols"): 141867520 + 92843264,
     ("fp64", "gather_blend"): 9670144 + 9472,
