@@ -38,6 +38,11 @@ WORKLOAD = "kite4096"
 METRIC = "2D-FC extend+FFT grid-points/sec at 4096^2"
 UNIT = "grid-points/s"
 FP64_PEAK_TFLOPS = 1.25   # GB300 FP64 (nominal; 152 SMs x 2 DFMA/clk x 2 flop x ~2.06 GHz)
+# FP32 issue rate: 152 SMs x 128 FP32 lanes x 2.07 GHz (nominal maximum SM clock)
+FP32_PEAK_GINSTR = 152 * 128 * 2.07
+# FP32 instructions per (point, node) term of the double-float double-layer sums
+# (k_dlp): two coordinate differences 22, the term 82, the accumulation 11
+DLP_INSTR_PER_TERM = 115
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of a kernel scope
 # on this workload, from one ncu capture of the current kernels (cold cache, serialised
@@ -466,10 +471,18 @@ def poisson_star1024(fc2d, torch, dev, solves=3):
     got = out.cpu().numpy()[0]
     inside = got != 0
     err = float(np.abs(got - ue)[inside].max() / np.abs(ue[inside]).max())
+    info = plan.fc2d_poisson_info()
+    kms = {k: v[1] / v[0] for k, v in prof.items()}
+    # the far-field sums: (inside points - near points) x N_b terms, FP32-issue bound
+    terms = (plan.n_inside - info["n_near"]) * len(xy)
+    ach = terms * DLP_INSTR_PER_TERM / (kms["dlp_far"] * 1e-3) / 1e9
+    roof = {"bound": "alu", "kernel": "dlp_far (k_dlp, N_b nodes)", "achieved": ach,
+            "peak": FP32_PEAK_GINSTR, "unit": "G FP32 instr/s", "frac": ach / FP32_PEAK_GINSTR,
+            "terms": terms, "instr_per_term": DLP_INSTR_PER_TERM,
+            "peak_source": "nominal: 152 SMs x 128 FP32 lanes x 2.07 GHz"}
     return {"workload": "star1024 Poisson, u = sin(2x) e^y", "ms_per_solve": 1e3 * dt,
             "value": g.nx * g.ny / dt, "unit": UNIT, "max_rel_err_vs_exact": err,
-            "gmres": plan.fc2d_poisson_info(),
-            "kernels_ms": {k: v[1] / v[0] for k, v in prof.items()}}
+            "gmres": info, "kernels_ms": kms, "roofline": roof}
 
 
 def poisson_kite_oscillatory(fc2d, torch, dev, h=1.25e-3, solves=3):
