@@ -189,7 +189,8 @@ def test_values_outside_the_domain_are_ignored(case):
 # --------------------------------------------------------------------------- #
 # mixed precision: FP64 matching values and Gram coefficients, TF32 hi/lo tensor-core
 # contraction with FP32 accumulation, FP32 DFT.  Bar: 1e-6 relative max-norm against
-# the FP64 oracle (BASELINE's mixed-precision target).
+# the FP64 oracle (the mixed form's accuracy target: the TF32 hi/lo products keep about
+# 2^-21 relative, the FP32 DFT about log2(N) 2^-24).
 # --------------------------------------------------------------------------- #
 TOL_MIXED = 1e-6
 _mplans = {}
