@@ -466,19 +466,25 @@ __global__ void __launch_bounds__(256, 2) k_gather_blend_tc(GatherArgs g, TcArgs
 }
 
 // ------------------------------------------------------------------------- //
-// Blend and interpolation in one kernel (mixed form, M = 8).  CTA (c, f) computes the
-// kTcComputed = 64 normals c*kTcOwned + i (mod B) of function f as above (MMA N = 64,
-// 16 warps, one gather pass), keeps their strip values in a shared [64][ldS] tile (zero
-// padded; ldS a multiple of 4, >= Cr + 12, and not 16 mod 32 words so that neighbouring
-// rows fall in different banks) and interpolates the strip points it owns (Section 3.4)
-// from that tile, two per thread in flight, writing the strip-point values; F is not
-// written.  B = 8192 gives 144 CTAs: one wave on 152 SMs.
+// Blend and interpolation in one kernel (mixed form, M = 8).  CTA (c, fb) computes the
+// kTcComputed = 64 normals start_c + i (mod B) of NF functions fb NF .. fb NF + NF - 1 as
+// above (MMA N = 64 per function, 16 warps, one gather pass per function), keeps their
+// strip values in shared [64][ldS] tiles (zero padded; ldS a multiple of 4, >= Cr + 12,
+// and not 16 mod 32 words so that neighbouring rows fall in different banks) and
+// interpolates the strip points it owns (Section 3.4) from those tiles, two per thread
+// in flight, writing the strip-point values; F is not written.  With NF = 2 (calls of
+// several functions) the stencil tables, the TMEM allocation, the A_r tiles and each
+// point's interpolation weights serve both functions.
 // ------------------------------------------------------------------------- //
 constexpr int kGiThreads = kTcComputed * 8;
-constexpr int kGiTmemCols = 128;  // two tiles of 64 columns
-constexpr int kGiStageOff = 2 * kMaxCrPad * 32 + 2 * kTcComputed * 32;
-constexpr int kGiBarOff = kGiStageOff + kTcComputed * kTcMaxLd * 4;
-constexpr int kGiSmem = kGiBarOff + 16;
+template <int NF> __host__ __device__ constexpr int gi_tmem_cols() { return 128 * NF; }  // 2 tiles of 64 per function
+template <int NF> __host__ __device__ constexpr int gi_stage_off() {
+  return 2 * kMaxCrPad * 32 + 2 * NF * kTcComputed * 32;
+}
+template <int NF> __host__ __device__ constexpr int gi_bar_off() {
+  return gi_stage_off<NF>() + NF * kTcComputed * kTcMaxLd * 4;
+}
+template <int NF> __host__ __device__ constexpr int gi_smem() { return gi_bar_off<NF>() + 16; }
 
 struct OwnArgs {
   const int32_t* off;    // [n_own + 1]
@@ -490,35 +496,39 @@ struct OwnArgs {
   float* vals;           // [n_f][n_strip]
 };
 
+template <int NF>
 __global__ void __launch_bounds__(kGiThreads, 1) k_gather_interp_tc(GatherArgs g, TcArgs a,
-                                                                      OwnArgs o) {
+                                                                      OwnArgs o, int n_f) {
   constexpr int MM = 8;
+  constexpr uint32_t kCols = gi_tmem_cols<NF>();
   extern __shared__ __align__(1024) unsigned char smem[];
   unsigned char* a_hi = smem;
   unsigned char* a_lo = smem + kMaxCrPad * 32;
+  // function ff's C tiles at c_hi/c_lo + ff * kTcComputed * 32 (c_lo after all c_hi)
   unsigned char* c_hi = smem + 2 * kMaxCrPad * 32;
-  unsigned char* c_lo = c_hi + kTcComputed * 32;
-  float* stage = reinterpret_cast<float*>(smem + kGiStageOff);  // [64][ldS]
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + kGiBarOff);
+  unsigned char* c_lo = c_hi + NF * kTcComputed * 32;
+  float* stage0 = reinterpret_cast<float*>(smem + gi_stage_off<NF>());  // NF x [64][ldS]
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + gi_bar_off<NF>());
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mbar + 1);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int c = blockIdx.x, f = blockIdx.y;
+  const int c = blockIdx.x, f0 = blockIdx.y * NF;
+  const int nfl = min(NF, n_f - f0);  // functions of this CTA (the last may have fewer)
   const int ldS = a.ldF;  // staging row length (see the launcher)
   const int nqt = (a.Cr + kTcQTile - 1) / kTcQTile;
   const int o0 = __ldg(o.off + c), o1 = __ldg(o.off + c + 1);
 
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
-                 ::"r"(smem_u32(tmem_slot)), "r"(kGiTmemCols));
+                 ::"r"(smem_u32(tmem_slot)), "r"(kCols));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   if (tid == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(mbar)));
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  for (int idx = tid; idx < kTcComputed * (ldS - a.Cr - 1); idx += blockDim.x) {
-    const int r = idx / (ldS - a.Cr - 1);
-    stage[r * ldS + a.Cr + 1 + (idx - r * (ldS - a.Cr - 1))] = 0.f;
+  for (int idx = tid; idx < NF * kTcComputed * (ldS - a.Cr - 1); idx += blockDim.x) {
+    const int r = idx / (ldS - a.Cr - 1);  // row of the NF stacked tiles
+    stage0[r * ldS + a.Cr + 1 + (idx - r * (ldS - a.Cr - 1))] = 0.f;
   }
   {
     constexpr int kPer = (kMaxCrPad * 8 + kGiThreads - 1) / kGiThreads;
@@ -562,6 +572,9 @@ __global__ void __launch_bounds__(kGiThreads, 1) k_gather_interp_tc(GatherArgs g
     for (int i = 0; i < kMaxD; ++i) qv[i] = (s < d && i < d) ? __ldg(g.Q + i * d + s) : 0.0;
     pdl_wait();
     pdl_trigger();
+    for (int ff = 0; ff < nfl; ++ff) {
+    const int f = f0 + ff;
+    float* stage = stage0 + (size_t)ff * kTcComputed * ldS;
     const double* fg = g.f_grid + (size_t)f * g.grid_stride;
     const double* fb = g.f_bdry ? g.f_bdry + (size_t)f * g.n_bdry : nullptr;
     double val[MM];
@@ -579,7 +592,7 @@ __global__ void __launch_bounds__(kGiThreads, 1) k_gather_interp_tc(GatherArgs g
     for (int e = 1; e < MM; ++e) acc = fma(wnv[e], __shfl_sync(0xffffffffu, star, g0 + e - 1), acc);
     const double fD = s < nq ? acc : (s == d - 1 ? fbp : 0.0);
     // the value at the foot: the boundary datum, or its extrapolation (interior data)
-    const double f0 = __shfl_sync(0xffffffffu, fD, g0 + d - 1);
+    const double fv0 = __shfl_sync(0xffffffffu, fD, g0 + d - 1);
     double cs = 0.0;
 #pragma unroll
     for (int i = 0; i < kMaxD; ++i) {
@@ -588,9 +601,11 @@ __global__ void __launch_bounds__(kGiThreads, 1) k_gather_interp_tc(GatherArgs g
     }
     const double v = s < d ? cs : 0.0;
     const float hi = to_tf32((float)v);
-    *reinterpret_cast<float*>(c_hi + kmaj_off(ln, s)) = hi;
-    *reinterpret_cast<float*>(c_lo + kmaj_off(ln, s)) = (float)(v - (double)hi);
-    if (s == 0) stage[ln * ldS] = (float)f0;
+    *reinterpret_cast<float*>(c_hi + ff * kTcComputed * 32 + kmaj_off(ln, s)) = hi;
+    *reinterpret_cast<float*>(c_lo + ff * kTcComputed * 32 + kmaj_off(ln, s)) =
+        (float)(v - (double)hi);
+    if (s == 0) stage[ln * ldS] = (float)fv0;
+    }  // functions of the CTA
   }
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -599,10 +614,11 @@ __global__ void __launch_bounds__(kGiThreads, 1) k_gather_interp_tc(GatherArgs g
   const uint32_t tmem = *tmem_slot;
   if (tid == 0) {
     const uint32_t idesc = idesc_tf32(kTcQTile, kTcComputed);
-    const uint64_t dch = umma_desc(smem_u32(c_hi), 128, 256);
-    const uint64_t dcl = umma_desc(smem_u32(c_lo), 128, 256);
+    for (int ff = 0; ff < nfl; ++ff)
     for (int t = 0; t < nqt; ++t) {
-      const uint32_t dt = tmem + (uint32_t)(t * kTcComputed);
+      const uint64_t dch = umma_desc(smem_u32(c_hi + ff * kTcComputed * 32), 128, 256);
+      const uint64_t dcl = umma_desc(smem_u32(c_lo + ff * kTcComputed * 32), 128, 256);
+      const uint32_t dt = tmem + (uint32_t)((ff * 2 + t) * kTcComputed);
       const uint64_t dah = umma_desc(smem_u32(a_hi) + t * kTcQTile * 32, 128, 256);
       const uint64_t dal = umma_desc(smem_u32(a_lo) + t * kTcQTile * 32, 128, 256);
       asm volatile(
@@ -641,10 +657,12 @@ __global__ void __launch_bounds__(kGiThreads, 1) k_gather_interp_tc(GatherArgs g
   done = __all_sync(0xffffffffu, done != 0) ? 1u : 0u;
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const int quarter = warp & 3, t = warp >> 2;
+  for (int ff = 0; ff < nfl; ++ff)
   if (done && t < nqt) {
+    float* stage = stage0 + (size_t)ff * kTcComputed * ldS;
     // lanes = fine points 128 t + 32 quarter + lane; columns = the 64 normals
     uint32_t r[kTcComputed];
-    const uint32_t addr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(t * kTcComputed);
+    const uint32_t addr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)((ff * 2 + t) * kTcComputed);
 #pragma unroll
     for (int h = 0; h < kTcComputed / 32; ++h) {
       uint32_t* rr = r + 32 * h;
@@ -695,16 +713,21 @@ __global__ void __launch_bounds__(kGiThreads, 1) k_gather_interp_tc(GatherArgs g
         load(idx2, q1);
         k1 = __ldg(o.k + idx2);
       }
-      o.vals[(size_t)f * o.n_strip + k0] = interp_apply<MM, float, float, float, true>(ia, stage, q0);
-      if (k1 >= 0)
-        o.vals[(size_t)f * o.n_strip + k1] = interp_apply<MM, float, float, float, true>(ia, stage, q1);
+#pragma unroll
+      for (int ff = 0; ff < NF; ++ff) {
+        if (ff >= nfl) break;
+        const float* stage = stage0 + (size_t)ff * kTcComputed * ldS;
+        float* out = o.vals + (size_t)(f0 + ff) * o.n_strip;
+        out[k0] = interp_apply<MM, float, float, float, true>(ia, stage, q0);
+        if (k1 >= 0) out[k1] = interp_apply<MM, float, float, float, true>(ia, stage, q1);
+      }
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if (warp == 0) {
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
-                 "r"(kGiTmemCols));
+                 "r"(kCols));
   }
 }
 
@@ -726,9 +749,18 @@ fc2d_status launch_gather_interp_tc(const GatherArgs& g, int n_f, int ldS, const
   a.Ar_lo = Ar_lo;
   a.status = status;
   OwnArgs o{own_off, own_k, own_pack, own_w, own_start, n_own, n_strip, vals};
-  cudaFuncSetAttribute(k_gather_interp_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kGiSmem);
-  return cuda_check(launch_pdl(k_gather_interp_tc, dim3(n_own, n_f), dim3(kGiThreads),
-                               (size_t)kGiSmem, s, g, a, o),
+  // two functions per CTA when the call has several
+  if (n_f == 1) {
+    cudaFuncSetAttribute(k_gather_interp_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         gi_smem<1>());
+    return cuda_check(launch_pdl(k_gather_interp_tc<1>, dim3(n_own, 1), dim3(kGiThreads),
+                                 (size_t)gi_smem<1>(), s, g, a, o, n_f),
+                      "blend + interpolation launch");
+  }
+  cudaFuncSetAttribute(k_gather_interp_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       gi_smem<2>());
+  return cuda_check(launch_pdl(k_gather_interp_tc<2>, dim3(n_own, (n_f + 1) / 2),
+                               dim3(kGiThreads), (size_t)gi_smem<2>(), s, g, a, o, n_f),
                     "blend + interpolation launch");
 }
 

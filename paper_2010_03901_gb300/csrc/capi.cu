@@ -180,9 +180,11 @@ fc2d_status strip_values(fc2d_plan_s* p, int n_f, const double* fg, const double
   const bool f64 = p->prm.precision == FC2D_FP64;
   void* F = ws(p, L.oF);
   if (!f64 && p->dev.own[0].off) {
-    // mixed form, M = 8: blend and interpolation in one kernel, F stays on chip.  One CTA
-    // per SM when the call's CTAs fit in about one wave, else the fewest CTAs.
-    const auto& o = (p->dev.own[1].n && (int64_t)n_f * p->dev.own[0].n > 3 * (int64_t)p->n_sm / 2)
+    // mixed form, M = 8: blend and interpolation in one kernel, F stays on chip (two
+    // functions per CTA when n_f > 1).  One CTA per SM when the call's CTAs fit in about
+    // one wave, else the fewest CTAs.
+    const int64_t per_range = n_f == 1 ? 1 : (n_f + 1) / 2;
+    const auto& o = (p->dev.own[1].n && per_range * p->dev.own[0].n > 3 * (int64_t)p->n_sm / 2)
                         ? p->dev.own[1]
                         : p->dev.own[0];
     ProfScope ps(p, "gather_blend_interp_tc", s);
