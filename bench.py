@@ -572,7 +572,7 @@ def ff_interior_kite2048(fc2d, torch, dev, steps=20):
                         "u = 32 Gaussians (w = 0.05, centres >= 0.3 inside), u_t = 0",
             "ms_per_large_step": ms, "large_steps_per_s": 1e3 / ms,
             "value": g.nx * g.ny / (ms * 1e-3), "unit": UNIT, "kernels_ms": kms,
-            "roofline": {"bound": "alu", "kernel": "wave_cols (k_wave_cols)", "achieved": ach,
+            "roofline": {"bound": "alu", "kernel": "wave_cols (k_wave_cols_p2)", "achieved": ach,
                          "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                          "frac": ach / FP64_PEAK_TFLOPS, "peak_source": "nominal FP64 rate",
                          "flops": "4 column DFTs x 5 N log2 N, modal advance not counted"}}

@@ -847,6 +847,73 @@ static void cols4k_launch(const FftArgs& fa, int n_f, void* inter, void* fhat, c
   launch_pdl(k_cols4k_b, grid, dim3(128), 0, s, fa, drop, (float2*)inter, (float2*)fhat);
 }
 
+// ------------------------------------------------------------------------- //
+// Fourier Forwarding modal advance on power-of-two columns (FP64; see wave.cu for the
+// formulas): one block per (column, pair), both columns in place in padded shared
+// memory, the compile-time Stockham stages of block_fft for the forward transforms, the
+// advance, and the inverse transforms as forward transforms of the conjugates.
+// ------------------------------------------------------------------------- //
+template <int LOGNY>
+__global__ void __launch_bounds__((1 << LOGNY) / 8, LOGNY == 11 ? 2 : 1)
+    k_wave_cols_p2(FftArgs fa, int n_f, double2* __restrict__ inter, double c, double t,
+                   double Lx, double Ly) {
+  using C = double2;
+  constexpr int N = 1 << LOGNY, E = 8;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* A = reinterpret_cast<C*>(smem_raw);
+  C* Bv = A + padded<double>(N);
+  const int kx = blockIdx.x, f = blockIdx.y, tid = threadIdx.x;
+  C* colu = inter + (size_t)f * N * fa.pitch + kx;
+  C* colt = inter + (size_t)(n_f + f) * N * fa.pitch + kx;
+  const C* tw = reinterpret_cast<const C*>(fa.tsy);
+  for (int y = tid; y < N; y += blockDim.x) {
+    A[pad<double>(y)] = colu[(size_t)y * fa.pitch];
+    Bv[pad<double>(y)] = colt[(size_t)y * fa.pitch];
+  }
+  __syncthreads();
+#pragma unroll 1
+  for (int h = 0; h < 2; ++h) block_fft<double, LOGNY, E>(h ? Bv : A, tid, true, tw, 1);
+  const double two_pi = 6.283185307179586476925286766559;
+  for (int ky = tid; ky < N; ky += blockDim.x) {
+    const int m = ky <= N / 2 ? ky : ky - N;
+    const double fl = kx / Lx, fm = m / Ly;
+    const double w = two_pi * c * sqrt(fl * fl + fm * fm);
+    const C a0 = A[pad<double>(ky)], b0 = Bv[pad<double>(ky)];
+    const C F = C{a0.x * fa.scale, a0.y * fa.scale};
+    const C G = C{b0.x * fa.scale, b0.y * fa.scale};
+    C a, at;
+    if (w == 0.0) {
+      a = C{F.x + t * G.x, F.y + t * G.y};
+      at = G;
+    } else {
+      double sn, co;
+      sincos(w * t, &sn, &co);
+      const double sw = sn / w;
+      a = C{F.x * co + G.x * sw, F.y * co + G.y * sw};
+      at = C{-F.x * w * sn + G.x * co, -F.y * w * sn + G.y * co};
+    }
+    A[pad<double>(ky)] = C{a.x, -a.y};  // conj: inverse by a forward transform
+    Bv[pad<double>(ky)] = C{at.x, -at.y};
+  }
+  __syncthreads();
+#pragma unroll 1
+  for (int h = 0; h < 2; ++h) block_fft<double, LOGNY, E>(h ? Bv : A, tid, true, tw, 1);
+  for (int y = tid; y < N; y += blockDim.x) {
+    const C u = A[pad<double>(y)], v = Bv[pad<double>(y)];
+    colu[(size_t)y * fa.pitch] = C{u.x, -u.y};
+    colt[(size_t)y * fa.pitch] = C{v.x, -v.y};
+  }
+}
+
+template <int LOGNY>
+static void wave_cols_p2_launch(const FftArgs& fa, int n_f, void* inter, double c, double t,
+                                double Lx, double Ly, cudaStream_t s) {
+  const size_t sm = 2 * (size_t)padded<double>(1 << LOGNY) * sizeof(double2);
+  cudaFuncSetAttribute(k_wave_cols_p2<LOGNY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  k_wave_cols_p2<LOGNY><<<dim3(fa.nx / 2 + 1, n_f), (1 << LOGNY) / 8, sm, s>>>(
+      fa, n_f, (double2*)inter, c, t, Lx, Ly);
+}
+
 template <typename T, typename TV, int L>
 static void rows_launch(const FftArgs& fa, const RowArgs& ra, int n_f, int mode, const void* ext,
                         const double* fg, const void* vals, void* inter, cudaStream_t s) {
@@ -967,6 +1034,16 @@ bool launch_fft_cols_p2(const FftArgs& fa, int n_f, bool fp64, void* inter, void
     default: return false;
   }
 #undef FC2D_COLS
+}
+
+// Fourier Forwarding columns of 2048 or 4096 points; false (nothing launched) otherwise.
+bool launch_wave_cols_p2(const FftArgs& fa, int n_f, void* inter, double c, double t,
+                         double Lx, double Ly, cudaStream_t s) {
+  switch (ilog2_exact(fa.ny)) {
+    case 11: p2::wave_cols_p2_launch<11>(fa, n_f, inter, c, t, Lx, Ly, s); return true;
+    case 12: p2::wave_cols_p2_launch<12>(fa, n_f, inter, c, t, Lx, Ly, s); return true;
+    default: return false;
+  }
 }
 
 }  // namespace fc2d

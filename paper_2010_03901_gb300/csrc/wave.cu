@@ -71,8 +71,12 @@ __global__ void __launch_bounds__(256) k_wave_cols(FftArgs fa, int n_f, double2*
   for (int y = threadIdx.x; y < ny; y += blockDim.x) colt[(size_t)y * fa.pitch] = C{r[y].x, -r[y].y};
 }
 
+bool launch_wave_cols_p2(const FftArgs& fa, int n_f, void* inter, double c, double t,
+                         double Lx, double Ly, cudaStream_t s);
+
 void launch_wave_cols(const FftArgs& fa, int n_f, void* inter, double c, double t, double Lx,
                       double Ly, cudaStream_t s) {
+  if (launch_wave_cols_p2(fa, n_f, inter, c, t, Lx, Ly, s)) return;
   const size_t sm = 3 * (size_t)fa.ny * sizeof(double2);
   cudaFuncSetAttribute(k_wave_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   k_wave_cols<<<dim3(fa.nx / 2 + 1, n_f), 256, sm, s>>>(fa, n_f, (double2*)inter, c, t, Lx, Ly);
