@@ -584,7 +584,7 @@ def ff_interior_kite2048(fc2d, torch, dev, steps=20):
 
 def stars8_batched(fc2d, torch, dev, replays=10):
     """Eight stars (grids 256^2..2048^2 by concavity), 32 trigonometric sums per domain,
-    fc2d_extend_coeffs per domain, the 8 calls captured in one CUDA graph and replayed;
+    one fc2d_group_extend_coeffs call per step (one CUDA graph, a branch per domain);
     mixed and FP64.  Inputs are made on the host and copied once; the error is checked
     against the oracle on function 0 of the smallest and of the largest domain."""
     from oracle import fc2d as OF
@@ -611,7 +611,8 @@ def stars8_batched(fc2d, torch, dev, replays=10):
                        "grids " + ", ".join(f"{w.grid.nx}^2" for w in sorted(
                            stars, key=lambda s: s.grid.nx)) +
                        ", 32 degree-12 trigonometric sums per domain",
-           "points_per_step": points, "unit": UNIT, "launch": "one CUDA graph of the 8 calls"}
+           "points_per_step": points, "unit": UNIT,
+           "launch": "fc2d_group_extend_coeffs: one CUDA graph, a branch per domain"}
     small = min(range(8), key=lambda i: stars[i].grid.nx)
     large = max(range(8), key=lambda i: stars[i].grid.nx)
     for name, prec, dt in (("mixed", fc2d.FC2D_MIXED, torch.float32),
@@ -623,24 +624,19 @@ def stars8_batched(fc2d, torch, dev, replays=10):
                                   dict(B=p.B, k1=p.k1), precision=prec)
             fh = torch.empty((n_f, g.ny, g.nx // 2 + 1, 2), dtype=dt, device=dev)
             runs.append((plan, fg, fb, fh))
-        s = torch.cuda.Stream(dev)
-        with torch.cuda.stream(s):
-            for plan, fg, fb, fh in runs:
-                plan.fc2d_extend_coeffs(n_f, fg, fb, fh, s)
-        s.synchronize()
-        graph = torch.cuda.CUDAGraph()
-        with torch.cuda.graph(graph, stream=s):
-            for plan, fg, fb, fh in runs:
-                plan.fc2d_extend_coeffs(n_f, fg, fb, fh, s)
-        for _ in range(3):
-            graph.replay()
+        grp = fc2d.fc2d_group_create([r[0] for r in runs])
+        gargs = ([n_f] * len(runs), [r[1] for r in runs], [r[2] for r in runs],
+                 [r[3] for r in runs])
+        for _ in range(3):  # the first call captures the graph, the others replay it
+            grp.fc2d_group_extend_coeffs(*gargs)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record()
         for _ in range(replays):
-            graph.replay()
+            grp.fc2d_group_extend_coeffs(*gargs)
         e1.record()
         torch.cuda.synchronize()
+        grp.fc2d_group_destroy()
         for plan, *_ in runs:
             plan.fc2d_sync_status()
         ms = e0.elapsed_time(e1) / replays

@@ -253,6 +253,25 @@ fc2d_status fc2d_profile_read(fc2d_plan_t plan, int max_kernels, char* names_hos
 /* Waits for the stream and returns the plan's latched device status. */
 fc2d_status fc2d_sync_status(fc2d_plan_t plan, void* stream);
 
+/* Plan groups: the extension + DFT of several domains (uneven grids and function
+ * counts) in one launch.  fc2d_group_create keeps the plans (not owned: destroy the
+ * group before them).  fc2d_group_extend_coeffs runs fc2d_extend_coeffs of every plan
+ * i on n_f[i] functions, f_grid_dev[i] / f_bdry_dev[i] (f_bdry_dev itself, or an entry,
+ * may be NULL: interior data only) / fhat_dev[i] as for that call, as one CUDA graph
+ * launched on `stream`: each plan on its own branch, so the domains' kernels run
+ * concurrently.  The graph is captured on the first call (the plans' workspaces are
+ * allocated before the capture) and replayed while n_f and every pointer stay the same;
+ * a call with other arguments captures anew.  Calls on one group must not overlap in
+ * time on different streams (the plans' workspaces are shared).  The result equals the
+ * separate calls bit for bit. */
+typedef struct fc2d_group_s* fc2d_group_t;
+fc2d_status fc2d_group_create(const fc2d_plan_t* plans, int n, fc2d_group_t* out);
+fc2d_status fc2d_group_extend_coeffs(fc2d_group_t group, const int* n_f,
+                                     const double* const* f_grid_dev,
+                                     const double* const* f_bdry_dev, void* const* fhat_dev,
+                                     void* stream);
+void fc2d_group_destroy(fc2d_group_t group);
+
 void fc2d_destroy(fc2d_plan_t plan);
 
 /* Text of the last error on this host thread ("" if none). */

@@ -220,6 +220,16 @@ static fc2d_status check_interior(fc2d_plan_t p, const double* fb, const char* w
   return FC2D_OK;
 }
 
+namespace fc2d {
+// the plan workspace for an n_f-function call (plan groups allocate it before capturing)
+fc2d_status ensure_plan_workspace(fc2d_plan_s* p, int n_f) {
+  fc2d_status st = check_nf(p, n_f);
+  if (st) return st;
+  cudaSetDevice(p->device);
+  return ensure_workspace(p, layout(p, n_f).total);
+}
+}  // namespace fc2d
+
 extern "C" fc2d_status fc2d_blend(fc2d_plan_t p, int n_f, const double* fg, const double* fb,
                                   void* F, void* stream) {
   fc2d_status st = check_nf(p, n_f);

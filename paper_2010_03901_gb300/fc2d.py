@@ -73,6 +73,8 @@ def load_library(path: str = LIB_PATH):
         "fc2d_inside_points": [P, P],
         "fc2d_extend_coeffs_compact": [P, ct.c_int, P, P, P, P],
         "fc2d_extend_coeffs_complex": [P, ct.c_int, P, P, P, P],
+        "fc2d_group_create": [P, ct.c_int, P],
+        "fc2d_group_extend_coeffs": [P, P, P, P, P, P],
         "fc2d_coeffs_static": [P, ct.c_int, P, P, P],
         "fc2d_sync_status": [P, P],
         "fc2d_poisson_plan": [P, ct.c_int],
@@ -89,6 +91,8 @@ def load_library(path: str = LIB_PATH):
         fn.restype = ct.c_int
     lib.fc2d_destroy.argtypes = [P]
     lib.fc2d_destroy.restype = None
+    lib.fc2d_group_destroy.argtypes = [P]
+    lib.fc2d_group_destroy.restype = None
     lib.fc2d_last_error.argtypes = []
     lib.fc2d_last_error.restype = ct.c_char_p
     return lib
@@ -267,3 +271,40 @@ class Plan:
 
 def fc2d_plan(boundary, grid, params=None, precision=FC2D_FP64) -> Plan:
     return Plan(boundary, grid, params, precision)
+
+
+class Group:
+    """A plan group: the extension + DFT of several domains as one CUDA graph, each plan
+    on its own branch (fc2d_group_create).  Keeps references to its plans."""
+
+    def __init__(self, plans):
+        self.plans = list(plans)
+        arr = (ct.c_void_p * len(self.plans))(*[pl.handle for pl in self.plans])
+        h = ct.c_void_p()
+        _check(_lib.fc2d_group_create(arr, len(self.plans), ct.byref(h)))
+        self.handle = h
+
+    def fc2d_group_extend_coeffs(self, n_f, f_grid, f_bdry, fhat, stream=None):
+        """n_f: per plan; f_grid, fhat: per plan device tensors; f_bdry: per plan tensors
+        or None entries (interior data only), or None."""
+        n = len(self.plans)
+        nf = (ct.c_int * n)(*n_f)
+        fg = (ct.c_void_p * n)(*[_ptr(x) for x in f_grid])
+        fh = (ct.c_void_p * n)(*[_ptr(x) for x in fhat])
+        fb = None if f_bdry is None else (ct.c_void_p * n)(*[_ptr(x) for x in f_bdry])
+        _check(_lib.fc2d_group_extend_coeffs(self.handle, nf, fg, fb, fh, _stream(stream)))
+
+    def fc2d_group_destroy(self):
+        if self.handle:
+            _lib.fc2d_group_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.fc2d_group_destroy()
+        except Exception:
+            pass
+
+
+def fc2d_group_create(plans) -> Group:
+    return Group(plans)

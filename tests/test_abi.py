@@ -47,6 +47,8 @@ def test_argument_errors_are_status_codes(lib):
 def test_binding_names_match_the_abi():
     from paper_2010_03901_gb300 import fc2d
     names = declared_symbols()
-    methods = {m for m in dir(fc2d.Plan) if m.startswith("fc2d_")} | {"fc2d_plan"}
+    methods = ({m for m in dir(fc2d.Plan) if m.startswith("fc2d_")} |
+               {m for m in dir(fc2d.Group) if m.startswith("fc2d_")} |
+               {"fc2d_plan", "fc2d_group_create"})
     skip = {"fc2d_plan_info", "fc2d_last_error", "fc2d_fc_matrices_compute"}
     assert (names - skip) <= methods | {"fc2d_destroy"}, names - methods

@@ -1,0 +1,88 @@
+"""Plan groups (fc2d_group_extend_coeffs): several domains in one CUDA graph with a
+branch per plan.  The spectra must equal separate fc2d_extend_coeffs calls bit for bit,
+on the first call (capture), on replays over updated inputs, after a re-capture with
+other buffers, and with interior data only."""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import fc2d as OF
+from oracle import geometry as OG
+
+pytestmark = pytest.mark.gpu
+
+NAMES = ["disk64", "star200", "kite160x144"]
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.fail("GPU test run without a CUDA device")
+    return torch
+
+
+def _setup(torch, fc2d, prec, seed):
+    dev = torch.device("cuda:0")
+    dt = torch.float64 if prec == fc2d.FC2D_FP64 else torch.float32
+    plans, fg, fb, out, ref, n_f = [], [], [], [], [], []
+    for i, name in enumerate(NAMES):
+        w = W.workload(name)
+        g, p = w.grid, w.params
+        plan = fc2d.fc2d_plan(w.boundary.arrays(), (g.a0, g.b0, g.h, g.nx, g.ny),
+                              dict(B=p.B, k1=p.k1), precision=prec)
+        geo = OG.build_geometry(w)
+        nf = 1 + i  # uneven function counts
+        fs = [W.trig_sum(8, seed + 10 * i + k) for k in range(nf)]
+        fg.append(torch.tensor(np.stack([W.grid_values(w, f) for f in fs]), device=dev))
+        fb.append(torch.tensor(np.stack([OF.boundary_values(geo, f) for f in fs]), device=dev))
+        out.append(torch.zeros((nf, g.ny, g.nx // 2 + 1, 2), dtype=dt, device=dev))
+        ref.append(torch.zeros_like(out[-1]))
+        plans.append(plan)
+        n_f.append(nf)
+    return plans, fg, fb, out, ref, n_f
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_group_equals_separate_calls(torch_cuda, precision):
+    torch = torch_cuda
+    from paper_2010_03901_gb300 import fc2d
+    prec = fc2d.FC2D_FP64 if precision == "fp64" else fc2d.FC2D_MIXED
+    plans, fg, fb, out, ref, n_f = _setup(torch, fc2d, prec, 3)
+    grp = fc2d.fc2d_group_create(plans)
+    grp.fc2d_group_extend_coeffs(n_f, fg, fb, out)
+    for i, pl in enumerate(plans):
+        pl.fc2d_extend_coeffs(n_f[i], fg[i], fb[i], ref[i])
+        pl.fc2d_sync_status()
+    for i in range(len(plans)):
+        assert torch.equal(out[i], ref[i]), i
+    # replay over updated inputs (same buffers)
+    for i in range(len(plans)):
+        fg[i].mul_(-0.5).add_(0.25)
+        fb[i].mul_(-0.5).add_(0.25)
+    grp.fc2d_group_extend_coeffs(n_f, fg, fb, out)
+    for i, pl in enumerate(plans):
+        pl.fc2d_extend_coeffs(n_f[i], fg[i], fb[i], ref[i])
+    torch.cuda.synchronize()
+    for i in range(len(plans)):
+        assert torch.equal(out[i], ref[i]), i
+    # other output buffers: captured anew
+    out2 = [torch.full_like(o, 3.0) for o in out]
+    grp.fc2d_group_extend_coeffs(n_f, fg, fb, out2)
+    torch.cuda.synchronize()
+    for i in range(len(plans)):
+        assert torch.equal(out2[i], ref[i]), i
+    grp.fc2d_group_destroy()
+
+
+def test_group_interior_data_only(torch_cuda):
+    torch = torch_cuda
+    from paper_2010_03901_gb300 import fc2d
+    plans, fg, fb, out, ref, n_f = _setup(torch, fc2d, fc2d.FC2D_FP64, 7)
+    grp = fc2d.fc2d_group_create(plans)
+    grp.fc2d_group_extend_coeffs(n_f, fg, None, out)
+    for i, pl in enumerate(plans):
+        pl.fc2d_extend_coeffs(n_f[i], fg[i], None, ref[i])
+    torch.cuda.synchronize()
+    for i in range(len(plans)):
+        assert torch.equal(out[i], ref[i]), i
