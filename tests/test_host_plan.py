@@ -169,3 +169,28 @@ def test_owner_partition_is_balanced(seed, B, cap, n_cta):
     assert np.all(d >= 1) and np.all(d <= cap) and len(d) <= n_cta
     pre = np.concatenate([[0], np.cumsum(cnt)])
     assert (pre[st[1:]] - pre[st[:-1]]).max() == _min_max_partition(cnt, cap, n_cta)
+
+
+# --------------------------------------------------------------------------- #
+# Plan errors (the host plan code on the CPU): status and message
+# --------------------------------------------------------------------------- #
+def _with_grid(name, **kw):
+    from dataclasses import replace
+    w = W.workload(name)
+    return replace(w, grid=replace(w.grid, **kw))
+
+
+@pytest.mark.parametrize("grid,status,msg", [
+    (dict(nx=127), 7, "nx must be even"),
+    (dict(nx=126, ny=126, h=3.0 / 126), 7, "2^a 3^b 5^c"),
+    (dict(a0=-1.05, b0=-1.05, h=2.1 / 128), 2, "reaches the grid edge"),
+])
+def test_plan_rejects_bad_grids(grid, status, msg):
+    r = host_plan.run(_with_grid("disk128", **grid))
+    assert r["status"] == status and msg in r["error"], r["error"]
+
+
+@pytest.mark.parametrize("params", [dict(d=13, M=16), dict(d=1), dict(M=17), dict(C=1)])
+def test_plan_rejects_parameters_out_of_range(params):
+    r = host_plan.run(W.workload("disk128", **params))
+    assert r["status"] == 1 and "parameter out of range" in r["error"], r["error"]
