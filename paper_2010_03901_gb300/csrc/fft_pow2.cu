@@ -848,6 +848,61 @@ static void cols4k_launch(const FftArgs& fa, int n_f, void* inter, void* fhat, c
 }
 
 // ------------------------------------------------------------------------- //
+// Inverse real row DFT (FP64) of rows whose half length NH = 2^LOGNH is a power of
+// two: the inverse of the even/odd split gives Z_k = S_k + i conj(w^k) D_k from X_k and
+// conj(X_{NH-k}), the length-NH transform runs as a forward transform of conj(Z) on the
+// compile-time Stockham stages, and x_{2m} + i x_{2m+1} = conj of its result; plus the
+// quadratic term c00[f] (x^2 + y^2)/4 when c00 is given.  One block per (row, function).
+// ------------------------------------------------------------------------- //
+template <int LOGNH>
+__global__ void __launch_bounds__((1 << LOGNH) / 8)
+    k_inverse_rows_p2(FftArgs fa, const double2* __restrict__ inter,
+                      const double* __restrict__ c00, double a0, double b0, double h,
+                      double* __restrict__ up) {
+  using C = double2;
+  constexpr int NH = 1 << LOGNH, E = 8;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  C* buf = reinterpret_cast<C*>(smem_raw);
+  const int j = blockIdx.x, f = blockIdx.y, t = threadIdx.x;
+  const C* row = inter + ((size_t)f * fa.ny + j) * fa.pitch;
+  const C* rtw = reinterpret_cast<const C*>(fa.rtw);
+  pdl_wait();
+  pdl_trigger();
+  for (int k = t; k < NH; k += blockDim.x) {
+    const C bk = row[k];
+    C bc = row[NH - k];
+    bc.y = -bc.y;  // conj X_{NH-k}
+    const C sm = {bk.x + bc.x, bk.y + bc.y}, d = {bk.x - bc.x, bk.y - bc.y};
+    C w = __ldg(rtw + k);
+    w.y = -w.y;  // conj(w^k)
+    const C dw = {d.x * w.x - d.y * w.y, d.x * w.y + d.y * w.x};
+    buf[pad<double>(k)] = C{sm.x - dw.y, -(sm.y + dw.x)};  // conj(s + i dw)
+  }
+  __syncthreads();
+  block_fft<double, LOGNH, E>(buf, t, true, reinterpret_cast<const C*>(fa.tsx), 1);
+  const double q = c00 ? c00[f] * 0.25 : 0.0;
+  const double y = b0 + h * double(j);
+  double* out = up + ((size_t)f * fa.ny + j) * (2 * NH);
+  for (int m = t; m < NH; m += blockDim.x) {
+    const C z = buf[pad<double>(m)];
+    const double x0 = a0 + h * double(2 * m), x1 = a0 + h * double(2 * m + 1);
+    out[2 * m] = z.x + q * (x0 * x0 + y * y);
+    out[2 * m + 1] = -z.y + q * (x1 * x1 + y * y);
+  }
+}
+
+template <int LOGNH>
+static void inverse_rows_p2_launch(const FftArgs& fa, int n_f, const void* inter,
+                                   const double* c00, double a0, double b0, double h,
+                                   double* out, cudaStream_t s) {
+  const size_t sm = (size_t)padded<double>(1 << LOGNH) * sizeof(double2);
+  cudaFuncSetAttribute(k_inverse_rows_p2<LOGNH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)sm);
+  launch_pdl(k_inverse_rows_p2<LOGNH>, dim3(fa.ny, n_f), dim3((1 << LOGNH) / 8), sm, s, fa,
+             (const double2*)inter, c00, a0, b0, h, out);
+}
+
+// ------------------------------------------------------------------------- //
 // Fourier Forwarding modal advance on power-of-two columns (FP64; see wave.cu for the
 // formulas): one block per (column, pair), both columns in place in padded shared
 // memory, the compile-time Stockham stages of block_fft for the forward transforms, the
@@ -1036,9 +1091,23 @@ bool launch_fft_cols_p2(const FftArgs& fa, int n_f, bool fp64, void* inter, void
 #undef FC2D_COLS
 }
 
+// FP64 inverse real rows with nx/2 = 2^8 .. 2^11; false (nothing launched) otherwise.
+bool launch_inverse_rows_p2(const FftArgs& fa, int n_f, const void* inter, const double* c00,
+                            double a0, double b0, double h, double* out, cudaStream_t s) {
+  if (!fa.tsx || !fa.rtw) return false;  // needs the per-stage twiddle table
+  switch (ilog2_exact(fa.nx / 2)) {
+    case 8: p2::inverse_rows_p2_launch<8>(fa, n_f, inter, c00, a0, b0, h, out, s); return true;
+    case 9: p2::inverse_rows_p2_launch<9>(fa, n_f, inter, c00, a0, b0, h, out, s); return true;
+    case 10: p2::inverse_rows_p2_launch<10>(fa, n_f, inter, c00, a0, b0, h, out, s); return true;
+    case 11: p2::inverse_rows_p2_launch<11>(fa, n_f, inter, c00, a0, b0, h, out, s); return true;
+    default: return false;
+  }
+}
+
 // Fourier Forwarding columns of 2048 or 4096 points; false (nothing launched) otherwise.
 bool launch_wave_cols_p2(const FftArgs& fa, int n_f, void* inter, double c, double t,
                          double Lx, double Ly, cudaStream_t s) {
+  if (!fa.tsy) return false;  // needs the per-stage twiddle table
   switch (ilog2_exact(fa.ny)) {
     case 11: p2::wave_cols_p2_launch<11>(fa, n_f, inter, c, t, Lx, Ly, s); return true;
     case 12: p2::wave_cols_p2_launch<12>(fa, n_f, inter, c, t, Lx, Ly, s); return true;

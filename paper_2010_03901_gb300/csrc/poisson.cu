@@ -802,6 +802,8 @@ fc2d_status poisson_solve(fc2d_plan_s* p, int n_f, const double* fg, const doubl
   for (int i = 0; i < fa.nry; ++i) fa.ry[i] = p->fy.radix[i];
   fa.twx = p->fx.tw64;
   fa.twy = p->fy.tw64;
+  fa.tsx = p->fx.tws64;  // per-stage tables of the power-of-two inverse rows
+  fa.tsy = p->fy.tws64;
   fa.rtw = p->rtw64;
   fa.scale = 1.0 / ((double)nx * ny);
   {
@@ -816,9 +818,7 @@ fc2d_status poisson_solve(fc2d_plan_s* p, int n_f, const double* fg, const doubl
   }
   {
     ProfScope ps(p, "poisson_rows", s);
-    size_t sm = (size_t)nx * sizeof(double2);
-    cudaFuncSetAttribute(k_poisson_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    k_poisson_rows<<<dim3(ny, n_f), 256, sm, s>>>(fa, (const double2*)inter, P->c00, a0, b0, h, u);
+    launch_inverse_rows(fa, n_f, inter, P->c00, a0, b0, h, u, s);
   }
   fc2d_status st = cuda_check(cudaGetLastError(), "Poisson particular solution");
   if (st) return st;
@@ -868,8 +868,12 @@ fc2d_status poisson_solve(fc2d_plan_s* p, int n_f, const double* fg, const doubl
 }
 
 // inverse real 2D-DFT rows (after an inverse column pass) for callers outside this file
+bool launch_inverse_rows_p2(const FftArgs& fa, int n_f, const void* inter, const double* c00,
+                            double a0, double b0, double h, double* out, cudaStream_t s);
+
 void launch_inverse_rows(const FftArgs& fa, int n_f, const void* inter, const double* c00,
                          double a0, double b0, double h, double* out, cudaStream_t s) {
+  if (launch_inverse_rows_p2(fa, n_f, inter, c00, a0, b0, h, out, s)) return;
   size_t sm = (size_t)fa.nx * sizeof(double2);
   cudaFuncSetAttribute(k_poisson_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   k_poisson_rows<<<dim3(fa.ny, n_f), 256, sm, s>>>(fa, (const double2*)inter, c00, a0, b0, h, out);
