@@ -856,7 +856,10 @@ fc2d_status poisson_solve(fc2d_plan_s* p, int n_f, const double* fg, const doubl
         // boundary values g - u_p: reuse ghat for their coefficients
         k_density_dft<<<(unsigned)((Nb / 2 + 1 + 127) / 128), 128, 0, s>>>(
             Nb, P->g, (const double2*)P->twb, (double2*)P->ghat);
-        auto kc = MP == 8 ? k_dlp_close<8> : k_dlp_close<0>;
+        auto kc = MP == 8    ? k_dlp_close<8>
+                  : MP == 13 ? k_dlp_close<13>
+                  : MP == 15 ? k_dlp_close<15>
+                             : k_dlp_close<0>;
         kc<<<(unsigned)P->n_close, 256, 0, s>>>(
             (int)P->n_close, P->close_lin, P->close_geo, P->close_w, P->dnodes, MP, NR, a0, b0,
             h, P->posR, P->abR, Nb, (const double2*)P->ghat, uf);
