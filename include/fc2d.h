@@ -43,7 +43,8 @@
  *            fc2d_plan and the host queries are synchronous.
  * Errors:    argument and geometry errors are returned synchronously; the text is in
  *            fc2d_last_error().  Device-side conditions (a Newton search that did not
- *            converge) are latched in the plan and returned by fc2d_sync_status.
+ *            converge, a bounded wait that gave up) are latched in the plan and
+ *            returned (once) by fc2d_sync_status.
  *            No entry point aborts, traps or exits the process.
  * Threads:   a plan may be used by one host thread at a time.
  */
@@ -250,8 +251,18 @@ fc2d_status fc2d_profile(fc2d_plan_t plan, int enable);
 fc2d_status fc2d_profile_read(fc2d_plan_t plan, int max_kernels, char* names_host,
                               int64_t* launches_host, double* ms_host, int* n_out);
 
-/* Waits for the stream and returns the plan's latched device status. */
+/* Waits for the stream and returns the plan's latched device status, then clears it
+ * (a condition is reported once; the next call returns FC2D_OK unless a kernel latched
+ * a new one). */
 fc2d_status fc2d_sync_status(fc2d_plan_t plan, void* stream);
+
+/* Failure detection check (no operation of the paper).  Runs the bounded device wait
+ * of the tensor-core blend kernels on an mbarrier that nothing arrives on: after
+ * 2 x polls polls the kernel latches FC2D_ERR_TIMEOUT in the plan's status word and
+ * returns, so that fc2d_sync_status then returns FC2D_ERR_TIMEOUT; nothing hangs or
+ * traps and the plan stays usable.  polls in 1 .. 2^22 (FC2D_ERR_ARG otherwise); one
+ * block of 32 threads on `stream`, asynchronous. */
+fc2d_status fc2d_wait_selftest(fc2d_plan_t plan, uint32_t polls, void* stream);
 
 /* Plan groups: the extension + DFT of several domains (uneven grids and function
  * counts) in one launch.  fc2d_group_create keeps the plans (not owned: destroy the

@@ -42,6 +42,27 @@ __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
 }
 
+// Bounded wait for phase 0 of the mbarrier at shared address mbar (the MMAs' commit
+// arrives on it): at most `limit` polls.  If they run out, thread 0 latches
+// FC2D_ERR_TIMEOUT in *status and the wait is given `limit` polls once more, since
+// MMAs still in flight must end before their TMEM is freed.  True once the phase
+// completed.
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t mbar, int* status, uint32_t limit) {
+  uint32_t done = 0;
+  auto poll = [&] {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(done) : "r"(mbar), "r"(0) : "memory");
+  };
+  for (uint32_t it = 0; it < limit && !done; ++it) poll();
+  if (!done) {
+    if (threadIdx.x == 0) atomicExch(status, (int)FC2D_ERR_TIMEOUT);
+    for (uint32_t it = 0; it < limit && !done; ++it) poll();
+  }
+  return done != 0;
+}
+
 // K-major, no-swizzle shared-memory matrix descriptor (tcgen05 format).
 __device__ __forceinline__ uint64_t umma_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
   uint64_t d = 0;
@@ -159,22 +180,7 @@ __global__ void __launch_bounds__(128, 1) k_blend_tc(TcArgs a) {
         ::"r"(smem_u32(mbar)) : "memory");
   }
   // bounded wait for the MMAs (phase 0 of the mbarrier)
-  uint32_t done = 0;
-  for (uint32_t it = 0; it < kSpinLimit && !done; ++it) {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}\n"
-        : "=r"(done) : "r"(smem_u32(mbar)), "r"(0) : "memory");
-  }
-  if (!done) {
-    if (tid == 0) atomicExch(a.status, (int)FC2D_ERR_TIMEOUT);
-    for (uint32_t it = 0; it < kSpinLimit && !done; ++it) {
-      asm volatile(
-          "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-          "selp.u32 %0, 1, 0, p;\n\t}\n"
-          : "=r"(done) : "r"(smem_u32(mbar)), "r"(0) : "memory");
-    }
-  }
+  uint32_t done = mbar_wait_bounded(smem_u32(mbar), a.status, kSpinLimit) ? 1u : 0u;
   // the epilogue's tcgen05.ld is warp-collective: run it only if every lane saw the
   // MMAs complete
   done = __all_sync(0xffffffffu, done != 0) ? 1u : 0u;
@@ -402,22 +408,7 @@ __global__ void __launch_bounds__(256, 2) k_gather_blend_tc(GatherArgs g, TcArgs
         "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
         ::"r"(smem_u32(mbar)) : "memory");
   }
-  uint32_t done = 0;
-  for (uint32_t it = 0; it < kSpinLimit && !done; ++it) {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}\n"
-        : "=r"(done) : "r"(smem_u32(mbar)), "r"(0) : "memory");
-  }
-  if (!done) {
-    if (tid == 0) atomicExch(a.status, (int)FC2D_ERR_TIMEOUT);
-    for (uint32_t it = 0; it < kSpinLimit && !done; ++it) {
-      asm volatile(
-          "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-          "selp.u32 %0, 1, 0, p;\n\t}\n"
-          : "=r"(done) : "r"(smem_u32(mbar)), "r"(0) : "memory");
-    }
-  }
+  uint32_t done = mbar_wait_bounded(smem_u32(mbar), a.status, kSpinLimit) ? 1u : 0u;
   done = __all_sync(0xffffffffu, done != 0) ? 1u : 0u;
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const int quarter = warp & 3, t = warp >> 2;
@@ -638,22 +629,7 @@ __global__ void __launch_bounds__(kGiThreads, 1) k_gather_interp_tc(GatherArgs g
         "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
         ::"r"(smem_u32(mbar)) : "memory");
   }
-  uint32_t done = 0;
-  for (uint32_t it = 0; it < kSpinLimit && !done; ++it) {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}\n"
-        : "=r"(done) : "r"(smem_u32(mbar)), "r"(0) : "memory");
-  }
-  if (!done) {
-    if (tid == 0) atomicExch(a.status, (int)FC2D_ERR_TIMEOUT);
-    for (uint32_t it = 0; it < kSpinLimit && !done; ++it) {
-      asm volatile(
-          "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-          "selp.u32 %0, 1, 0, p;\n\t}\n"
-          : "=r"(done) : "r"(smem_u32(mbar)), "r"(0) : "memory");
-    }
-  }
+  uint32_t done = mbar_wait_bounded(smem_u32(mbar), a.status, kSpinLimit) ? 1u : 0u;
   done = __all_sync(0xffffffffu, done != 0) ? 1u : 0u;
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const int quarter = warp & 3, t = warp >> 2;
@@ -784,6 +760,24 @@ fc2d_status launch_gather_blend_tc(const GatherArgs& g, int n_f, int ldF, const 
   return cuda_check(
       launch_pdl(k, dim3((a.n_cols + kTcNormals - 1) / kTcNormals), dim3(256), sm, s, g, a),
       "fused tensor-core blend launch");
+}
+
+// A wait that nothing ends: mbar_wait_bounded, exactly as the tensor-core kernels call
+// it, on a fresh mbarrier that no thread or MMA arrives on, so that the timeout path
+// (FC2D_ERR_TIMEOUT latched, the kernel returns) can be run on purpose.  One warp.
+__global__ void __launch_bounds__(32) k_wait_probe(int* status, uint32_t limit) {
+  __shared__ __align__(8) uint64_t mbar;
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar)));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncwarp();
+  mbar_wait_bounded(smem_u32(&mbar), status, limit);
+}
+
+fc2d_status launch_wait_probe(int* status, uint32_t limit, cudaStream_t s) {
+  k_wait_probe<<<1, 32, 0, s>>>(status, limit);
+  return cuda_check(cudaGetLastError(), "wait probe launch");
 }
 
 }  // namespace fc2d

@@ -406,8 +406,18 @@ extern "C" fc2d_status fc2d_sync_status(fc2d_plan_t p, void* stream) {
   st = cuda_check(cudaMemcpy(&h, p->dev.status, sizeof(int), cudaMemcpyDeviceToHost),
                   "status read");
   if (st) return st;
-  if (h) return set_error((fc2d_status)h, "device status latched");
-  return FC2D_OK;
+  if (!h) return FC2D_OK;
+  // report once: clear the word, so that the plan's next calls start from FC2D_OK
+  st = cuda_check(cudaMemset(p->dev.status, 0, sizeof(int)), "status clear");
+  if (st) return st;
+  return set_error((fc2d_status)h, "device status latched");
+}
+
+extern "C" fc2d_status fc2d_wait_selftest(fc2d_plan_t p, uint32_t polls, void* stream) {
+  if (!p) return set_error(FC2D_ERR_ARG, "null plan");
+  if (polls < 1 || polls > (1u << 22)) return set_error(FC2D_ERR_ARG, "polls must be in 1 .. 2^22");
+  cudaSetDevice(p->device);
+  return fc2d::launch_wait_probe(p->dev.status, polls, (cudaStream_t)stream);
 }
 
 // ------------------------------------------------------------------------- //

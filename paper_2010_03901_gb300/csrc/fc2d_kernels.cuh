@@ -122,6 +122,9 @@ fc2d_status launch_gather_interp_tc(const GatherArgs& g, int n_f, int ldS, const
                                     const int32_t* own_k, const int32_t* own_pack,
                                     const float* own_w, const int32_t* own_start, int n_own,
                                     int n_strip, float* vals, int* status, cudaStream_t s);
+// The tensor-core kernels' bounded mbarrier wait on a barrier nothing arrives on: after
+// 2 x limit polls FC2D_ERR_TIMEOUT is latched in *status and the kernel returns.
+fc2d_status launch_wait_probe(int* status, uint32_t limit, cudaStream_t s);
 void launch_interp(const InterpArgs& a, int n_f, bool fp64, const void* F, void* vals,
                    cudaStream_t s);
 void launch_assemble(const RowArgs& a, int n_f, bool fp64, const double* f_grid,

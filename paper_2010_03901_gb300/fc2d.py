@@ -77,6 +77,7 @@ def load_library(path: str = LIB_PATH):
         "fc2d_group_extend_coeffs": [P, P, P, P, P, P],
         "fc2d_coeffs_static": [P, ct.c_int, P, P, P],
         "fc2d_sync_status": [P, P],
+        "fc2d_wait_selftest": [P, ct.c_uint32, P],
         "fc2d_poisson_plan": [P, ct.c_int],
         "fc2d_poisson_nodes": [P, P, P],
         "fc2d_poisson_info": [P, P, P, P],
@@ -256,6 +257,9 @@ class Plan:
 
     def fc2d_sync_status(self, stream=None):
         _check(_lib.fc2d_sync_status(self.handle, _stream(stream)))
+
+    def fc2d_wait_selftest(self, polls, stream=None):
+        _check(_lib.fc2d_wait_selftest(self.handle, int(polls), _stream(stream)))
 
     def fc2d_destroy(self):
         if self.handle:

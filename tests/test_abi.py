@@ -42,6 +42,10 @@ def test_argument_errors_are_status_codes(lib):
     assert b"null" in lib.fc2d_last_error()
     lib.fc2d_extend.restype = ct.c_int
     assert lib.fc2d_extend(None, 1, None, None, None, None) == 1
+    lib.fc2d_wait_selftest.restype = ct.c_int
+    lib.fc2d_wait_selftest.argtypes = [ct.c_void_p, ct.c_uint32, ct.c_void_p]
+    assert lib.fc2d_wait_selftest(None, 16, None) == 1
+    assert b"null plan" in lib.fc2d_last_error()
 
 
 def test_binding_names_match_the_abi():

@@ -1,6 +1,8 @@
 """Argument errors of the C ABI's calls return their status (FC2D_ERR_ARG = 1,
 FC2D_ERR_UNSUPPORTED = 7) with a message and launch nothing; the plan stays usable and
 its device status word reads FC2D_OK."""
+import time
+
 import numpy as np
 import pytest
 
@@ -76,3 +78,32 @@ def test_group_arguments(env):
     grp.fc2d_group_extend_coeffs([1], [fg], [fb], [fhat])
     plan.fc2d_sync_status()
     grp.fc2d_group_destroy()
+
+
+def test_a_stalled_device_wait_times_out_and_the_plan_stays_usable(env):
+    """Failure detection on the GPU without a fault: the tensor-core kernels' bounded
+    mbarrier wait, run on a barrier that nothing arrives on, gives up after its polls,
+    latches FC2D_ERR_TIMEOUT (4) and returns.  fc2d_sync_status reports it once, and the
+    plan then computes the same spectrum, bit for bit, as before the stall."""
+    torch, fc2d, w, _, mixed, fg, fb = env
+    g = w.grid
+    shape = (1, g.ny, g.nx // 2 + 1, 2)
+    before = torch.zeros(shape, dtype=torch.float32, device=fg.device)
+    mixed.fc2d_extend_coeffs(1, fg, fb, before)
+    mixed.fc2d_sync_status()
+    t0 = time.perf_counter()
+    mixed.fc2d_wait_selftest(1 << 12)
+    with pytest.raises(fc2d.Fc2dError, match="device status latched") as e:
+        mixed.fc2d_sync_status()
+    elapsed = time.perf_counter() - t0
+    assert _status(e) == 4
+    assert elapsed < 30, elapsed
+    mixed.fc2d_sync_status()  # reported once
+    after = torch.zeros(shape, dtype=torch.float32, device=fg.device)
+    mixed.fc2d_extend_coeffs(1, fg, fb, after)
+    mixed.fc2d_sync_status()
+    assert torch.equal(before, after)
+    for polls in (0, (1 << 22) + 1):
+        with pytest.raises(fc2d.Fc2dError, match="polls must be") as e:
+            mixed.fc2d_wait_selftest(polls)
+        assert _status(e) == 1
