@@ -727,14 +727,18 @@ def run_gpu(args):
             else:
                 line[name]["err_vs_oracle"] = err
     if rank == 0 and world == 1 and not args.no_extra:
-        line["poisson_star1024"] = poisson_star1024(fc2d, torch, dev)
-        line["poisson_kite_d10"] = poisson_kite_oscillatory(fc2d, torch, dev)
-        line["ff_interior_kite2048"] = ff_interior_kite2048(fc2d, torch, dev)
-        line["stars8_batched"] = stars8_batched(fc2d, torch, dev)
+        for name in args.extra.split(","):
+            line[name] = EXTRA_LINES[name](fc2d, torch, dev)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+EXTRA_LINES = {"poisson_star1024": poisson_star1024,
+               "poisson_kite_d10": poisson_kite_oscillatory,
+               "ff_interior_kite2048": ff_interior_kite2048,
+               "stars8_batched": stars8_batched}
 
 
 def main(argv=None):
@@ -748,7 +752,13 @@ def main(argv=None):
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the Poisson, Fourier Forwarding and batched-star lines")
+    ap.add_argument("--extra", default=",".join(EXTRA_LINES),
+                    help="comma-separated extra lines to run (default: all of "
+                         + ", ".join(EXTRA_LINES) + ")")
     args = ap.parse_args(argv)
+    bad = [n for n in args.extra.split(",") if n not in EXTRA_LINES]
+    if bad:
+        ap.error(f"unknown extra line(s): {', '.join(bad)}")
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":

@@ -46,6 +46,7 @@ struct PoissonState {
   int32_t *ui0 = nullptr, *uj0 = nullptr;                               // [Nb]
   double *uwx = nullptr, *uwy = nullptr;                                // [Nb][MP]
   int64_t n_far = 0, n_mid = 0, n_close = 0;
+  int n_sm = 0;  // SMs of the plan's device (k_dlp block sizes)
   int32_t *far_lin = nullptr, *mid_lin = nullptr, *close_lin = nullptr;
   double* close_geo = nullptr;  // [n_close][5]: foot x, y, normal x, y, theta
   double* close_w = nullptr;    // [n_close][MP]
@@ -345,6 +346,7 @@ __global__ void k_node_coef(int N, const double* x1, const double* y1, const dou
 }
 
 // v at listed grid points by the trapezoidal sum over N nodes; u = u_p + v there.
+// Blocks of 64, 128 or 256 threads (dlp_block), tiles of 256 nodes.
 // pos: per node (ix, iy, fx_hi, fx_lo), (fy_hi, fy_lo, -, -) in grid units.
 __global__ void __launch_bounds__(256) k_dlp(int n_pts, const int32_t* lin, int nx, double inv_h,
                                              int N, const float4* pos, const float4* ab,
@@ -357,10 +359,10 @@ __global__ void __launch_bounds__(256) k_dlp(int n_pts, const int32_t* lin, int 
   dfl acc = {0.f, 0.f};
   for (int t0 = 0; t0 < N; t0 += 256) {
     __syncthreads();
-    if (t0 + (int)threadIdx.x < N) {
-      s0[threadIdx.x] = pos[2 * (t0 + threadIdx.x)];
-      s1[threadIdx.x] = pos[2 * (t0 + threadIdx.x) + 1];
-      sc[threadIdx.x] = ab[t0 + threadIdx.x];
+    for (int q = threadIdx.x; q < 256 && t0 + q < N; q += blockDim.x) {
+      s0[q] = pos[2 * (t0 + q)];
+      s1[q] = pos[2 * (t0 + q) + 1];
+      sc[q] = ab[t0 + q];
     }
     __syncthreads();
     const int cnt = min(256, N - t0);
@@ -538,6 +540,8 @@ fc2d_status poisson_setup(fc2d_plan_s* p, int Nb) {
   auto* P = new PoissonState();
   P->Nb = Nb;
   P->MP = MP;
+  if (cudaDeviceGetAttribute(&P->n_sm, cudaDevAttrMultiProcessorCount, p->device) != cudaSuccess)
+    P->n_sm = 0;
   const Curve& cv = p->curve;
   const double a0 = p->grid.a0, b0 = p->grid.b0, h = p->grid.h;
   const double two_pi = 2.0 * M_PI;
@@ -707,6 +711,28 @@ fc2d_status poisson_setup(fc2d_plan_s* p, int Nb) {
 }
 
 // GMRES (no restart) for A phi = g on device vectors, host-side Hessenberg least squares.
+// Block size of a k_dlp launch over n points.  When all blocks of a launch are resident
+// at once (at most 2048 threads and, with 12 KB of node tiles each, 16 blocks per SM),
+// an SM's share is ceil(blocks / n_sm) blocks and the launch takes as long as the
+// largest share; take the size (256, 128 or 64 threads) with the smallest largest
+// share of points, the larger block on ties (fewer loads of each node tile).  Larger
+// launches run in waves that the block scheduler balances: 256 threads.
+static int dlp_block(int64_t n, int n_sm) {
+  if (n_sm <= 0) return 256;
+  int best = 256;
+  int64_t cost = INT64_MAX;
+  for (int bs : {256, 128, 64}) {
+    const int64_t blocks = (n + bs - 1) / bs;
+    if (blocks > (int64_t)n_sm * std::min(2048 / bs, 16)) continue;
+    const int64_t c = (blocks + n_sm - 1) / n_sm * bs;
+    if (c < cost) {
+      cost = c;
+      best = bs;
+    }
+  }
+  return best;
+}
+
 static fc2d_status gmres(PoissonState* P, cudaStream_t s, double tol) {
   const int n = P->Nb;
   const unsigned gb = (unsigned)((n + 255) / 256);
@@ -843,15 +869,19 @@ fc2d_status poisson_solve(fc2d_plan_s* p, int n_f, const double* fg, const doubl
                                                             P->abR);
     {
       ProfScope ps(p, "dlp_far", s);
-      if (P->n_far)
-        k_dlp<<<(unsigned)((P->n_far + 255) / 256), 256, 0, s>>>(
+      if (P->n_far) {
+        const int bs = dlp_block(P->n_far, P->n_sm);
+        k_dlp<<<(unsigned)((P->n_far + bs - 1) / bs), bs, 0, s>>>(
             (int)P->n_far, P->far_lin, nx, 1.0 / h, Nb, P->posB, P->ab, uf);
+      }
     }
     {
       ProfScope ps(p, "dlp_near", s);
-      if (P->n_mid)
-        k_dlp<<<(unsigned)((P->n_mid + 255) / 256), 256, 0, s>>>(
+      if (P->n_mid) {
+        const int bs = dlp_block(P->n_mid, P->n_sm);
+        k_dlp<<<(unsigned)((P->n_mid + bs - 1) / bs), bs, 0, s>>>(
             (int)P->n_mid, P->mid_lin, nx, 1.0 / h, NR, P->posR, P->abR, uf);
+      }
       if (P->n_close) {
         // boundary values g - u_p: reuse ghat for their coefficients
         k_density_dft<<<(unsigned)((Nb / 2 + 1 + 127) / 128), 128, 0, s>>>(
