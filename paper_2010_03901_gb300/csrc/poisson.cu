@@ -46,7 +46,9 @@ struct PoissonState {
   int32_t *ui0 = nullptr, *uj0 = nullptr;                               // [Nb]
   double *uwx = nullptr, *uwy = nullptr;                                // [Nb][MP]
   int64_t n_far = 0, n_mid = 0, n_close = 0;
-  int n_sm = 0;  // SMs of the plan's device (k_dlp block sizes)
+  int n_sm = 0;                 // SMs of the plan's device
+  int s_far = 1, s_mid = 1;     // node splits of the far and mid point sums (dlp_splits)
+  double* part = nullptr;       // [S][n] partial sums of a split launch
   int32_t *far_lin = nullptr, *mid_lin = nullptr, *close_lin = nullptr;
   double* close_geo = nullptr;  // [n_close][5]: foot x, y, normal x, y, theta
   double* close_w = nullptr;    // [n_close][MP]
@@ -346,26 +348,30 @@ __global__ void k_node_coef(int N, const double* x1, const double* y1, const dou
 }
 
 // v at listed grid points by the trapezoidal sum over N nodes; u = u_p + v there.
-// Blocks of 64, 128 or 256 threads (dlp_block), tiles of 256 nodes.
+// Blocks of 256 points, tiles of 256 nodes; blockIdx.y picks the node range of a split
+// launch (gridDim.y ranges, partial sums to part[blockIdx.y][n]; part NULL: no split).
 // pos: per node (ix, iy, fx_hi, fx_lo), (fy_hi, fy_lo, -, -) in grid units.
 __global__ void __launch_bounds__(256) k_dlp(int n_pts, const int32_t* lin, int nx, double inv_h,
                                              int N, const float4* pos, const float4* ab,
-                                             double* u) {
+                                             double* u, double* part) {
   __shared__ float4 s0[256], s1[256], sc[256];
   int n = blockIdx.x * blockDim.x + threadIdx.x;
   bool act = n < n_pts;
   int l = act ? lin[n] : 0;
   const float pi = (float)(l % nx), pj = (float)(l / nx);
+  // node range of this block row (the whole set when the launch is not split)
+  const int k0 = (int)((int64_t)N * blockIdx.y / gridDim.y);
+  const int k1 = (int)((int64_t)N * (blockIdx.y + 1) / gridDim.y);
   dfl acc = {0.f, 0.f};
-  for (int t0 = 0; t0 < N; t0 += 256) {
+  for (int t0 = k0; t0 < k1; t0 += 256) {
     __syncthreads();
-    for (int q = threadIdx.x; q < 256 && t0 + q < N; q += blockDim.x) {
+    for (int q = threadIdx.x; q < 256 && t0 + q < k1; q += blockDim.x) {
       s0[q] = pos[2 * (t0 + q)];
       s1[q] = pos[2 * (t0 + q) + 1];
       sc[q] = ab[t0 + q];
     }
     __syncthreads();
-    const int cnt = min(256, N - t0);
+    const int cnt = min(256, k1 - t0);
     for (int k = 0; k < cnt; ++k) {
       const float4 a = s0[k], b = s1[k], c = sc[k];
       const dfl dx = int_minus(pi - a.x, a.z, a.w), dy = int_minus(pj - a.y, b.x, b.y);
@@ -374,7 +380,20 @@ __global__ void __launch_bounds__(256) k_dlp(int n_pts, const int32_t* lin, int 
       acc = fast_two_sum(s.hi, s.lo + (acc.lo + term.lo));
     }
   }
-  if (act) u[l] += ((double)acc.hi + (double)acc.lo) * inv_h;
+  if (!act) return;
+  const double v = (double)acc.hi + (double)acc.lo;
+  if (part) part[(size_t)blockIdx.y * n_pts + n] = v;
+  else u[l] += v * inv_h;
+}
+
+// A split k_dlp launch's S partial sums per point, added in node-range order: u += sum / h.
+__global__ void __launch_bounds__(256) k_dlp_combine(int n_pts, const int32_t* lin, int S,
+                                                     const double* part, double inv_h, double* u) {
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= n_pts) return;
+  double v = 0.0;
+  for (int y = 0; y < S; ++y) v += part[(size_t)y * n_pts + n];
+  u[lin[n]] += v * inv_h;
 }
 
 // close points: one block per point; the MP - 1 refined sums along the normal (each
@@ -528,6 +547,20 @@ static void lagr(const double* nodes, int n, double t, double* w) {
       if (m != k) v *= (t - nodes[m]) / (nodes[k] - nodes[m]);
     w[k] = v;
   }
+}
+
+// Node splits of a k_dlp launch over n points and N nodes: each point's sum over the
+// nodes is cut into S consecutive node ranges, one row of blocks each (partial sums
+// combined by k_dlp_combine in range order), so that a launch over few points still
+// has about 48 warps per SM; below that the sums are bound by each warp's dependent
+// double-float chain rather than by issue.  At most 8 ranges of at least 1024 nodes.
+static int dlp_splits(int64_t n, int N, int n_sm) {
+  if (n_sm <= 0 || n <= 0) return 1;
+  const int64_t warps = (n + 255) / 256 * 8;
+  int64_t S = (48LL * n_sm + warps - 1) / warps;
+  S = std::min<int64_t>(S, 8);
+  S = std::min<int64_t>(S, std::max(1, N / 1024));
+  return (int)std::max<int64_t>(S, 1);
 }
 
 fc2d_status poisson_setup(fc2d_plan_s* p, int Nb) {
@@ -703,6 +736,11 @@ fc2d_status poisson_setup(fc2d_plan_s* p, int Nb) {
       (st = alloc(P, &P->phiR, NR)) || (st = alloc(P, &P->ab, (size_t)Nb)) ||
       (st = alloc(P, &P->abR, (size_t)NR)) || (st = alloc(P, &P->c00, 1024)))
     return fail(st);
+  P->s_far = dlp_splits(P->n_far, Nb, P->n_sm);
+  P->s_mid = dlp_splits(P->n_mid, NR, P->n_sm);
+  const size_t n_part = std::max(P->s_far > 1 ? (size_t)P->s_far * P->n_far : 0,
+                                 P->s_mid > 1 ? (size_t)P->s_mid * P->n_mid : 0);
+  if (n_part && (st = alloc(P, &P->part, n_part))) return fail(st);
   k_bie_matrix<<<dim3((Nb + 255) / 256, Nb), 256>>>(Nb, P->bx, P->by, P->bx1, P->by1, ddiag,
                                                     P->A);
   if ((st = cuda_check(cudaDeviceSynchronize(), "BIE matrix"))) return fail(st);
@@ -711,28 +749,6 @@ fc2d_status poisson_setup(fc2d_plan_s* p, int Nb) {
 }
 
 // GMRES (no restart) for A phi = g on device vectors, host-side Hessenberg least squares.
-// Block size of a k_dlp launch over n points.  When all blocks of a launch are resident
-// at once (at most 2048 threads and, with 12 KB of node tiles each, 16 blocks per SM),
-// an SM's share is ceil(blocks / n_sm) blocks and the launch takes as long as the
-// largest share; take the size (256, 128 or 64 threads) with the smallest largest
-// share of points, the larger block on ties (fewer loads of each node tile).  Larger
-// launches run in waves that the block scheduler balances: 256 threads.
-static int dlp_block(int64_t n, int n_sm) {
-  if (n_sm <= 0) return 256;
-  int best = 256;
-  int64_t cost = INT64_MAX;
-  for (int bs : {256, 128, 64}) {
-    const int64_t blocks = (n + bs - 1) / bs;
-    if (blocks > (int64_t)n_sm * std::min(2048 / bs, 16)) continue;
-    const int64_t c = (blocks + n_sm - 1) / n_sm * bs;
-    if (c < cost) {
-      cost = c;
-      best = bs;
-    }
-  }
-  return best;
-}
-
 static fc2d_status gmres(PoissonState* P, cudaStream_t s, double tol) {
   const int n = P->Nb;
   const unsigned gb = (unsigned)((n + 255) / 256);
@@ -867,21 +883,21 @@ fc2d_status poisson_solve(fc2d_plan_s* p, int n_f, const double* fg, const doubl
     k_node_coef<<<gb, 256, 0, s>>>(Nb, P->bx1, P->by1, P->phi, P->ab);
     k_node_coef<<<(unsigned)((NR + 255) / 256), 256, 0, s>>>(NR, P->rx1, P->ry1, P->phiR,
                                                             P->abR);
+    // the trapezoidal sums at n listed points over N nodes, split into S node ranges
+    auto dlp = [&](int64_t n, const int32_t* lin, int N, int S, const float4* pos,
+                   const float4* ab) {
+      const unsigned nb = (unsigned)((n + 255) / 256);
+      k_dlp<<<dim3(nb, (unsigned)S), 256, 0, s>>>((int)n, lin, nx, 1.0 / h, N, pos, ab, uf,
+                                                 S > 1 ? P->part : nullptr);
+      if (S > 1) k_dlp_combine<<<nb, 256, 0, s>>>((int)n, lin, S, P->part, 1.0 / h, uf);
+    };
     {
       ProfScope ps(p, "dlp_far", s);
-      if (P->n_far) {
-        const int bs = dlp_block(P->n_far, P->n_sm);
-        k_dlp<<<(unsigned)((P->n_far + bs - 1) / bs), bs, 0, s>>>(
-            (int)P->n_far, P->far_lin, nx, 1.0 / h, Nb, P->posB, P->ab, uf);
-      }
+      if (P->n_far) dlp(P->n_far, P->far_lin, Nb, P->s_far, P->posB, P->ab);
     }
     {
       ProfScope ps(p, "dlp_near", s);
-      if (P->n_mid) {
-        const int bs = dlp_block(P->n_mid, P->n_sm);
-        k_dlp<<<(unsigned)((P->n_mid + bs - 1) / bs), bs, 0, s>>>(
-            (int)P->n_mid, P->mid_lin, nx, 1.0 / h, NR, P->posR, P->abR, uf);
-      }
+      if (P->n_mid) dlp(P->n_mid, P->mid_lin, NR, P->s_mid, P->posR, P->abR);
       if (P->n_close) {
         // boundary values g - u_p: reuse ghat for their coefficients
         k_density_dft<<<(unsigned)((Nb / 2 + 1 + 127) / 128), 128, 0, s>>>(
