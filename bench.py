@@ -480,7 +480,7 @@ def poisson_star1024(fc2d, torch, dev, solves=3):
     # the far-field sums: (inside points - near points) x N_b terms, FP32-issue bound
     terms = (plan.n_inside - info["n_near"]) * len(xy)
     ach = terms * DLP_INSTR_PER_TERM / (kms["dlp_far"] * 1e-3) / 1e9
-    roof = {"bound": "alu", "kernel": "dlp_far (k_dlp, N_b nodes)", "achieved": ach,
+    roof = {"bound": "alu", "kernel": "dlp_far (k_dlp<false>, N_b nodes)", "achieved": ach,
             "peak": FP32_PEAK_GINSTR, "unit": "G FP32 instr/s", "frac": ach / FP32_PEAK_GINSTR,
             "terms": terms, "instr_per_term": DLP_INSTR_PER_TERM,
             "peak_source": "nominal: 152 SMs x 128 FP32 lanes x 2.07 GHz"}

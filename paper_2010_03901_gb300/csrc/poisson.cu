@@ -348,9 +348,10 @@ __global__ void k_node_coef(int N, const double* x1, const double* y1, const dou
 }
 
 // v at listed grid points by the trapezoidal sum over N nodes; u = u_p + v there.
-// Blocks of 256 points, tiles of 256 nodes; blockIdx.y picks the node range of a split
-// launch (gridDim.y ranges, partial sums to part[blockIdx.y][n]; part NULL: no split).
+// Blocks of 256 points, tiles of 256 nodes.  SPLIT: blockIdx.y picks one of gridDim.y
+// node ranges and the partial sums go to part[blockIdx.y][n] (k_dlp_combine adds them).
 // pos: per node (ix, iy, fx_hi, fx_lo), (fy_hi, fy_lo, -, -) in grid units.
+template <bool SPLIT>
 __global__ void __launch_bounds__(256) k_dlp(int n_pts, const int32_t* lin, int nx, double inv_h,
                                              int N, const float4* pos, const float4* ab,
                                              double* u, double* part) {
@@ -360,8 +361,8 @@ __global__ void __launch_bounds__(256) k_dlp(int n_pts, const int32_t* lin, int 
   int l = act ? lin[n] : 0;
   const float pi = (float)(l % nx), pj = (float)(l / nx);
   // node range of this block row (the whole set when the launch is not split)
-  const int k0 = (int)((int64_t)N * blockIdx.y / gridDim.y);
-  const int k1 = (int)((int64_t)N * (blockIdx.y + 1) / gridDim.y);
+  const int k0 = SPLIT ? (int)((int64_t)N * blockIdx.y / gridDim.y) : 0;
+  const int k1 = SPLIT ? (int)((int64_t)N * (blockIdx.y + 1) / gridDim.y) : N;
   dfl acc = {0.f, 0.f};
   for (int t0 = k0; t0 < k1; t0 += 256) {
     __syncthreads();
@@ -382,7 +383,7 @@ __global__ void __launch_bounds__(256) k_dlp(int n_pts, const int32_t* lin, int 
   }
   if (!act) return;
   const double v = (double)acc.hi + (double)acc.lo;
-  if (part) part[(size_t)blockIdx.y * n_pts + n] = v;
+  if (SPLIT) part[(size_t)blockIdx.y * n_pts + n] = v;
   else u[l] += v * inv_h;
 }
 
@@ -887,9 +888,13 @@ fc2d_status poisson_solve(fc2d_plan_s* p, int n_f, const double* fg, const doubl
     auto dlp = [&](int64_t n, const int32_t* lin, int N, int S, const float4* pos,
                    const float4* ab) {
       const unsigned nb = (unsigned)((n + 255) / 256);
-      k_dlp<<<dim3(nb, (unsigned)S), 256, 0, s>>>((int)n, lin, nx, 1.0 / h, N, pos, ab, uf,
-                                                 S > 1 ? P->part : nullptr);
-      if (S > 1) k_dlp_combine<<<nb, 256, 0, s>>>((int)n, lin, S, P->part, 1.0 / h, uf);
+      if (S == 1) {
+        k_dlp<false><<<nb, 256, 0, s>>>((int)n, lin, nx, 1.0 / h, N, pos, ab, uf, nullptr);
+        return;
+      }
+      k_dlp<true><<<dim3(nb, (unsigned)S), 256, 0, s>>>((int)n, lin, nx, 1.0 / h, N, pos, ab, uf,
+                                                       P->part);
+      k_dlp_combine<<<nb, 256, 0, s>>>((int)n, lin, S, P->part, 1.0 / h, uf);
     };
     {
       ProfScope ps(p, "dlp_far", s);
