@@ -67,3 +67,16 @@ def test_reference_arm_runs_on_rank_zero_only(monkeypatch, capsys):
     monkeypatch.setenv("WORLD_SIZE", "2")
     bench.main(["--impl", "reference", "--gpus", "2", "--steps", "1", "--warmup", "3"])
     assert capsys.readouterr().out == ""
+
+
+def test_bench_rejects_bad_arguments():
+    """bench.py refuses fewer than 3 warm-up steps and unknown extra lines, before any
+    GPU work; the default runs every extra line."""
+    sys.path.insert(0, ROOT)
+    import bench
+    for argv in (["--warmup", "2"], ["--extra", "poisson_star1024,nope"]):
+        with pytest.raises(SystemExit) as e:
+            bench.main(argv)
+        assert e.value.code == 2
+    assert set(bench.EXTRA_LINES) == {"poisson_star1024", "poisson_kite_d10",
+                                      "ff_interior_kite2048", "stars8_batched"}

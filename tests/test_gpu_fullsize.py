@@ -55,3 +55,47 @@ def test_full_size_spectrum(setup, precision):
         got = outs[k].cpu().numpy().astype(np.float64)[0]
         assert rel(got[..., 0] + 1j * got[..., 1], ref) < bar, k
     assert torch.equal(outs[0], outs[1]) and torch.equal(outs[0], outs[2])
+
+
+def test_full_size_fourier_forwarding_step():
+    """The Fourier Forwarding line's workload at its full size: the kite on a 2048^2
+    grid with d = 4, M = 7, c = 1, Delta T = 8h, u = 32 Gaussians of width 0.05 (seed 5)
+    and u_t = 0, in FP64, called back to back on the launching stream as bench.py times
+    it.  U_FC and its time derivative on the whole grid against the oracle's interior
+    step, with the bars of tests/test_gpu_wave.py (3e-11 of the extension's size,
+    through the propagator's operator norms)."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.fail("GPU test run without a CUDA device")
+    from oracle import fc2d as OF
+    from oracle import geometry as OG
+    from oracle import wave as OV
+    from oracle.fc_matrices import load_fc_matrices
+    from paper_2010_03901_gb300 import fc2d
+    w = W.workload("kite2048", d=4, M=7)
+    g, p = w.grid, w.params
+    geo = OG.build_geometry(w)
+    st = OF.matching_stencils(geo)
+    mats = load_fc_matrices(4, p.C, p.Z, p.n_os, p.n_r, p.m_F)
+    f0 = W.gaussian_sum(w.boundary, 32, 5, wmin=0.05, wmax=0.05, margin=0.3)
+    fg, fb = W.grid_values(w, f0), OF.boundary_values(geo, f0)
+    c, dT = 1.0, 8 * g.h
+    U, Ut = OV.interior_step(geo, mats, fg, fb, np.zeros_like(fg), np.zeros_like(fb), c, dT, st)
+    ef = np.abs(OF.extension(geo, mats, fg, fb, st)).max()
+
+    plan = fc2d.fc2d_plan(w.boundary.arrays(), (g.a0, g.b0, g.h, g.nx, g.ny),
+                          dict(d=4, M=7, B=p.B, k1=p.k1))
+    dev = torch.device("cuda:0")
+    u0 = torch.tensor(fg[None], device=dev)
+    ub = torch.tensor(fb[None], device=dev)
+    ut0, utb = torch.zeros_like(u0), torch.zeros_like(ub)
+    u1, ut1 = torch.empty_like(u0), torch.empty_like(u0)
+    stream = torch.cuda.current_stream()
+    for _ in range(2):
+        plan.fc2d_wave_interior(1, c, dT, u0, ub, ut0, utb, u1, ut1, stream)
+    plan.fc2d_sync_status(stream)
+    w_max = OV.frequencies(g, c).max()
+    eu = np.abs(u1.cpu().numpy()[0] - U).max()
+    et = np.abs(ut1.cpu().numpy()[0] - Ut).max()
+    assert eu < 3e-11 * ef, (eu, ef)
+    assert et < 3e-11 * w_max * ef, (et, w_max, ef)
