@@ -86,3 +86,79 @@ def test_graph_replay_equals_eager(stars):
     for (plan, *_), e, (*_, fh) in zip(runs, eager, runs):
         plan.fc2d_sync_status()
         assert torch.equal(e, fh)
+
+
+# --------------------------------------------------------------------------- #
+# The whole eight-star workload at its full size, as bench.py times it
+# --------------------------------------------------------------------------- #
+FULL_DOMAINS = (3, 4, 0)   # 2048^2, 1536^2 = 2^9 3 and 640^2 = 2^7 5
+FULL_SAMPLED = (0, 31)
+
+
+@pytest.fixture(scope="module")
+def full_group():
+    """Inputs of all eight stars (32 functions each) on the device, and the oracle's
+    spectra of the sampled functions on three of them."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.fail("GPU test run without a CUDA device")
+    from paper_2010_03901_gb300 import fc2d
+    dev = torch.device("cuda:0")
+    stars = W.stars8()
+    inputs = []
+    for i, w in enumerate(stars):
+        g, p = w.grid, w.params
+        probe = fc2d.fc2d_plan(w.boundary.arrays(), (g.a0, g.b0, g.h, g.nx, g.ny),
+                               dict(B=p.B, k1=p.k1))
+        xy = probe.fc2d_boundary_points()
+        probe.fc2d_destroy()
+        fs = W.star_functions(w, i, N_F)
+        xs, ys = g.coords()
+        fg = torch.empty((N_F, g.ny, g.nx), dtype=torch.float64, device=dev)
+        for m, t in enumerate(fs):
+            fg[m].copy_(torch.from_numpy(W.trig_grid(t, xs, ys)))
+        fb = torch.tensor(np.stack([t(xy[:, 0], xy[:, 1]) for t in fs]), device=dev)
+        inputs.append((w, fs, fg, fb))
+    mats = load_fc_matrices()
+    refs = {}
+    for i in FULL_DOMAINS:
+        w, fs = inputs[i][0], inputs[i][1]
+        geo = OG.build_geometry(w)
+        st = OF.matching_stencils(geo)
+        xs, ys = w.grid.coords()
+        for m in FULL_SAMPLED:
+            refs[i, m] = OF.coefficients(OF.extension(geo, mats, W.trig_grid(fs[m], xs, ys),
+                                                      OF.boundary_values(geo, fs[m]), st))
+    return torch, fc2d, inputs, refs
+
+
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+def test_full_size_star_group_against_oracle(full_group, precision):
+    """One fc2d_group_extend_coeffs call over all eight stars (256^2 to 2048^2, four of
+    them not powers of two) with 32 functions each, captured and then replayed as
+    bench.py times it; sampled functions of three domains against the oracle (1e-12
+    FP64, 1e-6 mixed relative max-norm)."""
+    torch, fc2d, inputs, refs = full_group
+    prec = fc2d.FC2D_FP64 if precision == "fp64" else fc2d.FC2D_MIXED
+    dt = torch.float64 if precision == "fp64" else torch.float32
+    plans, outs = [], []
+    for w, fs, fg, fb in inputs:
+        g, p = w.grid, w.params
+        plans.append(fc2d.fc2d_plan(w.boundary.arrays(), (g.a0, g.b0, g.h, g.nx, g.ny),
+                                    dict(B=p.B, k1=p.k1), precision=prec))
+        outs.append(torch.zeros((N_F, g.ny, g.nx // 2 + 1, 2), dtype=dt, device=fg.device))
+    grp = fc2d.fc2d_group_create(plans)
+    args = ([N_F] * 8, [x[2] for x in inputs], [x[3] for x in inputs], outs)
+    for _ in range(2):  # capture, then replay
+        grp.fc2d_group_extend_coeffs(*args)
+    torch.cuda.synchronize()
+    for pl in plans:
+        pl.fc2d_sync_status()
+    tol = 1e-12 if precision == "fp64" else 1e-6
+    for (i, m), ref in refs.items():
+        got = outs[i][m].cpu().numpy().astype(np.float64)
+        gm = got[..., 0] + 1j * got[..., 1]
+        assert rel(gm, ref) < tol, (inputs[i][0].name, m, rel(gm, ref))
+    grp.fc2d_group_destroy()
+    for pl in plans:
+        pl.fc2d_destroy()
