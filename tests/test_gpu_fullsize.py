@@ -3,7 +3,8 @@ y = 1.5 sin t on a 4096^2 grid with 8192 normals, f a sum of 16 Gaussians (seed 
 the launch configuration bench.py times (fc2d_extend_coeffs back to back on different
 input and output buffers).  The whole half spectrum is compared with the
 oracle's: 1e-6 (mixed), 1e-12 (FP64) relative max-norm, and the compact-input call
-must give the same spectrum bit for bit."""
+must give the same spectrum bit for bit.  The same from interior data only (no
+boundary values), and the Fourier Forwarding line's step at its full size."""
 import numpy as np
 import pytest
 
@@ -25,7 +26,7 @@ def setup():
     ref = bench.oracle_step(w, geo, st, mats, f)[0]
     fg = W.grid_values(w, f)
     fb = OF.boundary_values(geo, f)
-    return torch, w, fg, fb, ref
+    return torch, w, fg, fb, ref, geo, mats
 
 
 def rel(a, b):
@@ -34,7 +35,7 @@ def rel(a, b):
 
 @pytest.mark.parametrize("precision", ["mixed", "fp64"])
 def test_full_size_spectrum(setup, precision):
-    torch, w, fg, fb, ref = setup
+    torch, w, fg, fb, ref, *_ = setup
     from paper_2010_03901_gb300 import fc2d
     g, p = w.grid, w.params
     prec = fc2d.FC2D_FP64 if precision == "fp64" else fc2d.FC2D_MIXED
@@ -99,3 +100,42 @@ def test_full_size_fourier_forwarding_step():
     et = np.abs(ut1.cpu().numpy()[0] - Ut).max()
     assert eu < 3e-11 * ef, (eu, ef)
     assert et < 3e-11 * w_max * ef, (et, w_max, ef)
+
+
+@pytest.fixture(scope="module")
+def interior_ref(setup):
+    """The oracle's spectrum of the same f from interior data only (Remark 3.2 II),
+    with its extension's size and strip count for the FP64 bar."""
+    from oracle import fc2d as OF
+    torch, w, fg, fb, ref, geo, mats = setup
+    st = OF.matching_stencils(geo, interior=True)
+    ext = OF.extension(geo, mats, fg, None, st)
+    return OF.coefficients(ext), float(np.abs(ext).max()), len(geo.strip_lin)
+
+
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+def test_full_size_interior_data_only(setup, interior_ref, precision):
+    """f_bdry NULL at the full size, called back to back as bench.py times the headline.
+    Bars as in tests/test_gpu_interior.py: the interior-data strip values' 2e-10
+    carried through the normalised DFT (at least 1e-12) in FP64, 1e-6 mixed."""
+    torch, w, fg, fb, ref, *_ = setup
+    ref_i, ext_max, n_strip = interior_ref
+    from paper_2010_03901_gb300 import fc2d
+    g, p = w.grid, w.params
+    prec = fc2d.FC2D_FP64 if precision == "fp64" else fc2d.FC2D_MIXED
+    plan = fc2d.fc2d_plan(w.boundary.arrays(), (g.a0, g.b0, g.h, g.nx, g.ny),
+                          dict(B=p.B, k1=p.k1), precision=prec)
+    dev = torch.device("cuda:0")
+    dt = torch.float64 if precision == "fp64" else torch.float32
+    tg = torch.tensor(fg[None], device=dev)
+    outs = [torch.zeros((1, g.ny, g.nx // 2 + 1, 2), dtype=dt, device=dev) for _ in range(2)]
+    for out in outs:
+        plan.fc2d_extend_coeffs(1, tg, None, out)
+    plan.fc2d_sync_status()
+    if precision == "fp64":
+        bar = max(1e-12, 2e-10 * ext_max * n_strip / (g.nx * g.ny) / np.abs(ref_i).max())
+    else:
+        bar = 1e-6
+    got = outs[1].cpu().numpy().astype(np.float64)[0]
+    assert rel(got[..., 0] + 1j * got[..., 1], ref_i) < bar, (rel(got[..., 0] + 1j * got[..., 1], ref_i), bar)
+    assert torch.equal(outs[0], outs[1])
