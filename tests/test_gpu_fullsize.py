@@ -4,7 +4,8 @@ the launch configuration bench.py times (fc2d_extend_coeffs back to back on diff
 input and output buffers).  The whole half spectrum is compared with the
 oracle's: 1e-6 (mixed), 1e-12 (FP64) relative max-norm, and the compact-input call
 must give the same spectrum bit for bit.  The same from interior data only (no
-boundary values), and the Fourier Forwarding line's step at its full size."""
+boundary values) and for a complex f, and the Fourier Forwarding line's step at its
+full size."""
 import numpy as np
 import pytest
 
@@ -26,7 +27,7 @@ def setup():
     ref = bench.oracle_step(w, geo, st, mats, f)[0]
     fg = W.grid_values(w, f)
     fb = OF.boundary_values(geo, f)
-    return torch, w, fg, fb, ref, geo, mats
+    return torch, w, fg, fb, ref, geo, mats, st
 
 
 def rel(a, b):
@@ -107,7 +108,7 @@ def interior_ref(setup):
     """The oracle's spectrum of the same f from interior data only (Remark 3.2 II),
     with its extension's size and strip count for the FP64 bar."""
     from oracle import fc2d as OF
-    torch, w, fg, fb, ref, geo, mats = setup
+    torch, w, fg, fb, ref, geo, mats, _ = setup
     st = OF.matching_stencils(geo, interior=True)
     ext = OF.extension(geo, mats, fg, None, st)
     return OF.coefficients(ext), float(np.abs(ext).max()), len(geo.strip_lin)
@@ -139,3 +140,39 @@ def test_full_size_interior_data_only(setup, interior_ref, precision):
     got = outs[1].cpu().numpy().astype(np.float64)[0]
     assert rel(got[..., 0] + 1j * got[..., 1], ref_i) < bar, (rel(got[..., 0] + 1j * got[..., 1], ref_i), bar)
     assert torch.equal(outs[0], outs[1])
+
+
+@pytest.fixture(scope="module")
+def complex_ref(setup):
+    """A complex f on the same kite, f = (16 Gaussians) + i exp(sin x) cos y with its
+    boundary values, and the oracle's full spectrum of it."""
+    from oracle import fc2d as OF
+    torch, w, fg, fb, ref, geo, mats, st = setup
+    gi = W.grid_values(w, W.f_expsincos)
+    bi = OF.boundary_values(geo, W.f_expsincos)
+    ext = OF.extension_complex(geo, mats, fg + 1j * gi, fb + 1j * bi, st)
+    return gi, bi, OF.coefficients_complex(ext)
+
+
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+def test_full_size_complex_f(setup, complex_ref, precision):
+    """fc2d_extend_coeffs_complex at the full size: the whole [4096][4096] spectrum
+    against the oracle's complex extension and full DFT (1e-12 FP64, 1e-6 mixed, the
+    real path's bars: the full spectrum holds the two half spectra's numbers)."""
+    torch, w, fg, fb, *_ = setup
+    gi, bi, ref_c = complex_ref
+    from paper_2010_03901_gb300 import fc2d
+    g, p = w.grid, w.params
+    prec = fc2d.FC2D_FP64 if precision == "fp64" else fc2d.FC2D_MIXED
+    plan = fc2d.fc2d_plan(w.boundary.arrays(), (g.a0, g.b0, g.h, g.nx, g.ny),
+                          dict(B=p.B, k1=p.k1), precision=prec)
+    dev = torch.device("cuda:0")
+    dt = torch.float64 if precision == "fp64" else torch.float32
+    tg = torch.tensor(np.stack([fg, gi])[None], device=dev)
+    tb = torch.tensor(np.stack([fb, bi])[None], device=dev)
+    fhat = torch.zeros((1, g.ny, g.nx, 2), dtype=dt, device=dev)
+    plan.fc2d_extend_coeffs_complex(1, tg, tb, fhat)
+    plan.fc2d_sync_status()
+    got = fhat.cpu().numpy().astype(np.float64)[0]
+    bar = 1e-12 if precision == "fp64" else 1e-6
+    assert rel(got[..., 0] + 1j * got[..., 1], ref_c) < bar
