@@ -56,7 +56,7 @@ KERNELS_PER_SCOPE = {("mixed", "fft_cols", 4096): 2}
 MEASURED_TRAFFIC = {
     ("mixed", "fft_cols"): 67670784 + 7692544 + 67690240 + 8772608,  # k_cols4k_a + k_cols4k_b
     ("mixed", "fft_rows_fused"): 70923264 + 18913792,
-    ("mixed", "gather_blend_interp_tc"): 34110208 + 0,
+    ("mixed", "gather_blend_interp_tc"): 34112000 + 0,
     ("fp64", "fft_rows_fused"): 72384768 + 75083008,
     ("fp64", "fft_cols"): 141867520 + 92843264,
     ("fp64", "gather_blend"): 9670144 + 9472,
