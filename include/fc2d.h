@@ -271,10 +271,12 @@ fc2d_status fc2d_wait_selftest(fc2d_plan_t plan, uint32_t polls, void* stream);
  * may be NULL: interior data only) / fhat_dev[i] as for that call, as one CUDA graph
  * launched on `stream`: each plan on its own branch, so the domains' kernels run
  * concurrently.  The graph is captured on the first call (the plans' workspaces are
- * allocated before the capture) and replayed while n_f and every pointer stay the same;
- * a call with other arguments captures anew.  Calls on one group must not overlap in
- * time on different streams (the plans' workspaces are shared).  The result equals the
- * separate calls bit for bit. */
+ * allocated before the capture) and replayed while n_f, every pointer and every plan's
+ * workspace stay the same; a call with other arguments, or after a direct call on a
+ * member plan grew that plan's workspace, captures anew.  A plan may appear once in a
+ * group (FC2D_ERR_ARG otherwise).  Calls on one group must not overlap in time on
+ * different streams (the plans' workspaces are shared).  The result equals the separate
+ * calls bit for bit. */
 typedef struct fc2d_group_s* fc2d_group_t;
 fc2d_status fc2d_group_create(const fc2d_plan_t* plans, int n, fc2d_group_t* out);
 fc2d_status fc2d_group_extend_coeffs(fc2d_group_t group, const int* n_f,

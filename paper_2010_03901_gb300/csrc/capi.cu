@@ -110,7 +110,12 @@ InterpArgs interp_args(fc2d_plan_s* p, int ldF) {
   return a;
 }
 
-RowArgs row_args(fc2d_plan_s* p, bool compact = false) {
+}  // namespace
+
+// Argument blocks shared with the allocation-free entry point (static_scratch.cu).
+namespace fc2d {
+
+RowArgs row_args(fc2d_plan_s* p, bool compact) {
   RowArgs a{};
   a.nx = p->grid.nx;
   a.ny = p->grid.ny;
@@ -150,6 +155,10 @@ fc2d_status check_nf(fc2d_plan_s* p, int n_f) {
     return set_error(FC2D_ERR_ARG, "n_f too large");
   return FC2D_OK;
 }
+
+}  // namespace fc2d
+
+namespace {
 
 fc2d_status launched(const char* what) { return cuda_check(cudaGetLastError(), what); }
 

@@ -6,6 +6,8 @@
 
 #include "../../include/fc2d.h"
 
+struct fc2d_plan_s;
+
 namespace fc2d {
 
 constexpr int kMaxD = 8;
@@ -164,5 +166,11 @@ void launch_wave_cols(const FftArgs& fa, int n_f, void* inter, double c, double 
 // the columns; c00 (NULL allowed) adds c00[f] (x^2 + y^2)/4.
 void launch_inverse_rows(const FftArgs& fa, int n_f, const void* inter, const double* c00,
                          double a0, double b0, double h, double* out, cudaStream_t s);
+
+// Argument blocks of a plan (capi.cu): the row pass (compact: f given at the inside
+// points only) and the DFT of both axes; check_nf validates a function count.
+RowArgs row_args(fc2d_plan_s* p, bool compact = false);
+FftArgs fft_args(fc2d_plan_s* p);
+fc2d_status check_nf(fc2d_plan_s* p, int n_f);
 
 }  // namespace fc2d

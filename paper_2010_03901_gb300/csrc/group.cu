@@ -2,7 +2,11 @@
 // one CUDA graph.  Each plan runs on its own branch (forked from the launching stream and
 // joined back), so the kernels of small domains run side by side instead of one after
 // another; the graph is captured on the first call and replayed while the arguments
-// (function counts and pointers) stay the same, re-captured when they change.
+// (function counts and pointers) and every plan's workspace (base and size) stay the
+// same, re-captured when any of them changes.  The workspace is part of the key because
+// the captured kernels hold its address: a later call on a member plan that needs more
+// workspace frees the old one and allocates another, and a replay of the old graph would
+// then read and write freed memory.
 #include <cuda_runtime.h>
 
 #include <cstring>
@@ -44,8 +48,13 @@ static void group_free(fc2d_group_s* g) {
 
 extern "C" fc2d_status fc2d_group_create(const fc2d_plan_t* plans, int n, fc2d_group_t* out) {
   if (!plans || n < 1 || !out) return set_error(FC2D_ERR_ARG, "fc2d_group_create: bad argument");
-  for (int i = 0; i < n; ++i)
+  for (int i = 0; i < n; ++i) {
     if (!plans[i]) return set_error(FC2D_ERR_ARG, "fc2d_group_create: null plan");
+    // the branches run concurrently on each plan's own workspace
+    for (int j = 0; j < i; ++j)
+      if (plans[j] == plans[i])
+        return set_error(FC2D_ERR_ARG, "fc2d_group_create: a plan appears twice");
+  }
   auto* g = new fc2d_group_s();
   g->plans.assign(plans, plans + n);
   bool ok = cudaStreamCreateWithFlags(&g->cap, cudaStreamNonBlocking) == cudaSuccess &&
@@ -115,9 +124,17 @@ extern "C" fc2d_status fc2d_group_extend_coeffs(fc2d_group_t g, const int* n_f,
   for (int i = 0; i < n; ++i) {
     if (n_f[i] < 1 || !f_grid_dev[i] || !fhat_dev[i])
       return set_error(FC2D_ERR_ARG, "fc2d_group_extend_coeffs: bad entry");
+    // grow the workspaces now (outside any capture), so that the key below holds the
+    // buffers the kernels will use
+    fc2d_status st = ensure_plan_workspace(g->plans[i], n_f[i]);
+    if (st) return st;
+  }
+  for (int i = 0; i < n; ++i) {
     kptr.push_back(f_grid_dev[i]);
     kptr.push_back(f_bdry_dev ? f_bdry_dev[i] : nullptr);
     kptr.push_back(fhat_dev[i]);
+    kptr.push_back(g->plans[i]->ws.base);
+    kptr.push_back(reinterpret_cast<const void*>(g->plans[i]->ws.bytes));
   }
   if (!g->exec || knf != g->key_nf || kptr != g->key_ptr) {
     g->key_nf.clear();

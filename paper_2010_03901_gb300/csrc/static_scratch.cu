@@ -54,8 +54,9 @@ using namespace fc2d;
 
 extern "C" fc2d_status fc2d_coeffs_static(fc2d_plan_t p, int n_f, const void* ext,
                                           void* fhat, void* stream) {
-  if (!p || !ext || !fhat) return set_error(FC2D_ERR_ARG, "fc2d_coeffs_static: null argument");
-  if (n_f < 1) return set_error(FC2D_ERR_ARG, "fc2d_coeffs_static: n_f must be >= 1");
+  fc2d_status st = check_nf(p, n_f);
+  if (st) return st;
+  if (!ext || !fhat) return set_error(FC2D_ERR_ARG, "fc2d_coeffs_static: null argument");
   const bool f64 = p->prm.precision == FC2D_FP64;
   const size_t pitch = row_pitch(p);
   const size_t need = (size_t)n_f * p->grid.ny * pitch * 2 * (f64 ? 8 : 4);
@@ -67,28 +68,13 @@ extern "C" fc2d_status fc2d_coeffs_static(fc2d_plan_t p, int n_f, const void* ex
   cudaError_t e = cudaSetDevice(p->device);
   if (e != cudaSuccess) return cuda_check(e, "fc2d_coeffs_static: cudaSetDevice");
   void* scratch = nullptr;
-  fc2d_status st = scratch_address(p->device, &scratch);
+  st = scratch_address(p->device, &scratch);
   if (st) return st;
   // The row pass writes every intermediate element the column pass reads, so nothing
-  // needs clearing between calls.
-  FftArgs fa{};
-  fa.nx = p->grid.nx;
-  fa.ny = p->grid.ny;
-  fa.pitch = (int)pitch;
-  fa.nrx = p->fx.n_radix;
-  fa.nry = p->fy.n_radix;
-  for (int i = 0; i < fa.nrx; ++i) fa.rx[i] = p->fx.radix[i];
-  for (int i = 0; i < fa.nry; ++i) fa.ry[i] = p->fy.radix[i];
-  fa.twx = f64 ? (const void*)p->fx.tw64 : (const void*)p->fx.tw32;
-  fa.twy = f64 ? (const void*)p->fy.tw64 : (const void*)p->fy.tw32;
-  fa.rtw = f64 ? (const void*)p->rtw64 : (const void*)p->rtw32;
-  fa.tsx = f64 ? (const void*)p->fx.tws64 : (const void*)p->fx.tws32;
-  fa.tsy = f64 ? (const void*)p->fy.tws64 : (const void*)p->fy.tws32;
-  fa.scale = 1.0 / ((double)p->grid.nx * p->grid.ny);
-  RowArgs ra{};
-  ra.nx = p->grid.nx;
-  ra.ny = p->grid.ny;
-  ra.grid_stride = (int64_t)p->grid.nx * p->grid.ny;
+  // needs clearing between calls.  The argument blocks are the plan's own, as in
+  // fc2d_coeffs.
+  const FftArgs fa = fft_args(p);
+  const RowArgs ra = row_args(p);
   cudaStream_t s = (cudaStream_t)stream;
   launch_fft_rows(fa, ra, n_f, f64, 0, ext, nullptr, nullptr, scratch, s);
   launch_fft_cols(fa, n_f, f64, scratch, fhat, s);

@@ -86,3 +86,38 @@ def test_group_interior_data_only(torch_cuda):
     torch.cuda.synchronize()
     for i in range(len(plans)):
         assert torch.equal(out[i], ref[i]), i
+
+
+def test_group_after_a_member_workspace_grew(torch_cuda):
+    """A direct call with more functions on a member plan replaces that plan's workspace;
+    the next group call must capture anew (the old graph holds the freed buffer) and
+    still equal separate calls bit for bit."""
+    torch = torch_cuda
+    from paper_2010_03901_gb300 import fc2d
+    plans, fg, fb, out, ref, n_f = _setup(torch, fc2d, fc2d.FC2D_FP64, 11)
+    grp = fc2d.fc2d_group_create(plans)
+    grp.fc2d_group_extend_coeffs(n_f, fg, fb, out)
+    torch.cuda.synchronize()
+    # four functions on plan 0 (the group gives it one): a larger workspace
+    big_g = fg[0].repeat(4, 1, 1).contiguous()
+    big_b = fb[0].repeat(4, 1).contiguous()
+    big_o = torch.zeros((4,) + tuple(out[0].shape[1:]), dtype=out[0].dtype, device=out[0].device)
+    plans[0].fc2d_extend_coeffs(4, big_g, big_b, big_o)
+    torch.cuda.synchronize()
+    for o in out:
+        o.zero_()
+    grp.fc2d_group_extend_coeffs(n_f, fg, fb, out)
+    for i, pl in enumerate(plans):
+        pl.fc2d_extend_coeffs(n_f[i], fg[i], fb[i], ref[i])
+    torch.cuda.synchronize()
+    for i in range(len(plans)):
+        assert torch.equal(out[i], ref[i]), i
+    grp.fc2d_group_destroy()
+
+
+def test_group_rejects_a_repeated_plan(torch_cuda):
+    torch = torch_cuda
+    from paper_2010_03901_gb300 import fc2d
+    plans, *_ = _setup(torch, fc2d, fc2d.FC2D_FP64, 13)
+    with pytest.raises(RuntimeError):
+        fc2d.fc2d_group_create([plans[0], plans[1], plans[0]])
