@@ -1,5 +1,9 @@
 """Oracle: Fourier Forwarding for the wave equation (Section 4.2, eqs. (4.7)-(4.12)).
 
+forward_wave (below) is the whole method: U_FC on the interior combined with the
+near-boundary solver U_B of ``oracle/wave_boundary.py`` by eq. (4.9), large step after
+large step.
+
 TEST INFRASTRUCTURE ONLY (see ``oracle/__init__.py``).
 
 u_tt = c^2 (u_xx + u_yy) with u = f, u_t = g at t = 0 (eq. (4.7)).  One large step of
@@ -47,4 +51,82 @@ def interior_step(geo, mats, f_grid, f_bdry, g_grid, g_bdry, c, t, stencils=None
     n = gr.nx * gr.ny
     u = np.fft.irfft2(a * n, s=(gr.ny, gr.nx))
     ut = np.fft.irfft2(at * n, s=(gr.ny, gr.nx))
+    return u, ut
+
+
+def forward_wave(geo, mats, band, c, n_large, u0, ut0, g_fun=None, gt_fun=None):
+    """The Fourier Forwarding solution (eq. (4.9)) after n_large large steps.
+
+    Large step Delta T = n_c h / c (delta = c Delta T = n_c h, Section 4.2).  For each
+    large step j (T_j = j Delta T):
+      1. F, G: the 2D-FC expansions (eq. (4.10)) of u(T_j) and u_t(T_j) on H cap Omega
+         with the Dirichlet data g(T_j) and its time derivative on the curve;
+      2. U_FC(T_j + s Delta t) (eqs. (4.8), (4.12)) at the interface points of U_B, by a
+         full inverse DFT at each small step s = 0..S, S = 8 n_c (the paper's faster
+         small-square procedure is not followed here);
+      3. S small steps of U_B (``oracle/wave_boundary.py``); U_B is continued across
+         large steps (the first small step of all uses the Taylor start);
+      4. u(T_{j+1}) = U_FC(T_{j+1}) where dist >= delta, U_B(T_{j+1}) where dist < delta
+         (eq. (4.9)); u_t(T_{j+1}) = dU_FC/dt there, and at the U_B points the central
+         difference (u^{N+1} - u^{N-1})/(2 Delta t) with u^{N+1} one further small step
+         taken with this large step's U_FC (valid at the interface points for
+         s = S + 1, since they lie farther than delta + h/8 from the curve); at slaved
+         points the boundary polynomial of the time derivatives.
+    g_fun(t), gt_fun(t): Dirichlet data and its time derivative at the plan's boundary
+    points (None: zero).  u0, ut0: [ny][nx] (values outside the domain are ignored).
+    Returns u, u_t on [ny][nx] (zero outside the domain)."""
+    from oracle import wave_boundary as WB
+    gr = geo.grid
+    h, ny, nx = gr.h, gr.ny, gr.nx
+    S = 8 * band.n_c
+    dT = band.n_c * h / c
+    dt = dT / S
+    zero_b = np.zeros(len(geo.bdry_x))
+    gval = g_fun if g_fun is not None else (lambda t: zero_b)
+    gtval = gt_fun if gt_fun is not None else (lambda t: zero_b)
+    w = frequencies(gr, c)
+    n = nx * ny
+    inside = geo.inside
+    near = inside & (band.dist < band.delta)
+    u = np.where(inside, u0, 0.0)
+    ut = np.where(inside, ut0, 0.0)
+    uu = u.ravel()[band.unknown_lin]
+    u_prev = f_prev = None
+    for j in range(n_large):
+        T = j * dT
+        Fh = F.coefficients(F.extension(geo, mats, u, gval(T)))
+        Gh = F.coefficients(F.extension(geo, mats, ut, gtval(T)))
+
+        def ufc(tau, deriv=False):
+            a, at = advance_modes(Fh, Gh, w, tau)
+            return np.fft.irfft2((at if deriv else a) * n, s=(ny, nx))
+
+        for s in range(S):
+            m = j * S + s
+            f = ufc(s * dt).ravel()[band.iface_lin]
+            g = gval(m * dt)
+            if m == 0:
+                un = WB.first_step(band, h, uu, ut.ravel()[band.unknown_lin], f, g, dt)
+            else:
+                un = WB.step(band, h, uu, u_prev, f, f_prev, g)
+            u_prev, uu, f_prev = uu, un, f
+        T1 = (j + 1) * dT
+        Ug, Utg = ufc(dT), ufc(dT, True)
+        fN, ftN = Ug.ravel()[band.iface_lin], Utg.ravel()[band.iface_lin]
+        gN, gtN = gval(T1), gtval(T1)
+        u_extra = WB.step(band, h, uu, u_prev, fN, f_prev, gN)
+        ut_u = (u_extra - u_prev) / (2 * dt)
+        u_new, ut_new = Ug.ravel().copy(), Utg.ravel().copy()
+        nr = near.ravel()
+        sel = nr[band.unknown_lin]
+        u_new[band.unknown_lin[sel]] = uu[sel]
+        ut_new[band.unknown_lin[sel]] = ut_u[sel]
+        if len(band.slaved_lin):
+            us = WB.slaved_values(band, uu, fN, gN)
+            uts = WB.slaved_values(band, ut_u, ftN, gtN)
+            sel = nr[band.slaved_lin]
+            u_new[band.slaved_lin[sel]] = us[sel]
+            ut_new[band.slaved_lin[sel]] = uts[sel]
+        u = np.where(inside, u_new.reshape(ny, nx), 0.0)
+        ut = np.where(inside, ut_new.reshape(ny, nx), 0.0)
     return u, ut
