@@ -582,6 +582,139 @@ def ff_interior_kite2048(fc2d, torch, dev, steps=20):
                          "flops": "4 column DFTs x 5 N log2 N, modal advance not counted"}}
 
 
+def fp64_peak(fc2d, torch, dev, iters=1 << 16):
+    """Measured FP64 rate (TFLOP/s): the library's fused multiply-add probe on
+    8 x 152 blocks of 256 threads, best of 3 timed launches (CUDA events), with the SM
+    clock sampled during them (a rate at another clock scales with it)."""
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    blocks = 8 * n_sm
+    out = torch.empty(blocks * 256, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream()
+    fc2d.fc2d_probe_fp64(out, blocks, 1024, stream)
+    clk = ClockSampler(dev.index or 0)
+    clk.start()
+    best = 0.0
+    for _ in range(3):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        flops = fc2d.fc2d_probe_fp64(out, blocks, iters, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        best = max(best, flops / (e0.elapsed_time(e1) * 1e-3) / 1e12)
+    return {"tflops": best, "clocks": clk.stop(), "how": f"{blocks} blocks x 256 threads x 8 "
+            f"independent FMA chains x {iters} steps, best of 3 (CUDA events)"}
+
+
+def _disk_eigenmode_error(fc2d, torch, dev, h=0.005, n_c=8, T_target=2.0):
+    """Fourier Forwarding of the disk eigenmode J_2(j r) cos(2 phi) cos(j t),
+    j = j_{2,3} (zero Dirichlet data), to t ~ 2: max error on the grid points inside."""
+    from scipy.special import jn_zeros, jv
+    j = float(jn_zeros(2, 3)[-1])
+    B = int(round(2 * math.pi / h / 8)) * 8
+    g0 = W.fit_grid_smooth(-1.0, 1.0, -1.0, 1.0, h)
+    g = W.Grid(a0=g0.a0 - 0.31 * h, b0=g0.b0 - 0.17 * h, h=h, nx=g0.nx, ny=g0.ny)
+    plan = fc2d.fc2d_plan(W.disk().arrays(), (g.a0, g.b0, g.h, g.nx, g.ny),
+                          dict(d=4, M=7, B=B, k1=h))
+    x, y = g.coords()
+    X, Y = np.meshgrid(x, y)
+    mode = lambda t: jv(2, j * np.hypot(X, Y)) * np.cos(2 * np.arctan2(Y, X)) * np.cos(j * t)
+    n_large = int(round(T_target / (n_c * h)))
+    T = n_large * n_c * h
+    u = torch.tensor(mode(0.0)[None], device=dev)
+    ut = torch.zeros_like(u)
+    plan.fc2d_forward_wave(1, 1.0, n_c, n_large, u, ut)
+    plan.fc2d_sync_status()
+    got = u.cpu().numpy()[0]
+    inside = X * X + Y * Y < 1.0
+    err = float(np.abs(got - mode(T))[inside & (got != 0)].max())
+    return {"grid": f"{g.nx}x{g.ny}", "h": h, "n_c": n_c, "t": T, "small_steps": n_large * 8 * n_c,
+            "max_abs_error": err}
+
+
+def ff_solve_kite2048(fc2d, torch, dev, n_large=2):
+    """The whole Fourier Forwarding solve (Section 4.2, eq. (4.9); fc2d_forward_wave): the
+    kite at 2048^2, d = 4, c = 1, n_c = 8 (Delta T = 8 h, 64 small steps of CFL 0.125
+    per large step), zero Dirichlet data, 32 initial conditions in one call (a Gaussian of
+    width 0.05 each, centres at least 0.35 inside the curve, seeds 50..81, u_t = 0), FP64.
+    One call of n_large large steps is timed between two events on the launching stream
+    after a warm-up call (the band and scratch are built there); the per-kernel times come
+    from a second, profiled call.  Beside it: the measured FP64 rate and the error of the
+    same solver against the exact Dirichlet eigenmode (2, 3) of the unit disk at t ~ 2."""
+    w = W.workload("kite2048", d=4, M=7)
+    g, p = w.grid, w.params
+    n_c, n_f, c = 8, 32, 1.0
+    plan = fc2d.fc2d_plan(w.boundary.arrays(), (g.a0, g.b0, g.h, g.nx, g.ny),
+                          dict(d=4, M=7, B=p.B, k1=p.k1))
+    fs = [W.gaussian_sum(w.boundary, 1, 50 + k, wmin=0.05, wmax=0.05, margin=0.35)
+          for k in range(n_f)]
+    U0 = torch.tensor(np.stack([W.grid_values(w, f) for f in fs]), device=dev)
+    u, ut = torch.empty_like(U0), torch.empty_like(U0)
+    stream = torch.cuda.current_stream()
+    t0 = time.time()
+    u.copy_(U0)
+    ut.zero_()
+    plan.fc2d_forward_wave(n_f, c, n_c, 1, u, ut, None, None, stream)
+    torch.cuda.synchronize()
+    first_call_s = time.time() - t0
+    u.copy_(U0)
+    ut.zero_()
+    clk = ClockSampler(dev.index or 0)
+    clk.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    plan.fc2d_forward_wave(n_f, c, n_c, n_large, u, ut, None, None, stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clocks = clk.stop()
+    ms = e0.elapsed_time(e1)
+    plan.fc2d_sync_status(stream)
+    got = u.cpu().numpy()
+    finite = bool(np.isfinite(got).all())
+    amp = float(np.abs(got).max())
+    # per-kernel times (a second call with events around each kernel)
+    u.copy_(U0)
+    ut.zero_()
+    plan.fc2d_profile(True)
+    plan.fc2d_profile_read()
+    plan.fc2d_forward_wave(n_f, c, n_c, n_large, u, ut, None, None, stream)
+    torch.cuda.synchronize()
+    plan.fc2d_profile(False)
+    prof = plan.fc2d_profile_read()
+    counts = plan.fc2d_wave_band_info(n_c)
+    S = 8 * n_c
+    small = n_large * S
+    peak = fp64_peak(fc2d, torch, dev)
+    kms = {k: {"launches": v[0], "ms_per_launch": v[1] / v[0], "ms_total": v[1]}
+           for k, v in prof.items()}
+    # dominant kernel: the modal advance + inverse column DFT (k_ff_cols) or the inverse
+    # rows; FLOPs of one launch for n_f functions: 5 N log2 N per length-N complex DFT
+    nh = g.nx // 2
+    flops = {"ff_cols": n_f * (nh + 1) * 5.0 * g.ny * math.log2(g.ny),
+             "inverse_rows": n_f * g.ny * (5.0 * nh * math.log2(nh) + 10.0 * (nh + 1))}
+    top = max(("ff_cols", "inverse_rows"), key=lambda k: kms.get(k, {}).get("ms_total", 0.0))
+    ach = flops[top] / (kms[top]["ms_per_launch"] * 1e-3) / 1e12
+    eig = _disk_eigenmode_error(fc2d, torch, dev)
+    return {"workload": f"kite 2048^2 (a=0.65, b=1.5), d = 4, c = 1, n_c = 8 (Delta T = 8 h), "
+                        f"zero Dirichlet data, {n_f} initial conditions (one Gaussian each, "
+                        "w = 0.05, centres >= 0.35 inside, seeds 50..81), u_t = 0, FP64",
+            "n_f": n_f, "large_steps": n_large, "small_steps": small,
+            "ms": ms, "ms_per_large_step": ms / n_large, "ms_per_small_step": ms / small,
+            "small_steps_per_s": small / (ms * 1e-3),
+            "function_small_steps_per_s": n_f * small / (ms * 1e-3),
+            "value": n_f * g.nx * g.ny * small / (ms * 1e-3), "unit": "grid-point small steps/s",
+            "band": {"unknowns": counts[0], "slaved": counts[1], "interface": counts[2],
+                     "near": counts[3]},
+            "first_call_s": first_call_s, "finite": finite, "max_abs_u_end": amp,
+            "clocks": clocks, "kernels": kms, "gpu_launches_per_call": sum(v[0] for v in prof.values()),
+            "roofline": {"bound": "alu", "kernel": top, "achieved": ach, "peak": peak["tflops"],
+                         "unit": "TFLOP/s", "frac": ach / peak["tflops"],
+                         "peak_source": "measured FP64 FMA rate (fp64_peak)",
+                         "flops": "5 N log2 N per length-N complex DFT of the launch"},
+            "fp64_peak": peak, "disk_eigenmode": eig,
+            "parity": "tests/test_gpu_ff.py (element-wise against the oracle)"}
+
+
 def stars8_batched(fc2d, torch, dev, replays=10):
     """Eight stars (grids 256^2..2048^2 by concavity), 32 trigonometric sums per domain,
     one fc2d_group_extend_coeffs call per step (one CUDA graph, a branch per domain);
@@ -738,6 +871,7 @@ def run_gpu(args):
 EXTRA_LINES = {"poisson_star1024": poisson_star1024,
                "poisson_kite_d10": poisson_kite_oscillatory,
                "ff_interior_kite2048": ff_interior_kite2048,
+               "ff_solve_kite2048": ff_solve_kite2048,
                "stars8_batched": stars8_batched}
 
 

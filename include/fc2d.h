@@ -264,6 +264,58 @@ fc2d_status fc2d_sync_status(fc2d_plan_t plan, void* stream);
  * block of 32 threads on `stream`, asynchronous. */
 fc2d_status fc2d_wait_selftest(fc2d_plan_t plan, uint32_t polls, void* stream);
 
+/* Fourier Forwarding solve (Section 4.2, eq. (4.9)), FP64 plans: the wave equation
+ * u_tt = c^2 (u_xx + u_yy) in the domain with Dirichlet data g on the curve, advanced by
+ * n_large large steps Delta T = n_c h / c from t = 0.  Each large step combines the
+ * interior propagator U_FC (the 2D-FC expansions of u(T_j), u_t(T_j), eqs. (4.10)-(4.12))
+ * with the near-boundary solver U_B: S = 8 n_c small steps Delta t = Delta T / S (CFL
+ * c Delta t / h = 0.125, second-order Taylor, Section 4.2.1) on the grid points within
+ * n_c h + 2h of the curve, Dirichlet data imposed by cubic boundary polynomials along
+ * the grid lines (the embedded-boundary closure the paper cites), interface values from
+ * U_FC at every small step (full inverse DFT), a fourth-difference dissipation that
+ * makes the small step stable.  At T_{j+1} the grid takes U_FC where the distance to
+ * the curve is >= n_c h and U_B elsewhere (eq. (4.9)); U_B continues across large steps.
+ *   u_dev, ut_dev  [n_f][ny][nx] in: u and u_t at t = 0 (values inside the domain used);
+ *                  out: u and u_t at t = n_large Delta T inside the domain, 0 outside.
+ *   g_dir_dev      [n_large S + 1][n_f][n_bdry]: g at t = m Delta t at the plan's boundary
+ *                  points (fc2d_boundary_points), or NULL for g = 0.
+ *   gt_dir_dev     [n_large + 1][n_f][n_bdry]: dg/dt at t = j Delta T, or NULL for 0.
+ * 1 <= n_c <= 256; ny <= 7264.  The band and its operators are built on the first call
+ * for a given n_c (host, synchronous) and kept in the plan; scratch is allocated on the
+ * first call for a larger n_f.  Asynchronous on `stream` otherwise. */
+fc2d_status fc2d_forward_wave(fc2d_plan_t plan, int n_f, double c, int n_c, int n_large,
+                              double* u_dev, double* ut_dev, const double* g_dir_dev,
+                              const double* gt_dir_dev, void* stream);
+
+/* U_B's sets for large-step width n_c h (Section 4.2 near-boundary solver):
+ * counts[4] = {unknowns (stepped points), slaved points (values from a boundary
+ * polynomial), interface points (U_FC values the operators read), points nearer than
+ * n_c h to the curve (where U_B is the solution)}.  fc2d_wave_band_points copies the
+ * grid linear indices j nx + i of each set, ascending, into host arrays (NULL skips). */
+fc2d_status fc2d_wave_band_info(fc2d_plan_t plan, int n_c, int64_t* counts);
+fc2d_status fc2d_wave_band_points(fc2d_plan_t plan, int n_c, int32_t* unknown_lin,
+                                  int32_t* slaved_lin, int32_t* iface_lin, int32_t* near_lin);
+
+/* One U_B small step with caller data (the step fc2d_forward_wave takes), for tests:
+ * u, u_prev, ut and out are [n_unknown][n_f] (function-minor), grid / grid_prev the
+ * U_FC grids [n_f][ny][nx] at the step's time and the one before (interface values),
+ * g the Dirichlet data [n_f][n_bdry] (NULL: zero).  mode 0: out = u + dt ut + (c dt)^2/2
+ * L(u); 1: out = 2u - u_prev + (c dt)^2 L(u) - 0.3 D(u - u_prev); 2: the mode-1 value v
+ * stored as (v - u_prev)/(2 dt).  c dt = h/8. */
+fc2d_status fc2d_wave_ub_step(fc2d_plan_t plan, int n_c, int n_f, int mode, double c,
+                              const double* u_dev, const double* u_prev_dev,
+                              const double* ut_dev, const double* grid_dev,
+                              const double* grid_prev_dev, const double* g_dev, double* out_dev,
+                              void* stream);
+
+/* FP64 throughput probe (no operation of the paper): `blocks` blocks of 256 threads on
+ * `stream`, each thread running 8 independent fused multiply-add chains of `iters`
+ * steps, writing one value per thread to out_dev [blocks * 256].  *flops receives the
+ * floating-point operations launched (2 per fused multiply-add); timing the launch with
+ * events gives the FP64 rate the Fourier Forwarding roofline divides by. */
+fc2d_status fc2d_probe_fp64(double* out_dev, int blocks, int64_t iters, double* flops,
+                            void* stream);
+
 /* Plan groups: the extension + DFT of several domains (uneven grids and function
  * counts) in one launch.  fc2d_group_create keeps the plans (not owned: destroy the
  * group before them).  fc2d_group_extend_coeffs runs fc2d_extend_coeffs of every plan

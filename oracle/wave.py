@@ -54,7 +54,8 @@ def interior_step(geo, mats, f_grid, f_bdry, g_grid, g_bdry, c, t, stencils=None
     return u, ut
 
 
-def forward_wave(geo, mats, band, c, n_large, u0, ut0, g_fun=None, gt_fun=None):
+def forward_wave(geo, mats, band, c, n_large, u0, ut0, g_fun=None, gt_fun=None,
+                 stencils=None):
     """The Fourier Forwarding solution (eq. (4.9)) after n_large large steps.
 
     Large step Delta T = n_c h / c (delta = c Delta T = n_c h, Section 4.2).  For each
@@ -67,6 +68,7 @@ def forward_wave(geo, mats, band, c, n_large, u0, ut0, g_fun=None, gt_fun=None):
       3. S small steps of U_B (``oracle/wave_boundary.py``); U_B is continued across
          large steps (the first small step of all uses the Taylor start);
       4. u(T_{j+1}) = U_FC(T_{j+1}) where dist >= delta, U_B(T_{j+1}) where dist < delta
+         (with the decision margin of ``oracle/wave_boundary.py``)
          (eq. (4.9)); u_t(T_{j+1}) = dU_FC/dt there, and at the U_B points the central
          difference (u^{N+1} - u^{N-1})/(2 Delta t) with u^{N+1} one further small step
          taken with this large step's U_FC (valid at the interface points for
@@ -74,6 +76,7 @@ def forward_wave(geo, mats, band, c, n_large, u0, ut0, g_fun=None, gt_fun=None):
          points the boundary polynomial of the time derivatives.
     g_fun(t), gt_fun(t): Dirichlet data and its time derivative at the plan's boundary
     points (None: zero).  u0, ut0: [ny][nx] (values outside the domain are ignored).
+    stencils: the matching stencils of the geometry (computed when None).
     Returns u, u_t on [ny][nx] (zero outside the domain)."""
     from oracle import wave_boundary as WB
     gr = geo.grid
@@ -87,15 +90,16 @@ def forward_wave(geo, mats, band, c, n_large, u0, ut0, g_fun=None, gt_fun=None):
     w = frequencies(gr, c)
     n = nx * ny
     inside = geo.inside
-    near = inside & (band.dist < band.delta)
+    near = inside & (band.dist < band.delta - WB.TIE * h)
     u = np.where(inside, u0, 0.0)
     ut = np.where(inside, ut0, 0.0)
     uu = u.ravel()[band.unknown_lin]
     u_prev = f_prev = None
+    st = stencils if stencils is not None else F.matching_stencils(geo)
     for j in range(n_large):
         T = j * dT
-        Fh = F.coefficients(F.extension(geo, mats, u, gval(T)))
-        Gh = F.coefficients(F.extension(geo, mats, ut, gtval(T)))
+        Fh = F.coefficients(F.extension(geo, mats, u, gval(T), st))
+        Gh = F.coefficients(F.extension(geo, mats, ut, gtval(T), st))
 
         def ufc(tau, deriv=False):
             a, at = advance_modes(Fh, Gh, w, tau)

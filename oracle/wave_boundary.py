@@ -26,6 +26,13 @@ library follows; every constant is named here):
   that side (below) evaluated at the point, at every time level.  When a point could be
   slaved from several sides, the closest crossing wins (ties: x before y, lower side
   first).
+* Decisions on a threshold carry a margin TIE = 2^-30 (in units of h): a point is in
+  the band if dist < delta + 2h - TIE h, U_B's solution point if dist < delta - TIE h,
+  slaved if xi < XI_MIN - TIE, and a later side replaces an earlier one only if its xi
+  is smaller by more than TIE.  Symmetric grids put points exactly on these thresholds
+  (the unit disk on a grid through the origin with h = 1/16 has points at distance
+  exactly 6h), where two correct evaluations of the distance or the crossing differ in
+  the last bit; the margin makes every implementation decide such points alike.
 * Boundary polynomial of a chord side.  The degree <= Q_DEG Lagrange interpolant through
   the crossing of that side (the Dirichlet datum) and the Q_DEG non-slaved chord points
   nearest to it; on a chord with fewer non-slaved points it takes all of them and the
@@ -71,6 +78,7 @@ DISS_P = 4      # order of the differences in the dissipation
 SIGMA = 0.3     # dissipation coefficient
 BAND_EXTRA = 2  # the band reaches delta + BAND_EXTRA h from the curve
 CFL = 0.125     # c Delta t / h
+TIE = 2.0 ** -30  # decision margin (below)
 
 
 def central_weights(hw: int) -> np.ndarray:
@@ -144,7 +152,7 @@ class _Builder:
         self.delta = n_c * g.h
         reach = self.delta + BAND_EXTRA * g.h
         self.dist = inside_distance(geo, reach)
-        self.band = self.ins & (self.dist < reach)
+        self.band = self.ins & (self.dist < reach - TIE * g.h)
         # slaving
         self.slave = {}
         for j, i in zip(*np.nonzero(self.band)):
@@ -157,7 +165,7 @@ class _Builder:
                     if cr is None:  # the point lies on the curve where this line touches it
                         continue
                     xi = abs(cr[0] - self._coord(j, i, axis)) / self.h
-                    if xi < XI_MIN and (best is None or xi < best[0]):
+                    if xi < XI_MIN - TIE and (best is None or xi < best[0] - TIE):
                         best = (xi, axis, side)
             if best is not None:
                 self.slave[(j, i)] = best[1:]

@@ -549,6 +549,45 @@ extern "C" fc2d_status fc2d_poisson(fc2d_plan_t p, int n_f, const double* fg, co
 // ------------------------------------------------------------------------- //
 // Fourier Forwarding interior propagator (Section 4.2)
 // ------------------------------------------------------------------------- //
+namespace fc2d {
+// The 2D-FC spectra (eq. (3.1), normalised) of n_f functions u and n_f functions ut
+// (grid values + boundary data, as fc2d_extend takes them) into spec
+// [2 n_f][ny][nx/2+1] complex: u's first, then ut's.  FP64 plans; uses the plan
+// workspace for 2 n_f functions.
+fc2d_status wave_spectra(fc2d_plan_s* p, int n_f, const double* u, const double* ub,
+                         const double* ut, const double* utb, void* spec, cudaStream_t s) {
+  Layout L = layout(p, 2 * n_f);
+  fc2d_status st = ensure_workspace(p, L.total);
+  if (st) return st;
+  const size_t pitch = row_pitch(p);
+  FftArgs fa = fft_args(p);
+  for (int half = 0; half < 2; ++half) {
+    const double* fg = half ? ut : u;
+    const double* fb = half ? utb : ub;
+    double* F = reinterpret_cast<double*>(ws(p, L.oF)) + (size_t)half * n_f * p->prm.B * (p->Cr + 1);
+    double* vals = reinterpret_cast<double*>(ws(p, L.ovals)) + (size_t)half * n_f * p->strip_lin.size();
+    double2* inter = reinterpret_cast<double2*>(ws(p, L.ointer)) + (size_t)half * n_f * p->grid.ny * pitch;
+    {
+      ProfScope ps(p, "gather_blend", s);
+      launch_gather_blend(gather_args(p, fg, fb, F, nullptr, nullptr), n_f, true, s);
+    }
+    {
+      ProfScope ps(p, "interp", s);
+      launch_interp(interp_args(p, p->Cr + 1), n_f, true, F, vals, s);
+    }
+    {
+      ProfScope ps(p, "fft_rows_fused", s);
+      launch_fft_rows(fa, row_args(p), n_f, true, 1, nullptr, fg, vals, inter, s);
+    }
+  }
+  {
+    ProfScope ps(p, "fft_cols", s);
+    launch_fft_cols(fa, 2 * n_f, true, ws(p, L.ointer), spec, s);
+  }
+  return launched("wave spectra");
+}
+}  // namespace fc2d
+
 extern "C" fc2d_status fc2d_wave_interior(fc2d_plan_t p, int n_f, double c, double t,
                                           const double* u0, const double* u0_bdry,
                                           const double* ut0, const double* ut0_bdry,

@@ -736,6 +736,8 @@ extern "C" fc2d_status fc2d_plan(const fc2d_boundary* boundary, const fc2d_grid*
   }
   row_off[ny] = off;
   p->n_bdry = off;
+  p->col_off = col_off;
+  p->row_off = row_off;
 
   // matching stencils (Section 3.2), with boundary data and (gidx_i, gw_i, wn_i) from
   // interior data only (Remark 3.2 II: stars from grid nodes alone, the foot value
@@ -986,6 +988,7 @@ extern "C" fc2d_status fc2d_strip_points(fc2d_plan_t p, int32_t* lin, double* th
 extern "C" void fc2d_destroy(fc2d_plan_t p) {
   if (!p) return;
   poisson_destroy(p);
+  wave_destroy(p);
   void* ptrs[] = {p->dev.Q, p->dev.Ar, p->dev.Ar_hi, p->dev.Ar_lo, p->dev.gidx, p->dev.gw,
                   p->dev.wn, p->dev.s_lin, p->dev.s_theta, p->dev.s_eta, p->dev.s_w,
                   p->dev.s_pb, p->dev.s_sb, p->dev.own[0].off, p->dev.own[0].k,

@@ -105,6 +105,9 @@ struct fc2d_plan_s {
   // host copies
   std::vector<double> Q, Ar;                 // d*d, Cr*d
   std::vector<double> bdry_xy;               // 2*n_bdry
+  // boundary points of column i's crossings: col_off[i] .. col_off[i+1] (y ascending),
+  // of row j's: row_off[j] .. row_off[j+1] (x ascending)
+  std::vector<int64_t> col_off, row_off;
   std::vector<int32_t> strip_lin;
   std::vector<double> strip_theta, strip_eta;
   std::vector<int32_t> row_iv_off, row_iv, row_strip_off;
@@ -124,6 +127,7 @@ struct fc2d_plan_s {
   std::vector<fc2d::ProfileRecord> prof;       // events of the current record
   std::vector<void*> event_pool;               // reusable cudaEvent_t
   void* poisson = nullptr;                     // Poisson tables (poisson.cu)
+  void* wave = nullptr;                        // Fourier Forwarding state (ff.cu)
 };
 
 namespace fc2d {
@@ -155,6 +159,9 @@ void poisson_destroy(fc2d_plan_s* p);
 int poisson_nb(const fc2d_plan_s* p);
 const double* poisson_nodes(const fc2d_plan_s* p);
 void poisson_stats(const fc2d_plan_s* p, int* iters, double* resid, int64_t* n_near);
+
+// Fourier Forwarding state (ff.cu)
+void wave_destroy(fc2d_plan_s* p);
 
 // kernel timing: bracket one launch with events when the plan is profiling
 struct ProfScope {

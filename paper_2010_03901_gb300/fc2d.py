@@ -83,7 +83,13 @@ def load_library(path: str = LIB_PATH):
         "fc2d_poisson_info": [P, P, P, P],
         "fc2d_poisson": [P, ct.c_int, P, P, P, P, P, P],
         "fc2d_wave_interior": [P, ct.c_int, ct.c_double, ct.c_double, P, P, P, P, P, P, P],
+        "fc2d_forward_wave": [P, ct.c_int, ct.c_double, ct.c_int, ct.c_int, P, P, P, P, P],
+        "fc2d_wave_band_info": [P, ct.c_int, P],
+        "fc2d_wave_band_points": [P, ct.c_int, P, P, P, P],
+        "fc2d_wave_ub_step": [P, ct.c_int, ct.c_int, ct.c_int, ct.c_double, P, P, P, P, P, P,
+                              P, P],
         "fc2d_profile": [P, ct.c_int],
+        "fc2d_probe_fp64": [P, ct.c_int, ct.c_int64, P, P],
         "fc2d_profile_read": [P, ct.c_int, P, P, P, P],
     }
     for name, args in sigs.items():
@@ -239,6 +245,30 @@ class Plan:
                                        _ptr(ut0), _ptr(ut0_bdry), _ptr(u_out), _ptr(ut_out),
                                        _stream(stream)))
 
+    def fc2d_forward_wave(self, n_f, c, n_c, n_large, u, ut, g_dir=None, gt_dir=None,
+                          stream=None):
+        _check(_lib.fc2d_forward_wave(self.handle, n_f, c, n_c, n_large, _ptr(u), _ptr(ut),
+                                      _ptr(g_dir), _ptr(gt_dir), _stream(stream)))
+
+    def fc2d_wave_band_info(self, n_c):
+        """(unknowns, slaved, interface, near) counts of U_B's band for n_c."""
+        counts = np.zeros(4, np.int64)
+        _check(_lib.fc2d_wave_band_info(self.handle, n_c, counts.ctypes.data))
+        return tuple(int(v) for v in counts)
+
+    def fc2d_wave_band_points(self, n_c):
+        """Grid linear indices of the unknowns, slaved, interface and near points."""
+        n = self.fc2d_wave_band_info(n_c)
+        arrs = [np.zeros(max(k, 1), np.int32) for k in n]
+        _check(_lib.fc2d_wave_band_points(self.handle, n_c, *[a.ctypes.data for a in arrs]))
+        return [a[:k] for a, k in zip(arrs, n)]
+
+    def fc2d_wave_ub_step(self, n_c, n_f, mode, c, u, u_prev, ut, grid, grid_prev, g, out,
+                          stream=None):
+        _check(_lib.fc2d_wave_ub_step(self.handle, n_c, n_f, mode, c, _ptr(u), _ptr(u_prev),
+                                      _ptr(ut), _ptr(grid), _ptr(grid_prev), _ptr(g), _ptr(out),
+                                      _stream(stream)))
+
     def fc2d_profile(self, enable=True):
         _check(_lib.fc2d_profile(self.handle, 1 if enable else 0))
 
@@ -308,6 +338,13 @@ class Group:
             self.fc2d_group_destroy()
         except Exception:
             pass
+
+
+def fc2d_probe_fp64(out, blocks, iters, stream=None):
+    """Launch the FP64 fused multiply-add probe; returns the flops it performs."""
+    flops = ct.c_double()
+    _check(_lib.fc2d_probe_fp64(_ptr(out), blocks, iters, ct.byref(flops), _stream(stream)))
+    return flops.value
 
 
 def fc2d_group_create(plans) -> Group:

@@ -11,7 +11,8 @@ EXE = os.path.join(ROOT, "_build", "host_plan_harness")
 
 def build():
     deps = [SRC] + [os.path.join(ROOT, "paper_2010_03901_gb300", "csrc", f)
-                    for f in ("plan.cpp", "plan_internal.h", "dd.h")]
+                    for f in ("plan.cpp", "plan_internal.h", "dd.h", "wave_band.cpp",
+                              "wave_band.h")]
     if os.path.exists(EXE) and all(os.path.getmtime(d) < os.path.getmtime(EXE) for d in deps):
         return EXE
     os.makedirs(os.path.dirname(EXE), exist_ok=True)
@@ -23,13 +24,16 @@ def build():
     return EXE
 
 
-def run(w):
+def run(w, n_c=None):
+    """The plan's host tables; with n_c also the Fourier Forwarding band (wb_*)."""
     exe = build()
     cx, sx, cy, sy = w.boundary.arrays()
     g, p = w.grid, w.params
     args = [str(len(cx))] + [repr(float(v)) for arr in (cx, sx, cy, sy) for v in arr]
     args += [repr(float(g.a0)), repr(float(g.b0)), repr(float(g.h)), str(g.nx), str(g.ny)]
     args += [str(v) for v in (p.d, p.C, p.Z, p.n_os, p.n_r, p.M, p.B, p.m_F)] + [repr(float(p.k1))]
+    if n_c is not None:
+        args.append(str(int(n_c)))
     out = subprocess.run([exe] + args, check=True, capture_output=True).stdout
     res = {}
     pos = out.index(b"\n")
@@ -40,12 +44,18 @@ def run(w):
     types = {8: np.float64, 4: np.int32}
     while pos < len(out):
         end = out.index(b"\n", pos)
+        if out[pos:end].startswith(b"wave_status"):
+            head = out[pos:end].decode().split(maxsplit=2)
+            res["wave_status"] = int(head[1])
+            res["wave_error"] = head[2] if len(head) > 2 else ""
+            pos = end + 1
+            continue
         name, n, sz = out[pos:end].decode().split()
         n, sz = int(n), int(sz)
         dt = types[sz]
         if name in ("row_iv_off", "row_iv", "strip_lin", "gidx", "gidx_c", "row_iv_coff",
-                    "gidx_i", "interior_ok"):
-            dt = np.int32
+                    "gidx_i", "interior_ok") or (name.startswith("wb_") and sz == 4):
+            dt = np.uint32 if name.endswith("_col") else np.int32
         arr = np.frombuffer(out[end + 1:end + 1 + n * sz], dtype=dt)
         res[name] = arr
         pos = end + 1 + n * sz + 1

@@ -38,6 +38,7 @@ static cudaError_t h_attr(int* v, int, int) {
 #define cudaDeviceGetAttribute(v, a, d) h_attr((v), (int)(a), (d))
 
 #include "../paper_2010_03901_gb300/csrc/plan.cpp"
+#include "../paper_2010_03901_gb300/csrc/wave_band.cpp"
 
 namespace fc2d {
 fc2d_status foot_newton_gpu(const Curve& c, const std::vector<double>& qx,
@@ -85,6 +86,7 @@ fc2d_status foot_newton_gpu(const Curve& c, const std::vector<double>& qx,
   return FC2D_OK;
 }
 void poisson_destroy(fc2d_plan_s*) {}
+void wave_destroy(fc2d_plan_s*) {}
 // interpolation weights are a GPU step of the plan; the harness leaves them unset
 fc2d_status interp_weights_gpu(int, int, int, int, double, int, const double*, const double*,
                                bool, void*, int32_t*, int32_t*) {
@@ -111,7 +113,7 @@ int main(int argc, char** argv) {
     std::printf("\n");
     return 0;
   }
-  // argv: n_modes cx.. sx.. cy.. sy.. a0 b0 h nx ny d C Z n_os n_r M B m_F k1
+  // argv: n_modes cx.. sx.. cy.. sy.. a0 b0 h nx ny d C Z n_os n_r M B m_F k1 [n_c]
   int a = 1;
   int nm = std::atoi(argv[a++]);
   std::vector<double> cx(nm), sx(nm), cy(nm), sy(nm);
@@ -157,5 +159,26 @@ int main(int argc, char** argv) {
   dump("wn_i", p->dev.wn_i, B * d * M);
   const int32_t ok = p->interior_ok ? 1 : 0;
   dump("interior_ok", &ok, 1);
+  if (a < argc) {  // optional: the Fourier Forwarding band for n_c
+    fc2d::WaveBand wb;
+    st = fc2d::build_wave_band(p, std::atoi(argv[a++]), wb);
+    std::printf("wave_status %d %s\n", (int)st, fc2d_last_error());
+    if (st) return 0;
+    dump("wb_unknown_lin", wb.unknown_lin.data(), wb.unknown_lin.size());
+    dump("wb_slaved_lin", wb.slaved_lin.data(), wb.slaved_lin.size());
+    dump("wb_unknown_dist", wb.unknown_dist.data(), wb.unknown_dist.size());
+    dump("wb_slaved_dist", wb.slaved_dist.data(), wb.slaved_dist.size());
+    dump("wb_iface_lin", wb.iface_lin.data(), wb.iface_lin.size());
+    dump("wb_near_lin", wb.near_lin.data(), wb.near_lin.size());
+    dump("wb_near_src", wb.near_src.data(), wb.near_src.size());
+    for (auto* m : {&wb.L, &wb.D, &wb.S}) {
+      const char* nm = m == &wb.L ? "L" : (m == &wb.D ? "D" : "S");
+      std::string o = std::string("wb_") + nm + "_off", c = std::string("wb_") + nm + "_col",
+                  w = std::string("wb_") + nm + "_w";
+      dump(o.c_str(), m->off.data(), m->off.size());
+      dump(c.c_str(), m->col.data(), m->col.size());
+      dump(w.c_str(), m->w.data(), m->w.size());
+    }
+  }
   return 0;
 }

@@ -53,6 +53,6 @@ def test_binding_names_match_the_abi():
     names = declared_symbols()
     methods = ({m for m in dir(fc2d.Plan) if m.startswith("fc2d_")} |
                {m for m in dir(fc2d.Group) if m.startswith("fc2d_")} |
-               {"fc2d_plan", "fc2d_group_create"})
+               {"fc2d_plan", "fc2d_group_create", "fc2d_probe_fp64"})
     skip = {"fc2d_plan_info", "fc2d_last_error", "fc2d_fc_matrices_compute"}
     assert (names - skip) <= methods | {"fc2d_destroy"}, names - methods

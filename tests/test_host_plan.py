@@ -194,3 +194,67 @@ def test_plan_rejects_bad_grids(grid, status, msg):
 def test_plan_rejects_parameters_out_of_range(params):
     r = host_plan.run(W.workload("disk128", **params))
     assert r["status"] == 1 and "parameter out of range" in r["error"], r["error"]
+
+
+# --------------------------------------------------------------------------- #
+# The Fourier Forwarding band (wave_band.cpp, on the CPU) against the oracle
+# --------------------------------------------------------------------------- #
+def _rows(off, col, w, iface_map=None):
+    rows = []
+    for r in range(len(off) - 1):
+        d = {}
+        for k in range(off[r], off[r + 1]):
+            c = int(col[k])
+            d[(c >> 30, c & ((1 << 30) - 1))] = w[k]
+        rows.append(d)
+    return rows
+
+
+def _oracle_rows(mats, iface_lin):
+    rows = []
+    for r in range(mats["u"].shape[0]):
+        d = {}
+        for kind, code in (("u", 0), ("f", 1), ("g", 2)):
+            m = mats[kind].getrow(r)
+            for c, v in zip(m.indices, m.data):
+                d[(code, int(iface_lin[c]) if kind == "f" else int(c))] = v
+        rows.append(d)
+    return rows
+
+
+@pytest.mark.parametrize("name,n_c", [("disk64", 4), ("kite160x144", 6), ("star200", 8)])
+def test_wave_band_equals_the_oracle(name, n_c):
+    """U_B's sets bit for bit; second-difference and slaved-point weights within 1e-12 of
+    each row's largest (the crossings, hence the boundary-polynomial nodes, come from
+    independent root finders); the dissipation D = B^T B / 2 to 1e-15."""
+    from oracle import wave_boundary as OWB
+    w = W.workload(name, d=4, M=7)
+    r = host_plan.run(w, n_c)
+    assert r["status"] == 0 and r["wave_status"] == 0, (r["error"], r.get("wave_error"))
+    geo = OG.build_geometry(w)
+    band = OWB.build_band(geo, n_c)
+    assert np.array_equal(r["wb_unknown_lin"], band.unknown_lin)
+    assert np.array_equal(r["wb_slaved_lin"], band.slaved_lin)
+    assert np.array_equal(np.sort(r["wb_iface_lin"]), np.sort(band.iface_lin))
+    assert np.abs(r["wb_unknown_dist"] - band.dist.ravel()[band.unknown_lin]).max() < 1e-14
+    near = np.nonzero((geo.inside & (band.dist < band.delta - OWB.TIE * w.grid.h)).ravel())[0]
+    assert np.array_equal(r["wb_near_lin"], near)
+    for nm, mats in (("L", band.L), ("S", band.S)):
+        a = _rows(r[f"wb_{nm}_off"], r[f"wb_{nm}_col"], r[f"wb_{nm}_w"])
+        b = _oracle_rows(mats, band.iface_lin)
+        assert len(a) == len(b)
+        for ra, rb in zip(a, b):
+            assert set(ra) == set(rb)
+            scale = max(abs(v) for v in rb.values())
+            assert max(abs(ra[k] - rb[k]) for k in rb) <= 1e-12 * scale
+    Bu, Bf = band.Bd["u"], band.Bd["f"]
+    Du, Df = (Bu.T @ Bu / 2).toarray(), (Bu.T @ Bf / 2).toarray()
+    col_of = {int(v): k for k, v in enumerate(band.iface_lin)}
+    a = _rows(r["wb_D_off"], r["wb_D_col"], r["wb_D_w"])
+    nnz = 0
+    for ri, ra in enumerate(a):
+        for (kind, idx), v in ra.items():
+            ref = Du[ri, idx] if kind == 0 else Df[ri, col_of[idx]]
+            assert abs(v - ref) <= 1e-15
+            nnz += 1
+    assert nnz == int((Du != 0).sum() + (Df != 0).sum())

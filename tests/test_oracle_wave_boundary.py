@@ -65,7 +65,7 @@ def test_closure_reproduces_cubics(name, h):
     # interface points are inside and farther
     inside = geo.inside.ravel()
     d = band.dist.ravel()
-    reach = band.delta + WB.BAND_EXTRA * h
+    reach = band.delta + WB.BAND_EXTRA * h - WB.TIE * h
     assert inside[band.unknown_lin].all() and (d[band.unknown_lin] < reach).all()
     assert inside[band.iface_lin].all() and (d[band.iface_lin] >= reach).all()
     assert len(set(band.unknown_lin) | set(band.slaved_lin)) == int((inside & (d < reach)).sum())
