@@ -280,7 +280,7 @@ fc2d_status fc2d_wait_selftest(fc2d_plan_t plan, uint32_t polls, void* stream);
  *   g_dir_dev      [n_large S + 1][n_f][n_bdry]: g at t = m Delta t at the plan's boundary
  *                  points (fc2d_boundary_points), or NULL for g = 0.
  *   gt_dir_dev     [n_large + 1][n_f][n_bdry]: dg/dt at t = j Delta T, or NULL for 0.
- * 1 <= n_c <= 256; ny <= 7264.  The band and its operators are built on the first call
+ * 1 <= n_c <= 256; ny <= 4842.  The band and its operators are built on the first call
  * for a given n_c (host, synchronous) and kept in the plan; scratch is allocated on the
  * first call for a larger n_f.  Asynchronous on `stream` otherwise. */
 fc2d_status fc2d_forward_wave(fc2d_plan_t plan, int n_f, double c, int n_c, int n_large,

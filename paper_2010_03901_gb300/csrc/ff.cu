@@ -36,6 +36,8 @@ namespace fc2d {
 
 fc2d_status wave_spectra(fc2d_plan_s* p, int n_f, const double* u, const double* ub,
                          const double* ut, const double* utb, void* spec, cudaStream_t s);
+bool launch_ff_cols_p2(const FftArgs& fa, int n_f, int n_out, const void* spec, void* out,
+                       double c, double tau, double Lx, double Ly, cudaStream_t s);
 
 namespace {
 
@@ -244,41 +246,51 @@ __global__ void k_zero_outside(int nx, int ny, int n_f, const int32_t* __restric
 
 // Modal advance of the normalised half spectra (F: spec[f], G: spec[n_f + f]) to time
 // tau and the inverse column DFT (a forward transform of the conjugate), into the
-// row-pass layout [n_out][ny][pitch] for the inverse real row DFT.  blockIdx.z = 0: a(tau)
-// into out[f]; 1: a'(tau) into out[n_f + f].  One block per (column, function, output).
+// row-pass layout [n_out][ny][pitch] for the inverse real row DFT: blockIdx.y = 0: a(tau)
+// into out[f]; 1: a'(tau) into out[n_f + f].  One block per (column, output) loops over
+// the functions, so the column's time factors (t0, t1) are computed once: a = F t0 + G t1
+// with (cos w tau, sin(w tau)/w), or (-w sin w tau, cos w tau) for a'; (1, tau) and (0, 1)
+// at w = 0.  Mixed-radix sizes; power-of-two columns take k_ff_cols_p2 (fft_pow2.cu).
 __global__ void __launch_bounds__(256) k_ff_cols(FftArgs fa, int n_f, const double2* __restrict__ spec,
                                                  double2* __restrict__ out, double c, double tau,
                                                  double Lx, double Ly) {
   using C = double2;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int ny = fa.ny, nxh = fa.nx / 2 + 1, kx = blockIdx.x, f = blockIdx.y, which = blockIdx.z;
-  C* A = reinterpret_cast<C*>(smem_raw);
+  const int ny = fa.ny, nxh = fa.nx / 2 + 1, kx = blockIdx.x, which = blockIdx.y;
+  double2* tab = reinterpret_cast<double2*>(smem_raw);
+  C* A = tab + ny;
   C* S = A + ny;
-  const C* colF = spec + (size_t)f * ny * nxh + kx;
-  const C* colG = spec + (size_t)(n_f + f) * ny * nxh + kx;
   const double two_pi = 6.283185307179586476925286766559;
   for (int ky = threadIdx.x; ky < ny; ky += blockDim.x) {
     const int m = ky <= ny / 2 ? ky : ky - ny;
     const double fl = kx / Lx, fm = m / Ly;
     const double w = two_pi * c * sqrt(fl * fl + fm * fm);
-    const C F = colF[(size_t)ky * nxh], G = colG[(size_t)ky * nxh];
-    C a;
+    double t0, t1;
     if (w == 0.0) {
-      a = which ? G : C{F.x + tau * G.x, F.y + tau * G.y};
+      t0 = which ? 0.0 : 1.0;
+      t1 = which ? 1.0 : tau;
     } else {
       double sn, co;
       sincos(w * tau, &sn, &co);
-      if (which)
-        a = C{-F.x * w * sn + G.x * co, -F.y * w * sn + G.y * co};
-      else
-        a = C{F.x * co + G.x * (sn / w), F.y * co + G.y * (sn / w)};
+      t0 = which ? -w * sn : co;
+      t1 = which ? co : sn / w;
     }
-    A[ky] = C{a.x, -a.y};
+    tab[ky] = double2{t0, t1};
   }
-  __syncthreads();
-  const C* r = stockham<double>(A, S, ny, 1, fa.ry, fa.nry, reinterpret_cast<const C*>(fa.twy), 1);
-  C* dst = out + ((size_t)which * n_f + f) * ny * fa.pitch + kx;
-  for (int y = threadIdx.x; y < ny; y += blockDim.x) dst[(size_t)y * fa.pitch] = C{r[y].x, -r[y].y};
+  for (int f = 0; f < n_f; ++f) {
+    const C* colF = spec + (size_t)f * ny * nxh + kx;
+    const C* colG = spec + (size_t)(n_f + f) * ny * nxh + kx;
+    __syncthreads();
+    for (int ky = threadIdx.x; ky < ny; ky += blockDim.x) {
+      const double2 t = tab[ky];
+      const C F = colF[(size_t)ky * nxh], G = colG[(size_t)ky * nxh];
+      A[ky] = C{F.x * t.x + G.x * t.y, -(F.y * t.x + G.y * t.y)};
+    }
+    __syncthreads();
+    const C* r = stockham<double>(A, S, ny, 1, fa.ry, fa.nry, reinterpret_cast<const C*>(fa.twy), 1);
+    C* dst = out + ((size_t)which * n_f + f) * ny * fa.pitch + kx;
+    for (int y = threadIdx.x; y < ny; y += blockDim.x) dst[(size_t)y * fa.pitch] = C{r[y].x, -r[y].y};
+  }
 }
 
 unsigned blocks(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
@@ -383,8 +395,8 @@ extern "C" fc2d_status fc2d_forward_wave(fc2d_plan_t p, int n_f, double c, int n
   if (!u || !ut) return set_error(FC2D_ERR_ARG, "fc2d_forward_wave: null pointer");
   if (!(c > 0) || n_large < 0)
     return set_error(FC2D_ERR_ARG, "fc2d_forward_wave: c > 0 and n_large >= 0 required");
-  if (2 * (size_t)p->grid.ny * sizeof(double2) > 227 * 1024)
-    return set_error(FC2D_ERR_UNSUPPORTED, "fc2d_forward_wave: ny <= 7264");
+  if (3 * (size_t)p->grid.ny * sizeof(double2) > 227 * 1024)
+    return set_error(FC2D_ERR_UNSUPPORTED, "fc2d_forward_wave: ny <= 4842");
   if (n_large == 0) return FC2D_OK;
   cudaSetDevice(p->device);
   cudaStream_t s = (cudaStream_t)stream;
@@ -425,12 +437,13 @@ extern "C" fc2d_status fc2d_forward_wave(fc2d_plan_t p, int n_f, double c, int n
   auto gtat = [&](int64_t j) { return gt_dir ? gt_dir + (size_t)j * n_f * nb : nullptr; };
   FftArgs fa = fft_args(p);
   const double Lx = nx * h, Ly = ny * h;
-  const size_t smc = 2 * (size_t)ny * sizeof(double2);
+  const size_t smc = 3 * (size_t)ny * sizeof(double2);
   cudaFuncSetAttribute(k_ff_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smc);
   auto eval_ufc = [&](double tau, int n_out, double* out_u, double* out_ut) {
     {
       ProfScope ps(p, "ff_cols", s);
-      k_ff_cols<<<dim3(nxh, n_f, n_out), 256, smc, s>>>(fa, n_f, spec, inter, c, tau, Lx, Ly);
+      if (!launch_ff_cols_p2(fa, n_f, n_out, spec, inter, c, tau, Lx, Ly, s))
+        k_ff_cols<<<dim3(nxh, n_out), 256, smc, s>>>(fa, n_f, spec, inter, c, tau, Lx, Ly);
     }
     ProfScope ps(p, "inverse_rows", s);
     launch_inverse_rows(fa, n_f, inter, nullptr, p->grid.a0, p->grid.b0, h, out_u, s);

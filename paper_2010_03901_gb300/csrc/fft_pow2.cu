@@ -969,6 +969,71 @@ static void wave_cols_p2_launch(const FftArgs& fa, int n_f, void* inter, double 
       fa, n_f, (double2*)inter, c, t, Lx, Ly);
 }
 
+// ------------------------------------------------------------------------- //
+// Fourier Forwarding solve, per small step (FP64, ff.cu): the modal advance of the
+// normalised half spectra to time tau (a = F t0 + G t1 with (t0, t1) = (cos w tau,
+// sin(w tau)/w), or for the time derivative (-w sin w tau, cos w tau); (1, tau) and
+// (0, 1) at w = 0) and the inverse column DFT as a forward transform of the conjugate.
+// One block per (column, output) loops over the n_f functions, so the 2 ny time
+// factors of its column are computed once (in shared memory) for all of them; the
+// transform runs on the compile-time Stockham stages in padded shared memory.
+// ------------------------------------------------------------------------- //
+template <int LOGNY>
+__global__ void __launch_bounds__((1 << LOGNY) / 8)
+    k_ff_cols_p2(FftArgs fa, int n_f, const double2* __restrict__ spec, double2* __restrict__ out,
+                 double c, double tau, double Lx, double Ly) {
+  using C = double2;
+  constexpr int N = 1 << LOGNY, E = 8;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double2* tab = reinterpret_cast<double2*>(smem_raw);
+  C* buf = tab + N;
+  const int nxh = fa.nx / 2 + 1, kx = blockIdx.x, which = blockIdx.y, tid = threadIdx.x;
+  const double two_pi = 6.283185307179586476925286766559;
+  for (int ky = tid; ky < N; ky += blockDim.x) {
+    const int m = ky <= N / 2 ? ky : ky - N;
+    const double fl = kx / Lx, fm = m / Ly;
+    const double w = two_pi * c * sqrt(fl * fl + fm * fm);
+    double t0, t1;
+    if (w == 0.0) {
+      t0 = which ? 0.0 : 1.0;
+      t1 = which ? 1.0 : tau;
+    } else {
+      double sn, co;
+      sincos(w * tau, &sn, &co);
+      t0 = which ? -w * sn : co;
+      t1 = which ? co : sn / w;
+    }
+    tab[ky] = double2{t0, t1};
+  }
+  const C* tw = reinterpret_cast<const C*>(fa.tsy);
+  for (int f = 0; f < n_f; ++f) {
+    const C* colF = spec + (size_t)f * N * nxh + kx;
+    const C* colG = spec + (size_t)(n_f + f) * N * nxh + kx;
+    __syncthreads();  // the table is ready; the previous function's stores are done
+    for (int ky = tid; ky < N; ky += blockDim.x) {
+      const double2 t = tab[ky];
+      const C F = colF[(size_t)ky * nxh], G = colG[(size_t)ky * nxh];
+      buf[pad<double>(ky)] = C{F.x * t.x + G.x * t.y, -(F.y * t.x + G.y * t.y)};
+    }
+    __syncthreads();
+    block_fft<double, LOGNY, E>(buf, tid, true, tw, 1);
+    C* dst = out + ((size_t)which * n_f + f) * N * fa.pitch + kx;
+    for (int y = tid; y < N; y += blockDim.x) {
+      const C r = buf[pad<double>(y)];
+      dst[(size_t)y * fa.pitch] = C{r.x, -r.y};
+    }
+  }
+}
+
+template <int LOGNY>
+static void ff_cols_p2_launch(const FftArgs& fa, int n_f, int n_out, const void* spec, void* out,
+                              double c, double tau, double Lx, double Ly, cudaStream_t s) {
+  const size_t sm = ((size_t)(1 << LOGNY) + padded<double>(1 << LOGNY)) * sizeof(double2);
+  cudaFuncSetAttribute(k_ff_cols_p2<LOGNY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  k_ff_cols_p2<LOGNY><<<dim3(fa.nx / 2 + 1, n_out), (1 << LOGNY) / 8, sm, s>>>(
+      fa, n_f, (const double2*)spec, (double2*)out, c, tau, Lx, Ly);
+}
+
 template <typename T, typename TV, int L>
 static void rows_launch(const FftArgs& fa, const RowArgs& ra, int n_f, int mode, const void* ext,
                         const double* fg, const void* vals, void* inter, cudaStream_t s) {
@@ -1111,6 +1176,20 @@ bool launch_wave_cols_p2(const FftArgs& fa, int n_f, void* inter, double c, doub
   switch (ilog2_exact(fa.ny)) {
     case 11: p2::wave_cols_p2_launch<11>(fa, n_f, inter, c, t, Lx, Ly, s); return true;
     case 12: p2::wave_cols_p2_launch<12>(fa, n_f, inter, c, t, Lx, Ly, s); return true;
+    default: return false;
+  }
+}
+
+// Fourier Forwarding solve columns of 512 .. 4096 points; false (nothing launched)
+// otherwise.
+bool launch_ff_cols_p2(const FftArgs& fa, int n_f, int n_out, const void* spec, void* out,
+                       double c, double tau, double Lx, double Ly, cudaStream_t s) {
+  if (!fa.tsy) return false;  // needs the per-stage twiddle table
+  switch (ilog2_exact(fa.ny)) {
+    case 9: p2::ff_cols_p2_launch<9>(fa, n_f, n_out, spec, out, c, tau, Lx, Ly, s); return true;
+    case 10: p2::ff_cols_p2_launch<10>(fa, n_f, n_out, spec, out, c, tau, Lx, Ly, s); return true;
+    case 11: p2::ff_cols_p2_launch<11>(fa, n_f, n_out, spec, out, c, tau, Lx, Ly, s); return true;
+    case 12: p2::ff_cols_p2_launch<12>(fa, n_f, n_out, spec, out, c, tau, Lx, Ly, s); return true;
     default: return false;
   }
 }

@@ -120,16 +120,18 @@ def full_group():
         fb = torch.tensor(np.stack([t(xy[:, 0], xy[:, 1]) for t in fs]), device=dev)
         inputs.append((w, fs, fg, fb))
     mats = load_fc_matrices()
-    refs = {}
+    refs, exts, geos = {}, {}, {}
     for i in FULL_DOMAINS:
         w, fs = inputs[i][0], inputs[i][1]
         geo = OG.build_geometry(w)
+        geos[i] = geo
         st = OF.matching_stencils(geo)
         xs, ys = w.grid.coords()
         for m in FULL_SAMPLED:
-            refs[i, m] = OF.coefficients(OF.extension(geo, mats, W.trig_grid(fs[m], xs, ys),
-                                                      OF.boundary_values(geo, fs[m]), st))
-    return torch, fc2d, inputs, refs
+            exts[i, m] = OF.extension(geo, mats, W.trig_grid(fs[m], xs, ys),
+                                      OF.boundary_values(geo, fs[m]), st)
+            refs[i, m] = OF.coefficients(exts[i, m])
+    return torch, fc2d, inputs, refs, exts, geos
 
 
 @pytest.mark.parametrize("precision", ["mixed", "fp64"])
@@ -138,7 +140,7 @@ def test_full_size_star_group_against_oracle(full_group, precision):
     them not powers of two) with 32 functions each, captured and then replayed as
     bench.py times it; sampled functions of three domains against the oracle (1e-12
     FP64, 1e-6 mixed relative max-norm)."""
-    torch, fc2d, inputs, refs = full_group
+    torch, fc2d, inputs, refs, _, _ = full_group
     prec = fc2d.FC2D_FP64 if precision == "fp64" else fc2d.FC2D_MIXED
     dt = torch.float64 if precision == "fp64" else torch.float32
     plans, outs = [], []
@@ -162,3 +164,39 @@ def test_full_size_star_group_against_oracle(full_group, precision):
     grp.fc2d_group_destroy()
     for pl in plans:
         pl.fc2d_destroy()
+
+
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+def test_full_size_star_extension_element_wise(full_group, precision):
+    """The extended grids of the 2048^2 and 1536^2 stars point by point (fc2d_extend with
+    32 functions, the function count of the batched call): sampled functions 0 and 31,
+    every strip point within 3e-11 (FP64) / 1e-6 (mixed) of max|f^c| of the oracle's
+    extension, inside points equal to f (FP32-rounded in the mixed form), zero
+    elsewhere."""
+    torch, fc2d, inputs, refs, exts, geos = full_group
+    prec = fc2d.FC2D_FP64 if precision == "fp64" else fc2d.FC2D_MIXED
+    dt = torch.float64 if precision == "fp64" else torch.float32
+    bar = 3e-11 if precision == "fp64" else 1e-6
+    for i in FULL_DOMAINS[:2]:
+        w, fs, fg, fb = inputs[i]
+        g, p = w.grid, w.params
+        plan = fc2d.fc2d_plan(w.boundary.arrays(), (g.a0, g.b0, g.h, g.nx, g.ny),
+                              dict(B=p.B, k1=p.k1), precision=prec)
+        ext = torch.full((N_F, g.ny, g.nx), 7.0, dtype=dt, device=fg.device)
+        plan.fc2d_extend(N_F, fg, fb, ext)
+        plan.fc2d_sync_status()
+        geo = geos[i]
+        strip = np.zeros(g.ny * g.nx, bool)
+        strip[geo.strip_lin] = True
+        strip = strip.reshape(g.ny, g.nx)
+        for m in FULL_SAMPLED:
+            got = ext[m].cpu().numpy().astype(np.float64)
+            ref = exts[i, m]
+            f_in = fg[m].cpu().numpy()
+            if precision == "mixed":
+                f_in = f_in.astype(np.float32).astype(np.float64)
+            err = np.abs(got - ref)[strip].max() / np.abs(ref).max()
+            assert err < bar, (w.name, m, err)
+            assert np.array_equal(got[geo.inside], f_in[geo.inside])
+            assert np.all(got[~(geo.inside | strip)] == 0.0)
+        plan.fc2d_destroy()

@@ -59,6 +59,69 @@ def test_full_size_spectrum(setup, precision):
     assert torch.equal(outs[0], outs[1]) and torch.equal(outs[0], outs[2])
 
 
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+def test_full_size_extension_element_wise(setup, precision):
+    """The extended grid at 4096^2, point by point (the spectrum alone would let one
+    strip point be off by O(1) within the mixed bar: a strip error e moves the
+    normalised spectrum by e/N^2): every strip point within 3e-11 (FP64) / 1e-6 (mixed)
+    of max|f^c| against the oracle's extension, the inside points equal to f (bit for bit
+    in FP64, to FP32 rounding in the mixed form), zero elsewhere.  The strip values come
+    from the same kernels (and the same CTA partition, n_f = 1) as the timed
+    extend + DFT call."""
+    torch, w, fg, fb, ref_spec, geo, mats, st = setup
+    from oracle import fc2d as OF
+    from paper_2010_03901_gb300 import fc2d
+    g, p = w.grid, w.params
+    prec = fc2d.FC2D_FP64 if precision == "fp64" else fc2d.FC2D_MIXED
+    plan = fc2d.fc2d_plan(w.boundary.arrays(), (g.a0, g.b0, g.h, g.nx, g.ny),
+                          dict(B=p.B, k1=p.k1), precision=prec)
+    dev = torch.device("cuda:0")
+    dt = torch.float64 if precision == "fp64" else torch.float32
+    ext = torch.full((1, g.ny, g.nx), 7.0, dtype=dt, device=dev)
+    plan.fc2d_extend(1, torch.tensor(fg[None], device=dev), torch.tensor(fb[None], device=dev), ext)
+    plan.fc2d_sync_status()
+    got = ext.cpu().numpy().astype(np.float64)[0]
+    ref = OF.extension(geo, mats, fg, fb, st)
+    scale = np.abs(ref).max()
+    strip = np.zeros(g.ny * g.nx, bool)
+    strip[geo.strip_lin] = True
+    strip = strip.reshape(g.ny, g.nx)
+    bar = 3e-11 if precision == "fp64" else 1e-6
+    err = np.abs(got - ref)
+    assert err[strip].max() < bar * scale, (err[strip].max() / scale)
+    if precision == "fp64":
+        assert np.array_equal(got[geo.inside], fg[geo.inside])
+    else:
+        assert np.array_equal(got[geo.inside], fg[geo.inside].astype(np.float32).astype(np.float64))
+    assert np.all(got[~(geo.inside | strip)] == 0.0)
+    # number of strip points off by more than the bar: none (reported if any)
+    assert int((err[strip] >= bar * scale).sum()) == 0
+
+
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+def test_full_size_strip_values_element_wise(setup, precision):
+    """The strip values F[p][q] of all 8192 normals at 4096^2 (fc2d_blend) against the
+    oracle's blend of its matching values: 3e-11 (FP64) / 1e-6 (mixed) relative
+    max-norm, and each normal's row within the same bar of the whole array's max."""
+    torch, w, fg, fb, ref_spec, geo, mats, st = setup
+    from oracle import fc2d as OF
+    from paper_2010_03901_gb300 import fc2d
+    g, p = w.grid, w.params
+    prec = fc2d.FC2D_FP64 if precision == "fp64" else fc2d.FC2D_MIXED
+    plan = fc2d.fc2d_plan(w.boundary.arrays(), (g.a0, g.b0, g.h, g.nx, g.ny),
+                          dict(B=p.B, k1=p.k1), precision=prec)
+    dev = torch.device("cuda:0")
+    dt = torch.float64 if precision == "fp64" else torch.float32
+    F = torch.zeros((1, p.B, p.C * p.n_r + 1), dtype=dt, device=dev)
+    plan.fc2d_blend(1, torch.tensor(fg[None], device=dev), torch.tensor(fb[None], device=dev), F)
+    plan.fc2d_sync_status()
+    got = F.cpu().numpy().astype(np.float64)[0]
+    ref = OF.blend(mats, OF.matching_values(geo, st, fg, fb))
+    bar = 3e-11 if precision == "fp64" else 1e-6
+    per_normal = np.abs(got - ref).max(axis=1) / np.abs(ref).max()
+    assert per_normal.max() < bar, (per_normal.max(), int(per_normal.argmax()))
+
+
 def test_full_size_fourier_forwarding_step():
     """The Fourier Forwarding line's workload at its full size: the kite on a 2048^2
     grid with d = 4, M = 7, c = 1, Delta T = 8h, u = 32 Gaussians of width 0.05 (seed 5)

@@ -68,7 +68,8 @@ def test_poisson_parity(name, fc2d, torch_cuda):
 
 def test_star1024_manufactured(fc2d, torch_cuda):
     """The star r = 1 + 0.3 cos 5 theta at 1024^2 (k1 = 0.0013): max error against the
-    exact u = sin(2x) e^y, and parity with the oracle on sampled grid points."""
+    exact u = sin(2x) e^y over the grid points inside (the oracle parity of the Poisson
+    solve is test_poisson_parity's, on three smaller domains)."""
     w = W.workload("star1024")
     u_ex, f = W.u_manufactured, W.lap_u_manufactured
     u, phi, plan = run_gpu(w, f, u_ex, fc2d, torch_cuda)
