@@ -728,7 +728,7 @@ def _disk_eigenmode_error(fc2d, torch, dev, h=0.005, n_c=8, T_target=2.0):
             "max_abs_error": err}
 
 
-def ff_solve_kite2048(fc2d, torch, dev, n_large=2):
+def ff_solve_kite2048(fc2d, torch, dev, n_large=2, squares=False, extras=True):
     """The whole Fourier Forwarding solve (Section 4.2, eq. (4.9); fc2d_forward_wave): the
     kite at 2048^2, d = 4, c = 1, n_c = 8 (Delta T = 8 h, 64 small steps of CFL 0.125
     per large step), zero Dirichlet data, 32 initial conditions in one call (a Gaussian of
@@ -750,7 +750,7 @@ def ff_solve_kite2048(fc2d, torch, dev, n_large=2):
     t0 = time.time()
     u.copy_(U0)
     ut.zero_()
-    plan.fc2d_forward_wave(n_f, c, n_c, 1, u, ut, None, None, stream)
+    plan.fc2d_forward_wave(n_f, c, n_c, 1, u, ut, None, None, stream, squares=squares)
     torch.cuda.synchronize()
     first_call_s = time.time() - t0
     u.copy_(U0)
@@ -760,7 +760,7 @@ def ff_solve_kite2048(fc2d, torch, dev, n_large=2):
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     e0.record(stream)
-    plan.fc2d_forward_wave(n_f, c, n_c, n_large, u, ut, None, None, stream)
+    plan.fc2d_forward_wave(n_f, c, n_c, n_large, u, ut, None, None, stream, squares=squares)
     e1.record(stream)
     torch.cuda.synchronize()
     clocks = clk.stop()
@@ -774,23 +774,32 @@ def ff_solve_kite2048(fc2d, torch, dev, n_large=2):
     ut.zero_()
     plan.fc2d_profile(True)
     plan.fc2d_profile_read()
-    plan.fc2d_forward_wave(n_f, c, n_c, n_large, u, ut, None, None, stream)
+    plan.fc2d_forward_wave(n_f, c, n_c, n_large, u, ut, None, None, stream, squares=squares)
     torch.cuda.synchronize()
     plan.fc2d_profile(False)
     prof = plan.fc2d_profile_read()
-    counts = plan.fc2d_wave_band_info(n_c)
+    counts = plan.fc2d_wave_band_info(n_c, squares=squares)
     S = 8 * n_c
     small = n_large * S
-    peak = fp64_peak(fc2d, torch, dev)
+    peak = fp64_peak(fc2d, torch, dev) if extras else None
     kms = {k: {"launches": v[0], "ms_per_launch": v[1] / v[0], "ms_total": v[1]}
            for k, v in prof.items()}
-    # dominant kernel: the modal advance + inverse column DFT (k_ff_cols) or the inverse
-    # rows; FLOPs of one launch for n_f functions: 5 N log2 N per length-N complex DFT
+    # dominant kernel, FLOPs of one launch for n_f functions (5 N log2 N per length-N
+    # complex DFT): the modal advance + inverse column DFT (k_ff_cols) or the inverse
+    # rows of the full U_FC; with squares the per-small-step square inversion (k_sq_eval:
+    # per square and function pair a 64 x 64 complex DFT, 2 x 64 x 5 x 64 x 6)
     nh = g.nx // 2
     flops = {"ff_cols": n_f * (nh + 1) * 5.0 * g.ny * math.log2(g.ny),
-             "inverse_rows": n_f * g.ny * (5.0 * nh * math.log2(nh) + 10.0 * (nh + 1))}
-    top = max(("ff_cols", "inverse_rows"), key=lambda k: kms.get(k, {}).get("ms_total", 0.0))
+             "inverse_rows": n_f * g.ny * (5.0 * nh * math.log2(nh) + 10.0 * (nh + 1)),
+             "sq_eval": counts[4] * ((n_f + 1) // 2) * 2 * 64 * 5.0 * 64 * 6}
+    top = max(flops, key=lambda k: kms.get(k, {}).get("ms_total", 0.0))
     ach = flops[top] / (kms[top]["ms_per_launch"] * 1e-3) / 1e12
+    if not extras:
+        return {"ms_per_large_step": ms / n_large, "ms_per_small_step": ms / small,
+                "small_steps_per_s": small / (ms * 1e-3), "finite": finite,
+                "max_abs_u_end": amp, "squares": counts[4], "kernels": kms,
+                "band": {"unknowns": counts[0], "interface": counts[2]}, "clocks": clocks,
+                "top_kernel": top, "top_tflops": ach}
     eig = _disk_eigenmode_error(fc2d, torch, dev)
     return {"workload": f"kite 2048^2 (a=0.65, b=1.5), d = 4, c = 1, n_c = 8 (Delta T = 8 h), "
                         f"zero Dirichlet data, {n_f} initial conditions (one Gaussian each, "
@@ -809,7 +818,9 @@ def ff_solve_kite2048(fc2d, torch, dev, n_large=2):
                          "peak_source": "measured FP64 FMA rate (fp64_peak)",
                          "flops": "5 N log2 N per length-N complex DFT of the launch"},
             "fp64_peak": peak, "disk_eigenmode": eig,
-            "parity": "tests/test_gpu_ff.py (element-wise against the oracle)"}
+            "parity": "tests/test_gpu_ff.py (element-wise against the oracle)",
+            "small_squares": ff_solve_kite2048(fc2d, torch, dev, n_large, squares=True,
+                                               extras=False)}
 
 
 def stars8_batched(fc2d, torch, dev, replays=10):

@@ -271,9 +271,16 @@ fc2d_status fc2d_wait_selftest(fc2d_plan_t plan, uint32_t polls, void* stream);
  * with the near-boundary solver U_B: S = 8 n_c small steps Delta t = Delta T / S (CFL
  * c Delta t / h = 0.125, second-order Taylor, Section 4.2.1) on the grid points within
  * n_c h + 2h of the curve, Dirichlet data imposed by cubic boundary polynomials along
- * the grid lines (the embedded-boundary closure the paper cites), interface values from
- * U_FC at every small step (full inverse DFT), a fourth-difference dissipation that
- * makes the small step stable.  At T_{j+1} the grid takes U_FC where the distance to
+ * the grid lines (the embedded-boundary closure the paper cites), a fourth-difference
+ * dissipation that makes the small step stable, and interface values (the band's inner
+ * edge) at every small step either from U_FC by a full inverse DFT (interface_mode 0) or
+ * by the paper's small-square procedure (interface_mode 1): squares of 37 x 37 grid
+ * points inside the domain, each expanded by 1D-FC along rows and columns into a 64 x 64
+ * periodic box once per large step, advanced modally and inverted at every small step
+ * at the interface points within (18 - n_c) h of its centre; in that mode the band
+ * reaches (ceil(sqrt(2) n_c) + 2) h, so that squares inside the domain reach every
+ * interface point, and n_c <= 18 (FC2D_ERR_GEOMETRY if a domain is too narrow or curved
+ * for the squares).  At T_{j+1} the grid takes U_FC where the distance to
  * the curve is >= n_c h and U_B elsewhere (eq. (4.9)); U_B continues across large steps.
  *   u_dev, ut_dev  [n_f][ny][nx] in: u and u_t at t = 0 (values inside the domain used);
  *                  out: u and u_t at t = n_large Delta T inside the domain, 0 outside.
@@ -284,19 +291,22 @@ fc2d_status fc2d_wait_selftest(fc2d_plan_t plan, uint32_t polls, void* stream);
  * for a given n_c (host, synchronous) and kept in the plan; scratch is allocated on the
  * first call for a larger n_f.  Asynchronous on `stream` otherwise. */
 fc2d_status fc2d_forward_wave(fc2d_plan_t plan, int n_f, double c, int n_c, int n_large,
-                              double* u_dev, double* ut_dev, const double* g_dir_dev,
-                              const double* gt_dir_dev, void* stream);
+                              int interface_mode, double* u_dev, double* ut_dev,
+                              const double* g_dir_dev, const double* gt_dir_dev, void* stream);
 
-/* U_B's sets for large-step width n_c h (Section 4.2 near-boundary solver):
- * counts[4] = {unknowns (stepped points), slaved points (values from a boundary
- * polynomial), interface points (U_FC values the operators read), points nearer than
- * n_c h to the curve (where U_B is the solution)}.  fc2d_wave_band_points copies the
- * grid linear indices j nx + i of each set, ascending, into host arrays (NULL skips). */
-fc2d_status fc2d_wave_band_info(fc2d_plan_t plan, int n_c, int64_t* counts);
-fc2d_status fc2d_wave_band_points(fc2d_plan_t plan, int n_c, int32_t* unknown_lin,
-                                  int32_t* slaved_lin, int32_t* iface_lin, int32_t* near_lin);
+/* U_B's sets for large-step width n_c h and an interface mode (Section 4.2
+ * near-boundary solver): counts[5] = {unknowns (stepped points), slaved points (values
+ * from a boundary polynomial), interface points (U_FC values the operators read), points
+ * nearer than n_c h to the curve (where U_B is the solution), squares (mode 1; else 0)}.
+ * fc2d_wave_band_points copies the grid linear indices j nx + i of the first four sets,
+ * ascending, into host arrays (NULL skips). */
+fc2d_status fc2d_wave_band_info(fc2d_plan_t plan, int n_c, int interface_mode, int64_t* counts);
+fc2d_status fc2d_wave_band_points(fc2d_plan_t plan, int n_c, int interface_mode,
+                                  int32_t* unknown_lin, int32_t* slaved_lin, int32_t* iface_lin,
+                                  int32_t* near_lin);
 
-/* One U_B small step with caller data (the step fc2d_forward_wave takes), for tests:
+/* One U_B small step with caller data (the step fc2d_forward_wave takes with
+ * interface_mode 0), for tests:
  * u, u_prev, ut and out are [n_unknown][n_f] (function-minor), grid / grid_prev the
  * U_FC grids [n_f][ny][nx] at the step's time and the one before (interface values),
  * g the Dirichlet data [n_f][n_bdry] (NULL: zero).  mode 0: out = u + dt ut + (c dt)^2/2

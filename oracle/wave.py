@@ -55,7 +55,7 @@ def interior_step(geo, mats, f_grid, f_bdry, g_grid, g_bdry, c, t, stencils=None
 
 
 def forward_wave(geo, mats, band, c, n_large, u0, ut0, g_fun=None, gt_fun=None,
-                 stencils=None):
+                 stencils=None, squares=None, mats_1d=None):
     """The Fourier Forwarding solution (eq. (4.9)) after n_large large steps.
 
     Large step Delta T = n_c h / c (delta = c Delta T = n_c h, Section 4.2).  For each
@@ -77,6 +77,10 @@ def forward_wave(geo, mats, band, c, n_large, u0, ut0, g_fun=None, gt_fun=None,
     g_fun(t), gt_fun(t): Dirichlet data and its time derivative at the plan's boundary
     points (None: zero).  u0, ut0: [ny][nx] (values outside the domain are ignored).
     stencils: the matching stencils of the geometry (computed when None).
+    squares: a placement of ``oracle/wave_squares.py`` (with a band built for it): the
+    interface values of the small steps then come from the small squares' expansions
+    (the paper's small-square procedure) instead of the full inverse DFT; mats_1d: the
+    d = 4 FC matrices of the squares' 1D continuations (default: mats).
     Returns u, u_t on [ny][nx] (zero outside the domain)."""
     from oracle import wave_boundary as WB
     gr = geo.grid
@@ -105,9 +109,16 @@ def forward_wave(geo, mats, band, c, n_large, u0, ut0, g_fun=None, gt_fun=None,
             a, at = advance_modes(Fh, Gh, w, tau)
             return np.fft.irfft2((at if deriv else a) * n, s=(ny, nx))
 
+        if squares is not None:
+            from oracle import wave_squares as WS
+            sq_spec = WS.square_spectra(geo, mats_1d if mats_1d is not None else mats,
+                                        squares, u, ut)
         for s in range(S):
             m = j * S + s
-            f = ufc(s * dt).ravel()[band.iface_lin]
+            if squares is None:
+                f = ufc(s * dt).ravel()[band.iface_lin]
+            else:
+                f = WS.evaluate(geo, squares, sq_spec, band.iface_lin, h, c, s * dt)
             g = gval(m * dt)
             if m == 0:
                 un = WB.first_step(band, h, uu, ut.ravel()[band.unknown_lin], f, g, dt)

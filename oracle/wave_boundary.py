@@ -134,6 +134,7 @@ class Band:
     'g' with one row per unknown (L, B) or per slaved point (S)."""
     n_c: int
     delta: float
+    reach: float                     # the band's outer distance from the curve
     dist: np.ndarray                 # [ny][nx] distance of inside points (inf: far)
     unknown_lin: np.ndarray          # linear indices of the unknowns
     slaved_lin: np.ndarray           # linear indices of the slaved points
@@ -144,13 +145,14 @@ class Band:
 
 
 class _Builder:
-    def __init__(self, geo, n_c):
+    def __init__(self, geo, n_c, reach_cells=None):
         self.geo = geo
         g = geo.grid
         self.h, self.nx, self.ny = g.h, g.nx, g.ny
         self.ins = geo.inside
         self.delta = n_c * g.h
-        reach = self.delta + BAND_EXTRA * g.h
+        reach = (n_c + BAND_EXTRA if reach_cells is None else reach_cells) * g.h
+        self.reach = reach
         self.dist = inside_distance(geo, reach)
         self.band = self.ins & (self.dist < reach - TIE * g.h)
         # slaving
@@ -313,9 +315,11 @@ def _assemble(rows, n_u, n_f, n_g):
     return out
 
 
-def build_band(geo, n_c: int) -> Band:
-    """The near-boundary solver's sets and operators for large-step width delta = n_c h."""
-    b = _Builder(geo, n_c)
+def build_band(geo, n_c: int, reach_cells=None) -> Band:
+    """The near-boundary solver's sets and operators for large-step width delta = n_c h;
+    the band reaches reach_cells h from the curve (default n_c + 2; the small-square
+    interface procedure needs a deeper band, ``oracle/wave_squares.py``)."""
+    b = _Builder(geo, n_c, reach_cells)
     lap = [b.laplacian_row(*divmod(int(lin), b.nx)) for lin in b.lin_u]
     dis = b.dissipation_rows()
     slaved = sorted(j * b.nx + i for (j, i) in b.slave)
@@ -324,7 +328,8 @@ def build_band(geo, n_c: int) -> Band:
     iface_lin = np.zeros(n_f, dtype=np.int64)
     for lin, k in b.iface.items():
         iface_lin[k] = lin
-    band = Band(n_c=n_c, delta=b.delta, dist=b.dist, unknown_lin=b.lin_u.astype(np.int64),
+    band = Band(n_c=n_c, delta=b.delta, reach=b.reach, dist=b.dist,
+                unknown_lin=b.lin_u.astype(np.int64),
                 slaved_lin=np.array(slaved, dtype=np.int64), iface_lin=iface_lin)
     band.L = _assemble(lap, n_u, n_f, n_g)
     band.Bd = _assemble(dis, n_u, n_f, n_g)

@@ -48,12 +48,25 @@ struct DevCsr {
   int64_t rows = 0, nnz = 0;
 };
 
+struct DevSquares {
+  SquareSet host;
+  int32_t* origin = nullptr;        // [n_sq][2] (row, column) of the first grid point
+  int32_t* served_off = nullptr;    // [n_sq + 1]
+  int32_t* served_lin = nullptr;
+  int32_t* served_local = nullptr;
+  double* A = nullptr;              // [C][d]
+  double* Q = nullptr;              // [d][d]
+  double2* tw = nullptr;            // exp(-2 pi i t / P), t < P
+  int n = 0;
+};
+
 struct DevBand {
   WaveBand host;
   DevCsr L, D, S;
   int32_t* unknown_lin = nullptr;
   int32_t* near_lin = nullptr;
   int32_t* near_src = nullptr;
+  std::unique_ptr<DevSquares> sq;   // the small-square procedure's squares (mode 1)
 };
 
 struct Scratch {
@@ -63,7 +76,7 @@ struct Scratch {
 };
 
 struct WaveState {
-  std::map<int, std::unique_ptr<DevBand>> bands;  // by n_c
+  std::map<std::pair<int, int>, std::unique_ptr<DevBand>> bands;  // by (n_c, interface mode)
   Scratch scr;
 };
 
@@ -98,16 +111,47 @@ WaveState* state(fc2d_plan_s* p) {
   return static_cast<WaveState*>(p->wave);
 }
 
-fc2d_status get_band(fc2d_plan_s* p, int n_c, DevBand** out) {
+// The band reach (grid units) for an interface mode: 0 full U_FC at every small step,
+// 1 the small squares (whose service needs interface points at sqrt(2) n_c h or more).
+int reach_cells(int n_c, int mode) {
+  return mode ? (int)std::ceil(std::sqrt(2.0) * n_c) + 2 : n_c + kUbBandExtra;
+}
+
+fc2d_status upload_squares(const fc2d_plan_s* p, DevBand& b, int n_c) {
+  auto q = std::make_unique<DevSquares>();
+  fc2d_status st = build_wave_squares(p, b.host, n_c, q->host);
+  if (st) return st;
+  const SquareSet& h = q->host;
+  q->n = (int)h.origin_j.size();
+  std::vector<int32_t> origin(2 * (size_t)q->n);
+  for (int k = 0; k < q->n; ++k) {
+    origin[2 * k] = h.origin_j[k];
+    origin[2 * k + 1] = h.origin_i[k];
+  }
+  std::vector<double2> tw(h.P);
+  for (int t = 0; t < h.P; ++t) {
+    const double ang = -2.0 * M_PI * double(t) / double(h.P);
+    tw[t] = double2{std::cos(ang), std::sin(ang)};
+  }
+  if ((st = upload(&q->origin, origin)) || (st = upload(&q->served_off, h.served_off)) ||
+      (st = upload(&q->served_lin, h.served_lin)) || (st = upload(&q->served_local, h.served_local)) ||
+      (st = upload(&q->A, h.A)) || (st = upload(&q->Q, h.Q)) || (st = upload(&q->tw, tw)))
+    return st;
+  b.sq = std::move(q);
+  return FC2D_OK;
+}
+
+fc2d_status get_band(fc2d_plan_s* p, int n_c, int mode, DevBand** out) {
   WaveState* W = state(p);
-  auto it = W->bands.find(n_c);
+  auto it = W->bands.find({n_c, mode});
   if (it != W->bands.end()) {
     *out = it->second.get();
     return FC2D_OK;
   }
   auto b = std::make_unique<DevBand>();
-  fc2d_status st = build_wave_band(p, n_c, b->host);
+  fc2d_status st = build_wave_band(p, n_c, reach_cells(n_c, mode), b->host);
   if (st) return st;
+  if (mode && (st = upload_squares(p, *b, n_c))) return st;
   // operator entries of a grid kind must index the grid (30 bits), boundary data too
   if ((int64_t)p->grid.nx * p->grid.ny > (int64_t)kKeyIndex || p->n_bdry > (int64_t)kKeyIndex)
     return set_error(FC2D_ERR_UNSUPPORTED, "wave band: grid too large for the operator keys");
@@ -116,7 +160,7 @@ fc2d_status get_band(fc2d_plan_s* p, int n_c, DevBand** out) {
       (st = upload(&b->near_lin, b->host.near_lin)) || (st = upload(&b->near_src, b->host.near_src)))
     return st;
   *out = b.get();
-  W->bands[n_c] = std::move(b);
+  W->bands[{n_c, mode}] = std::move(b);
   return FC2D_OK;
 }
 
@@ -293,6 +337,160 @@ __global__ void __launch_bounds__(256) k_ff_cols(FftArgs fa, int n_f, const doub
   }
 }
 
+// ------------------------------------------------------------------------- //
+// The small-square procedure (Section 4.2; wave_band.cpp builds the squares)
+// ------------------------------------------------------------------------- //
+constexpr int kSqThreads = 256;
+
+// 1D-FC continuation (eq. (2.7)) of the length-n sequence x[0], x[st], ..., x[(n-1) st]
+// (complex values: two real functions at once) into x[n st] .. x[(n + C - 1) st]:
+// the C values (A Q^T r)_k + (A Q^T l)_{C-1-k}, r the last d values, l the first d in
+// reverse order.  One thread per continuation point.
+__device__ __forceinline__ void fc1d_continue(double2* x, int st, int n, int C, int d,
+                                              const double* __restrict__ A,
+                                              const double* __restrict__ Q, int k) {
+  double2 cr[kMaxD], cl[kMaxD];
+  for (int i = 0; i < d; ++i) {  // Gram coefficients c = Q^T f
+    double2 r = {0.0, 0.0}, l = {0.0, 0.0};
+    for (int m = 0; m < d; ++m) {
+      const double qm = __ldg(Q + m * d + i);
+      const double2 fr = x[(size_t)(n - d + m) * st], fl = x[(size_t)(d - 1 - m) * st];
+      r.x += qm * fr.x;
+      r.y += qm * fr.y;
+      l.x += qm * fl.x;
+      l.y += qm * fl.y;
+    }
+    cr[i] = r;
+    cl[i] = l;
+  }
+  double2 vr = {0.0, 0.0}, vl = {0.0, 0.0};
+  for (int i = 0; i < d; ++i) {
+    const double ar = __ldg(A + k * d + i), al = __ldg(A + (C - 1 - k) * d + i);
+    vr.x += ar * cr[i].x;
+    vr.y += ar * cr[i].y;
+    vl.x += al * cl[i].x;
+    vl.y += al * cl[i].y;
+  }
+  x[(size_t)(n + k) * st] = double2{vl.x + vr.x, vl.y + vr.y};
+}
+
+// In-place transpose of a P x P complex matrix in shared memory (a -> b).
+__device__ __forceinline__ void sq_transpose(const double2* a, double2* b, int P) {
+  for (int t = threadIdx.x; t < P * P; t += blockDim.x) {
+    const int r = t / P, c = t - r * P;
+    b[c * P + r] = a[t];
+  }
+  __syncthreads();
+}
+
+// Once per large step: each square's expansion.  Block (square, function): the square's
+// u and u_t as one complex field z = u + i u_t, continued along rows, then columns, to
+// P x P; its 2D DFT, normalised, stored transposed: Z[l][m] (l: x frequency).
+__global__ void __launch_bounds__(kSqThreads) k_sq_forward(
+    int P, int n_side, int C, int d, int nx, int64_t grid_stride, int n_f,
+    const int32_t* __restrict__ origin, const double* __restrict__ A,
+    const double* __restrict__ Q, const double2* __restrict__ tw, const double* __restrict__ u,
+    const double* __restrict__ ut, double2* __restrict__ Z) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double2* buf = reinterpret_cast<double2*>(smem_raw);
+  double2* scr = buf + P * P;
+  const int sq = blockIdx.x, f = blockIdx.y;
+  const int j0 = __ldg(origin + 2 * sq), i0 = __ldg(origin + 2 * sq + 1);
+  const double* uf = u + (size_t)f * grid_stride;
+  const double* tf = ut + (size_t)f * grid_stride;
+  for (int t = threadIdx.x; t < n_side * n_side; t += blockDim.x) {
+    const int y = t / n_side, x = t - y * n_side;
+    const size_t g = (size_t)(j0 + y) * nx + (i0 + x);
+    buf[y * P + x] = double2{uf[g], tf[g]};
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < n_side * C; t += blockDim.x) {  // rows
+    const int y = t / C, k = t - y * C;
+    fc1d_continue(buf + y * P, 1, n_side, C, d, A, Q, k);
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < P * C; t += blockDim.x) {  // columns
+    const int x = t / C, k = t - x * C;
+    fc1d_continue(buf + x, P, n_side, C, d, A, Q, k);
+  }
+  __syncthreads();
+  int radix[2] = {8, 8};
+  double2* r = stockham<double>(buf, scr, P, P, radix, 2, tw, 1);  // along x: r[y][l]
+  double2* o = r == buf ? scr : buf;
+  sq_transpose(r, o, P);                                           // o[l][y]
+  r = stockham<double>(o, r, P, P, radix, 2, tw, 1);               // r[l][m]
+  const double sc = 1.0 / ((double)P * P);
+  double2* dst = Z + ((size_t)sq * n_f + f) * P * P;
+  for (int t = threadIdx.x; t < P * P; t += blockDim.x) dst[t] = double2{r[t].x * sc, r[t].y * sc};
+}
+
+// Every small step: U at the served interface points at time tau = s dt after the
+// expansion.  Block (square, function pair): for functions f0 = 2 blockIdx.y and f0 + 1
+// the spectra of u and u_t are separated from Z (hat f = (Z_k + conj Z_-k)/2, hat g =
+// (Z_k - conj Z_-k)/(2i)), advanced with the time factors (cos w tau, sin(w tau)/w) of
+// the P-periodic box (table tab[l][m]), packed as a_f0 + i a_f1 and inverted (a forward
+// transform of the conjugate); the real part is f0's field, the imaginary part f1's.
+__global__ void __launch_bounds__(kSqThreads) k_sq_eval(
+    int P, int n_f, const double2* __restrict__ Z, const double2* __restrict__ tab,
+    const double2* __restrict__ tw, const int32_t* __restrict__ served_off,
+    const int32_t* __restrict__ served_lin, const int32_t* __restrict__ served_local,
+    int64_t grid_stride, double* __restrict__ out) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double2* buf = reinterpret_cast<double2*>(smem_raw);
+  double2* scr = buf + P * P;
+  const int sq = blockIdx.x, f0 = 2 * blockIdx.y;
+  const bool two = f0 + 1 < n_f;
+  const double2* Z0 = Z + ((size_t)sq * n_f + f0) * P * P;
+  const double2* Z1 = Z0 + (size_t)P * P;
+  for (int t = threadIdx.x; t < P * P; t += blockDim.x) {
+    const int l = t / P, m = t - l * P;
+    const int tn = ((P - l) % P) * P + (P - m) % P;  // the index of -k
+    const double2 tt = tab[t];
+    auto adv = [&](const double2* Zf) {
+      const double2 zk = Zf[t], zn = Zf[tn];
+      const double2 F = {0.5 * (zk.x + zn.x), 0.5 * (zk.y - zn.y)};   // (Z_k + conj Z_-k)/2
+      const double2 G = {0.5 * (zk.y + zn.y), -0.5 * (zk.x - zn.x)};  // (Z_k - conj Z_-k)/(2i)
+      return double2{F.x * tt.x + G.x * tt.y, F.y * tt.x + G.y * tt.y};
+    };
+    const double2 a0 = adv(Z0);
+    const double2 a1 = two ? adv(Z1) : double2{0.0, 0.0};
+    buf[t] = double2{a0.x - a1.y, -(a0.y + a1.x)};  // conj(a0 + i a1)
+  }
+  __syncthreads();
+  int radix[2] = {8, 8};
+  double2* r = stockham<double>(buf, scr, P, P, radix, 2, tw, 1);  // along m: r[l][y]
+  double2* o = r == buf ? scr : buf;
+  sq_transpose(r, o, P);                                           // o[y][l]
+  r = stockham<double>(o, r, P, P, radix, 2, tw, 1);               // r[y][x] (conjugated)
+  const int s0 = __ldg(served_off + sq), s1 = __ldg(served_off + sq + 1);
+  for (int k = s0 + threadIdx.x; k < s1; k += blockDim.x) {
+    const double2 v = r[__ldg(served_local + k)];
+    const int32_t lin = __ldg(served_lin + k);
+    out[(size_t)f0 * grid_stride + lin] = v.x;
+    if (two) out[(size_t)(f0 + 1) * grid_stride + lin] = -v.y;
+  }
+}
+
+// The box's time factors for the small steps s = 0..S-1: tab[s][l][m] =
+// (cos w tau, sin(w tau)/w) at tau = s dt ((1, tau) at w = 0), w = 2 pi c |k| / (P h).
+__global__ void k_sq_table(int P, int S, double c, double h, double dt, double2* __restrict__ tab) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (int64_t)S * P * P) return;
+  const int s = (int)(t / (P * P)), lm = (int)(t - (int64_t)s * P * P);
+  const int l = lm / P, m = lm - l * P;
+  const int ls = l <= P / 2 ? l : l - P, ms = m <= P / 2 ? m : m - P;
+  const double L = P * h, tau = s * dt;
+  const double fl = ls / L, fm = ms / L;
+  const double w = 6.283185307179586476925286766559 * c * sqrt(fl * fl + fm * fm);
+  if (w == 0.0) {
+    tab[t] = double2{1.0, tau};
+  } else {
+    double sn, co;
+    sincos(w * tau, &sn, &co);
+    tab[t] = double2{co, sn / w};
+  }
+}
+
 unsigned blocks(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
 }  // namespace
@@ -308,6 +506,12 @@ void wave_destroy(fc2d_plan_s* p) {
     cudaFree(b.unknown_lin);
     cudaFree(b.near_lin);
     cudaFree(b.near_src);
+    if (b.sq) {
+      DevSquares& q = *b.sq;
+      for (void* ptr : {(void*)q.origin, (void*)q.served_off, (void*)q.served_lin,
+                        (void*)q.served_local, (void*)q.A, (void*)q.Q, (void*)q.tw})
+        cudaFree(ptr);
+    }
   }
   cudaFree(W->scr.base);
   delete W;
@@ -330,28 +534,35 @@ fc2d_status wave_checks(fc2d_plan_t p, int n_c, const char* who) {
 
 }  // namespace
 
-extern "C" fc2d_status fc2d_wave_band_info(fc2d_plan_t p, int n_c, int64_t* counts) {
+extern "C" fc2d_status fc2d_wave_band_info(fc2d_plan_t p, int n_c, int interface_mode,
+                                           int64_t* counts) {
   fc2d_status st = wave_checks(p, n_c, "fc2d_wave_band_info");
   if (st) return st;
   if (!counts) return set_error(FC2D_ERR_ARG, "fc2d_wave_band_info: null argument");
+  if (interface_mode < 0 || interface_mode > 1)
+    return set_error(FC2D_ERR_ARG, "fc2d_wave_band_info: interface_mode 0 or 1");
   cudaSetDevice(p->device);
   DevBand* b;
-  if ((st = get_band(p, n_c, &b))) return st;
+  if ((st = get_band(p, n_c, interface_mode, &b))) return st;
   counts[0] = (int64_t)b->host.unknown_lin.size();
   counts[1] = (int64_t)b->host.slaved_lin.size();
   counts[2] = (int64_t)b->host.iface_lin.size();
   counts[3] = (int64_t)b->host.near_lin.size();
+  counts[4] = b->sq ? (int64_t)b->sq->n : 0;
   return FC2D_OK;
 }
 
-extern "C" fc2d_status fc2d_wave_band_points(fc2d_plan_t p, int n_c, int32_t* unknown_lin,
+extern "C" fc2d_status fc2d_wave_band_points(fc2d_plan_t p, int n_c, int interface_mode,
+                                             int32_t* unknown_lin,
                                              int32_t* slaved_lin, int32_t* iface_lin,
                                              int32_t* near_lin) {
   fc2d_status st = wave_checks(p, n_c, "fc2d_wave_band_points");
   if (st) return st;
+  if (interface_mode < 0 || interface_mode > 1)
+    return set_error(FC2D_ERR_ARG, "fc2d_wave_band_points: interface_mode 0 or 1");
   cudaSetDevice(p->device);
   DevBand* b;
-  if ((st = get_band(p, n_c, &b))) return st;
+  if ((st = get_band(p, n_c, interface_mode, &b))) return st;
   const WaveBand& w = b->host;
   auto cp = [](int32_t* dst, const std::vector<int32_t>& v) {
     if (dst && !v.empty()) std::memcpy(dst, v.data(), v.size() * sizeof(int32_t));
@@ -375,7 +586,7 @@ extern "C" fc2d_status fc2d_wave_ub_step(fc2d_plan_t p, int n_c, int n_f, int mo
     return set_error(FC2D_ERR_ARG, "fc2d_wave_ub_step: bad mode, c or null pointer");
   cudaSetDevice(p->device);
   DevBand* b;
-  if ((st = get_band(p, n_c, &b))) return st;
+  if ((st = get_band(p, n_c, 0, &b))) return st;
   const double h = p->grid.h, cdt2 = (kUbCfl * h) * (kUbCfl * h);
   const double dt = kUbCfl * h / c;
   const int64_t n = b->L.rows;
@@ -387,21 +598,24 @@ extern "C" fc2d_status fc2d_wave_ub_step(fc2d_plan_t p, int n_c, int n_f, int mo
 }
 
 extern "C" fc2d_status fc2d_forward_wave(fc2d_plan_t p, int n_f, double c, int n_c, int n_large,
-                                         double* u, double* ut, const double* g_dir,
-                                         const double* gt_dir, void* stream) {
+                                         int interface_mode, double* u, double* ut,
+                                         const double* g_dir, const double* gt_dir,
+                                         void* stream) {
   fc2d_status st = wave_checks(p, n_c, "fc2d_forward_wave");
   if (st) return st;
   if ((st = check_nf(p, n_f))) return st;
   if (!u || !ut) return set_error(FC2D_ERR_ARG, "fc2d_forward_wave: null pointer");
   if (!(c > 0) || n_large < 0)
     return set_error(FC2D_ERR_ARG, "fc2d_forward_wave: c > 0 and n_large >= 0 required");
+  if (interface_mode < 0 || interface_mode > 1)
+    return set_error(FC2D_ERR_ARG, "fc2d_forward_wave: interface_mode 0 or 1");
   if (3 * (size_t)p->grid.ny * sizeof(double2) > 227 * 1024)
     return set_error(FC2D_ERR_UNSUPPORTED, "fc2d_forward_wave: ny <= 4842");
   if (n_large == 0) return FC2D_OK;
   cudaSetDevice(p->device);
   cudaStream_t s = (cudaStream_t)stream;
   DevBand* b;
-  if ((st = get_band(p, n_c, &b))) return st;
+  if ((st = get_band(p, n_c, interface_mode, &b))) return st;
   const int nx = p->grid.nx, ny = p->grid.ny, nxh = nx / 2 + 1;
   const int64_t NN = (int64_t)nx * ny, nb = p->n_bdry, Nu = b->L.rows;
   const size_t pitch = row_pitch(p);
@@ -413,7 +627,10 @@ extern "C" fc2d_status fc2d_forward_wave(fc2d_plan_t p, int n_f, double c, int n
   const size_t b_spec = al((size_t)2 * n_f * ny * nxh * 16), b_inter = al((size_t)2 * n_f * ny * pitch * 16),
                b_grid = al((size_t)n_f * NN * 8), b_ub = al((size_t)std::max<int64_t>(1, Nu) * n_f * 8),
                b_zero = al((size_t)n_f * nb * 8);
-  const size_t need = b_spec + b_inter + 2 * b_grid + 4 * b_ub + b_zero;
+  const DevSquares* sq = b->sq.get();
+  const int P = sq ? sq->host.P : 0, n_sq = sq ? sq->n : 0;
+  const size_t b_sqz = al((size_t)n_sq * n_f * P * P * 16), b_sqt = al((size_t)S * P * P * 16);
+  const size_t need = b_spec + b_inter + 2 * b_grid + 4 * b_ub + b_zero + b_sqz + b_sqt;
   WaveState* W = state(p);
   if (W->scr.bytes < need) {
     cudaDeviceSynchronize();
@@ -432,7 +649,15 @@ extern "C" fc2d_status fc2d_forward_wave(fc2d_plan_t p, int n_f, double c, int n
   for (int k = 0; k < 4; ++k)
     ub[k] = reinterpret_cast<double*>(base + b_spec + b_inter + 2 * b_grid + k * b_ub);
   double* zero = reinterpret_cast<double*>(base + b_spec + b_inter + 2 * b_grid + 4 * b_ub);
+  double2* sqZ = reinterpret_cast<double2*>(base + b_spec + b_inter + 2 * b_grid + 4 * b_ub + b_zero);
+  double2* sqT = reinterpret_cast<double2*>(base + b_spec + b_inter + 2 * b_grid + 4 * b_ub + b_zero + b_sqz);
   cudaMemsetAsync(zero, 0, (size_t)n_f * nb * 8, s);
+  const size_t sm_sq = 2 * (size_t)P * P * sizeof(double2);
+  if (sq) {
+    cudaFuncSetAttribute(k_sq_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_sq);
+    cudaFuncSetAttribute(k_sq_eval, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_sq);
+    k_sq_table<<<blocks((int64_t)S * P * P, 256), 256, 0, s>>>(P, S, c, h, dt, sqT);
+  }
   auto gat = [&](int64_t m) { return g_dir ? g_dir + (size_t)m * n_f * nb : nullptr; };
   auto gtat = [&](int64_t j) { return gt_dir ? gt_dir + (size_t)j * n_f * nb : nullptr; };
   FftArgs fa = fft_args(p);
@@ -469,11 +694,24 @@ extern "C" fc2d_status fc2d_forward_wave(fc2d_plan_t p, int n_f, double c, int n
   int f_cur = 0;  // U_FC grid of the current small step; the other holds the previous one
   for (int j = 0; j < n_large; ++j) {
     const int64_t m0 = (int64_t)j * S;
+    if (sq) {  // the squares' expansions of u(T_j), u_t(T_j), before u and ut change
+      ProfScope ps(p, "sq_forward", s);
+      const SquareSet& H = sq->host;
+      k_sq_forward<<<dim3(n_sq, n_f), kSqThreads, sm_sq, s>>>(
+          P, 2 * H.a + 1, H.C, H.d, nx, NN, n_f, sq->origin, sq->A, sq->Q, sq->tw, u, ut, sqZ);
+    }
     if ((st = wave_spectra(p, n_f, u, g_dir ? gat(m0) : zero, ut, gt_dir ? gtat(j) : zero, spec, s)))
       return st;
     for (int sidx = 0; sidx < S; ++sidx) {
       const int64_t m = m0 + sidx;
-      eval_ufc(sidx * dt, 1, ufc[f_cur], nullptr);
+      if (sq) {
+        ProfScope ps(p, "sq_eval", s);
+        k_sq_eval<<<dim3(n_sq, (n_f + 1) / 2), kSqThreads, sm_sq, s>>>(
+            P, n_f, sqZ, sqT + (size_t)sidx * P * P, sq->tw, sq->served_off, sq->served_lin,
+            sq->served_local, NN, ufc[f_cur]);
+      } else {
+        eval_ufc(sidx * dt, 1, ufc[f_cur], nullptr);
+      }
       if (m == 0) {
         ub_step(0, ub[i_cur], nullptr, ub[i_ut], ufc[f_cur], nullptr, gat(m), ub[i_next]);
       } else {

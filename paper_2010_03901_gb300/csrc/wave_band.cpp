@@ -29,6 +29,14 @@
 //   window of five consecutive non-slaved points of a chord holding an unknown.
 // The stepping itself (ff.cu): u^{n+1} = 2u^n - u^{n-1} + (h/8)^2 L(u^n) - 0.3 D(u^n -
 // u^{n-1}), with u^1 = u^0 + dt u_t^0 + (h/8)^2/2 L(u^0).
+//
+// The small-square procedure (build_wave_squares): squares of (2a+1)^2 grid points, all
+// inside the domain, a = (P - C - 1)/2 (P = 64, C the continuation length), each serving
+// the interface points q with |q - centre|_inf <= R = a - n_c (grid units), so that the
+// disk of radius n_c h around q, its domain of dependence over a large step, lies in the
+// square.  Placement: the interface points by increasing linear index; for the first one
+// not yet served, among the centres within R of it whose square is inside, the one
+// serving the most unserved points (ties: smaller row, then column) serves them all.
 #include "wave_band.h"
 
 #include <algorithm>
@@ -287,7 +295,7 @@ void to_csr(const std::vector<Form>& rows, Csr& out) {
 
 }  // namespace
 
-fc2d_status build_wave_band(const fc2d_plan_s* p, int n_c, WaveBand& out) {
+fc2d_status build_wave_band(const fc2d_plan_s* p, int n_c, int reach_cells, WaveBand& out) {
   Builder bd;
   bd.p = p;
   bd.nx = p->grid.nx;
@@ -303,7 +311,7 @@ fc2d_status build_wave_band(const fc2d_plan_s* p, int n_c, WaveBand& out) {
   out = WaveBand();
   out.n_c = n_c;
   out.delta = n_c * bd.h;
-  out.reach = out.delta + kUbBandExtra * bd.h;
+  out.reach = double(reach_cells) * bd.h;
   fc2d_status st = band_distances(bd, out.reach);
   if (st) return st;
   // band and slaving
@@ -409,6 +417,101 @@ fc2d_status build_wave_band(const fc2d_plan_s* p, int n_c, WaveBand& out) {
       }
     }
   }
+  return FC2D_OK;
+}
+
+fc2d_status build_wave_squares(const fc2d_plan_s* p, const WaveBand& band, int n_c,
+                               SquareSet& out) {
+  out = SquareSet();
+  const int nx = p->grid.nx, ny = p->grid.ny, C = p->prm.C, d = p->prm.d, n_r = p->prm.n_r;
+  out.P = kSqP;
+  out.C = C;
+  out.d = d;
+  out.a = (kSqP - C - 1) / 2;
+  out.R = out.a - n_c;
+  if (out.R < 0 || 2 * out.a + 1 + C != kSqP)
+    return set_error(FC2D_ERR_UNSUPPORTED, "small squares: n_c too large for a 64-point box");
+  const int a = out.a, R = out.R;
+  // summed-area table of the inside mask
+  std::vector<int64_t> S((size_t)(nx + 1) * (ny + 1), 0);
+  for (int j = 0; j < ny; ++j) {
+    int64_t run = 0;
+    std::vector<uint8_t> row(nx, 0);
+    for (int k = p->row_iv_off[j]; k < p->row_iv_off[j + 1]; ++k)
+      for (int i = p->row_iv[2 * k]; i <= p->row_iv[2 * k + 1]; ++i) row[i] = 1;
+    for (int i = 0; i < nx; ++i) {
+      run += row[i];
+      S[(size_t)(j + 1) * (nx + 1) + i + 1] = S[(size_t)j * (nx + 1) + i + 1] + run;
+    }
+  }
+  auto inside_square = [&](int cj, int ci) {
+    const int j0 = cj - a, j1 = cj + a + 1, i0 = ci - a, i1 = ci + a + 1;
+    if (j0 < 0 || i0 < 0 || j1 > ny || i1 > nx) return false;
+    const int64_t v = S[(size_t)j1 * (nx + 1) + i1] - S[(size_t)j0 * (nx + 1) + i1] -
+                      S[(size_t)j1 * (nx + 1) + i0] + S[(size_t)j0 * (nx + 1) + i0];
+    return v == (int64_t)(2 * a + 1) * (2 * a + 1);
+  };
+  const std::vector<int32_t>& q = band.iface_lin;  // ascending
+  const int n = (int)q.size();
+  std::vector<int32_t> qj(n), qi(n), owner(n, -1);
+  for (int t = 0; t < n; ++t) {
+    qj[t] = q[t] / nx;
+    qi[t] = q[t] % nx;
+  }
+  // interface points by row, for the neighbourhood queries
+  std::vector<std::vector<int32_t>> by_row(ny);
+  for (int t = 0; t < n; ++t) by_row[qj[t]].push_back(t);
+  std::vector<std::vector<int32_t>> served;
+  for (int t = 0; t < n; ++t) {
+    if (owner[t] >= 0) continue;
+    std::vector<int32_t> loc;
+    for (int j = std::max(0, qj[t] - 2 * R); j <= std::min(ny - 1, qj[t] + 2 * R); ++j)
+      for (int32_t u : by_row[j])
+        if (std::abs(qi[u] - qi[t]) <= 2 * R) loc.push_back(u);
+    bool found = false;
+    int best_score = -1, bj = 0, bi = 0;
+    for (int dj = -R; dj <= R; ++dj)
+      for (int di = -R; di <= R; ++di) {
+        const int cj = qj[t] + dj, ci = qi[t] + di;
+        if (!inside_square(cj, ci)) continue;
+        int score = 0;
+        for (int32_t u : loc)
+          if (owner[u] < 0 && std::abs(qj[u] - cj) <= R && std::abs(qi[u] - ci) <= R) ++score;
+        if (!found || score > best_score || (score == best_score && (cj < bj || (cj == bj && ci < bi)))) {
+          found = true;
+          best_score = score;
+          bj = cj;
+          bi = ci;
+        }
+      }
+    if (!found)
+      return set_error(FC2D_ERR_GEOMETRY,
+                       "small squares: no square inside the domain serves an interface point "
+                       "(the domain is too narrow or too curved for 37-point squares)");
+    std::vector<int32_t> mine;
+    for (int32_t u : loc)
+      if (owner[u] < 0 && std::abs(qj[u] - bj) <= R && std::abs(qi[u] - bi) <= R) {
+        owner[u] = (int32_t)served.size();
+        mine.push_back(u);
+      }
+    std::sort(mine.begin(), mine.end());
+    served.push_back(mine);
+    out.origin_j.push_back(bj - a);
+    out.origin_i.push_back(bi - a);
+  }
+  out.served_off.assign(1, 0);
+  for (size_t k = 0; k < served.size(); ++k) {
+    for (int32_t u : served[k]) {
+      out.served_lin.push_back(q[u]);
+      out.served_local.push_back((qj[u] - out.origin_j[k]) * kSqP + (qi[u] - out.origin_i[k]));
+    }
+    out.served_off.push_back((int32_t)out.served_lin.size());
+  }
+  // the coarse continuation matrix A: the refined one at every n_r-th fine point
+  out.A.assign((size_t)C * d, 0.0);
+  for (int k = 0; k < C; ++k)
+    for (int j = 0; j < d; ++j) out.A[(size_t)k * d + j] = p->Ar[(size_t)((k + 1) * n_r - 1) * d + j];
+  out.Q = p->Q;
   return FC2D_OK;
 }
 

@@ -52,7 +52,24 @@ struct WaveBand {
   std::vector<int32_t> near_src;       // >= 0: unknown index, < 0: -1 - slaved index
 };
 
-// Build U_B's band and operators for large-step width delta = n_c h.
-fc2d_status build_wave_band(const fc2d_plan_s* p, int n_c, WaveBand& out);
+// Build U_B's band and operators for large-step width delta = n_c h, the band reaching
+// reach_cells h from the curve (n_c + 2 with interface values from the full U_FC,
+// ceil(sqrt(2) n_c) + 2 for the small-square procedure).
+fc2d_status build_wave_band(const fc2d_plan_s* p, int n_c, int reach_cells, WaveBand& out);
+
+// The small-square interface procedure (Section 4.2): squares of (2a+1)^2 grid points
+// inside the domain, each with a P x P periodic expansion (P = 2a + 1 + C), serving the
+// interface points within a - n_c of its centre (max norm, grid units).
+constexpr int kSqP = 64;  // periodic length of a square's expansion
+struct SquareSet {
+  int a = 0, R = 0, P = kSqP, C = 0, d = 0;
+  std::vector<int32_t> origin_j, origin_i;   // first grid row / column of each square
+  std::vector<int32_t> served_off;           // [n_sq + 1]
+  std::vector<int32_t> served_lin;           // grid linear index of each served point
+  std::vector<int32_t> served_local;         // its row * P + column in the square's box
+  std::vector<double> A, Q;                  // coarse continuation A [C][d], Gram Q [d][d]
+};
+fc2d_status build_wave_squares(const fc2d_plan_s* p, const WaveBand& band, int n_c,
+                               SquareSet& out);
 
 }  // namespace fc2d

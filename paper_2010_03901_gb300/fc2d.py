@@ -83,9 +83,10 @@ def load_library(path: str = LIB_PATH):
         "fc2d_poisson_info": [P, P, P, P],
         "fc2d_poisson": [P, ct.c_int, P, P, P, P, P, P],
         "fc2d_wave_interior": [P, ct.c_int, ct.c_double, ct.c_double, P, P, P, P, P, P, P],
-        "fc2d_forward_wave": [P, ct.c_int, ct.c_double, ct.c_int, ct.c_int, P, P, P, P, P],
-        "fc2d_wave_band_info": [P, ct.c_int, P],
-        "fc2d_wave_band_points": [P, ct.c_int, P, P, P, P],
+        "fc2d_forward_wave": [P, ct.c_int, ct.c_double, ct.c_int, ct.c_int, ct.c_int, P, P, P,
+                              P, P],
+        "fc2d_wave_band_info": [P, ct.c_int, ct.c_int, P],
+        "fc2d_wave_band_points": [P, ct.c_int, ct.c_int, P, P, P, P],
         "fc2d_wave_ub_step": [P, ct.c_int, ct.c_int, ct.c_int, ct.c_double, P, P, P, P, P, P,
                               P, P],
         "fc2d_profile": [P, ct.c_int],
@@ -246,21 +247,25 @@ class Plan:
                                        _stream(stream)))
 
     def fc2d_forward_wave(self, n_f, c, n_c, n_large, u, ut, g_dir=None, gt_dir=None,
-                          stream=None):
-        _check(_lib.fc2d_forward_wave(self.handle, n_f, c, n_c, n_large, _ptr(u), _ptr(ut),
-                                      _ptr(g_dir), _ptr(gt_dir), _stream(stream)))
+                          stream=None, squares=False):
+        """squares: the interface values from the small-square procedure (mode 1)."""
+        _check(_lib.fc2d_forward_wave(self.handle, n_f, c, n_c, n_large, 1 if squares else 0,
+                                      _ptr(u), _ptr(ut), _ptr(g_dir), _ptr(gt_dir),
+                                      _stream(stream)))
 
-    def fc2d_wave_band_info(self, n_c):
-        """(unknowns, slaved, interface, near) counts of U_B's band for n_c."""
-        counts = np.zeros(4, np.int64)
-        _check(_lib.fc2d_wave_band_info(self.handle, n_c, counts.ctypes.data))
+    def fc2d_wave_band_info(self, n_c, squares=False):
+        """(unknowns, slaved, interface, near, squares) counts of U_B's band for n_c."""
+        counts = np.zeros(5, np.int64)
+        _check(_lib.fc2d_wave_band_info(self.handle, n_c, 1 if squares else 0,
+                                        counts.ctypes.data))
         return tuple(int(v) for v in counts)
 
-    def fc2d_wave_band_points(self, n_c):
+    def fc2d_wave_band_points(self, n_c, squares=False):
         """Grid linear indices of the unknowns, slaved, interface and near points."""
-        n = self.fc2d_wave_band_info(n_c)
+        n = self.fc2d_wave_band_info(n_c, squares)[:4]
         arrs = [np.zeros(max(k, 1), np.int32) for k in n]
-        _check(_lib.fc2d_wave_band_points(self.handle, n_c, *[a.ctypes.data for a in arrs]))
+        _check(_lib.fc2d_wave_band_points(self.handle, n_c, 1 if squares else 0,
+                                          *[a.ctypes.data for a in arrs]))
         return [a[:k] for a, k in zip(arrs, n)]
 
     def fc2d_wave_ub_step(self, n_c, n_f, mode, c, u, u_prev, ut, grid, grid_prev, g, out,

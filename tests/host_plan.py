@@ -24,8 +24,9 @@ def build():
     return EXE
 
 
-def run(w, n_c=None):
-    """The plan's host tables; with n_c also the Fourier Forwarding band (wb_*)."""
+def run(w, n_c=None, squares=False):
+    """The plan's host tables; with n_c also the Fourier Forwarding band (wb_*), and with
+    squares the band of the small-square procedure and its squares (sq_*)."""
     exe = build()
     cx, sx, cy, sy = w.boundary.arrays()
     g, p = w.grid, w.params
@@ -34,6 +35,8 @@ def run(w, n_c=None):
     args += [str(v) for v in (p.d, p.C, p.Z, p.n_os, p.n_r, p.M, p.B, p.m_F)] + [repr(float(p.k1))]
     if n_c is not None:
         args.append(str(int(n_c)))
+        if squares:
+            args.append("1")
     out = subprocess.run([exe] + args, check=True, capture_output=True).stdout
     res = {}
     pos = out.index(b"\n")
@@ -44,17 +47,18 @@ def run(w, n_c=None):
     types = {8: np.float64, 4: np.int32}
     while pos < len(out):
         end = out.index(b"\n", pos)
-        if out[pos:end].startswith(b"wave_status"):
+        if out[pos:end].startswith((b"wave_status", b"squares_status")):
             head = out[pos:end].decode().split(maxsplit=2)
-            res["wave_status"] = int(head[1])
-            res["wave_error"] = head[2] if len(head) > 2 else ""
+            key = head[0].split("_")[0]
+            res[key + "_status"] = int(head[1])
+            res[key + "_error"] = head[2] if len(head) > 2 else ""
             pos = end + 1
             continue
         name, n, sz = out[pos:end].decode().split()
         n, sz = int(n), int(sz)
         dt = types[sz]
         if name in ("row_iv_off", "row_iv", "strip_lin", "gidx", "gidx_c", "row_iv_coff",
-                    "gidx_i", "interior_ok") or (name.startswith("wb_") and sz == 4):
+                    "gidx_i", "interior_ok") or (name.startswith(("wb_", "sq_")) and sz == 4):
             dt = np.uint32 if name.endswith("_col") else np.int32
         arr = np.frombuffer(out[end + 1:end + 1 + n * sz], dtype=dt)
         res[name] = arr

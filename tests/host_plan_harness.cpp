@@ -113,7 +113,7 @@ int main(int argc, char** argv) {
     std::printf("\n");
     return 0;
   }
-  // argv: n_modes cx.. sx.. cy.. sy.. a0 b0 h nx ny d C Z n_os n_r M B m_F k1 [n_c]
+  // argv: n_modes cx.. sx.. cy.. sy.. a0 b0 h nx ny d C Z n_os n_r M B m_F k1 [n_c [squares]]
   int a = 1;
   int nm = std::atoi(argv[a++]);
   std::vector<double> cx(nm), sx(nm), cy(nm), sy(nm);
@@ -161,7 +161,10 @@ int main(int argc, char** argv) {
   dump("interior_ok", &ok, 1);
   if (a < argc) {  // optional: the Fourier Forwarding band for n_c
     fc2d::WaveBand wb;
-    st = fc2d::build_wave_band(p, std::atoi(argv[a++]), wb);
+    const int n_c = std::atoi(argv[a++]);
+    const int squares = a < argc ? std::atoi(argv[a++]) : 0;
+    const int reach = squares ? (int)std::ceil(std::sqrt(2.0) * n_c) + 2 : n_c + fc2d::kUbBandExtra;
+    st = fc2d::build_wave_band(p, n_c, reach, wb);
     std::printf("wave_status %d %s\n", (int)st, fc2d_last_error());
     if (st) return 0;
     dump("wb_unknown_lin", wb.unknown_lin.data(), wb.unknown_lin.size());
@@ -178,6 +181,17 @@ int main(int argc, char** argv) {
       dump(o.c_str(), m->off.data(), m->off.size());
       dump(c.c_str(), m->col.data(), m->col.size());
       dump(w.c_str(), m->w.data(), m->w.size());
+    }
+    if (squares) {
+      fc2d::SquareSet sq;
+      st = fc2d::build_wave_squares(p, wb, n_c, sq);
+      std::printf("squares_status %d %s\n", (int)st, fc2d_last_error());
+      if (st) return 0;
+      dump("sq_origin_j", sq.origin_j.data(), sq.origin_j.size());
+      dump("sq_origin_i", sq.origin_i.data(), sq.origin_i.size());
+      dump("sq_served_off", sq.served_off.data(), sq.served_off.size());
+      dump("sq_served_lin", sq.served_lin.data(), sq.served_lin.size());
+      dump("sq_served_local", sq.served_local.data(), sq.served_local.size());
     }
   }
   return 0;

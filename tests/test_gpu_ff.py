@@ -238,3 +238,116 @@ def test_full_size_fourier_forwarding_solve(torch_cuda):
         et = np.abs(got_ut[k][ins] - ref_ut[ins]).max()
         assert eu < TOL_EXT * (mu + T * mut), (k, eu, mu)
         assert et < TOL_EXT * (w_max * mu + mut), (k, et, mu, mut)
+
+
+def _disk_offset(h):
+    from tests.fc2d_check import paper_setup
+    w = paper_setup(W.disk(), h, d=4, smooth=True)
+    g = W.Grid(a0=w.grid.a0 - 0.31 * h, b0=w.grid.b0 - 0.17 * h, h=h, nx=w.grid.nx,
+               ny=w.grid.ny)
+    return W.Workload(w.name, w.boundary, g, w.params)
+
+
+def test_forward_wave_small_squares_parity(torch_cuda):
+    """The small-square procedure (interface_mode 1) against the oracle's forward_wave
+    with the same squares: the deeper band's sets and the squares' count, then two large
+    steps of two functions with zero Dirichlet data, and one large step of the plane
+    wave with its time-dependent Dirichlet data, at every inside point within the bar of
+    the module docstring."""
+    torch = torch_cuda
+    from oracle import wave_squares as OWS
+    from paper_2010_03901_gb300 import fc2d
+    h, n_c = 0.01, 6
+    w = _disk_offset(h)
+    g, p = w.grid, w.params
+    plan = fc2d.fc2d_plan(w.boundary.arrays(), (g.a0, g.b0, g.h, g.nx, g.ny),
+                          dict(d=4, M=p.M, B=p.B, k1=p.k1))
+    geo = OG.build_geometry(w)
+    band = OWB.build_band(geo, n_c, OWS.band_reach_cells(n_c))
+    sq = OWS.place(geo, band.iface_lin, n_c)
+    counts = plan.fc2d_wave_band_info(n_c, squares=True)
+    assert counts[4] == len(sq.centres)
+    unk, sl, iface, near = plan.fc2d_wave_band_points(n_c, squares=True)
+    assert np.array_equal(unk, band.unknown_lin) and np.array_equal(sl, band.slaved_lin)
+    mats = load_fc_matrices(d=4)
+    st = OF.matching_stencils(geo)
+    dev = torch.device("cuda:0")
+    U0, Ut0 = [], []
+    for k in range(2):
+        a, b, _, _ = _initial(w, geo, 60 + 3 * k)
+        U0.append(a)
+        Ut0.append(b)
+    n_large, c = 2, 1.0
+    u = torch.tensor(np.stack(U0), device=dev)
+    ut = torch.tensor(np.stack(Ut0), device=dev)
+    plan.fc2d_forward_wave(2, c, n_c, n_large, u, ut, squares=True)
+    plan.fc2d_sync_status()
+    got_u, got_ut = u.cpu().numpy(), ut.cpu().numpy()
+    T = n_large * n_c * h
+    w_max = OV.frequencies(g, c).max()
+    ins = geo.inside
+    for k in range(2):
+        ref_u, ref_ut = OV.forward_wave(geo, mats, band, c, n_large, U0[k], Ut0[k],
+                                        stencils=st, squares=sq)
+        mu, mut = np.abs(ref_u[ins]).max(), np.abs(ref_ut[ins]).max()
+        assert np.abs(got_u[k][ins] - ref_u[ins]).max() < TOL_EXT * n_large * (mu + T * mut)
+        assert np.abs(got_ut[k][ins] - ref_ut[ins]).max() < TOL_EXT * n_large * (w_max * mu + mut)
+    kap = 10.5
+    ue = lambda x, y, t: np.cos(2 * kap * (x + t) / 3) + np.cos(kap * (y + t))
+    ute = lambda x, y, t: (-(2 * kap / 3) * np.sin(2 * kap * (x + t) / 3)
+                           - kap * np.sin(kap * (y + t)))
+    S = 8 * n_c
+    dt = n_c * h / S
+    X, Y = np.meshgrid(geo.xs, geo.ys)
+    gdir = np.stack([ue(geo.bdry_x, geo.bdry_y, m * dt) for m in range(S + 1)])[:, None, :]
+    gtdir = np.stack([ute(geo.bdry_x, geo.bdry_y, j * S * dt) for j in range(2)])[:, None, :]
+    u = torch.tensor(ue(X, Y, 0.0)[None], device=dev)
+    ut = torch.tensor(ute(X, Y, 0.0)[None], device=dev)
+    plan.fc2d_forward_wave(1, c, n_c, 1, u, ut, torch.tensor(gdir, device=dev),
+                           torch.tensor(gtdir, device=dev), squares=True)
+    plan.fc2d_sync_status()
+    ref_u, ref_ut = OV.forward_wave(geo, mats, band, c, 1, ue(X, Y, 0.0), ute(X, Y, 0.0),
+                                    lambda t: ue(geo.bdry_x, geo.bdry_y, t),
+                                    lambda t: ute(geo.bdry_x, geo.bdry_y, t),
+                                    stencils=st, squares=sq)
+    assert np.abs(u.cpu().numpy()[0][ins] - ref_u[ins]).max() < TOL_EXT * (2 + n_c * h * kap * 2)
+    assert np.abs(ut.cpu().numpy()[0][ins] - ref_ut[ins]).max() < TOL_EXT * (w_max * 2 + 2 * kap)
+
+
+def test_full_size_small_squares_solve(torch_cuda):
+    """The bench's FF workload with the small-square procedure, at full size and in the
+    bench's launch configuration (kite 2048^2, n_c = 8, 32 functions, one large step):
+    the squares as the oracle places them, functions 0 and 31 against the oracle's solve
+    with the same squares at every inside point."""
+    torch = torch_cuda
+    from oracle import wave_squares as OWS
+    from paper_2010_03901_gb300 import fc2d
+    w = W.workload("kite2048", d=4, M=7)
+    g, p = w.grid, w.params
+    n_c, n_f = 8, 32
+    plan = fc2d.fc2d_plan(w.boundary.arrays(), (g.a0, g.b0, g.h, g.nx, g.ny),
+                          dict(d=4, M=7, B=p.B, k1=p.k1))
+    fs = [W.gaussian_sum(w.boundary, 1, 50 + k, wmin=0.05, wmax=0.05, margin=0.35)
+          for k in range(n_f)]
+    U0 = np.stack([W.grid_values(w, f) for f in fs])
+    dev = torch.device("cuda:0")
+    u = torch.tensor(U0, device=dev)
+    ut = torch.zeros_like(u)
+    plan.fc2d_forward_wave(n_f, 1.0, n_c, 1, u, ut, squares=True)
+    plan.fc2d_sync_status()
+    got_u, got_ut = u.cpu().numpy(), ut.cpu().numpy()
+    geo = OG.build_geometry(w)
+    band = OWB.build_band(geo, n_c, OWS.band_reach_cells(n_c))
+    sq = OWS.place(geo, band.iface_lin, n_c)
+    assert plan.fc2d_wave_band_info(n_c, squares=True)[4] == len(sq.centres)
+    mats = load_fc_matrices(d=4)
+    st = OF.matching_stencils(geo)
+    T = n_c * g.h
+    w_max = OV.frequencies(g, 1.0).max()
+    ins = geo.inside
+    for k in (0, n_f - 1):
+        ref_u, ref_ut = OV.forward_wave(geo, mats, band, 1.0, 1, U0[k], np.zeros_like(U0[k]),
+                                        stencils=st, squares=sq)
+        mu, mut = np.abs(ref_u[ins]).max(), np.abs(ref_ut[ins]).max()
+        assert np.abs(got_u[k][ins] - ref_u[ins]).max() < TOL_EXT * (mu + T * mut), k
+        assert np.abs(got_ut[k][ins] - ref_ut[ins]).max() < TOL_EXT * (w_max * mu + mut), k

@@ -258,3 +258,28 @@ def test_wave_band_equals_the_oracle(name, n_c):
             assert abs(v - ref) <= 1e-15
             nnz += 1
     assert nnz == int((Du != 0).sum() + (Df != 0).sum())
+
+
+@pytest.mark.parametrize("name,n_c", [("kite1024", 8)])
+def test_wave_squares_equal_the_oracle(name, n_c):
+    """The small-square procedure's band (deeper) and square placement of the host code
+    equal the oracle's: the same squares in the same order, serving the same points."""
+    from oracle import wave_boundary as OWB
+    from oracle import wave_squares as OWS
+    w = W.workload(name, d=4, M=7)
+    r = host_plan.run(w, n_c, squares=True)
+    assert r["status"] == 0 and r["wave_status"] == 0 and r["squares_status"] == 0, r
+    geo = OG.build_geometry(w)
+    band = OWB.build_band(geo, n_c, OWS.band_reach_cells(n_c))
+    sq = OWS.place(geo, band.iface_lin, n_c)
+    assert np.array_equal(r["wb_unknown_lin"], band.unknown_lin)
+    assert np.array_equal(r["sq_origin_j"], sq.centres[:, 0] - sq.a)
+    assert np.array_equal(r["sq_origin_i"], sq.centres[:, 1] - sq.a)
+    iface = np.asarray(band.iface_lin)
+    lin = np.concatenate([np.sort(iface[s]) for s in sq.served])
+    assert np.array_equal(r["sq_served_lin"], lin)
+    nx = w.grid.nx
+    qj, qi = np.divmod(r["sq_served_lin"], nx)
+    k = np.repeat(np.arange(len(sq.centres)), np.diff(r["sq_served_off"]))
+    assert np.array_equal(r["sq_served_local"],
+                          (qj - r["sq_origin_j"][k]) * 64 + (qi - r["sq_origin_i"][k]))
