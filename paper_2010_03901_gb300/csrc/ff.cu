@@ -57,6 +57,7 @@ struct DevSquares {
   double* A = nullptr;              // [C][d]
   double* Q = nullptr;              // [d][d]
   double2* tw = nullptr;            // exp(-2 pi i t / P), t < P
+  int32_t* rows = nullptr;          // [n_sq][2]: first and last box row holding served points
   int n = 0;
 };
 
@@ -128,6 +129,16 @@ fc2d_status upload_squares(const fc2d_plan_s* p, DevBand& b, int n_c) {
     origin[2 * k] = h.origin_j[k];
     origin[2 * k + 1] = h.origin_i[k];
   }
+  std::vector<int32_t> rows(2 * (size_t)q->n);
+  for (int k = 0; k < q->n; ++k) {
+    int lo = h.P, hi = -1;
+    for (int i = h.served_off[k]; i < h.served_off[k + 1]; ++i) {
+      lo = std::min(lo, h.served_local[i] / h.P);
+      hi = std::max(hi, h.served_local[i] / h.P);
+    }
+    rows[2 * k] = lo;
+    rows[2 * k + 1] = hi;
+  }
   std::vector<double2> tw(h.P);
   for (int t = 0; t < h.P; ++t) {
     const double ang = -2.0 * M_PI * double(t) / double(h.P);
@@ -135,7 +146,8 @@ fc2d_status upload_squares(const fc2d_plan_s* p, DevBand& b, int n_c) {
   }
   if ((st = upload(&q->origin, origin)) || (st = upload(&q->served_off, h.served_off)) ||
       (st = upload(&q->served_lin, h.served_lin)) || (st = upload(&q->served_local, h.served_local)) ||
-      (st = upload(&q->A, h.A)) || (st = upload(&q->Q, h.Q)) || (st = upload(&q->tw, tw)))
+      (st = upload(&q->A, h.A)) || (st = upload(&q->Q, h.Q)) || (st = upload(&q->tw, tw)) ||
+      (st = upload(&q->rows, rows)))
     return st;
   b.sq = std::move(q);
   return FC2D_OK;
@@ -424,28 +436,97 @@ __global__ void __launch_bounds__(kSqThreads) k_sq_forward(
   for (int t = threadIdx.x; t < P * P; t += blockDim.x) dst[t] = double2{r[t].x * sc, r[t].y * sc};
 }
 
+// 64-point DFT of the padded sequence x[pad(e)], e < 64 (pad(e) = e + e/8), by the 8
+// threads q = 0..7 of a group, as 8 x 8: X[k1 + 8 k2] = sum_q w8^(q k2) w64^(q k1)
+// sum_r x[q + 8 r] w8^(r k1); the result replaces x in natural order.  Every thread of
+// the block calls it (three barriers, the last after the result is stored); `active`
+// false: a group with nothing to transform.
+__device__ __forceinline__ int sq_pad(int e) { return e + (e >> 3); }
+
+// Forward 8-point DFT in registers (radix 2 x 4: two 4-point DFTs of the even and odd
+// entries, the twiddles exp(-2 pi i k/8), one butterfly).
+__device__ __forceinline__ void dft8_regs(double2 (&v)[8]) {
+  const double s = 0.70710678118654752440;
+  auto d4 = [](double2& a0, double2& a1, double2& a2, double2& a3) {
+    const double2 t0 = cadd(a0, a2), t1 = csub(a0, a2), t2 = cadd(a1, a3);
+    const double2 t3 = mul_mi(csub(a1, a3));
+    a0 = cadd(t0, t2);
+    a2 = csub(t0, t2);
+    a1 = cadd(t1, t3);
+    a3 = csub(t1, t3);
+  };
+  double2 e0 = v[0], e1 = v[2], e2 = v[4], e3 = v[6], o0 = v[1], o1 = v[3], o2 = v[5], o3 = v[7];
+  d4(e0, e1, e2, e3);
+  d4(o0, o1, o2, o3);
+  const double2 w1 = {s * (o1.x + o1.y), s * (o1.y - o1.x)};
+  const double2 w2 = mul_mi(o2);
+  const double2 w3 = {s * (o3.y - o3.x), -s * (o3.x + o3.y)};
+  v[0] = cadd(e0, o0);
+  v[4] = csub(e0, o0);
+  v[1] = cadd(e1, w1);
+  v[5] = csub(e1, w1);
+  v[2] = cadd(e2, w2);
+  v[6] = csub(e2, w2);
+  v[3] = cadd(e3, w3);
+  v[7] = csub(e3, w3);
+}
+
+__device__ __forceinline__ void fft64(double2* x, int q, bool active,
+                                      const double2* __restrict__ tw) {
+  double2 v[8];
+  if (active) {
+#pragma unroll
+    for (int r = 0; r < 8; ++r) v[r] = x[sq_pad(q + 8 * r)];
+    dft8_regs(v);
+#pragma unroll
+    for (int k = 1; k < 8; ++k) v[k] = cmul(v[k], __ldg(tw + q * k));  // w64^(q k1)
+#pragma unroll
+    for (int k = 0; k < 8; ++k) x[sq_pad(q + 8 * k)] = v[k];
+  }
+  __syncthreads();
+  if (active) {
+#pragma unroll
+    for (int r = 0; r < 8; ++r) v[r] = x[sq_pad(8 * q + r)];  // thread q is k1 here
+    dft8_regs(v);
+  }
+  __syncthreads();
+  if (active) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) x[sq_pad(q + 8 * k)] = v[k];
+  }
+  __syncthreads();
+}
+
+constexpr int kSqPad = 72;        // padded length of a 64-point sequence
+constexpr int kSqEvalThreads = 512;
+
 // Every small step: U at the served interface points at time tau = s dt after the
-// expansion.  Block (square, function pair): for functions f0 = 2 blockIdx.y and f0 + 1
-// the spectra of u and u_t are separated from Z (hat f = (Z_k + conj Z_-k)/2, hat g =
-// (Z_k - conj Z_-k)/(2i)), advanced with the time factors (cos w tau, sin(w tau)/w) of
-// the P-periodic box (table tab[l][m]), packed as a_f0 + i a_f1 and inverted (a forward
-// transform of the conjugate); the real part is f0's field, the imaginary part f1's.
-__global__ void __launch_bounds__(kSqThreads) k_sq_eval(
-    int P, int n_f, const double2* __restrict__ Z, const double2* __restrict__ tab,
+// expansion.  Block (square, function pair) of 512 threads (64 groups of 8): for functions
+// f0 = 2 blockIdx.y and f0 + 1 the spectra of u and u_t are separated from Z (hat f =
+// (Z_k + conj Z_-k)/2, hat g = (Z_k - conj Z_-k)/(2i)), advanced with the time factors
+// (cos w tau, sin(w tau)/w) of the P-periodic box (table tab[l][m]) and packed as
+// conj(a_f0 + i a_f1); the inverse 2D DFT runs as forward 64-point DFTs along m for every
+// l, a transpose of the rows the served points need (rows r0..r1 of the square), and
+// forward DFTs along l for those rows; the real part of the conjugated result is f0's
+// field, the imaginary part with its sign changed f1's.
+__global__ void __launch_bounds__(kSqEvalThreads, 2) k_sq_eval(
+    int n_f, const double2* __restrict__ Z, const double2* __restrict__ tab,
     const double2* __restrict__ tw, const int32_t* __restrict__ served_off,
     const int32_t* __restrict__ served_lin, const int32_t* __restrict__ served_local,
-    int64_t grid_stride, double* __restrict__ out) {
+    const int32_t* __restrict__ rows, int64_t grid_stride, double* __restrict__ out) {
+  constexpr int P = kSqP;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  double2* buf = reinterpret_cast<double2*>(smem_raw);
-  double2* scr = buf + P * P;
+  double2* T1 = reinterpret_cast<double2*>(smem_raw);  // [64][72]: transform l along m
+  double2* T2 = T1 + P * kSqPad;                        // [rows][72]: transform y along l
   const int sq = blockIdx.x, f0 = 2 * blockIdx.y;
   const bool two = f0 + 1 < n_f;
   const double2* Z0 = Z + ((size_t)sq * n_f + f0) * P * P;
   const double2* Z1 = Z0 + (size_t)P * P;
+  const int g = threadIdx.x >> 3, q = threadIdx.x & 7;
   for (int t = threadIdx.x; t < P * P; t += blockDim.x) {
     const int l = t / P, m = t - l * P;
-    const int tn = ((P - l) % P) * P + (P - m) % P;  // the index of -k
-    const double2 tt = tab[t];
+    const int tn = ((P - l) & (P - 1)) * P + ((P - m) & (P - 1));  // the index of -k
+    const double2 tt = __ldg(tab + t);
     auto adv = [&](const double2* Zf) {
       const double2 zk = Zf[t], zn = Zf[tn];
       const double2 F = {0.5 * (zk.x + zn.x), 0.5 * (zk.y - zn.y)};   // (Z_k + conj Z_-k)/2
@@ -454,17 +535,21 @@ __global__ void __launch_bounds__(kSqThreads) k_sq_eval(
     };
     const double2 a0 = adv(Z0);
     const double2 a1 = two ? adv(Z1) : double2{0.0, 0.0};
-    buf[t] = double2{a0.x - a1.y, -(a0.y + a1.x)};  // conj(a0 + i a1)
+    T1[l * kSqPad + sq_pad(m)] = double2{a0.x - a1.y, -(a0.y + a1.x)};  // conj(a0 + i a1)
   }
   __syncthreads();
-  int radix[2] = {8, 8};
-  double2* r = stockham<double>(buf, scr, P, P, radix, 2, tw, 1);  // along m: r[l][y]
-  double2* o = r == buf ? scr : buf;
-  sq_transpose(r, o, P);                                           // o[y][l]
-  r = stockham<double>(o, r, P, P, radix, 2, tw, 1);               // r[y][x] (conjugated)
+  fft64(T1 + g * kSqPad, q, true, tw);  // T1[l][y]
+  const int r0 = __ldg(rows + 2 * sq), nr = __ldg(rows + 2 * sq + 1) - r0 + 1;
+  for (int t = threadIdx.x; t < nr * P; t += blockDim.x) {
+    const int yr = t / P, l = t - yr * P;
+    T2[yr * kSqPad + sq_pad(l)] = T1[l * kSqPad + sq_pad(r0 + yr)];
+  }
+  __syncthreads();
+  fft64(T2 + g * kSqPad, q, g < nr, tw);  // T2[y - r0][x]
   const int s0 = __ldg(served_off + sq), s1 = __ldg(served_off + sq + 1);
   for (int k = s0 + threadIdx.x; k < s1; k += blockDim.x) {
-    const double2 v = r[__ldg(served_local + k)];
+    const int loc = __ldg(served_local + k), y = loc / P, x = loc - y * P;
+    const double2 v = T2[(y - r0) * kSqPad + sq_pad(x)];
     const int32_t lin = __ldg(served_lin + k);
     out[(size_t)f0 * grid_stride + lin] = v.x;
     if (two) out[(size_t)(f0 + 1) * grid_stride + lin] = -v.y;
@@ -509,7 +594,8 @@ void wave_destroy(fc2d_plan_s* p) {
     if (b.sq) {
       DevSquares& q = *b.sq;
       for (void* ptr : {(void*)q.origin, (void*)q.served_off, (void*)q.served_lin,
-                        (void*)q.served_local, (void*)q.A, (void*)q.Q, (void*)q.tw})
+                        (void*)q.served_local, (void*)q.A, (void*)q.Q, (void*)q.tw,
+                        (void*)q.rows})
         cudaFree(ptr);
     }
   }
@@ -653,9 +739,20 @@ extern "C" fc2d_status fc2d_forward_wave(fc2d_plan_t p, int n_f, double c, int n
   double2* sqT = reinterpret_cast<double2*>(base + b_spec + b_inter + 2 * b_grid + 4 * b_ub + b_zero + b_sqz);
   cudaMemsetAsync(zero, 0, (size_t)n_f * nb * 8, s);
   const size_t sm_sq = 2 * (size_t)P * P * sizeof(double2);
+  int max_rows = 0;
+  if (sq)
+    for (int k = 0; k < n_sq; ++k) {
+      int lo = P, hi = -1;
+      for (int i = sq->host.served_off[k]; i < sq->host.served_off[k + 1]; ++i) {
+        lo = std::min(lo, sq->host.served_local[i] / P);
+        hi = std::max(hi, sq->host.served_local[i] / P);
+      }
+      max_rows = std::max(max_rows, hi - lo + 1);
+    }
+  const size_t sm_ev = (size_t)(P + max_rows) * kSqPad * sizeof(double2);
   if (sq) {
     cudaFuncSetAttribute(k_sq_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_sq);
-    cudaFuncSetAttribute(k_sq_eval, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_sq);
+    cudaFuncSetAttribute(k_sq_eval, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_ev);
     k_sq_table<<<blocks((int64_t)S * P * P, 256), 256, 0, s>>>(P, S, c, h, dt, sqT);
   }
   auto gat = [&](int64_t m) { return g_dir ? g_dir + (size_t)m * n_f * nb : nullptr; };
@@ -706,9 +803,9 @@ extern "C" fc2d_status fc2d_forward_wave(fc2d_plan_t p, int n_f, double c, int n
       const int64_t m = m0 + sidx;
       if (sq) {
         ProfScope ps(p, "sq_eval", s);
-        k_sq_eval<<<dim3(n_sq, (n_f + 1) / 2), kSqThreads, sm_sq, s>>>(
-            P, n_f, sqZ, sqT + (size_t)sidx * P * P, sq->tw, sq->served_off, sq->served_lin,
-            sq->served_local, NN, ufc[f_cur]);
+        k_sq_eval<<<dim3(n_sq, (n_f + 1) / 2), kSqEvalThreads, sm_ev, s>>>(
+            n_f, sqZ, sqT + (size_t)sidx * P * P, sq->tw, sq->served_off, sq->served_lin,
+            sq->served_local, sq->rows, NN, ufc[f_cur]);
       } else {
         eval_ufc(sidx * dt, 1, ufc[f_cur], nullptr);
       }
