@@ -823,6 +823,64 @@ def ff_solve_kite2048(fc2d, torch, dev, n_large=2, squares=False, extras=True):
                                                extras=False)}
 
 
+def ff_scaling(fc2d, torch, dev, n_f=8, n_c=8):
+    """Cost of a Fourier Forwarding small step against the grid size (Section 4.2: with
+    the small-square procedure the interface values cost O(perimeter / h) squares of
+    fixed size per small step, about O(sqrt N), against O(N log N) for the full inverse
+    DFT).  The kite at 1024^2, 2048^2, 4096^2 (d = 4, n_c = 8, 8 Gaussians, zero
+    Dirichlet data), one large step of 64 small steps per mode after a warm-up call,
+    kernels timed with events: per small step the interface evaluation (full: k_ff_cols +
+    inverse rows; squares: k_sq_eval) and the U_B step, per large step the whole call."""
+    out = {}
+    for N in (1024, 2048, 4096):
+        name = f"kite{N}"
+        w = W.workload(name, d=4, M=7)
+        g, p = w.grid, w.params
+        plan = fc2d.fc2d_plan(w.boundary.arrays(), (g.a0, g.b0, g.h, g.nx, g.ny),
+                              dict(d=4, M=7, B=p.B, k1=p.k1))
+        fs = [W.gaussian_sum(w.boundary, 1, 50 + k, wmin=0.05, wmax=0.05, margin=0.35)
+              for k in range(n_f)]
+        U0 = torch.tensor(np.stack([W.grid_values(w, f) for f in fs]), device=dev)
+        u, ut = torch.empty_like(U0), torch.empty_like(U0)
+        row = {"grid": f"{N}x{N}", "points": N * N}
+        for mode in (False, True):
+            u.copy_(U0)
+            ut.zero_()
+            plan.fc2d_forward_wave(n_f, 1.0, n_c, 1, u, ut, squares=mode)  # builds the band
+            u.copy_(U0)
+            ut.zero_()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            plan.fc2d_forward_wave(n_f, 1.0, n_c, 1, u, ut, squares=mode)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            u.copy_(U0)
+            ut.zero_()
+            plan.fc2d_profile(True)
+            plan.fc2d_profile_read()
+            plan.fc2d_forward_wave(n_f, 1.0, n_c, 1, u, ut, squares=mode)
+            torch.cuda.synchronize()
+            plan.fc2d_profile(False)
+            prof = plan.fc2d_profile_read()
+            S = 8 * n_c
+            per = lambda k: prof[k][1] / prof[k][0] if k in prof else 0.0
+            if mode:
+                iface = per("sq_eval")
+            else:
+                iface = per("ff_cols") + per("inverse_rows")
+            counts = plan.fc2d_wave_band_info(n_c, squares=mode)
+            row["squares" if mode else "full_inverse_dft"] = {
+                "ms_per_large_step": ms, "interface_ms_per_small_step": iface,
+                "ub_step_ms": per("ub_step"), "unknowns": counts[0], "interface_points": counts[2],
+                "n_squares": counts[4]}
+        plan.fc2d_destroy()
+        out[name] = row
+    return {"workload": f"kite N^2, d = 4, n_c = 8, {n_f} Gaussians, one large step (64 small "
+                        "steps) per mode, FP64", "n_f": n_f, "by_grid": out}
+
+
 def stars8_batched(fc2d, torch, dev, replays=10):
     """Eight stars (grids 256^2..2048^2 by concavity), 32 trigonometric sums per domain,
     one fc2d_group_extend_coeffs call per step (one CUDA graph, a branch per domain);
@@ -980,6 +1038,7 @@ EXTRA_LINES = {"poisson_star1024": poisson_star1024,
                "poisson_kite_d10": poisson_kite_oscillatory,
                "ff_interior_kite2048": ff_interior_kite2048,
                "ff_solve_kite2048": ff_solve_kite2048,
+               "ff_scaling": ff_scaling,
                "stars8_batched": stars8_batched}
 
 

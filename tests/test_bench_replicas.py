@@ -80,4 +80,4 @@ def test_bench_rejects_bad_arguments():
         assert e.value.code == 2
     assert set(bench.EXTRA_LINES) == {"poisson_star1024", "poisson_kite_d10",
                                       "ff_interior_kite2048", "ff_solve_kite2048",
-                                      "stars8_batched"}
+                                      "ff_scaling", "stars8_batched"}
