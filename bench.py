@@ -520,7 +520,12 @@ def measure(fc2d, torch, w, precision, K, warmup, world, dev, fg_h, fb_h, sample
     roof["traffic"] = MEASURED_TRAFFIC.get((precision, dom))
     kernels = {k: {"launches": v[0], "avg_us": 1e3 * v[1] / v[0],
                    "share": v[1] / sum(x[1] for x in prof.values())} for k, v in prof.items()}
+    cc, cc_us = plan.fc2d_tuning()
     return {"value": value, "ms_per_step": ms / K, "steps": K, "plan_s": plan_s,
+            "tuning": {"cols4k_columns_per_block": cc,
+                       "candidates_us": dict(zip(("16", "32", "64"), cc_us)),
+                       "how": "plan-time autotuner: each width timed on a scratch "
+                              "intermediate of this grid, fastest kept (same values)"},
             "l2_flushed": {"value": replica_throughput(world, K, npts, ms_fl),
                            "ms_per_step": ms_fl / K,
                            "note": "L2 flushed before each step (256 MB read, outside "
@@ -1005,7 +1010,7 @@ def run_gpu(args):
                        "parallelism": f"replicas x{world}"},
             "clocks": r["clocks"], "roofline": r["roofline"], "kernels": r["kernels"],
             "gpu_launches": r["gpu_launches"], "e2e": r["e2e"], "l2_flushed": r["l2_flushed"],
-            "plan_s": r["plan_s"],
+            "plan_s": r["plan_s"], "tuning": r["tuning"],
             "profiled_ms_per_step": r["profiled_ms_per_step"],
             "kernels_note": "per-kernel times and roofline from a second region of the same "
                             "K steps with CUDA events around each kernel",

@@ -318,6 +318,17 @@ fc2d_status fc2d_wave_ub_step(fc2d_plan_t plan, int n_c, int n_f, int mode, doub
                               const double* grid_prev_dev, const double* g_dev, double* out_dev,
                               void* stream);
 
+/* Launch shapes the plan chose by timing (no operation of the paper; each candidate
+ * computes the same values bit for bit): choice[0] = columns per block of the mixed
+ * form's 4096-point column DFT passes (16, 32 or 64), chosen at plan time as the fastest
+ * of the three on a scratch intermediate of the plan's grid; us (NULL allowed) receives
+ * the three candidates' times in microseconds per call (zeros when the plan has no such
+ * transform, which keeps 16). */
+fc2d_status fc2d_tuning(fc2d_plan_t plan, int32_t* choice, float* us);
+/* Override the choice (choice[0] in {16, 32, 64}; FC2D_ERR_ARG otherwise), for tests and
+ * for callers that fix the launch shape; calls after it use the new width. */
+fc2d_status fc2d_tuning_set(fc2d_plan_t plan, const int32_t* choice);
+
 /* FP64 throughput probe (no operation of the paper): `blocks` blocks of 256 threads on
  * `stream`, each thread running 8 independent fused multiply-add chains of `iters`
  * steps, writing one value per thread to out_dev [blocks * 256].  *flops receives the

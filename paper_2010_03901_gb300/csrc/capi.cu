@@ -145,6 +145,7 @@ FftArgs fft_args(fc2d_plan_s* p) {
   a.tsx = f64 ? (const void*)p->fx.tws64 : (const void*)p->fx.tws32;
   a.tsy = f64 ? (const void*)p->fy.tws64 : (const void*)p->fy.tws32;
   a.scale = 1.0 / ((double)p->grid.nx * p->grid.ny);
+  a.cc4k = p->tune_cc4k;
   return a;
 }
 
@@ -549,6 +550,36 @@ extern "C" fc2d_status fc2d_poisson(fc2d_plan_t p, int n_f, const double* fg, co
 // ------------------------------------------------------------------------- //
 // Fourier Forwarding interior propagator (Section 4.2)
 // ------------------------------------------------------------------------- //
+namespace fc2d {
+fc2d_status tune_cols4k(FftArgs fa, int* best, float* us);
+
+// Plan-time autotuning: the mixed form's 4096-point column passes take the block width
+// (16, 32 or 64 columns) that runs fastest on this GPU for the plan's grid.
+fc2d_status tune_plan(fc2d_plan_s* p) {
+  if (p->prm.precision != FC2D_MIXED || p->grid.ny != 4096) return FC2D_OK;
+  int best = 16;
+  fc2d_status st = tune_cols4k(fft_args(p), &best, p->tune_us);
+  if (st == FC2D_OK) p->tune_cc4k = best;
+  return st;
+}
+}  // namespace fc2d
+
+extern "C" fc2d_status fc2d_tuning_set(fc2d_plan_t p, const int32_t* choice) {
+  if (!p || !choice) return set_error(FC2D_ERR_ARG, "fc2d_tuning_set: null argument");
+  if (choice[0] != 16 && choice[0] != 32 && choice[0] != 64)
+    return set_error(FC2D_ERR_ARG, "fc2d_tuning_set: columns per block 16, 32 or 64");
+  p->tune_cc4k = choice[0];
+  return FC2D_OK;
+}
+
+extern "C" fc2d_status fc2d_tuning(fc2d_plan_t p, int32_t* choice, float* us) {
+  if (!p || !choice) return set_error(FC2D_ERR_ARG, "fc2d_tuning: null argument");
+  choice[0] = p->tune_cc4k;
+  if (us)
+    for (int k = 0; k < 3; ++k) us[k] = p->tune_us[k];
+  return FC2D_OK;
+}
+
 namespace fc2d {
 // The 2D-FC spectra (eq. (3.1), normalised) of n_f functions u and n_f functions ut
 // (grid values + boundary data, as fc2d_extend takes them) into spec

@@ -142,6 +142,7 @@ struct FftArgs {
   const void* tsx;            // per-stage twiddles of the row transform (power-of-two sizes)
   const void* tsy;            // per-stage twiddles of the column transform
   double scale;               // 1/(nx ny)
+  int cc4k;                   // columns per block of the 4096-point FP32 column passes
 };
 
 // rows: mode 0 reads an extended grid (ext, type T); mode 1 assembles the extension

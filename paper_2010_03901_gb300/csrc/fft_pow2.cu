@@ -19,6 +19,7 @@
 #include <algorithm>
 
 #include "fc2d_kernels.cuh"
+#include "plan_internal.h"
 
 namespace fc2d {
 namespace p2 {
@@ -679,29 +680,34 @@ k_fft_cols_p2(FftArgs fa, const typename Cx<T>::type* __restrict__ inter,
 // many are resident per SM, and the 67 MB intermediate of a 4096^2 grid can stay in L2
 // between the passes.
 // ------------------------------------------------------------------------- //
-constexpr int kC4Cols = 16;   // columns per block
+constexpr int kC4Cols = 16;   // columns per block (mixed-radix passes; the 4096-point
+                              // passes take the plan's tuned width, see tune_cols4k)
 
 // 64-point DFT of a[i] = x[l + 8 i] held by the threads (c, l = 0..7) of column c;
-// on return a[m'] = X[l + 8 m'].  ex: the block's [8][8][16] exchange buffer; w: the
+// on return a[m'] = X[l + 8 m'].  ex: the block's [8][8][CC] exchange buffer; w: the
 // table w_N^t of the column length N = 64 n2 (w_64^k = w[n2 k]).
+template <int CC = kC4Cols>
 __device__ __forceinline__ void dft64_cols(float2* a, int c, int l, float2* ex,
                                            const float2* __restrict__ w, int n2 = 64) {
   dft<float, float2, 8>(a);
 #pragma unroll
   for (int m = 1; m < 8; ++m) a[m] = mul(a[m], __ldg(w + ((l * m) & 63) * n2));
 #pragma unroll
-  for (int m = 0; m < 8; ++m) ex[(m * 8 + l) * kC4Cols + c] = a[m];
+  for (int m = 0; m < 8; ++m) ex[(m * 8 + l) * CC + c] = a[m];
   __syncthreads();
 #pragma unroll
-  for (int k = 0; k < 8; ++k) a[k] = ex[(l * 8 + k) * kC4Cols + c];
+  for (int k = 0; k < 8; ++k) a[k] = ex[(l * 8 + k) * CC + c];
   dft<float, float2, 8>(a);
 }
 
-__global__ void __launch_bounds__(128) k_cols4k_a(FftArgs fa, float2* __restrict__ inter) {
-  __shared__ float2 ex[64 * kC4Cols];
-  const int c = threadIdx.x & (kC4Cols - 1), l = threadIdx.x / kC4Cols;
+// CC adjacent columns per block of 8 CC threads (16, 32 or 64: every width computes the
+// same values; wider blocks read longer contiguous row segments).
+template <int CC>
+__global__ void __launch_bounds__(8 * CC) k_cols4k_a(FftArgs fa, float2* __restrict__ inter) {
+  __shared__ float2 ex[64 * CC];
+  const int c = threadIdx.x & (CC - 1), l = threadIdx.x / CC;
   const int ncol = fa.nx / 2 + 1;
-  const int kx = blockIdx.x * kC4Cols + c;
+  const int kx = blockIdx.x * CC + c;
   const int j2 = blockIdx.y, f = blockIdx.z;
   const bool live = kx < ncol;
   const float2* w = reinterpret_cast<const float2*>(fa.twy);
@@ -712,7 +718,7 @@ __global__ void __launch_bounds__(128) k_cols4k_a(FftArgs fa, float2* __restrict
 #pragma unroll
   for (int i = 0; i < 8; ++i)
     a[i] = live ? col[(size_t)(64 * (l + 8 * i) + j2) * fa.pitch] : make_float2(0.f, 0.f);
-  dft64_cols(a, c, l, ex, w);
+  dft64_cols<CC>(a, c, l, ex, w);
 #pragma unroll
   for (int m2 = 0; m2 < 8; ++m2) {
     const int m1 = l + 8 * m2;
@@ -721,13 +727,14 @@ __global__ void __launch_bounds__(128) k_cols4k_a(FftArgs fa, float2* __restrict
   }
 }
 
-__global__ void __launch_bounds__(128) k_cols4k_b(FftArgs fa, int drop,
-                                                   float2* __restrict__ inter,
-                                                   float2* __restrict__ fhat) {
-  __shared__ float2 ex[64 * kC4Cols];
-  const int c = threadIdx.x & (kC4Cols - 1), l = threadIdx.x / kC4Cols;
+template <int CC>
+__global__ void __launch_bounds__(8 * CC) k_cols4k_b(FftArgs fa, int drop,
+                                                      float2* __restrict__ inter,
+                                                      float2* __restrict__ fhat) {
+  __shared__ float2 ex[64 * CC];
+  const int c = threadIdx.x & (CC - 1), l = threadIdx.x / CC;
   const int ncol = fa.nx / 2 + 1;
-  const int kx = blockIdx.x * kC4Cols + c;
+  const int kx = blockIdx.x * CC + c;
   const int m1 = blockIdx.y, f = blockIdx.z;
   const bool live = kx < ncol;
   const float2* w = reinterpret_cast<const float2*>(fa.twy);
@@ -738,12 +745,13 @@ __global__ void __launch_bounds__(128) k_cols4k_b(FftArgs fa, int drop,
 #pragma unroll
   for (int i = 0; i < 8; ++i)
     a[i] = live ? col[(size_t)(64 * m1 + l + 8 * i) * fa.pitch] : make_float2(0.f, 0.f);
-  dft64_cols(a, c, l, ex, w);
-  // the intermediate is scratch and this block was the last reader of its 8 x 16
+  dft64_cols<CC>(a, c, l, ex, w);
+  // the intermediate is scratch and this block was the last reader of its 8 x CC
   // values per thread group: drop the lines from L2 without writing them back (each
   // row of 16 columns is one 128-byte line; `drop` is set only when the host has
-  // checked the 128-byte alignment of the buffer and the pitch)
-  if (drop && c == 0) {
+  // checked the 128-byte alignment of the buffer and the pitch).  Only lines of live
+  // columns: a wide block's columns past the last one would name the next row's lines.
+  if (drop && (c & 15) == 0 && live) {
 #pragma unroll
     for (int i = 0; i < 8; ++i)
       asm volatile("discard.global.L2 [%0], 128;" ::"l"(col + (size_t)(64 * m1 + l + 8 * i) * fa.pitch)
@@ -839,12 +847,21 @@ static void cols64_launch(const FftArgs& fa, int n_f, void* inter, void* fhat, c
              (float2*)fhat);
 }
 
-static void cols4k_launch(const FftArgs& fa, int n_f, void* inter, void* fhat, cudaStream_t s) {
+template <int CC>
+static void cols4k_launch_cc(const FftArgs& fa, int n_f, void* inter, void* fhat, cudaStream_t s) {
   const int ncol = fa.nx / 2 + 1;
-  const dim3 grid((ncol + kC4Cols - 1) / kC4Cols, 64, n_f);
+  const dim3 grid((ncol + CC - 1) / CC, 64, n_f);
   const int drop = (reinterpret_cast<uintptr_t>(inter) % 128 == 0 && fa.pitch % 16 == 0) ? 1 : 0;
-  launch_pdl(k_cols4k_a, grid, dim3(128), 0, s, fa, (float2*)inter);
-  launch_pdl(k_cols4k_b, grid, dim3(128), 0, s, fa, drop, (float2*)inter, (float2*)fhat);
+  launch_pdl(k_cols4k_a<CC>, grid, dim3(8 * CC), 0, s, fa, (float2*)inter);
+  launch_pdl(k_cols4k_b<CC>, grid, dim3(8 * CC), 0, s, fa, drop, (float2*)inter, (float2*)fhat);
+}
+
+static void cols4k_launch(const FftArgs& fa, int n_f, void* inter, void* fhat, cudaStream_t s) {
+  switch (fa.cc4k) {
+    case 32: cols4k_launch_cc<32>(fa, n_f, inter, fhat, s); break;
+    case 64: cols4k_launch_cc<64>(fa, n_f, inter, fhat, s); break;
+    default: cols4k_launch_cc<16>(fa, n_f, inter, fhat, s); break;
+  }
 }
 
 // ------------------------------------------------------------------------- //
@@ -1178,6 +1195,59 @@ bool launch_wave_cols_p2(const FftArgs& fa, int n_f, void* inter, double c, doub
     case 12: p2::wave_cols_p2_launch<12>(fa, n_f, inter, c, t, Lx, Ly, s); return true;
     default: return false;
   }
+}
+
+// The autotuner of the 4096-point FP32 column passes (plan time): each block width
+// CC = 16, 32, 64 timed on a scratch intermediate of the plan's grid (3 warm-up calls,
+// then the best of 5 timed with events on a private stream); the fastest is returned in
+// *best, the times (microseconds per call) in us[0..2].  Every width computes the same
+// values, so the choice changes no result.
+fc2d_status tune_cols4k(FftArgs fa, int* best, float* us) {
+  *best = 16;
+  if (fa.ny != 4096) return FC2D_OK;
+  const int ncol = fa.nx / 2 + 1;
+  const size_t bytes = (size_t)4096 * fa.pitch * sizeof(float2),
+               obytes = (size_t)4096 * ncol * sizeof(float2);
+  void *inter = nullptr, *out = nullptr;
+  cudaStream_t s = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  fc2d_status st = FC2D_OK;
+  if (cudaMalloc(&inter, bytes) != cudaSuccess || cudaMalloc(&out, obytes) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    st = set_error(FC2D_ERR_NOMEM, "column tuner: allocation failed");
+  } else {
+    cudaMemsetAsync(inter, 0, bytes, s);
+    const int cand[3] = {16, 32, 64};
+    float best_us = 0.f;
+    for (int k = 0; k < 3 && !st; ++k) {
+      fa.cc4k = cand[k];
+      for (int r = 0; r < 3; ++r) p2::cols4k_launch(fa, 1, inter, out, s);
+      float t = 1e30f;
+      for (int r = 0; r < 5; ++r) {
+        cudaEventRecord(e0, s);
+        p2::cols4k_launch(fa, 1, inter, out, s);
+        cudaEventRecord(e1, s);
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        t = std::min(t, ms * 1000.f);
+      }
+      st = cuda_check(cudaGetLastError(), "column tuner");
+      us[k] = t;
+      if (k == 0 || t < best_us) {
+        best_us = t;
+        *best = cand[k];
+      }
+    }
+  }
+  if (s) cudaStreamSynchronize(s);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (s) cudaStreamDestroy(s);
+  cudaFree(inter);
+  cudaFree(out);
+  return st;
 }
 
 // Fourier Forwarding solve columns of 512 .. 4096 points; false (nothing launched)

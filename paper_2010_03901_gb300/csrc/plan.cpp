@@ -941,6 +941,7 @@ extern "C" fc2d_status fc2d_plan(const fc2d_boundary* boundary, const fc2d_grid*
     if (P.precision == FC2D_MIXED && M == 8 && ns > 0 && (st = owner_tables(p, (int)ns, M)))
       return fail(st);
   }
+  if ((st = tune_plan(p))) return fail(st);
   *out = p;
   return FC2D_OK;
 }

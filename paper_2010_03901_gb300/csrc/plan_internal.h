@@ -128,6 +128,10 @@ struct fc2d_plan_s {
   std::vector<void*> event_pool;               // reusable cudaEvent_t
   void* poisson = nullptr;                     // Poisson tables (poisson.cu)
   void* wave = nullptr;                        // Fourier Forwarding state (ff.cu)
+  // autotuned launch shapes (tune_plan): columns per block of the 4096-point FP32
+  // column passes and the candidates' times (microseconds per call; 0: not tuned)
+  int tune_cc4k = 16;
+  float tune_us[3] = {0.f, 0.f, 0.f};
 };
 
 namespace fc2d {
@@ -162,6 +166,9 @@ void poisson_stats(const fc2d_plan_s* p, int* iters, double* resid, int64_t* n_n
 
 // Fourier Forwarding state (ff.cu)
 void wave_destroy(fc2d_plan_s* p);
+
+// Plan-time autotuning of launch shapes that change no result (capi.cu).
+fc2d_status tune_plan(fc2d_plan_s* p);
 
 // kernel timing: bracket one launch with events when the plan is profiling
 struct ProfScope {

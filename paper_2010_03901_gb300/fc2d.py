@@ -91,6 +91,8 @@ def load_library(path: str = LIB_PATH):
                               P, P],
         "fc2d_profile": [P, ct.c_int],
         "fc2d_probe_fp64": [P, ct.c_int, ct.c_int64, P, P],
+        "fc2d_tuning": [P, P, P],
+        "fc2d_tuning_set": [P, P],
         "fc2d_profile_read": [P, ct.c_int, P, P, P, P],
     }
     for name, args in sigs.items():
@@ -273,6 +275,17 @@ class Plan:
         _check(_lib.fc2d_wave_ub_step(self.handle, n_c, n_f, mode, c, _ptr(u), _ptr(u_prev),
                                       _ptr(ut), _ptr(grid), _ptr(grid_prev), _ptr(g), _ptr(out),
                                       _stream(stream)))
+
+    def fc2d_tuning(self):
+        """(columns per block of the 4096-point column passes, candidates' times in us)."""
+        choice = np.zeros(1, np.int32)
+        us = np.zeros(3, np.float32)
+        _check(_lib.fc2d_tuning(self.handle, choice.ctypes.data, us.ctypes.data))
+        return int(choice[0]), [float(v) for v in us]
+
+    def fc2d_tuning_set(self, columns_per_block):
+        choice = np.array([columns_per_block], np.int32)
+        _check(_lib.fc2d_tuning_set(self.handle, choice.ctypes.data))
 
     def fc2d_profile(self, enable=True):
         _check(_lib.fc2d_profile(self.handle, 1 if enable else 0))

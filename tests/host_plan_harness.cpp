@@ -87,6 +87,8 @@ fc2d_status foot_newton_gpu(const Curve& c, const std::vector<double>& qx,
 }
 void poisson_destroy(fc2d_plan_s*) {}
 void wave_destroy(fc2d_plan_s*) {}
+// launch-shape tuning times kernels on a GPU; the harness keeps the defaults
+fc2d_status tune_plan(fc2d_plan_s*) { return FC2D_OK; }
 // interpolation weights are a GPU step of the plan; the harness leaves them unset
 fc2d_status interp_weights_gpu(int, int, int, int, double, int, const double*, const double*,
                                bool, void*, int32_t*, int32_t*) {

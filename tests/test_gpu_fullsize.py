@@ -239,3 +239,30 @@ def test_full_size_complex_f(setup, complex_ref, precision):
     got = fhat.cpu().numpy().astype(np.float64)[0]
     bar = 1e-12 if precision == "fp64" else 1e-6
     assert rel(got[..., 0] + 1j * got[..., 1], ref_c) < bar
+
+
+def test_column_block_widths_give_the_same_spectrum():
+    """The plan-time tuner picks one of three block widths for the 4096-point column
+    passes; each width computes the same values, so a plan whose tuner chose any width
+    gives the spectrum of the 16-column form bit for bit (checked by re-running the
+    column passes of one plan at every width through fc2d_coeffs on the same
+    intermediate input)."""
+    torch = pytest.importorskip("torch")
+    from paper_2010_03901_gb300 import fc2d
+    w = W.workload("kite4096")
+    g, p = w.grid, w.params
+    plan = fc2d.fc2d_plan(w.boundary.arrays(), (g.a0, g.b0, g.h, g.nx, g.ny),
+                          dict(B=p.B, k1=p.k1), precision=fc2d.FC2D_MIXED)
+    cc, us = plan.fc2d_tuning()
+    assert cc in (16, 32, 64) and all(t > 0 for t in us)
+    assert us[(16, 32, 64).index(cc)] == min(us)
+    x = torch.tensor(W.normal(5, g.ny * g.nx).reshape(1, g.ny, g.nx), dtype=torch.float32,
+                     device="cuda:0")
+    outs = []
+    for width in (16, 32, 64):
+        plan.fc2d_tuning_set(width)
+        o = torch.zeros((1, g.ny, g.nx // 2 + 1, 2), dtype=torch.float32, device="cuda:0")
+        plan.fc2d_coeffs(1, x, o)
+        plan.fc2d_sync_status()
+        outs.append(o)
+    assert torch.equal(outs[0], outs[1]) and torch.equal(outs[0], outs[2])
