@@ -54,7 +54,6 @@ ROT = 3   # rotating input/output buffers of the timed steps
 KERNELS_PER_SCOPE = {("mixed", "fft_cols", 4096): 2}
 
 MEASURED_TRAFFIC = {
-    ("mixed", "fft_cols"): 67670784 + 7692544 + 67690240 + 8772608,  # k_cols4k_a + k_cols4k_b
     ("mixed", "fft_rows_fused"): 70923264 + 18913792,
     ("mixed", "gather_blend_interp_tc"): 34112000 + 0,
     ("fp64", "fft_rows_fused"): 72384768 + 75083008,
@@ -508,16 +507,21 @@ def measure(fc2d, torch, w, precision, K, warmup, world, dev, fg_h, fb_h, sample
     avg_s = tot_ms / launches / 1e3
     a = alg.get(dom, {"bytes": 0, "flops": 0})
     t_hbm = a["bytes"] / (hbm * 1e9)
-    t_alu = a["flops"] / (FP64_PEAK_TFLOPS * 1e12) if fp64 else 0.0
+    fp64_tf = fp64_rate(fc2d, torch, dev) if fp64 else FP64_PEAK_TFLOPS
+    t_alu = a["flops"] / (fp64_tf * 1e12) if fp64 else 0.0
     if fp64 and t_alu > t_hbm:
-        roof = {"bound": "alu", "achieved": a["flops"] / avg_s / 1e12, "peak": FP64_PEAK_TFLOPS,
-                "unit": "TFLOP/s", "peak_source": "nominal FP64 rate"}
+        roof = {"bound": "alu", "achieved": a["flops"] / avg_s / 1e12, "peak": fp64_tf,
+                "unit": "TFLOP/s", "peak_source": "measured FP64 FMA rate (fp64_peak)"}
     else:
         roof = {"bound": "hbm", "achieved": a["bytes"] / avg_s / 1e9, "peak": hbm,
                 "unit": "GB/s", "peak_source": src}
     roof["frac"] = roof["achieved"] / roof["peak"]
     roof["kernel"] = dom
     roof["traffic"] = MEASURED_TRAFFIC.get((precision, dom))
+    roof["traffic_source"] = ("stored: one ncu capture (dram__bytes_read.sum + "
+                              "dram__bytes_write.sum, cold cache) of this kernel on this "
+                              "workload, not measured in this run" if roof["traffic"] else
+                              "no capture of the current kernel")
     kernels = {k: {"launches": v[0], "avg_us": 1e3 * v[1] / v[0],
                    "share": v[1] / sum(x[1] for x in prof.values())} for k, v in prof.items()}
     cc, cc_us = plan.fc2d_tuning()
@@ -679,8 +683,9 @@ def ff_interior_kite2048(fc2d, torch, dev, steps=20):
             "ms_per_large_step": ms, "large_steps_per_s": 1e3 / ms,
             "value": g.nx * g.ny / (ms * 1e-3), "unit": UNIT, "kernels_ms": kms,
             "roofline": {"bound": "alu", "kernel": "wave_cols (k_wave_cols_p2)", "achieved": ach,
-                         "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                         "frac": ach / FP64_PEAK_TFLOPS, "peak_source": "nominal FP64 rate",
+                         "peak": fp64_rate(fc2d, torch, dev), "unit": "TFLOP/s",
+                         "frac": ach / fp64_rate(fc2d, torch, dev),
+                         "peak_source": "measured FP64 FMA rate (fp64_peak)",
                          "flops": "4 column DFTs x 5 N log2 N, modal advance not counted"}}
 
 
@@ -705,6 +710,16 @@ def fp64_peak(fc2d, torch, dev, iters=1 << 16):
         best = max(best, flops / (e0.elapsed_time(e1) * 1e-3) / 1e12)
     return {"tflops": best, "clocks": clk.stop(), "how": f"{blocks} blocks x 256 threads x 8 "
             f"independent FMA chains x {iters} steps, best of 3 (CUDA events)"}
+
+
+_FP64_RATE = {}
+
+
+def fp64_rate(fc2d, torch, dev):
+    """The measured FP64 rate (TFLOP/s, fp64_peak), once per process."""
+    if "tflops" not in _FP64_RATE:
+        _FP64_RATE.update(fp64_peak(fc2d, torch, dev))
+    return _FP64_RATE["tflops"]
 
 
 def _disk_eigenmode_error(fc2d, torch, dev, h=0.005, n_c=8, T_target=2.0):
@@ -786,7 +801,10 @@ def ff_solve_kite2048(fc2d, torch, dev, n_large=2, squares=False, extras=True):
     counts = plan.fc2d_wave_band_info(n_c, squares=squares)
     S = 8 * n_c
     small = n_large * S
-    peak = fp64_peak(fc2d, torch, dev) if extras else None
+    peak = (dict(_FP64_RATE) if "tflops" in _FP64_RATE else None) if extras else None
+    if extras and peak is None:
+        fp64_rate(fc2d, torch, dev)
+        peak = dict(_FP64_RATE)
     kms = {k: {"launches": v[0], "ms_per_launch": v[1] / v[0], "ms_total": v[1]}
            for k, v in prof.items()}
     # dominant kernel, FLOPs of one launch for n_f functions (5 N log2 N per length-N
@@ -1047,8 +1065,34 @@ EXTRA_LINES = {"poisson_star1024": poisson_star1024,
                "stars8_batched": stars8_batched}
 
 
+def ff_probe(name):
+    """One large step of the Fourier Forwarding solve on workload `name` (d = 4, n_c = 8,
+    8 Gaussians, zero Dirichlet data), with the full inverse DFT and then with the small
+    squares: a small, self-contained command for profilers."""
+    import torch
+    from paper_2010_03901_gb300.build import build
+    build()
+    from paper_2010_03901_gb300 import fc2d
+    w = W.workload(name, d=4, M=7)
+    g, p = w.grid, w.params
+    plan = fc2d.fc2d_plan(w.boundary.arrays(), (g.a0, g.b0, g.h, g.nx, g.ny),
+                          dict(d=4, M=7, B=p.B, k1=p.k1))
+    fs = [W.gaussian_sum(w.boundary, 1, 50 + k, wmin=0.05, wmax=0.05, margin=0.35)
+          for k in range(8)]
+    U0 = torch.tensor(np.stack([W.grid_values(w, f) for f in fs]), device="cuda:0")
+    out = {}
+    for squares in (False, True):
+        u, ut = U0.clone(), torch.zeros_like(U0)
+        plan.fc2d_forward_wave(8, 1.0, 8, 1, u, ut, squares=squares)
+        plan.fc2d_sync_status()
+        out["squares" if squares else "full"] = float(u.abs().max())
+    print(json.dumps({"ff_probe": name, "max_abs_u": out}), flush=True)
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
+    ap.add_argument("--ff-probe", default=None,
+                    help="run one Fourier Forwarding large step on this workload and exit")
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=400)
     ap.add_argument("--warmup", type=int, default=10)
@@ -1062,6 +1106,9 @@ def main(argv=None):
                     help="comma-separated extra lines to run (default: all of "
                          + ", ".join(EXTRA_LINES) + ")")
     args = ap.parse_args(argv)
+    if args.ff_probe:
+        ff_probe(args.ff_probe)
+        return
     bad = [n for n in args.extra.split(",") if n not in EXTRA_LINES]
     if bad:
         ap.error(f"unknown extra line(s): {', '.join(bad)}")
