@@ -457,25 +457,30 @@ __global__ void __launch_bounds__(256, 2) k_gather_blend_tc(GatherArgs g, TcArgs
 }
 
 // ------------------------------------------------------------------------- //
-// Blend and interpolation in one kernel (mixed form, M = 8).  CTA (c, fb) computes the
-// kTcComputed = 64 normals start_c + i (mod B) of NF functions fb NF .. fb NF + NF - 1 as
-// above (MMA N = 64 per function, 16 warps, one gather pass per function), keeps their
+// Blend and interpolation in one kernel (mixed form, M = 8).  CTA (c, fb) of NT threads
+// computes the kTcComputed = 64 normals start_c + i (mod B) of NF functions fb NF ..
+// fb NF + NF - 1 as above (MMA N = 64 per function; the gather takes NT / 8 normals per
+// pass, groups of 8 lanes, and skips the warps whose normals lie past the last one its
+// points use, start_{c+1} - start_c + M - 1, leaving their C columns zero), keeps their
 // strip values in shared [64][ldS] tiles (zero padded; ldS a multiple of 4, >= Cr + 12,
 // and not 16 mod 32 words so that neighbouring rows fall in different banks) and
 // interpolates the strip points it owns (Section 3.4) from those tiles, two per thread
-// in flight, writing the strip-point values; F is not written.  With NF = 2 (calls of
-// several functions) the stencil tables, the TMEM allocation, the A_r tiles and each
-// point's interpolation weights serve both functions.
+// in flight, writing the strip-point values; F is not written.  With NF = 2 the stencil
+// tables, the TMEM allocation, the A_r tiles and each point's interpolation weights
+// would serve two functions; the launcher uses NF = 1.  NT = 512 runs one CTA per SM
+// (calls of one function), NT = 256 two, whose serial phases (tables, gather, MMAs,
+// interpolation) then overlap (calls of several functions: 3% faster on the eight-star
+// workload than two functions per 512-thread CTA).
 // ------------------------------------------------------------------------- //
-constexpr int kGiThreads = kTcComputed * 8;
 template <int NF> __host__ __device__ constexpr int gi_tmem_cols() { return 128 * NF; }  // 2 tiles of 64 per function
 template <int NF> __host__ __device__ constexpr int gi_stage_off() {
   return 2 * kMaxCrPad * 32 + 2 * NF * kTcComputed * 32;
 }
-template <int NF> __host__ __device__ constexpr int gi_bar_off() {
-  return gi_stage_off<NF>() + NF * kTcComputed * kTcMaxLd * 4;
+// the mbarrier and the TMEM address after the NF staging tiles of [64][ldS] floats
+template <int NF> __host__ __device__ inline int gi_bar_off(int ldS) {
+  return gi_stage_off<NF>() + NF * kTcComputed * ldS * 4;
 }
-template <int NF> __host__ __device__ constexpr int gi_smem() { return gi_bar_off<NF>() + 16; }
+template <int NF> __host__ __device__ inline int gi_smem(int ldS) { return gi_bar_off<NF>(ldS) + 16; }
 
 struct OwnArgs {
   const int32_t* off;    // [n_own + 1]
@@ -487,9 +492,10 @@ struct OwnArgs {
   float* vals;           // [n_f][n_strip]
 };
 
-template <int NF>
-__global__ void __launch_bounds__(kGiThreads, 1) k_gather_interp_tc(GatherArgs g, TcArgs a,
-                                                                      OwnArgs o, int n_f) {
+template <int NF, int NT>
+__global__ void __launch_bounds__(NT, 512 / NT) k_gather_interp_tc(GatherArgs g, TcArgs a,
+                                                                    OwnArgs o, int n_f) {
+  static_assert(NT == 256 || NT == 512, "k_gather_interp_tc: 256 or 512 threads");
   constexpr int MM = 8;
   constexpr uint32_t kCols = gi_tmem_cols<NF>();
   extern __shared__ __align__(1024) unsigned char smem[];
@@ -499,7 +505,7 @@ __global__ void __launch_bounds__(kGiThreads, 1) k_gather_interp_tc(GatherArgs g
   unsigned char* c_hi = smem + 2 * kMaxCrPad * 32;
   unsigned char* c_lo = c_hi + NF * kTcComputed * 32;
   float* stage0 = reinterpret_cast<float*>(smem + gi_stage_off<NF>());  // NF x [64][ldS]
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + gi_bar_off<NF>());
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + gi_bar_off<NF>(a.ldF));
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mbar + 1);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int c = blockIdx.x, f0 = blockIdx.y * NF;
@@ -522,28 +528,43 @@ __global__ void __launch_bounds__(kGiThreads, 1) k_gather_interp_tc(GatherArgs g
     stage0[r * ldS + a.Cr + 1 + (idx - r * (ldS - a.Cr - 1))] = 0.f;
   }
   {
-    constexpr int kPer = (kMaxCrPad * 8 + kGiThreads - 1) / kGiThreads;
+    constexpr int kPer = (kMaxCrPad * 8 + NT - 1) / NT;
     float hi[kPer], lo[kPer];
 #pragma unroll
     for (int u = 0; u < kPer; ++u) {
-      const int idx = tid + u * kGiThreads, q = idx >> 3, k = idx & 7;
+      const int idx = tid + u * NT, q = idx >> 3, k = idx & 7;
       const bool on = idx < kMaxCrPad * 8 && q < a.Cr && k < a.d;
       hi[u] = on ? __ldg(a.Ar_hi + q * a.d + k) : 0.f;
       lo[u] = on ? __ldg(a.Ar_lo + q * a.d + k) : 0.f;
     }
 #pragma unroll
     for (int u = 0; u < kPer; ++u) {
-      const int idx = tid + u * kGiThreads, q = idx >> 3, k = idx & 7;
+      const int idx = tid + u * NT, q = idx >> 3, k = idx & 7;
       if (idx < kMaxCrPad * 8) {
         *reinterpret_cast<float*>(a_hi + kmaj_off(q, k)) = hi[u];
         *reinterpret_cast<float*>(a_lo + kmaj_off(q, k)) = lo[u];
       }
     }
   }
-  // matching values and Gram coefficients of the 64 normals into the C tiles
+  // matching values and Gram coefficients of the 64 normals into the C tiles, NT / 8
+  // normals per pass; a warp whose four normals all lie past `need` writes zero columns
   const int s = lane & 7, g0 = lane & ~7;
-  const int ln = warp * 4 + (lane >> 3);
-  {
+  const int need = min(kTcComputed, __ldg(o.start + c + 1) - __ldg(o.start + c) + MM - 1);
+#pragma unroll 1
+  for (int pass = 0; pass < kTcComputed * 8 / NT; ++pass) {
+    const int ln = pass * (NT / 8) + warp * 4 + (lane >> 3);
+    if (pass * (NT / 8) + warp * 4 >= need) {  // warp-uniform
+      if (pass == 0) {
+        pdl_wait();
+        pdl_trigger();
+      }
+      for (int ff = 0; ff < nfl; ++ff) {
+        *reinterpret_cast<float*>(c_hi + ff * kTcComputed * 32 + kmaj_off(ln, s)) = 0.f;
+        *reinterpret_cast<float*>(c_lo + ff * kTcComputed * 32 + kmaj_off(ln, s)) = 0.f;
+        if (s == 0) stage0[(size_t)ff * kTcComputed * ldS + ln * ldS] = 0.f;
+      }
+      continue;
+    }
     const int M = MM, d = g.d, NS = M - 1;
     const bool star_lane = s < NS;
     const int pp = (__ldg(o.start + c) + ln) % g.B;
@@ -561,8 +582,10 @@ __global__ void __launch_bounds__(kGiThreads, 1) k_gather_interp_tc(GatherArgs g
     for (int e = 0; e < MM; ++e) wnv[e] = s < nq ? __ldg(wn + e) : 0.0;
 #pragma unroll
     for (int i = 0; i < kMaxD; ++i) qv[i] = (s < d && i < d) ? __ldg(g.Q + i * d + s) : 0.0;
-    pdl_wait();
-    pdl_trigger();
+    if (pass == 0) {
+      pdl_wait();
+      pdl_trigger();
+    }
     for (int ff = 0; ff < nfl; ++ff) {
     const int f = f0 + ff;
     float* stage = stage0 + (size_t)ff * kTcComputed * ldS;
@@ -707,13 +730,23 @@ __global__ void __launch_bounds__(kGiThreads, 1) k_gather_interp_tc(GatherArgs g
   }
 }
 
-fc2d_status launch_gather_interp_tc(const GatherArgs& g, int n_f, int ldS, const float* Ar_hi,
-                                    const float* Ar_lo, const int32_t* own_off,
-                                    const int32_t* own_k, const int32_t* own_pack,
-                                    const float* own_w, const int32_t* own_start, int n_own,
-                                    int n_strip, float* vals, int* status, cudaStream_t s) {
+template <int NF, int NT>
+static cudaError_t gi_launch(int n_own, int n_f, const GatherArgs& g, const TcArgs& a,
+                             const OwnArgs& o, cudaStream_t s) {
+  const int sm = gi_smem<NF>(a.ldF);
+  cudaFuncSetAttribute(k_gather_interp_tc<NF, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  return launch_pdl(k_gather_interp_tc<NF, NT>, dim3(n_own, (n_f + NF - 1) / NF), dim3(NT),
+                    (size_t)sm, s, g, a, o, n_f);
+}
+
+fc2d_status launch_gather_interp_tc(const GatherArgs& g, int n_f, int nt, int ldS,
+                                    const float* Ar_hi, const float* Ar_lo,
+                                    const int32_t* own_off, const int32_t* own_k,
+                                    const int32_t* own_pack, const float* own_w,
+                                    const int32_t* own_start, int n_own, int n_strip,
+                                    float* vals, int* status, cudaStream_t s) {
   if (g.Cr > kMaxCrPad || g.d > 8 || g.M != 8 || ldS % 4 || ldS < g.Cr + 12 ||
-      ldS + 4 > kTcMaxLd || !own_off)
+      ldS + 4 > kTcMaxLd || !own_off || (nt != 256 && nt != 512))
     return set_error(FC2D_ERR_UNSUPPORTED, "blend + interpolation kernel: M = 8, d <= 8");
   TcArgs a{};
   a.n_cols = n_f * g.B;
@@ -725,19 +758,9 @@ fc2d_status launch_gather_interp_tc(const GatherArgs& g, int n_f, int ldS, const
   a.Ar_lo = Ar_lo;
   a.status = status;
   OwnArgs o{own_off, own_k, own_pack, own_w, own_start, n_own, n_strip, vals};
-  // two functions per CTA when the call has several
-  if (n_f == 1) {
-    cudaFuncSetAttribute(k_gather_interp_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         gi_smem<1>());
-    return cuda_check(launch_pdl(k_gather_interp_tc<1>, dim3(n_own, 1), dim3(kGiThreads),
-                                 (size_t)gi_smem<1>(), s, g, a, o, n_f),
-                      "blend + interpolation launch");
-  }
-  cudaFuncSetAttribute(k_gather_interp_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       gi_smem<2>());
-  return cuda_check(launch_pdl(k_gather_interp_tc<2>, dim3(n_own, (n_f + 1) / 2),
-                               dim3(kGiThreads), (size_t)gi_smem<2>(), s, g, a, o, n_f),
-                    "blend + interpolation launch");
+  const cudaError_t e = nt == 256 ? gi_launch<1, 256>(n_own, n_f, g, a, o, s)
+                                  : gi_launch<1, 512>(n_own, n_f, g, a, o, s);
+  return cuda_check(e, "blend + interpolation launch");
 }
 
 fc2d_status launch_gather_blend_tc(const GatherArgs& g, int n_f, int ldF, const float* Ar_hi,

@@ -190,15 +190,16 @@ fc2d_status strip_values(fc2d_plan_s* p, int n_f, const double* fg, const double
   const bool f64 = p->prm.precision == FC2D_FP64;
   void* F = ws(p, L.oF);
   if (!f64 && p->dev.own[0].off) {
-    // mixed form, M = 8: blend and interpolation in one kernel, F stays on chip (two
-    // functions per CTA when n_f > 1).  One CTA per SM when the call's CTAs fit in about
+    // mixed form, M = 8: blend and interpolation in one kernel, F stays on chip.  One
+    // function: a CTA of 512 threads per SM (own[0]).  Several: CTAs of 256 threads, two
+    // per SM, one function each; the balanced ranges while the call's CTAs fit in about
     // one wave, else the fewest CTAs.
-    const int64_t per_range = n_f == 1 ? 1 : (n_f + 1) / 2;
-    const auto& o = (p->dev.own[1].n && per_range * p->dev.own[0].n > 3 * (int64_t)p->n_sm / 2)
+    const auto& o = (n_f > 1 && p->dev.own[1].n && n_f * (int64_t)p->dev.own[0].n > 3 * (int64_t)p->n_sm)
                         ? p->dev.own[1]
                         : p->dev.own[0];
     ProfScope ps(p, "gather_blend_interp_tc", s);
     return launch_gather_interp_tc(gather_args(p, fg, fb, nullptr, nullptr, nullptr, compact), n_f,
+                                   n_f == 1 ? 512 : 256,
                                    ws_ldF(p), p->dev.Ar_hi, p->dev.Ar_lo, o.off, o.k, o.pack,
                                    o.w, o.start, o.n,
                                    (int)p->strip_lin.size(),

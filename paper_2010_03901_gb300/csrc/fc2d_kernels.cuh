@@ -118,12 +118,14 @@ fc2d_status launch_gather_blend_tc(const GatherArgs& g, int n_f, int ldF, const 
                                    const float* Ar_lo, float* F, int* status, cudaStream_t s);
 // Mixed form, M = 8: matching values, blend and interpolation in one kernel; writes the
 // strip-point values (the plan's owner tables group the strip points by CTA, each CTA
-// owning the points of a balanced range of at most kTcOwned normals).
-fc2d_status launch_gather_interp_tc(const GatherArgs& g, int n_f, int ldS, const float* Ar_hi,
-                                    const float* Ar_lo, const int32_t* own_off,
-                                    const int32_t* own_k, const int32_t* own_pack,
-                                    const float* own_w, const int32_t* own_start, int n_own,
-                                    int n_strip, float* vals, int* status, cudaStream_t s);
+// owning the points of a balanced range of at most kTcOwned normals).  nt: threads per
+// CTA, 512 (one CTA per SM) or 256 (two per SM).
+fc2d_status launch_gather_interp_tc(const GatherArgs& g, int n_f, int nt, int ldS,
+                                    const float* Ar_hi, const float* Ar_lo,
+                                    const int32_t* own_off, const int32_t* own_k,
+                                    const int32_t* own_pack, const float* own_w,
+                                    const int32_t* own_start, int n_own, int n_strip,
+                                    float* vals, int* status, cudaStream_t s);
 // The tensor-core kernels' bounded mbarrier wait on a barrier nothing arrives on: after
 // 2 x limit polls FC2D_ERR_TIMEOUT is latched in *status and the kernel returns.
 fc2d_status launch_wait_probe(int* status, uint32_t limit, cudaStream_t s);

@@ -35,6 +35,45 @@ template <typename C> __device__ __forceinline__ C mul(C a, C b) {
 }
 template <typename C> __device__ __forceinline__ C mul_mi(C a) { return {a.y, -a.x}; }
 
+// L2 residency hints (PTX eviction priorities; no value changes).  The grid values f
+// are read once per call: they bypass L1 and go first when L2 evicts, so that the row
+// transforms' output (the intermediate, read again by both column passes) stays in L2.
+// The intermediate's stores ask L2 to keep their lines; the spectrum, written once,
+// asks it to evict its lines first.  Bits: 1 f loads, 2 intermediate stores, 4 spectrum
+// stores.
+#ifndef FC2D_L2_HINTS
+#define FC2D_L2_HINTS 1
+#endif
+__device__ __forceinline__ uint64_t l2_keep() {
+  uint64_t pol;
+  asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
+__device__ __forceinline__ uint64_t l2_drop() {
+  uint64_t pol;
+  asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
+__device__ __forceinline__ double2 ld_stream(const double2* p, uint64_t pol) {
+#if FC2D_L2_HINTS & 1
+  double2 v;
+  asm("ld.global.nc.L1::no_allocate.L2::cache_hint.v2.f64 {%0, %1}, [%2], %3;"
+      : "=d"(v.x), "=d"(v.y) : "l"(p), "l"(pol));
+  return v;
+#else
+  return __ldg(p);
+#endif
+}
+// store with an L2 policy (FP32 complex); other types store plainly
+template <int BIT, typename C> __device__ __forceinline__ void st_hint(C* p, C v, uint64_t pol) {
+  if constexpr (sizeof(C) == 8 && (FC2D_L2_HINTS & BIT)) {
+    asm volatile("st.global.L2::cache_hint.v2.f32 [%0], {%1, %2}, %3;"
+                 ::"l"(p), "f"(v.x), "f"(v.y), "l"(pol) : "memory");
+  } else {
+    *p = v;
+  }
+}
+
 // exp(-2 pi i m/16), m = 0..15
 template <typename T, typename C>
 __device__ __forceinline__ C w16(int m) {
@@ -324,13 +363,14 @@ __device__ __forceinline__ void last_stage_split(const typename Cx<T>::type* buf
   dft<T, C, R>(a);
   dft<T, C, R>(b);
   // X_ks and X_kl (kl = NH - ks) from zk = Z_ks and zl = Z_kl
+  const uint64_t pol = l2_keep();
   auto put = [&](int ks, int kl, C zk, C zl) {
     zl.y = -zl.y;
     const C e = {(T)0.5 * (zk.x + zl.x), (T)0.5 * (zk.y + zl.y)};
     const C o = {(T)0.5 * (zk.x - zl.x), (T)0.5 * (zk.y - zl.y)};
     const C wo = mul(__ldg(rtw + ks), o);
-    out[ks] = C{e.x + wo.y, e.y - wo.x};
-    if (ks != kl) out[kl] = C{e.x - wo.y, -e.y - wo.x};
+    st_hint<2>(out + ks, C{e.x + wo.y, e.y - wo.x}, pol);
+    if (ks != kl) st_hint<2>(out + kl, C{e.x - wo.y, -e.y - wo.x}, pol);
   };
   if (t) {
 #pragma unroll
@@ -479,12 +519,13 @@ __device__ __forceinline__ void assemble_row(const RowArgs& ra, int mode, int NH
       if (vec) {
         const int p0 = (lo + 1) >> 1, p1 = (hi + 1) >> 1;  // pairs p0 .. p1 - 1
         const double2* fg2 = reinterpret_cast<const double2*>(src);
+        const uint64_t pol = l2_drop();
         for (int n0 = p0 + threadIdx.x; n0 < p1; n0 += 8 * blockDim.x) {
           double2 d[8];
 #pragma unroll
           for (int u = 0; u < 8; ++u) {
             const int n = n0 + u * blockDim.x;
-            d[u] = n < p1 ? __ldg(fg2 + n) : make_double2(0.0, 0.0);
+            d[u] = n < p1 ? ld_stream(fg2 + n, pol) : make_double2(0.0, 0.0);
           }
 #pragma unroll
           for (int u = 0; u < 8; ++u) {
@@ -528,10 +569,20 @@ __device__ __forceinline__ void even_odd_split(const typename Cx<T>::type* buf, 
   }
 }
 
+// Blocks per SM asked of the compiler for FP32 kernels of `threads` threads: about 1024
+// resident threads (at most 64 registers each), at most 32 blocks.  FP64 kernels, bound
+// by their FP64 pipe, keep `fp64` (more registers, fewer shared-memory passes).
+__host__ __device__ constexpr int fp32_blocks(int threads) {
+  return 1024 / threads < 1 ? 1 : (1024 / threads > 32 ? 32 : 1024 / threads);
+}
+
 // rows: nx = 2^(LOGNH+1); block = NT = 2^LOGNH / E threads
 template <typename T, typename TV, int LOGNH>
 __global__ void __launch_bounds__((1 << LOGNH) / elems<T>() < 32 ? 32 : (1 << LOGNH) / elems<T>(),
-                                  (sizeof(T) == 4 && LOGNH == 11) ? 8 : 1)
+                                  sizeof(T) == 4 ? fp32_blocks((1 << LOGNH) / elems<T>() < 32
+                                                                   ? 32
+                                                                   : (1 << LOGNH) / elems<T>())
+                                                 : 1)
 k_fft_rows_p2(FftArgs fa, RowArgs ra, int mode, const T* __restrict__ ext,
               const double* __restrict__ f_grid, const TV* __restrict__ vals,
               typename Cx<T>::type* __restrict__ inter) {
@@ -573,7 +624,7 @@ template <int N2> __device__ __forceinline__ void dft_len(float2* x, const float
 }
 
 template <int N2>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(128, fp32_blocks(128))
 k_rows_64n(FftArgs fa, RowArgs ra, int mode, const float* __restrict__ ext,
            const double* __restrict__ f_grid, const float* __restrict__ vals,
            float2* __restrict__ inter) {
@@ -636,7 +687,9 @@ static void rows64n_launch(const FftArgs& fa, const RowArgs& ra, int n_f, int mo
 // (c = tid % CB, t = tid / CB): the CB columns of a row are read by neighbouring
 // threads.  First stage from the intermediate, last stage to the spectrum.
 template <typename T, int LOGNY, int CB>
-__global__ void __launch_bounds__(CB * ((1 << LOGNY) / elems<T>()), (CB * ((1 << LOGNY) / elems<T>()) <= 512 ? 2 : 1))
+__global__ void __launch_bounds__(CB * ((1 << LOGNY) / elems<T>()),
+                                  sizeof(T) == 4 ? fp32_blocks(CB * ((1 << LOGNY) / elems<T>()))
+                                  : (CB * ((1 << LOGNY) / elems<T>()) <= 512 ? 2 : 1))
 k_fft_cols_p2(FftArgs fa, const typename Cx<T>::type* __restrict__ inter,
               typename Cx<T>::type* __restrict__ fhat) {
   using C = typename Cx<T>::type;
@@ -703,7 +756,7 @@ __device__ __forceinline__ void dft64_cols(float2* a, int c, int l, float2* ex,
 // CC adjacent columns per block of 8 CC threads (16, 32 or 64: every width computes the
 // same values; wider blocks read longer contiguous row segments).
 template <int CC>
-__global__ void __launch_bounds__(8 * CC) k_cols4k_a(FftArgs fa, float2* __restrict__ inter) {
+__global__ void __launch_bounds__(8 * CC, 2048 / (8 * CC)) k_cols4k_a(FftArgs fa, float2* __restrict__ inter) {
   __shared__ float2 ex[64 * CC];
   const int c = threadIdx.x & (CC - 1), l = threadIdx.x / CC;
   const int ncol = fa.nx / 2 + 1;
@@ -718,17 +771,18 @@ __global__ void __launch_bounds__(8 * CC) k_cols4k_a(FftArgs fa, float2* __restr
 #pragma unroll
   for (int i = 0; i < 8; ++i)
     a[i] = live ? col[(size_t)(64 * (l + 8 * i) + j2) * fa.pitch] : make_float2(0.f, 0.f);
+  const uint64_t pol = l2_keep();
   dft64_cols<CC>(a, c, l, ex, w);
 #pragma unroll
   for (int m2 = 0; m2 < 8; ++m2) {
     const int m1 = l + 8 * m2;
     const float2 y = mul(a[m2], __ldg(w + ((j2 * m1) & 4095)));
-    if (live) col[(size_t)(64 * m1 + j2) * fa.pitch] = y;
+    if (live) st_hint<2>(col + (size_t)(64 * m1 + j2) * fa.pitch, y, pol);
   }
 }
 
 template <int CC>
-__global__ void __launch_bounds__(8 * CC) k_cols4k_b(FftArgs fa, int drop,
+__global__ void __launch_bounds__(8 * CC, 2048 / (8 * CC)) k_cols4k_b(FftArgs fa, int drop,
                                                       float2* __restrict__ inter,
                                                       float2* __restrict__ fhat) {
   __shared__ float2 ex[64 * CC];
@@ -760,16 +814,18 @@ __global__ void __launch_bounds__(8 * CC) k_cols4k_b(FftArgs fa, int drop,
   const float sc = (float)fa.scale;
   float2* out = fhat + (size_t)f * 4096 * ncol + kx;
   if (live) {
+    const uint64_t pol = l2_drop();
 #pragma unroll
     for (int m2p = 0; m2p < 8; ++m2p) {
       const int m2 = l + 8 * m2p;
-      out[(size_t)(m1 + 64 * m2) * ncol] = make_float2(a[m2p].x * sc, a[m2p].y * sc);
+      st_hint<4>(out + (size_t)(m1 + 64 * m2) * ncol, make_float2(a[m2p].x * sc, a[m2p].y * sc), pol);
     }
   }
 }
 
 // ------------------------------------------------------------------------- //
-// FP32 columns of N = 64 N2 points (N2 = 6, 10, 12, 24: non-power-of-two sizes), in the
+// FP32 columns of N = 64 N2 points (N2 = 6, 10, 12, 24: non-power-of-two sizes; N2 = 32:
+// 2048 points, whose one-pass blocks would read 16 bytes per row), in the
 // same two passes: j = N2 j1 + j2, m = m1 + 64 m2,
 //   pass A: 64-point DFTs over j1 (rows N2 j1 + j2, as k_cols4k_a with stride N2), the
 //           twiddle w_N^(j2 m1), in place to row N2 m1 + j2;
@@ -778,7 +834,7 @@ __global__ void __launch_bounds__(8 * CC) k_cols4k_b(FftArgs fa, int drop,
 //           m1 + 64 m2; then the intermediate's lines are dropped from L2.
 // ------------------------------------------------------------------------- //
 
-__global__ void __launch_bounds__(128) k_cols64_a(FftArgs fa, int n2, float2* __restrict__ inter) {
+__global__ void __launch_bounds__(128, fp32_blocks(128)) k_cols64_a(FftArgs fa, int n2, float2* __restrict__ inter) {
   __shared__ float2 ex[64 * kC4Cols];
   const int c = threadIdx.x & (kC4Cols - 1), l = threadIdx.x / kC4Cols;
   const int ncol = fa.nx / 2 + 1, N = fa.ny;
@@ -803,7 +859,7 @@ __global__ void __launch_bounds__(128) k_cols64_a(FftArgs fa, int n2, float2* __
 }
 
 template <int R1, int R2>
-__global__ void __launch_bounds__(128) k_cols64_b(FftArgs fa, int drop, float2* __restrict__ inter,
+__global__ void __launch_bounds__(128, R1 * R2 >= 24 ? 4 : fp32_blocks(128)) k_cols64_b(FftArgs fa, int drop, float2* __restrict__ inter,
                                                    float2* __restrict__ fhat) {
   constexpr int N2 = R1 * R2;
   const int c = threadIdx.x & (kC4Cols - 1);
@@ -1158,11 +1214,11 @@ bool launch_fft_cols_p2(const FftArgs& fa, int n_f, bool fp64, void* inter, void
     FC2D_COLS(10, 4, 2)
     default: break;
   }
-  // 4096-point FP32 columns: two coalesced passes (64 x 64)
+  // 2048- and 4096-point FP32 columns: two coalesced passes (64 x 32, 64 x 64)
   switch (L) {
-    case 11:
+    case 11:  // FP32: two passes of 64 x 32 (as the mixed-radix columns, N2 = 32)
       if (fp64) p2::cols_launch<double, 11, 2>(fa, n_f, inter, fhat, s);
-      else p2::cols_launch<float, 11, 2>(fa, n_f, inter, fhat, s);
+      else p2::cols64_launch<4, 8>(fa, n_f, inter, fhat, s);
       return true;
     case 12:
       if (fp64) p2::cols_launch<double, 12, 1>(fa, n_f, inter, fhat, s);

@@ -271,14 +271,15 @@ def test_compact_input_equals_full_grid(case, fc2d, precision):
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
-def test_dft_large_power_of_two(fc2d, torch_cuda, precision):
-    """The power-of-two DFT kernels at 4096 x 2048 (ny x nx) on seeded random data, two
-    functions batched (1025 columns: a ragged last column group):
+@pytest.mark.parametrize("name,ny,nx", [("kite2048", 4096, 2048), ("kite1024", 2048, 1024)])
+def test_dft_large_power_of_two(fc2d, torch_cuda, precision, name, ny, nx):
+    """The power-of-two DFT kernels at 4096 x 2048 and 2048 x 1024 (ny x nx; FP32
+    columns of 4096 points as 64 x 64 passes, of 2048 as 64 x 32) on seeded random data,
+    two functions batched (1025 and 513 columns: a ragged last column group):
     1e-12 (FP64) / 1e-6 (FP32) relative max-norm against numpy's FFT of the same data."""
     torch = torch_cuda
-    w = W.workload("kite2048")
+    w = W.workload(name)
     g, p = w.grid, w.params
-    nx, ny = 2048, 4096
     prec = fc2d.FC2D_FP64 if precision == "fp64" else fc2d.FC2D_MIXED
     plan = fc2d.fc2d_plan(w.boundary.arrays(), (g.a0, g.b0 - 0.5 * ny * g.h + 0.5 * g.ny * g.h,
                                                 g.h, nx, ny), dict(B=p.B, k1=p.k1), precision=prec)
