@@ -934,7 +934,8 @@ def stars8_batched(fc2d, torch, dev, replays=10):
                            stars, key=lambda s: s.grid.nx)) +
                        ", 32 degree-12 trigonometric sums per domain",
            "points_per_step": points, "unit": UNIT,
-           "launch": "fc2d_group_extend_coeffs: one CUDA graph, a branch per domain"}
+           "launch": "fc2d_group_extend_coeffs: one CUDA graph (mixed: the form the "
+                     "group's autotuner keeps, see group_tuning; FP64: a branch per domain)"}
     small = min(range(8), key=lambda i: stars[i].grid.nx)
     large = max(range(8), key=lambda i: stars[i].grid.nx)
     for name, prec, dt in (("mixed", fc2d.FC2D_MIXED, torch.float32),
@@ -958,6 +959,7 @@ def stars8_batched(fc2d, torch, dev, replays=10):
             grp.fc2d_group_extend_coeffs(*gargs)
         e1.record()
         torch.cuda.synchronize()
+        form, threads, tune_us = grp.fc2d_group_tuning()
         grp.fc2d_group_destroy()
         for plan, *_ in runs:
             plan.fc2d_sync_status()
@@ -975,6 +977,13 @@ def stars8_batched(fc2d, torch, dev, replays=10):
             errs[w.name] = float(np.abs(got - ref).max() / np.abs(ref).max())
         out[name] = {"value": points / (ms / 1e3), "ms_per_step": ms, "replays": replays,
                      "err_vs_oracle": errs}
+        if threads:
+            out[name]["group_tuning"] = {
+                "form": form, "queue_threads": threads,
+                "us": {k: round(v, 1) for k, v in tune_us.items()},
+                "how": "capture-time autotuner: the persistent blend kernel timed with 256 "
+                       "and 512 threads per CTA, then the graph with it and the graph with "
+                       "a branch per domain timed on the call's inputs; the faster kept"}
         for plan, *_ in runs:
             plan.fc2d_destroy()
     return out

@@ -342,20 +342,35 @@ fc2d_status fc2d_probe_fp64(double* out_dev, int blocks, int64_t iters, double* 
  * group before them).  fc2d_group_extend_coeffs runs fc2d_extend_coeffs of every plan
  * i on n_f[i] functions, f_grid_dev[i] / f_bdry_dev[i] (f_bdry_dev itself, or an entry,
  * may be NULL: interior data only) / fhat_dev[i] as for that call, as one CUDA graph
- * launched on `stream`: each plan on its own branch, so the domains' kernels run
- * concurrently.  The graph is captured on the first call (the plans' workspaces are
- * allocated before the capture) and replayed while n_f, every pointer and every plan's
- * workspace stay the same; a call with other arguments, or after a direct call on a
- * member plan grew that plan's workspace, captures anew.  A plan may appear once in a
- * group (FC2D_ERR_ARG otherwise).  Calls on one group must not overlap in time on
- * different streams (the plans' workspaces are shared).  The result equals the separate
- * calls bit for bit. */
+ * launched on `stream`, in one of two forms:
+ *   branches:   every plan's whole call on its own branch, concurrently;
+ *   persistent: the strip-point values (Sections 3.2-3.4) of all mixed-form members
+ *               from one persistent kernel whose CTAs take work items (plan, range of
+ *               normals, function) from a queue, longest first; then every plan's row
+ *               and column DFTs on its own branch (FP64 members: their whole call).
+ * The graph is captured on the first call, after earlier work on the device has
+ * finished and the plans' workspaces are allocated.  With mixed-form members both forms
+ * are captured and timed on the call's inputs (the persistent kernel's CTA shape, 256
+ * threads two per SM or 512 one per SM, timed first) and the faster is kept.  The graph
+ * is replayed while n_f, every pointer and every plan's workspace stay the same; a call
+ * with other arguments, or after a direct call on a member plan grew that plan's
+ * workspace, captures anew.  A plan may appear once in a group (FC2D_ERR_ARG
+ * otherwise).  Calls on one group must not overlap in time on different streams (the
+ * plans' workspaces are shared).  The result equals the separate calls bit for bit.
+ * fc2d_group_tuning: choice[0] the kept form (0 branches, 1 persistent), choice[1] the
+ * persistent kernel's threads per CTA (0 before the first capture or without mixed-form
+ * members); us[4]: microseconds per launch of the persistent kernel with 256 and 512
+ * threads, of the branches graph and of the persistent graph (0 for what was not
+ * timed).  fc2d_group_tuning_set fixes the choice for later captures ({form, threads},
+ * threads 256 or 512; NULL: tune again) and makes the next call capture anew. */
 typedef struct fc2d_group_s* fc2d_group_t;
 fc2d_status fc2d_group_create(const fc2d_plan_t* plans, int n, fc2d_group_t* out);
 fc2d_status fc2d_group_extend_coeffs(fc2d_group_t group, const int* n_f,
                                      const double* const* f_grid_dev,
                                      const double* const* f_bdry_dev, void* const* fhat_dev,
                                      void* stream);
+fc2d_status fc2d_group_tuning(fc2d_group_t group, int32_t* choice, float* us);
+fc2d_status fc2d_group_tuning_set(fc2d_group_t group, const int32_t* choice);
 void fc2d_group_destroy(fc2d_group_t group);
 
 void fc2d_destroy(fc2d_plan_t plan);

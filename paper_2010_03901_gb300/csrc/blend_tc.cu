@@ -23,6 +23,8 @@
 // again, frees its TMEM and returns.
 #include <cuda_runtime.h>
 
+#include <cstring>
+
 #include <algorithm>
 #include <cstdint>
 
@@ -47,13 +49,14 @@ __device__ __forceinline__ uint32_t smem_u32(const void* p) {
 // FC2D_ERR_TIMEOUT in *status and the wait is given `limit` polls once more, since
 // MMAs still in flight must end before their TMEM is freed.  True once the phase
 // completed.
-__device__ __forceinline__ bool mbar_wait_bounded(uint32_t mbar, int* status, uint32_t limit) {
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t mbar, int* status, uint32_t limit,
+                                                  uint32_t parity = 0) {
   uint32_t done = 0;
   auto poll = [&] {
     asm volatile(
         "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t}\n"
-        : "=r"(done) : "r"(mbar), "r"(0) : "memory");
+        : "=r"(done) : "r"(mbar), "r"(parity) : "memory");
   };
   for (uint32_t it = 0; it < limit && !done; ++it) poll();
   if (!done) {
@@ -492,37 +495,54 @@ struct OwnArgs {
   float* vals;           // [n_f][n_strip]
 };
 
+// TMEM columns for the CTA (warp 0) and the MMA mbarrier (thread 0); both become
+// visible to the CTA at the item's first barrier.
+template <int NF>
+__device__ __forceinline__ void gi_setup(uint64_t* mbar, uint32_t* tmem_slot) {
+  if ((threadIdx.x >> 5) == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                 ::"r"(smem_u32(tmem_slot)), "r"(gi_tmem_cols<NF>()));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(mbar)));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+}
+
+template <int NF>
+__device__ __forceinline__ void gi_release(uint32_t tmem) {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if ((threadIdx.x >> 5) == 0) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(gi_tmem_cols<NF>()));
+  }
+}
+
+// One work item: range c of the owner set, function block fblk (functions fblk NF ..).
+// The CTA holds gi_tmem_cols<NF>() TMEM columns (address in *tmem_slot) and the
+// mbarrier, whose phase this item's MMAs complete has parity `parity`.  Returns, to
+// every thread, false when that wait timed out (the status is set; the caller stops).
 template <int NF, int NT>
-__global__ void __launch_bounds__(NT, 512 / NT) k_gather_interp_tc(GatherArgs g, TcArgs a,
-                                                                    OwnArgs o, int n_f) {
-  static_assert(NT == 256 || NT == 512, "k_gather_interp_tc: 256 or 512 threads");
+__device__ __forceinline__ bool gi_item(const GatherArgs& g, const TcArgs& a, const OwnArgs& o,
+                                        int n_f, int c, int fblk, unsigned char* smem,
+                                        uint64_t* mbar, const uint32_t* tmem_slot,
+                                        uint32_t parity) {
   constexpr int MM = 8;
-  constexpr uint32_t kCols = gi_tmem_cols<NF>();
-  extern __shared__ __align__(1024) unsigned char smem[];
   unsigned char* a_hi = smem;
   unsigned char* a_lo = smem + kMaxCrPad * 32;
   // function ff's C tiles at c_hi/c_lo + ff * kTcComputed * 32 (c_lo after all c_hi)
   unsigned char* c_hi = smem + 2 * kMaxCrPad * 32;
   unsigned char* c_lo = c_hi + NF * kTcComputed * 32;
   float* stage0 = reinterpret_cast<float*>(smem + gi_stage_off<NF>());  // NF x [64][ldS]
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + gi_bar_off<NF>(a.ldF));
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mbar + 1);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int c = blockIdx.x, f0 = blockIdx.y * NF;
-  const int nfl = min(NF, n_f - f0);  // functions of this CTA (the last may have fewer)
+  const int f0 = fblk * NF;
+  const int nfl = min(NF, n_f - f0);  // functions of this item (the last may have fewer)
   const int ldS = a.ldF;  // staging row length (see the launcher)
   const int nqt = (a.Cr + kTcQTile - 1) / kTcQTile;
   const int o0 = __ldg(o.off + c), o1 = __ldg(o.off + c + 1);
 
-  if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
-                 ::"r"(smem_u32(tmem_slot)), "r"(kCols));
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
-  }
-  if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(mbar)));
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
   for (int idx = tid; idx < NF * kTcComputed * (ldS - a.Cr - 1); idx += blockDim.x) {
     const int r = idx / (ldS - a.Cr - 1);  // row of the NF stacked tiles
     stage0[r * ldS + a.Cr + 1 + (idx - r * (ldS - a.Cr - 1))] = 0.f;
@@ -652,7 +672,7 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_gather_interp_tc(GatherArgs g,
         "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
         ::"r"(smem_u32(mbar)) : "memory");
   }
-  uint32_t done = mbar_wait_bounded(smem_u32(mbar), a.status, kSpinLimit) ? 1u : 0u;
+  uint32_t done = mbar_wait_bounded(smem_u32(mbar), a.status, kSpinLimit, parity) ? 1u : 0u;
   done = __all_sync(0xffffffffu, done != 0) ? 1u : 0u;
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const int quarter = warp & 3, t = warp >> 2;
@@ -722,12 +742,56 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_gather_interp_tc(GatherArgs g,
       }
     }
   }
+  // the next item rewrites the staging tiles and TMEM: every thread is past its reads
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-  __syncthreads();
-  if (warp == 0) {
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
-                 "r"(kCols));
+  return __syncthreads_and(done != 0) != 0;
+}
+
+template <int NF, int NT>
+__global__ void __launch_bounds__(NT, 512 / NT) k_gather_interp_tc(GatherArgs g, TcArgs a,
+                                                                    OwnArgs o, int n_f) {
+  static_assert(NT == 256 || NT == 512, "k_gather_interp_tc: 256 or 512 threads");
+  extern __shared__ __align__(1024) unsigned char smem[];
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(smem + gi_bar_off<NF>(a.ldF));
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(mbar + 1);
+  gi_setup<NF>(mbar, tmem_slot);
+  gi_item<NF, NT>(g, a, o, n_f, blockIdx.x, blockIdx.y, smem, mbar, tmem_slot, 0);
+  gi_release<NF>(*tmem_slot);
+}
+
+// Persistent form for a plan group: each CTA takes work items (plan, range, function)
+// from `items` in order, one at a time, through the atomic counter (zeroed before the
+// launch), and runs them with its one TMEM allocation and mbarrier.  The items are
+// sorted by decreasing cost on the host, so the longest start first and the uneven
+// domains' work ends together.  A timed-out wait ends the CTA's loop.
+struct GiWork {
+  GatherArgs g;
+  TcArgs a;
+  OwnArgs o;
+  int n_f;
+};
+
+template <int NT>
+__global__ void __launch_bounds__(NT, 512 / NT) k_gather_interp_queue(const GiWork* __restrict__ work,
+                                                                       const int4* __restrict__ items,
+                                                                       int n_items, int* counter) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ uint32_t tmem_slot;
+  __shared__ int next;
+  gi_setup<1>(&mbar, &tmem_slot);
+  uint32_t parity = 0;
+  for (;;) {
+    if (threadIdx.x == 0) next = atomicAdd(counter, 1);
+    __syncthreads();
+    const int it = next;
+    if (it >= n_items) break;  // the same value in every thread
+    const int4 w = items[it];
+    const GiWork& W = work[w.x];
+    if (!gi_item<1, NT>(W.g, W.a, W.o, W.n_f, w.y, w.z, smem, &mbar, &tmem_slot, parity)) break;
+    parity ^= 1u;
   }
+  gi_release<1>(tmem_slot);
 }
 
 template <int NF, int NT>
@@ -739,28 +803,62 @@ static cudaError_t gi_launch(int n_own, int n_f, const GatherArgs& g, const TcAr
                     (size_t)sm, s, g, a, o, n_f);
 }
 
-fc2d_status launch_gather_interp_tc(const GatherArgs& g, int n_f, int nt, int ldS,
-                                    const float* Ar_hi, const float* Ar_lo,
-                                    const int32_t* own_off, const int32_t* own_k,
-                                    const int32_t* own_pack, const float* own_w,
-                                    const int32_t* own_start, int n_own, int n_strip,
-                                    float* vals, int* status, cudaStream_t s) {
+// The fused kernel's argument blocks from a call's description.
+static fc2d_status gi_args(const GiPlanArgs& in, TcArgs* a, OwnArgs* o) {
+  const GatherArgs& g = in.g;
+  const int ldS = in.ldS;
   if (g.Cr > kMaxCrPad || g.d > 8 || g.M != 8 || ldS % 4 || ldS < g.Cr + 12 ||
-      ldS + 4 > kTcMaxLd || !own_off || (nt != 256 && nt != 512))
+      ldS + 4 > kTcMaxLd || !in.own_off)
     return set_error(FC2D_ERR_UNSUPPORTED, "blend + interpolation kernel: M = 8, d <= 8");
-  TcArgs a{};
-  a.n_cols = n_f * g.B;
-  a.Cr = g.Cr;
-  a.d = g.d;
-  a.ldF = (ldS % 32 == 16) ? ldS + 4 : ldS;  // staging rows: avoid a 16-word stride
-  a.ncr_pad = (g.Cr + 15) / 16 * 16;
-  a.Ar_hi = Ar_hi;
-  a.Ar_lo = Ar_lo;
-  a.status = status;
-  OwnArgs o{own_off, own_k, own_pack, own_w, own_start, n_own, n_strip, vals};
-  const cudaError_t e = nt == 256 ? gi_launch<1, 256>(n_own, n_f, g, a, o, s)
-                                  : gi_launch<1, 512>(n_own, n_f, g, a, o, s);
+  *a = TcArgs{};
+  a->n_cols = in.n_f * g.B;
+  a->Cr = g.Cr;
+  a->d = g.d;
+  a->ldF = (ldS % 32 == 16) ? ldS + 4 : ldS;  // staging rows: avoid a 16-word stride
+  a->ncr_pad = (g.Cr + 15) / 16 * 16;
+  a->Ar_hi = in.Ar_hi;
+  a->Ar_lo = in.Ar_lo;
+  a->status = in.status;
+  *o = OwnArgs{in.own_off, in.own_k, in.own_pack, in.own_w, in.own_start, in.n_own, in.n_strip,
+               in.vals};
+  return FC2D_OK;
+}
+
+fc2d_status launch_gather_interp_tc(const GiPlanArgs& in, int nt, cudaStream_t s) {
+  TcArgs a;
+  OwnArgs o;
+  fc2d_status st = gi_args(in, &a, &o);
+  if (st) return st;
+  if (nt != 256 && nt != 512)
+    return set_error(FC2D_ERR_UNSUPPORTED, "blend + interpolation kernel: 256 or 512 threads");
+  const cudaError_t e = nt == 256 ? gi_launch<1, 256>(in.n_own, in.n_f, in.g, a, o, s)
+                                  : gi_launch<1, 512>(in.n_own, in.n_f, in.g, a, o, s);
   return cuda_check(e, "blend + interpolation launch");
+}
+
+size_t gi_work_bytes() { return sizeof(GiWork); }
+
+fc2d_status gi_work_fill(const GiPlanArgs& in, void* out, int* ldS) {
+  GiWork w{};
+  fc2d_status st = gi_args(in, &w.a, &w.o);
+  if (st) return st;
+  w.g = in.g;
+  w.n_f = in.n_f;
+  std::memcpy(out, &w, sizeof(w));
+  *ldS = w.a.ldF;
+  return FC2D_OK;
+}
+
+fc2d_status launch_gather_interp_queue(const void* work, const int4* items, int n_items,
+                                       int* counter, int nt, int max_ldS, int n_cta,
+                                       cudaStream_t s) {
+  if (nt != 256 && nt != 512)
+    return set_error(FC2D_ERR_UNSUPPORTED, "blend + interpolation queue: 256 or 512 threads");
+  const int sm = gi_stage_off<1>() + kTcComputed * max_ldS * 4;
+  auto k = nt == 256 ? k_gather_interp_queue<256> : k_gather_interp_queue<512>;
+  cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  k<<<n_cta, nt, sm, s>>>(static_cast<const GiWork*>(work), items, n_items, counter);
+  return cuda_check(cudaGetLastError(), "blend + interpolation queue launch");
 }
 
 fc2d_status launch_gather_blend_tc(const GatherArgs& g, int n_f, int ldF, const float* Ar_hi,

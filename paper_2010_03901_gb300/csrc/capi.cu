@@ -184,26 +184,46 @@ fc2d_status mixed_blend(fc2d_plan_s* p, int n_f, const double* fg, const double*
                          p->dev.Ar_hi, p->dev.Ar_lo, static_cast<float*>(F), p->dev.status, s);
 }
 
+// The fused blend + interpolation call (mixed form, M = 8) for n_f functions: one
+// function on CTAs of 512 threads, one per SM (own[0]); several on CTAs of 256 threads,
+// two per SM, one function each, over the balanced ranges while the call's CTAs fit in
+// about one wave, else over the fewest CTAs (own[1]).
+GiPlanArgs gi_call(fc2d_plan_s* p, int n_f, const double* fg, const double* fb,
+                   const Layout& L, bool compact, int* nt, const DeviceTables::Owners** own) {
+  const auto& o = (n_f > 1 && p->dev.own[1].n && n_f * (int64_t)p->dev.own[0].n > 3 * (int64_t)p->n_sm)
+                      ? p->dev.own[1]
+                      : p->dev.own[0];
+  GiPlanArgs a{};
+  a.g = gather_args(p, fg, fb, nullptr, nullptr, nullptr, compact);
+  a.n_f = n_f;
+  a.ldS = ws_ldF(p);
+  a.Ar_hi = p->dev.Ar_hi;
+  a.Ar_lo = p->dev.Ar_lo;
+  a.own_off = o.off;
+  a.own_k = o.k;
+  a.own_pack = o.pack;
+  a.own_start = o.start;
+  a.own_w = o.w;
+  a.n_own = o.n;
+  a.n_strip = (int)p->strip_lin.size();
+  a.vals = reinterpret_cast<float*>(ws(p, L.ovals));
+  a.status = p->dev.status;
+  *nt = n_f == 1 ? 512 : 256;
+  if (own) *own = &o;
+  return a;
+}
+
 // Steps 5 and 6 into workspace: strip values F, then the strip-point values.
 fc2d_status strip_values(fc2d_plan_s* p, int n_f, const double* fg, const double* fb,
                          const Layout& L, cudaStream_t s, bool compact = false) {
   const bool f64 = p->prm.precision == FC2D_FP64;
   void* F = ws(p, L.oF);
   if (!f64 && p->dev.own[0].off) {
-    // mixed form, M = 8: blend and interpolation in one kernel, F stays on chip.  One
-    // function: a CTA of 512 threads per SM (own[0]).  Several: CTAs of 256 threads, two
-    // per SM, one function each; the balanced ranges while the call's CTAs fit in about
-    // one wave, else the fewest CTAs.
-    const auto& o = (n_f > 1 && p->dev.own[1].n && n_f * (int64_t)p->dev.own[0].n > 3 * (int64_t)p->n_sm)
-                        ? p->dev.own[1]
-                        : p->dev.own[0];
+    // mixed form, M = 8: blend and interpolation in one kernel, F stays on chip
+    int nt = 0;
+    const GiPlanArgs a = gi_call(p, n_f, fg, fb, L, compact, &nt, nullptr);
     ProfScope ps(p, "gather_blend_interp_tc", s);
-    return launch_gather_interp_tc(gather_args(p, fg, fb, nullptr, nullptr, nullptr, compact), n_f,
-                                   n_f == 1 ? 512 : 256,
-                                   ws_ldF(p), p->dev.Ar_hi, p->dev.Ar_lo, o.off, o.k, o.pack,
-                                   o.w, o.start, o.n,
-                                   (int)p->strip_lin.size(),
-                                   reinterpret_cast<float*>(ws(p, L.ovals)), p->dev.status, s);
+    return launch_gather_interp_tc(a, nt, s);
   }
   if (f64) {
     ProfScope ps(p, "gather_blend", s);
@@ -310,19 +330,24 @@ extern "C" fc2d_status fc2d_coeffs(fc2d_plan_t p, int n_f, const void* ext, void
   return launched("fc2d_coeffs");
 }
 
-extern "C" fc2d_status fc2d_extend_coeffs(fc2d_plan_t p, int n_f, const double* fg,
-                                          const double* fb, void* fhat, void* stream) {
+namespace fc2d {
+
+// The argument checks of fc2d_extend_coeffs.
+fc2d_status extend_coeffs_check(fc2d_plan_s* p, int n_f, const double* fg, const double* fb,
+                                const void* fhat) {
   fc2d_status st = check_nf(p, n_f);
   if (st) return st;
   if (!fg || !fhat) return set_error(FC2D_ERR_ARG, "fc2d_extend_coeffs: null pointer");
-  if ((st = check_interior(p, fb, "fc2d_extend_coeffs"))) return st;
-  cudaSetDevice(p->device);
-  Layout L = layout(p, n_f);
-  if ((st = ensure_workspace(p, L.total))) return st;
-  cudaStream_t s = (cudaStream_t)stream;
+  return check_interior(p, fb, "fc2d_extend_coeffs");
+}
+
+// Steps 6-7 of fc2d_extend_coeffs after the strip-point values are in the workspace:
+// the fused row DFT (f and the strip values) and the column DFT.
+fc2d_status extend_coeffs_dft(fc2d_plan_s* p, int n_f, const double* fg, void* fhat,
+                              cudaStream_t s) {
   const bool f64 = p->prm.precision == FC2D_FP64;
+  const Layout L = layout(p, n_f);
   FftArgs fa = fft_args(p);
-  if ((st = strip_values(p, n_f, fg, fb, L, s))) return st;
   {
     ProfScope ps(p, "fft_rows_fused", s);
     launch_fft_rows(fa, row_args(p), n_f, f64, 1, nullptr, fg, ws(p, L.ovals),
@@ -333,6 +358,36 @@ extern "C" fc2d_status fc2d_extend_coeffs(fc2d_plan_t p, int n_f, const double* 
     launch_fft_cols(fa, n_f, f64, ws(p, L.ointer), fhat, s);
   }
   return launched("fc2d_extend_coeffs");
+}
+
+// A group member whose strip values the group's persistent kernel computes: mixed form
+// with the fused kernel's tables.  Its call description and each range's strip-point
+// count (the cost of a work item).
+bool group_fused(const fc2d_plan_s* p) {
+  return p->prm.precision == FC2D_MIXED && p->dev.own[0].off;
+}
+GiPlanArgs group_fused_args(fc2d_plan_s* p, int n_f, const double* fg, const double* fb,
+                            std::vector<int32_t>* points) {
+  int nt = 0;
+  const DeviceTables::Owners* o = nullptr;
+  const GiPlanArgs a = gi_call(p, n_f, fg, fb, layout(p, n_f), false, &nt, &o);
+  points->resize(o->n);
+  for (int c = 0; c < o->n; ++c) (*points)[c] = o->off_host[c + 1] - o->off_host[c];
+  return a;
+}
+
+}  // namespace fc2d
+
+extern "C" fc2d_status fc2d_extend_coeffs(fc2d_plan_t p, int n_f, const double* fg,
+                                          const double* fb, void* fhat, void* stream) {
+  fc2d_status st = extend_coeffs_check(p, n_f, fg, fb, fhat);
+  if (st) return st;
+  cudaSetDevice(p->device);
+  Layout L = layout(p, n_f);
+  if ((st = ensure_workspace(p, L.total))) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  if ((st = strip_values(p, n_f, fg, fb, L, s))) return st;
+  return extend_coeffs_dft(p, n_f, fg, fhat, s);
 }
 
 extern "C" fc2d_status fc2d_extend_coeffs_complex(fc2d_plan_t p, int n_f, const double* fg,

@@ -118,14 +118,28 @@ fc2d_status launch_gather_blend_tc(const GatherArgs& g, int n_f, int ldF, const 
                                    const float* Ar_lo, float* F, int* status, cudaStream_t s);
 // Mixed form, M = 8: matching values, blend and interpolation in one kernel; writes the
 // strip-point values (the plan's owner tables group the strip points by CTA, each CTA
-// owning the points of a balanced range of at most kTcOwned normals).  nt: threads per
-// CTA, 512 (one CTA per SM) or 256 (two per SM).
-fc2d_status launch_gather_interp_tc(const GatherArgs& g, int n_f, int nt, int ldS,
-                                    const float* Ar_hi, const float* Ar_lo,
-                                    const int32_t* own_off, const int32_t* own_k,
-                                    const int32_t* own_pack, const float* own_w,
-                                    const int32_t* own_start, int n_own, int n_strip,
-                                    float* vals, int* status, cudaStream_t s);
+// owning the points of a balanced range of at most kTcOwned normals).
+struct GiPlanArgs {
+  GatherArgs g;
+  int n_f, ldS;                 // functions; staging row length (workspace ldF)
+  const float *Ar_hi, *Ar_lo;   // split A_r
+  const int32_t *own_off, *own_k, *own_pack, *own_start;  // the chosen owner set
+  const float* own_w;
+  int n_own, n_strip;
+  float* vals;                  // [n_f][n_strip] strip-point values out
+  int* status;                  // the plan's device status word
+};
+// nt: threads per CTA, 512 (one CTA per SM) or 256 (two per SM)
+fc2d_status launch_gather_interp_tc(const GiPlanArgs& in, int nt, cudaStream_t s);
+// Persistent form for plan groups: work items (plan, range, function) as int4
+// {plan, range, function, 0}, taken in order through *counter (zero at launch) by n_cta
+// CTAs of nt threads.  work: one record per plan (gi_work_bytes() each, written by
+// gi_work_fill, which also returns the plan's staging row length); max_ldS: the largest.
+size_t gi_work_bytes();
+fc2d_status gi_work_fill(const GiPlanArgs& in, void* out, int* ldS);
+fc2d_status launch_gather_interp_queue(const void* work, const int4* items, int n_items,
+                                       int* counter, int nt, int max_ldS, int n_cta,
+                                       cudaStream_t s);
 // The tensor-core kernels' bounded mbarrier wait on a barrier nothing arrives on: after
 // 2 x limit polls FC2D_ERR_TIMEOUT is latched in *status and the kernel returns.
 fc2d_status launch_wait_probe(int* status, uint32_t limit, cudaStream_t s);

@@ -474,6 +474,7 @@ static fc2d_status owner_set(fc2d_plan_s* p, const std::vector<int32_t>& pb,
   for (int idx = 0; idx < ns; ++idx)
     for (int b = 0; b < 2 * M; ++b) wp[(size_t)b * ns + idx] = w[(size_t)b * ns + perm[idx]];
   out.n = n_own;
+  out.off_host = off;
   fc2d_status st;
   if ((st = upload(&out.off, off)) || (st = upload(&out.k, perm)) ||
       (st = upload(&out.pack, pack)) || (st = upload(&out.w, wp)) ||

@@ -66,6 +66,7 @@ struct DeviceTables {
     float* w = nullptr;        // [2M][n_strip] interpolation weights, grouped order
     int32_t* start = nullptr;  // [n + 1] first normal owned by each CTA, then B
     int n = 0;                 // CTAs per function (ownership ranges)
+    std::vector<int32_t> off_host;  // host copy of off (work costs of plan groups)
   } own[2];
   // per-row tables
   int32_t* row_iv_off = nullptr;    // [ny+1] offsets into row_iv

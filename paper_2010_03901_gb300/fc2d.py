@@ -93,6 +93,8 @@ def load_library(path: str = LIB_PATH):
         "fc2d_probe_fp64": [P, ct.c_int, ct.c_int64, P, P],
         "fc2d_tuning": [P, P, P],
         "fc2d_tuning_set": [P, P],
+        "fc2d_group_tuning": [P, P, P],
+        "fc2d_group_tuning_set": [P, P],
         "fc2d_profile_read": [P, ct.c_int, P, P, P, P],
     }
     for name, args in sigs.items():
@@ -345,6 +347,24 @@ class Group:
         fh = (ct.c_void_p * n)(*[_ptr(x) for x in fhat])
         fb = None if f_bdry is None else (ct.c_void_p * n)(*[_ptr(x) for x in f_bdry])
         _check(_lib.fc2d_group_extend_coeffs(self.handle, nf, fg, fb, fh, _stream(stream)))
+
+    def fc2d_group_tuning(self):
+        """(form kept: "persistent" or "branches", persistent kernel threads per CTA,
+        {"queue256", "queue512", "branches", "persistent"}: microseconds per launch)."""
+        ch = (ct.c_int32 * 2)()
+        us = (ct.c_float * 4)()
+        _check(_lib.fc2d_group_tuning(self.handle, ch, us))
+        return ("persistent" if ch[0] else "branches", ch[1],
+                dict(zip(("queue256", "queue512", "branches", "persistent"), us)))
+
+    def fc2d_group_tuning_set(self, form=None, threads=256):
+        """Fix the captured form ("persistent" or "branches") and the persistent kernel's
+        threads per CTA for later captures; form None: tune again."""
+        if form is None:
+            _check(_lib.fc2d_group_tuning_set(self.handle, None))
+        else:
+            ch = (ct.c_int32 * 2)(1 if form == "persistent" else 0, threads)
+            _check(_lib.fc2d_group_tuning_set(self.handle, ch))
 
     def fc2d_group_destroy(self):
         if self.handle:
