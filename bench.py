@@ -748,7 +748,8 @@ def _disk_eigenmode_error(fc2d, torch, dev, h=0.005, n_c=8, T_target=2.0):
             "max_abs_error": err}
 
 
-def ff_solve_kite2048(fc2d, torch, dev, n_large=2, squares=False, extras=True):
+def ff_solve_kite2048(fc2d, torch, dev, n_large=2, squares=False, extras=True,
+                      double_float=False):
     """The whole Fourier Forwarding solve (Section 4.2, eq. (4.9); fc2d_forward_wave): the
     kite at 2048^2, d = 4, c = 1, n_c = 8 (Delta T = 8 h, 64 small steps of CFL 0.125
     per large step), zero Dirichlet data, 32 initial conditions in one call (a Gaussian of
@@ -756,7 +757,10 @@ def ff_solve_kite2048(fc2d, torch, dev, n_large=2, squares=False, extras=True):
     One call of n_large large steps is timed between two events on the launching stream
     after a warm-up call (the band and scratch are built there); the per-kernel times come
     from a second, profiled call.  Beside it: the measured FP64 rate and the error of the
-    same solver against the exact Dirichlet eigenmode (2, 3) of the unit disk at t ~ 2."""
+    same solver against the exact Dirichlet eigenmode (2, 3) of the unit disk at t ~ 2,
+    and the same solve with the small-square procedure (interface mode 1) and with its
+    evaluation in double-float arithmetic (mode 2; there the dominant kernel's "TFLOP/s"
+    counts the FP64-equivalent DFT flops it replaces)."""
     w = W.workload("kite2048", d=4, M=7)
     g, p = w.grid, w.params
     n_c, n_f, c = 8, 32, 1.0
@@ -770,7 +774,8 @@ def ff_solve_kite2048(fc2d, torch, dev, n_large=2, squares=False, extras=True):
     t0 = time.time()
     u.copy_(U0)
     ut.zero_()
-    plan.fc2d_forward_wave(n_f, c, n_c, 1, u, ut, None, None, stream, squares=squares)
+    plan.fc2d_forward_wave(n_f, c, n_c, 1, u, ut, None, None, stream, squares=squares,
+                           double_float=double_float)
     torch.cuda.synchronize()
     first_call_s = time.time() - t0
     u.copy_(U0)
@@ -780,7 +785,8 @@ def ff_solve_kite2048(fc2d, torch, dev, n_large=2, squares=False, extras=True):
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     e0.record(stream)
-    plan.fc2d_forward_wave(n_f, c, n_c, n_large, u, ut, None, None, stream, squares=squares)
+    plan.fc2d_forward_wave(n_f, c, n_c, n_large, u, ut, None, None, stream, squares=squares,
+                           double_float=double_float)
     e1.record(stream)
     torch.cuda.synchronize()
     clocks = clk.stop()
@@ -794,7 +800,8 @@ def ff_solve_kite2048(fc2d, torch, dev, n_large=2, squares=False, extras=True):
     ut.zero_()
     plan.fc2d_profile(True)
     plan.fc2d_profile_read()
-    plan.fc2d_forward_wave(n_f, c, n_c, n_large, u, ut, None, None, stream, squares=squares)
+    plan.fc2d_forward_wave(n_f, c, n_c, n_large, u, ut, None, None, stream, squares=squares,
+                           double_float=double_float)
     torch.cuda.synchronize()
     plan.fc2d_profile(False)
     prof = plan.fc2d_profile_read()
@@ -843,7 +850,9 @@ def ff_solve_kite2048(fc2d, torch, dev, n_large=2, squares=False, extras=True):
             "fp64_peak": peak, "disk_eigenmode": eig,
             "parity": "tests/test_gpu_ff.py (element-wise against the oracle)",
             "small_squares": ff_solve_kite2048(fc2d, torch, dev, n_large, squares=True,
-                                               extras=False)}
+                                               extras=False),
+            "small_squares_double_float": ff_solve_kite2048(
+                fc2d, torch, dev, n_large, squares=True, extras=False, double_float=True)}
 
 
 def ff_scaling(fc2d, torch, dev, n_f=8, n_c=8):

@@ -280,7 +280,11 @@ fc2d_status fc2d_wait_selftest(fc2d_plan_t plan, uint32_t polls, void* stream);
  * at the interface points within (18 - n_c) h of its centre; in that mode the band
  * reaches (ceil(sqrt(2) n_c) + 2) h, so that squares inside the domain reach every
  * interface point, and n_c <= 18 (FC2D_ERR_GEOMETRY if a domain is too narrow or curved
- * for the squares).  At T_{j+1} the grid takes U_FC where the distance to
+ * for the squares).  interface_mode 2: the squares of mode 1 with their every-small-step
+ * evaluation (the modal advance and the two passes of inverse 64-point DFTs) in
+ * double-float arithmetic, pairs of FP32 values holding about 44 significant bits (the
+ * FP32 pipe issues 64 times the FP64 rate on this part); the expansions, U_B and U_FC at
+ * T_{j+1} stay FP64 (fc2d_wave_band_* take mode 1 for its sets).  At T_{j+1} the grid takes U_FC where the distance to
  * the curve is >= n_c h and U_B elsewhere (eq. (4.9)); U_B continues across large steps.
  *   u_dev, ut_dev  [n_f][ny][nx] in: u and u_t at t = 0 (values inside the domain used);
  *                  out: u and u_t at t = n_large Delta T inside the domain, 0 outside.

@@ -57,6 +57,7 @@ struct DevSquares {
   double* A = nullptr;              // [C][d]
   double* Q = nullptr;              // [d][d]
   double2* tw = nullptr;            // exp(-2 pi i t / P), t < P
+  float4* tw_df = nullptr;          // the same as double-float pairs (re hi, lo, im hi, lo)
   int32_t* rows = nullptr;          // [n_sq][2]: first and last box row holding served points
   int n = 0;
 };
@@ -140,14 +141,17 @@ fc2d_status upload_squares(const fc2d_plan_s* p, DevBand& b, int n_c) {
     rows[2 * k + 1] = hi;
   }
   std::vector<double2> tw(h.P);
+  std::vector<float4> tw_df(h.P);
   for (int t = 0; t < h.P; ++t) {
     const double ang = -2.0 * M_PI * double(t) / double(h.P);
     tw[t] = double2{std::cos(ang), std::sin(ang)};
+    const float ch = (float)tw[t].x, sh = (float)tw[t].y;
+    tw_df[t] = float4{ch, (float)(tw[t].x - (double)ch), sh, (float)(tw[t].y - (double)sh)};
   }
   if ((st = upload(&q->origin, origin)) || (st = upload(&q->served_off, h.served_off)) ||
       (st = upload(&q->served_lin, h.served_lin)) || (st = upload(&q->served_local, h.served_local)) ||
       (st = upload(&q->A, h.A)) || (st = upload(&q->Q, h.Q)) || (st = upload(&q->tw, tw)) ||
-      (st = upload(&q->rows, rows)))
+      (st = upload(&q->tw_df, tw_df)) || (st = upload(&q->rows, rows)))
     return st;
   b.sq = std::move(q);
   return FC2D_OK;
@@ -395,9 +399,17 @@ __device__ __forceinline__ void sq_transpose(const double2* a, double2* b, int P
   __syncthreads();
 }
 
+// A complex double as double-float pairs: hi = RN(x), lo = RN(x - hi).
+__device__ __forceinline__ float4 split_df(double2 v) {
+  const float rh = __double2float_rn(v.x), ih = __double2float_rn(v.y);
+  return float4{rh, __double2float_rn(v.x - (double)rh), ih, __double2float_rn(v.y - (double)ih)};
+}
+
 // Once per large step: each square's expansion.  Block (square, function): the square's
 // u and u_t as one complex field z = u + i u_t, continued along rows, then columns, to
 // P x P; its 2D DFT, normalised, stored transposed: Z[l][m] (l: x frequency).
+// DF: Z as double-float pairs (float4 re hi, re lo, im hi, im lo) for k_sq_eval_df.
+template <bool DF>
 __global__ void __launch_bounds__(kSqThreads) k_sq_forward(
     int P, int n_side, int C, int d, int nx, int64_t grid_stride, int n_f,
     const int32_t* __restrict__ origin, const double* __restrict__ A,
@@ -433,7 +445,11 @@ __global__ void __launch_bounds__(kSqThreads) k_sq_forward(
   r = stockham<double>(o, r, P, P, radix, 2, tw, 1);               // r[l][m]
   const double sc = 1.0 / ((double)P * P);
   double2* dst = Z + ((size_t)sq * n_f + f) * P * P;
-  for (int t = threadIdx.x; t < P * P; t += blockDim.x) dst[t] = double2{r[t].x * sc, r[t].y * sc};
+  for (int t = threadIdx.x; t < P * P; t += blockDim.x) {
+    const double2 v = double2{r[t].x * sc, r[t].y * sc};
+    if constexpr (DF) reinterpret_cast<float4*>(dst)[t] = split_df(v);
+    else dst[t] = v;
+  }
 }
 
 // 64-point DFT of the padded sequence x[pad(e)], e < 64 (pad(e) = e + e/8), by the 8
@@ -556,8 +572,158 @@ __global__ void __launch_bounds__(kSqEvalThreads, 2) k_sq_eval(
   }
 }
 
+// ------------------------------------------------------------------------- //
+// The same evaluation in double-float arithmetic (interface mode 2).  A real number is
+// the unevaluated sum hi + lo of two floats; sums use Knuth's TwoSum with the low parts
+// added after it and Dekker's FastTwoSum to renormalise, products the FMA form of
+// Dekker's TwoProduct (Dekker 1971; Knuth, TAOCP vol. 2, 4.2.2).  Each operation is
+// accurate to about 2^-44 of its operands' size, on the FP32 pipe, which on this part
+// issues 64 times as many operations as the FP64 pipe.
+// ------------------------------------------------------------------------- //
+struct df2 {
+  float hi, lo;
+};
+struct dfc {
+  df2 re, im;
+};
+__device__ __forceinline__ df2 df_fast(float a, float b) {  // |a| >= |b| or a = 0
+  const float s = __fadd_rn(a, b);
+  return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ df2 df_add(df2 a, df2 b) {
+  const float s = __fadd_rn(a.hi, b.hi), bb = __fsub_rn(s, a.hi);
+  const float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fsub_rn(b.hi, bb));
+  return df_fast(s, __fadd_rn(e, __fadd_rn(a.lo, b.lo)));
+}
+__device__ __forceinline__ df2 df_neg(df2 a) { return {-a.hi, -a.lo}; }
+__device__ __forceinline__ df2 df_sub(df2 a, df2 b) { return df_add(a, df_neg(b)); }
+__device__ __forceinline__ df2 df_mul(df2 a, df2 b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = fmaf(a.hi, b.hi, -p);
+  e = fmaf(a.hi, b.lo, e);
+  e = fmaf(a.lo, b.hi, e);
+  return df_fast(p, e);
+}
+__device__ __forceinline__ df2 df_half(df2 a) { return {0.5f * a.hi, 0.5f * a.lo}; }
+__device__ __forceinline__ dfc dfc_load(float4 v) { return {{v.x, v.y}, {v.z, v.w}}; }
+__device__ __forceinline__ float4 dfc_store(dfc a) { return float4{a.re.hi, a.re.lo, a.im.hi, a.im.lo}; }
+__device__ __forceinline__ dfc dfc_add(dfc a, dfc b) { return {df_add(a.re, b.re), df_add(a.im, b.im)}; }
+__device__ __forceinline__ dfc dfc_sub(dfc a, dfc b) { return {df_sub(a.re, b.re), df_sub(a.im, b.im)}; }
+__device__ __forceinline__ dfc dfc_mul_mi(dfc a) { return {a.im, df_neg(a.re)}; }  // -i a
+__device__ __forceinline__ dfc dfc_mul(dfc a, dfc b) {
+  return {df_sub(df_mul(a.re, b.re), df_mul(a.im, b.im)),
+          df_add(df_mul(a.re, b.im), df_mul(a.im, b.re))};
+}
+__device__ __forceinline__ double df_to_double(df2 a) { return (double)a.hi + (double)a.lo; }
+
+// Forward 8-point DFT in registers (as dft8_regs)
+__device__ __forceinline__ void dft8_df(dfc (&v)[8]) {
+  constexpr double kS = 0.70710678118654752440;
+  const df2 s = {(float)kS, (float)(kS - (double)(float)kS)};
+  auto d4 = [](dfc& a0, dfc& a1, dfc& a2, dfc& a3) {
+    const dfc t0 = dfc_add(a0, a2), t1 = dfc_sub(a0, a2), t2 = dfc_add(a1, a3);
+    const dfc t3 = dfc_mul_mi(dfc_sub(a1, a3));
+    a0 = dfc_add(t0, t2);
+    a2 = dfc_sub(t0, t2);
+    a1 = dfc_add(t1, t3);
+    a3 = dfc_sub(t1, t3);
+  };
+  dfc e0 = v[0], e1 = v[2], e2 = v[4], e3 = v[6], o0 = v[1], o1 = v[3], o2 = v[5], o3 = v[7];
+  d4(e0, e1, e2, e3);
+  d4(o0, o1, o2, o3);
+  const dfc w1 = {df_mul(s, df_add(o1.re, o1.im)), df_mul(s, df_sub(o1.im, o1.re))};
+  const dfc w2 = dfc_mul_mi(o2);
+  const dfc w3 = {df_mul(s, df_sub(o3.im, o3.re)), df_neg(df_mul(s, df_add(o3.re, o3.im)))};
+  v[0] = dfc_add(e0, o0);
+  v[4] = dfc_sub(e0, o0);
+  v[1] = dfc_add(e1, w1);
+  v[5] = dfc_sub(e1, w1);
+  v[2] = dfc_add(e2, w2);
+  v[6] = dfc_sub(e2, w2);
+  v[3] = dfc_add(e3, w3);
+  v[7] = dfc_sub(e3, w3);
+}
+
+// 64-point DFT of the padded sequence x[pad(e)] (as fft64)
+__device__ __forceinline__ void fft64_df(float4* x, int q, bool active,
+                                         const float4* __restrict__ tw) {
+  dfc v[8];
+  if (active) {
+#pragma unroll
+    for (int r = 0; r < 8; ++r) v[r] = dfc_load(x[sq_pad(q + 8 * r)]);
+    dft8_df(v);
+#pragma unroll
+    for (int k = 1; k < 8; ++k) v[k] = dfc_mul(v[k], dfc_load(__ldg(tw + q * k)));
+#pragma unroll
+    for (int k = 0; k < 8; ++k) x[sq_pad(q + 8 * k)] = dfc_store(v[k]);
+  }
+  __syncthreads();
+  if (active) {
+#pragma unroll
+    for (int r = 0; r < 8; ++r) v[r] = dfc_load(x[sq_pad(8 * q + r)]);
+    dft8_df(v);
+  }
+  __syncthreads();
+  if (active) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) x[sq_pad(q + 8 * k)] = dfc_store(v[k]);
+  }
+  __syncthreads();
+}
+
+// k_sq_eval in double-float: Z and tab hold double-float pairs (float4), tw_df the box's
+// twiddles; the served values are converted to double on output.
+__global__ void __launch_bounds__(kSqEvalThreads, 2) k_sq_eval_df(
+    int n_f, const float4* __restrict__ Z, const float4* __restrict__ tab,
+    const float4* __restrict__ tw, const int32_t* __restrict__ served_off,
+    const int32_t* __restrict__ served_lin, const int32_t* __restrict__ served_local,
+    const int32_t* __restrict__ rows, int64_t grid_stride, double* __restrict__ out) {
+  constexpr int P = kSqP;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float4* T1 = reinterpret_cast<float4*>(smem_raw);  // [64][72]: transform l along m
+  float4* T2 = T1 + P * kSqPad;                       // [rows][72]: transform y along l
+  const int sq = blockIdx.x, f0 = 2 * blockIdx.y;
+  const bool two = f0 + 1 < n_f;
+  const float4* Z0 = Z + ((size_t)sq * n_f + f0) * P * P;
+  const float4* Z1 = Z0 + (size_t)P * P;
+  const int g = threadIdx.x >> 3, q = threadIdx.x & 7;
+  for (int t = threadIdx.x; t < P * P; t += blockDim.x) {
+    const int l = t / P, m = t - l * P;
+    const int tn = ((P - l) & (P - 1)) * P + ((P - m) & (P - 1));  // the index of -k
+    const dfc tt = dfc_load(__ldg(tab + t));                        // (cos w tau, sin(w tau)/w)
+    auto adv = [&](const float4* Zf) {
+      const dfc zk = dfc_load(Zf[t]), zn = dfc_load(Zf[tn]);
+      const dfc F = {df_half(df_add(zk.re, zn.re)), df_half(df_sub(zk.im, zn.im))};
+      const dfc G = {df_half(df_add(zk.im, zn.im)), df_neg(df_half(df_sub(zk.re, zn.re)))};
+      return dfc{df_add(df_mul(F.re, tt.re), df_mul(G.re, tt.im)),
+                 df_add(df_mul(F.im, tt.re), df_mul(G.im, tt.im))};
+    };
+    const dfc a0 = adv(Z0);
+    const dfc a1 = two ? adv(Z1) : dfc{{0.f, 0.f}, {0.f, 0.f}};
+    T1[l * kSqPad + sq_pad(m)] = dfc_store(dfc{df_sub(a0.re, a1.im), df_neg(df_add(a0.im, a1.re))});
+  }
+  __syncthreads();
+  fft64_df(T1 + g * kSqPad, q, true, tw);  // T1[l][y]
+  const int r0 = __ldg(rows + 2 * sq), nr = __ldg(rows + 2 * sq + 1) - r0 + 1;
+  for (int t = threadIdx.x; t < nr * P; t += blockDim.x) {
+    const int yr = t / P, l = t - yr * P;
+    T2[yr * kSqPad + sq_pad(l)] = T1[l * kSqPad + sq_pad(r0 + yr)];
+  }
+  __syncthreads();
+  fft64_df(T2 + g * kSqPad, q, g < nr, tw);  // T2[y - r0][x]
+  const int s0 = __ldg(served_off + sq), s1 = __ldg(served_off + sq + 1);
+  for (int k = s0 + threadIdx.x; k < s1; k += blockDim.x) {
+    const int loc = __ldg(served_local + k), y = loc / P, x = loc - y * P;
+    const dfc v = dfc_load(T2[(y - r0) * kSqPad + sq_pad(x)]);
+    const int32_t lin = __ldg(served_lin + k);
+    out[(size_t)f0 * grid_stride + lin] = df_to_double(v.re);
+    if (two) out[(size_t)(f0 + 1) * grid_stride + lin] = -df_to_double(v.im);
+  }
+}
+
 // The box's time factors for the small steps s = 0..S-1: tab[s][l][m] =
 // (cos w tau, sin(w tau)/w) at tau = s dt ((1, tau) at w = 0), w = 2 pi c |k| / (P h).
+template <bool DF>
 __global__ void k_sq_table(int P, int S, double c, double h, double dt, double2* __restrict__ tab) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (int64_t)S * P * P) return;
@@ -567,13 +733,16 @@ __global__ void k_sq_table(int P, int S, double c, double h, double dt, double2*
   const double L = P * h, tau = s * dt;
   const double fl = ls / L, fm = ms / L;
   const double w = 6.283185307179586476925286766559 * c * sqrt(fl * fl + fm * fm);
+  double2 v;
   if (w == 0.0) {
-    tab[t] = double2{1.0, tau};
+    v = double2{1.0, tau};
   } else {
     double sn, co;
     sincos(w * tau, &sn, &co);
-    tab[t] = double2{co, sn / w};
+    v = double2{co, sn / w};
   }
+  if constexpr (DF) reinterpret_cast<float4*>(tab)[t] = split_df(v);
+  else tab[t] = v;
 }
 
 unsigned blocks(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
@@ -594,7 +763,7 @@ void wave_destroy(fc2d_plan_s* p) {
     if (b.sq) {
       DevSquares& q = *b.sq;
       for (void* ptr : {(void*)q.origin, (void*)q.served_off, (void*)q.served_lin,
-                        (void*)q.served_local, (void*)q.A, (void*)q.Q, (void*)q.tw,
+                        (void*)q.served_local, (void*)q.A, (void*)q.Q, (void*)q.tw, (void*)q.tw_df,
                         (void*)q.rows})
         cudaFree(ptr);
     }
@@ -693,15 +862,17 @@ extern "C" fc2d_status fc2d_forward_wave(fc2d_plan_t p, int n_f, double c, int n
   if (!u || !ut) return set_error(FC2D_ERR_ARG, "fc2d_forward_wave: null pointer");
   if (!(c > 0) || n_large < 0)
     return set_error(FC2D_ERR_ARG, "fc2d_forward_wave: c > 0 and n_large >= 0 required");
-  if (interface_mode < 0 || interface_mode > 1)
-    return set_error(FC2D_ERR_ARG, "fc2d_forward_wave: interface_mode 0 or 1");
+  if (interface_mode < 0 || interface_mode > 2)
+    return set_error(FC2D_ERR_ARG, "fc2d_forward_wave: interface_mode 0, 1 or 2");
   if (3 * (size_t)p->grid.ny * sizeof(double2) > 227 * 1024)
     return set_error(FC2D_ERR_UNSUPPORTED, "fc2d_forward_wave: ny <= 4842");
   if (n_large == 0) return FC2D_OK;
   cudaSetDevice(p->device);
   cudaStream_t s = (cudaStream_t)stream;
   DevBand* b;
-  if ((st = get_band(p, n_c, interface_mode, &b))) return st;
+  // mode 2: the squares of mode 1, evaluated in double-float arithmetic
+  const bool df = interface_mode == 2;
+  if ((st = get_band(p, n_c, interface_mode ? 1 : 0, &b))) return st;
   const int nx = p->grid.nx, ny = p->grid.ny, nxh = nx / 2 + 1;
   const int64_t NN = (int64_t)nx * ny, nb = p->n_bdry, Nu = b->L.rows;
   const size_t pitch = row_pitch(p);
@@ -751,9 +922,12 @@ extern "C" fc2d_status fc2d_forward_wave(fc2d_plan_t p, int n_f, double c, int n
     }
   const size_t sm_ev = (size_t)(P + max_rows) * kSqPad * sizeof(double2);
   if (sq) {
-    cudaFuncSetAttribute(k_sq_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_sq);
+    cudaFuncSetAttribute(k_sq_forward<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_sq);
+    cudaFuncSetAttribute(k_sq_forward<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_sq);
     cudaFuncSetAttribute(k_sq_eval, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_ev);
-    k_sq_table<<<blocks((int64_t)S * P * P, 256), 256, 0, s>>>(P, S, c, h, dt, sqT);
+    cudaFuncSetAttribute(k_sq_eval_df, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_ev);
+    if (df) k_sq_table<true><<<blocks((int64_t)S * P * P, 256), 256, 0, s>>>(P, S, c, h, dt, sqT);
+    else k_sq_table<false><<<blocks((int64_t)S * P * P, 256), 256, 0, s>>>(P, S, c, h, dt, sqT);
   }
   auto gat = [&](int64_t m) { return g_dir ? g_dir + (size_t)m * n_f * nb : nullptr; };
   auto gtat = [&](int64_t j) { return gt_dir ? gt_dir + (size_t)j * n_f * nb : nullptr; };
@@ -794,8 +968,9 @@ extern "C" fc2d_status fc2d_forward_wave(fc2d_plan_t p, int n_f, double c, int n
     if (sq) {  // the squares' expansions of u(T_j), u_t(T_j), before u and ut change
       ProfScope ps(p, "sq_forward", s);
       const SquareSet& H = sq->host;
-      k_sq_forward<<<dim3(n_sq, n_f), kSqThreads, sm_sq, s>>>(
-          P, 2 * H.a + 1, H.C, H.d, nx, NN, n_f, sq->origin, sq->A, sq->Q, sq->tw, u, ut, sqZ);
+      auto kf = df ? k_sq_forward<true> : k_sq_forward<false>;
+      kf<<<dim3(n_sq, n_f), kSqThreads, sm_sq, s>>>(P, 2 * H.a + 1, H.C, H.d, nx, NN, n_f,
+                                                     sq->origin, sq->A, sq->Q, sq->tw, u, ut, sqZ);
     }
     if ((st = wave_spectra(p, n_f, u, g_dir ? gat(m0) : zero, ut, gt_dir ? gtat(j) : zero, spec, s)))
       return st;
@@ -803,9 +978,15 @@ extern "C" fc2d_status fc2d_forward_wave(fc2d_plan_t p, int n_f, double c, int n
       const int64_t m = m0 + sidx;
       if (sq) {
         ProfScope ps(p, "sq_eval", s);
-        k_sq_eval<<<dim3(n_sq, (n_f + 1) / 2), kSqEvalThreads, sm_ev, s>>>(
-            n_f, sqZ, sqT + (size_t)sidx * P * P, sq->tw, sq->served_off, sq->served_lin,
-            sq->served_local, sq->rows, NN, ufc[f_cur]);
+        if (df)
+          k_sq_eval_df<<<dim3(n_sq, (n_f + 1) / 2), kSqEvalThreads, sm_ev, s>>>(
+              n_f, reinterpret_cast<const float4*>(sqZ),
+              reinterpret_cast<const float4*>(sqT) + (size_t)sidx * P * P, sq->tw_df,
+              sq->served_off, sq->served_lin, sq->served_local, sq->rows, NN, ufc[f_cur]);
+        else
+          k_sq_eval<<<dim3(n_sq, (n_f + 1) / 2), kSqEvalThreads, sm_ev, s>>>(
+              n_f, sqZ, sqT + (size_t)sidx * P * P, sq->tw, sq->served_off, sq->served_lin,
+              sq->served_local, sq->rows, NN, ufc[f_cur]);
       } else {
         eval_ufc(sidx * dt, 1, ufc[f_cur], nullptr);
       }

@@ -251,9 +251,11 @@ class Plan:
                                        _stream(stream)))
 
     def fc2d_forward_wave(self, n_f, c, n_c, n_large, u, ut, g_dir=None, gt_dir=None,
-                          stream=None, squares=False):
-        """squares: the interface values from the small-square procedure (mode 1)."""
-        _check(_lib.fc2d_forward_wave(self.handle, n_f, c, n_c, n_large, 1 if squares else 0,
+                          stream=None, squares=False, double_float=False):
+        """squares: the interface values from the small-square procedure (mode 1);
+        with double_float, its small-step evaluation in double-float arithmetic (mode 2)."""
+        mode = (2 if double_float else 1) if squares else 0
+        _check(_lib.fc2d_forward_wave(self.handle, n_f, c, n_c, n_large, mode,
                                       _ptr(u), _ptr(ut), _ptr(g_dir), _ptr(gt_dir),
                                       _stream(stream)))
 

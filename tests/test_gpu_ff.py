@@ -9,7 +9,10 @@ near-boundary solver U_B, through the C ABI, against the oracle on the same inpu
 * the whole solve over several large steps equals the oracle's forward_wave at every
   grid point inside the domain, u and u_t, within the bar derived below;
 * the plane wave of Section 4.2.1's first example is reproduced to the oracle's
-  accuracy against the exact solution.
+  accuracy against the exact solution;
+* the small-square procedure (interface mode 1) and its double-float evaluation (mode
+  2, with the bar's addition derived at EPS_DF below) equal the oracle's solve with the
+  same squares.
 
 Bar of the whole solve.  Each large step starts with two 2D-FC extensions, whose grid
 values the GPU and the oracle agree on to 3e-11 of max|f| (the blend's conditioning
@@ -30,6 +33,21 @@ from oracle.fc_matrices import load_fc_matrices
 pytestmark = pytest.mark.gpu
 
 TOL_EXT = 3e-11
+# Double-float small-square evaluation (interface mode 2): every interface value of a
+# small step carries an error of at most EPS_DF times the field's size (each double-float
+# operation ~2^-44 of its operands; a 64 x 64 transform and the advance chain ~20 of them
+# per output, given a factor 3 of margin: 64 2^-44).  U_B's stable steps add the
+# errors of the S n_large evaluations without amplifying them, so u moves by at most
+# S n_large EPS_DF |u|, and u_t, a centred difference over 2 dt, by that over dt.
+EPS_DF = 64 * 2.0 ** -44
+
+
+def df_bars(double_float, S, n_large, dt, size):
+    """(u, u_t) additions to the parity bars for the double-float mode."""
+    if not double_float:
+        return 0.0, 0.0
+    e = S * n_large * EPS_DF * size
+    return e, e / dt
 CASES = [("disk64", 4), ("kite160x144", 6), ("star200", 8)]
 
 
@@ -248,7 +266,8 @@ def _disk_offset(h):
     return W.Workload(w.name, w.boundary, g, w.params)
 
 
-def test_forward_wave_small_squares_parity(torch_cuda):
+@pytest.mark.parametrize("double_float", [False, True])
+def test_forward_wave_small_squares_parity(torch_cuda, double_float):
     """The small-square procedure (interface_mode 1) against the oracle's forward_wave
     with the same squares: the deeper band's sets and the squares' count, then two large
     steps of two functions with zero Dirichlet data, and one large step of the plane
@@ -280,18 +299,21 @@ def test_forward_wave_small_squares_parity(torch_cuda):
     n_large, c = 2, 1.0
     u = torch.tensor(np.stack(U0), device=dev)
     ut = torch.tensor(np.stack(Ut0), device=dev)
-    plan.fc2d_forward_wave(2, c, n_c, n_large, u, ut, squares=True)
+    plan.fc2d_forward_wave(2, c, n_c, n_large, u, ut, squares=True, double_float=double_float)
     plan.fc2d_sync_status()
     got_u, got_ut = u.cpu().numpy(), ut.cpu().numpy()
     T = n_large * n_c * h
     w_max = OV.frequencies(g, c).max()
     ins = geo.inside
+    S = 8 * n_c
     for k in range(2):
         ref_u, ref_ut = OV.forward_wave(geo, mats, band, c, n_large, U0[k], Ut0[k],
                                         stencils=st, squares=sq)
         mu, mut = np.abs(ref_u[ins]).max(), np.abs(ref_ut[ins]).max()
-        assert np.abs(got_u[k][ins] - ref_u[ins]).max() < TOL_EXT * n_large * (mu + T * mut)
-        assert np.abs(got_ut[k][ins] - ref_ut[ins]).max() < TOL_EXT * n_large * (w_max * mu + mut)
+        du, dut = df_bars(double_float, S, n_large, n_c * h / S / c, mu + T * mut)
+        assert np.abs(got_u[k][ins] - ref_u[ins]).max() < TOL_EXT * n_large * (mu + T * mut) + du
+        assert (np.abs(got_ut[k][ins] - ref_ut[ins]).max()
+                < TOL_EXT * n_large * (w_max * mu + mut) + dut)
     kap = 10.5
     ue = lambda x, y, t: np.cos(2 * kap * (x + t) / 3) + np.cos(kap * (y + t))
     ute = lambda x, y, t: (-(2 * kap / 3) * np.sin(2 * kap * (x + t) / 3)
@@ -304,17 +326,22 @@ def test_forward_wave_small_squares_parity(torch_cuda):
     u = torch.tensor(ue(X, Y, 0.0)[None], device=dev)
     ut = torch.tensor(ute(X, Y, 0.0)[None], device=dev)
     plan.fc2d_forward_wave(1, c, n_c, 1, u, ut, torch.tensor(gdir, device=dev),
-                           torch.tensor(gtdir, device=dev), squares=True)
+                           torch.tensor(gtdir, device=dev), squares=True,
+                           double_float=double_float)
     plan.fc2d_sync_status()
     ref_u, ref_ut = OV.forward_wave(geo, mats, band, c, 1, ue(X, Y, 0.0), ute(X, Y, 0.0),
                                     lambda t: ue(geo.bdry_x, geo.bdry_y, t),
                                     lambda t: ute(geo.bdry_x, geo.bdry_y, t),
                                     stencils=st, squares=sq)
-    assert np.abs(u.cpu().numpy()[0][ins] - ref_u[ins]).max() < TOL_EXT * (2 + n_c * h * kap * 2)
-    assert np.abs(ut.cpu().numpy()[0][ins] - ref_ut[ins]).max() < TOL_EXT * (w_max * 2 + 2 * kap)
+    du, dut = df_bars(double_float, S, 1, dt, 2 + n_c * h * kap * 2)
+    assert (np.abs(u.cpu().numpy()[0][ins] - ref_u[ins]).max()
+            < TOL_EXT * (2 + n_c * h * kap * 2) + du)
+    assert (np.abs(ut.cpu().numpy()[0][ins] - ref_ut[ins]).max()
+            < TOL_EXT * (w_max * 2 + 2 * kap) + dut)
 
 
-def test_full_size_small_squares_solve(torch_cuda):
+@pytest.mark.parametrize("double_float", [False, True])
+def test_full_size_small_squares_solve(torch_cuda, double_float):
     """The bench's FF workload with the small-square procedure, at full size and in the
     bench's launch configuration (kite 2048^2, n_c = 8, 32 functions, one large step):
     the squares as the oracle places them, functions 0 and 31 against the oracle's solve
@@ -333,7 +360,7 @@ def test_full_size_small_squares_solve(torch_cuda):
     dev = torch.device("cuda:0")
     u = torch.tensor(U0, device=dev)
     ut = torch.zeros_like(u)
-    plan.fc2d_forward_wave(n_f, 1.0, n_c, 1, u, ut, squares=True)
+    plan.fc2d_forward_wave(n_f, 1.0, n_c, 1, u, ut, squares=True, double_float=double_float)
     plan.fc2d_sync_status()
     got_u, got_ut = u.cpu().numpy(), ut.cpu().numpy()
     geo = OG.build_geometry(w)
@@ -345,9 +372,11 @@ def test_full_size_small_squares_solve(torch_cuda):
     T = n_c * g.h
     w_max = OV.frequencies(g, 1.0).max()
     ins = geo.inside
+    S = 8 * n_c
     for k in (0, n_f - 1):
         ref_u, ref_ut = OV.forward_wave(geo, mats, band, 1.0, 1, U0[k], np.zeros_like(U0[k]),
                                         stencils=st, squares=sq)
         mu, mut = np.abs(ref_u[ins]).max(), np.abs(ref_ut[ins]).max()
-        assert np.abs(got_u[k][ins] - ref_u[ins]).max() < TOL_EXT * (mu + T * mut), k
-        assert np.abs(got_ut[k][ins] - ref_ut[ins]).max() < TOL_EXT * (w_max * mu + mut), k
+        du, dut = df_bars(double_float, S, 1, n_c * g.h / S, np.abs(U0[k]).max() + T * mut)
+        assert np.abs(got_u[k][ins] - ref_u[ins]).max() < TOL_EXT * (mu + T * mut) + du, k
+        assert np.abs(got_ut[k][ins] - ref_ut[ins]).max() < TOL_EXT * (w_max * mu + mut) + dut, k
