@@ -308,7 +308,7 @@ __device__ __forceinline__ dfl df_add(dfl x, dfl y) {
   return fast_two_sum(s.hi, s.lo + t.lo);
 }
 __device__ __forceinline__ dfl df_mul(dfl x, dfl y) {
-  const float p = x.hi * y.hi;
+  const float p = __fmul_rn(x.hi, y.hi);  // never fused into the sum below
   float e = fmaf(x.hi, y.hi, -p);
   e = fmaf(x.hi, y.lo, e);
   e = fmaf(x.lo, y.hi, e);
