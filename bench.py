@@ -54,9 +54,8 @@ ROT = 3   # rotating input/output buffers of the timed steps
 KERNELS_PER_SCOPE = {("mixed", "fft_cols", 4096): 2}
 
 MEASURED_TRAFFIC = {
-    ("mixed", "fft_rows_fused"): 70923264 + 18913792,
-    ("mixed", "gather_blend_interp_tc"): 34112000 + 0,
-    ("fp64", "fft_rows_fused"): 72384768 + 75083008,
+    ("mixed", "fft_rows_fused"): 70907136 + 9798144,
+    ("mixed", "gather_blend_interp_tc"): 34111232 + 256,
     ("fp64", "fft_cols"): 141867520 + 92843264,
     ("fp64", "gather_blend"): 9670144 + 9472,
 }
@@ -1085,8 +1084,8 @@ EXTRA_LINES = {"poisson_star1024": poisson_star1024,
 
 def ff_probe(name):
     """One large step of the Fourier Forwarding solve on workload `name` (d = 4, n_c = 8,
-    8 Gaussians, zero Dirichlet data), with the full inverse DFT and then with the small
-    squares: a small, self-contained command for profilers."""
+    8 Gaussians, zero Dirichlet data), with the full inverse DFT, the small squares and
+    the small squares in double-float: a small, self-contained command for profilers."""
     import torch
     from paper_2010_03901_gb300.build import build
     build()
@@ -1099,11 +1098,12 @@ def ff_probe(name):
           for k in range(8)]
     U0 = torch.tensor(np.stack([W.grid_values(w, f) for f in fs]), device="cuda:0")
     out = {}
-    for squares in (False, True):
+    for mode in ("full", "squares", "squares_double_float"):
         u, ut = U0.clone(), torch.zeros_like(U0)
-        plan.fc2d_forward_wave(8, 1.0, 8, 1, u, ut, squares=squares)
+        plan.fc2d_forward_wave(8, 1.0, 8, 1, u, ut, squares=mode != "full",
+                               double_float=mode == "squares_double_float")
         plan.fc2d_sync_status()
-        out["squares" if squares else "full"] = float(u.abs().max())
+        out[mode] = float(u.abs().max())
     print(json.dumps({"ff_probe": name, "max_abs_u": out}), flush=True)
 
 
