@@ -56,6 +56,7 @@ KERNELS_PER_SCOPE = {("mixed", "fft_cols", 4096): 2}
 MEASURED_TRAFFIC = {
     ("mixed", "fft_rows_fused"): 70907136 + 9798144,
     ("mixed", "gather_blend_interp_tc"): 34111232 + 256,
+    ("fp64", "fft_rows_fused"): 72354816 + 72103424,
     ("fp64", "fft_cols"): 141867520 + 92843264,
     ("fp64", "gather_blend"): 9670144 + 9472,
 }
