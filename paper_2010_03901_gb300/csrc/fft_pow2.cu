@@ -220,20 +220,29 @@ __device__ __forceinline__ void dft_ct(float2* x, const float2* __restrict__ wt,
 }
 
 // Round-to-nearest-even double -> float on the integer pipe (the FP64 pipe that the
-// conversion instruction uses is narrow on this part).  For doubles whose exponent e
-// lies in [897, 1148] (float exponents 1..252, so no overflow even after rounding up):
-// the high word of (hi:lo) << 3 holds e's low 9 bits above the top 23 mantissa bits;
-// subtracting 896 << 23 (mod 2^32) rebases the exponent, the 29 dropped bits round the
-// result (ties to even; a mantissa carry moves into the exponent), and the sign is put
-// back.  Other values (zero, subnormal, huge, inf, NaN) take the hardware conversion.
+// conversion instruction uses is narrow on this part), for doubles whose exponent e lies
+// in [897, 1148] (float exponents 1..252, so no overflow even after rounding up): add
+// 2^28 - 1 plus bit 29 to the 64-bit pattern (round half to even at bit 29; a mantissa
+// carry moves into the exponent), keep bits 29..60 (e's low 9 bits over the top 23
+// mantissa bits), rebase the exponent by 896 (mod 2^32) and put the sign back.  Other
+// values (zero, subnormal, huge, inf, NaN) take the hardware conversion.
+__device__ __forceinline__ bool d2f_in_range(unsigned hi) {
+  return (hi & 0x7FF00000u) - (897u << 20) <= (251u << 20);
+}
+__device__ __forceinline__ float d2f_in(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned long long u = b + 0x0FFFFFFFull + ((b >> 29) & 1ull);
+  const unsigned r = (unsigned)(u >> 29) - (896u << 23);
+  return __uint_as_float(r | ((unsigned)(b >> 32) & 0x80000000u));
+}
 __device__ __forceinline__ float d2f_rn(double x) {
-  const unsigned lo = (unsigned)__double2loint(x), hi = (unsigned)__double2hiint(x);
-  const unsigned e = (hi >> 20) & 0x7FFu;
-  if (e - 897u > 251u) return __double2float_rn(x);
-  unsigned r = __funnelshift_l(lo, hi, 3) - (896u << 23);
-  const unsigned dropped = lo & 0x1FFFFFFFu;
-  r += (dropped + (r & 1u)) > 0x10000000u ? 1u : 0u;
-  return __uint_as_float(r | (hi & 0x80000000u));
+  return d2f_in_range((unsigned)__double2hiint(x)) ? d2f_in(x) : __double2float_rn(x);
+}
+// both values of a pair, one range test
+__device__ __forceinline__ float2 d2f2_rn(double2 v) {
+  if (d2f_in_range((unsigned)__double2hiint(v.x)) && d2f_in_range((unsigned)__double2hiint(v.y)))
+    return float2{d2f_in(v.x), d2f_in(v.y)};
+  return float2{__double2float_rn(v.x), __double2float_rn(v.y)};
 }
 template <typename T> __device__ __forceinline__ T from_double(double x) { return (T)x; }
 template <> __device__ __forceinline__ float from_double<float>(double x) { return d2f_rn(x); }
@@ -244,6 +253,16 @@ template <> __device__ __forceinline__ float from_double<float>(double x) { retu
 template <typename T> __host__ __device__ constexpr int pad_shift() { return sizeof(T) == 4 ? 4 : 3; }
 template <typename T> __device__ __forceinline__ int pad(int i) { return i + (i >> pad_shift<T>()); }
 template <typename T> __host__ __device__ constexpr int padded(int n) { return n + (n >> pad_shift<T>()); }
+// pad(i + r S) for r = 0..R-1 as pad(i) plus a compile-time offset, which the shared
+// memory instructions take as an immediate: exact when S is a multiple of the pad unit
+// U (then pad(i + r S) = pad(i) + r (S + S / U)), or when S = 1, R divides U and i is a
+// multiple of R (then i and i + R - 1 lie in one unit).
+template <typename T, int S, int R> __host__ __device__ constexpr bool pad_affine() {
+  return S % (1 << pad_shift<T>()) == 0 || (S == 1 && (1 << pad_shift<T>()) % R == 0);
+}
+template <typename T, int S> __host__ __device__ constexpr int pad_step() {
+  return S % (1 << pad_shift<T>()) == 0 ? S + S / (1 << pad_shift<T>()) : S;
+}
 
 // Offset of the twiddle block of the stage with sub-transform length NS in the
 // per-stage table (blocks of R x NS entries for every stage with NS > 1, in order).
@@ -273,8 +292,14 @@ __device__ __forceinline__ void stage(typename Cx<T>::type* buf, int t, bool act
 #pragma unroll
     for (int m = 0; m < M; ++m) {
       const int j = t + m * NT;
+      if constexpr (NR % (1 << pad_shift<T>()) == 0) {
+        const C* src = buf + pad<T>(j);
 #pragma unroll
-      for (int r = 0; r < R; ++r) v[m * R + r] = buf[pad<T>(j + r * NR)];
+        for (int r = 0; r < R; ++r) v[m * R + r] = src[r * pad_step<T, NR>()];
+      } else {
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[m * R + r] = buf[pad<T>(j + r * NR)];
+      }
     }
   }
   __syncthreads();
@@ -290,8 +315,14 @@ __device__ __forceinline__ void stage(typename Cx<T>::type* buf, int t, bool act
     }
     dft<T, C, R>(v + m * R);
     const int base = (j / NS) * NS * R + k;
+    if constexpr (pad_affine<T, NS, R>()) {
+      C* dst = buf + pad<T>(base);
 #pragma unroll
-    for (int r = 0; r < R; ++r) buf[pad<T>(base + r * NS)] = v[m * R + r];
+      for (int r = 0; r < R; ++r) dst[r * pad_step<T, NS>()] = v[m * R + r];
+    } else {
+#pragma unroll
+      for (int r = 0; r < R; ++r) buf[pad<T>(base + r * NS)] = v[m * R + r];
+    }
   }
   }
   __syncthreads();
@@ -334,7 +365,8 @@ template <int LOGN, int E> __host__ __device__ constexpr int last_ns() {
 }
 
 // The real row's spectrum from the complex transform Z of its pairs (as
-// even_odd_split), with the last Stockham stage done in registers: thread t takes the
+// even_odd_split; FP32 only: rtw is followed by its halved copy), with the last
+// Stockham stage done in registers: thread t takes the
 // butterflies j = t and j = NS - t (thread 0: 0 and NS/2), whose outputs are Z_k,
 // k = j + NS r, and their partners Z_{NH-k}, so the split needs no exchange.  Needs
 // NS = 2 NT (true for nx/2 = 2048 with E = 16 or 8).  buf holds the input of the last
@@ -350,10 +382,13 @@ __device__ __forceinline__ void last_stage_split(const typename Cx<T>::type* buf
   static_assert(NS == 2 * (N / E), "last_stage_split: NS must be twice the thread count");
   const int j1 = t, j2 = t ? NS - t : NS / 2;
   C a[R], b[R];
+  static_assert(pad_affine<T, NS, R>() && NS > 1, "last_stage_split: NS a multiple of the pad unit");
+  const C* s1 = buf + pad<T>(j1);
+  const C* s2 = buf + pad<T>(j2);
 #pragma unroll
   for (int r = 0; r < R; ++r) {
-    a[r] = buf[pad<T>(j1 + r * NS)];
-    b[r] = buf[pad<T>(j2 + r * NS)];
+    a[r] = s1[r * pad_step<T, NS>()];
+    b[r] = s2[r * pad_step<T, NS>()];
   }
 #pragma unroll
   for (int r = 1; r < R; ++r) {
@@ -362,22 +397,38 @@ __device__ __forceinline__ void last_stage_split(const typename Cx<T>::type* buf
   }
   dft<T, C, R>(a);
   dft<T, C, R>(b);
-  // X_ks and X_kl (kl = NH - ks) from zk = Z_ks and zl = Z_kl
+  // X_ks and X_kl (kl = NH - ks) from zk = Z_ks and zl = Z_kl: with e2 = 2e, o2 = 2o and
+  // the halved table rtwh = rtw/2 (exact), w o = rtwh o2 and e = e2/2 enters through a
+  // fused multiply-add: the same values as (e, o, rtw) with fewer instructions
+  const C* rtwh = rtw + N + 1;
   const uint64_t pol = l2_keep();
   auto put = [&](int ks, int kl, C zk, C zl) {
     zl.y = -zl.y;
-    const C e = {(T)0.5 * (zk.x + zl.x), (T)0.5 * (zk.y + zl.y)};
-    const C o = {(T)0.5 * (zk.x - zl.x), (T)0.5 * (zk.y - zl.y)};
-    const C wo = mul(__ldg(rtw + ks), o);
-    st_hint<2>(out + ks, C{e.x + wo.y, e.y - wo.x}, pol);
-    if (ks != kl) st_hint<2>(out + kl, C{e.x - wo.y, -e.y - wo.x}, pol);
+    const C e2 = {zk.x + zl.x, zk.y + zl.y};
+    const C o2 = {zk.x - zl.x, zk.y - zl.y};
+    const C wo = mul(__ldg(rtwh + ks), o2);
+    st_hint<2>(out + ks, C{fma((T)0.5, e2.x, wo.y), fma((T)0.5, e2.y, -wo.x)}, pol);
+    if (ks != kl) st_hint<2>(out + kl, C{fma((T)0.5, e2.x, -wo.y), fma((T)-0.5, e2.y, -wo.x)}, pol);
   };
   if (t) {
+    // k = j1 + r NS and its partner N - k = j2 + (R - 1 - r) NS (never equal for t > 0),
+    // addressed from four base pointers with compile-time offsets
+    C* o_up = out + j1;
+    C* o_dn = out + (N - j1);
+    const C* w_up = rtwh + j1;
+    const C* w_dn = rtwh + (N - j1);
+    auto put2 = [&](C* ok, C* ol, const C* wk, C zk, C zl) {
+      zl.y = -zl.y;
+      const C e2 = {zk.x + zl.x, zk.y + zl.y};
+      const C o2 = {zk.x - zl.x, zk.y - zl.y};
+      const C wo = mul(__ldg(wk), o2);
+      st_hint<2>(ok, C{fma((T)0.5, e2.x, wo.y), fma((T)0.5, e2.y, -wo.x)}, pol);
+      st_hint<2>(ol, C{fma((T)0.5, e2.x, -wo.y), fma((T)-0.5, e2.y, -wo.x)}, pol);
+    };
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-      const int k = j1 + r * NS;  // partner N - k = j2 + (R - 1 - r) NS
-      if (r < R / 2) put(k, N - k, a[r], b[R - 1 - r]);
-      else put(N - k, k, b[R - 1 - r], a[r]);
+      if (r < R / 2) put2(o_up + r * NS, o_dn - r * NS, w_up + r * NS, a[r], b[R - 1 - r]);
+      else put2(o_dn - r * NS, o_up + r * NS, w_dn - r * NS, b[R - 1 - r], a[r]);
     }
   } else {
     put(0, N, a[0], a[0]);
@@ -418,8 +469,14 @@ __device__ __forceinline__ void stage_first_global(const typename Cx<T>::type* _
   for (int m = 0; m < M; ++m) {
     const int j = t + m * NT;
     dft<T, C, R>(v + m * R);
+    if constexpr (pad_affine<T, 1, R>()) {
+      C* dst = buf + pad<T>(j * R);
 #pragma unroll
-    for (int r = 0; r < R; ++r) buf[pad<T>(j * R + r)] = v[m * R + r];
+      for (int r = 0; r < R; ++r) dst[r] = v[m * R + r];
+    } else {
+#pragma unroll
+      for (int r = 0; r < R; ++r) buf[pad<T>(j * R + r)] = v[m * R + r];
+    }
   }
   __syncthreads();
 }
@@ -440,8 +497,14 @@ __device__ __forceinline__ void stage_last_global(const typename Cx<T>::type* bu
 #pragma unroll
   for (int m = 0; m < M; ++m) {
     const int j = t + m * NT;
+    if constexpr (NR % (1 << pad_shift<T>()) == 0) {
+      const C* src = buf + pad<T>(j);
 #pragma unroll
-    for (int r = 0; r < R; ++r) v[m * R + r] = buf[pad<T>(j + r * NR)];
+      for (int r = 0; r < R; ++r) v[m * R + r] = src[r * pad_step<T, NR>()];
+    } else {
+#pragma unroll
+      for (int r = 0; r < R; ++r) v[m * R + r] = buf[pad<T>(j + r * NR)];
+    }
   }
 #pragma unroll
   for (int m = 0; m < M; ++m) {
@@ -485,7 +548,8 @@ __device__ __forceinline__ void fft_rest_to_global(typename Cx<T>::type* buf, in
 // before the strip values, which the previous kernel (the blend + interpolation) writes.
 // f itself was written before that kernel's own wait returned, and this kernel was
 // launched after that kernel triggered, so f may be read before the wait.
-template <typename T, typename TV>
+// NTHR: the block size (blockDim.x) when known at compile time, else 0
+template <typename T, typename TV, int NTHR = 0>
 __device__ __forceinline__ void assemble_row(const RowArgs& ra, int mode, int NH, int j, int f,
                                              const T* __restrict__ ext,
                                              const double* __restrict__ f_grid,
@@ -493,12 +557,13 @@ __device__ __forceinline__ void assemble_row(const RowArgs& ra, int mode, int NH
                                              typename Cx<T>::type* buf) {
   using C = typename Cx<T>::type;
   const int nx = 2 * NH;
+  const int nthr = NTHR ? NTHR : (int)blockDim.x;
   auto put = [&](int i, T v) { reinterpret_cast<T*>(&buf[pad<T>(i >> 1)])[i & 1] = v; };
   if (mode == 0) {
     pdl_wait();
     pdl_trigger();
     const T* src = ext + (size_t)f * ra.grid_stride + (size_t)j * nx;
-    for (int n = threadIdx.x; n < NH; n += blockDim.x) {
+    for (int n = threadIdx.x; n < NH; n += nthr) {
       const C v = reinterpret_cast<const C*>(src)[n];
       buf[pad<T>(n)] = v;
     }
@@ -507,7 +572,12 @@ __device__ __forceinline__ void assemble_row(const RowArgs& ra, int mode, int NH
     const double* fg = mode == 1 ? f_grid + (size_t)f * ra.grid_stride + (size_t)j * nx
                                  : f_grid + (size_t)f * ra.grid_stride;
     const int iv0 = __ldg(ra.row_iv_off + j), iv1 = __ldg(ra.row_iv_off + j + 1);
-    for (int n = threadIdx.x; n < NH; n += blockDim.x) buf[pad<T>(n)] = C{(T)0, (T)0};
+    if (NTHR > 0 && NTHR % (1 << pad_shift<T>()) == 0 && NH % NTHR == 0) {
+      C* z = buf + pad<T>(threadIdx.x);  // n = t + i NTHR: pad(n) = pad(t) + i pad_step
+      for (int i = 0; i < NH / NTHR; ++i) z[i * pad_step<T, (NTHR > 0 ? NTHR : 1)>()] = C{(T)0, (T)0};
+    } else {
+      for (int n = threadIdx.x; n < NH; n += nthr) buf[pad<T>(n)] = C{(T)0, (T)0};
+    }
     __syncthreads();
     // inside intervals [lo, hi]: the pairs n with lo <= 2n and 2n + 1 <= hi as one
     // 16-byte load each when the source is 16-byte aligned at even i (eight loads in
@@ -520,23 +590,32 @@ __device__ __forceinline__ void assemble_row(const RowArgs& ra, int mode, int NH
         const int p0 = (lo + 1) >> 1, p1 = (hi + 1) >> 1;  // pairs p0 .. p1 - 1
         const double2* fg2 = reinterpret_cast<const double2*>(src);
         const uint64_t pol = l2_drop();
-        for (int n0 = p0 + threadIdx.x; n0 < p1; n0 += 8 * blockDim.x) {
+        for (int n0 = p0 + threadIdx.x; n0 < p1; n0 += 8 * nthr) {
+          // pairs n0 + u nthr from two base pointers (with a compile-time block size that
+          // is a multiple of the pad unit, pad(n0 + u nthr) = pad(n0) + u pad_step)
+          constexpr bool affine = NTHR > 0 && NTHR % (1 << pad_shift<T>()) == 0;
+          const double2* s2 = fg2 + n0;
+          C* d2 = buf + pad<T>(n0);
           double2 d[8];
 #pragma unroll
           for (int u = 0; u < 8; ++u) {
-            const int n = n0 + u * blockDim.x;
-            d[u] = n < p1 ? ld_stream(fg2 + n, pol) : make_double2(0.0, 0.0);
+            const int n = n0 + u * nthr;
+            d[u] = n < p1 ? ld_stream(s2 + u * nthr, pol) : make_double2(0.0, 0.0);
           }
 #pragma unroll
           for (int u = 0; u < 8; ++u) {
-            const int n = n0 + u * blockDim.x;
-            if (n < p1) buf[pad<T>(n)] = C{from_double<T>(d[u].x), from_double<T>(d[u].y)};
+            const int n = n0 + u * nthr;
+            if (n < p1) {
+              C* dst = affine ? d2 + u * pad_step<T, (NTHR > 0 ? NTHR : 1)>() : buf + pad<T>(n);
+              if constexpr (sizeof(T) == 4) *dst = d2f2_rn(d[u]);
+              else *dst = C{d[u].x, d[u].y};
+            }
           }
         }
         if (threadIdx.x == 0 && (lo & 1)) put(lo, from_double<T>(__ldg(src + lo)));
         if (threadIdx.x == 0 && !(hi & 1)) put(hi, from_double<T>(__ldg(src + hi)));
       } else {
-        for (int i = lo + threadIdx.x; i <= hi; i += blockDim.x) put(i, from_double<T>(__ldg(src + i)));
+        for (int i = lo + threadIdx.x; i <= hi; i += nthr) put(i, from_double<T>(__ldg(src + i)));
       }
     }
     const int s0 = __ldg(ra.row_strip_off + j), s1 = __ldg(ra.row_strip_off + j + 1);
@@ -544,7 +623,7 @@ __device__ __forceinline__ void assemble_row(const RowArgs& ra, int mode, int NH
     const TV* v = vals + (size_t)f * ra.n_strip;
     pdl_wait();
     pdl_trigger();
-    for (int k = s0 + threadIdx.x; k < s1; k += blockDim.x) put(__ldg(ra.s_lin + k) - base, (T)__ldg(v + k));
+    for (int k = s0 + threadIdx.x; k < s1; k += nthr) put(__ldg(ra.s_lin + k) - base, (T)__ldg(v + k));
   }
   __syncthreads();
 }
@@ -576,13 +655,14 @@ __host__ __device__ constexpr int fp32_blocks(int threads) {
   return 1024 / threads < 1 ? 1 : (1024 / threads > 32 ? 32 : 1024 / threads);
 }
 
-// rows: nx = 2^(LOGNH+1); block = NT = 2^LOGNH / E threads
+// rows: nx = 2^(LOGNH+1); the transform's NT = 2^LOGNH / E threads, the block at least
+// one warp (row_threads: the launch's block size, which assemble_row's loops assume)
+template <typename T, int LOGNH> __host__ __device__ constexpr int row_threads() {
+  return (1 << LOGNH) / elems<T>() < 32 ? 32 : (1 << LOGNH) / elems<T>();
+}
 template <typename T, typename TV, int LOGNH>
-__global__ void __launch_bounds__((1 << LOGNH) / elems<T>() < 32 ? 32 : (1 << LOGNH) / elems<T>(),
-                                  sizeof(T) == 4 ? fp32_blocks((1 << LOGNH) / elems<T>() < 32
-                                                                   ? 32
-                                                                   : (1 << LOGNH) / elems<T>())
-                                                 : 1)
+__global__ void __launch_bounds__(row_threads<T, LOGNH>(),
+                                  sizeof(T) == 4 ? fp32_blocks(row_threads<T, LOGNH>()) : 1)
 k_fft_rows_p2(FftArgs fa, RowArgs ra, int mode, const T* __restrict__ ext,
               const double* __restrict__ f_grid, const TV* __restrict__ vals,
               typename Cx<T>::type* __restrict__ inter) {
@@ -593,7 +673,7 @@ k_fft_rows_p2(FftArgs fa, RowArgs ra, int mode, const T* __restrict__ ext,
   extern __shared__ __align__(16) unsigned char smem_raw[];
   C* buf = reinterpret_cast<C*>(smem_raw);
   const int j = blockIdx.x, f = blockIdx.y, t = threadIdx.x;
-  assemble_row<T, TV>(ra, mode, NH, j, f, ext, f_grid, vals, buf);
+  assemble_row<T, TV, row_threads<T, LOGNH>()>(ra, mode, NH, j, f, ext, f_grid, vals, buf);
   const C* tw = reinterpret_cast<const C*>(fa.tsx);
   C* out = inter + ((size_t)f * fa.ny + j) * fa.pitch;
   // FP32: the last stage and the split in registers (for FP64, bound by its FP64 pipe,
@@ -1110,7 +1190,7 @@ static void ff_cols_p2_launch(const FftArgs& fa, int n_f, int n_out, const void*
 template <typename T, typename TV, int L>
 static void rows_launch(const FftArgs& fa, const RowArgs& ra, int n_f, int mode, const void* ext,
                         const double* fg, const void* vals, void* inter, cudaStream_t s) {
-  constexpr int NT = (1 << L) / elems<T>() < 32 ? 32 : (1 << L) / elems<T>();
+  constexpr int NT = row_threads<T, L>();
   const size_t sm = (size_t)padded<T>(1 << L) * sizeof(typename Cx<T>::type);
   auto k = k_fft_rows_p2<T, TV, L>;
   cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);

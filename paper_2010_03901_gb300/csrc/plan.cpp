@@ -877,7 +877,9 @@ extern "C" fc2d_status fc2d_plan(const fc2d_boundary* boundary, const fc2d_grid*
   }
   std::vector<float> tw32x(p->fx.tw_host.begin(), p->fx.tw_host.end());
   std::vector<float> tw32y(p->fy.tw_host.begin(), p->fy.tw_host.end());
+  // FP32: the table, then the same halved (exactly) for the row kernel's split
   std::vector<float> rtw32(p->rtw_host.begin(), p->rtw_host.end());
+  for (size_t k = 0, n = p->rtw_host.size(); k < n; ++k) rtw32.push_back(0.5f * rtw32[k]);
   std::vector<double> tsx64 = stage_twiddles(p->fx, 8), tsy64 = stage_twiddles(p->fy, 8);
   std::vector<double> tsx16 = stage_twiddles(p->fx, 16), tsy16 = stage_twiddles(p->fy, 16);
   std::vector<float> tsx32(tsx16.begin(), tsx16.end()), tsy32(tsy16.begin(), tsy16.end());

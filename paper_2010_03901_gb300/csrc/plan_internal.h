@@ -120,7 +120,7 @@ struct fc2d_plan_s {
   fc2d::FftAxis fx, fy;                      // nx/2 (complex) and ny
   std::vector<double> rtw_host;              // exp(-2 pi i k/nx), k <= nx/2 (R2C post-process)
   double* rtw64 = nullptr;
-  float* rtw32 = nullptr;
+  float* rtw32 = nullptr;   // [2][nx/2 + 1] complex: exp(-2 pi i k/nx), then halved
   fc2d::DeviceTables dev;
   fc2d::Workspace ws;
   int host_status = 0;
