@@ -286,7 +286,6 @@ __device__ __forceinline__ void stage(typename Cx<T>::type* buf, int t, bool act
   constexpr int NT = N / E;
   constexpr int NR = N / R;
   constexpr int M = E / R;
-  constexpr int TSTEP = N / (NS * R);
   C v[E];
   if (active) {
 #pragma unroll
@@ -492,7 +491,6 @@ __device__ __forceinline__ void stage_last_global(const typename Cx<T>::type* bu
   constexpr int NT = N / E;
   constexpr int NR = N / R;
   constexpr int M = E / R;
-  constexpr int TSTEP = N / (NS * R);
   C v[E];
 #pragma unroll
   for (int m = 0; m < M; ++m) {
@@ -574,7 +572,8 @@ __device__ __forceinline__ void assemble_row(const RowArgs& ra, int mode, int NH
     const int iv0 = __ldg(ra.row_iv_off + j), iv1 = __ldg(ra.row_iv_off + j + 1);
     if (NTHR > 0 && NTHR % (1 << pad_shift<T>()) == 0 && NH % NTHR == 0) {
       C* z = buf + pad<T>(threadIdx.x);  // n = t + i NTHR: pad(n) = pad(t) + i pad_step
-      for (int i = 0; i < NH / NTHR; ++i) z[i * pad_step<T, (NTHR > 0 ? NTHR : 1)>()] = C{(T)0, (T)0};
+      for (int i = 0; i < NH / (NTHR > 0 ? NTHR : 1); ++i)
+        z[i * pad_step<T, (NTHR > 0 ? NTHR : 1)>()] = C{(T)0, (T)0};
     } else {
       for (int n = threadIdx.x; n < NH; n += nthr) buf[pad<T>(n)] = C{(T)0, (T)0};
     }
@@ -824,7 +823,7 @@ __device__ __forceinline__ void dft64_cols(float2* a, int c, int l, float2* ex,
                                            const float2* __restrict__ w, int n2 = 64) {
   dft<float, float2, 8>(a);
 #pragma unroll
-  for (int m = 1; m < 8; ++m) a[m] = mul(a[m], __ldg(w + ((l * m) & 63) * n2));
+  for (int m = 1; m < 8; ++m) a[m] = mul(a[m], __ldg(w + (l * m) * n2));  // l m <= 49
 #pragma unroll
   for (int m = 0; m < 8; ++m) ex[(m * 8 + l) * CC + c] = a[m];
   __syncthreads();
@@ -835,6 +834,8 @@ __device__ __forceinline__ void dft64_cols(float2* a, int c, int l, float2* ex,
 
 // CC adjacent columns per block of 8 CC threads (16, 32 or 64: every width computes the
 // same values; wider blocks read longer contiguous row segments).
+// Row offsets within one function's slab (4096 x pitch < 2^32 elements) in 32-bit
+// unsigned arithmetic: one multiply and one wide add per access.
 template <int CC>
 __global__ void __launch_bounds__(8 * CC, 2048 / (8 * CC)) k_cols4k_a(FftArgs fa, float2* __restrict__ inter) {
   __shared__ float2 ex[64 * CC];
@@ -850,14 +851,14 @@ __global__ void __launch_bounds__(8 * CC, 2048 / (8 * CC)) k_cols4k_a(FftArgs fa
   float2 a[8];
 #pragma unroll
   for (int i = 0; i < 8; ++i)
-    a[i] = live ? col[(size_t)(64 * (l + 8 * i) + j2) * fa.pitch] : make_float2(0.f, 0.f);
+    a[i] = live ? col[(unsigned)(64 * (l + 8 * i) + j2) * (unsigned)fa.pitch] : make_float2(0.f, 0.f);
   const uint64_t pol = l2_keep();
   dft64_cols<CC>(a, c, l, ex, w);
 #pragma unroll
   for (int m2 = 0; m2 < 8; ++m2) {
     const int m1 = l + 8 * m2;
-    const float2 y = mul(a[m2], __ldg(w + ((j2 * m1) & 4095)));
-    if (live) st_hint<2>(col + (size_t)(64 * m1 + j2) * fa.pitch, y, pol);
+    const float2 y = mul(a[m2], __ldg(w + j2 * m1));  // j2 m1 <= 63 * 63
+    if (live) st_hint<2>(col + (unsigned)(64 * m1 + j2) * (unsigned)fa.pitch, y, pol);
   }
 }
 
@@ -878,7 +879,7 @@ __global__ void __launch_bounds__(8 * CC, 2048 / (8 * CC)) k_cols4k_b(FftArgs fa
   float2 a[8];
 #pragma unroll
   for (int i = 0; i < 8; ++i)
-    a[i] = live ? col[(size_t)(64 * m1 + l + 8 * i) * fa.pitch] : make_float2(0.f, 0.f);
+    a[i] = live ? col[(unsigned)(64 * m1 + l + 8 * i) * (unsigned)fa.pitch] : make_float2(0.f, 0.f);
   dft64_cols<CC>(a, c, l, ex, w);
   // the intermediate is scratch and this block was the last reader of its 8 x CC
   // values per thread group: drop the lines from L2 without writing them back (each
@@ -888,7 +889,7 @@ __global__ void __launch_bounds__(8 * CC, 2048 / (8 * CC)) k_cols4k_b(FftArgs fa
   if (drop && (c & 15) == 0 && live) {
 #pragma unroll
     for (int i = 0; i < 8; ++i)
-      asm volatile("discard.global.L2 [%0], 128;" ::"l"(col + (size_t)(64 * m1 + l + 8 * i) * fa.pitch)
+      asm volatile("discard.global.L2 [%0], 128;" ::"l"(col + (unsigned)(64 * m1 + l + 8 * i) * (unsigned)fa.pitch)
                    : "memory");
   }
   const float sc = (float)fa.scale;
@@ -898,7 +899,7 @@ __global__ void __launch_bounds__(8 * CC, 2048 / (8 * CC)) k_cols4k_b(FftArgs fa
 #pragma unroll
     for (int m2p = 0; m2p < 8; ++m2p) {
       const int m2 = l + 8 * m2p;
-      st_hint<4>(out + (size_t)(m1 + 64 * m2) * ncol, make_float2(a[m2p].x * sc, a[m2p].y * sc), pol);
+      st_hint<4>(out + (unsigned)(m1 + 64 * m2) * (unsigned)ncol, make_float2(a[m2p].x * sc, a[m2p].y * sc), pol);
     }
   }
 }
