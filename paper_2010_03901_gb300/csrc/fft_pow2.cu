@@ -881,15 +881,18 @@ __global__ void __launch_bounds__(8 * CC, 2048 / (8 * CC)) k_cols4k_b(FftArgs fa
   for (int i = 0; i < 8; ++i)
     a[i] = live ? col[(unsigned)(64 * m1 + l + 8 * i) * (unsigned)fa.pitch] : make_float2(0.f, 0.f);
   dft64_cols<CC>(a, c, l, ex, w);
-  // the intermediate is scratch and this block was the last reader of its 8 x CC
-  // values per thread group: drop the lines from L2 without writing them back (each
-  // row of 16 columns is one 128-byte line; `drop` is set only when the host has
-  // checked the 128-byte alignment of the buffer and the pitch).  Only lines of live
-  // columns: a wide block's columns past the last one would name the next row's lines.
-  if (drop && (c & 15) == 0 && live) {
-#pragma unroll
-    for (int i = 0; i < 8; ++i)
-      asm volatile("discard.global.L2 [%0], 128;" ::"l"(col + (unsigned)(64 * m1 + l + 8 * i) * (unsigned)fa.pitch)
+  // the intermediate is scratch and this block was the last reader of its 64 rows x CC
+  // columns (every load completed before the transform's barrier): drop the lines from
+  // L2 without writing them back (each row of 16 columns is one 128-byte line; `drop` is
+  // set only when the host has checked the 128-byte alignment of the buffer and the
+  // pitch), one line per thread.  Only lines of live columns: a wide block's columns past
+  // the last one would name the next row's lines.
+  if (drop && (int)threadIdx.x < 64 * (CC / 16)) {
+    const int r = threadIdx.x & 63, g = threadIdx.x >> 6;
+    const int kx0 = blockIdx.x * CC + 16 * g;
+    if (kx0 < ncol)
+      asm volatile("discard.global.L2 [%0], 128;" ::"l"(inter + (size_t)f * 4096 * fa.pitch +
+                                                         (unsigned)(64 * m1 + r) * (unsigned)fa.pitch + kx0)
                    : "memory");
   }
   const float sc = (float)fa.scale;
@@ -915,6 +918,8 @@ __global__ void __launch_bounds__(8 * CC, 2048 / (8 * CC)) k_cols4k_b(FftArgs fa
 //           m1 + 64 m2; then the intermediate's lines are dropped from L2.
 // ------------------------------------------------------------------------- //
 
+// (row offsets within one function's slab in 32-bit unsigned arithmetic, as the
+// 4096-point passes)
 __global__ void __launch_bounds__(128, fp32_blocks(128)) k_cols64_a(FftArgs fa, int n2, float2* __restrict__ inter) {
   __shared__ float2 ex[64 * kC4Cols];
   const int c = threadIdx.x & (kC4Cols - 1), l = threadIdx.x / kC4Cols;
@@ -929,13 +934,13 @@ __global__ void __launch_bounds__(128, fp32_blocks(128)) k_cols64_a(FftArgs fa, 
   float2 a[8];
 #pragma unroll
   for (int i = 0; i < 8; ++i)
-    a[i] = live ? col[(size_t)(n2 * (l + 8 * i) + j2) * fa.pitch] : make_float2(0.f, 0.f);
+    a[i] = live ? col[(unsigned)(n2 * (l + 8 * i) + j2) * (unsigned)fa.pitch] : make_float2(0.f, 0.f);
   dft64_cols(a, c, l, ex, w, n2);
 #pragma unroll
   for (int m2 = 0; m2 < 8; ++m2) {
     const int m1 = l + 8 * m2;
     const float2 y = mul(a[m2], __ldg(w + j2 * m1));  // j2 m1 < N
-    if (live) col[(size_t)(n2 * m1 + j2) * fa.pitch] = y;
+    if (live) col[(unsigned)(n2 * m1 + j2) * (unsigned)fa.pitch] = y;
   }
 }
 
@@ -955,21 +960,21 @@ __global__ void __launch_bounds__(128, R1 * R2 >= 24 ? 4 : fp32_blocks(128)) k_c
   float2 x[N2];
 #pragma unroll
   for (int j2 = 0; j2 < N2; ++j2)
-    x[j2] = live ? col[(size_t)(N2 * m1 + j2) * fa.pitch] : make_float2(0.f, 0.f);
+    x[j2] = live ? col[(unsigned)(N2 * m1 + j2) * (unsigned)fa.pitch] : make_float2(0.f, 0.f);
   dft_ct<R1, R2>(x, w, 64);  // w_N2^t = w_N^(64 t)
   const float sc = (float)fa.scale;
   float2* out = fhat + (size_t)f * N * ncol + kx;
   if (live) {
 #pragma unroll
     for (int m2 = 0; m2 < N2; ++m2)
-      out[(size_t)(m1 + 64 * m2) * ncol] = make_float2(x[m2].x * sc, x[m2].y * sc);
+      out[(unsigned)(m1 + 64 * m2) * (unsigned)ncol] = make_float2(x[m2].x * sc, x[m2].y * sc);
   }
   // last reader of the intermediate: drop its lines (one 128-byte line per row of the
   // block's 16 columns; `drop` only when the host checked the alignment)
   if (drop && c == 0) {
 #pragma unroll
     for (int j2 = 0; j2 < N2; ++j2)
-      asm volatile("discard.global.L2 [%0], 128;" ::"l"(col + (size_t)(N2 * m1 + j2) * fa.pitch)
+      asm volatile("discard.global.L2 [%0], 128;" ::"l"(col + (unsigned)(N2 * m1 + j2) * (unsigned)fa.pitch)
                    : "memory");
   }
 }
