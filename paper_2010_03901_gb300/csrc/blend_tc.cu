@@ -737,8 +737,8 @@ __device__ __forceinline__ bool gi_item(const GatherArgs& g, const TcArgs& a, co
         if (ff >= nfl) break;
         const float* stage = stage0 + (size_t)ff * kTcComputed * ldS;
         float* out = o.vals + (size_t)(f0 + ff) * o.n_strip;
-        out[k0] = interp_apply<MM, float, float, float, true>(ia, stage, q0);
-        if (k1 >= 0) out[k1] = interp_apply<MM, float, float, float, true>(ia, stage, q1);
+        out[k0] = interp_apply<MM, float, float, float, true, false>(ia, stage, q0);
+        if (k1 >= 0) out[k1] = interp_apply<MM, float, float, float, true, false>(ia, stage, q1);
       }
     }
   }

@@ -37,8 +37,10 @@ __device__ __forceinline__ InterpPoint<MM, TW> interp_load(const InterpArgs& a, 
 }
 
 // The value of a strip point from the strip values Ff of one function ([B][ldF]); Ff
-// may be global or shared memory (plain loads).
-template <int MM, typename TF, typename TW, typename TA, bool VEC>
+// may be global or shared memory (plain loads).  WRAP false: the M normals pb .. pb+M-1
+// lie inside Ff without the cyclic wrap (a CTA's local tile), so its rows are one base
+// pointer plus multiples of ldF.
+template <int MM, typename TF, typename TW, typename TA, bool VEC, bool WRAP = true>
 __device__ __forceinline__ TA interp_apply(const InterpArgs& a, const TF* __restrict__ Ff,
                                            const InterpPoint<MM, TW>& q) {
   const int M = MM > 0 ? MM : a.M;
@@ -56,11 +58,13 @@ __device__ __forceinline__ TA interp_apply(const InterpArgs& a, const TF* __rest
       const TA w3 = (b >= 3 && b - 3 < MM) ? (TA)q.eta[b >= 3 ? b - 3 : 0] : (TA)0;
       ws[b] = sh == 0 ? w0 : sh == 1 ? w1 : sh == 2 ? w2 : w3;
     }
+    const TF* row0 = Ff + q.pb * ld + s0;  // used without the wrap
 #pragma unroll
     for (int ai = 0; ai < MM; ++ai) {
       int pr = q.pb + ai;
       pr = pr < 0 ? pr + B : (pr >= B ? pr - B : pr);
-      const float4* row = reinterpret_cast<const float4*>(Ff + (size_t)pr * ld + s0);
+      const float4* row = reinterpret_cast<const float4*>(
+          WRAP ? Ff + (size_t)pr * ld + s0 : row0 + ai * ld);
       TA v = 0;
 #pragma unroll
       for (int u = 0; u < 3; ++u) {
