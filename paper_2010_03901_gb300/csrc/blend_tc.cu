@@ -641,6 +641,20 @@ __device__ __forceinline__ bool gi_item(const GatherArgs& g, const TcArgs& a, co
     if (s == 0) stage[ln * ldS] = (float)fv0;
     }  // functions of the CTA
   }
+  // the interpolation's plan records of this CTA's points (16 weight rows, packed
+  // indices, strip indices) into L2 while the MMAs and the epilogue run
+  {
+    const int nl = ((o1 - o0) * 4 + 127) / 128 + 1;  // 128-byte lines per record row
+    for (int idx = tid; idx < 18 * nl; idx += NT) {
+      const int rowi = idx / nl, line = idx - rowi * nl;
+      const char* base = rowi < 16 ? reinterpret_cast<const char*>(o.w + (size_t)rowi * o.n_strip + o0)
+                         : rowi == 16 ? reinterpret_cast<const char*>(o.pack + o0)
+                                      : reinterpret_cast<const char*>(o.k + o0);
+      const char* a = base + (size_t)line * 128;
+      // stay inside the record row: the last line starts before its end
+      if (a < base + (size_t)(o1 - o0) * 4) asm volatile("prefetch.global.L2 [%0];" ::"l"(a));
+    }
+  }
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
