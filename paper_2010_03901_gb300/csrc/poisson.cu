@@ -56,6 +56,7 @@ struct PoissonState {
   double* dnodes = nullptr;         // device copy
   // per-solve workspace
   double *V = nullptr, *w = nullptr, *h = nullptr, *g = nullptr, *phi = nullptr;
+  struct GmresDev* gm = nullptr;  // GMRES's Hessenberg part and state (device)
   double *ghat = nullptr, *phiR = nullptr, *c00 = nullptr;
   float4 *ab = nullptr, *abR = nullptr;        // double-float node coefficients [Nb], [R Nb]
   float4 *posB = nullptr, *posR = nullptr;     // nodes in grid units [Nb][2], [R Nb][2]
@@ -201,7 +202,10 @@ __global__ void k_bie_matrix(int Nb, const double* x, const double* y, const dou
 }
 
 // y = A x, one warp per row
-__global__ void k_gemv(int n, const double* A, const double* x, double* y) {
+// The GMRES vector kernels return at once when *stop is set (a batch of iterations
+// launched ahead of the host's convergence check ran past the converged one).
+__global__ void k_gemv(int n, const double* A, const double* x, double* y, const int* stop) {
+  if (*stop) return;
   int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
   if (row >= n) return;
   const double* a = A + (size_t)row * n;
@@ -212,10 +216,10 @@ __global__ void k_gemv(int n, const double* A, const double* x, double* y) {
 }
 
 // h[i] = <V_i, w>, i < m (one block per i)
-__global__ void k_dots(int n, int m, const double* V, const double* w, double* h) {
+__global__ void k_dots(int n, int m, const double* V, const double* w, double* h, const int* stop) {
   __shared__ double red[256];
   int i = blockIdx.x;
-  if (i >= m) return;
+  if (i >= m || *stop) return;
   double s = 0.0;
   for (int k = threadIdx.x; k < n; k += blockDim.x) s = fma(V[(size_t)i * n + k], w[k], s);
   red[threadIdx.x] = s;
@@ -228,17 +232,18 @@ __global__ void k_dots(int n, int m, const double* V, const double* w, double* h
 }
 
 // w -= sum_{i<m} h[i] V_i
-__global__ void k_sub_proj(int n, int m, const double* V, const double* h, double* w) {
+__global__ void k_sub_proj(int n, int m, const double* V, const double* h, double* w,
+                           const int* stop) {
   int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= n) return;
+  if (k >= n || *stop) return;
   double s = w[k];
   for (int i = 0; i < m; ++i) s = fma(-h[i], V[(size_t)i * n + k], s);
   w[k] = s;
 }
 
-__global__ void k_scale_to(int n, const double* w, const double* nrm, double* v) {
+__global__ void k_scale_to(int n, const double* w, const double* nrm, double* v, const int* stop) {
   int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k < n) v[k] = w[k] / *nrm;
+  if (k < n && !*stop) v[k] = w[k] / *nrm;
 }
 
 // x = sum_{i<m} y[i] V_i
@@ -248,6 +253,69 @@ __global__ void k_combine(int n, int m, const double* V, const double* y, double
   double s = 0.0;
   for (int i = 0; i < m; ++i) s = fma(y[i], V[(size_t)i * n + k], s);
   x[k] = s;
+}
+
+// GMRES's small dense part on the device (one thread): the Hessenberg matrix H, the
+// Givens rotations (cs, sn), the rotated right-hand side e and the state, so that the
+// host reads the state once per batch of iterations instead of after every dot product.
+struct GmresDev {
+  double H[(kGmresMax + 1) * kGmresMax];  // H[i][j] at i kGmresMax + j
+  double cs[kGmresMax], sn[kGmresMax], e[kGmresMax + 1], y[kGmresMax];
+  double h1[kGmresMax + 1], h2[kGmresMax + 1];  // the two Gram-Schmidt passes' projections
+  double nn, hn, beta, resid;                   // ||w||^2, ||w||, ||g||, |e_m| / beta
+  int stop, done, m, pad;                       // stop: no further vector work
+};
+
+// beta = ||g|| (nn holds <g, g>); V_0 = g / beta follows with hn = beta
+__global__ void k_gmres_init(GmresDev* G) {
+  const double beta = sqrt(G->nn);
+  G->beta = beta;
+  G->hn = beta;
+  G->e[0] = beta;
+  G->m = 0;
+  G->resid = 0.0;
+  G->done = beta == 0.0 ? 1 : 0;
+  G->stop = G->done;
+}
+
+// Iteration j after the two projections (h1, h2) and <w, w> (nn): column j of H, the
+// earlier rotations applied to it, its own rotation, the residual estimate |e_{j+1}|.
+__global__ void k_gmres_step(GmresDev* G, int j, double tol) {
+  if (G->done) return;
+  double* H = G->H;
+  for (int i = 0; i <= j; ++i) H[i * kGmresMax + j] = G->h1[i] + G->h2[i];
+  const double hn = sqrt(G->nn);
+  G->hn = hn;
+  H[(j + 1) * kGmresMax + j] = hn;
+  for (int i = 0; i < j; ++i) {
+    const double a = H[i * kGmresMax + j], b = H[(i + 1) * kGmresMax + j];
+    H[i * kGmresMax + j] = G->cs[i] * a + G->sn[i] * b;
+    H[(i + 1) * kGmresMax + j] = -G->sn[i] * a + G->cs[i] * b;
+  }
+  const double a = H[j * kGmresMax + j], b = H[(j + 1) * kGmresMax + j];
+  const double r = hypot(a, b);
+  G->cs[j] = r == 0 ? 1.0 : a / r;
+  G->sn[j] = r == 0 ? 0.0 : b / r;
+  H[j * kGmresMax + j] = r;
+  H[(j + 1) * kGmresMax + j] = 0.0;
+  G->e[j + 1] = -G->sn[j] * G->e[j];
+  G->e[j] = G->cs[j] * G->e[j];
+  G->m = j + 1;
+  G->resid = fabs(G->e[j + 1]) / G->beta;
+  if (fabs(G->e[j + 1]) <= tol * G->beta || hn == 0.0 || j + 1 == kGmresMax) {
+    G->done = 1;
+    G->stop = 1;
+  }
+}
+
+// y from the triangular system R y = e over the first m columns
+__global__ void k_gmres_solve(GmresDev* G) {
+  const int m = G->m;
+  for (int i = m - 1; i >= 0; --i) {
+    double sacc = G->e[i];
+    for (int k = i + 1; k < m; ++k) sacc -= G->H[i * kGmresMax + k] * G->y[k];
+    G->y[i] = sacc / G->H[i * kGmresMax + i];
+  }
 }
 
 // hat phi_k = (1/Nb) sum_j phi_j e^{-2 pi i jk/Nb}, k = 0..Nb/2
@@ -732,7 +800,8 @@ fc2d_status poisson_setup(fc2d_plan_s* p, int Nb) {
   double* ddiag = nullptr;
   if ((st = up(P, &ddiag, diag)) || (st = alloc(P, &P->A, (size_t)Nb * Nb)) ||
       (st = alloc(P, &P->V, (size_t)(kGmresMax + 1) * Nb)) || (st = alloc(P, &P->w, Nb)) ||
-      (st = alloc(P, &P->h, kGmresMax + 2)) || (st = alloc(P, &P->g, Nb)) ||
+      (st = alloc(P, &P->h, kGmresMax + 2)) || (st = alloc(P, &P->gm, 1)) ||
+      (st = alloc(P, &P->g, Nb)) ||
       (st = alloc(P, &P->phi, Nb)) || (st = alloc(P, &P->ghat, 2 * (Nb / 2 + 1))) ||
       (st = alloc(P, &P->phiR, NR)) || (st = alloc(P, &P->ab, (size_t)Nb)) ||
       (st = alloc(P, &P->abR, (size_t)NR)) || (st = alloc(P, &P->c00, 1024)))
@@ -749,80 +818,47 @@ fc2d_status poisson_setup(fc2d_plan_s* p, int Nb) {
   return FC2D_OK;
 }
 
-// GMRES (no restart) for A phi = g on device vectors, host-side Hessenberg least squares.
+// GMRES (no restart) for A phi = g: Arnoldi with classical Gram-Schmidt twice on device
+// vectors, the Hessenberg least squares by Givens rotations on the device
+// (k_gmres_step); iterations are launched in batches of kGmresBatch and the host reads
+// the state once per batch (the vector kernels of iterations past convergence return
+// at once).
+constexpr int kGmresBatch = 8;
 static fc2d_status gmres(PoissonState* P, cudaStream_t s, double tol) {
   const int n = P->Nb;
   const unsigned gb = (unsigned)((n + 255) / 256);
-  std::vector<double> H((size_t)(kGmresMax + 1) * kGmresMax, 0.0), cs(kGmresMax), sn(kGmresMax),
-      e(kGmresMax + 1, 0.0), hcol(kGmresMax + 2);
+  GmresDev* G = P->gm;
+  int* stop = &G->stop;
+  cudaMemsetAsync(stop, 0, sizeof(int), s);
   // beta = ||g||, V_0 = g / beta
-  k_dots<<<1, 256, 0, s>>>(n, 1, P->g, P->g, P->h);
-  double beta2 = 0;
-  cudaMemcpyAsync(&beta2, P->h, 8, cudaMemcpyDeviceToHost, s);
-  cudaStreamSynchronize(s);
-  double beta = std::sqrt(beta2);
-  if (beta == 0) {
-    cudaMemsetAsync(P->phi, 0, n * 8, s);
-    P->last_iters = 0;
-    return FC2D_OK;
-  }
-  double hb[1] = {beta};
-  cudaMemcpyAsync(P->h + kGmresMax + 1, hb, 8, cudaMemcpyHostToDevice, s);
-  k_scale_to<<<gb, 256, 0, s>>>(n, P->g, P->h + kGmresMax + 1, P->V);
-  e[0] = beta;
-  int m = 0;
-  for (int j = 0; j < kGmresMax; ++j) {
-    double* vj = P->V + (size_t)j * n;
-    k_gemv<<<(unsigned)((n * 32 + 255) / 256), 256, 0, s>>>(n, P->A, vj, P->w);
-    // classical Gram-Schmidt, twice
-    for (int pass = 0; pass < 2; ++pass) {
-      k_dots<<<j + 1, 256, 0, s>>>(n, j + 1, P->V, P->w, P->h);
-      k_sub_proj<<<gb, 256, 0, s>>>(n, j + 1, P->V, P->h, P->w);
-      std::vector<double> hp(j + 1);
-      cudaMemcpyAsync(hp.data(), P->h, (j + 1) * 8, cudaMemcpyDeviceToHost, s);
-      cudaStreamSynchronize(s);
-      for (int i = 0; i <= j; ++i) H[(size_t)i * kGmresMax + j] += hp[i];
+  k_dots<<<1, 256, 0, s>>>(n, 1, P->g, P->g, &G->nn, stop);
+  k_gmres_init<<<1, 1, 0, s>>>(G);
+  k_scale_to<<<gb, 256, 0, s>>>(n, P->g, &G->hn, P->V, stop);
+  int state[4] = {0, 0, 0, 0};  // stop, done, m, pad
+  for (int j0 = 0; j0 < kGmresMax && !state[1]; j0 += kGmresBatch) {
+    for (int j = j0; j < std::min(j0 + kGmresBatch, kGmresMax); ++j) {
+      const double* vj = P->V + (size_t)j * n;
+      k_gemv<<<(unsigned)((n * 32 + 255) / 256), 256, 0, s>>>(n, P->A, vj, P->w, stop);
+      k_dots<<<j + 1, 256, 0, s>>>(n, j + 1, P->V, P->w, G->h1, stop);
+      k_sub_proj<<<gb, 256, 0, s>>>(n, j + 1, P->V, G->h1, P->w, stop);
+      k_dots<<<j + 1, 256, 0, s>>>(n, j + 1, P->V, P->w, G->h2, stop);
+      k_sub_proj<<<gb, 256, 0, s>>>(n, j + 1, P->V, G->h2, P->w, stop);
+      k_dots<<<1, 256, 0, s>>>(n, 1, P->w, P->w, &G->nn, stop);
+      k_gmres_step<<<1, 1, 0, s>>>(G, j, tol);
+      k_scale_to<<<gb, 256, 0, s>>>(n, P->w, &G->hn, P->V + (size_t)(j + 1) * n, stop);
     }
-    k_dots<<<1, 256, 0, s>>>(n, 1, P->w, P->w, P->h);
-    double nn = 0;
-    cudaMemcpyAsync(&nn, P->h, 8, cudaMemcpyDeviceToHost, s);
-    cudaStreamSynchronize(s);
-    double hn = std::sqrt(nn);
-    H[(size_t)(j + 1) * kGmresMax + j] = hn;
-    if (hn > 0) {
-      double hv[1] = {hn};
-      cudaMemcpyAsync(P->h + kGmresMax + 1, hv, 8, cudaMemcpyHostToDevice, s);
-      k_scale_to<<<gb, 256, 0, s>>>(n, P->w, P->h + kGmresMax + 1, P->V + (size_t)(j + 1) * n);
-    }
-    // Givens rotations
-    for (int i = 0; i < j; ++i) {
-      double a = H[(size_t)i * kGmresMax + j], b = H[(size_t)(i + 1) * kGmresMax + j];
-      H[(size_t)i * kGmresMax + j] = cs[i] * a + sn[i] * b;
-      H[(size_t)(i + 1) * kGmresMax + j] = -sn[i] * a + cs[i] * b;
-    }
-    double a = H[(size_t)j * kGmresMax + j], b = H[(size_t)(j + 1) * kGmresMax + j];
-    double r = std::hypot(a, b);
-    cs[j] = r == 0 ? 1.0 : a / r;
-    sn[j] = r == 0 ? 0.0 : b / r;
-    H[(size_t)j * kGmresMax + j] = r;
-    H[(size_t)(j + 1) * kGmresMax + j] = 0.0;
-    e[j + 1] = -sn[j] * e[j];
-    e[j] = cs[j] * e[j];
-    m = j + 1;
-    if (std::fabs(e[j + 1]) <= tol * beta || hn == 0) break;
+    cudaMemcpyAsync(state, stop, sizeof(state), cudaMemcpyDeviceToHost, s);
+    if (cudaStreamSynchronize(s) != cudaSuccess) return cuda_check(cudaGetLastError(), "GMRES");
   }
-  // solve the triangular system and combine
-  std::vector<double> yv(m);
-  for (int i = m - 1; i >= 0; --i) {
-    double sacc = e[i];
-    for (int k = i + 1; k < m; ++k) sacc -= H[(size_t)i * kGmresMax + k] * yv[k];
-    yv[i] = sacc / H[(size_t)i * kGmresMax + i];
-  }
-  cudaMemcpyAsync(P->h, yv.data(), m * 8, cudaMemcpyHostToDevice, s);
-  k_combine<<<gb, 256, 0, s>>>(n, m, P->V, P->h, P->phi);
+  const int m = state[2];
+  double resid = 0.0;
+  cudaMemcpyAsync(&resid, &G->resid, sizeof(double), cudaMemcpyDeviceToHost, s);
+  k_gmres_solve<<<1, 1, 0, s>>>(G);
+  k_combine<<<gb, 256, 0, s>>>(n, m, P->V, G->y, P->phi);
+  if (cudaStreamSynchronize(s) != cudaSuccess) return cuda_check(cudaGetLastError(), "GMRES");
   P->last_iters = m;
-  P->last_resid = std::fabs(e[m]) / beta;
-  if (std::fabs(e[m]) > 1e3 * tol * beta)
+  P->last_resid = resid;
+  if (resid > 1e3 * tol)
     return set_error(FC2D_ERR_NOT_CONVERGED, "GMRES did not reach its tolerance");
   return cuda_check(cudaGetLastError(), "GMRES");
 }
