@@ -499,6 +499,7 @@ def measure(fc2d, torch, w, precision, K, warmup, world, dev, fg_h, fb_h, sample
 
     e2e_ms, e2e_h2d = e2e(True)
     e2e_full_ms, e2e_full_h2d = e2e(False)
+    link = host_link(torch, dev, e2e_h2d, int(fhat.numel() * fhat.element_size()))
     # roofline of the dominant kernel
     hbm, src = peaks()
     alg = algorithmic(plan, w, fp64)
@@ -543,10 +544,52 @@ def measure(fc2d, torch, w, precision, K, warmup, world, dev, fg_h, fb_h, sample
                     "pipeline": "copy-in, compute, copy-out on three streams, two buffers",
                     "h2d_bytes_per_step": e2e_h2d,
                     "d2h_bytes_per_step": int(fhat.numel() * fhat.element_size()),
+                    "ms_per_step": e2e_ms, "host_link": link,
                     "full_grid": {"api": "fc2d_extend_coeffs (f on the whole grid)",
                                   "value": replica_throughput(world, 1, npts, e2e_full_ms),
                                   "h2d_bytes_per_step": e2e_full_h2d}},
             "fhat": fhat}
+
+
+def host_link(torch, dev, h2d_bytes, d2h_bytes, reps=10):
+    """The host link alone, with the e2e pipeline's byte counts: pinned-memory copies of
+    h2d_bytes in and d2h_bytes out, each direction alone and both at once on two
+    streams (GB/s per direction, CUDA events), and the step time those copies alone
+    would take with both directions busy."""
+    h_in = torch.empty(h2d_bytes // 8, dtype=torch.float64).pin_memory()
+    h_out = torch.empty(d2h_bytes // 8, dtype=torch.float64).pin_memory()
+    d_in = torch.empty(h_in.numel(), dtype=torch.float64, device=dev)
+    d_out = torch.empty(h_out.numel(), dtype=torch.float64, device=dev)
+    s1, s2 = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
+    cur = torch.cuda.current_stream(dev)
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(cur)
+        for _ in range(reps):
+            fn()
+        b.record(cur)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps
+
+    def both():
+        s1.wait_stream(cur)
+        s2.wait_stream(cur)
+        with torch.cuda.stream(s1):
+            d_in.copy_(h_in, non_blocking=True)
+        with torch.cuda.stream(s2):
+            h_out.copy_(d_out, non_blocking=True)
+        cur.wait_stream(s1)
+        cur.wait_stream(s2)
+
+    t_in = timed(lambda: d_in.copy_(h_in, non_blocking=True))
+    t_out = timed(lambda: h_out.copy_(d_out, non_blocking=True))
+    t_both = timed(both)
+    return {"h2d_GBs": h2d_bytes / t_in / 1e6, "d2h_GBs": d2h_bytes / t_out / 1e6,
+            "both_ms": t_both,
+            "note": "the step's copies alone, both directions at once: the e2e floor"}
 
 
 def poisson_star1024(fc2d, torch, dev, solves=3):
@@ -748,19 +791,20 @@ def _disk_eigenmode_error(fc2d, torch, dev, h=0.005, n_c=8, T_target=2.0):
             "max_abs_error": err}
 
 
-def ff_solve_kite2048(fc2d, torch, dev, n_large=2, squares=False, extras=True,
-                      double_float=False):
+def ff_solve_kite2048(fc2d, torch, dev, n_large=2, mode=1, extras=True):
     """The whole Fourier Forwarding solve (Section 4.2, eq. (4.9); fc2d_forward_wave): the
     kite at 2048^2, d = 4, c = 1, n_c = 8 (Delta T = 8 h, 64 small steps of CFL 0.125
     per large step), zero Dirichlet data, 32 initial conditions in one call (a Gaussian of
-    width 0.05 each, centres at least 0.35 inside the curve, seeds 50..81, u_t = 0), FP64.
-    One call of n_large large steps is timed between two events on the launching stream
-    after a warm-up call (the band and scratch are built there); the per-kernel times come
-    from a second, profiled call.  Beside it: the measured FP64 rate and the error of the
-    same solver against the exact Dirichlet eigenmode (2, 3) of the unit disk at t ~ 2,
-    and the same solve with the small-square procedure (interface mode 1) and with its
-    evaluation in double-float arithmetic (mode 2; there the dominant kernel's "TFLOP/s"
-    counts the FP64-equivalent DFT flops it replaces)."""
+    width 0.05 each, centres at least 0.35 inside the curve, seeds 50..81, u_t = 0), FP64,
+    with the paper's small-square interface procedure (interface mode 1).  One call of
+    n_large large steps is timed between two events on the launching stream after a
+    warm-up call (the band and scratch are built there); the per-kernel times come from a
+    second, profiled call.  Beside it: the measured FP64 rate, the error of the same
+    solver against the exact Dirichlet eigenmode (2, 3) of the unit disk at t ~ 2, and the
+    same solve with the full inverse DFT at every small step (mode 0) and with the
+    squares evaluated in double-float arithmetic (mode 2; there the dominant kernel's
+    "TFLOP/s" counts the FP64-equivalent DFT flops it replaces)."""
+    squares, double_float = mode >= 1, mode == 2
     w = W.workload("kite2048", d=4, M=7)
     g, p = w.grid, w.params
     n_c, n_f, c = 8, 32, 1.0
@@ -833,7 +877,8 @@ def ff_solve_kite2048(fc2d, torch, dev, n_large=2, squares=False, extras=True,
     eig = _disk_eigenmode_error(fc2d, torch, dev)
     return {"workload": f"kite 2048^2 (a=0.65, b=1.5), d = 4, c = 1, n_c = 8 (Delta T = 8 h), "
                         f"zero Dirichlet data, {n_f} initial conditions (one Gaussian each, "
-                        "w = 0.05, centres >= 0.35 inside, seeds 50..81), u_t = 0, FP64",
+                        "w = 0.05, centres >= 0.35 inside, seeds 50..81), u_t = 0, FP64; "
+                        "interface values by the small-square procedure (interface mode 1)",
             "n_f": n_f, "large_steps": n_large, "small_steps": small,
             "ms": ms, "ms_per_large_step": ms / n_large, "ms_per_small_step": ms / small,
             "small_steps_per_s": small / (ms * 1e-3),
@@ -849,10 +894,10 @@ def ff_solve_kite2048(fc2d, torch, dev, n_large=2, squares=False, extras=True,
                          "flops": "5 N log2 N per length-N complex DFT of the launch"},
             "fp64_peak": peak, "disk_eigenmode": eig,
             "parity": "tests/test_gpu_ff.py (element-wise against the oracle)",
-            "small_squares": ff_solve_kite2048(fc2d, torch, dev, n_large, squares=True,
-                                               extras=False),
-            "small_squares_double_float": ff_solve_kite2048(
-                fc2d, torch, dev, n_large, squares=True, extras=False, double_float=True)}
+            "full_inverse_dft": ff_solve_kite2048(fc2d, torch, dev, n_large, mode=0,
+                                                  extras=False),
+            "small_squares_double_float": ff_solve_kite2048(fc2d, torch, dev, n_large, mode=2,
+                                                            extras=False)}
 
 
 def ff_scaling(fc2d, torch, dev, n_f=8, n_c=8):
