@@ -80,6 +80,9 @@ struct Scratch {
 struct WaveState {
   std::map<std::pair<int, int>, std::unique_ptr<DevBand>> bands;  // by (n_c, interface mode)
   Scratch scr;
+  // double-float twiddles for U_FC in interface mode 2 (built on first use):
+  // w_ny^t (t < ny), w_{nx/2}^t (t < nx/2), w_nx^k (k <= nx/2), as (re hi, lo, im hi, lo)
+  float4 *df_twy = nullptr, *df_twx = nullptr, *df_rtw = nullptr;
 };
 
 template <typename T>
@@ -154,6 +157,27 @@ fc2d_status upload_squares(const fc2d_plan_s* p, DevBand& b, int n_c) {
       (st = upload(&q->tw_df, tw_df)) || (st = upload(&q->rows, rows)))
     return st;
   b.sq = std::move(q);
+  return FC2D_OK;
+}
+
+// The double-float twiddle tables of interface mode 2, from the plan's FP64 tables
+// (interleaved re, im): hi = RN(v), lo = RN(v - hi).
+fc2d_status df_tables(fc2d_plan_s* p, WaveState* W) {
+  if (W->df_twy) return FC2D_OK;
+  auto split = [](const std::vector<double>& v, size_t n) {
+    std::vector<float4> out(n);
+    for (size_t t = 0; t < n; ++t) {
+      const double re = v[2 * t], im = v[2 * t + 1];
+      const float rh = (float)re, ih = (float)im;
+      out[t] = float4{rh, (float)(re - (double)rh), ih, (float)(im - (double)ih)};
+    }
+    return out;
+  };
+  fc2d_status st;
+  if ((st = upload(&W->df_twy, split(p->fy.tw_host, (size_t)p->grid.ny))) ||
+      (st = upload(&W->df_twx, split(p->fx.tw_host, (size_t)p->grid.nx / 2))) ||
+      (st = upload(&W->df_rtw, split(p->rtw_host, (size_t)p->grid.nx / 2 + 1))))
+    return st;
   return FC2D_OK;
 }
 
@@ -721,6 +745,246 @@ __global__ void __launch_bounds__(kSqEvalThreads, 2) k_sq_eval_df(
   }
 }
 
+// ------------------------------------------------------------------------- //
+// U_FC at T_{j+1} in double-float (interface mode 2): the modal advance and the inverse
+// column DFT (k_ff_cols_df), then the inverse real rows (k_inverse_rows_df), on a
+// power-of-two Stockham transform in double-float.  Doubles enter through split_fast and
+// leave through df_to_double_fast, both on the integer and FP32 pipes.
+// ------------------------------------------------------------------------- //
+
+// x as hi + lo, hi = RN(x) and lo = RN(x - hi), for |x| in [2^-74, 2^125] (exponent e in
+// [949, 1148]) on the integer pipe: hi by rounding the 64-bit pattern at bit 29 (as
+// d2f_rn), x - hi as the integer difference of the patterns of x and of hi (in units of
+// x's ulp 2^(e-1075), |d| <= 2^28; a carry into hi's exponent keeps the difference
+// exact), converted to float and scaled by that ulp.  Zero gives (0, 0); other values
+// take the FP64 conversions.
+__device__ __forceinline__ df2 split_fast(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned h32 = (unsigned)(b >> 32), e = (h32 >> 20) & 0x7FFu;
+  if (e - 949u > 1148u - 949u) {
+    if ((b << 1) == 0ull) return {__uint_as_float(h32 & 0x80000000u), 0.f};
+    const float h = __double2float_rn(x);
+    return {h, __double2float_rn(x - (double)h)};
+  }
+  const unsigned long long u = b + 0x0FFFFFFFull + ((b >> 29) & 1ull);
+  const unsigned sign = h32 & 0x80000000u;
+  const float hi = __uint_as_float(((unsigned)(u >> 29) - (896u << 23)) | sign);
+  const long long d = (long long)(b - (u & ~0x1FFFFFFFull));  // |x| - |hi| in ulps
+  const float ulp = __uint_as_float((e - 948u) << 23);        // 2^(e - 1075)
+  const float lo = __int2float_rn((int)d) * ulp;
+  return {hi, __uint_as_float(__float_as_uint(lo) ^ sign)};
+}
+
+// hi + lo as a double: the two floats widened on the integer pipe (normal floats; zero
+// and others through the hardware conversion), one FP64 addition.
+__device__ __forceinline__ double f2d_fast(float v) {
+  const unsigned a = __float_as_uint(v), ex = (a >> 23) & 0xFFu;
+  if (ex - 1u > 253u) return (double)v;  // zero, subnormal, inf, NaN
+  const unsigned long long bits = ((unsigned long long)(a & 0x80000000u) << 32) |
+                                  ((unsigned long long)(ex + 896u) << 52) |
+                                  ((unsigned long long)(a & 0x7FFFFFu) << 29);
+  return __longlong_as_double((long long)bits);
+}
+__device__ __forceinline__ double df_to_double_fast(df2 a) { return f2d_fast(a.hi) + f2d_fast(a.lo); }
+
+// length-R DFT in registers for the Stockham stages (R = 8, 4, 2)
+template <int R> __device__ __forceinline__ void dft_df(dfc* v) {
+  if constexpr (R == 8) {
+    dfc w[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) w[i] = v[i];
+    dft8_df(w);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) v[i] = w[i];
+  } else if constexpr (R == 4) {
+    const dfc t0 = dfc_add(v[0], v[2]), t1 = dfc_sub(v[0], v[2]), t2 = dfc_add(v[1], v[3]);
+    const dfc t3 = dfc_mul_mi(dfc_sub(v[1], v[3]));
+    v[0] = dfc_add(t0, t2);
+    v[2] = dfc_sub(t0, t2);
+    v[1] = dfc_add(t1, t3);
+    v[3] = dfc_sub(t1, t3);
+  } else {
+    const dfc a = v[0], b = v[1];
+    v[0] = dfc_add(a, b);
+    v[1] = dfc_sub(a, b);
+  }
+}
+
+// One Stockham stage of radix R over N = 2^LOGN values in padded shared memory (index
+// sq_pad), NS the product of the earlier radices: the N/R butterflies j go to the N/8
+// threads, 8/R each; inputs x[j + r N/R], twiddles w_N^(r k N/(NS R)) with k = j mod NS
+// (tw[t] = w_N^t), outputs at (j/NS) NS R + k + r NS.  Reads, barrier, writes, barrier.
+template <int LOGN, int R, int NS>
+__device__ __forceinline__ void stage_df(float4* buf, int t, const float4* __restrict__ tw) {
+  constexpr int N = 1 << LOGN, NT = N / 8, M = 8 / R, NR = N / R;
+  dfc v[8];
+#pragma unroll
+  for (int mm = 0; mm < M; ++mm) {
+    const int j = t + mm * NT;
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[mm * R + r] = dfc_load(buf[sq_pad(j + r * NR)]);
+  }
+  __syncthreads();
+#pragma unroll
+  for (int mm = 0; mm < M; ++mm) {
+    const int j = t + mm * NT;
+    const int k = j & (NS - 1);
+    if constexpr (NS > 1) {
+#pragma unroll
+      for (int r = 1; r < R; ++r)
+        v[mm * R + r] = dfc_mul(v[mm * R + r], dfc_load(__ldg(tw + r * k * (N / (NS * R)))));
+    }
+    dft_df<R>(v + mm * R);
+    const int base = (j / NS) * NS * R + k;
+#pragma unroll
+    for (int r = 0; r < R; ++r) buf[sq_pad(base + r * NS)] = dfc_store(v[mm * R + r]);
+  }
+  __syncthreads();
+}
+
+// Forward DFT of N = 2^LOGN padded values by N/8 threads (radix 8, the last stage 4 or 2)
+template <int LOGN, int NS = 1>
+__device__ __forceinline__ void fft_df(float4* buf, int t, const float4* __restrict__ tw) {
+  constexpr int N = 1 << LOGN;
+  if constexpr (NS < N) {
+    constexpr int R = N / NS >= 8 ? 8 : N / NS;
+    stage_df<LOGN, R, NS>(buf, t, tw);
+    fft_df<LOGN, NS * R>(buf, t, tw);
+  }
+}
+
+// k_ff_cols_p2 in double-float: the time factors (FP64, split), the FP64 half spectra
+// split on load, the advance a = F t0 + G t1 conjugated into shared memory, the forward
+// transform (the inverse of the conjugate), the conjugate of the result to the
+// intermediate as double-float pairs (float4).  Block (column, output) of N/8 threads.
+template <int LOGNY>
+__global__ void __launch_bounds__((1 << LOGNY) / 8)
+    k_ff_cols_df(FftArgs fa, int n_f, const double2* __restrict__ spec, float4* __restrict__ out,
+                 double c, double tau, double Lx, double Ly, const float4* __restrict__ tw) {
+  constexpr int N = 1 << LOGNY;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float4* tab = reinterpret_cast<float4*>(smem_raw);
+  float4* buf = tab + N;
+  const int nxh = fa.nx / 2 + 1, kx = blockIdx.x, which = blockIdx.y, tid = threadIdx.x;
+  const double two_pi = 6.283185307179586476925286766559;
+  for (int ky = tid; ky < N; ky += blockDim.x) {
+    const int m = ky <= N / 2 ? ky : ky - N;
+    const double fl = kx / Lx, fm = m / Ly;
+    const double w = two_pi * c * sqrt(fl * fl + fm * fm);
+    double t0, t1;
+    if (w == 0.0) {
+      t0 = which ? 0.0 : 1.0;
+      t1 = which ? 1.0 : tau;
+    } else {
+      double sn, co;
+      sincos(w * tau, &sn, &co);
+      t0 = which ? -w * sn : co;
+      t1 = which ? co : sn / w;
+    }
+    tab[ky] = split_df(double2{t0, t1});
+  }
+  for (int f = 0; f < n_f; ++f) {
+    const double2* colF = spec + (size_t)f * N * nxh + kx;
+    const double2* colG = spec + (size_t)(n_f + f) * N * nxh + kx;
+    __syncthreads();  // the table is ready; the previous function's stores are done
+    for (int ky = tid; ky < N; ky += blockDim.x) {
+      const dfc t = dfc_load(tab[ky]);  // re: t0, im: t1
+      const double2 F = colF[(size_t)ky * nxh], G = colG[(size_t)ky * nxh];
+      const df2 fr = split_fast(F.x), fi = split_fast(F.y);
+      const df2 gr = split_fast(G.x), gi = split_fast(G.y);
+      const df2 ar = df_add(df_mul(fr, t.re), df_mul(gr, t.im));
+      const df2 ai = df_add(df_mul(fi, t.re), df_mul(gi, t.im));
+      buf[sq_pad(ky)] = dfc_store(dfc{ar, df_neg(ai)});
+    }
+    __syncthreads();
+    fft_df<LOGNY>(buf, tid, tw);
+    float4* dst = out + ((size_t)which * n_f + f) * N * fa.pitch + kx;
+    for (int y = tid; y < N; y += blockDim.x) {
+      const dfc r = dfc_load(buf[sq_pad(y)]);
+      dst[(size_t)y * fa.pitch] = dfc_store(dfc{r.re, df_neg(r.im)});
+    }
+  }
+}
+
+// k_inverse_rows_p2 in double-float (no quadratic term): Z_k = S_k + i conj(w^k) D_k from
+// X_k and conj(X_{NH-k}) (double-float intermediate rows), the forward transform of
+// conj(Z), x_{2m} + i x_{2m+1} = conj of its result, written as doubles.
+template <int LOGNH>
+__global__ void __launch_bounds__((1 << LOGNH) / 8)
+    k_inverse_rows_df(FftArgs fa, const float4* __restrict__ inter, double* __restrict__ up,
+                      const float4* __restrict__ rtw, const float4* __restrict__ tw) {
+  constexpr int NH = 1 << LOGNH;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float4* buf = reinterpret_cast<float4*>(smem_raw);
+  const int j = blockIdx.x, f = blockIdx.y, t = threadIdx.x;
+  const float4* row = inter + ((size_t)f * fa.ny + j) * fa.pitch;
+  for (int k = t; k < NH; k += blockDim.x) {
+    const dfc bk = dfc_load(row[k]);
+    dfc bc = dfc_load(row[NH - k]);
+    bc.im = df_neg(bc.im);  // conj X_{NH-k}
+    const dfc sm = dfc_add(bk, bc), d = dfc_sub(bk, bc);
+    dfc w = dfc_load(__ldg(rtw + k));
+    w.im = df_neg(w.im);    // conj(w^k)
+    const dfc dw = dfc_mul(d, w);
+    buf[sq_pad(k)] = dfc_store(dfc{df_sub(sm.re, dw.im), df_neg(df_add(sm.im, dw.re))});
+  }
+  __syncthreads();
+  fft_df<LOGNH>(buf, t, tw);
+  double* o = up + ((size_t)f * fa.ny + j) * (2 * NH);
+  for (int m = t; m < NH; m += blockDim.x) {
+    const dfc z = dfc_load(buf[sq_pad(m)]);
+    o[2 * m] = df_to_double_fast(z.re);
+    o[2 * m + 1] = -df_to_double_fast(z.im);
+  }
+}
+
+// The U_FC evaluation at tau in double-float for power-of-two grids (ny = 2^9..2^12,
+// nx = 2^9..2^12); false (nothing launched) otherwise.
+template <int LOGNY>
+static void ff_cols_df_launch(const FftArgs& fa, int n_f, int n_out, const double2* spec,
+                              float4* out, double c, double tau, double Lx, double Ly,
+                              const float4* tw, cudaStream_t s) {
+  const size_t sm = ((size_t)(1 << LOGNY) + (1 << LOGNY) + (1 << LOGNY) / 8) * sizeof(float4);
+  cudaFuncSetAttribute(k_ff_cols_df<LOGNY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  k_ff_cols_df<LOGNY><<<dim3(fa.nx / 2 + 1, n_out), (1 << LOGNY) / 8, sm, s>>>(
+      fa, n_f, spec, out, c, tau, Lx, Ly, tw);
+}
+template <int LOGNH>
+static void inverse_rows_df_launch(const FftArgs& fa, int n_f, const float4* inter, double* up,
+                                   const float4* rtw, const float4* tw, cudaStream_t s) {
+  const size_t sm = ((size_t)(1 << LOGNH) + (1 << LOGNH) / 8) * sizeof(float4);
+  cudaFuncSetAttribute(k_inverse_rows_df<LOGNH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  k_inverse_rows_df<LOGNH><<<dim3(fa.ny, n_f), (1 << LOGNH) / 8, sm, s>>>(fa, inter, up, rtw, tw);
+}
+bool df_sizes_ok(int nx, int ny) {
+  auto p2 = [](int v, int lo, int hi) {
+    for (int l = lo; l <= hi; ++l)
+      if (v == (1 << l)) return true;
+    return false;
+  };
+  return p2(ny, 9, 12) && p2(nx / 2, 8, 11) && nx % 2 == 0;
+}
+bool ff_cols_df(const FftArgs& fa, int n_f, int n_out, const double2* spec, float4* out, double c,
+                double tau, double Lx, double Ly, const float4* tw, cudaStream_t s) {
+  switch (fa.ny) {
+    case 512: ff_cols_df_launch<9>(fa, n_f, n_out, spec, out, c, tau, Lx, Ly, tw, s); return true;
+    case 1024: ff_cols_df_launch<10>(fa, n_f, n_out, spec, out, c, tau, Lx, Ly, tw, s); return true;
+    case 2048: ff_cols_df_launch<11>(fa, n_f, n_out, spec, out, c, tau, Lx, Ly, tw, s); return true;
+    case 4096: ff_cols_df_launch<12>(fa, n_f, n_out, spec, out, c, tau, Lx, Ly, tw, s); return true;
+    default: return false;
+  }
+}
+bool inverse_rows_df(const FftArgs& fa, int n_f, const float4* inter, double* up, const float4* rtw,
+                     const float4* tw, cudaStream_t s) {
+  switch (fa.nx / 2) {
+    case 256: inverse_rows_df_launch<8>(fa, n_f, inter, up, rtw, tw, s); return true;
+    case 512: inverse_rows_df_launch<9>(fa, n_f, inter, up, rtw, tw, s); return true;
+    case 1024: inverse_rows_df_launch<10>(fa, n_f, inter, up, rtw, tw, s); return true;
+    case 2048: inverse_rows_df_launch<11>(fa, n_f, inter, up, rtw, tw, s); return true;
+    default: return false;
+  }
+}
+
 // The box's time factors for the small steps s = 0..S-1: tab[s][l][m] =
 // (cos w tau, sin(w tau)/w) at tau = s dt ((1, tau) at w = 0), w = 2 pi c |k| / (P h).
 template <bool DF>
@@ -769,6 +1033,9 @@ void wave_destroy(fc2d_plan_s* p) {
     }
   }
   cudaFree(W->scr.base);
+  cudaFree(W->df_twy);
+  cudaFree(W->df_twx);
+  cudaFree(W->df_rtw);
   delete W;
   p->wave = nullptr;
 }
@@ -935,6 +1202,19 @@ extern "C" fc2d_status fc2d_forward_wave(fc2d_plan_t p, int n_f, double c, int n
   const double Lx = nx * h, Ly = ny * h;
   const size_t smc = 3 * (size_t)ny * sizeof(double2);
   cudaFuncSetAttribute(k_ff_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smc);
+  // interface mode 2 on power-of-two grids: U_FC at T_{j+1} in double-float too
+  const bool df_ufc = df && df_sizes_ok(nx, ny);
+  if (df_ufc && (st = df_tables(p, W))) return st;
+  auto eval_ufc_df = [&](double tau, double* out_u, double* out_ut) {
+    float4* interf = reinterpret_cast<float4*>(inter);
+    {
+      ProfScope ps(p, "ff_cols", s);
+      ff_cols_df(fa, n_f, 2, spec, interf, c, tau, Lx, Ly, W->df_twy, s);
+    }
+    ProfScope ps(p, "inverse_rows", s);
+    inverse_rows_df(fa, n_f, interf, out_u, W->df_rtw, W->df_twx, s);
+    inverse_rows_df(fa, n_f, interf + (size_t)n_f * ny * pitch, out_ut, W->df_rtw, W->df_twx, s);
+  };
   auto eval_ufc = [&](double tau, int n_out, double* out_u, double* out_ut) {
     {
       ProfScope ps(p, "ff_cols", s);
@@ -1003,7 +1283,8 @@ extern "C" fc2d_status fc2d_forward_wave(fc2d_plan_t p, int n_f, double c, int n
     }
     // T_{j+1}: U_FC and its time derivative on the grid (into u, ut), then U_B's time
     // derivative from one further step and the merge of eq. (4.9)
-    eval_ufc(dT, 2, u, ut);
+    if (df_ufc) eval_ufc_df(dT, u, ut);
+    else eval_ufc(dT, 2, u, ut);
     const int64_t mN = m0 + S;
     ub_step(2, ub[i_cur], ub[i_prev], nullptr, u, ufc[1 - f_cur], gat(mN), ub[i_ut]);
     const int64_t n_near = (int64_t)b->host.near_lin.size();

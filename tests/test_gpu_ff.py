@@ -38,7 +38,10 @@ TOL_EXT = 3e-11
 # operation ~2^-44 of its operands; a 64 x 64 transform and the advance chain ~20 of them
 # per output, given a factor 3 of margin: 64 2^-44).  U_B's stable steps add the
 # errors of the S n_large evaluations without amplifying them, so u moves by at most
-# S n_large EPS_DF |u|, and u_t, a centred difference over 2 dt, by that over dt.
+# S n_large EPS_DF |u|, and u_t, a centred difference over 2 dt, by that over dt.  On
+# power-of-two grids mode 2 also evaluates U_FC at T_{j+1} in double-float: EPS_DF |u|
+# per large step for u and EPS_DF w_max |u| for u_t, inside those terms (S > 1, and
+# S / dt exceeds w_max on every grid tested).
 EPS_DF = 64 * 2.0 ** -44
 
 
@@ -48,6 +51,8 @@ def df_bars(double_float, S, n_large, dt, size):
         return 0.0, 0.0
     e = S * n_large * EPS_DF * size
     return e, e / dt
+
+
 CASES = [("disk64", 4), ("kite160x144", 6), ("star200", 8)]
 
 
@@ -380,3 +385,36 @@ def test_full_size_small_squares_solve(torch_cuda, double_float):
         du, dut = df_bars(double_float, S, 1, n_c * g.h / S, np.abs(U0[k]).max() + T * mut)
         assert np.abs(got_u[k][ins] - ref_u[ins]).max() < TOL_EXT * (mu + T * mut) + du, k
         assert np.abs(got_ut[k][ins] - ref_ut[ins]).max() < TOL_EXT * (w_max * mu + mut) + dut, k
+
+
+def test_double_float_mode_against_fp64_squares(torch_cuda):
+    """Interface mode 2 on a power-of-two grid (the squares' evaluation and U_FC at
+    T_{j+1} in double-float) against mode 1 (FP64) on the same inputs: kite 1024^2,
+    n_c = 8, four functions, two large steps; u and u_t inside the domain within the
+    double-float bar (df_bars, which holds the U_FC evaluation's ~2^-44 |u| too)."""
+    torch = torch_cuda
+    from paper_2010_03901_gb300 import fc2d
+    w = W.workload("kite1024", d=4, M=7)
+    g, p = w.grid, w.params
+    n_c, n_f, n_large = 8, 4, 2
+    plan = fc2d.fc2d_plan(w.boundary.arrays(), (g.a0, g.b0, g.h, g.nx, g.ny),
+                          dict(d=4, M=7, B=p.B, k1=p.k1))
+    fs = [W.gaussian_sum(w.boundary, 1, 90 + k, wmin=0.05, wmax=0.05, margin=0.35)
+          for k in range(n_f)]
+    U0 = torch.tensor(np.stack([W.grid_values(w, f) for f in fs]), device="cuda:0")
+    out = []
+    for df in (False, True):
+        u, ut = U0.clone(), torch.zeros_like(U0)
+        plan.fc2d_forward_wave(n_f, 1.0, n_c, n_large, u, ut, squares=True, double_float=df)
+        plan.fc2d_sync_status()
+        out.append((u.cpu().numpy(), ut.cpu().numpy()))
+    ins = OG.build_geometry(w).inside
+    S = 8 * n_c
+    T = n_large * n_c * g.h
+    for k in range(n_f):
+        (u1, t1), (u2, t2) = (out[0][0][k], out[0][1][k]), (out[1][0][k], out[1][1][k])
+        size = float(U0[k].abs().max()) + T * np.abs(t1[ins]).max()
+        du, dut = df_bars(True, S, n_large, n_c * g.h / S, size)
+        assert np.abs(u2[ins] - u1[ins]).max() < du, k
+        assert np.abs(t2[ins] - t1[ins]).max() < dut, k
+        assert np.array_equal(u2[~ins], u1[~ins])
