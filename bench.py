@@ -54,8 +54,9 @@ ROT = 3   # rotating input/output buffers of the timed steps
 KERNELS_PER_SCOPE = {("mixed", "fft_cols", 4096): 2}
 
 MEASURED_TRAFFIC = {
-    ("mixed", "fft_rows_fused"): 70907136 + 9798144,
-    ("mixed", "gather_blend_interp_tc"): 34111232 + 256,
+    ("mixed", "fft_rows_fused"): 70898688 + 8000768,
+    ("mixed", "gather_blend_interp_tc"): 34114048 + 0,
+    ("mixed", "fft_cols"): (67674624 + 7534592) + (67655168 + 6790400),
     ("fp64", "fft_rows_fused"): 72354816 + 72103424,
     ("fp64", "fft_cols"): 141867520 + 92843264,
     ("fp64", "gather_blend"): 9670144 + 9472,
