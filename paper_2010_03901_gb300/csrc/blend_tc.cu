@@ -38,7 +38,6 @@ constexpr int kTileN = 128;           // normals per CTA (MMA M)
 constexpr int kMaxCrPad = 256;        // MMA N limit
 constexpr int kTmemCols = 256;        // power of two >= N
 constexpr uint32_t kSpinLimit = 1u << 22;
-constexpr int kStageBytes = kTileN * (kMaxCrPad + 1) * 4;  // fused kernel's output staging
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
