@@ -23,10 +23,9 @@
 // again, frees its TMEM and returns.
 #include <cuda_runtime.h>
 
-#include <cstring>
-
 #include <algorithm>
 #include <cstdint>
+#include <cstring>
 
 #include "fc2d_kernels.cuh"
 #include "interp.cuh"
@@ -43,8 +42,8 @@ __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
 }
 
-// Bounded wait for phase 0 of the mbarrier at shared address mbar (the MMAs' commit
-// arrives on it): at most `limit` polls.  If they run out, thread 0 latches
+// Bounded wait for the phase of parity `parity` (0 for the first use) of the mbarrier at
+// shared address mbar (the MMAs' commit arrives on it): at most `limit` polls.  If they run out, thread 0 latches
 // FC2D_ERR_TIMEOUT in *status and the wait is given `limit` polls once more, since
 // MMAs still in flight must end before their TMEM is freed.  True once the phase
 // completed.
