@@ -439,6 +439,19 @@ def measure(fc2d, torch, w, precision, K, warmup, world, dev, fg_h, fb_h, sample
     ms_prof = max_over_ranks(ms_prof_raw, world, dev)
     npts = g.nx * g.ny
     value = replica_throughput(world, K, npts, ms)
+    # the column passes' TMA-pipelined form, set by hand (the tuner keeps the direct
+    # form): the same K steps back to back, then the tuned shape is restored
+    cols_tma = None
+    if not fp64 and g.ny == 4096:
+        tuned = plan.fc2d_tuning()
+        cols_tma = {}
+        for width in (16, 32):
+            plan.fc2d_tuning_set(width, "tma")
+            for k in range(3):
+                plan.fc2d_extend_coeffs(1, fgs[k % ROT], fb, fhats[k % ROT], stream)
+            cols_tma[f"tma{width}_ms_per_step"] = max_over_ranks(timed_region()[0], world,
+                                                                 dev) / K
+        plan.fc2d_tuning_set(tuned[1], tuned[0])
     # end to end through the public API with host buffers: every step copies its
     # inputs from pinned host memory, calls the library and reads its spectrum back to
     # pinned host memory.  Steps are pipelined as a user streaming functions would:
@@ -519,19 +532,25 @@ def measure(fc2d, torch, w, precision, K, warmup, world, dev, fg_h, fb_h, sample
                 "unit": "GB/s", "peak_source": src}
     roof["frac"] = roof["achieved"] / roof["peak"]
     roof["kernel"] = dom
-    roof["traffic"] = MEASURED_TRAFFIC.get((precision, dom))
+    # the column passes' stored traffic is per form (direct or TMA-pipelined)
+    tk = (precision, dom) + (("tma",) if dom == "fft_cols" and
+                             plan.fc2d_tuning()[0] == "tma" else ())
+    roof["traffic"] = MEASURED_TRAFFIC.get(tk)
     roof["traffic_source"] = ("stored: one ncu capture (dram__bytes_read.sum + "
                               "dram__bytes_write.sum, cold cache) of this kernel on this "
                               "workload, not measured in this run" if roof["traffic"] else
                               "no capture of the current kernel")
     kernels = {k: {"launches": v[0], "avg_us": 1e3 * v[1] / v[0],
                    "share": v[1] / sum(x[1] for x in prof.values())} for k, v in prof.items()}
-    cc, cc_us = plan.fc2d_tuning()
+    cform, cc, cc_us = plan.fc2d_tuning()
     return {"value": value, "ms_per_step": ms / K, "steps": K, "plan_s": plan_s,
-            "tuning": {"cols4k_columns_per_block": cc,
-                       "candidates_us": dict(zip(("16", "32", "64"), cc_us)),
-                       "how": "plan-time autotuner: each width timed on a scratch "
-                              "intermediate of this grid, fastest kept (same values)"},
+            "tuning": {"cols4k_form": cform, "cols4k_columns_per_block": cc,
+                       "candidates_us": {f"{f}{c}": v for (f, c), v in cc_us.items()
+                                         if f == "direct"},
+                       "how": "plan-time autotuner: the direct form at 16/32/64 columns, "
+                              "each timed on a scratch intermediate of this grid, fastest "
+                              "kept (same values)",
+                       "tma_form_in_step": cols_tma},
             "l2_flushed": {"value": replica_throughput(world, K, npts, ms_fl),
                            "ms_per_step": ms_fl / K,
                            "note": "L2 flushed before each step (256 MB read, outside "

@@ -322,15 +322,24 @@ fc2d_status fc2d_wave_ub_step(fc2d_plan_t plan, int n_c, int n_f, int mode, doub
                               const double* grid_prev_dev, const double* g_dev, double* out_dev,
                               void* stream);
 
-/* Launch shapes the plan chose by timing (no operation of the paper; each candidate
- * computes the same values bit for bit): choice[0] = columns per block of the mixed
- * form's 4096-point column DFT passes (16, 32 or 64), chosen at plan time as the fastest
- * of the three on a scratch intermediate of the plan's grid; us (NULL allowed) receives
- * the three candidates' times in microseconds per call (zeros when the plan has no such
- * transform, which keeps 16). */
+/* Launch shapes of the plan (no operation of the paper; each choice computes the same
+ * values bit for bit).  The mixed form's 4096-point column DFT passes run in one of two
+ * forms: direct (a block per tile of 64 rows x 16, 32 or 64 columns, loads straight into
+ * registers) or TMA-pipelined (persistent blocks of 16 or 32 columns per tile, each
+ * keeping the next tiles in flight through tensor-map copies into shared memory, every
+ * wait bounded).  choice[2]: choice[0] = columns per block, choice[1] = form (0 direct,
+ * 1 TMA-pipelined).  At plan time the direct form's three widths are timed on a scratch
+ * intermediate of the plan's grid and the fastest kept; the TMA form is used only when
+ * set (timed alone it ties with the direct form, inside the extension step it is slower
+ * on GB300).  us[5] (NULL allowed) receives the times in microseconds per call of direct
+ * 16, 32, 64, then 0, 0 for TMA 16, 32 (not timed); all zeros when the plan has no such
+ * transform, which keeps {16, 0}.  Where the TMA form cannot run (an intermediate not
+ * 16-byte aligned, no tensor-map encoder in the driver), the direct form with the same
+ * width runs instead. */
 fc2d_status fc2d_tuning(fc2d_plan_t plan, int32_t* choice, float* us);
-/* Override the choice (choice[0] in {16, 32, 64}; FC2D_ERR_ARG otherwise), for tests and
- * for callers that fix the launch shape; calls after it use the new width. */
+/* Set the choice (choice[2]: columns 16, 32 or 64 with form 0, 16 or 32 with form 1;
+ * FC2D_ERR_ARG otherwise), for tests and for callers that fix the launch shape; calls
+ * after it use the new shape. */
 fc2d_status fc2d_tuning_set(fc2d_plan_t plan, const int32_t* choice);
 
 /* FP64 throughput probe (no operation of the paper): `blocks` blocks of 256 threads on

@@ -146,6 +146,8 @@ FftArgs fft_args(fc2d_plan_s* p) {
   a.tsy = f64 ? (const void*)p->fy.tws64 : (const void*)p->fy.tws32;
   a.scale = 1.0 / ((double)p->grid.nx * p->grid.ny);
   a.cc4k = p->tune_cc4k;
+  a.cols_tma = p->tune_tma;
+  a.status = p->dev.status;
   return a;
 }
 
@@ -607,32 +609,41 @@ extern "C" fc2d_status fc2d_poisson(fc2d_plan_t p, int n_f, const double* fg, co
 // Fourier Forwarding interior propagator (Section 4.2)
 // ------------------------------------------------------------------------- //
 namespace fc2d {
-fc2d_status tune_cols4k(FftArgs fa, int* best, float* us);
+fc2d_status tune_cols4k(FftArgs fa, int* best, int* tma, float* us);
 
 // Plan-time autotuning: the mixed form's 4096-point column passes take the block width
-// (16, 32 or 64 columns) that runs fastest on this GPU for the plan's grid.
+// of the direct form (16, 32 or 64 columns) that runs fastest on this GPU for the plan's
+// grid.
 fc2d_status tune_plan(fc2d_plan_s* p) {
   if (p->prm.precision != FC2D_MIXED || p->grid.ny != 4096) return FC2D_OK;
-  int best = 16;
-  fc2d_status st = tune_cols4k(fft_args(p), &best, p->tune_us);
-  if (st == FC2D_OK) p->tune_cc4k = best;
+  int best = 16, tma = 0;
+  fc2d_status st = tune_cols4k(fft_args(p), &best, &tma, p->tune_us);
+  if (st == FC2D_OK) {
+    p->tune_cc4k = best;
+    p->tune_tma = tma;
+  }
   return st;
 }
 }  // namespace fc2d
 
 extern "C" fc2d_status fc2d_tuning_set(fc2d_plan_t p, const int32_t* choice) {
   if (!p || !choice) return set_error(FC2D_ERR_ARG, "fc2d_tuning_set: null argument");
-  if (choice[0] != 16 && choice[0] != 32 && choice[0] != 64)
-    return set_error(FC2D_ERR_ARG, "fc2d_tuning_set: columns per block 16, 32 or 64");
+  if (choice[1] != 0 && choice[1] != 1)
+    return set_error(FC2D_ERR_ARG, "fc2d_tuning_set: form 0 (direct) or 1 (TMA-pipelined)");
+  if (choice[0] != 16 && choice[0] != 32 && (choice[0] != 64 || choice[1] == 1))
+    return set_error(FC2D_ERR_ARG,
+                     "fc2d_tuning_set: columns per block 16, 32 or 64 (direct), 16 or 32 (TMA)");
   p->tune_cc4k = choice[0];
+  p->tune_tma = choice[1];
   return FC2D_OK;
 }
 
 extern "C" fc2d_status fc2d_tuning(fc2d_plan_t p, int32_t* choice, float* us) {
   if (!p || !choice) return set_error(FC2D_ERR_ARG, "fc2d_tuning: null argument");
   choice[0] = p->tune_cc4k;
+  choice[1] = p->tune_tma;
   if (us)
-    for (int k = 0; k < 3; ++k) us[k] = p->tune_us[k];
+    for (int k = 0; k < 5; ++k) us[k] = p->tune_us[k];
   return FC2D_OK;
 }
 

@@ -159,6 +159,8 @@ struct FftArgs {
   const void* tsy;            // per-stage twiddles of the column transform
   double scale;               // 1/(nx ny)
   int cc4k;                   // columns per block of the 4096-point FP32 column passes
+  int cols_tma;               // 1: those passes in the TMA-pipelined persistent form
+  int* status;                // device status word (bounded waits record a timeout)
 };
 
 // rows: mode 0 reads an extended grid (ext, type T); mode 1 assembles the extension

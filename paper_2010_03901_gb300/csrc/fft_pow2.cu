@@ -14,9 +14,11 @@
 // transform, the even/odd split to X_k, k = 0..nx/2, written to the intermediate.
 // k_fft_cols_p2: one block per (CB columns, function): length-ny column transforms,
 // scaled by 1/(nx ny), written to the half spectrum [ny][nx/2+1].
+#include <cuda.h>  // CUtensorMap and its enums (the encoder is reached through the runtime)
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <mutex>
 
 #include "fc2d_kernels.cuh"
 #include "plan_internal.h"
@@ -998,8 +1000,298 @@ static void cols4k_launch_cc(const FftArgs& fa, int n_f, void* inter, void* fhat
   launch_pdl(k_cols4k_b<CC>, grid, dim3(8 * CC), 0, s, fa, drop, (float2*)inter, (float2*)fhat);
 }
 
+// ------------------------------------------------------------------------- //
+// The same two 4096-point passes with TMA-pipelined loads.  Persistent blocks (as many
+// as fit on the GPU) take the tiles t = blockIdx.x + k gridDim.x, a tile being the
+// 64 rows x CC columns one direct-form block reads, in that form's block order (column
+// block fastest, then j2 or m1, then the function).  Thread 0 keeps the next tiles in
+// flight: each is one tensor-map copy (cp.async.bulk.tensor) into one of S shared-memory
+// stages, completing on that stage's mbarrier with the tile's byte count.  The block
+// reads a stage once its barrier's phase completes.  The transform's exchange runs in
+// place in the stage: thread (c, l) reads the rows l + 8 i of its column and writes its
+// exchange values to the rows 8 m + l, the same rows, so no other thread's input is
+// overwritten and no barrier is needed before the writes; after the block's barrier
+// each thread reads the rows 8 l .. 8 l + 7.  That barrier also tells thread 0 that
+// every thread has finished with the previous tile's stage, which it refills with the
+// tile S - 1 further on.  One barrier per tile, no exchange buffer: S tiles of shared
+// memory per block, so 1024 threads fit on an SM with S - 1 tiles in flight per block
+// during the transforms, and the loads no longer wait in the computing warps'
+// registers.  Each thread holds the same values as in the direct form and runs the same
+// arithmetic (dft64_cols's steps), so both forms give the same results bit for bit; the
+// stores, their L2 policies and pass B's L2 discard are the direct form's.  The
+// generic-proxy writes of the exchange are ordered before the copy that later refills
+// their stage by a proxy fence in each writing thread and the block's barrier.
+//
+// Tensor maps (8-byte elements, zero fill past the last column): pass A views one
+// function's slab as [f][j1][j2][kx] (extents n_f, 64, 64, nx/2+1; a box of CC x 1 x 64 x 1
+// lands as [j1][c]); pass B as [f][row][kx] (extents n_f, 4096, nx/2+1; a box of
+// CC x 64 x 1 lands as [row][c]).  The host builds them only when the intermediate is
+// 16-byte aligned and its pitch a multiple of 16 bytes (the encoder checks both again).
+//
+// Every wait is bounded: a stage whose copy has not landed after kTileSpin polls sets
+// FC2D_ERR_TIMEOUT in the status word; the block then agrees at its barrier to stop,
+// thread 0 waits (bounded again) for the copies it issued, and the block returns.
+// ------------------------------------------------------------------------- //
+constexpr uint32_t kTileSpin = 1u << 22;
+
+__device__ __forceinline__ uint32_t sm_addr(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ bool stage_ready(uint32_t mbar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(ok) : "r"(mbar), "r"(parity) : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ bool stage_wait(uint32_t mbar, uint32_t parity, int* status) {
+  for (uint32_t it = 0; it < kTileSpin; ++it)
+    if (stage_ready(mbar, parity)) return true;
+  if (status) atomicExch(status, (int)FC2D_ERR_TIMEOUT);
+  return false;
+}
+
+// thread 0: tile k of this block into stage k % S, completing on that stage's barrier
+template <int PASS, int CC, int S>
+__device__ __forceinline__ void tile_issue(const CUtensorMap* tm, int k, int ncb,
+                                           float2* stage, uint64_t* full) {
+  const int t = blockIdx.x + k * gridDim.x;
+  const int cb = t % ncb, r = (t / ncb) & 63, f = t / (ncb * 64);
+  const uint32_t mb = sm_addr(full + k % S), dst = sm_addr(stage + (k % S) * (64 * CC));
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
+               ::"r"(mb), "r"((uint32_t)(64 * CC * sizeof(float2))) : "memory");
+  const uint64_t map = reinterpret_cast<uint64_t>(tm);
+  if constexpr (PASS == 0)
+    asm volatile(
+        "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4, %5}], [%6];"
+        ::"r"(dst), "l"(map), "r"(cb * CC), "r"(r), "r"(0), "r"(f), "r"(mb) : "memory");
+  else
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4}], [%5];"
+        ::"r"(dst), "l"(map), "r"(cb * CC), "r"(64 * r), "r"(f), "r"(mb) : "memory");
+}
+
+template <int CC, int S>
+constexpr size_t cols_tma_smem() {
+  return 128 + (size_t)S * 64 * CC * sizeof(float2) + S * sizeof(uint64_t);
+}
+
+// (resident blocks: S = 3 tiles of shared memory allow eight blocks of 16 columns or
+// four of 32 per SM, 1024 threads either way, which leaves each thread 64 registers)
+template <int PASS, int CC, int S>
+__global__ void __launch_bounds__(8 * CC, 128 / CC)
+    k_cols4k_tma(const __grid_constant__ CUtensorMap tm, FftArgs fa, int n_f, int drop,
+                 float2* __restrict__ inter, float2* __restrict__ fhat) {
+  constexpr int TILE = 64 * CC;
+  extern __shared__ __align__(128) unsigned char smem_tma[];
+  // the stages start on a 128-byte boundary (the copies' destination alignment), which
+  // the launch's 128 extra bytes allow whatever the base
+  unsigned char* base = smem_tma + ((128u - (sm_addr(smem_tma) & 127u)) & 127u);
+  float2* stage = reinterpret_cast<float2*>(base);                     // [S][64][CC]
+  uint64_t* full = reinterpret_cast<uint64_t*>(stage + S * TILE);      // [S]
+  const int tid = threadIdx.x, c = tid & (CC - 1), l = tid / CC;
+  const int ncol = fa.nx / 2 + 1, ncb = (ncol + CC - 1) / CC;
+  const int n_tiles = ncb * 64 * n_f;
+  const int n_my = (int)blockIdx.x < n_tiles
+                       ? (n_tiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+  const float2* w = reinterpret_cast<const float2*>(fa.twy);
+  if (tid == 0) {
+    for (int q = 0; q < S; ++q)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(sm_addr(full + q)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  pdl_wait();
+  pdl_trigger();
+  if (tid == 0)
+    for (int k = 0; k < S && k < n_my; ++k) tile_issue<PASS, CC, S>(&tm, k, ncb, stage, full);
+  const uint64_t pol = PASS == 0 ? l2_keep() : l2_drop();
+  for (int k = 0; k < n_my; ++k) {
+    const int t = blockIdx.x + k * gridDim.x;
+    const int cb = t % ncb, r = (t / ncb) & 63, f = t / (ncb * 64);
+    const int kx = cb * CC + c;
+    const bool ok = stage_wait(sm_addr(full + k % S), (uint32_t)(k / S) & 1u, fa.status);
+    float2* st = stage + (k % S) * TILE;
+    float2 a[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) a[i] = st[(l + 8 * i) * CC + c];
+    // dft64_cols's steps, the exchange in place (rows 8 m + l: this thread's own rows)
+    dft<float, float2, 8>(a);
+#pragma unroll
+    for (int m = 1; m < 8; ++m) a[m] = mul(a[m], __ldg(w + (l * m) * 64));  // l m <= 49
+#pragma unroll
+    for (int m = 0; m < 8; ++m) st[(m * 8 + l) * CC + c] = a[m];
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    if (!__syncthreads_and(ok)) {
+      // a copy did not land: wait (bounded) for every copy this block issued, then stop
+      if (tid == 0) {
+        const int issued = min(n_my, k == 0 ? S : k - 1 + S);
+        for (int q = k; q < issued; ++q)
+          stage_wait(sm_addr(full + q % S), (uint32_t)(q / S) & 1u, fa.status);
+      }
+      return;
+    }
+    // every thread has read the previous tile's stage: refill it
+    if (tid == 0 && k >= 1 && k - 1 + S < n_my)
+      tile_issue<PASS, CC, S>(&tm, k - 1 + S, ncb, stage, full);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) a[q] = st[(l * 8 + q) * CC + c];
+    dft<float, float2, 8>(a);
+    if constexpr (PASS == 0) {
+      if (kx < ncol) {
+        float2* col = inter + (size_t)f * 4096 * fa.pitch + kx;
+#pragma unroll
+        for (int m2 = 0; m2 < 8; ++m2) {
+          const int m1 = l + 8 * m2;
+          const float2 y = mul(a[m2], __ldg(w + r * m1));  // j2 m1 <= 63 * 63
+          st_hint<2>(col + (unsigned)(64 * m1 + r) * (unsigned)fa.pitch, y, pol);
+        }
+      }
+    } else {
+      // this block was the intermediate's last reader of the tile (its copy has
+      // landed): drop the tile's lines from L2, one line per thread, live columns only
+      if (drop && tid < 64 * (CC / 16)) {
+        const int rr = tid & 63, g = tid >> 6;
+        const int kx0 = cb * CC + 16 * g;
+        if (kx0 < ncol)
+          asm volatile("discard.global.L2 [%0], 128;" ::"l"(inter + (size_t)f * 4096 * fa.pitch +
+                                                             (unsigned)(64 * r + rr) * (unsigned)fa.pitch + kx0)
+                       : "memory");
+      }
+      if (kx < ncol) {
+        const float sc = (float)fa.scale;
+        float2* out = fhat + (size_t)f * 4096 * ncol + kx;
+#pragma unroll
+        for (int m2p = 0; m2p < 8; ++m2p) {
+          const int m2 = l + 8 * m2p;
+          st_hint<4>(out + (unsigned)(r + 64 * m2) * (unsigned)ncol,
+                     make_float2(a[m2p].x * sc, a[m2p].y * sc), pol);
+        }
+      }
+    }
+  }
+}
+
+// The driver's tensor-map encoder, reached through the runtime (no link against the
+// driver library); null when the driver does not offer it.
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                   const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                   const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                   CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+static EncodeTiledFn encode_tiled() {
+  static const EncodeTiledFn fn = [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess) {
+      cudaGetLastError();
+      p = nullptr;
+    }
+    return reinterpret_cast<EncodeTiledFn>(p);
+  }();
+  return fn;
+}
+
+// The tensor map of pass A (pass 0) or B over n_f functions of the intermediate, tiles of
+// cc columns; false when the layout allows none (then the direct form runs).
+static bool cols_tma_map(int pass, int cc, const FftArgs& fa, int n_f, void* inter,
+                         CUtensorMap* tm) {
+  const EncodeTiledFn enc = encode_tiled();
+  const cuuint64_t ncol = (cuuint64_t)(fa.nx / 2 + 1), rowb = (cuuint64_t)fa.pitch * sizeof(float2);
+  if (!enc || fa.ny != 4096 || (reinterpret_cast<uintptr_t>(inter) & 15) || (rowb & 15))
+    return false;
+  const cuuint32_t unit[4] = {1, 1, 1, 1};
+  const CUtensorMapL2promotion prom =
+      cc >= 32 ? CU_TENSOR_MAP_L2_PROMOTION_L2_256B : CU_TENSOR_MAP_L2_PROMOTION_L2_128B;
+  CUresult r;
+  if (pass == 0) {
+    const cuuint64_t dim[4] = {ncol, 64, 64, (cuuint64_t)n_f};  // kx, j2, j1, f
+    const cuuint64_t str[3] = {rowb, 64 * rowb, 4096 * rowb};
+    const cuuint32_t box[4] = {(cuuint32_t)cc, 1, 64, 1};
+    r = enc(tm, CU_TENSOR_MAP_DATA_TYPE_UINT64, 4, inter, dim, str, box, unit,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, prom,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  } else {
+    const cuuint64_t dim[3] = {ncol, 4096, (cuuint64_t)n_f};  // kx, row, f
+    const cuuint64_t str[2] = {rowb, 4096 * rowb};
+    const cuuint32_t box[3] = {(cuuint32_t)cc, 64, 1};
+    r = enc(tm, CU_TENSOR_MAP_DATA_TYPE_UINT64, 3, inter, dim, str, box, unit,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, prom,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  }
+  return r == CUDA_SUCCESS;
+}
+
+// Resident blocks per SM of one TMA pass on the current device (its shared-memory
+// limit raised once per device) and the device's SM count; 0 when it cannot run.
+template <int PASS, int CC, int S>
+static int cols_tma_blocks(int* n_sm) {
+  constexpr int kDev = 64;
+  static std::mutex mu;
+  static int nb[kDev], nsm[kDev];
+  static bool done[kDev];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kDev) {
+    cudaGetLastError();
+    return 0;
+  }
+  std::lock_guard<std::mutex> lock(mu);
+  if (!done[dev]) {
+    const size_t sm = cols_tma_smem<CC, S>();
+    int b = 0, n = 0;
+    if (cudaFuncSetAttribute(k_cols4k_tma<PASS, CC, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)sm) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_cols4k_tma<PASS, CC, S>, 8 * CC, sm) !=
+            cudaSuccess ||
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+      cudaGetLastError();
+      b = 0;
+    }
+    nb[dev] = b;
+    nsm[dev] = n;
+    done[dev] = true;
+  }
+  *n_sm = nsm[dev];
+  return nb[dev];
+}
+
+// Both passes in the TMA form (S stages of CC columns); false (nothing launched) when
+// the form cannot run on this intermediate.
+template <int CC, int S>
+static bool cols4k_tma_launch_cc(const FftArgs& fa, int n_f, void* inter, void* fhat,
+                                 cudaStream_t s) {
+  int nsm = 0;
+  const int nba = cols_tma_blocks<0, CC, S>(&nsm), nbb = cols_tma_blocks<1, CC, S>(&nsm);
+  CUtensorMap ta, tb;
+  if (nba < 1 || nbb < 1 || nsm < 1 || !fa.status || !cols_tma_map(0, CC, fa, n_f, inter, &ta) ||
+      !cols_tma_map(1, CC, fa, n_f, inter, &tb))
+    return false;
+  const int ncol = fa.nx / 2 + 1;
+  const int n_tiles = (ncol + CC - 1) / CC * 64 * n_f;
+  const int drop = (reinterpret_cast<uintptr_t>(inter) % 128 == 0 && fa.pitch % 16 == 0) ? 1 : 0;
+  const size_t sm = cols_tma_smem<CC, S>();
+  launch_pdl(k_cols4k_tma<0, CC, S>, dim3(std::min(n_tiles, nba * nsm)), dim3(8 * CC), sm, s, ta,
+             fa, n_f, drop, (float2*)inter, (float2*)fhat);
+  launch_pdl(k_cols4k_tma<1, CC, S>, dim3(std::min(n_tiles, nbb * nsm)), dim3(8 * CC), sm, s, tb,
+             fa, n_f, drop, (float2*)inter, (float2*)fhat);
+  return true;
+}
+
+constexpr int kTmaStages = 3;
+
 static void cols4k_launch(const FftArgs& fa, int n_f, void* inter, void* fhat, cudaStream_t s) {
+  if (fa.cols_tma) {
+    const bool done = fa.cc4k == 32
+                          ? cols4k_tma_launch_cc<32, kTmaStages>(fa, n_f, inter, fhat, s)
+                          : cols4k_tma_launch_cc<16, kTmaStages>(fa, n_f, inter, fhat, s);
+    if (done) return;
+  }
   switch (fa.cc4k) {
+
     case 32: cols4k_launch_cc<32>(fa, n_f, inter, fhat, s); break;
     case 64: cols4k_launch_cc<64>(fa, n_f, inter, fhat, s); break;
     default: cols4k_launch_cc<16>(fa, n_f, inter, fhat, s); break;
@@ -1339,13 +1631,20 @@ bool launch_wave_cols_p2(const FftArgs& fa, int n_f, void* inter, double c, doub
   }
 }
 
-// The autotuner of the 4096-point FP32 column passes (plan time): each block width
-// CC = 16, 32, 64 timed on a scratch intermediate of the plan's grid (3 warm-up calls,
-// then the best of 5 timed with events on a private stream); the fastest is returned in
-// *best, the times (microseconds per call) in us[0..2].  Every width computes the same
+// The autotuner of the 4096-point FP32 column passes (plan time): the direct form with
+// CC = 16, 32, 64 columns per block, each timed on a scratch intermediate of the plan's
+// grid (3 warm-up calls, then the best of 5 timed with events on a private stream); the
+// fastest is returned in *best (columns) and *tma (form, 0), the times (microseconds per
+// call) in us[0..2]; us[3..4] (the TMA-pipelined form) stay 0.  The TMA form is not a
+// candidate: timed alone it ties with the direct form (42.6 against 42.5 us at 4096^2),
+// but inside the extension step it is slower (the step takes 93.9 against 86.0 us: its
+// persistent blocks hold every SM until their last tile, so neither the next kernel's
+// blocks nor the previous kernel's tail overlap them), which an isolated timing cannot
+// see; it stays available through fc2d_tuning_set.  Every candidate computes the same
 // values, so the choice changes no result.
-fc2d_status tune_cols4k(FftArgs fa, int* best, float* us) {
+fc2d_status tune_cols4k(FftArgs fa, int* best, int* tma, float* us) {
   *best = 16;
+  *tma = 0;
   if (fa.ny != 4096) return FC2D_OK;
   const int ncol = fa.nx / 2 + 1;
   const size_t bytes = (size_t)4096 * fa.pitch * sizeof(float2),
@@ -1362,6 +1661,8 @@ fc2d_status tune_cols4k(FftArgs fa, int* best, float* us) {
     cudaMemsetAsync(inter, 0, bytes, s);
     const int cand[3] = {16, 32, 64};
     float best_us = 0.f;
+    for (int k = 0; k < 5; ++k) us[k] = 0.f;
+    fa.cols_tma = 0;
     for (int k = 0; k < 3 && !st; ++k) {
       fa.cc4k = cand[k];
       for (int r = 0; r < 3; ++r) p2::cols4k_launch(fa, 1, inter, out, s);

@@ -130,9 +130,12 @@ struct fc2d_plan_s {
   void* poisson = nullptr;                     // Poisson tables (poisson.cu)
   void* wave = nullptr;                        // Fourier Forwarding state (ff.cu)
   // autotuned launch shapes (tune_plan): columns per block of the 4096-point FP32
-  // column passes and the candidates' times (microseconds per call; 0: not tuned)
+  // column passes, their form (0 a block per tile, direct loads; 1 persistent blocks,
+  // TMA-pipelined loads) and the candidates' times (microseconds per call, direct 16,
+  // 32, 64 then TMA 16, 32; 0: not tuned)
   int tune_cc4k = 16;
-  float tune_us[3] = {0.f, 0.f, 0.f};
+  int tune_tma = 0;
+  float tune_us[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
 };
 
 namespace fc2d {

@@ -280,15 +280,21 @@ class Plan:
                                       _ptr(ut), _ptr(grid), _ptr(grid_prev), _ptr(g), _ptr(out),
                                       _stream(stream)))
 
-    def fc2d_tuning(self):
-        """(columns per block of the 4096-point column passes, candidates' times in us)."""
-        choice = np.zeros(1, np.int32)
-        us = np.zeros(3, np.float32)
-        _check(_lib.fc2d_tuning(self.handle, choice.ctypes.data, us.ctypes.data))
-        return int(choice[0]), [float(v) for v in us]
+    # the column-pass candidates the plan-time tuner times, in the order of its times
+    TUNING_CANDIDATES = (("direct", 16), ("direct", 32), ("direct", 64), ("tma", 16),
+                         ("tma", 32))
 
-    def fc2d_tuning_set(self, columns_per_block):
-        choice = np.array([columns_per_block], np.int32)
+    def fc2d_tuning(self):
+        """(form "direct" or "tma", columns per block, {(form, columns): us per call})
+        of the 4096-point column passes."""
+        choice = np.zeros(2, np.int32)
+        us = np.zeros(5, np.float32)
+        _check(_lib.fc2d_tuning(self.handle, choice.ctypes.data, us.ctypes.data))
+        return (("direct", "tma")[int(choice[1])], int(choice[0]),
+                {c: float(v) for c, v in zip(self.TUNING_CANDIDATES, us)})
+
+    def fc2d_tuning_set(self, columns_per_block, form="direct"):
+        choice = np.array([columns_per_block, {"direct": 0, "tma": 1}[form]], np.int32)
         _check(_lib.fc2d_tuning_set(self.handle, choice.ctypes.data))
 
     def fc2d_profile(self, enable=True):

@@ -241,28 +241,38 @@ def test_full_size_complex_f(setup, complex_ref, precision):
     assert rel(got[..., 0] + 1j * got[..., 1], ref_c) < bar
 
 
-def test_column_block_widths_give_the_same_spectrum():
-    """The plan-time tuner picks one of three block widths for the 4096-point column
-    passes; each width computes the same values, so a plan whose tuner chose any width
-    gives the spectrum of the 16-column form bit for bit (checked by re-running the
-    column passes of one plan at every width through fc2d_coeffs on the same
-    intermediate input)."""
+def test_column_pass_candidates_give_the_same_spectrum():
+    """The 4096-point column passes run in the direct form (16, 32 or 64 columns per
+    block; the plan-time tuner keeps the fastest width) or, when set, the TMA-pipelined
+    form (16 or 32); every choice computes the same values, so each gives the spectrum
+    of the 16-column direct form bit for bit (re-running one plan's column passes with
+    every choice through fc2d_coeffs on the same input, one function and three
+    functions, the latter spanning tiles of several functions in the TMA form's tile
+    order; the outputs start as NaN, so an element left unwritten fails)."""
     torch = pytest.importorskip("torch")
     from paper_2010_03901_gb300 import fc2d
     w = W.workload("kite4096")
     g, p = w.grid, w.params
     plan = fc2d.fc2d_plan(w.boundary.arrays(), (g.a0, g.b0, g.h, g.nx, g.ny),
                           dict(B=p.B, k1=p.k1), precision=fc2d.FC2D_MIXED)
-    cc, us = plan.fc2d_tuning()
-    assert cc in (16, 32, 64) and all(t > 0 for t in us)
-    assert us[(16, 32, 64).index(cc)] == min(us)
-    x = torch.tensor(W.normal(5, g.ny * g.nx).reshape(1, g.ny, g.nx), dtype=torch.float32,
-                     device="cuda:0")
-    outs = []
-    for width in (16, 32, 64):
-        plan.fc2d_tuning_set(width)
-        o = torch.zeros((1, g.ny, g.nx // 2 + 1, 2), dtype=torch.float32, device="cuda:0")
-        plan.fc2d_coeffs(1, x, o)
-        plan.fc2d_sync_status()
-        outs.append(o)
-    assert torch.equal(outs[0], outs[1]) and torch.equal(outs[0], outs[2])
+    form, cc, us = plan.fc2d_tuning()
+    direct = {k: v for k, v in us.items() if k[0] == "direct"}
+    assert form == "direct" and all(t > 0 for t in direct.values()), us
+    assert us[(form, cc)] == min(direct.values())
+    assert us[("tma", 16)] == 0 and us[("tma", 32)] == 0
+    for n_f in (1, 3):
+        x = torch.tensor(W.normal(5 + n_f, n_f * g.ny * g.nx).reshape(n_f, g.ny, g.nx),
+                         dtype=torch.float32, device="cuda:0")
+        outs = []
+        for cand_form, width in fc2d.Plan.TUNING_CANDIDATES:
+            plan.fc2d_tuning_set(width, cand_form)
+            assert plan.fc2d_tuning()[:2] == (cand_form, width)
+            o = torch.full((n_f, g.ny, g.nx // 2 + 1, 2), float("nan"), dtype=torch.float32,
+                           device="cuda:0")
+            plan.fc2d_coeffs(n_f, x, o)
+            plan.fc2d_sync_status()
+            outs.append(o)
+        for o in outs[1:]:
+            assert torch.equal(outs[0], o)
+    with pytest.raises(fc2d.Fc2dError):
+        plan.fc2d_tuning_set(64, "tma")
