@@ -1646,6 +1646,17 @@ fc2d_status tune_cols4k(FftArgs fa, int* best, int* tma, float* us) {
   *best = 16;
   *tma = 0;
   if (fa.ny != 4096) return FC2D_OK;
+  // the TMA form's one-time host setup (shared-memory limit, occupancy, the encoder),
+  // here at plan time, outside any stream capture a later call may run under
+  {
+    int nsm = 0;
+    using p2::kTmaStages;
+    p2::cols_tma_blocks<0, 16, kTmaStages>(&nsm);
+    p2::cols_tma_blocks<1, 16, kTmaStages>(&nsm);
+    p2::cols_tma_blocks<0, 32, kTmaStages>(&nsm);
+    p2::cols_tma_blocks<1, 32, kTmaStages>(&nsm);
+    p2::encode_tiled();
+  }
   const int ncol = fa.nx / 2 + 1;
   const size_t bytes = (size_t)4096 * fa.pitch * sizeof(float2),
                obytes = (size_t)4096 * ncol * sizeof(float2);

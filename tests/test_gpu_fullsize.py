@@ -5,7 +5,8 @@ input and output buffers).  The whole half spectrum is compared with the
 oracle's: 1e-6 (mixed), 1e-12 (FP64) relative max-norm, and the compact-input call
 must give the same spectrum bit for bit.  The same from interior data only (no
 boundary values) and for a complex f, and the Fourier Forwarding line's step at its
-full size."""
+full size.  Every column-pass form and width gives the same spectrum, the TMA form
+also inside a plan group's captured graph."""
 import numpy as np
 import pytest
 
@@ -276,3 +277,43 @@ def test_column_pass_candidates_give_the_same_spectrum():
             assert torch.equal(outs[0], o)
     with pytest.raises(fc2d.Fc2dError):
         plan.fc2d_tuning_set(64, "tma")
+
+
+def test_tma_column_form_under_group_capture(setup):
+    """The TMA-pipelined column form set on the kite 4096^2 plan, run inside a plan
+    group's captured CUDA graph (first call, then a replay over a new input): the
+    spectra equal separate fc2d_extend_coeffs calls in the direct form bit for bit, and
+    the first equals the oracle's within the mixed bar."""
+    torch, w, fg, fb, ref, geo, mats, st = setup
+    from paper_2010_03901_gb300 import fc2d
+    g, p = w.grid, w.params
+    dev = torch.device("cuda:0")
+    plan = fc2d.fc2d_plan(w.boundary.arrays(), (g.a0, g.b0, g.h, g.nx, g.ny),
+                          dict(B=p.B, k1=p.k1), precision=fc2d.FC2D_MIXED)
+    tuned = plan.fc2d_tuning()
+    fgd = torch.tensor(fg[None], device=dev)
+    fbd = torch.tensor(fb[None], device=dev)
+    shape = (1, g.ny, g.nx // 2 + 1, 2)
+    plan.fc2d_tuning_set(16, "tma")
+    grp = fc2d.fc2d_group_create([plan])
+    out = torch.full(shape, float("nan"), dtype=torch.float32, device=dev)
+    grp.fc2d_group_extend_coeffs([1], [fgd], [fbd], [out])
+    first = out.clone()
+    fgd.mul_(-0.5)
+    fbd.mul_(-0.5)
+    grp.fc2d_group_extend_coeffs([1], [fgd], [fbd], [out])
+    torch.cuda.synchronize()
+    plan.fc2d_sync_status()
+    plan.fc2d_tuning_set(tuned[1], tuned[0])
+    assert plan.fc2d_tuning()[0] == "direct"
+    sep = torch.zeros(shape, dtype=torch.float32, device=dev)
+    plan.fc2d_extend_coeffs(1, fgd, fbd, sep)
+    plan.fc2d_sync_status()
+    assert torch.equal(out, sep)
+    fgd.mul_(-2.0)
+    fbd.mul_(-2.0)
+    plan.fc2d_extend_coeffs(1, fgd, fbd, sep)
+    plan.fc2d_sync_status()
+    assert torch.equal(first, sep)
+    got = first.cpu().numpy().astype(np.float64)[0]
+    assert rel(got[..., 0] + 1j * got[..., 1], ref) < 1e-6
