@@ -439,19 +439,6 @@ def measure(fc2d, torch, w, precision, K, warmup, world, dev, fg_h, fb_h, sample
     ms_prof = max_over_ranks(ms_prof_raw, world, dev)
     npts = g.nx * g.ny
     value = replica_throughput(world, K, npts, ms)
-    # the column passes' TMA-pipelined form, set by hand (the tuner keeps the direct
-    # form): the same K steps back to back, then the tuned shape is restored
-    cols_tma = None
-    if not fp64 and g.ny == 4096:
-        tuned = plan.fc2d_tuning()
-        cols_tma = {}
-        for width in (16, 32):
-            plan.fc2d_tuning_set(width, "tma")
-            for k in range(3):
-                plan.fc2d_extend_coeffs(1, fgs[k % ROT], fb, fhats[k % ROT], stream)
-            cols_tma[f"tma{width}_ms_per_step"] = max_over_ranks(timed_region()[0], world,
-                                                                 dev) / K
-        plan.fc2d_tuning_set(tuned[1], tuned[0])
     # end to end through the public API with host buffers: every step copies its
     # inputs from pinned host memory, calls the library and reads its spectrum back to
     # pinned host memory.  Steps are pipelined as a user streaming functions would:
@@ -545,12 +532,12 @@ def measure(fc2d, torch, w, precision, K, warmup, world, dev, fg_h, fb_h, sample
     cform, cc, cc_us = plan.fc2d_tuning()
     return {"value": value, "ms_per_step": ms / K, "steps": K, "plan_s": plan_s,
             "tuning": {"cols4k_form": cform, "cols4k_columns_per_block": cc,
-                       "candidates_us": {f"{f}{c}": v for (f, c), v in cc_us.items()
-                                         if f == "direct"},
-                       "how": "plan-time autotuner: the direct form at 16/32/64 columns, "
-                              "each timed on a scratch intermediate of this grid, fastest "
-                              "kept (same values)",
-                       "tma_form_in_step": cols_tma},
+                       "candidates_us_per_step": {f"{f}{c}": v for (f, c), v in
+                                                  cc_us.items()},
+                       "how": "plan-time autotuner: the column passes' direct form at "
+                              "16/32/64 columns and TMA-pipelined form at 16/32, each "
+                              "timed inside the plan's own extension step (synthetic "
+                              "input, 10 steps), fastest kept (same values)"},
             "l2_flushed": {"value": replica_throughput(world, K, npts, ms_fl),
                            "ms_per_step": ms_fl / K,
                            "note": "L2 flushed before each step (256 MB read, outside "

@@ -328,14 +328,14 @@ fc2d_status fc2d_wave_ub_step(fc2d_plan_t plan, int n_c, int n_f, int mode, doub
  * registers) or TMA-pipelined (persistent blocks of 16 or 32 columns per tile, each
  * keeping the next tiles in flight through tensor-map copies into shared memory, every
  * wait bounded).  choice[2]: choice[0] = columns per block, choice[1] = form (0 direct,
- * 1 TMA-pipelined).  At plan time the direct form's three widths are timed on a scratch
- * intermediate of the plan's grid and the fastest kept; the TMA form is used only when
- * set (timed alone it ties with the direct form, inside the extension step it is slower
- * on GB300).  us[5] (NULL allowed) receives the times in microseconds per call of direct
- * 16, 32, 64, then 0, 0 for TMA 16, 32 (not timed); all zeros when the plan has no such
- * transform, which keeps {16, 0}.  Where the TMA form cannot run (an intermediate not
- * 16-byte aligned, no tensor-map encoder in the driver), the direct form with the same
- * width runs instead. */
+ * 1 TMA-pipelined).  At plan time every candidate runs inside the plan's own extension
+ * step (one function, synthetic inputs allocated for the purpose, 3 warm-up and 10
+ * timed steps) and the fastest step is kept; us[5] (NULL allowed) receives the step
+ * times in microseconds of direct 16, 32, 64, then TMA 16, 32 (0 for a candidate that
+ * cannot run; all zeros when the plan has no such transform, or no memory was left
+ * for the tuning inputs, which keeps {16, 0}).  Where the TMA form cannot run (an
+ * intermediate not 16-byte aligned, no tensor-map encoder in the driver), a plan set to
+ * it runs the direct form with the same width. */
 fc2d_status fc2d_tuning(fc2d_plan_t plan, int32_t* choice, float* us);
 /* Set the choice (choice[2]: columns 16, 32 or 64 with form 0, 16 or 32 with form 1;
  * FC2D_ERR_ARG otherwise), for tests and for callers that fix the launch shape; calls

@@ -1,6 +1,7 @@
 // C-ABI entry points that launch the 2D-FC kernels (declared in include/fc2d.h).
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
 #include <cstdio>
 #include <cstring>
@@ -609,19 +610,81 @@ extern "C" fc2d_status fc2d_poisson(fc2d_plan_t p, int n_f, const double* fg, co
 // Fourier Forwarding interior propagator (Section 4.2)
 // ------------------------------------------------------------------------- //
 namespace fc2d {
-fc2d_status tune_cols4k(FftArgs fa, int* best, int* tma, float* us);
+void cols4k_prepare();
+bool cols4k_tma_usable(const FftArgs& fa, int cc, int n_f, void* inter);
 
-// Plan-time autotuning: the mixed form's 4096-point column passes take the block width
-// of the direct form (16, 32 or 64 columns) that runs fastest on this GPU for the plan's
-// grid.
+// Plan-time autotuning of the mixed form's 4096-point column passes.  Every candidate
+// (the direct form with 16, 32 or 64 columns per block, the TMA-pipelined form with 16
+// or 32) runs inside this plan's own extension step: fc2d_extend_coeffs of one function
+// on two alternating synthetic inputs and outputs (each byte 0x3F, so every value is a
+// normal double and the FP64 to FP32 conversions take their usual path; two grids of
+// f exceed the L2 together), 3 warm-up steps, then 10 timed back to back with events
+// on a private stream.  The fastest step is kept.  The passes timed on their own do not
+// predict the step, where their blocks also overlap the previous and the next kernel.
+// Without the memory for the inputs the plan keeps the untuned shape {16, direct}.
 fc2d_status tune_plan(fc2d_plan_s* p) {
   if (p->prm.precision != FC2D_MIXED || p->grid.ny != 4096) return FC2D_OK;
-  int best = 16, tma = 0;
-  fc2d_status st = tune_cols4k(fft_args(p), &best, &tma, p->tune_us);
-  if (st == FC2D_OK) {
-    p->tune_cc4k = best;
-    p->tune_tma = tma;
+  cols4k_prepare();
+  const size_t ng = (size_t)p->grid.nx * p->grid.ny;
+  const size_t nh = (size_t)p->grid.ny * (p->grid.nx / 2 + 1) * 2 * sizeof(float);
+  const size_t nb = (size_t)std::max<int64_t>(1, p->n_bdry) * sizeof(double);
+  void *fg[2] = {nullptr, nullptr}, *fh[2] = {nullptr, nullptr}, *fb = nullptr;
+  cudaStream_t s = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  fc2d_status st = FC2D_OK;
+  bool have = cudaMalloc(&fb, nb) == cudaSuccess;
+  for (int i = 0; i < 2; ++i)
+    have = have && cudaMalloc(&fg[i], ng * sizeof(double)) == cudaSuccess &&
+           cudaMalloc(&fh[i], nh) == cudaSuccess;
+  have = have && cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) == cudaSuccess &&
+         cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess;
+  if (!have) {
+    cudaGetLastError();  // not enough memory to time: the untuned shape stays
+  } else {
+    for (int i = 0; i < 2; ++i) cudaMemsetAsync(fg[i], 0x3F, ng * sizeof(double), s);
+    cudaMemsetAsync(fb, 0x3F, nb, s);
+    const int cand[5] = {16, 32, 64, 16, 32}, form[5] = {0, 0, 0, 1, 1};
+    float best_us = 0.f;
+    int best = -1;
+    for (int k = 0; k < 5 && !st; ++k) {
+      p->tune_cc4k = cand[k];
+      p->tune_tma = form[k];
+      p->tune_us[k] = 0.f;
+      const double* fb_arg = p->n_bdry > 0 ? (const double*)fb : nullptr;
+      int n = 0;
+      for (; n < 3 && !st; ++n)
+        st = fc2d_extend_coeffs(p, 1, (const double*)fg[n & 1], fb_arg, fh[n & 1], s);
+      // a TMA candidate that cannot run on this plan's intermediate is not timed
+      if (st || (form[k] && !cols4k_tma_usable(fft_args(p), cand[k], 1,
+                                                 ws(p, layout(p, 1).ointer))))
+        continue;
+      cudaEventRecord(e0, s);
+      for (int r = 0; r < 10 && !st; ++r, ++n)
+        st = fc2d_extend_coeffs(p, 1, (const double*)fg[n & 1], fb_arg, fh[n & 1], s);
+      cudaEventRecord(e1, s);
+      if (!st) st = cuda_check(cudaEventSynchronize(e1), "column tuner");
+      float ms = 0.f;
+      if (!st) st = cuda_check(cudaEventElapsedTime(&ms, e0, e1), "column tuner");
+      if (st) break;
+      p->tune_us[k] = ms * 100.f;  // microseconds per step (10 steps)
+      if (best < 0 || p->tune_us[k] < best_us) {
+        best_us = p->tune_us[k];
+        best = k;
+      }
+    }
+    if (!st) st = fc2d_sync_status(p, s);
+    p->tune_cc4k = best >= 0 ? cand[best] : 16;
+    p->tune_tma = best >= 0 ? form[best] : 0;
   }
+  if (s) cudaStreamSynchronize(s);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (s) cudaStreamDestroy(s);
+  for (int i = 0; i < 2; ++i) {
+    cudaFree(fg[i]);
+    cudaFree(fh[i]);
+  }
+  cudaFree(fb);
   return st;
 }
 }  // namespace fc2d

@@ -1631,77 +1631,33 @@ bool launch_wave_cols_p2(const FftArgs& fa, int n_f, void* inter, double c, doub
   }
 }
 
-// The autotuner of the 4096-point FP32 column passes (plan time): the direct form with
-// CC = 16, 32, 64 columns per block, each timed on a scratch intermediate of the plan's
-// grid (3 warm-up calls, then the best of 5 timed with events on a private stream); the
-// fastest is returned in *best (columns) and *tma (form, 0), the times (microseconds per
-// call) in us[0..2]; us[3..4] (the TMA-pipelined form) stay 0.  The TMA form is not a
-// candidate: timed alone it ties with the direct form (42.6 against 42.5 us at 4096^2),
-// but inside the extension step it is slower (the step takes 93.9 against 86.0 us: its
-// persistent blocks hold every SM until their last tile, so neither the next kernel's
-// blocks nor the previous kernel's tail overlap them), which an isolated timing cannot
-// see; it stays available through fc2d_tuning_set.  Every candidate computes the same
-// values, so the choice changes no result.
-fc2d_status tune_cols4k(FftArgs fa, int* best, int* tma, float* us) {
-  *best = 16;
-  *tma = 0;
-  if (fa.ny != 4096) return FC2D_OK;
-  // the TMA form's one-time host setup (shared-memory limit, occupancy, the encoder),
-  // here at plan time, outside any stream capture a later call may run under
-  {
-    int nsm = 0;
-    using p2::kTmaStages;
-    p2::cols_tma_blocks<0, 16, kTmaStages>(&nsm);
-    p2::cols_tma_blocks<1, 16, kTmaStages>(&nsm);
-    p2::cols_tma_blocks<0, 32, kTmaStages>(&nsm);
-    p2::cols_tma_blocks<1, 32, kTmaStages>(&nsm);
-    p2::encode_tiled();
-  }
-  const int ncol = fa.nx / 2 + 1;
-  const size_t bytes = (size_t)4096 * fa.pitch * sizeof(float2),
-               obytes = (size_t)4096 * ncol * sizeof(float2);
-  void *inter = nullptr, *out = nullptr;
-  cudaStream_t s = nullptr;
-  cudaEvent_t e0 = nullptr, e1 = nullptr;
-  fc2d_status st = FC2D_OK;
-  if (cudaMalloc(&inter, bytes) != cudaSuccess || cudaMalloc(&out, obytes) != cudaSuccess ||
-      cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess ||
-      cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
-    st = set_error(FC2D_ERR_NOMEM, "column tuner: allocation failed");
-  } else {
-    cudaMemsetAsync(inter, 0, bytes, s);
-    const int cand[3] = {16, 32, 64};
-    float best_us = 0.f;
-    for (int k = 0; k < 5; ++k) us[k] = 0.f;
-    fa.cols_tma = 0;
-    for (int k = 0; k < 3 && !st; ++k) {
-      fa.cc4k = cand[k];
-      for (int r = 0; r < 3; ++r) p2::cols4k_launch(fa, 1, inter, out, s);
-      float t = 1e30f;
-      for (int r = 0; r < 5; ++r) {
-        cudaEventRecord(e0, s);
-        p2::cols4k_launch(fa, 1, inter, out, s);
-        cudaEventRecord(e1, s);
-        cudaEventSynchronize(e1);
-        float ms = 0.f;
-        cudaEventElapsedTime(&ms, e0, e1);
-        t = std::min(t, ms * 1000.f);
-      }
-      st = cuda_check(cudaGetLastError(), "column tuner");
-      us[k] = t;
-      if (k == 0 || t < best_us) {
-        best_us = t;
-        *best = cand[k];
-      }
-    }
-  }
-  if (s) cudaStreamSynchronize(s);
-  if (e0) cudaEventDestroy(e0);
-  if (e1) cudaEventDestroy(e1);
-  if (s) cudaStreamDestroy(s);
-  cudaFree(inter);
-  cudaFree(out);
-  return st;
+// One-time host setup of the 4096-point passes' TMA form on the current device (the
+// shared-memory limit, the occupancy query, the tensor-map encoder), at plan time,
+// outside any stream capture a later call may run under.
+void cols4k_prepare() {
+  int nsm = 0;
+  using p2::kTmaStages;
+  p2::cols_tma_blocks<0, 16, kTmaStages>(&nsm);
+  p2::cols_tma_blocks<1, 16, kTmaStages>(&nsm);
+  p2::cols_tma_blocks<0, 32, kTmaStages>(&nsm);
+  p2::cols_tma_blocks<1, 32, kTmaStages>(&nsm);
+  p2::encode_tiled();
+}
+
+// Whether the TMA form with cc columns per tile can run on the intermediate `inter` of
+// n_f functions (its launch shape on this device and both tensor maps); where it cannot,
+// a plan set to it runs the direct form with the same width.
+bool cols4k_tma_usable(const FftArgs& fa, int cc, int n_f, void* inter) {
+  if (fa.ny != 4096 || !fa.status || (cc != 16 && cc != 32)) return false;
+  int nsm = 0;
+  using p2::kTmaStages;
+  const int nb = cc == 32 ? std::min(p2::cols_tma_blocks<0, 32, kTmaStages>(&nsm),
+                                     p2::cols_tma_blocks<1, 32, kTmaStages>(&nsm))
+                          : std::min(p2::cols_tma_blocks<0, 16, kTmaStages>(&nsm),
+                                     p2::cols_tma_blocks<1, 16, kTmaStages>(&nsm));
+  CUtensorMap t;
+  return nb > 0 && nsm > 0 && p2::cols_tma_map(0, cc, fa, n_f, inter, &t) &&
+         p2::cols_tma_map(1, cc, fa, n_f, inter, &t);
 }
 
 // Fourier Forwarding solve columns of 512 .. 4096 points; false (nothing launched)

@@ -285,8 +285,8 @@ class Plan:
                          ("tma", 32))
 
     def fc2d_tuning(self):
-        """(form "direct" or "tma", columns per block, {(form, columns): us per call})
-        of the 4096-point column passes."""
+        """(form "direct" or "tma", columns per block, {(form, columns): microseconds
+        per extension step at plan time}) of the 4096-point column passes."""
         choice = np.zeros(2, np.int32)
         us = np.zeros(5, np.float32)
         _check(_lib.fc2d_tuning(self.handle, choice.ctypes.data, us.ctypes.data))

@@ -244,12 +244,13 @@ def test_full_size_complex_f(setup, complex_ref, precision):
 
 def test_column_pass_candidates_give_the_same_spectrum():
     """The 4096-point column passes run in the direct form (16, 32 or 64 columns per
-    block; the plan-time tuner keeps the fastest width) or, when set, the TMA-pipelined
-    form (16 or 32); every choice computes the same values, so each gives the spectrum
-    of the 16-column direct form bit for bit (re-running one plan's column passes with
-    every choice through fc2d_coeffs on the same input, one function and three
-    functions, the latter spanning tiles of several functions in the TMA form's tile
-    order; the outputs start as NaN, so an element left unwritten fails)."""
+    block) or the TMA-pipelined form (16 or 32); the plan-time tuner times each inside
+    the plan's extension step and keeps the fastest.  Every choice computes the same
+    values, so each gives the spectrum of the 16-column direct form bit for bit
+    (re-running one plan's column passes with every choice through fc2d_coeffs on the
+    same input, one function and three functions, the latter spanning tiles of several
+    functions in the TMA form's tile order; the outputs start as NaN, so an element left
+    unwritten fails)."""
     torch = pytest.importorskip("torch")
     from paper_2010_03901_gb300 import fc2d
     w = W.workload("kite4096")
@@ -257,10 +258,8 @@ def test_column_pass_candidates_give_the_same_spectrum():
     plan = fc2d.fc2d_plan(w.boundary.arrays(), (g.a0, g.b0, g.h, g.nx, g.ny),
                           dict(B=p.B, k1=p.k1), precision=fc2d.FC2D_MIXED)
     form, cc, us = plan.fc2d_tuning()
-    direct = {k: v for k, v in us.items() if k[0] == "direct"}
-    assert form == "direct" and all(t > 0 for t in direct.values()), us
-    assert us[(form, cc)] == min(direct.values())
-    assert us[("tma", 16)] == 0 and us[("tma", 32)] == 0
+    assert all(t > 0 for t in us.values()), us  # every candidate ran in the step
+    assert us[(form, cc)] == min(us.values())
     for n_f in (1, 3):
         x = torch.tensor(W.normal(5 + n_f, n_f * g.ny * g.nx).reshape(n_f, g.ny, g.nx),
                          dtype=torch.float32, device="cuda:0")
@@ -290,7 +289,6 @@ def test_tma_column_form_under_group_capture(setup):
     dev = torch.device("cuda:0")
     plan = fc2d.fc2d_plan(w.boundary.arrays(), (g.a0, g.b0, g.h, g.nx, g.ny),
                           dict(B=p.B, k1=p.k1), precision=fc2d.FC2D_MIXED)
-    tuned = plan.fc2d_tuning()
     fgd = torch.tensor(fg[None], device=dev)
     fbd = torch.tensor(fb[None], device=dev)
     shape = (1, g.ny, g.nx // 2 + 1, 2)
@@ -304,8 +302,7 @@ def test_tma_column_form_under_group_capture(setup):
     grp.fc2d_group_extend_coeffs([1], [fgd], [fbd], [out])
     torch.cuda.synchronize()
     plan.fc2d_sync_status()
-    plan.fc2d_tuning_set(tuned[1], tuned[0])
-    assert plan.fc2d_tuning()[0] == "direct"
+    plan.fc2d_tuning_set(32, "direct")
     sep = torch.zeros(shape, dtype=torch.float32, device=dev)
     plan.fc2d_extend_coeffs(1, fgd, fbd, sep)
     plan.fc2d_sync_status()
