@@ -815,7 +815,7 @@ k_fft_cols_p2(FftArgs fa, const typename Cx<T>::type* __restrict__ inter,
 // between the passes.
 // ------------------------------------------------------------------------- //
 constexpr int kC4Cols = 16;   // columns per block (mixed-radix passes; the 4096-point
-                              // passes take the plan's tuned width, see tune_cols4k)
+                              // passes take the width tuned at plan time, tune_plan)
 
 // 64-point DFT of a[i] = x[l + 8 i] held by the threads (c, l = 0..7) of column c;
 // on return a[m'] = X[l + 8 m'].  ex: the block's [8][8][CC] exchange buffer; w: the
