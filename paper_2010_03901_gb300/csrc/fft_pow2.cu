@@ -1011,9 +1011,9 @@ static void cols4k_launch_cc(const FftArgs& fa, int n_f, void* inter, void* fhat
 // place in the stage: thread (c, l) reads the rows l + 8 i of its column and writes its
 // exchange values to the rows 8 m + l, the same rows, so no other thread's input is
 // overwritten and no barrier is needed before the writes; after the block's barrier
-// each thread reads the rows 8 l .. 8 l + 7.  That barrier also tells thread 0 that
-// every thread has finished with the previous tile's stage, which it refills with the
-// tile S - 1 further on.  One barrier per tile, no exchange buffer: S tiles of shared
+// each thread reads the rows 8 l .. 8 l + 7.  The barrier of tile k also tells thread 0
+// that every thread has finished with the stage of tile k - 1, which it refills with
+// tile k - 1 + S.  One barrier per tile, no exchange buffer: S tiles of shared
 // memory per block, so 1024 threads fit on an SM with S - 1 tiles in flight per block
 // during the transforms, and the loads no longer wait in the computing warps'
 // registers.  Each thread holds the same values as in the direct form and runs the same
