@@ -382,11 +382,12 @@ __global__ void __launch_bounds__(256) k_ff_cols(FftArgs fa, int n_f, const doub
 // ------------------------------------------------------------------------- //
 constexpr int kSqThreads = 256;
 
-// 1D-FC continuation (eq. (2.7)) of the length-n sequence x[0], x[st], ..., x[(n-1) st]
-// (complex values: two real functions at once) into x[n st] .. x[(n + C - 1) st]:
+// 1D-FC continuation (eq. (2.7)) of the length-n sequence x[at(0)], ..., x[at(n-1)]
+// (complex values: two real functions at once) into x[at(n)] .. x[at(n + C - 1)]:
 // the C values (A Q^T r)_k + (A Q^T l)_{C-1-k}, r the last d values, l the first d in
 // reverse order.  One thread per continuation point.
-__device__ __forceinline__ void fc1d_continue(double2* x, int st, int n, int C, int d,
+template <typename At>
+__device__ __forceinline__ void fc1d_continue(double2* x, At at, int n, int C, int d,
                                               const double* __restrict__ A,
                                               const double* __restrict__ Q, int k) {
   double2 cr[kMaxD], cl[kMaxD];
@@ -394,7 +395,7 @@ __device__ __forceinline__ void fc1d_continue(double2* x, int st, int n, int C, 
     double2 r = {0.0, 0.0}, l = {0.0, 0.0};
     for (int m = 0; m < d; ++m) {
       const double qm = __ldg(Q + m * d + i);
-      const double2 fr = x[(size_t)(n - d + m) * st], fl = x[(size_t)(d - 1 - m) * st];
+      const double2 fr = x[at(n - d + m)], fl = x[at(d - 1 - m)];
       r.x += qm * fr.x;
       r.y += qm * fr.y;
       l.x += qm * fl.x;
@@ -411,72 +412,10 @@ __device__ __forceinline__ void fc1d_continue(double2* x, int st, int n, int C, 
     vl.x += al * cl[i].x;
     vl.y += al * cl[i].y;
   }
-  x[(size_t)(n + k) * st] = double2{vl.x + vr.x, vl.y + vr.y};
+  x[at(n + k)] = double2{vl.x + vr.x, vl.y + vr.y};
 }
 
-// In-place transpose of a P x P complex matrix in shared memory (a -> b).
-__device__ __forceinline__ void sq_transpose(const double2* a, double2* b, int P) {
-  for (int t = threadIdx.x; t < P * P; t += blockDim.x) {
-    const int r = t / P, c = t - r * P;
-    b[c * P + r] = a[t];
-  }
-  __syncthreads();
-}
-
-// A complex double as double-float pairs: hi = RN(x), lo = RN(x - hi).
-__device__ __forceinline__ float4 split_df(double2 v) {
-  const float rh = __double2float_rn(v.x), ih = __double2float_rn(v.y);
-  return float4{rh, __double2float_rn(v.x - (double)rh), ih, __double2float_rn(v.y - (double)ih)};
-}
-
-// Once per large step: each square's expansion.  Block (square, function): the square's
-// u and u_t as one complex field z = u + i u_t, continued along rows, then columns, to
-// P x P; its 2D DFT, normalised, stored transposed: Z[l][m] (l: x frequency).
-// DF: Z as double-float pairs (float4 re hi, re lo, im hi, im lo) for k_sq_eval_df.
-template <bool DF>
-__global__ void __launch_bounds__(kSqThreads) k_sq_forward(
-    int P, int n_side, int C, int d, int nx, int64_t grid_stride, int n_f,
-    const int32_t* __restrict__ origin, const double* __restrict__ A,
-    const double* __restrict__ Q, const double2* __restrict__ tw, const double* __restrict__ u,
-    const double* __restrict__ ut, double2* __restrict__ Z) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  double2* buf = reinterpret_cast<double2*>(smem_raw);
-  double2* scr = buf + P * P;
-  const int sq = blockIdx.x, f = blockIdx.y;
-  const int j0 = __ldg(origin + 2 * sq), i0 = __ldg(origin + 2 * sq + 1);
-  const double* uf = u + (size_t)f * grid_stride;
-  const double* tf = ut + (size_t)f * grid_stride;
-  for (int t = threadIdx.x; t < n_side * n_side; t += blockDim.x) {
-    const int y = t / n_side, x = t - y * n_side;
-    const size_t g = (size_t)(j0 + y) * nx + (i0 + x);
-    buf[y * P + x] = double2{uf[g], tf[g]};
-  }
-  __syncthreads();
-  for (int t = threadIdx.x; t < n_side * C; t += blockDim.x) {  // rows
-    const int y = t / C, k = t - y * C;
-    fc1d_continue(buf + y * P, 1, n_side, C, d, A, Q, k);
-  }
-  __syncthreads();
-  for (int t = threadIdx.x; t < P * C; t += blockDim.x) {  // columns
-    const int x = t / C, k = t - x * C;
-    fc1d_continue(buf + x, P, n_side, C, d, A, Q, k);
-  }
-  __syncthreads();
-  int radix[2] = {8, 8};
-  double2* r = stockham<double>(buf, scr, P, P, radix, 2, tw, 1);  // along x: r[y][l]
-  double2* o = r == buf ? scr : buf;
-  sq_transpose(r, o, P);                                           // o[l][y]
-  r = stockham<double>(o, r, P, P, radix, 2, tw, 1);               // r[l][m]
-  const double sc = 1.0 / ((double)P * P);
-  double2* dst = Z + ((size_t)sq * n_f + f) * P * P;
-  for (int t = threadIdx.x; t < P * P; t += blockDim.x) {
-    const double2 v = double2{r[t].x * sc, r[t].y * sc};
-    if constexpr (DF) reinterpret_cast<float4*>(dst)[t] = split_df(v);
-    else dst[t] = v;
-  }
-}
-
-// 64-point DFT of the padded sequence x[pad(e)], e < 64 (pad(e) = e + e/8), by the 8
+// 64-point DFT of the padded sequence x[pad(e) ST], e < 64 (pad(e) = e + e/8), by the 8
 // threads q = 0..7 of a group, as 8 x 8: X[k1 + 8 k2] = sum_q w8^(q k2) w64^(q k1)
 // sum_r x[q + 8 r] w8^(r k1); the result replaces x in natural order.  Every thread of
 // the block calls it (three barriers, the last after the result is stored); `active`
@@ -511,30 +450,100 @@ __device__ __forceinline__ void dft8_regs(double2 (&v)[8]) {
   v[7] = csub(e3, w3);
 }
 
+template <int ST = 1>
 __device__ __forceinline__ void fft64(double2* x, int q, bool active,
                                       const double2* __restrict__ tw) {
   double2 v[8];
   if (active) {
 #pragma unroll
-    for (int r = 0; r < 8; ++r) v[r] = x[sq_pad(q + 8 * r)];
+    for (int r = 0; r < 8; ++r) v[r] = x[sq_pad(q + 8 * r) * ST];
     dft8_regs(v);
 #pragma unroll
     for (int k = 1; k < 8; ++k) v[k] = cmul(v[k], __ldg(tw + q * k));  // w64^(q k1)
 #pragma unroll
-    for (int k = 0; k < 8; ++k) x[sq_pad(q + 8 * k)] = v[k];
+    for (int k = 0; k < 8; ++k) x[sq_pad(q + 8 * k) * ST] = v[k];
   }
   __syncthreads();
   if (active) {
 #pragma unroll
-    for (int r = 0; r < 8; ++r) v[r] = x[sq_pad(8 * q + r)];  // thread q is k1 here
+    for (int r = 0; r < 8; ++r) v[r] = x[sq_pad(8 * q + r) * ST];  // thread q is k1 here
     dft8_regs(v);
   }
   __syncthreads();
   if (active) {
 #pragma unroll
-    for (int k = 0; k < 8; ++k) x[sq_pad(q + 8 * k)] = v[k];
+    for (int k = 0; k < 8; ++k) x[sq_pad(q + 8 * k) * ST] = v[k];
   }
   __syncthreads();
+}
+
+// A complex double as double-float pairs: hi = RN(x), lo = RN(x - hi).
+__device__ __forceinline__ float4 split_df(double2 v) {
+  const float rh = __double2float_rn(v.x), ih = __double2float_rn(v.y);
+  return float4{rh, __double2float_rn(v.x - (double)rh), ih, __double2float_rn(v.y - (double)ih)};
+}
+
+// Once per large step: each square's expansion.  Block (square, function): the square's
+// u and u_t as one complex field z = u + i u_t, continued along rows, then columns, to
+// P x P; its 2D DFT, normalised, stored transposed: Z[l][m] (l: x frequency).
+// DF: Z as double-float pairs (float4 re hi, re lo, im hi, im lo) for k_sq_eval_df.
+// One padded buffer holds the field and both transforms in place: value (y, x) at
+// sq_pad(y) kSqRow + sq_pad(x).  The 64-point DFTs (fft64, 8 threads each) run along x at
+// unit stride and along y at stride kSqRow; kSqRow is odd in 16-byte units, so both
+// access patterns of fft64 (consecutive and every 8th element) spread over all banks in
+// either direction.  83 KB of shared memory allow two blocks per SM.
+constexpr int kSqRow = 73;                       // row stride (complex values)
+constexpr int kSqRows = 64 + 64 / 8 - 1;         // sq_pad(63) + 1 rows
+constexpr size_t kSqForwardSmem = (size_t)kSqRows * kSqRow * sizeof(double2);
+
+template <bool DF>
+__global__ void __launch_bounds__(kSqThreads, 2) k_sq_forward(
+    int n_side, int C, int d, int nx, int64_t grid_stride, int n_f,
+    const int32_t* __restrict__ origin, const double* __restrict__ A,
+    const double* __restrict__ Q, const double2* __restrict__ tw, const double* __restrict__ u,
+    const double* __restrict__ ut, double2* __restrict__ Z) {
+  constexpr int P = kSqP;  // n_side + C = P (the host checks)
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  double2* buf = reinterpret_cast<double2*>(smem_raw);
+  const int sq = blockIdx.x, f = blockIdx.y;
+  const int j0 = __ldg(origin + 2 * sq), i0 = __ldg(origin + 2 * sq + 1);
+  const double* uf = u + (size_t)f * grid_stride;
+  const double* tf = ut + (size_t)f * grid_stride;
+  for (int t = threadIdx.x; t < n_side * n_side; t += blockDim.x) {
+    const int y = t / n_side, x = t - y * n_side;
+    const size_t g = (size_t)(j0 + y) * nx + (i0 + x);
+    buf[sq_pad(y) * kSqRow + sq_pad(x)] = double2{uf[g], tf[g]};
+  }
+  __syncthreads();
+  const auto along_x = [](int i) { return sq_pad(i); };
+  const auto along_y = [](int i) { return sq_pad(i) * kSqRow; };
+  for (int t = threadIdx.x; t < n_side * C; t += blockDim.x) {  // rows
+    const int y = t / C, k = t - y * C;
+    fc1d_continue(buf + sq_pad(y) * kSqRow, along_x, n_side, C, d, A, Q, k);
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < P * C; t += blockDim.x) {  // columns
+    const int x = t / C, k = t - x * C;
+    fc1d_continue(buf + sq_pad(x), along_y, n_side, C, d, A, Q, k);
+  }
+  __syncthreads();
+  const int g = threadIdx.x >> 3, q = threadIdx.x & 7;
+  constexpr int G = kSqThreads / 8;  // transforms per call
+#pragma unroll 1
+  for (int y0 = 0; y0 < P; y0 += G)  // along x: (y, l)
+    fft64<1>(buf + sq_pad(y0 + g) * kSqRow, q, y0 + g < P, tw);
+#pragma unroll 1
+  for (int l0 = 0; l0 < P; l0 += G)  // along y: (m, l)
+    fft64<kSqRow>(buf + sq_pad(l0 + g), q, l0 + g < P, tw);
+  const double sc = 1.0 / ((double)P * P);
+  double2* dst = Z + ((size_t)sq * n_f + f) * P * P;
+  for (int t = threadIdx.x; t < P * P; t += blockDim.x) {
+    const int l = t / P, m = t - l * P;
+    const double2 w = buf[sq_pad(m) * kSqRow + sq_pad(l)];
+    const double2 v = double2{w.x * sc, w.y * sc};
+    if constexpr (DF) reinterpret_cast<float4*>(dst)[t] = split_df(v);
+    else dst[t] = v;
+  }
 }
 
 constexpr int kSqPad = 72;        // padded length of a 64-point sequence
@@ -1176,7 +1185,7 @@ extern "C" fc2d_status fc2d_forward_wave(fc2d_plan_t p, int n_f, double c, int n
   double2* sqZ = reinterpret_cast<double2*>(base + b_spec + b_inter + 2 * b_grid + 4 * b_ub + b_zero);
   double2* sqT = reinterpret_cast<double2*>(base + b_spec + b_inter + 2 * b_grid + 4 * b_ub + b_zero + b_sqz);
   cudaMemsetAsync(zero, 0, (size_t)n_f * nb * 8, s);
-  const size_t sm_sq = 2 * (size_t)P * P * sizeof(double2);
+  const size_t sm_sq = kSqForwardSmem;
   int max_rows = 0;
   if (sq)
     for (int k = 0; k < n_sq; ++k) {
@@ -1249,7 +1258,7 @@ extern "C" fc2d_status fc2d_forward_wave(fc2d_plan_t p, int n_f, double c, int n
       ProfScope ps(p, "sq_forward", s);
       const SquareSet& H = sq->host;
       auto kf = df ? k_sq_forward<true> : k_sq_forward<false>;
-      kf<<<dim3(n_sq, n_f), kSqThreads, sm_sq, s>>>(P, 2 * H.a + 1, H.C, H.d, nx, NN, n_f,
+      kf<<<dim3(n_sq, n_f), kSqThreads, sm_sq, s>>>(2 * H.a + 1, H.C, H.d, nx, NN, n_f,
                                                      sq->origin, sq->A, sq->Q, sq->tw, u, ut, sqZ);
     }
     if ((st = wave_spectra(p, n_f, u, g_dir ? gat(m0) : zero, ut, gt_dir ? gtat(j) : zero, spec, s)))
